@@ -1,0 +1,723 @@
+/*
+ * Plain, slow CPU oracle for SPAI-GMRES-IR (Carson & Khan, arXiv 2202.10204).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code, header, table or helper with the CUDA path; it is written from the
+ * paper's definitions:
+ *   - Section 2.2, eq. (fronormmin) and (redprob): column-wise Frobenius
+ *     least squares on the shadow I_k of the pattern J_k;
+ *   - Algorithm 1 (Grote-Huckle / Sedlacek variant): fixed or adaptive
+ *     pattern, rho_jk scores, mean-acceptance, up to beta additions per step;
+ *   - Section 4 (experimental set-up): SPAI is run on A^T D where D scales
+ *     every column of A^T to max-abs 1, and P = M^T D;
+ *   - Algorithm 3 (SPAI-GMRES-IR): x0 = P b in u_f, residual in u_r,
+ *     left-preconditioned MGS-GMRES in u_g with products in u_p, update in u.
+ *
+ * Arithmetic model.  Double is native.  Quad is _Float128 (software, IEEE
+ * binary128).  Single is obtained by rounding a double result to float, and
+ * half by a hand-written round-to-nearest-even "chop" to 11 significant bits
+ * with exponent range [-14, 15], gradual underflow to 2^-24 and overflow to
+ * +-Inf (the paper simulates half with the chop library, Section 4).  A
+ * double result of +,-,*,/,sqrt on operands of precision p (p = half or
+ * single) rounded to p equals the correctly rounded p-result, because 53 >=
+ * 2*24 + 2.  The file must be compiled with -ffp-contract=off.
+ *
+ * Two SPAI arithmetic modes:
+ *   MODE_PEROP : every operation rounded to u_f (the paper's model);
+ *   MODE_ACC32 : at u_f = half, stored values are rounded to half but every
+ *                inner product / norm is accumulated in binary32 and rounded
+ *                to half once (the FP16-storage / FP32-accumulate model).  At
+ *                u_f = single or double the two modes coincide.
+ *
+ * Readings of points where the paper is silent or garbled (each one is a
+ * parameter or a documented constant):
+ *   R1  L_k = { l in I_k : s_l != 0 }, and I_k always contains k.
+ *   R2  N_l = { j : b_lj != 0 } \ J_k (row l of B), J~_k = union of N_l.
+ *   R3  rho_j^2 = max(0, ||s||^2 - (s^T b_j)^2 / ||b_j||^2) with b_j the full
+ *       column j of B (rho_restricted=1: b_j restricted to I_k).  The
+ *       selection statistics (rho^2, the mean) are accumulated in binary32
+ *       at u_f = half, in u_f otherwise.
+ *   R4  mean over J~_k; acceptable = rho_j <= mean; add the
+ *       min(beta, max_fill - |J_k|) acceptable indices with smallest rho,
+ *       ties broken by the smaller index.
+ *   R5  at most alpha + 1 least-squares solves; no augmentation after the
+ *       last one.
+ *   R6  |J_k| <= max_fill; an initial pattern larger than the cap keeps k,
+ *       then the indices nearest to k (ties: smaller index).
+ *   R7  MGS-GMRES, x0 = 0, no restart, stop when |g_{j+1}| / beta <= tau;
+ *       Givens rotations, H, g and y in double.
+ *   R8  IR stop: before step i, nbe_i = ||r_i||_inf / (||A||_inf ||x_i||_inf
+ *       + ||b||_inf) <= stop_tol; at most i_max GMRES solves.
+ *   R10 pattern(A) / pattern(A^2) initial patterns: J_k = nonzero rows of
+ *       column k of A (resp. A^2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PH 0 /* half,   u = 2^-11  */
+#define PS 1 /* single, u = 2^-24  */
+#define PD 2 /* double, u = 2^-53  */
+#define PQ 3 /* quad,   u = 2^-113 */
+
+#define MODE_PEROP 0
+#define MODE_ACC32 1
+
+#define PAT_IDENTITY 0
+#define PAT_A 1
+#define PAT_A2 2
+
+/* column flags */
+#define CF_CONVERGED 1   /* ||s|| <= eps reached                */
+#define CF_FILLCAP 2     /* stopped because |J_k| hit max_fill  */
+#define CF_ALPHA 4       /* stopped because alpha steps done    */
+#define CF_NOCAND 8      /* no acceptable candidate to add      */
+#define CF_SINGULAR 16   /* a zero pivot in R                   */
+#define CF_NONFINITE 32  /* Inf/NaN appeared (overflow in u_f)  */
+
+/* IR status flags */
+#define IR_CONVERGED 1
+#define IR_MAXSTEPS 2
+#define IR_BREAKDOWN 4
+#define IR_NONFINITE 8
+
+/* ------------------------------------------------------------------ */
+/* Rounding to a precision (Table 1)                                   */
+/* ------------------------------------------------------------------ */
+
+/* Round a double to IEEE binary16, round-to-nearest-even, written out from
+ * the format's definition: 11 significant bits, normal exponents [-14, 15],
+ * subnormal quantum 2^-24, largest finite 65504. */
+double orc_chop_half(double x)
+{
+    if (isnan(x)) return x;
+    double ax = fabs(x);
+    if (ax == 0.0) return x;
+    /* 65520 is the midpoint between 65504 and 2^16; ties go to the even
+     * neighbour 2^16, which overflows. */
+    if (ax >= 65520.0) return x > 0 ? INFINITY : -INFINITY;
+    int e;
+    frexp(ax, &e);          /* ax = f * 2^e, f in [0.5, 1) => leading bit 2^(e-1) */
+    int lead = e - 1;
+    if (lead < -14) lead = -14; /* subnormal range: fixed quantum 2^-24 */
+    double quantum = ldexp(1.0, lead - 10);
+    double q = rint(ax / quantum) * quantum; /* rint: nearest-even */
+    return x < 0 ? -q : q;
+}
+
+static double rnd(double x, int p)
+{
+    switch (p) {
+    case PH: return orc_chop_half(x);
+    case PS: return (double)(float)x;
+    default: return x;
+    }
+}
+
+double orc_round(double x, int p) { return rnd(x, p); }
+
+/* ------------------------------------------------------------------ */
+/* Inner products in a precision under a mode                          */
+/* ------------------------------------------------------------------ */
+
+/* sum_i x[i*sx] * y[i*sy] computed in precision p. */
+static double dot_p(const double* x, int sx, const double* y, int sy, int len, int p, int mode)
+{
+    if (p == PH && mode == MODE_ACC32) {
+        float acc = 0.0f;
+        for (int i = 0; i < len; i++) {
+            float t = (float)x[(size_t)i * sx] * (float)y[(size_t)i * sy];
+            acc = acc + t;
+        }
+        return orc_chop_half((double)acc);
+    }
+    double acc = 0.0;
+    for (int i = 0; i < len; i++) {
+        double t = rnd(x[(size_t)i * sx] * y[(size_t)i * sy], p);
+        acc = rnd(acc + t, p);
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Dense least squares by Householder QR (Algorithm 1, QR + solve)     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Solve min || ebar - Abar mbar ||_2 for Abar (m x nc, column-major, values
+ * already in u_f) by Householder QR in precision p under mode, then
+ * mbar = R^{-1} (Q^T ebar)(1:nc) by back substitution, then the explicit
+ * residual sbar = Abar mbar - ebar and ||sbar||_2 (Algorithm 1, the QR,
+ * solve and residual lines).  Reflector: v = x - alpha e_1 with
+ * alpha = -sign(x_1) ||x||, sign(0) = +1; H = I - 2 v v^T / (v^T v).
+ * Returns flags (CF_SINGULAR / CF_NONFINITE).  sbar may be NULL.
+ */
+int orc_dense_ls(int m, int nc, const double* Abar, const double* ebar, int p, int mode,
+                 double* mbar, double* sbar, double* snorm)
+{
+    int flags = 0;
+    double* W = (double*)malloc(sizeof(double) * (size_t)m * (nc + 1)); /* [Abar | ebar] */
+    double* v = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double* s = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    memcpy(W, Abar, sizeof(double) * (size_t)m * nc);
+    memcpy(W + (size_t)m * nc, ebar, sizeof(double) * (size_t)m);
+    int steps = nc < m ? nc : m;
+    for (int c = 0; c < steps; c++) {
+        double* x = W + (size_t)c * m + c;
+        int len = m - c;
+        double sig2 = dot_p(x, 1, x, 1, len, p, mode);
+        double nrm = rnd(sqrt(sig2), p);
+        if (nrm == 0.0) continue; /* zero column: H = I, R(c,c) = 0 */
+        double alpha = x[0] >= 0.0 ? -nrm : nrm;
+        for (int i = 0; i < len; i++) v[i] = x[i];
+        v[0] = rnd(x[0] - alpha, p);
+        double vtv = dot_p(v, 1, v, 1, len, p, mode);
+        for (int t = c + 1; t <= nc; t++) { /* trailing columns and ebar */
+            double* a = W + (size_t)t * m + c;
+            double sv = dot_p(v, 1, a, 1, len, p, mode);
+            double f = rnd(rnd(2.0 * sv, p) / vtv, p);
+            for (int i = 0; i < len; i++) a[i] = rnd(a[i] - rnd(f * v[i], p), p);
+        }
+        x[0] = alpha;
+        for (int i = 1; i < len; i++) x[i] = 0.0;
+    }
+    /* back substitution R mbar = (Q^T ebar)(1:nc) */
+    const double* y = W + (size_t)m * nc;
+    for (int c = nc - 1; c >= 0; c--) {
+        if (c >= m) { mbar[c] = 0.0; flags |= CF_SINGULAR; continue; }
+        double acc = y[c];
+        /* acc - sum_{t>c} R(c,t) mbar(t), accumulated per mode */
+        double sum = 0.0;
+        if (nc - 1 - c > 0) sum = dot_p(W + (size_t)(c + 1) * m + c, m, mbar + c + 1, 1, nc - 1 - c, p, mode);
+        acc = rnd(acc - sum, p);
+        double rcc = W[(size_t)c * m + c];
+        if (rcc == 0.0) { mbar[c] = 0.0; flags |= CF_SINGULAR; continue; }
+        mbar[c] = rnd(acc / rcc, p);
+    }
+    /* explicit residual sbar = Abar mbar - ebar with the original Abar */
+    for (int i = 0; i < m; i++) {
+        double am = dot_p(Abar + i, m, mbar, 1, nc, p, mode);
+        s[i] = rnd(am - ebar[i], p);
+    }
+    *snorm = rnd(sqrt(dot_p(s, 1, s, 1, m, p, mode)), p);
+    if (sbar) memcpy(sbar, s, sizeof(double) * (size_t)m);
+    for (int c = 0; c < nc; c++) if (!isfinite(mbar[c])) flags |= CF_NONFINITE;
+    if (!isfinite(*snorm)) flags |= CF_NONFINITE;
+    free(W); free(v); free(s);
+    return flags;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sparse helpers                                                      */
+/* ------------------------------------------------------------------ */
+
+static int cmp_int(const void* a, const void* b)
+{
+    int x = *(const int*)a, y = *(const int*)b;
+    return (x > y) - (x < y);
+}
+
+/* sort ascending and drop duplicates; returns the new length */
+static int sort_unique(int* v, int len)
+{
+    if (len <= 1) return len;
+    qsort(v, (size_t)len, sizeof(int), cmp_int);
+    int w = 1;
+    for (int i = 1; i < len; i++) if (v[i] != v[w - 1]) v[w++] = v[i];
+    return w;
+}
+
+static int find_sorted(const int* v, int len, int key)
+{
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        if (v[mid] == key) return mid;
+        if (v[mid] < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* structure of A^T (column lists of A): colptr[n+1], rowidx[nnz] sorted */
+static void transpose_structure(int n, const int64_t* rp, const int* ci, int64_t* cp, int* ri)
+{
+    for (int j = 0; j <= n; j++) cp[j] = 0;
+    for (int i = 0; i < n; i++)
+        for (int64_t q = rp[i]; q < rp[i + 1]; q++) cp[ci[q] + 1]++;
+    for (int j = 0; j < n; j++) cp[j + 1] += cp[j];
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int j = 0; j < n; j++) cur[j] = cp[j];
+    for (int i = 0; i < n; i++) /* rows in increasing order => sorted lists */
+        for (int64_t q = rp[i]; q < rp[i + 1]; q++) ri[cur[ci[q]]++] = i;
+    free(cur);
+}
+
+/* order for the fill cap (R6): k first, then by |j-k|, then by j */
+static int g_cap_k;
+static int cmp_cap(const void* a, const void* b)
+{
+    int x = *(const int*)a, y = *(const int*)b;
+    long dx = labs((long)x - g_cap_k), dy = labs((long)y - g_cap_k);
+    if (dx != dy) return (dx > dy) - (dx < dy);
+    return (x > y) - (x < y);
+}
+
+static int apply_cap(int* J, int len, int k, int max_fill)
+{
+    if (len <= max_fill) return len;
+    g_cap_k = k;
+    qsort(J, (size_t)len, sizeof(int), cmp_cap);
+    len = max_fill;
+    qsort(J, (size_t)len, sizeof(int), cmp_int);
+    return len;
+}
+
+/* ------------------------------------------------------------------ */
+/* SPAI (Algorithm 1 on B = A^T D, P = M^T D)                           */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int init;            /* PAT_IDENTITY, PAT_A, PAT_A2 */
+    int adaptive;        /* 0 fixed pattern, 1 Grote-Huckle augmentation */
+    double eps;          /* column tolerance */
+    int alpha, beta;     /* alpha < 0 => ceil(n / beta) */
+    int max_fill;        /* cap on |J_k| */
+    int uf;              /* precision of the construction */
+    int mode;            /* MODE_PEROP / MODE_ACC32 */
+    int rho_restricted;  /* R3 literal reading */
+    int scale;           /* 1: run on A^T D (Section 4); 0: on A^T */
+} orc_spai_opts;
+
+/* Candidate scores rho_j (Algorithm 1, rho_jk line; reading R3).
+ * s: residual on I (length m, in u_f); cand: candidate indices; B's column j
+ * is row j of A times d_j.  Writes rho (length ncand). */
+void orc_rho(int n, const int64_t* rp, const int* ci, const double* val, const double* d,
+             int m, const int* I, const double* s, int ncand, const int* cand, int uf,
+             int rho_restricted, double* rho)
+{
+    (void)n;
+    int ps = (uf == PH) ? PS : uf; /* statistics precision (R3) */
+    double s2 = 0.0;
+    for (int i = 0; i < m; i++) s2 = rnd(s2 + rnd(s[i] * s[i], ps), ps);
+    for (int c = 0; c < ncand; c++) {
+        int j = cand[c];
+        double num = 0.0, den = 0.0;
+        for (int64_t q = rp[j]; q < rp[j + 1]; q++) {
+            double bij = rnd(val[q] * d[j], uf); /* b_ij = a_ji d_j in u_f */
+            int pos = find_sorted(I, m, ci[q]);
+            if (pos >= 0) num = rnd(num + rnd(s[pos] * bij, ps), ps);
+            if (!rho_restricted || pos >= 0) den = rnd(den + rnd(bij * bij, ps), ps);
+        }
+        double r2 = s2;
+        if (den > 0.0) r2 = rnd(s2 - rnd(rnd(num * num, ps) / den, ps), ps);
+        if (r2 < 0.0) r2 = 0.0;
+        rho[c] = rnd(sqrt(r2), ps);
+    }
+}
+
+/* Selection (Algorithm 1, mean and "add up to beta" lines; reading R4).
+ * Returns the number selected; sel receives the chosen indices. */
+int orc_select(int ncand, const int* cand, const double* rho, int uf, int nmax, int* sel)
+{
+    if (ncand <= 0 || nmax <= 0) return 0;
+    int ps = (uf == PH) ? PS : uf;
+    double sum = 0.0;
+    for (int c = 0; c < ncand; c++) sum = rnd(sum + rho[c], ps);
+    double mean = rnd(sum / (double)ncand, ps);
+    int* used = (int*)calloc((size_t)ncand, sizeof(int));
+    int nsel = 0;
+    for (int t = 0; t < nmax; t++) {
+        int best = -1;
+        for (int c = 0; c < ncand; c++) {
+            if (used[c] || !(rho[c] <= mean)) continue;
+            if (best < 0 || rho[c] < rho[best] || (rho[c] == rho[best] && cand[c] < cand[best])) best = c;
+        }
+        if (best < 0) break;
+        used[best] = 1;
+        sel[nsel++] = cand[best];
+    }
+    free(used);
+    return nsel;
+}
+
+/*
+ * Build the SPAI preconditioner P = M^T D.
+ * Inputs: CSR A (n, rp[n+1], ci[nnz], val[nnz]), options.
+ * Outputs (caller-allocated):
+ *   d[n]                 scaling (1 if !scale)
+ *   Jcnt[n]              |J_k|
+ *   Jidx[n*max_fill]     J_k (sorted), padded
+ *   mval[n*max_fill]     mbar_k in u_f (padded)
+ *   colres[n]            ||sbar_k|| as computed in u_f
+ *   colres64[n]          ||e_k - B(:,J_k) mbar_k||_2 re-evaluated in double
+ *   flags[n]             CF_* flags
+ *   nsolve[n]            least-squares solves performed for column k
+ *   Icnt[n]              |I_k| of the last solve
+ * Column subset: if cols != NULL only those ncols columns are computed.
+ */
+int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const orc_spai_opts* o,
+             int ncols, const int* cols, double* d, int* Jcnt, int* Jidx, double* mval,
+             double* colres, double* colres64, int* flags, int* nsolve, int* Icnt)
+{
+    int64_t nnz = rp[n];
+    int64_t* cp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int* ri = (int*)malloc(sizeof(int) * (size_t)(nnz > 0 ? nnz : 1));
+    transpose_structure(n, rp, ci, cp, ri);
+    /* scaling D: d_j = 1 / max_i |a_ji| (Section 4: every column of A^T,
+     * i.e. every row of A, gets max-abs 1) */
+    for (int j = 0; j < n; j++) {
+        double mx = 0.0;
+        for (int64_t q = rp[j]; q < rp[j + 1]; q++) if (fabs(val[q]) > mx) mx = fabs(val[q]);
+        d[j] = o->scale ? (mx > 0.0 ? 1.0 / mx : 1.0) : 1.0;
+    }
+    int beta = o->beta;
+    int alpha = o->alpha < 0 ? (n + beta - 1) / (beta > 0 ? beta : 1) : o->alpha;
+    int F = o->max_fill;
+    int total = ncols > 0 && cols ? ncols : n;
+    /* scratch large enough for any single column */
+    int maxrow = 0, maxcol = 0;
+    for (int i = 0; i < n; i++) if (rp[i + 1] - rp[i] > maxrow) maxrow = (int)(rp[i + 1] - rp[i]);
+    for (int j = 0; j < n; j++) if (cp[j + 1] - cp[j] > maxcol) maxcol = (int)(cp[j + 1] - cp[j]);
+    size_t capI = (size_t)F * maxrow + 2;
+    size_t capJ0 = (size_t)maxcol * maxcol + (size_t)F + 2;
+    size_t capC = capI * (size_t)(maxcol + 1) + 2;
+    int* J = (int*)malloc(sizeof(int) * (capJ0 > (size_t)F ? capJ0 : (size_t)F + 2));
+    int* I = (int*)malloc(sizeof(int) * capI);
+    int* cand = (int*)malloc(sizeof(int) * capC);
+    double* rho = (double*)malloc(sizeof(double) * capC);
+    int* sel = (int*)malloc(sizeof(int) * (size_t)(beta + 1));
+    double* Abar = (double*)malloc(sizeof(double) * capI * (size_t)F);
+    double* ebar = (double*)malloc(sizeof(double) * capI);
+    double* mb = (double*)malloc(sizeof(double) * (size_t)F);
+    double* sb = (double*)malloc(sizeof(double) * capI);
+    for (int t = 0; t < total; t++) {
+        int k = (cols && ncols > 0) ? cols[t] : t;
+        /* initial pattern J_k (R10), capped (R6) */
+        int nj = 0;
+        if (o->init == PAT_IDENTITY) {
+            J[nj++] = k;
+        } else if (o->init == PAT_A) {
+            for (int64_t q = cp[k]; q < cp[k + 1]; q++) J[nj++] = ri[q];
+        } else {
+            for (int64_t q = cp[k]; q < cp[k + 1]; q++) {
+                int i = ri[q];
+                for (int64_t q2 = cp[i]; q2 < cp[i + 1]; q2++) J[nj++] = ri[q2];
+            }
+        }
+        nj = sort_unique(J, nj);
+        nj = apply_cap(J, nj, k, F);
+        int fl = 0, ns = 0, m = 0;
+        double snorm = 0.0;
+        for (int step = 0; step <= alpha; step++) {
+            /* shadow I_k = union of nonzero columns of rows j in J_k, plus k */
+            m = 0;
+            for (int c = 0; c < nj; c++)
+                for (int64_t q = rp[J[c]]; q < rp[J[c] + 1]; q++) if (val[q] != 0.0) I[m++] = ci[q];
+            I[m++] = k;
+            m = sort_unique(I, m);
+            /* Abar = B(I_k, J_k) in u_f, ebar = e_k(I_k) */
+            for (size_t z = 0; z < (size_t)m * nj; z++) Abar[z] = 0.0;
+            for (int c = 0; c < nj; c++) {
+                int j = J[c];
+                for (int64_t q = rp[j]; q < rp[j + 1]; q++) {
+                    if (val[q] == 0.0) continue;
+                    int pos = find_sorted(I, m, ci[q]);
+                    Abar[(size_t)c * m + pos] = rnd(val[q] * d[j], o->uf);
+                }
+            }
+            for (int i = 0; i < m; i++) ebar[i] = (I[i] == k) ? 1.0 : 0.0;
+            fl &= ~(CF_SINGULAR | CF_NONFINITE);
+            fl |= orc_dense_ls(m, nj, Abar, ebar, o->uf, o->mode, mb, sb, &snorm);
+            ns++;
+            if (snorm <= o->eps) { fl |= CF_CONVERGED; break; }
+            if (!o->adaptive) break;
+            if (step == alpha) { fl |= CF_ALPHA; break; }
+            if (nj >= F) { fl |= CF_FILLCAP; break; }
+            /* L_k (R1) and the candidate set J~_k (R2) */
+            int nc = 0;
+            for (int i = 0; i < m; i++) {
+                if (sb[i] == 0.0) continue;
+                int l = I[i];
+                for (int64_t q = cp[l]; q < cp[l + 1]; q++) {
+                    int j = ri[q];
+                    if (find_sorted(J, nj, j) < 0) cand[nc++] = j;
+                }
+            }
+            nc = sort_unique(cand, nc);
+            if (nc == 0) { fl |= CF_NOCAND; break; }
+            orc_rho(n, rp, ci, val, d, m, I, sb, nc, cand, o->uf, o->rho_restricted, rho);
+            int room = F - nj;
+            int nadd = orc_select(nc, cand, rho, o->uf, beta < room ? beta : room, sel);
+            if (nadd == 0) { fl |= CF_NOCAND; break; }
+            for (int a = 0; a < nadd; a++) J[nj++] = sel[a];
+            nj = sort_unique(J, nj);
+        }
+        Jcnt[k] = nj;
+        for (int c = 0; c < F; c++) {
+            Jidx[(size_t)k * F + c] = c < nj ? J[c] : -1;
+            mval[(size_t)k * F + c] = c < nj ? mb[c] : 0.0;
+        }
+        colres[k] = snorm;
+        flags[k] = fl;
+        nsolve[k] = ns;
+        Icnt[k] = m;
+        /* true residual in double: || e_k - B(:,J) mbar || over I_k */
+        double acc = 0.0;
+        for (int i = 0; i < m; i++) {
+            double bm = 0.0;
+            for (int c = 0; c < nj; c++) {
+                int j = J[c];
+                for (int64_t q = rp[j]; q < rp[j + 1]; q++)
+                    if (ci[q] == I[i]) bm += val[q] * d[j] * mb[c];
+            }
+            double e = (I[i] == k) ? 1.0 : 0.0;
+            acc += (e - bm) * (e - bm);
+        }
+        colres64[k] = sqrt(acc);
+    }
+    free(cp); free(ri); free(J); free(I); free(cand); free(rho); free(sel);
+    free(Abar); free(ebar); free(mb); free(sb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sparse matrix-vector products in a precision                        */
+/* ------------------------------------------------------------------ */
+
+/* y = M x with M's values and x rounded to p, products and sums in p
+ * (acc32 at p = half: products and sums in binary32), y rounded to p. */
+static void spmv_p(int n, const int64_t* rp, const int* ci, const double* mv, const double* x,
+                   int p, int mode, double* y)
+{
+    for (int i = 0; i < n; i++) {
+        if (p == PH && mode == MODE_ACC32) {
+            float acc = 0.0f;
+            for (int64_t q = rp[i]; q < rp[i + 1]; q++) {
+                float t = (float)orc_chop_half(mv[q]) * (float)orc_chop_half(x[ci[q]]);
+                acc = acc + t;
+            }
+            y[i] = orc_chop_half((double)acc);
+        } else {
+            double acc = 0.0;
+            for (int64_t q = rp[i]; q < rp[i + 1]; q++)
+                acc = rnd(acc + rnd(rnd(mv[q], p) * rnd(x[ci[q]], p), p), p);
+            y[i] = acc;
+        }
+    }
+}
+
+/* r = b - A x in precision ur, stored in precision u (Algorithm 3 residual) */
+static void residual_ur(int n, const int64_t* rp, const int* ci, const double* av, const double* b,
+                        const double* x, int ur, int u, double* r)
+{
+    for (int i = 0; i < n; i++) {
+        if (ur == PQ) {
+            _Float128 s = (_Float128)b[i];
+            for (int64_t q = rp[i]; q < rp[i + 1]; q++) s = s - (_Float128)av[q] * (_Float128)x[ci[q]];
+            r[i] = rnd((double)s, u);
+        } else {
+            double s = b[i];
+            for (int64_t q = rp[i]; q < rp[i + 1]; q++) s = rnd(s - rnd(av[q] * x[ci[q]], ur), ur);
+            r[i] = rnd(s, u);
+        }
+    }
+}
+
+static double norm_inf(int n, const double* x)
+{
+    double m = 0.0;
+    for (int i = 0; i < n; i++) if (fabs(x[i]) > m) m = fabs(x[i]);
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Left-preconditioned MGS-GMRES (Algorithm 3, GMRES line; reading R7)  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int ug, up;      /* GMRES working precision, product precision */
+    double tau;      /* relative tolerance on the preconditioned residual */
+    int maxit;       /* iteration cap */
+} orc_gmres_opts;
+
+/*
+ * Solve (P A) d = P r from d0 = 0.  P may be NULL (P = I).  The result d is
+ * in u_g precision values.  Returns the number of iterations; *breakdown is
+ * set when h_{j+1,j} = 0.  relres receives |g_k| / beta (or 0).
+ */
+int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
+              const int64_t* prp, const int* pci, const double* pv,
+              const double* r, const orc_gmres_opts* o, double* d, int* breakdown, double* relres)
+{
+    int ug = o->ug, up = o->up, K = o->maxit;
+    double* t = (double*)malloc(sizeof(double) * (size_t)n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    double** V = (double**)calloc((size_t)K + 1, sizeof(double*));
+    double* H = (double*)calloc((size_t)(K + 1) * (K + 1), sizeof(double)); /* H[i*(K)+j] row-major (K+1) x K */
+    double* cs = (double*)calloc((size_t)K + 1, sizeof(double));
+    double* sn = (double*)calloc((size_t)K + 1, sizeof(double));
+    double* g = (double*)calloc((size_t)K + 2, sizeof(double));
+    *breakdown = 0;
+    /* z = P r in u_p, stored in u_g */
+    if (prp) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, w);
+    else for (int i = 0; i < n; i++) w[i] = rnd(r[i], up);
+    for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
+    double beta = rnd(sqrt(dot_p(w, 1, w, 1, n, ug, MODE_PEROP)), ug);
+    for (int i = 0; i < n; i++) d[i] = 0.0;
+    *relres = 0.0;
+    if (beta == 0.0 || K == 0) {
+        free(t); free(w); free(V); free(H); free(cs); free(sn); free(g);
+        return 0;
+    }
+    V[0] = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i < n; i++) V[0][i] = rnd(w[i] / beta, ug);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < K; j++) {
+        /* w = P (A v_j), both products in u_p */
+        spmv_p(n, arp, aci, av, V[j], up, MODE_PEROP, t);
+        if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
+        else for (int i = 0; i < n; i++) w[i] = t[i];
+        for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
+        /* modified Gram-Schmidt in u_g */
+        double* h = (double*)calloc((size_t)j + 2, sizeof(double));
+        for (int i = 0; i <= j; i++) {
+            double hij = dot_p(V[i], 1, w, 1, n, ug, MODE_PEROP);
+            h[i] = hij;
+            for (int q = 0; q < n; q++) w[q] = rnd(w[q] - rnd(hij * V[i][q], ug), ug);
+        }
+        h[j + 1] = rnd(sqrt(dot_p(w, 1, w, 1, n, ug, MODE_PEROP)), ug);
+        double hnext = h[j + 1];
+        /* Givens rotations in double */
+        for (int i = 0; i < j; i++) {
+            double tmp = cs[i] * h[i] + sn[i] * h[i + 1];
+            h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+            h[i] = tmp;
+        }
+        double den = sqrt(h[j] * h[j] + h[j + 1] * h[j + 1]);
+        if (den == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+        else { cs[j] = h[j] / den; sn[j] = h[j + 1] / den; }
+        h[j] = den;
+        h[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        for (int i = 0; i <= j; i++) H[(size_t)i * K + j] = h[i];
+        free(h);
+        k = j + 1;
+        *relres = fabs(g[j + 1]) / beta;
+        if (hnext == 0.0) { *breakdown = 1; break; }
+        V[j + 1] = (double*)malloc(sizeof(double) * (size_t)n);
+        for (int i = 0; i < n; i++) V[j + 1][i] = rnd(w[i] / hnext, ug);
+        if (*relres <= o->tau) break;
+    }
+    /* y = R^{-1} g(0:k) in double, d = V_k y in u_g */
+    double* y = (double*)calloc((size_t)k + 1, sizeof(double));
+    for (int i = k - 1; i >= 0; i--) {
+        double acc = g[i];
+        for (int l = i + 1; l < k; l++) acc -= H[(size_t)i * K + l] * y[l];
+        y[i] = H[(size_t)i * K + i] != 0.0 ? acc / H[(size_t)i * K + i] : 0.0;
+    }
+    for (int q = 0; q < n; q++) {
+        double acc = 0.0;
+        for (int i = 0; i < k; i++) acc = rnd(acc + rnd(V[i][q] * rnd(y[i], ug), ug), ug);
+        d[q] = acc;
+    }
+    for (int i = 0; i <= K; i++) free(V[i]);
+    free(y); free(t); free(w); free(V); free(H); free(cs); free(sn); free(g);
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* SPAI-GMRES-IR (Algorithm 3)                                         */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int uf, u, ug, up, ur;  /* the five precisions */
+    int mode;               /* arithmetic mode of the u_f product x0 = P b */
+    double tau;             /* GMRES tolerance */
+    int gmres_maxit;        /* per GMRES solve */
+    int imax;               /* maximum number of refinement steps */
+    double stop_tol;        /* R8 backward-error threshold */
+} orc_ir_opts;
+
+/*
+ * Inputs: CSR A (values double), CSR P (structure + values pv_up for u_p use,
+ * pv_uf for the u_f product; P may be NULL for no preconditioner), b.
+ * Outputs: x[n] (values in precision u), its[imax] GMRES iterations per
+ * step, nbe[imax+1] backward error before each step, *steps, status flags.
+ */
+int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
+                 const int64_t* prp, const int* pci, const double* pv_up, const double* pv_uf,
+                 const double* b, const orc_ir_opts* o, double* x, int* its, double* nbe,
+                 int* steps)
+{
+    int status = 0;
+    double* r = (double*)malloc(sizeof(double) * (size_t)n);
+    double* dd = (double*)malloc(sizeof(double) * (size_t)n);
+    double* ur_b = (double*)malloc(sizeof(double) * (size_t)n);
+    /* ||A||_inf */
+    double anorm = 0.0;
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t q = arp[i]; q < arp[i + 1]; q++) s += fabs(av[q]);
+        if (s > anorm) anorm = s;
+    }
+    double bnorm = norm_inf(n, b);
+    /* x0 = P b in u_f, stored in u (P = I: x0 = b rounded) */
+    if (prp) spmv_p(n, prp, pci, pv_uf, b, o->uf, o->mode, x);
+    else for (int i = 0; i < n; i++) x[i] = rnd(b[i], o->uf);
+    for (int i = 0; i < n; i++) x[i] = rnd(x[i], o->u);
+    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit };
+    int i;
+    *steps = 0;
+    for (i = 0; i <= o->imax; i++) {
+        residual_ur(n, arp, aci, av, b, x, o->ur, o->u, r);
+        double rn = norm_inf(n, r), xn = norm_inf(n, x);
+        double den = anorm * xn + bnorm;
+        nbe[i] = den > 0.0 ? rn / den : 0.0;
+        if (!isfinite(nbe[i])) { status |= IR_NONFINITE; break; }
+        if (nbe[i] <= o->stop_tol) { status |= IR_CONVERGED; break; }
+        if (i == o->imax) { status |= IR_MAXSTEPS; break; }
+        int bd = 0;
+        double rr;
+        its[i] = orc_gmres(n, arp, aci, av, prp, pci, pv_up, r, &go, dd, &bd, &rr);
+        if (bd) status |= IR_BREAKDOWN;
+        for (int q = 0; q < n; q++) x[q] = rnd(x[q] + rnd(dd[q], o->u), o->u);
+        *steps = i + 1;
+    }
+    (void)ur_b;
+    free(r); free(dd); free(ur_b);
+    return status;
+}
+
+/* Exported single steps, used by the oracle's own pins. */
+void orc_spmv(int n, const int64_t* rp, const int* ci, const double* mv, const double* x, int p,
+              int mode, double* y)
+{
+    spmv_p(n, rp, ci, mv, x, p, mode, y);
+}
+
+void orc_residual(int n, const int64_t* rp, const int* ci, const double* av, const double* b,
+                  const double* x, int ur, int u, double* r)
+{
+    residual_ur(n, rp, ci, av, b, x, ur, u, r);
+}
+
+/* Arithmetic probes for the chop pin: op 0 add, 1 sub, 2 mul, 3 div, 4 sqrt,
+ * each on half operands with the result chopped to half. */
+void orc_half_ops(int cnt, const double* a, const double* b, int op, double* out)
+{
+    for (int i = 0; i < cnt; i++) {
+        double x = orc_chop_half(a[i]), y = orc_chop_half(b[i]), z;
+        switch (op) {
+        case 0: z = x + y; break;
+        case 1: z = x - y; break;
+        case 2: z = x * y; break;
+        case 3: z = x / y; break;
+        default: z = sqrt(fabs(x)); break;
+        }
+        out[i] = orc_chop_half(z);
+    }
+}

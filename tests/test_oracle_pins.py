@@ -1,0 +1,455 @@
+"""Pins for the CPU oracle: checks against facts the paper and mathematics fix.
+
+Each test compares the oracle with something other than itself: a library
+routine (numpy float16, numpy/scipy least squares), exact rational
+arithmetic, a closed form from the paper (eq. trueres, the 2 sqrt(n) eps and
+2 n eps bounds of Section 3, GMRES finite termination), or a hand-computed
+example.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.optimize import minimize_scalar
+
+import oracle as O
+from paper_2202_10204_gb300 import synth
+
+
+def dense_to_csr(M):
+    return synth._to_csr(sp.csr_matrix(np.asarray(M, dtype=np.float64)))
+
+
+# ---------------------------------------------------------------- Table 1: chop
+
+
+def test_chop_half_matches_numpy_float16_conversion():
+    rng = np.random.default_rng(0)
+    # spread over normal, subnormal and overflow ranges
+    x = rng.normal(size=200000) * 2.0 ** rng.integers(-30, 18, size=200000)
+    # exact ties at half precision (odd multiples of half a quantum)
+    ties = (rng.integers(0, 2 ** 11, size=5000) * 2 + 1) * 2.0 ** -12
+    x = np.concatenate([x, ties, -ties, [65504.0, 65519.99, 65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26, 0.0]])
+    ref = x.astype(np.float16).astype(np.float64)
+    got = O.chop_half(x)
+    assert np.array_equal(np.isinf(got), np.isinf(ref))
+    fin = np.isfinite(ref)
+    assert np.array_equal(got[fin], ref[fin])
+
+
+@pytest.mark.parametrize("op", [0, 1, 2, 3, 4])
+def test_half_arithmetic_matches_numpy_float16(op):
+    rng = np.random.default_rng(op + 1)
+    a = (rng.normal(size=100000) * 2.0 ** rng.integers(-16, 9, size=100000)).astype(np.float16)
+    b = (rng.normal(size=100000) * 2.0 ** rng.integers(-16, 9, size=100000)).astype(np.float16)
+    b[b == 0] = np.float16(1.0)
+    with np.errstate(all="ignore"):
+        ref = {0: a + b, 1: a - b, 2: a * b, 3: a / b, 4: np.sqrt(np.abs(a))}[op].astype(np.float64)
+    got = O.half_ops(a.astype(np.float64), b.astype(np.float64), op)
+    same = (got == ref) | (np.isnan(got) & np.isnan(ref))
+    assert same.all()
+
+
+def test_unit_roundoffs_table1():
+    # Table 1: half 2^-11, single 2^-24, double 2^-53 -- the spacing just above 1 is 2u
+    for p, u in ((O.HALF, 2.0 ** -11), (O.SINGLE, 2.0 ** -24)):
+        assert O.round_to(1.0 + u, p) == 1.0          # tie to even
+        assert O.round_to(1.0 + 1.5 * u, p) == 1.0 + 2 * u
+    assert O.UNIT_ROUNDOFF[O.DOUBLE] == np.finfo(np.float64).eps / 2
+
+
+# ---------------------------------------------------------------- least squares
+
+
+def exact_lstsq(A, e):
+    """Normal equations in exact rational arithmetic (brute force)."""
+    m, nc = A.shape
+    Af = [[Fraction(float(A[i, j])) for j in range(nc)] for i in range(m)]
+    ef = [Fraction(float(v)) for v in e]
+    G = [[sum(Af[i][a] * Af[i][b] for i in range(m)) for b in range(nc)] for a in range(nc)]
+    r = [sum(Af[i][a] * ef[i] for i in range(m)) for a in range(nc)]
+    for c in range(nc):  # Gaussian elimination (G is SPD: no pivoting needed)
+        for rr in range(c + 1, nc):
+            f = G[rr][c] / G[c][c]
+            for q in range(c, nc):
+                G[rr][q] -= f * G[c][q]
+            r[rr] -= f * r[c]
+    x = [Fraction(0)] * nc
+    for c in range(nc - 1, -1, -1):
+        x[c] = (r[c] - sum(G[c][q] * x[q] for q in range(c + 1, nc))) / G[c][c]
+    return np.array([float(v) for v in x])
+
+
+@pytest.mark.parametrize("shape", [(3, 1), (5, 3), (8, 5), (7, 7)])
+def test_dense_ls_double_matches_exact(shape):
+    rng = np.random.default_rng(sum(shape))
+    m, nc = shape
+    for trial in range(5):
+        A = rng.normal(size=(m, nc))
+        e = np.zeros(m); e[rng.integers(m)] = 1.0
+        x_ex = exact_lstsq(A, e)
+        mb, sb, sn, fl = O.dense_ls(A, e, "double")
+        kappa = np.linalg.cond(A)
+        assert fl == 0
+        assert np.max(np.abs(mb - x_ex)) <= 50 * 2.0 ** -53 * kappa ** 2 * max(1, np.max(np.abs(x_ex)))
+        # explicit residual and its norm
+        s_ref = A @ x_ex - e
+        assert abs(sn - np.linalg.norm(s_ref)) <= 1e-12 * max(1.0, np.linalg.norm(e))
+        np.testing.assert_allclose(sb, A @ mb - e, atol=1e-14)
+
+
+@pytest.mark.parametrize("uf,u", [("single", 2.0 ** -24), ("half", 2.0 ** -11)])
+@pytest.mark.parametrize("mode", [O.MODE_PEROP, O.MODE_ACC32])
+def test_dense_ls_low_precision_error_bound(uf, u, mode):
+    rng = np.random.default_rng(7)
+    for trial in range(20):
+        m, nc = 9, 4
+        A = O.round_to(rng.uniform(-1, 1, size=(m, nc)), uf)
+        e = np.zeros(m); e[trial % m] = 1.0
+        x_ex = np.linalg.lstsq(A, e, rcond=None)[0]
+        mb, sb, sn, fl = O.dense_ls(A, e, uf, mode)
+        kappa = np.linalg.cond(A)
+        # Householder LS (Higham, ASNA Thm 20.3): error O(m nc u kappa^2) relative
+        rel = np.linalg.norm(mb - x_ex) / np.linalg.norm(x_ex)
+        assert rel <= 4 * m * nc * u * kappa ** 2
+        # values are representable in u_f
+        assert np.array_equal(mb, O.round_to(mb, uf))
+        # the reported ||sbar|| is the u_f norm of the explicit residual
+        r_true = np.linalg.norm(A @ mb - e)
+        assert abs(sn - r_true) <= 4 * m * nc * u * max(r_true, 1.0)
+
+
+def test_dense_ls_square_is_solve():
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(6, 6)) + 6 * np.eye(6)
+    e = np.eye(6)[2]
+    mb, sb, sn, fl = O.dense_ls(A, e, "double")
+    np.testing.assert_allclose(mb, np.linalg.solve(A, e), rtol=1e-13, atol=1e-14)
+    assert sn <= 1e-14
+
+
+# ---------------------------------------------------------------- SPAI special cases
+
+
+def test_spai_diagonal_identity_pattern_is_exact_inverse():
+    a = np.array([2.0, -3.0, 0.5, 7.0, -0.25])
+    A = dense_to_csr(np.diag(a))
+    for uf in ("double", "single", "half"):
+        S = O.spai(A, init=O.PAT_IDENTITY, uf=uf, max_fill=4)
+        rp, col, val, _ = O.assemble_P(S, up="double")
+        assert np.array_equal(col, np.arange(5))
+        np.testing.assert_allclose(val, 1.0 / a, rtol=4 * O.UNIT_ROUNDOFF[O.prec(uf)])
+        assert np.all(S["flags"] & O.CF_CONVERGED)
+
+
+def test_spai_full_pattern_gives_inverse():
+    rng = np.random.default_rng(11)
+    n = 10
+    Ad = rng.normal(size=(n, n)) + 4 * np.eye(n)
+    A = dense_to_csr(Ad)
+    S = O.spai(A, init=O.PAT_A, uf="double", max_fill=n, eps=1e-12)
+    rp, col, val, _ = O.assemble_P(S, up="double")
+    P = sp.csr_matrix((val, col, rp), shape=(n, n)).toarray()
+    np.testing.assert_allclose(P @ Ad, np.eye(n), atol=1e-12 * np.linalg.cond(Ad))
+    # and GMRES on P A converges in one iteration (P A = I)
+    b = rng.normal(size=n)
+    d, k, bd, rr = O.gmres(A, b, (rp, col, val), tau=1e-10)
+    assert k == 1
+    np.testing.assert_allclose(Ad @ d, b, atol=1e-10)
+
+
+def test_spai_block_diagonal_exact_block_inverse():
+    rng = np.random.default_rng(5)
+    blocks = [rng.normal(size=(s, s)) + 3 * np.eye(s) for s in (3, 4, 2, 5)]
+    Ad = sp.block_diag([sp.coo_matrix(bk) for bk in blocks]).toarray()
+    n = Ad.shape[0]
+    A = dense_to_csr(Ad)
+    S = O.spai(A, init=O.PAT_A, uf="double", max_fill=8, eps=1e-10)
+    rp, col, val, _ = O.assemble_P(S, up="double")
+    P = sp.csr_matrix((val, col, rp), shape=(n, n)).toarray()
+    np.testing.assert_allclose(P, np.linalg.inv(Ad), atol=1e-12)
+    assert np.max(S["colres64"]) < 1e-13
+
+
+def test_spai_column_matches_library_lstsq():
+    A, b, x = synth.cfg_small_2d()
+    Ms = synth.to_scipy(A)
+    n = Ms.shape[0]
+    S = O.spai(A, init=O.PAT_A, uf="double", max_fill=30, cols=[0, 17, 500, 1023])
+    rowmax = np.abs(Ms).max(axis=1).toarray().ravel()
+    B = (Ms.T @ sp.diags(1.0 / rowmax)).tocsc()  # B = A^T D
+    for k in (0, 17, 500, 1023):
+        J = S["Jidx"][k][: S["Jcnt"][k]]
+        assert np.array_equal(J, np.sort(Ms[:, [k]].nonzero()[0]))  # pattern(A), column k
+        BJ = B[:, J].toarray()
+        I = np.union1d(np.nonzero(np.any(BJ != 0, axis=1))[0], [k])
+        e = (I == k).astype(float)
+        m_ref = np.linalg.lstsq(BJ[I], e, rcond=None)[0]
+        np.testing.assert_allclose(S["mbar"][k][: len(J)], m_ref, rtol=1e-12, atol=1e-13)
+        assert abs(S["colres64"][k] - np.linalg.norm(BJ @ m_ref - np.eye(n)[k])) < 1e-12
+
+
+def test_pattern_A2_matches_scipy():
+    A = synth.conv_diff_3d(6, 50.0, seed=3)
+    Ms = synth.to_scipy(A)
+    A2 = (abs(Ms) @ abs(Ms)).tocsc()
+    S = O.spai(A, init=O.PAT_A2, uf="single", max_fill=25, cols=list(range(0, 216, 7)))
+    for k in range(0, 216, 7):
+        J = S["Jidx"][k][: S["Jcnt"][k]]
+        ref = np.sort(A2[:, k].nonzero()[0])
+        assert len(ref) <= 25
+        assert np.array_equal(J, ref)
+    # interior column of the 7-point stencil: |pattern(A^2)| = 25
+    k = 2 * 36 + 2 * 6 + 2
+    assert S["Jcnt"][k] == 25 or k not in range(0, 216, 7)
+
+
+def test_fill_cap_keeps_k_and_nearest():
+    A = synth.conv_diff_3d(6, 50.0, seed=3)
+    k = 2 * 36 + 3 * 6 + 2
+    S = O.spai(A, init=O.PAT_A2, uf="double", max_fill=7, cols=[k])
+    J = S["Jidx"][k][: S["Jcnt"][k]]
+    assert S["Jcnt"][k] == 7 and k in J
+    Ms = synth.to_scipy(A)
+    full = np.sort((abs(Ms) @ abs(Ms))[:, k].nonzero()[0])
+    order = sorted(full, key=lambda j: (j != k, abs(j - k), j))
+    assert np.array_equal(J, np.sort(order[:7]))
+
+
+# ---------------------------------------------------------------- Grote-Huckle
+
+
+def test_rho_is_univariate_residual_minimum():
+    A = synth.random_sparse(60, 6, seed=2)
+    Ms = synth.to_scipy(A)
+    rowmax = np.abs(Ms).max(axis=1).toarray().ravel()
+    d = 1.0 / rowmax
+    B = (Ms.T @ sp.diags(d)).toarray()
+    rng = np.random.default_rng(1)
+    I = np.sort(rng.choice(60, size=20, replace=False))
+    s = np.zeros(60); s[I] = rng.normal(size=20)
+    cand = np.array([3, 10, 25, 41, 59], dtype=np.int32)
+    rho = O.rho(A, d, I, s[I], cand, "double")
+    for c, j in enumerate(cand):
+        f = lambda mu: np.linalg.norm(s + mu * B[:, j])
+        best = minimize_scalar(f, bounds=(-100, 100), method="bounded", options={"xatol": 1e-12}).fun
+        assert abs(rho[c] - best) <= 1e-7 * max(1.0, best)
+    # literal (restricted) reading uses ||b_j(I)|| instead of ||b_j||
+    rho_r = O.rho(A, d, I, s[I], cand, "double", rho_restricted=True)
+    for c, j in enumerate(cand):
+        bI = B[I, j]
+        if np.linalg.norm(bI) > 0:
+            ref = np.sqrt(max(0.0, s @ s - (s[I] @ bI) ** 2 / (bI @ bI)))
+            assert abs(rho_r[c] - ref) <= 1e-12
+
+
+def test_selection_hand_example():
+    # candidates and scores; mean = (0.5+0.2+0.9+0.2+0.4+0.8)/6 = 0.5
+    cand = [3, 7, 1, 9, 4, 6]
+    rho = [0.5, 0.2, 0.9, 0.2, 0.4, 0.8]
+    # acceptable (rho <= 0.5): 3, 7, 9, 4; order by rho then index: 7, 9, 4, 3
+    assert list(O.select(cand, rho, 3)) == [7, 9, 4]
+    assert list(O.select(cand, rho, 8)) == [7, 9, 4, 3]
+    assert list(O.select(cand, rho, 0)) == []
+    assert list(O.select([5], [0.3], 2)) == [5]
+
+
+@pytest.mark.parametrize("uf", ["double", "single"])
+def test_adaptive_meets_column_criterion(uf):
+    # eq. (trueres): every column of an uncapped adaptive run satisfies
+    # ||e_k - A^T D m_k|| <= eps up to the rounding term (<= 2 eps, Section 3)
+    A = synth.conv_diff_2d(8, 10.0, 1.0, 0.1, seed=4)
+    n = 64
+    for eps in (0.5, 0.3, 0.1):
+        S = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=eps, beta=8, alpha=n, max_fill=n, uf=uf)
+        assert np.all(S["flags"] & O.CF_CONVERGED)
+        assert np.all(S["colres"] <= eps)
+        assert np.all(S["colres64"] <= 2 * eps)
+
+
+def test_adaptive_global_bounds():
+    # ||I - A^T D M||_F <= 2 sqrt(n) eps and ||I - P A||_inf <= 2 n eps (eq. AM1)
+    A = synth.random_sparse(80, 5, seed=9)
+    n = 80
+    Ad = synth.to_scipy(A).toarray()
+    for eps in (0.4, 0.2):
+        S = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=eps, alpha=n, max_fill=n, uf="single")
+        assert np.all(S["flags"] & O.CF_CONVERGED)
+        rp, col, val, _ = O.assemble_P(S, up="double")
+        P = sp.csr_matrix((val, col, rp), shape=(n, n)).toarray()
+        d = S["d"]
+        M = (P / d[None, :]).T  # P = M^T D
+        B = Ad.T @ np.diag(d)
+        assert np.linalg.norm(np.eye(n) - B @ M, "fro") <= 2 * np.sqrt(n) * eps
+        assert np.linalg.norm(np.eye(n) - P @ Ad, np.inf) <= 2 * n * eps
+
+
+def test_larger_eps_gives_sparser_preconditioner():
+    # qualitative trend of Section 4 (Tables 4-6): larger eps -> fewer nonzeros
+    A = synth.random_sparse(200, 6, seed=12)
+    nnz = []
+    for eps in (0.2, 0.35, 0.5):
+        S = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=eps, max_fill=60, uf="single")
+        nnz.append(int(S["Jcnt"].sum()))
+    assert nnz[0] > nnz[1] > nnz[2]
+
+
+def test_half_modes_agree_to_half_precision():
+    A, b, x = synth.cfg_small_2d()
+    S1 = O.spai(A, init=O.PAT_A, uf="half", mode=O.MODE_PEROP, max_fill=30)
+    S2 = O.spai(A, init=O.PAT_A, uf="half", mode=O.MODE_ACC32, max_fill=30)
+    rel = np.abs(S1["colres64"] - S2["colres64"]) / S2["colres64"]
+    assert np.max(rel) < 1e-2
+    # both are near the double-precision optimum (the LS residual is stationary)
+    S3 = O.spai(A, init=O.PAT_A, uf="double", max_fill=30)
+    assert np.max(np.abs(S2["colres64"] - S3["colres64"]) / S3["colres64"]) < 1e-3
+
+
+# ---------------------------------------------------------------- GMRES
+
+
+def test_gmres_terminates_in_at_most_n_iterations():
+    rng = np.random.default_rng(21)
+    for n in (5, 17, 40, 64):
+        Ad = rng.normal(size=(n, n)) + np.sqrt(n) * np.eye(n)
+        A = dense_to_csr(Ad)
+        r = rng.normal(size=n)
+        d, k, bd, rr = O.gmres(A, r, None, tau=1e-14, maxit=n)
+        assert k <= n
+        assert np.linalg.norm(Ad @ d - r) <= 1e-10 * np.linalg.norm(r)
+
+
+def test_gmres_distinct_eigenvalues_bound():
+    rng = np.random.default_rng(4)
+    n = 30
+    S = rng.normal(size=(n, n)) + 5 * np.eye(n)
+    lam = np.array([1.0, 2.0, 5.0])[rng.integers(0, 3, size=n)]
+    Ad = S @ np.diag(lam) @ np.linalg.inv(S)
+    A = dense_to_csr(Ad)
+    r = rng.normal(size=n)
+    d, k, bd, rr = O.gmres(A, r, None, tau=1e-12, maxit=n)
+    assert k <= 3
+    np.testing.assert_allclose(Ad @ d, r, atol=1e-8 * np.linalg.norm(r))
+
+
+def test_gmres_zero_rhs():
+    A = dense_to_csr(np.eye(4) * 2)
+    d, k, bd, rr = O.gmres(A, np.zeros(4), None)
+    assert k == 0 and np.all(d == 0)
+
+
+def test_gmres_preconditioned_equals_unpreconditioned_on_PA():
+    # left preconditioning: GMRES on (P, A) behaves like GMRES on the product P A
+    rng = np.random.default_rng(8)
+    n = 20
+    Ad = rng.normal(size=(n, n)) + 5 * np.eye(n)
+    Pd = np.diag(1.0 / np.diag(Ad))
+    r = rng.normal(size=n)
+    d1, k1, _, _ = O.gmres(dense_to_csr(Ad), r, dense_to_csr(Pd), tau=1e-10)
+    d2, k2, _, _ = O.gmres(dense_to_csr(Pd @ Ad), Pd @ r, None, tau=1e-10)
+    assert k1 == k2
+    np.testing.assert_allclose(d1, d2, rtol=1e-8, atol=1e-10)
+
+
+# ---------------------------------------------------------------- residual and IR
+
+
+def test_quad_residual_is_exactly_rounded():
+    rng = np.random.default_rng(2)
+    n = 12
+    Ad = rng.normal(size=(n, n))
+    A = dense_to_csr(Ad)
+    x = rng.normal(size=n)
+    b = Ad @ x + rng.normal(size=n) * 1e-14
+    r = O.residual(A, b, x, "quad", "double")
+    for i in range(n):
+        ex = Fraction(b[i]) - sum(Fraction(Ad[i, j]) * Fraction(x[j]) for j in range(n))
+        assert r[i] == float(ex)  # Fraction -> float rounds to nearest
+
+
+def exact_solve(Ad, b):
+    n = len(b)
+    M = [[Fraction(float(v)) for v in row] + [Fraction(float(b[i]))] for i, row in enumerate(Ad)]
+    for c in range(n):
+        p = max(range(c, n), key=lambda r: abs(M[r][c]))
+        M[c], M[p] = M[p], M[c]
+        for r in range(c + 1, n):
+            f = M[r][c] / M[c][c]
+            if f:
+                for q in range(c, n + 1):
+                    M[r][q] -= f * M[c][q]
+    x = [Fraction(0)] * n
+    for c in range(n - 1, -1, -1):
+        x[c] = (M[c][n] - sum(M[c][q] * x[q] for q in range(c + 1, n))) / M[c][c]
+    return np.array([float(v) for v in x])
+
+
+def test_ir_reaches_working_accuracy_quad_residual():
+    # Theorems 1-2: with u_r = quad, forward error ~ u and backward error <= q u
+    A = synth.conv_diff_2d(5, 10.0, 1.0, 0.1, seed=3)
+    Ad = synth.to_scipy(A).toarray()
+    b = np.random.default_rng(1).normal(size=25)
+    x_ex = exact_solve(Ad, b)
+    S = O.spai(A, init=O.PAT_A, uf="single", max_fill=30)
+    P = O.assemble_P(S, up="double", uf="single")
+    R = O.gmres_ir(A, b, P, uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+    assert R["status"] & O.IR_CONVERGED
+    u = 2.0 ** -53
+    assert np.max(np.abs(R["x"] - x_ex)) / np.max(np.abs(x_ex)) <= 2 * u
+    assert R["nbe"][-1] <= 5 * u
+
+
+def test_ir_single_working_precision():
+    A, b, x = synth.cfg_small_2d()
+    S = O.spai(A, init=O.PAT_A, uf="half", max_fill=30)
+    P = O.assemble_P(S, up="single", uf="half")
+    R = O.gmres_ir(A, b, P, uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4)
+    assert R["status"] & O.IR_CONVERGED
+    assert R["nbe"][-1] <= 5 * 2.0 ** -24
+    assert np.array_equal(R["x"], O.round_to(R["x"], "single"))
+    ferr = np.max(np.abs(R["x"] - x)) / np.max(np.abs(x))
+    assert ferr < 1e-5
+
+
+def test_ir_without_preconditioner_is_plain_gmres_ir():
+    A, b, x = synth.cfg_small_2d()
+    R = O.gmres_ir(A, b, None, uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+    assert R["status"] & O.IR_CONVERGED
+    S = O.spai(A, init=O.PAT_A, uf="single", max_fill=30)
+    R2 = O.gmres_ir(A, b, O.assemble_P(S, "double", "single"), uf="single", u="double", ug="double",
+                    up="double", ur="quad", tau=1e-4)
+    # the preconditioner lowers the iteration count (Tables 4-6 trend)
+    assert R2["total_its"] < R["total_its"]
+
+
+# ---------------------------------------------------------------- products in u_p / u_f
+
+
+@pytest.mark.parametrize("p,u", [("double", 2.0 ** -53), ("single", 2.0 ** -24), ("half", 2.0 ** -11)])
+@pytest.mark.parametrize("mode", [O.MODE_PEROP, O.MODE_ACC32])
+def test_spmv_error_bound(p, u, mode):
+    # |fl(M x) - M x| <= gamma_q |M||x| with the operands first rounded to p
+    A = synth.conv_diff_3d(5, 50.0, seed=2)
+    Ms = synth.to_scipy(A)
+    x = np.random.default_rng(0).normal(size=Ms.shape[0])
+    Mp = Ms.copy(); Mp.data = O.round_to(Mp.data, p)
+    xp = O.round_to(x, p)
+    y = O.spmv(A, x, p, mode)
+    exact = Mp @ xp
+    bound = abs(Mp) @ abs(xp)
+    q = 7
+    assert np.all(np.abs(y - exact) <= (q + 1) * u * bound + 1e-300)
+    assert np.array_equal(y, O.round_to(y, p))
+    if p == "double":
+        np.testing.assert_allclose(y, Ms @ x, rtol=1e-13, atol=1e-13)
+
+
+def test_gmres_single_precision_converges_to_tau():
+    A, b, x = synth.cfg_small_2d()
+    Ad = synth.to_scipy(A)
+    r = np.random.default_rng(3).normal(size=1024)
+    d, k, bd, rr = O.gmres(A, r, None, ug="single", up="single", tau=1e-4)
+    assert rr <= 1e-4
+    assert np.linalg.norm(Ad @ d - r) / np.linalg.norm(r) <= 1e-3
+    assert np.array_equal(d, O.round_to(d, "single"))
