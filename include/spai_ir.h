@@ -1,0 +1,187 @@
+/*
+ * spai_ir.h -- C ABI of the GB300 SPAI-GMRES-IR library.
+ *
+ * Solves sparse nonsingular A x = b by GMRES-based iterative refinement left-
+ * preconditioned by a Frobenius-norm sparse approximate inverse (Carson &
+ * Khan, "Mixed precision iterative refinement with sparse approximate
+ * inverse preconditioning", arXiv 2202.10204):
+ *   - the preconditioner is Algorithm 1 (Grote-Huckle / Sedlacek SPAI) run on
+ *     A^T D, D the diagonal that scales every column of A^T (every row of A)
+ *     to max-abs 1, and P = M^T D (Section 3 and Section 4 set-up);
+ *   - the solve is Algorithm 3 (SPAI-GMRES-IR) with the five precisions
+ *     (u_f, u, u_g, u_p, u_r) of Section 3.1.
+ *
+ * Conventions for every entry point:
+ *   - return value 0 is success, > 0 a warning, < 0 an error (SPAI_* codes);
+ *     spai_strerror() names each code.  No entry point aborts the process.
+ *   - the caller owns every buffer it passes; the library never frees or
+ *     keeps a caller pointer beyond the call, except solver_submit, which
+ *     copies its inputs before returning.
+ *   - CSR arrays: rowptr[n+1] int64 (rowptr[0] = 0, non-decreasing), col[nnz]
+ *     int32 in [0, n) sorted ascending within a row, val[nnz] float64.
+ *     With on_device = 1 all three are device pointers on the context's
+ *     device, otherwise host pointers.
+ *   - all work runs on the context's CUDA stream on one GPU; every call
+ *     returns after its results are complete.
+ *   - calls on one context are serialised by the context; distinct contexts
+ *     may be used from different threads.
+ */
+#ifndef SPAI_IR_H
+#define SPAI_IR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SPAI_OK 0
+#define SPAI_WARN_NOT_CONVERGED 1  /* IR stopped at i_max above the stop tolerance  */
+#define SPAI_WARN_FILLCAP 2        /* some SPAI columns stopped at the fill cap     */
+#define SPAI_PENDING 3             /* solver_poll: request not finished yet          */
+#define SPAI_ERR_INVALID_ARG (-1)  /* bad pointer, size, option or CSR structure     */
+#define SPAI_ERR_ZERO_ROW (-2)     /* a row of A has no nonzero: A is singular       */
+#define SPAI_ERR_NONFINITE (-3)    /* Inf/NaN in the input or overflow in u_f        */
+#define SPAI_ERR_NO_MEMORY (-4)    /* device allocation failed                       */
+#define SPAI_ERR_ADMISSION (-5)    /* request larger than the context's HBM budget   */
+#define SPAI_ERR_TIMEOUT (-6)      /* a bounded device-side wait expired             */
+#define SPAI_ERR_CUDA (-7)         /* a CUDA runtime call failed                     */
+#define SPAI_ERR_UNSUPPORTED (-8)  /* precision tuple or size outside what is built  */
+#define SPAI_ERR_NOT_FOUND (-9)    /* unknown ticket                                 */
+#define SPAI_ERR_INTERNAL (-10)    /* device-side consistency check failed           */
+
+/* ---- precisions (Table 1) -------------------------------------------- */
+typedef enum {
+    SPAI_HALF = 0,   /* IEEE binary16, u = 2^-11 */
+    SPAI_SINGLE = 1, /* IEEE binary32, u = 2^-24 */
+    SPAI_DOUBLE = 2, /* IEEE binary64, u = 2^-53 */
+    SPAI_QUAD = 3    /* u_r only: the residual is computed in double-double */
+} spai_prec;
+
+/* initial pattern J of Algorithm 1 (Section 2.2: identity, or the pattern of
+ * A or of a power of A).  Column k of the pattern is the nonzero rows of
+ * column k of A (resp. A^2). */
+typedef enum { SPAI_PAT_IDENTITY = 0, SPAI_PAT_A = 1, SPAI_PAT_A2 = 2 } spai_pattern_init;
+
+/* refinement stopping rule (Algorithm 3 fixes only i_max) */
+typedef enum {
+    IR_STOP_BACKWARD = 0, /* stop before step i once ||r_i||_inf/(||A||_inf||x_i||_inf+||b||_inf) <= stop_tol */
+    IR_STOP_FIXED = 1     /* always run ir_max_steps steps */
+} ir_stop_rule;
+
+typedef struct {
+    int64_t n, nnz;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    int on_device; /* 1: device pointers (borrowed for the call), 0: host */
+} spai_csr;
+
+/* Algorithm 1 parameters. */
+typedef struct {
+    spai_pattern_init init; /* initial pattern J                                  */
+    int adaptive;           /* 0: fixed pattern, 1: Grote-Huckle augmentation     */
+    double eps;             /* column tolerance: stop when ||s_k||_2 <= eps       */
+    int alpha;              /* max augmentation steps per column; < 0: ceil(n/beta) */
+    int beta;               /* max indices added per step (>= 1 when adaptive)    */
+    int max_fill;           /* cap on |J_k|, 1..31; larger initial patterns keep k
+                               and the indices nearest to k                        */
+    spai_prec uf;           /* precision of the construction (half/single/double) */
+    int scale;              /* 1: run on A^T D (recommended), 0: on A^T           */
+    int rho_restricted;     /* 1: rho_jk uses ||b_j(I_k)|| (literal Algorithm 1)  */
+} spai_opts;
+
+/* Algorithm 3 parameters: the five precisions, tau, i_max and the stop rule. */
+typedef struct {
+    spai_prec uf, u, ug, up, ur; /* u in {single,double}; ug,up in {single,double};
+                                    ur in {double,quad}, ur >= u                */
+    double tau;                  /* GMRES relative tolerance on ||P(r - A d)||/||P r|| */
+    int gmres_max_it;            /* iterations per GMRES solve (1..1024); <= 0: min(n, 500) */
+    int ir_max_steps;            /* i_max (1..64)                                      */
+    ir_stop_rule stop;
+    double stop_tol;             /* <= 0: q*u, q the largest row nonzero count of A    */
+} ir_opts;
+
+#define SPAI_IR_MAX_STEPS 64
+
+typedef struct {
+    int64_t n;
+    int64_t nnz_P;             /* nonzeros of P = sum_k |J_k|                        */
+    int64_t cols_converged;    /* columns with ||s_k|| <= eps                         */
+    int64_t cols_fillcap;      /* columns stopped at max_fill above eps               */
+    int64_t cols_nonfinite;    /* columns with Inf/NaN (overflow in u_f)              */
+    int max_I, max_J;          /* largest |I_k| and |J_k|                             */
+    double ms;                 /* device time of the build, milliseconds              */
+    /* optional per-column host outputs, filled when non-NULL (length n each): */
+    double* colres;            /* ||s_k||_2 as computed in u_f                         */
+    int32_t* nJ;               /* |J_k|                                                */
+    int32_t* nI;               /* |I_k| of the final least-squares solve               */
+    int32_t* flags;            /* bit 0 converged, 1 fill cap, 2 alpha, 3 no candidate,
+                                  4 zero pivot, 5 non-finite                           */
+} spai_stats;
+
+typedef struct {
+    int steps;                           /* GMRES solves performed                   */
+    int total_its;                       /* sum of its[]                             */
+    int its[SPAI_IR_MAX_STEPS];          /* GMRES iterations per refinement step     */
+    double nbe[SPAI_IR_MAX_STEPS + 1];   /* normwise backward error before each step */
+    double final_nbe;                    /* backward error of the returned x         */
+    int flags;                           /* 1 converged, 2 max steps, 4 breakdown, 8 non-finite */
+    int64_t nnz_P;
+    double ms_spai, ms_ir;               /* device time of the two phases            */
+} ir_stats;
+
+typedef struct spai_ctx_s* spai_ctx;
+typedef struct spai_precond_s* spai_precond;
+
+/* Create a context on `device` that runs on `cuda_stream` (a cudaStream_t;
+ * NULL: the context creates its own).  hbm_budget_bytes bounds the device
+ * memory the serving queue admits (0: 90% of free memory at creation). */
+int spai_ctx_create(spai_ctx* out, int device, void* cuda_stream, size_t hbm_budget_bytes);
+void spai_ctx_destroy(spai_ctx ctx);
+
+/* Algorithm 1 on A^T D (Section 2.2, Algorithm 1; Section 4 scaling), giving
+ * the left preconditioner P = M^T D in CSR on the device.  *P_out is owned by
+ * the caller and released with spai_precond_free.  st may be NULL. */
+int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_precond* P_out,
+               spai_stats* st);
+
+/* Size of P: *n and *nnz (either may be NULL). */
+int spai_precond_info(spai_precond P, int64_t* n, int64_t* nnz);
+
+/* Copy P to host buffers: rowptr[n+1], col[nnz], val[nnz] (float64, the
+ * unrounded values mbar_k * d(J_k)); any pointer may be NULL. */
+int spai_precond_export(spai_precond P, int64_t* rowptr, int32_t* col, double* val);
+
+void spai_precond_free(spai_precond P);
+
+/* Algorithm 3 (SPAI-GMRES-IR).  P: a preconditioner from spai_build; if NULL
+ * and sopts != NULL one is built first (and freed); if both are NULL the
+ * solve is unpreconditioned GMRES-IR (P = I).  b[n] and x[n] (float64) are
+ * device pointers when A->on_device, host pointers otherwise; x is output
+ * only.  st may be NULL. */
+int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_opts* sopts,
+                   const double* b, double* x, const ir_opts* opts, ir_stats* st);
+
+/* Serving queue.  solver_submit copies A and b (host or device, as
+ * A->on_device says) into the context and returns a ticket at once; requests
+ * are admitted to the GPU while their estimated device footprint fits the
+ * context's HBM budget, and admitted requests run concurrently.  Returns
+ * SPAI_ERR_ADMISSION if the request alone exceeds the budget. */
+int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_opts* sopts,
+                  const ir_opts* opts, uint64_t* ticket);
+
+/* SPAI_PENDING while the request runs; otherwise copies the solution into the
+ * host buffer x[n] (may be NULL), fills st (may be NULL), releases the ticket
+ * and returns the request's own status. */
+int solver_poll(spai_ctx ctx, uint64_t ticket, double* x, ir_stats* st);
+
+const char* spai_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPAI_IR_H */

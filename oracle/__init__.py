@@ -23,7 +23,9 @@ UNIT_ROUNDOFF = {HALF: 2.0 ** -11, SINGLE: 2.0 ** -24, DOUBLE: 2.0 ** -53, QUAD:
 MODE_PEROP, MODE_ACC32 = 0, 1
 PAT_IDENTITY, PAT_A, PAT_A2 = 0, 1, 2
 
-CF_CONVERGED, CF_FILLCAP, CF_ALPHA, CF_NOCAND, CF_SINGULAR, CF_NONFINITE = 1, 2, 4, 8, 16, 32
+CF_CONVERGED, CF_FILLCAP, CF_ALPHA, CF_NOCAND, CF_SINGULAR, CF_NONFINITE, CF_TOOBIG = 1, 2, 4, 8, 16, 32, 64
+# largest shadow |I_k| an adaptive augmentation may reach (the CUDA tile limit)
+MAX_SHADOW = 512
 IR_CONVERGED, IR_MAXSTEPS, IR_BREAKDOWN, IR_NONFINITE = 1, 2, 4, 8
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -48,7 +50,7 @@ class SpaiOpts(C.Structure):
     _fields_ = [("init", C.c_int), ("adaptive", C.c_int), ("eps", C.c_double),
                 ("alpha", C.c_int), ("beta", C.c_int), ("max_fill", C.c_int),
                 ("uf", C.c_int), ("mode", C.c_int), ("rho_restricted", C.c_int),
-                ("scale", C.c_int)]
+                ("scale", C.c_int), ("max_shadow", C.c_int)]
 
 
 class GmresOpts(C.Structure):
@@ -146,7 +148,7 @@ def select(cand, rho_vals, nmax, uf="double"):
 
 
 def spai(A, init=PAT_IDENTITY, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fill=30, uf="double",
-         mode=MODE_ACC32, rho_restricted=False, scale=True, cols=None):
+         mode=MODE_ACC32, rho_restricted=False, scale=True, cols=None, max_shadow=MAX_SHADOW):
     """SPAI of Algorithm 1 run on A^T D; returns a dict with P = M^T D pieces.
 
     ``P_rows[k]`` / ``P_vals[k]`` hold row k of P (= column k of M scaled by
@@ -157,7 +159,7 @@ def spai(A, init=PAT_IDENTITY, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fi
     n = len(rp) - 1
     F = int(max_fill)
     o = SpaiOpts(int(init), int(bool(adaptive)), float(eps), int(alpha), int(beta), F, prec(uf), int(mode),
-                 int(bool(rho_restricted)), int(bool(scale)))
+                 int(bool(rho_restricted)), int(bool(scale)), int(max_shadow))
     d = np.zeros(n)
     Jcnt = np.zeros(n, dtype=np.int32)
     Jidx = np.full(n * F, -1, dtype=np.int32)

@@ -51,6 +51,9 @@
  *       + ||b||_inf) <= stop_tol; at most i_max GMRES solves.
  *   R10 pattern(A) / pattern(A^2) initial patterns: J_k = nonzero rows of
  *       column k of A (resp. A^2).
+ *   R11 an augmentation whose new shadow |I_k| exceeds max_shadow (the
+ *       CUDA tile height, 512 rows) is undone and the column keeps its
+ *       previous pattern and solve (flag CF_TOOBIG).
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,6 +79,7 @@
 #define CF_NOCAND 8      /* no acceptable candidate to add      */
 #define CF_SINGULAR 16   /* a zero pivot in R                   */
 #define CF_NONFINITE 32  /* Inf/NaN appeared (overflow in u_f)  */
+#define CF_TOOBIG 64     /* augmentation undone: shadow over max_shadow */
 
 /* IR status flags */
 #define IR_CONVERGED 1
@@ -288,6 +292,8 @@ typedef struct {
     int mode;            /* MODE_PEROP / MODE_ACC32 */
     int rho_restricted;  /* R3 literal reading */
     int scale;           /* 1: run on A^T D (Section 4); 0: on A^T */
+    int max_shadow;      /* adaptive: an augmentation whose shadow |I_k| would
+                            exceed this is undone and the column stops (<= 0: none) */
 } orc_spai_opts;
 
 /* Candidate scores rho_j (Algorithm 1, rho_jk line; reading R3).
@@ -385,6 +391,8 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
     size_t capC = capI * (size_t)(maxcol + 1) + 2;
     int* J = (int*)malloc(sizeof(int) * (capJ0 > (size_t)F ? capJ0 : (size_t)F + 2));
     int* I = (int*)malloc(sizeof(int) * capI);
+    int* Iprev = (int*)malloc(sizeof(int) * capI);
+    int* Jprev = (int*)malloc(sizeof(int) * ((size_t)F + 2));
     int* cand = (int*)malloc(sizeof(int) * capC);
     double* rho = (double*)malloc(sizeof(double) * capC);
     int* sel = (int*)malloc(sizeof(int) * (size_t)(beta + 1));
@@ -408,7 +416,7 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
         }
         nj = sort_unique(J, nj);
         nj = apply_cap(J, nj, k, F);
-        int fl = 0, ns = 0, m = 0;
+        int fl = 0, ns = 0, m = 0, nj_prev = nj, m_prev = 0;
         double snorm = 0.0;
         for (int step = 0; step <= alpha; step++) {
             /* shadow I_k = union of nonzero columns of rows j in J_k, plus k */
@@ -417,6 +425,15 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
                 for (int64_t q = rp[J[c]]; q < rp[J[c] + 1]; q++) if (val[q] != 0.0) I[m++] = ci[q];
             I[m++] = k;
             m = sort_unique(I, m);
+            if (step > 0 && o->max_shadow > 0 && m > o->max_shadow) {
+                /* undo the last augmentation: keep the previous pattern and solve */
+                nj = nj_prev;
+                for (int c = 0; c < nj; c++) J[c] = Jprev[c];
+                m = m_prev;
+                for (int i = 0; i < m; i++) I[i] = Iprev[i];
+                fl |= CF_TOOBIG;
+                break;
+            }
             /* Abar = B(I_k, J_k) in u_f, ebar = e_k(I_k) */
             for (size_t z = 0; z < (size_t)m * nj; z++) Abar[z] = 0.0;
             for (int c = 0; c < nj; c++) {
@@ -451,6 +468,10 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
             int room = F - nj;
             int nadd = orc_select(nc, cand, rho, o->uf, beta < room ? beta : room, sel);
             if (nadd == 0) { fl |= CF_NOCAND; break; }
+            nj_prev = nj;
+            m_prev = m;
+            for (int c = 0; c < nj; c++) Jprev[c] = J[c];
+            for (int i = 0; i < m; i++) Iprev[i] = I[i];
             for (int a = 0; a < nadd; a++) J[nj++] = sel[a];
             nj = sort_unique(J, nj);
         }
@@ -477,7 +498,7 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
         }
         colres64[k] = sqrt(acc);
     }
-    free(cp); free(ri); free(J); free(I); free(cand); free(rho); free(sel);
+    free(cp); free(ri); free(J); free(I); free(Iprev); free(Jprev); free(cand); free(rho); free(sel);
     free(Abar); free(ebar); free(mb); free(sb);
     return 0;
 }

@@ -1,0 +1,13 @@
+"""SPAI-GMRES-IR on one GB300 (sm_103a): sparse approximate inverse
+preconditioning inside five-precision GMRES-based iterative refinement
+(Carson & Khan, arXiv 2202.10204).
+
+The numerical work lives in the CUDA library (``csrc/``, C ABI in
+``include/spai_ir.h``); ``_lib`` is its ctypes binding and ``synth`` builds
+seeded test systems.
+"""
+from ._lib import (Context, Precond, SpaiError, gmres_ir_solve, make_ir_opts, make_spai_opts, solver_poll,
+                   solver_submit, spai_build, strerror)
+
+__all__ = ["Context", "Precond", "SpaiError", "gmres_ir_solve", "make_ir_opts", "make_spai_opts", "solver_poll",
+           "solver_submit", "spai_build", "strerror"]

@@ -1,0 +1,419 @@
+// The C ABI (include/spai_ir.h): contexts, preconditioner objects, host <->
+// device marshalling and the serving queue.  All numerical work is done by
+// the kernels in spai_build.cu and gmres_ir.cu.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+void spai_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? SPAI_ERR_NO_MEMORY : SPAI_ERR_CUDA;
+    }
+    return 0;
+}
+
+void dev_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+int csr_validate_host(const spai_csr* A)
+{
+    if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
+    if (A->n > INT32_MAX) return SPAI_ERR_UNSUPPORTED;
+    if (A->on_device) return 0;  // device arrays are checked by the kernels' own guards
+    if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) return SPAI_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < A->n; i++) {
+        int64_t b = A->rowptr[i], e = A->rowptr[i + 1];
+        if (e < b) return SPAI_ERR_INVALID_ARG;
+        if (e == b) return SPAI_ERR_ZERO_ROW;
+        for (int64_t q = b; q < e; q++) {
+            int32_t c = A->col[q];
+            if (c < 0 || c >= A->n) return SPAI_ERR_INVALID_ARG;
+            if (q > b && A->col[q - 1] >= c) return SPAI_ERR_INVALID_ARG;
+        }
+    }
+    return 0;
+}
+
+int csr_to_device(const spai_csr* A, DevCsr* out, cudaStream_t s)
+{
+    out->n = A->n;
+    out->nnz = A->nnz;
+    if (A->on_device) {
+        out->rowptr = const_cast<int64_t*>(A->rowptr);
+        out->col = const_cast<int32_t*>(A->col);
+        out->val = const_cast<double*>(A->val);
+        out->owned = false;
+        return 0;
+    }
+    int rc;
+    if ((rc = dev_alloc((void**)&out->rowptr, sizeof(int64_t) * (A->n + 1), s))) return rc;
+    if ((rc = dev_alloc((void**)&out->col, sizeof(int32_t) * std::max<int64_t>(A->nnz, 1), s))) return rc;
+    if ((rc = dev_alloc((void**)&out->val, sizeof(double) * std::max<int64_t>(A->nnz, 1), s))) return rc;
+    out->owned = true;
+    SPAI_CUDA_TRY(cudaMemcpyAsync(out->rowptr, A->rowptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyHostToDevice, s));
+    SPAI_CUDA_TRY(cudaMemcpyAsync(out->col, A->col, sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice, s));
+    SPAI_CUDA_TRY(cudaMemcpyAsync(out->val, A->val, sizeof(double) * A->nnz, cudaMemcpyHostToDevice, s));
+    return 0;
+}
+
+void csr_release(DevCsr* d, cudaStream_t s)
+{
+    if (d->owned) {
+        dev_free(d->rowptr, s);
+        dev_free(d->col, s);
+        dev_free(d->val, s);
+    }
+    d->rowptr = nullptr;
+    d->col = nullptr;
+    d->val = nullptr;
+    d->owned = false;
+}
+
+size_t estimate_footprint(int64_t n, int64_t nnz, const spai_opts* so, const ir_opts* io)
+{
+    size_t F = so ? (size_t)so->max_fill : 1;
+    size_t kmax = io && io->gmres_max_it > 0 ? (size_t)io->gmres_max_it : (size_t)std::min<int64_t>(n, 500);
+    size_t N = (size_t)n;
+    size_t a = (size_t)nnz * 12 + (N + 1) * 8;                         // A
+    size_t spai = so ? N * F * 24 + N * 48 + (size_t)nnz * 4 : 0;    // SPAI scratch
+    size_t p = so ? N * F * 24 + (N + 1) * 8 : 0;                     // P (double + u_f + f32 + col)
+    size_t ir = N * 8 * (kmax + 1) + N * 48 + (kmax + 2) * (kmax + 1) * 8 + (size_t)nnz * 4;
+    return a + std::max(spai + p, p + ir) + (1u << 20);
+}
+
+// ------------------------------------------------------------------ serving
+
+struct ServeRequest {
+    uint64_t ticket = 0;
+    int64_t n = 0, nnz = 0;
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> col;
+    std::vector<double> val, b, x;
+    spai_opts so{};
+    ir_opts io{};
+    bool has_so = false;
+    size_t bytes = 0;
+    bool done = false;
+    int status = 0;
+    ir_stats st{};
+};
+
+static void run_request(spai_ctx ctx, cudaStream_t s, ServeRequest* r)
+{
+    cudaSetDevice(ctx->device);
+    spai_csr A{r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(), 0};
+    DevCsr dA;
+    double *db = nullptr, *dx = nullptr;
+    spai_precond P = nullptr;
+    int rc = csr_to_device(&A, &dA, s);
+    if (!rc) rc = dev_alloc((void**)&db, sizeof(double) * r->n, s);
+    if (!rc) rc = dev_alloc((void**)&dx, sizeof(double) * r->n, s);
+    if (!rc && cudaMemcpyAsync(db, r->b.data(), sizeof(double) * r->n, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    int wrc = 0;
+    if (!rc && r->has_so) {
+        spai_stats sst{};
+        rc = spai_build_dev(ctx->device, ctx->num_sms, s, dA, &r->so, &P, &sst);
+        if (rc > 0) { wrc = rc; rc = 0; }
+        r->st.ms_spai = sst.ms;
+    }
+    if (rc >= 0 && !(rc < 0)) {
+        int rr = gmres_ir_dev(ctx->device, ctx->num_sms, s, dA, P, db, dx, &r->io, &r->st);
+        if (rr < 0) rc = rr; else if (rr > 0) wrc = rr;
+    }
+    if (rc >= 0) {
+        r->x.resize(r->n);
+        if (cudaMemcpyAsync(r->x.data(), dx, sizeof(double) * r->n, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
+    if (P) spai_precond_free(P);
+    dev_free(db, s);
+    dev_free(dx, s);
+    csr_release(&dA, s);
+    cudaStreamSynchronize(s);
+    r->status = rc < 0 ? rc : wrc;
+}
+
+static void worker_loop(spai_ctx ctx, int widx)
+{
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->worker_streams[widx];
+    for (;;) {
+        ServeRequest* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            // admit the oldest request once its footprint fits the budget
+            ctx->qcv.wait(lk, [&] {
+                return ctx->stopping || (!ctx->pending.empty() && ctx->in_use + ctx->pending.front()->bytes <= ctx->budget);
+            });
+            if (ctx->stopping && ctx->pending.empty()) return;
+            if (ctx->pending.empty()) continue;
+            r = ctx->pending.front();
+            ctx->pending.pop_front();
+            ctx->in_use += r->bytes;
+        }
+        run_request(ctx, s, r);
+        {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            ctx->in_use -= r->bytes;
+            r->done = true;
+        }
+        ctx->qcv.notify_all();
+    }
+}
+
+extern "C" {
+
+int spai_ctx_create(spai_ctx* out, int device, void* cuda_stream, size_t hbm_budget_bytes)
+{
+    if (!out) return SPAI_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    SPAI_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return SPAI_ERR_INVALID_ARG;
+    SPAI_CUDA_TRY(cudaSetDevice(device));
+    int coop = 0;
+    SPAI_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+    if (!coop) return SPAI_ERR_UNSUPPORTED;
+    spai_ctx c = new spai_ctx_s();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return SPAI_ERR_CUDA; }
+        c->own_stream = true;
+    }
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)fr);
+    *out = c;
+    return 0;
+}
+
+void spai_ctx_destroy(spai_ctx c)
+{
+    if (!c) return;
+    {
+        std::lock_guard<std::mutex> lk(c->qmu);
+        c->stopping = true;
+    }
+    c->qcv.notify_all();
+    for (auto& t : c->workers) t.join();
+    for (auto s : c->worker_streams) cudaStreamDestroy(s);
+    for (auto& kv : c->tickets) delete kv.second;
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_precond* P_out, spai_stats* st)
+{
+    if (!ctx || !A || !opts || !P_out) return SPAI_ERR_INVALID_ARG;
+    *P_out = nullptr;
+    int rc = csr_validate_host(A);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    DevCsr dA;
+    rc = csr_to_device(A, &dA, ctx->stream);
+    if (!rc) rc = spai_build_dev(ctx->device, ctx->num_sms, ctx->stream, dA, opts, P_out, st);
+    csr_release(&dA, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    return rc;
+}
+
+int spai_precond_info(spai_precond P, int64_t* n, int64_t* nnz)
+{
+    if (!P) return SPAI_ERR_INVALID_ARG;
+    if (n) *n = P->n;
+    if (nnz) *nnz = P->nnz;
+    return 0;
+}
+
+int spai_precond_export(spai_precond P, int64_t* rowptr, int32_t* col, double* val)
+{
+    if (!P) return SPAI_ERR_INVALID_ARG;
+    SPAI_CUDA_TRY(cudaSetDevice(P->device));
+    cudaStream_t s = P->stream;
+    if (rowptr) SPAI_CUDA_TRY(cudaMemcpyAsync(rowptr, P->rowptr, sizeof(int64_t) * (P->n + 1), cudaMemcpyDeviceToHost, s));
+    if (col) SPAI_CUDA_TRY(cudaMemcpyAsync(col, P->col, sizeof(int32_t) * P->nnz, cudaMemcpyDeviceToHost, s));
+    if (val) SPAI_CUDA_TRY(cudaMemcpyAsync(val, P->val, sizeof(double) * P->nnz, cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
+void spai_precond_free(spai_precond P)
+{
+    if (!P) return;
+    cudaSetDevice(P->device);
+    cudaStream_t s = P->stream;
+    dev_free(P->rowptr, s);
+    dev_free(P->col, s);
+    dev_free(P->val, s);
+    dev_free(P->val_f32, s);
+    dev_free(P->val_uf, s);
+    cudaStreamSynchronize(s);
+    delete P;
+}
+
+int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_opts* sopts, const double* b,
+                   double* x, const ir_opts* opts, ir_stats* st)
+{
+    if (!ctx || !A || !b || !x || !opts) return SPAI_ERR_INVALID_ARG;
+    int rc = csr_validate_host(A);
+    if (rc) return rc;
+    if (P && P->n != A->n) return SPAI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    if (st) memset(st, 0, sizeof(*st));
+    DevCsr dA;
+    double *db = nullptr, *dx = nullptr;
+    spai_precond own = nullptr;
+    int wrc = 0;
+    rc = csr_to_device(A, &dA, s);
+    if (!rc) {
+        if (A->on_device) {
+            db = const_cast<double*>(b);
+            dx = x;
+        } else {
+            rc = dev_alloc((void**)&db, sizeof(double) * A->n, s);
+            if (!rc) rc = dev_alloc((void**)&dx, sizeof(double) * A->n, s);
+            if (!rc && cudaMemcpyAsync(db, b, sizeof(double) * A->n, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        }
+    }
+    if (!rc && !P && sopts) {
+        spai_stats sst{};
+        rc = spai_build_dev(ctx->device, ctx->num_sms, s, dA, sopts, &own, &sst);
+        if (rc > 0) { wrc = rc; rc = 0; }
+        if (st) st->ms_spai = sst.ms;
+        P = own;
+    }
+    if (!rc) {
+        int rr = gmres_ir_dev(ctx->device, ctx->num_sms, s, dA, P, db, dx, opts, st);
+        if (rr < 0) rc = rr; else if (rr > 0) wrc = rr;
+    }
+    if (!rc && !A->on_device) {
+        if (cudaMemcpyAsync(x, dx, sizeof(double) * A->n, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
+    if (own) spai_precond_free(own);
+    if (!A->on_device) {
+        dev_free(db, s);
+        dev_free(dx, s);
+    }
+    csr_release(&dA, s);
+    cudaStreamSynchronize(s);
+    return rc ? rc : wrc;
+}
+
+int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_opts* sopts, const ir_opts* opts,
+                  uint64_t* ticket)
+{
+    if (!ctx || !A || !b || !opts || !ticket) return SPAI_ERR_INVALID_ARG;
+    int rc = csr_validate_host(A);
+    if (rc) return rc;
+    size_t bytes = estimate_footprint(A->n, A->nnz, sopts, opts);
+    if (bytes > ctx->budget) return SPAI_ERR_ADMISSION;
+    ServeRequest* r = new ServeRequest();
+    r->n = A->n;
+    r->nnz = A->nnz;
+    r->rowptr.resize(A->n + 1);
+    r->col.resize(A->nnz);
+    r->val.resize(A->nnz);
+    r->b.resize(A->n);
+    if (A->on_device) {
+        cudaSetDevice(ctx->device);
+        if (cudaMemcpy(r->rowptr.data(), A->rowptr, sizeof(int64_t) * (A->n + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(r->col.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(r->val.data(), A->val, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(r->b.data(), b, sizeof(double) * A->n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            delete r;
+            return SPAI_ERR_CUDA;
+        }
+    } else {
+        memcpy(r->rowptr.data(), A->rowptr, sizeof(int64_t) * (A->n + 1));
+        memcpy(r->col.data(), A->col, sizeof(int32_t) * A->nnz);
+        memcpy(r->val.data(), A->val, sizeof(double) * A->nnz);
+        memcpy(r->b.data(), b, sizeof(double) * A->n);
+    }
+    if (sopts) { r->so = *sopts; r->has_so = true; }
+    r->io = *opts;
+    r->bytes = bytes;
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        if (ctx->workers.empty()) {
+            const int nw = 4;
+            cudaSetDevice(ctx->device);
+            for (int i = 0; i < nw; i++) {
+                cudaStream_t s;
+                if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { delete r; return SPAI_ERR_CUDA; }
+                ctx->worker_streams.push_back(s);
+            }
+            for (int i = 0; i < nw; i++) ctx->workers.emplace_back(worker_loop, ctx, i);
+        }
+        r->ticket = ctx->next_ticket++;
+        ctx->tickets[r->ticket] = r;
+        ctx->pending.push_back(r);
+        *ticket = r->ticket;
+    }
+    ctx->qcv.notify_all();
+    return 0;
+}
+
+int solver_poll(spai_ctx ctx, uint64_t ticket, double* x, ir_stats* st)
+{
+    if (!ctx) return SPAI_ERR_INVALID_ARG;
+    ServeRequest* r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        auto it = ctx->tickets.find(ticket);
+        if (it == ctx->tickets.end()) return SPAI_ERR_NOT_FOUND;
+        r = it->second;
+        if (!r->done) return SPAI_PENDING;
+        ctx->tickets.erase(it);
+    }
+    if (x && r->status >= 0) memcpy(x, r->x.data(), sizeof(double) * r->n);
+    if (st) *st = r->st;
+    int rc = r->status;
+    delete r;
+    return rc;
+}
+
+const char* spai_strerror(int code)
+{
+    switch (code) {
+    case SPAI_OK: return "ok";
+    case SPAI_WARN_NOT_CONVERGED: return "refinement stopped at i_max above the stop tolerance";
+    case SPAI_WARN_FILLCAP: return "some SPAI columns stopped at the fill cap above eps";
+    case SPAI_PENDING: return "request pending";
+    case SPAI_ERR_INVALID_ARG: return "invalid argument";
+    case SPAI_ERR_ZERO_ROW: return "a row of A has no nonzero entry (A is singular)";
+    case SPAI_ERR_NONFINITE: return "non-finite value (input, or overflow in u_f)";
+    case SPAI_ERR_NO_MEMORY: return "device memory allocation failed";
+    case SPAI_ERR_ADMISSION: return "request exceeds the context's HBM budget";
+    case SPAI_ERR_TIMEOUT: return "a bounded device-side wait expired";
+    case SPAI_ERR_CUDA: return "CUDA runtime error";
+    case SPAI_ERR_UNSUPPORTED: return "precision tuple or size not supported";
+    case SPAI_ERR_NOT_FOUND: return "unknown ticket";
+    case SPAI_ERR_INTERNAL: return "device-side consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Host-side objects behind the C ABI (context, preconditioner, device CSR).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/spai_ir.h"
+
+// A CSR matrix resident on the device.  When `owned` is false the pointers
+// are borrowed from the caller for the duration of one call.
+struct DevCsr {
+    int64_t n = 0, nnz = 0;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    bool owned = false;
+};
+
+struct spai_precond_s {
+    int device = 0;
+    int64_t n = 0, nnz = 0;
+    int64_t* rowptr = nullptr;   // n + 1
+    int32_t* col = nullptr;      // nnz
+    double* val = nullptr;       // nnz, unrounded mbar_k * d(J_k)
+    float* val_f32 = nullptr;    // lazily made copy rounded to single (u_p = single)
+    void* val_uf = nullptr;      // copy rounded to u_f (used by x0 = P b)
+    int uf = SPAI_DOUBLE;
+    cudaStream_t stream = nullptr;
+};
+
+struct ServeRequest;
+
+struct spai_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0;
+    int num_sms = 0;
+    std::mutex mu;  // serialises the synchronous entry points
+    // serving queue
+    std::mutex qmu;
+    std::condition_variable qcv;
+    std::deque<ServeRequest*> pending;
+    std::map<uint64_t, ServeRequest*> tickets;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> worker_streams;
+    size_t in_use = 0;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+};
+
+// stream-ordered device allocation helpers
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+// upload or borrow a CSR
+int csr_to_device(const spai_csr* A, DevCsr* out, cudaStream_t s);
+void csr_release(DevCsr* d, cudaStream_t s);
+int csr_validate_host(const spai_csr* A);
+
+// phase implementations (spai_build.cu / gmres_ir.cu)
+int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
+                   spai_precond* P_out, spai_stats* st);
+int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
+                 const double* b_dev, double* x_dev, const ir_opts* o, ir_stats* st);
+
+// bytes the solve of an n x n system with nnz nonzeros may hold on the device
+size_t estimate_footprint(int64_t n, int64_t nnz, const spai_opts* so, const ir_opts* io);

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (the arithmetic of each side is stated in the oracle's header):
+* SPAI pattern J_k: bit-exact (integer work).
+* SPAI columns: the residual ||B(:,J_k) mbar_k - e_k||_2 re-evaluated in
+  float64 for both sides' mbar agrees to 1e-3 relative at u_f = half, 1e-6
+  at single and 1e-10 at double, plus the representation floor
+  4 u_f || |B(:,J_k)| |mbar_k| ||_2 (the u_f term of eq. (rhatbnd): storing
+  mbar in u_f moves the residual by that much whichever side computes it);
+  at least 99% of the columns must meet the relative tolerance alone.
+* GMRES-IR: same number of refinement steps, total GMRES iterations within
+  10%, normwise backward and forward errors within 10x of the oracle's.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_2202_10204_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2202_10204_gb300 as S  # noqa: E402
+
+RES_TOL = {"half": 1e-3, "single": 1e-6, "double": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = S.Context(0)
+    yield c
+    c.close()
+
+
+def true_colres(A, d, J_rows, J_cnt, mbar, floor=False):
+    """|| B(:, J_k) m_k - e_k ||_2 in float64 for every column k (B = A^T D);
+    with floor=True also || |B(:,J_k)| |m_k| ||_2."""
+    Ms = synth.to_scipy(A)
+    n = Ms.shape[0]
+    B = (Ms.T @ sp.diags(d)).tocsc()
+    rows, cols, vals = [], [], []
+    for k in range(n):
+        c = J_cnt[k]
+        rows.extend(J_rows[k][:c]); cols.extend([k] * c); vals.extend(mbar[k][:c])
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    R = (B @ M - sp.identity(n)).tocsc()
+    res = np.sqrt(np.asarray(R.multiply(R).sum(axis=0)).ravel())
+    if not floor:
+        return res
+    Q = (abs(B) @ abs(M)).tocsc()
+    return res, np.sqrt(np.asarray(Q.multiply(Q).sum(axis=0)).ravel())
+
+
+def assert_colres(res_gpu, res_orc, absbm, uf, mask=None):
+    tol = RES_TOL[uf]
+    u = O.UNIT_ROUNDOFF[O.prec(uf)]
+    diff = np.abs(res_gpu - res_orc)
+    if mask is not None:
+        diff, res_orc, absbm = diff[mask], res_orc[mask], absbm[mask]
+    floor = (4 * u + 64 * 2.0 ** -53) * absbm  # u_f representation + float64 evaluation
+    assert np.all(diff <= tol * res_orc + floor), np.max(diff - tol * res_orc - floor)
+    assert np.mean(diff <= tol * res_orc) >= 0.99, np.mean(diff <= tol * res_orc)
+
+
+def gpu_spai(ctx, A, **kw):
+    P, st = S.spai_build(ctx, A, S.make_spai_opts(**kw), per_column=True)
+    rp, ci, va = P.export()
+    return P, st, (rp, ci, va)
+
+
+def split_rows(rp, ci, va, d):
+    """Row k of P -> (J_k, mbar_k = P(k, J_k) / d(J_k))."""
+    n = len(rp) - 1
+    cnt = np.diff(rp).astype(np.int32)
+    F = int(cnt.max()) if n else 1
+    J = np.full((n, F), -1, dtype=np.int64)
+    M = np.zeros((n, F))
+    for k in range(n):
+        c = cnt[k]
+        J[k, :c] = ci[rp[k]:rp[k + 1]]
+        M[k, :c] = va[rp[k]:rp[k + 1]] / d[ci[rp[k]:rp[k + 1]]]
+    return J, cnt, M
+
+
+SPAI_CASES = [
+    ("2d-patA", lambda: synth.conv_diff_2d(20, 10.0, 1.0, 0.1, seed=1), O.PAT_A, 30),
+    ("3d-patA2", lambda: synth.conv_diff_3d(9, 50.0, seed=3), O.PAT_A2, 25),
+    ("rand-patA", lambda: synth.random_sparse(700, 9, seed=5), O.PAT_A, 12),
+    ("3d-capped", lambda: synth.conv_diff_3d((7, 6, 5), 50.0, seed=8), O.PAT_A2, 9),
+]
+
+
+@pytest.mark.parametrize("uf", ["half", "single", "double"])
+@pytest.mark.parametrize("name,make,init,F", SPAI_CASES)
+def test_spai_fixed_pattern_parity(ctx, name, make, init, F, uf):
+    A = make()
+    P, st, (rp, ci, va) = gpu_spai(ctx, A, init=init, max_fill=F, uf=uf, eps=0.0)
+    ref = O.spai(A, init=init, max_fill=F, uf=uf, eps=0.0)
+    n = ref["n"]
+    # pattern: bit-exact
+    assert np.array_equal(np.diff(rp), ref["Jcnt"])
+    for k in range(n):
+        assert np.array_equal(ci[rp[k]:rp[k + 1]], ref["Jidx"][k][: ref["Jcnt"][k]])
+    assert np.array_equal(st["nI"], ref["Icnt"])
+    J, cnt, M = split_rows(rp, ci, va, ref["d"])
+    res_gpu, absbm = true_colres(A, ref["d"], J, cnt, M, floor=True)
+    assert_colres(res_gpu, ref["colres64"], absbm, uf)
+    # the u_f-computed norms the kernel reports agree to a few u_f
+    u = O.UNIT_ROUNDOFF[O.prec(uf)]
+    assert np.all(np.abs(st["colres"] - ref["colres"]) <= 64 * u * ref["colres"] + 8 * u * absbm + 1e-14)
+    P.free()
+
+
+@pytest.mark.parametrize("uf", ["single", "double"])
+def test_spai_adaptive_parity(ctx, uf):
+    A = synth.random_sparse(400, 6, seed=12)
+    for eps in (0.5, 0.3):
+        P, st, (rp, ci, va) = gpu_spai(ctx, A, init=O.PAT_IDENTITY, adaptive=True, eps=eps, beta=8, max_fill=30,
+                                       uf=uf)
+        ref = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=eps, beta=8, max_fill=30, uf=uf)
+        n = ref["n"]
+        same = np.array([np.array_equal(ci[rp[k]:rp[k + 1]], ref["Jidx"][k][: ref["Jcnt"][k]]) for k in range(n)])
+        # selections may flip only on near-ties of rho: allow < 1% of columns
+        assert same.mean() >= 0.99, same.mean()
+        J, cnt, M = split_rows(rp, ci, va, ref["d"])
+        res_gpu, absbm = true_colres(A, ref["d"], J, cnt, M, floor=True)
+        assert_colres(res_gpu, ref["colres64"], absbm, uf, mask=same)
+        # every column meets eq. (trueres) or stopped at the cap / alpha
+        conv = (st["flags"] & 1) != 0
+        assert np.all(res_gpu[conv] <= 2 * eps)
+        assert np.array_equal(conv[same], (ref["flags"][same] & 1) != 0)
+        P.free()
+
+
+def run_pair(ctx, A, b, init, F, uf, u, ug, up, ur, tau, eps=0.0, adaptive=False):
+    so = S.make_spai_opts(init=init, max_fill=F, uf=uf, eps=eps, adaptive=adaptive)
+    io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    Sr = O.spai(A, init=init, max_fill=F, uf=uf, eps=eps, adaptive=adaptive)
+    ref = O.gmres_ir(A, b, O.assemble_P(Sr, up, uf), uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau)
+    return x, st, ref
+
+
+def errors(A, b, x, x_true):
+    Ms = synth.to_scipy(A)
+    nbe = np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b)))
+    fe = np.max(np.abs(x - x_true)) / np.max(np.abs(x_true))
+    return nbe, fe
+
+
+def check_ir(A, b, x_true, x, st, ref, u):
+    assert st["steps"] == ref["steps"], (st["its"], list(ref["its"]))
+    assert abs(st["total_its"] - ref["total_its"]) <= max(1, 0.1 * ref["total_its"]), (st["its"], list(ref["its"]))
+    nb_g, fe_g = errors(A, b, x, x_true)
+    nb_o, fe_o = errors(A, b, ref["x"], x_true)
+    assert nb_g <= 10 * max(nb_o, u)
+    assert fe_g <= 10 * max(fe_o, u)
+
+
+def test_ir_small_2d_single_double_quad(ctx):
+    A, b, x_true = synth.cfg_small_2d()
+    x, st, ref = run_pair(ctx, A, b, O.PAT_A, 30, "single", "double", "double", "double", "quad", 1e-4)
+    check_ir(A, b, x_true, x, st, ref, 2.0 ** -53)
+    assert st["final_nbe"] <= 1e-15
+    assert st["flags"] & 1
+
+
+def test_ir_3d_half_single(ctx):
+    A, b, x_true = synth.cfg_large_3d(N=16)
+    x, st, ref = run_pair(ctx, A, b, O.PAT_A2, 25, "half", "single", "single", "single", "double", 1e-4)
+    check_ir(A, b, x_true, x, st, ref, 2.0 ** -24)
+
+
+@pytest.mark.parametrize("tup", [("single", "double", "single", "single", "double"),
+                                 ("half", "single", "single", "double", "double"),
+                                 ("double", "double", "double", "double", "double"),
+                                 ("single", "double", "double", "single", "quad")])
+def test_ir_precision_tuples(ctx, tup):
+    uf, u, ug, up, ur = tup
+    A = synth.conv_diff_2d(24, 20.0, 1.0, 0.1, seed=7)
+    b, x_true = synth.rhs(A, seed=9)
+    tau = 1e-4 if ug == "single" else 1e-8
+    x, st, ref = run_pair(ctx, A, b, O.PAT_A, 30, uf, u, ug, up, ur, tau)
+    check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
+
+
+def test_ir_unpreconditioned(ctx):
+    A, b, x_true = synth.cfg_small_2d()
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, opts=io)
+    ref = O.gmres_ir(A, b, None, uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+    check_ir(A, b, x_true, x, st, ref, 2.0 ** -53)
+
+
+def test_ir_adaptive_random(ctx):
+    A = synth.random_sparse(600, 8, seed=21, log10_scale=3.0)
+    b, x_true = synth.rhs(A, seed=3)
+    x, st, ref = run_pair(ctx, A, b, O.PAT_IDENTITY, 30, "single", "double", "double", "double", "quad", 1e-8,
+                          eps=0.4, adaptive=True)
+    check_ir(A, b, x_true, x, st, ref, 2.0 ** -53)
+
+
+def test_device_buffers_match_host_buffers(ctx):
+    A, b, x_true = synth.cfg_small_2d()
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+    xh = np.zeros_like(b)
+    S.gmres_ir_solve(ctx, A, b, xh, sopts=so, opts=io)
+    Ad = tuple(torch.from_numpy(a).cuda() for a in A)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    torch.cuda.synchronize()
+    S.gmres_ir_solve(ctx, Ad, bd, xd, sopts=so, opts=io)
+    assert np.array_equal(xd.cpu().numpy(), xh)  # deterministic: bitwise equal
+
+
+def test_edge_cases(ctx):
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8)
+    so = S.make_spai_opts(init=0, max_fill=4, uf="single")
+    # n = 1
+    A1 = (np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([4.0]))
+    x = np.zeros(1)
+    st = S.gmres_ir_solve(ctx, A1, np.array([2.0]), x, sopts=so, opts=io)
+    assert x[0] == 0.5
+    # diagonal system: identity pattern is the exact inverse, one iteration
+    a = np.array([2.0, -3.0, 0.5, 7.0, -0.25])
+    Ad = synth._to_csr(sp.diags(a))
+    b = np.arange(1.0, 6.0)
+    x = np.zeros(5)
+    st = S.gmres_ir_solve(ctx, Ad, b, x, sopts=so, opts=io)
+    np.testing.assert_allclose(x, b / a, rtol=1e-15)
+    # zero right-hand side: x = 0 with no GMRES work
+    A, b, _ = synth.cfg_small_2d()
+    x = np.ones_like(b)
+    st = S.gmres_ir_solve(ctx, A, np.zeros_like(b), x, sopts=S.make_spai_opts(init=1, max_fill=30), opts=io)
+    assert np.all(x == 0) and st["steps"] == 0
+    # a zero row is singular
+    Az = (np.array([0, 1, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([1.0]))
+    with pytest.raises(S.SpaiError) as e:
+        S.gmres_ir_solve(ctx, Az, np.ones(2), np.zeros(2), sopts=so, opts=io)
+    assert e.value.code == -2
+    # unsorted columns are rejected
+    Au = (np.array([0, 2, 3], dtype=np.int64), np.array([1, 0, 1], dtype=np.int32), np.array([1.0, 2.0, 3.0]))
+    with pytest.raises(S.SpaiError) as e:
+        S.gmres_ir_solve(ctx, Au, np.ones(2), np.zeros(2), sopts=so, opts=io)
+    assert e.value.code == -1
+    # unsupported fill cap
+    with pytest.raises(S.SpaiError) as e:
+        S.spai_build(ctx, A, S.make_spai_opts(init=1, max_fill=40))
+    assert e.value.code == -8
