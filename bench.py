@@ -1,0 +1,332 @@
+"""Benchmark: SPAI-GMRES-IR solves/s on the 64^3 convection-diffusion system.
+
+Workload (one "step" = one full solve: SPAI build on A^T D with pattern(A^2)
+plus the whole refinement loop): 3D 7-point convection-diffusion on a 64^3
+grid (n = 262144, 1,810,432 nonzeros), per-cell coefficients lognormal(0,1),
+Peclet 50 upwind; precisions (u_f,u,u_g,u_p,u_r) = (half, single, single,
+single, double); tau = 1e-4; b = A x_true with x_true ~ N(0,1).  Inputs are
+seeded and synthetic.
+
+N > 1 (torchrun): every rank solves its own copy (independent replicas, weak
+scaling); no collective is on the data path.
+
+``--impl reference`` times the CPU oracle (the only reference that exists for
+this method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPAI-GMRES-IR solves/s (64^3 conv-diff, (half,single,single,single,double))"
+UNIT = "solves/s"
+WORKLOAD = "3D 7-point convection-diffusion 64^3, n=262144, lognormal(0,1) cells, Peclet 50, SPAI pattern(A^2)"
+TUPLE = dict(uf="half", u="single", ug="single", up="single", ur="double")
+TAU = 1e-4
+MAX_FILL = 25
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, default=64, help="grid points per dimension")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def nproc():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def oracle_sample(grid=20):
+    """One oracle solve of the same generator at grid^3 (single thread)."""
+    import oracle as O
+    from paper_2202_10204_gb300 import synth
+    A, b, x = synth.cfg_large_3d(N=grid)
+    t0 = time.perf_counter()
+    S = O.spai(A, init=O.PAT_A2, max_fill=MAX_FILL, uf=TUPLE["uf"], eps=0.3)
+    P = O.assemble_P(S, TUPLE["up"], TUPLE["uf"])
+    R = O.gmres_ir(A, b, P, tau=TAU, **TUPLE)
+    dt = time.perf_counter() - t0
+    return dt, grid ** 3, R
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n_full = args.grid ** 3
+    grid = 20
+    import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(grid)
+    times = []
+    for _ in range(args.steps):
+        dt, n_s, R = oracle_sample(grid)
+        times.append(dt * n_full / n_s)  # scaled to the full-size system (linear in n)
+    tot = sum(times)
+    value = args.steps / tot
+    sample = ("oracle SPAI-GMRES-IR of the same generator at %d^3 (n=%d), 1 thread, time scaled by n to %d^3"
+              % (grid, grid ** 3, args.grid))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * tot / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, n=n_full, tuple=TUPLE, tau=TAU),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device_index=0):
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(rows))
+
+
+# ---------------------------------------------------------------- algorithmic bytes
+
+def ir_kernel_bytes(n, nnz_a, nnz_p, its, s_u=4, s_g=4, s_p=4):
+    """Algorithmic HBM bytes of one refinement-kernel launch.
+
+    Per Arnoldi iteration j: SpMV A (values in u_p + int32 cols + int64 rowptr,
+    read v, write t), SpMV P (same, read t), MGS (read V(:,0..j) once, write
+    v_{j+1} and the published w).  Per refinement step: residual (A in fp64,
+    b, x, r), z = P r, correction d = V y (read V(:,0..k-1), x in and out).
+    The final residual evaluation is included.
+    """
+    rp = (n + 1) * 8
+    spmv_a = nnz_a * (s_p + 4) + rp + n * s_g + n * s_p
+    spmv_p = nnz_p * (s_p + 4) + rp + n * s_p
+    resid = nnz_a * (8 + 4) + rp + n * 8 + n * s_u + n * s_u
+    total = resid  # the last residual (the stop test)
+    for k in its:
+        total += resid + nnz_p * (s_p + 4) + rp + n * s_u + n * s_g
+        for j in range(k):
+            total += spmv_a + spmv_p + (j + 1) * n * s_g + 2 * n * s_g
+        total += k * n * s_g + 2 * n * s_u
+    return total
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    import paper_2202_10204_gb300 as S
+    from paper_2202_10204_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    A, b, x_true = synth.cfg_large_3d(N=args.grid)
+    n = len(A[0]) - 1
+    nnz = len(A[1])
+    Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    ctx = S.Context(local, stream=stream)
+    so = S.make_spai_opts(init=2, max_fill=MAX_FILL, uf=TUPLE["uf"], eps=0.3)
+    io = S.make_ir_opts(tau=TAU, **TUPLE)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        P, sst = S.spai_build(ctx, Ad, so)
+        st = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io)
+        P.free()
+        st["ms_spai"] = sst["ms"]
+        st["ms_spai_kernel"] = sst["ms_kernel"]
+        st["launches"] += sst["launches"]
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    with ClockSampler(clk_path) as cs:
+        time.sleep(0.3)
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(stream)
+            stats.append(step())
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    per = [e0.elapsed_time(e1) for e0, e1 in ev]
+    tot_ms = float(sum(per))
+    t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tot_max = float(t.item())
+    value = world * args.steps / (tot_max / 1000.0)
+
+    # correctness of the timed solves (the metric counts solves meeting the accuracy bar)
+    x = xd.cpu().numpy()
+    Ms = synth.to_scipy(A)
+    nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+    fe = float(np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)))
+    last = stats[-1]
+
+    # dominant kernel roofline: the persistent refinement kernel (HBM-bound)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    ir_ms = [s["ms_kernel"] for s in stats]
+    ir_bytes = [ir_kernel_bytes(n, nnz, s["nnz_P"], s["its"]) for s in stats]
+    achieved = float(np.mean([b_ / (m / 1000.0) for b_, m in zip(ir_bytes, ir_ms)]) / 1e9)
+    spai_ms = float(np.mean([s["ms_spai"] for s in stats]))
+    launches = int(sum(s["launches"] for s in stats))
+    lat = np.array(per)
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = tuple(torch.from_numpy(a).pin_memory() for a in A)
+        bh = torch.from_numpy(b).pin_memory()
+        xh = torch.zeros_like(bh).pin_memory()
+        S.gmres_ir_solve(ctx, Ah, bh, xh, sopts=so, opts=io)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ke = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(ke):
+            S.gmres_ir_solve(ctx, Ah, bh, xh, sopts=so, opts=io)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        h2d = sum(a.numel() * a.element_size() for a in Ah) + bh.numel() * 8
+        e2e = dict(value=world * ke / (float(te.item()) / 1000.0), unit=UNIT, h2d_bytes_per_step=int(h2d),
+                   d2h_bytes_per_step=int(n * 8 + 4 * 2), steps=ke)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle as O
+            O.build()
+            g = 32
+            dt, n_s, R = oracle_sample(g)
+            cpu = dict(value=1.0 / (dt * n / n_s), unit=UNIT, cores=1, kind="oracle",
+                       sample="oracle SPAI-GMRES-IR of the same generator at %d^3 (n=%d) in %.1f s, 1 thread, "
+                              "time scaled by n to %d^3" % (g, n_s, dt, args.grid))
+        except Exception as e:  # the baseline is reported, never required
+            cpu = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample="failed: %s" % e)
+
+    clocks = cs.summary(local)
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=tot_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f16/f32 (u_f half; u, u_g, u_p single; u_r double)", data="synthetic",
+            config=dict(workload=WORKLOAD, n=n, nnz=nnz, nnz_P=int(last["nnz_P"]), tuple=TUPLE, tau=TAU,
+                        max_fill=MAX_FILL, l2="flushed between timed steps (256 MiB write)",
+                        parallelism="replicas" if world > 1 else "single GPU"),
+            latency_ms=dict(p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99))),
+            spai_cols_per_s=n / (spai_ms / 1000.0),
+            phases_ms=dict(spai_build=spai_ms, spai_column_kernel=float(np.mean([s["ms_spai_kernel"] for s in stats])),
+                           ir_total=float(np.mean([s["ms_ir"] for s in stats])),
+                           ir_kernel=float(np.mean(ir_ms))),
+            ir=dict(steps=last["steps"], its=last["its"], total_its=last["total_its"], grid=last["grid"],
+                    backward_error=nbe, forward_error=fe, nbe_trace=last["nbe"]),
+            roofline=dict(kernel="k_ir (persistent refinement kernel)", bound="hbm", achieved=achieved,
+                          peak=hbm_peak, unit="GB/s", frac=achieved / hbm_peak, traffic=None,
+                          peak_source=peak_src, algorithmic_bytes_per_launch=float(np.mean(ir_bytes))),
+            gpu_launches=launches,
+            clocks=clocks,
+            e2e=e2e,
+            cpu_baseline=cpu,
+        )
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -114,6 +114,8 @@ typedef struct {
     int64_t cols_nonfinite;    /* columns with Inf/NaN (overflow in u_f)              */
     int max_I, max_J;          /* largest |I_k| and |J_k|                             */
     double ms;                 /* device time of the build, milliseconds              */
+    double ms_kernel;          /* device time of the column kernel alone              */
+    int launches;              /* kernels the build launched                          */
     /* optional per-column host outputs, filled when non-NULL (length n each): */
     double* colres;            /* ||s_k||_2 as computed in u_f                         */
     int32_t* nJ;               /* |J_k|                                                */
@@ -131,6 +133,9 @@ typedef struct {
     int flags;                           /* 1 converged, 2 max steps, 4 breakdown, 8 non-finite */
     int64_t nnz_P;
     double ms_spai, ms_ir;               /* device time of the two phases            */
+    double ms_kernel;                    /* device time of the refinement kernel alone */
+    int launches;                        /* kernels launched (build included)        */
+    int grid;                            /* blocks of the refinement kernel          */
 } ir_stats;
 
 typedef struct spai_ctx_s* spai_ctx;

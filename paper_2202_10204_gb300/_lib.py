@@ -49,14 +49,15 @@ class ir_opts(C.Structure):
 class spai_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_P", C.c_int64), ("cols_converged", C.c_int64),
                 ("cols_fillcap", C.c_int64), ("cols_nonfinite", C.c_int64), ("max_I", C.c_int),
-                ("max_J", C.c_int), ("ms", C.c_double), ("colres", C.c_void_p), ("nJ", C.c_void_p),
-                ("nI", C.c_void_p), ("flags", C.c_void_p)]
+                ("max_J", C.c_int), ("ms", C.c_double), ("ms_kernel", C.c_double), ("launches", C.c_int),
+                ("colres", C.c_void_p), ("nJ", C.c_void_p), ("nI", C.c_void_p), ("flags", C.c_void_p)]
 
 
 class ir_stats(C.Structure):
     _fields_ = [("steps", C.c_int), ("total_its", C.c_int), ("its", C.c_int * SPAI_IR_MAX_STEPS),
                 ("nbe", C.c_double * (SPAI_IR_MAX_STEPS + 1)), ("final_nbe", C.c_double), ("flags", C.c_int),
-                ("nnz_P", C.c_int64), ("ms_spai", C.c_double), ("ms_ir", C.c_double)]
+                ("nnz_P", C.c_int64), ("ms_spai", C.c_double), ("ms_ir", C.c_double),
+                ("ms_kernel", C.c_double), ("launches", C.c_int), ("grid", C.c_int)]
 
 
 _lib = None
@@ -212,7 +213,8 @@ def spai_build(ctx: Context, A, opts: spai_opts, per_column=False):
     h = C.c_void_p()
     rc = _check(lib().spai_build(ctx.h, C.byref(csr), C.byref(opts), C.byref(h), C.byref(st)), "spai_build")
     out = dict(n=st.n, nnz_P=st.nnz_P, cols_converged=st.cols_converged, cols_fillcap=st.cols_fillcap,
-               cols_nonfinite=st.cols_nonfinite, max_I=st.max_I, max_J=st.max_J, ms=st.ms, rc=rc)
+               cols_nonfinite=st.cols_nonfinite, max_I=st.max_I, max_J=st.max_J, ms=st.ms,
+               ms_kernel=st.ms_kernel, launches=st.launches, rc=rc)
     out.update(cols)
     return Precond(h), out
 
@@ -220,7 +222,8 @@ def spai_build(ctx: Context, A, opts: spai_opts, per_column=False):
 def _ir_dict(st, rc):
     s = st.steps
     return dict(steps=s, total_its=st.total_its, its=list(st.its[:s]), nbe=list(st.nbe[:s + 1]),
-                final_nbe=st.final_nbe, flags=st.flags, nnz_P=st.nnz_P, ms_spai=st.ms_spai, ms_ir=st.ms_ir, rc=rc)
+                final_nbe=st.final_nbe, flags=st.flags, nnz_P=st.nnz_P, ms_spai=st.ms_spai, ms_ir=st.ms_ir,
+                ms_kernel=st.ms_kernel, launches=st.launches, grid=st.grid, rc=rc)
 
 
 def gmres_ir_solve(ctx: Context, A, b, x, P: Precond | None = None, sopts: spai_opts | None = None,

@@ -130,6 +130,7 @@ static void run_request(spai_ctx ctx, cudaStream_t s, ServeRequest* r)
         rc = spai_build_dev(ctx->device, ctx->num_sms, s, dA, &r->so, &P, &sst);
         if (rc > 0) { wrc = rc; rc = 0; }
         r->st.ms_spai = sst.ms;
+        r->st.launches = sst.launches;
     }
     if (rc >= 0 && !(rc < 0)) {
         int rr = gmres_ir_dev(ctx->device, ctx->num_sms, s, dA, P, db, dx, &r->io, &r->st);
@@ -301,7 +302,7 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
         spai_stats sst{};
         rc = spai_build_dev(ctx->device, ctx->num_sms, s, dA, sopts, &own, &sst);
         if (rc > 0) { wrc = rc; rc = 0; }
-        if (st) st->ms_spai = sst.ms;
+        if (st) { st->ms_spai = sst.ms; st->launches = sst.launches; }
         P = own;
     }
     if (!rc) {

@@ -176,7 +176,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch
         unsigned e = *epoch + 1u;
         *epoch = e;
         const unsigned target = e * gridDim.x;
-        __threadfence();
+        // release: the bar.sync above orders the block's writes before it
         red_release_add_u32(gb.count, 1u);
         int ok = 1;
         const long long t0 = clock64();
@@ -191,7 +191,6 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch
                 }
             }
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();

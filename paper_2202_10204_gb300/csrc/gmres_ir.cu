@@ -32,7 +32,7 @@ using namespace spai;
 
 namespace {
 
-constexpr int IR_THREADS = 512;
+constexpr int IR_THREADS = 1024;
 constexpr int KMAX_LIMIT = 1024;
 
 struct IrArgs {
@@ -74,6 +74,27 @@ template <class T> __device__ __forceinline__ T ldv_(const T* p) { return ldcg(p
 
 // Sum of a block-uniform value over all blocks; every block gets the same
 // bits.  Returns false if the barrier failed.
+// Lane-strided sum of the G partials of `slot`, all loads in flight at once
+// (the partials live in L2; a dependent chain of loads would serialise their
+// latency).  Fixed order: lane l adds l, l+32, l+64, ...
+template <class T>
+__device__ __forceinline__ T lane_partial_sum(const double* part, int slot, int comp)
+{
+    const unsigned G = gridDim.x, lane = threadIdx.x;
+    const double* base = part + (size_t)slot * G * 2 + comp;
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        unsigned i = lane + 32u * u;
+        v[u] = i < G ? __ldcg(base + (size_t)i * 2) : 0.0;
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int u = 0; u < 8; u++) acc += (T)v[u];
+    for (unsigned i = lane + 256u; i < G; i += 32) acc += (T)__ldcg(base + (size_t)i * 2);
+    return acc;
+}
+
 template <class T>
 __device__ bool gsum(const IrArgs& a, IrShared* sh, T v, T& out)
 {
@@ -81,8 +102,7 @@ __device__ bool gsum(const IrArgs& a, IrShared* sh, T v, T& out)
     if (threadIdx.x == 0) a.part[(size_t)(slot * gridDim.x + blockIdx.x) * 2] = (double)v;
     if (!grid_sync(a.gb, &sh->epoch, &sh->flag)) return false;
     if (threadIdx.x < 32) {
-        T acc = T(0);
-        for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) acc += (T)__ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2]);
+        T acc = lane_partial_sum<T>(a.part, slot, 0);
         acc = warp_sum(acc);
         if (threadIdx.x == 0) { sh->bcast[0] = (double)acc; sh->slot = slot ^ 1; }
     }
@@ -103,8 +123,10 @@ __device__ bool gmax2(const IrArgs& a, IrShared* sh, double v0, double v1, doubl
     if (threadIdx.x < 32) {
         double m0 = 0.0, m1 = 0.0;
         for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) {
-            m0 = fmax(m0, __ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2]));
-            m1 = fmax(m1, __ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2 + 1]));
+            double p0 = __ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2]);
+            double p1 = __ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2 + 1]);
+            m0 = fmax(m0, p0);
+            m1 = fmax(m1, p1);
         }
         m0 = warp_max(m0);
         m1 = warp_max(m1);
@@ -139,7 +161,7 @@ __device__ __forceinline__ void spmv_rows(int64_t r0, int64_t r1, int L, const i
 }
 
 template <class TU, class TG, class TP, int RM>
-__global__ void __launch_bounds__(IR_THREADS) k_ir(IrArgs a)
+__global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ IrShared shs;
@@ -454,9 +476,12 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     const int imax = o->ir_max_steps;
 
     int rc = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, ek0 = nullptr, ek1 = nullptr;
     SPAI_CUDA_TRY(cudaEventCreate(&e0));
     SPAI_CUDA_TRY(cudaEventCreate(&e1));
+    SPAI_CUDA_TRY(cudaEventCreate(&ek0));
+    SPAI_CUDA_TRY(cudaEventCreate(&ek1));
+    int nl = 0;  // kernels launched
     const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
     void *x = nullptr, *r = nullptr, *wbuf = nullptr, *tbuf = nullptr, *V = nullptr, *aval_p = nullptr;
     double *R = nullptr, *part = nullptr, *nbe = nullptr;
@@ -498,6 +523,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     if (o->up == SPAI_SINGLE) {
         TRY(dev_alloc(&aval_p, sizeof(float) * (A.nnz > 0 ? A.nnz : 1), s));
         k_to_float<<<gb, tb, 0, s>>>(A.nnz, A.val, (float*)aval_p);
+        nl++;
     }
     // P in u_p
     if (P) {
@@ -505,6 +531,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
             if (!P->val_f32) {
                 TRY(dev_alloc((void**)&P->val_f32, sizeof(float) * (P->nnz > 0 ? P->nnz : 1), s));
                 k_to_float<<<gb, tb, 0, s>>>(P->nnz, P->val, P->val_f32);
+                nl++;
             }
             pval_p = P->val_f32;
         } else {
@@ -512,6 +539,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         }
     }
     k_norms<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, b, norms);
+    nl++;
     CTRY(cudaMemcpyAsync(h_norms, norms, sizeof(h_norms), cudaMemcpyDeviceToHost, s));
     // x0 = P b in u_f, stored in u
     {
@@ -529,6 +557,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
             else X0(double, double);
         }
 #undef X0
+        nl++;
         CTRY(cudaGetLastError());
     }
     CTRY(cudaStreamSynchronize(s));
@@ -558,6 +587,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         a.lp = P ? lanes_for(n > 0 ? (double)P->nnz / n : 1.0) : 1;
         a.its = its; a.nbe = nbe; a.out = outv;
         const int rm = o->ur == SPAI_QUAD ? 2 : 1;
+        CTRY(cudaEventRecord(ek0, s));
         if (o->u == SPAI_DOUBLE) {
             if (o->ug == SPAI_DOUBLE) {
                 if (o->up == SPAI_DOUBLE) TRY((launch_ir_rm<double, double, double>(a, rm, num_sms, s, &grid)));
@@ -576,8 +606,11 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
             }
         }
     }
+    CTRY(cudaEventRecord(ek1, s));
+    nl++;
     if (o->u == SPAI_SINGLE) k_to_double<float><<<gb, tb, 0, s>>>(n, (const float*)x, xout);
     else k_to_double<double><<<gb, tb, 0, s>>>(n, (const double*)x, xout);
+    nl++;
     CTRY(cudaGetLastError());
     CTRY(cudaEventRecord(e1, s));
     CTRY(cudaMemcpyAsync(h_out, outv, sizeof(h_out), cudaMemcpyDeviceToHost, s));
@@ -600,6 +633,10 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         st->ms_ir = ms;
+        cudaEventElapsedTime(&ms, ek0, ek1);
+        st->ms_kernel = ms;
+        st->launches += nl;
+        st->grid = grid;
         st->nnz_P = P ? P->nnz : 0;
     }
     if (h_out[1] & 8) rc = SPAI_ERR_NONFINITE;
@@ -612,6 +649,8 @@ done:
     dev_free(bar, s); dev_free(norms, s);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (ek0) cudaEventDestroy(ek0);
+    if (ek1) cudaEventDestroy(ek1);
     if (rc < 0) cudaStreamSynchronize(s);
     return rc;
 }

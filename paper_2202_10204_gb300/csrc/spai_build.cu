@@ -732,9 +732,12 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
     if (o->adaptive && o->beta < 1) return SPAI_ERR_INVALID_ARG;
     if (!(o->eps >= 0.0)) return SPAI_ERR_INVALID_ARG;
     const int F = o->max_fill;
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, ek0, ek1;
     SPAI_CUDA_TRY(cudaEventCreate(&e0));
     SPAI_CUDA_TRY(cudaEventCreate(&e1));
+    SPAI_CUDA_TRY(cudaEventCreate(&ek0));
+    SPAI_CUDA_TRY(cudaEventCreate(&ek1));
+    int nl = 0;  // kernels launched
     SPAI_CUDA_TRY(cudaEventRecord(e0, s));
 
     int rc = 0;
@@ -780,13 +783,16 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         int gb = (int)std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32);
         if (gb < 1) gb = 1;
         k_scale<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, o->scale, d, err);
+        nl++;
         int gq = (int)std::min<int64_t>((nnz + tb - 1) / tb, (int64_t)num_sms * 32);
         if (gq < 1) gq = 1;
         k_col_count<<<gq, tb, 0, s>>>(nnz, A.col, ccount);
         TRY(scan_counts(n, ccount, cp, s));
+        nl += 1 + 3;
         if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         k_col_fill<<<gb, tb, 0, s>>>(n, A.rowptr, A.col, cp, ccount, ri);
         k_col_sort<<<gb, tb, 0, s>>>(n, cp, ri);
+        nl += 2;
     }
     {
         // the pattern: buffer for the uncapped union of pattern(A^2)
@@ -799,6 +805,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, cp, ri, Jidx, Jcnt, cap, err);
         k_shadow_count<<<(unsigned)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms * 64), 256, 0, s>>>(
             n, F, A.rowptr, A.col, A.val, Jidx, Jcnt, Icnt, err + 1);
+        nl += 2;
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaMemcpyAsync(h_err, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -809,6 +816,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         int* mr = err + 3;
         k_max_row<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8) + 1, 256, 0, s>>>(n, A.rowptr, mr);
         k_max_row<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8) + 1, 256, 0, s>>>(n, cp, mr + 1);
+        nl += 2;
         if (cudaMemcpyAsync(&maxrow, mr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaMemcpyAsync(&maxcol, mr + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -831,15 +839,19 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         // raw candidate capacity: |I| * (largest column count of A); power of two
         while (cmax < (int64_t)a.mmax * maxcol) cmax <<= 1;
         a.cmax = cmax > 8192 ? 8192 : (cmax < 256 ? 256 : cmax);
+        if (cudaEventRecord(ek0, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (o->uf == SPAI_HALF) TRY(launch_spai<__half>(a, o->adaptive != 0, num_sms, smem_cap, s));
         else if (o->uf == SPAI_SINGLE) TRY(launch_spai<float>(a, o->adaptive != 0, num_sms, smem_cap, s));
         else TRY(launch_spai<double>(a, o->adaptive != 0, num_sms, smem_cap, s));
+        if (cudaEventRecord(ek1, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        nl++;
     }
     // assemble P
     P = new spai_precond_s();
     P->n = n; P->uf = o->uf; P->stream = s; P->device = device;
     TRY(dev_alloc((void**)&P->rowptr, sizeof(int64_t) * (n + 1), s));
     TRY(scan_counts(n, Jcnt, P->rowptr, s));
+    nl += 3;
     if (cudaMemcpyAsync(&P->nnz, P->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     TRY(dev_alloc((void**)&P->col, sizeof(int32_t) * (P->nnz > 0 ? P->nnz : 1), s));
@@ -856,6 +868,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         else
             k_assemble<double><<<gb, tb, 0, s>>>(n, F, Jidx, Jcnt, Praw, P->rowptr, P->col, P->val, (double*)P->val_uf);
         k_flag_stats<<<gb, tb, 0, s>>>(n, flags, Jcnt, fstat, err + 2);
+        nl += 2;
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     }
     if (cudaEventRecord(e1, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -880,6 +893,9 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         st->ms = ms;
+        cudaEventElapsedTime(&ms, ek0, ek1);
+        st->ms_kernel = ms;
+        st->launches = nl;
     }
     if (h_fstat[2] > 0) rc = SPAI_ERR_NONFINITE;
     else if (h_fstat[1] > 0) rc = SPAI_WARN_FILLCAP;
@@ -890,6 +906,8 @@ done:
     dev_free(Praw, s); dev_free(colres, s); dev_free(mval, s); dev_free(fstat, s);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(ek0);
+    cudaEventDestroy(ek1);
     if (rc < 0) {
         if (P) spai_precond_free(P);
         *P_out = nullptr;
