@@ -34,29 +34,40 @@ namespace {
 
 constexpr int IR_THREADS = 1024;
 constexpr int KMAX_LIMIT = 1024;
+constexpr int MAX_GRID = 160;   // exchange slots are polled by one warp, SPL slots per lane
+constexpr int SPL = (MAX_GRID + 31) / 32;
+constexpr int PF = 4;           // rows per thread whose next basis entries are prefetched
+
+// SELL-32: rows in slices of 32; slice s stores its entries column-major
+// (entry c of row 32s+l at off[s] + 32c + l), padded to the slice's longest
+// row with (col = own row, val = 0).  Loads of one entry slot by a warp are
+// one contiguous 128-byte line.
+struct Sell {
+    const int64_t* off;  // nslices + 1 element offsets
+    const int32_t* col;
+    const void* val;     // precision u_p
+};
 
 struct IrArgs {
     int64_t n;
-    int64_t rb;                 // rows per block
-    const int64_t* arp;
+    int64_t rb;                 // rows per block (multiple of 32)
+    Sell A, P;                  // P.off == nullptr: P = I
+    const int64_t* arp;         // A in CSR, float64 (residual)
     const int32_t* aci;
-    const double* aval;         // A in double (residual)
-    const void* aval_p;         // A in u_p
-    const int64_t* prp;         // P (may be null: P = I)
-    const int32_t* pci;
-    const void* pval_p;         // P in u_p
+    const double* aval;
     const double* b;
     void* x;                    // n, precision u
     void* r;                    // n, precision u
     void* wbuf;                 // n, precision u_g: published w (or z)
     void* tbuf;                 // n, precision u_p: t = A v
-    void* V;                    // ldv x (kmax + 1), precision u_g; only own rows are ever read back
+    void* V;                    // ldv x (kmax + 1), precision u_g; a block reads back only its own rows
     int64_t ldv;
     double* R;                  // (kmax + 1) x kmax column-major, written by block 0
-    double* part;              // 2 slots x gridDim.x partials (two values each)
-    GridBarrier gb;
+    unsigned long long* msg;    // [2 parities][gridDim.x][4] epoch-tagged words
+    int* err;
+    long long limit;            // clock64 cycles a wait may take
     double anorm, bnorm, tau, stop_tol;
-    int kmax, imax, stop_rule, la, lp;
+    int kmax, imax, stop_rule;
     int* its;                   // imax
     double* nbe;                // imax + 1
     int* out;                   // [0] steps, [1] flags
@@ -64,99 +75,239 @@ struct IrArgs {
 
 struct IrShared {
     unsigned epoch;
-    int flag;
-    int slot;
+    int ok;
     double bcast[2];
     double resid;
 };
 
-template <class T> __device__ __forceinline__ T ldv_(const T* p) { return ldcg(p); }
-
-// Sum of a block-uniform value over all blocks; every block gets the same
-// bits.  Returns false if the barrier failed.
-// Lane-strided sum of the G partials of `slot`, all loads in flight at once
-// (the partials live in L2; a dependent chain of loads would serialise their
-// latency).  Fixed order: lane l adds l, l+32, l+64, ...
-template <class T>
-__device__ __forceinline__ T lane_partial_sum(const double* part, int slot, int comp)
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
 {
-    const unsigned G = gridDim.x, lane = threadIdx.x;
-    const double* base = part + (size_t)slot * G * 2 + comp;
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-        unsigned i = lane + 32u * u;
-        v[u] = i < G ? __ldcg(base + (size_t)i * 2) : 0.0;
-    }
-    T acc = T(0);
-#pragma unroll
-    for (int u = 0; u < 8; u++) acc += (T)v[u];
-    for (unsigned i = lane + 256u; i < G; i += 32) acc += (T)__ldcg(base + (size_t)i * 2);
-    return acc;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-template <class T>
-__device__ bool gsum(const IrArgs& a, IrShared* sh, T v, T& out)
+// One exchange round among all blocks of the co-resident grid.  Thread 0
+// publishes NW 32-bit payload words, each tagged with the round's epoch in
+// the upper 32 bits (one single-copy-atomic 64-bit store per word) after a
+// fence that orders everything the block wrote before the preceding
+// __syncthreads.  Warp 0 then polls every block's words of that epoch (lane
+// l owns blocks l, l+32, ...), feeding them to `acc` in that fixed order,
+// until one pass sees every word carry the epoch; it then fences (acquire)
+// and `acc.finish` combines the lanes and publishes to shared memory.  Slots
+// alternate between two parities, so a block can only overwrite a slot after
+// every block has read it.  The wait is bounded: on expiry SPAI_ERR_TIMEOUT
+// goes to *err and every block leaves.  Must be called by all threads after
+// a __syncthreads that follows the block's writes.
+template <int NW, bool DATA, class Acc>
+__device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const uint32_t* pay, Acc& acc)
 {
-    const int slot = sh->slot;
-    if (threadIdx.x == 0) a.part[(size_t)(slot * gridDim.x + blockIdx.x) * 2] = (double)v;
-    if (!grid_sync(a.gb, &sh->epoch, &sh->flag)) return false;
+    const unsigned G = gridDim.x;
     if (threadIdx.x < 32) {
-        T acc = lane_partial_sum<T>(a.part, slot, 0);
-        acc = warp_sum(acc);
-        if (threadIdx.x == 0) { sh->bcast[0] = (double)acc; sh->slot = slot ^ 1; }
-    }
-    __syncthreads();
-    out = (T)sh->bcast[0];
-    return true;
-}
-
-// Max of two block-uniform values over all blocks.
-__device__ bool gmax2(const IrArgs& a, IrShared* sh, double v0, double v1, double& o0, double& o1)
-{
-    const int slot = sh->slot;
-    if (threadIdx.x == 0) {
-        a.part[(size_t)(slot * gridDim.x + blockIdx.x) * 2] = v0;
-        a.part[(size_t)(slot * gridDim.x + blockIdx.x) * 2 + 1] = v1;
-    }
-    if (!grid_sync(a.gb, &sh->epoch, &sh->flag)) return false;
-    if (threadIdx.x < 32) {
-        double m0 = 0.0, m1 = 0.0;
-        for (unsigned i = threadIdx.x; i < gridDim.x; i += 32) {
-            double p0 = __ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2]);
-            double p1 = __ldcg(&a.part[(size_t)(slot * gridDim.x + i) * 2 + 1]);
-            m0 = fmax(m0, p0);
-            m1 = fmax(m1, p1);
+        const unsigned ep = sh->epoch + 1u;
+        unsigned long long* base = a.msg + (size_t)(ep & 1u) * G * 4;
+        if (threadIdx.x == 0) {
+            if (DATA) __threadfence();
+#pragma unroll
+            for (int k = 0; k < NW; k++)
+                st_relaxed_u64(base + (size_t)blockIdx.x * 4 + k, ((unsigned long long)ep << 32) | pay[k]);
         }
-        m0 = warp_max(m0);
-        m1 = warp_max(m1);
-        if (threadIdx.x == 0) { sh->bcast[0] = m0; sh->bcast[1] = m1; sh->slot = slot ^ 1; }
+        const unsigned lane = threadIdx.x;
+        const long long t0 = clock64();
+        int ok = 1;
+        for (unsigned spins = 1;; spins++) {
+            bool all = true;
+            acc.reset();
+#pragma unroll
+            for (int u = 0; u < SPL; u++) {
+                const unsigned i = lane + 32u * u;
+                if (i < G) {
+                    uint32_t wv[NW];
+#pragma unroll
+                    for (int k = 0; k < NW; k++) {
+                        unsigned long long w = ld_relaxed_u64(base + (size_t)i * 4 + k);
+                        all = all && (unsigned)(w >> 32) == ep;
+                        wv[k] = (uint32_t)w;
+                    }
+                    acc.add(wv);
+                }
+            }
+            if (__all_sync(0xffffffffu, all)) break;
+            if ((spins & 31u) == 0u) {
+                int bad = 0;
+                if (lane == 0) {
+                    if (ld_relaxed_i32(a.err) != 0) bad = 1;
+                    else if (clock64() - t0 > a.limit) { atomicCAS(a.err, 0, SPAI_ERR_TIMEOUT); bad = 1; }
+                }
+                if (__shfl_sync(0xffffffffu, bad, 0)) { ok = 0; break; }
+            }
+        }
+        if (DATA) __threadfence();
+        if (ok) acc.finish(lane, sh);
+        __syncwarp();
+        if (lane == 0) { sh->ok = ok; sh->epoch = ep; }
     }
     __syncthreads();
+    return sh->ok != 0;
+}
+
+template <class T> struct SumAcc {
+    T v;
+    __device__ void reset() { v = T(0); }
+    __device__ void add(const uint32_t* w)
+    {
+        if (sizeof(T) == 8) v += (T)__longlong_as_double((long long)(((unsigned long long)w[0] << 32) | w[1]));
+        else v += (T)__uint_as_float(w[0]);
+    }
+    __device__ void finish(unsigned lane, IrShared* sh)
+    {
+        T t = warp_sum(v);
+        if (lane == 0) sh->bcast[0] = (double)t;
+    }
+};
+
+struct Max2Acc {
+    double m0, m1;
+    __device__ void reset() { m0 = 0.0; m1 = 0.0; }
+    __device__ void add(const uint32_t* w)
+    {
+        m0 = fmax(m0, __longlong_as_double((long long)(((unsigned long long)w[0] << 32) | w[1])));
+        m1 = fmax(m1, __longlong_as_double((long long)(((unsigned long long)w[2] << 32) | w[3])));
+    }
+    __device__ void finish(unsigned lane, IrShared* sh)
+    {
+        double t0 = warp_max(m0), t1 = warp_max(m1);
+        if (lane == 0) { sh->bcast[0] = t0; sh->bcast[1] = t1; }
+    }
+};
+
+struct NoAcc {
+    __device__ void reset() {}
+    __device__ void add(const uint32_t*) {}
+    __device__ void finish(unsigned, IrShared*) {}
+};
+
+// Sum over all blocks of a per-thread value, in a fixed order; the result
+// is identical in every block.  DATA: the round also publishes the global
+// writes made before it (release/acquire); without it only the scalar
+// travels, in the same single-copy-atomic word as its epoch.
+template <bool DATA, class T>
+__device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    constexpr int NW = sizeof(T) == 8 ? 2 : 1;
+    uint32_t pay[2] = {0u, 0u};
+    if (wid == 0) {
+        T t = lane < nw ? red[lane] : T(0);
+        t = warp_sum(t);
+        if (sizeof(T) == 8) {
+            unsigned long long u = (unsigned long long)__double_as_longlong((double)t);
+            pay[0] = (uint32_t)(u >> 32);
+            pay[1] = (uint32_t)u;
+        } else {
+            pay[0] = __float_as_uint((float)t);
+        }
+    }
+    SumAcc<T> acc;
+    bool good = exchange<NW, DATA>(a, sh, pay, acc);
+    out = (T)sh->bcast[0];
+    return good;
+}
+
+// Max of two non-negative doubles over all blocks.
+__device__ bool xmax2(const IrArgs& a, IrShared* sh, double* red, double v0, double v1, double& o0, double& o1)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v0 = warp_max(v0);
+    v1 = warp_max(v1);
+    if (lane == 0) { red[wid] = v0; red[32 + wid] = v1; }
+    __syncthreads();
+    uint32_t pay[4] = {0u, 0u, 0u, 0u};
+    if (wid == 0) {
+        double t0 = warp_max(lane < nw ? red[lane] : 0.0);
+        double t1 = warp_max(lane < nw ? red[32 + lane] : 0.0);
+        unsigned long long u0 = (unsigned long long)__double_as_longlong(t0);
+        unsigned long long u1 = (unsigned long long)__double_as_longlong(t1);
+        pay[0] = (uint32_t)(u0 >> 32); pay[1] = (uint32_t)u0;
+        pay[2] = (uint32_t)(u1 >> 32); pay[3] = (uint32_t)u1;
+    }
+    Max2Acc acc;
+    bool good = exchange<4, true>(a, sh, pay, acc);
     o0 = sh->bcast[0];
     o1 = sh->bcast[1];
-    return true;
+    return good;
 }
 
-template <class T> __device__ __forceinline__ T to_t(double v) { return (T)v; }
-
-// y[row] = sum_q M[row, q] * f(src[col]) with L lanes per row, for the
-// block's rows; result handed to `store(row, value)`.
-template <class TP, class Load, class Store>
-__device__ __forceinline__ void spmv_rows(int64_t r0, int64_t r1, int L, const int64_t* __restrict__ rp,
-                                          const int32_t* __restrict__ ci, const TP* __restrict__ mv, Load load,
-                                          Store store)
+// plain barrier (no payload)
+__device__ bool xbar(const IrArgs& a, IrShared* sh)
 {
-    const int per = blockDim.x / L;
-    const int g = threadIdx.x / L, l = threadIdx.x % L;
-    for (int64_t base = r0; base < r1; base += per) {
-        int64_t row = base + g;
-        TP acc = TP(0);
-        if (row < r1) {
-            for (int64_t q = rp[row] + l; q < rp[row + 1]; q += L) acc = fma(mv[q], (TP)load(ci[q]), acc);
+    __syncthreads();
+    uint32_t pay[1] = {0u};
+    NoAcc acc;
+    return exchange<1, true>(a, sh, pay, acc);
+}
+
+// y = M x for the block's rows (SELL-32), two rows per thread per pass with
+// their loads interleaved; `store(row, value)` receives each result.  The
+// slice offsets of the block live in shared memory (soff[0..nsl]).
+template <class TP, class Load, class Store>
+__device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t* soff, const int32_t* __restrict__ col,
+                                          const TP* __restrict__ val, Load load, Store store)
+{
+    const int tid = threadIdx.x, BT = blockDim.x, lane = tid & 31;
+    constexpr int U = 4;
+    for (int64_t base = r0; base < r1; base += 2 * BT) {
+        const int64_t ra = base + tid, rb = base + BT + tid;
+        const bool va = ra < r1, vb = rb < r1;
+        const int sa = (int)((ra - r0) >> 5), sb = (int)((rb - r0) >> 5);
+        const int64_t oa = va ? soff[sa] + lane : 0, ob = vb ? soff[sb] + lane : 0;
+        const int wa = va ? (int)((soff[sa + 1] - soff[sa]) >> 5) : 0;
+        const int wb = vb ? (int)((soff[sb + 1] - soff[sb]) >> 5) : 0;
+        TP acc_a = TP(0), acc_b = TP(0);
+        const int wmax = wa > wb ? wa : wb;
+        // software pipeline: the entries of chunk c+1 load while chunk c gathers
+        int ca[U], cb[U];
+        TP xa[U], xb[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            ca[u] = u < wa ? __ldg(col + oa + 32 * u) : -1;
+            xa[u] = u < wa ? __ldg(val + oa + 32 * u) : TP(0);
+            cb[u] = u < wb ? __ldg(col + ob + 32 * u) : -1;
+            xb[u] = u < wb ? __ldg(val + ob + 32 * u) : TP(0);
         }
-        for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (row < r1 && l == 0) store(row, acc);
+        for (int c0 = 0; c0 < wmax; c0 += U) {
+            TP ga[U], gb[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                ga[u] = ca[u] >= 0 ? (TP)load(ca[u]) : TP(0);
+                gb[u] = cb[u] >= 0 ? (TP)load(cb[u]) : TP(0);
+            }
+            TP ya[U], yb[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) { ya[u] = xa[u]; yb[u] = xb[u]; }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int c = c0 + U + u;
+                ca[u] = c < wa ? __ldg(col + oa + 32 * c) : -1;
+                xa[u] = c < wa ? __ldg(val + oa + 32 * c) : TP(0);
+                cb[u] = c < wb ? __ldg(col + ob + 32 * c) : -1;
+                xb[u] = c < wb ? __ldg(val + ob + 32 * c) : TP(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                acc_a = fma(ya[u], ga[u], acc_a);
+                acc_b = fma(yb[u], gb[u], acc_b);
+            }
+        }
+        if (va) store(ra, acc_a);
+        if (vb) store(rb, acc_b);
     }
 }
 
@@ -166,30 +317,40 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ IrShared shs;
     __shared__ TG redg[33];
-    __shared__ double redd[33];
+    __shared__ double redd[64];
     IrShared* sh = &shs;
     const int kmax = a.kmax;
-    double* cs = (double*)smem;           // kmax + 2
+    const int tid = threadIdx.x, BT = blockDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * a.rb;
+    const int64_t r1 = min(a.n, r0 + a.rb);
+    const int nsl = (int)((a.rb + 31) >> 5);
+    double* cs = (double*)smem;            // kmax + 2
     double* sn = cs + (kmax + 2);          // kmax + 2
     double* g = sn + (kmax + 2);           // kmax + 2
     double* hc = g + (kmax + 2);           // kmax + 2
     double* yv = hc + (kmax + 2);          // kmax + 2
-    TG* ws = (TG*)(yv + (kmax + 2));       // rb
-    const int tid = threadIdx.x, BT = blockDim.x;
-    const int64_t r0 = (int64_t)blockIdx.x * a.rb;
-    const int64_t r1 = min(a.n, r0 + a.rb);
+    int64_t* soa = (int64_t*)(yv + (kmax + 2));  // nsl + 1 slice offsets of A
+    int64_t* sop = soa + (nsl + 1);        // nsl + 1 slice offsets of P
+    TG* ws = (TG*)(sop + (nsl + 1));       // rb: w for the block's rows
     TU* x = (TU*)a.x;
     TU* r = (TU*)a.r;
     TG* wbuf = (TG*)a.wbuf;
     TP* tbuf = (TP*)a.tbuf;
     TG* V = (TG*)a.V;
-    const TP* av = (const TP*)a.aval_p;
-    const TP* pv = (const TP*)a.pval_p;
-    if (tid == 0) { sh->epoch = 0; sh->slot = 0; sh->flag = 1; }
+    const TP* av = (const TP*)a.A.val;
+    const TP* pv = (const TP*)a.P.val;
+    const bool hasP = a.P.off != nullptr;
+    const int64_t s0 = r0 >> 5;
+    const int64_t nslg = (a.n + 31) >> 5;
+    for (int i = tid; i <= nsl; i += BT) {
+        int64_t sg = min(s0 + i, nslg);
+        soa[i] = a.A.off[sg];
+        sop[i] = hasP ? a.P.off[sg] : 0;
+    }
+    if (tid == 0) { sh->epoch = 0; sh->ok = 1; }
     __syncthreads();
 
     int steps = 0, flags = 0;
-    // x (written by k_x0 before this launch) is visible to every block.
     for (int it = 0; it <= a.imax; it++) {
         // ---------------- residual r = b - A x in u_r, stored in u
         double rmax = 0.0, xmax = 0.0;
@@ -205,10 +366,8 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
             rmax = fmax(rmax, fabs((double)rv));
             xmax = fmax(xmax, fabs((double)x[row]));
         }
-        rmax = block_max(rmax, redd);
-        xmax = block_max(xmax, redd);
         double rn, xn;
-        if (!gmax2(a, sh, rmax, xmax, rn, xn)) return;
+        if (!xmax2(a, sh, redd, rmax, xmax, rn, xn)) return;
         const double den = a.anorm * xn + a.bnorm;
         const double nb = den > 0.0 ? rn / den : 0.0;
         if (blockIdx.x == 0 && tid == 0) a.nbe[it] = nb;
@@ -218,76 +377,113 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
 
         // ---------------- z = P r in u_p, stored in u_g; beta = ||z||
         TG part = TG(0);
-        if (a.prp) {
-            spmv_rows<TP>(r0, r1, a.lp, a.prp, a.pci, pv, [&](int c) { return (TP)ldcg(&r[c]); },
-                          [&](int64_t row, TP v) { TG z = (TG)v; ws[row - r0] = z; wbuf[row] = z; });
+        if (hasP) {
+            sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&r[c]); },
+                          [&](int64_t row, TP v) { TG z = (TG)v; ws[row - r0] = z; wbuf[row] = z; part = fma(z, z, part); });
         } else {
             for (int64_t row = r0 + tid; row < r1; row += BT) {
                 TG z = (TG)(TP)r[row];
                 ws[row - r0] = z;
                 wbuf[row] = z;
+                part = fma(z, z, part);
             }
         }
-        __syncthreads();
-        for (int64_t row = r0 + tid; row < r1; row += BT) { TG z = ws[row - r0]; part = fma(z, z, part); }
-        part = block_sum(part, redg);
         TG bsq;
-        if (!gsum(a, sh, part, bsq)) return;
+        if (!xsum<true>(a, sh, redg, part, bsq)) return;
         const TG beta = sqrt(bsq);
         int k = 0;
         if (beta > TG(0)) {
             for (int64_t row = r0 + tid; row < r1; row += BT) V[row] = ws[row - r0] / beta;
-            if (tid == 0) { g[0] = (double)beta; }
+            if (tid == 0) g[0] = (double)beta;
             TG hdiv = beta;
             bool done = false;
             for (int j = 0; j < kmax && !done; j++) {
                 // ---- t = A v_j in u_p; v_j formed from the published w: fl(w / h)
-                spmv_rows<TP>(r0, r1, a.la, a.arp, a.aci, av, [&](int c) { return (TP)(ldcg(&wbuf[c]) / hdiv); },
+                sell_rows<TP>(r0, r1, soa, a.A.col, av, [&](int c) { return (TP)(ldcg(&wbuf[c]) / hdiv); },
                               [&](int64_t row, TP v) { tbuf[row] = v; });
-                if (!grid_sync(a.gb, &sh->epoch, &sh->flag)) return;
-                // ---- w = P t in u_p, stored in u_g (own rows, shared memory)
-                if (a.prp) {
-                    spmv_rows<TP>(r0, r1, a.lp, a.prp, a.pci, pv, [&](int c) { return ldcg(&tbuf[c]); },
+                // prefetch v_0 for the first Gram-Schmidt dot while the barrier runs
+                TG vc[PF];
+#pragma unroll
+                for (int u = 0; u < PF; u++) {
+                    int64_t row = r0 + tid + (int64_t)u * BT;
+                    vc[u] = row < r1 ? V[row] : TG(0);
+                }
+                if (!xbar(a, sh)) return;
+                // ---- w = P t in u_p, stored in u_g (own rows, shared memory); first MGS partial
+                part = TG(0);
+                if (hasP) {
+                    sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return ldcg(&tbuf[c]); },
                                   [&](int64_t row, TP v) { ws[row - r0] = (TG)v; });
                 } else {
                     for (int64_t row = r0 + tid; row < r1; row += BT) ws[row - r0] = (TG)ldcg(&tbuf[row]);
                 }
-                __syncthreads();
+                // sell_rows and the copy give thread tid the rows r0 + tid + u*BT, so
+                // the partial needs no __syncthreads
+#pragma unroll
+                for (int u = 0; u < PF; u++) {
+                    int64_t row = r0 + tid + (int64_t)u * BT;
+                    if (row < r1) part = fma(vc[u], ws[row - r0], part);
+                }
+                for (int64_t row = r0 + tid + (int64_t)PF * BT; row < r1; row += BT) part = fma(V[row], ws[row - r0], part);
                 // ---- modified Gram-Schmidt in u_g
-                const TG* Vj = V + r0;  // column 0, own rows start
-                part = TG(0);
-                for (int64_t row = r0 + tid; row < r1; row += BT) part = fma(Vj[row - r0], ws[row - r0], part);
                 for (int i = 0; i <= j; i++) {
-                    part = block_sum(part, redg);
+                    // prefetch v_{i+1} (own rows) before waiting for h_{i,j}
+                    const TG* Vn = V + (int64_t)(i + 1) * a.ldv;
+                    TG vn[PF];
+                    if (i < j) {
+#pragma unroll
+                        for (int u = 0; u < PF; u++) {
+                            int64_t row = r0 + tid + (int64_t)u * BT;
+                            vn[u] = row < r1 ? Vn[row] : TG(0);
+                        }
+                    }
                     TG h;
-                    if (!gsum(a, sh, part, h)) return;
+                    if (!xsum<false>(a, sh, redg, part, h)) return;
                     if (tid == 0) hc[i] = (double)h;
-                    const TG* Vi = V + (int64_t)i * a.ldv + r0;
-                    const TG* Vn = V + (int64_t)(i + 1) * a.ldv + r0;
+                    const TG* Vi = V + (int64_t)i * a.ldv;
                     part = TG(0);
                     if (i < j) {
-                        for (int64_t row = r0 + tid; row < r1; row += BT) {
-                            TG wv = fma(-h, Vi[row - r0], ws[row - r0]);
+#pragma unroll
+                        for (int u = 0; u < PF; u++) {
+                            int64_t row = r0 + tid + (int64_t)u * BT;
+                            if (row < r1) {
+                                TG wv = fma(-h, vc[u], ws[row - r0]);
+                                ws[row - r0] = wv;
+                                part = fma(vn[u], wv, part);
+                            }
+                            vc[u] = vn[u];
+                        }
+                        for (int64_t row = r0 + tid + (int64_t)PF * BT; row < r1; row += BT) {
+                            TG wv = fma(-h, Vi[row], ws[row - r0]);
                             ws[row - r0] = wv;
-                            part = fma(Vn[row - r0], wv, part);
+                            part = fma(Vn[row], wv, part);
                         }
                     } else {
-                        for (int64_t row = r0 + tid; row < r1; row += BT) {
-                            TG wv = fma(-h, Vi[row - r0], ws[row - r0]);
+#pragma unroll
+                        for (int u = 0; u < PF; u++) {
+                            int64_t row = r0 + tid + (int64_t)u * BT;
+                            if (row < r1) {
+                                TG wv = fma(-h, vc[u], ws[row - r0]);
+                                ws[row - r0] = wv;
+                                wbuf[row] = wv;
+                                part = fma(wv, wv, part);
+                            }
+                        }
+                        for (int64_t row = r0 + tid + (int64_t)PF * BT; row < r1; row += BT) {
+                            TG wv = fma(-h, Vi[row], ws[row - r0]);
                             ws[row - r0] = wv;
                             wbuf[row] = wv;
                             part = fma(wv, wv, part);
                         }
                     }
                 }
-                part = block_sum(part, redg);
                 TG hsq;
-                if (!gsum(a, sh, part, hsq)) return;
+                if (!xsum<true>(a, sh, redg, part, hsq)) return;
                 const TG hn = sqrt(hsq);
                 // ---- v_{j+1} = w / h_{j+1,j} (own rows)
                 if (hn > TG(0)) {
-                    TG* Vn = V + (int64_t)(j + 1) * a.ldv + r0;
-                    for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row - r0] = ws[row - r0] / hn;
+                    TG* Vn = V + (int64_t)(j + 1) * a.ldv;
+                    for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ws[row - r0] / hn;
                 }
                 // ---- Givens rotations in double (identical in every block)
                 if (tid == 0) {
@@ -314,7 +510,7 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
                 else if (sh->resid <= a.tau) done = true;
             }
             // ---- y = R^{-1} g (double), d = V y in u_g, x = x + d in u
-            if (!grid_sync(a.gb, &sh->epoch, &sh->flag)) return;  // R columns from block 0
+            if (!xbar(a, sh)) return;  // R columns from block 0
             if (tid < 32) {
                 for (int t = tid; t < k; t += 32) yv[t] = g[t];
                 __syncwarp();
@@ -339,11 +535,49 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
         if (blockIdx.x == 0 && tid == 0) a.its[it] = k;
         steps = it + 1;
         // x must be complete before the next residual
-        if (!grid_sync(a.gb, &sh->epoch, &sh->flag)) return;
+        if (!xbar(a, sh)) return;
     }
     if (blockIdx.x == 0 && tid == 0) {
         a.out[0] = steps;
         a.out[1] = flags;
+    }
+}
+
+// ---------------------------------------------------------------- SELL-32 conversion
+
+// width of each 32-row slice (longest row), times 32
+__global__ void k_sell_width(int64_t n, const int64_t* __restrict__ rp, int32_t* __restrict__ w32)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nsl = (n + 31) >> 5;
+    for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; s < nsl;
+         s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int64_t row = s * 32 + lane;
+        int len = row < n ? (int)(rp[row + 1] - rp[row]) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+        if (lane == 0) w32[s] = len * 32;
+    }
+}
+
+template <class TP>
+__global__ void k_sell_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ val, const int64_t* __restrict__ off, int32_t* __restrict__ scol,
+                            TP* __restrict__ sval)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nsl = (n + 31) >> 5;
+    for (int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; s < nsl;
+         s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t row = s * 32 + lane;
+        const int w = (int)((off[s + 1] - off[s]) >> 5);
+        const int64_t b = row < n ? rp[row] : 0;
+        const int len = row < n ? (int)(rp[row + 1] - b) : 0;
+        for (int c = 0; c < w; c++) {
+            int64_t o = off[s] + 32 * c + lane;
+            if (c < len) { scol[o] = ci[b + c]; sval[o] = (TP)val[b + c]; }
+            else { scol[o] = row < n ? (int32_t)row : 0; sval[o] = TP(0); }
+        }
     }
 }
 
@@ -372,11 +606,6 @@ __global__ void k_to_double(int64_t n, const TU* __restrict__ x, double* __restr
         out[i] = (double)x[i];
 }
 
-__global__ void k_to_float(int64_t n, const double* __restrict__ x, float* __restrict__ out)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __double2float_rn(x[i]);
-}
 
 // ||A||_inf, ||b||_inf, and the largest row count q
 __global__ void k_norms(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ val,
@@ -403,38 +632,20 @@ __global__ void k_norms(int64_t n, const int64_t* __restrict__ rp, const double*
     }
 }
 
-int lanes_for(double avg)
-{
-    int L = 1;
-    while (L < 32 && L < avg) L <<= 1;
-    return L;
-}
-
 template <class TU, class TG, class TP, int RM>
-int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, size_t fixed_smem_per_row, int* grid_out)
+int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, int* grid_out)
 {
     auto kern = k_ir<TU, TG, TP, RM>;
-    int occ = 0;
-    // choose the grid: at most the co-resident capacity, rows per block >= 256
-    int64_t G = (a.n + 255) / 256;
-    int maxg = 0;
-    for (int attempt = 0; attempt < 2; attempt++) {
-        int64_t g0 = G;
-        size_t smem = 0;
-        int64_t rb = (a.n + g0 - 1) / g0;
-        smem = sizeof(double) * 5 * (a.kmax + 2) + rb * fixed_smem_per_row + 64;
-        SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, IR_THREADS, smem));
-        maxg = occ * num_sms;
-        if (maxg < 1) return SPAI_ERR_UNSUPPORTED;
-        if (G > maxg) G = maxg; else break;
-    }
+    // one block per SM (1024 threads), at least 256 rows per block, rows per
+    // block a multiple of 32 so that blocks own whole SELL slices
+    int64_t G = std::min<int64_t>((a.n + 255) / 256, std::min(num_sms, MAX_GRID));
     if (G < 1) G = 1;
-    a.rb = (a.n + G - 1) / G;
+    a.rb = ((a.n + G - 1) / G + 31) & ~int64_t(31);
     G = (a.n + a.rb - 1) / a.rb;
-    if (G < 1) G = 1;
-    size_t smem = sizeof(double) * 5 * (a.kmax + 2) + a.rb * fixed_smem_per_row + 64;
+    const int64_t nsl = (a.rb + 31) >> 5;
+    const size_t smem = sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + a.rb * sizeof(TG) + 64;
     SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
     SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, IR_THREADS, smem));
     if ((int64_t)occ * num_sms < G) return SPAI_ERR_UNSUPPORTED;
     void* args[] = {(void*)&a};
@@ -446,19 +657,58 @@ int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, size_t fixed_smem_per_row,
 template <class TU, class TG, class TP>
 int launch_ir_rm(IrArgs& a, int rm, int num_sms, cudaStream_t s, int* grid)
 {
-    size_t per_row = sizeof(TG);
-    if (rm == 2) return launch_ir<TU, TG, TP, 2>(a, num_sms, s, per_row, grid);
-    return launch_ir<TU, TG, TP, 1>(a, num_sms, s, per_row, grid);
+    if (rm == 2) return launch_ir<TU, TG, TP, 2>(a, num_sms, s, grid);
+    return launch_ir<TU, TG, TP, 1>(a, num_sms, s, grid);
 }
 
 int prec_bytes(int p) { return p == SPAI_HALF ? 2 : (p == SPAI_SINGLE ? 4 : 8); }
 
 }  // namespace
 
+// SELL-32 copy of a CSR matrix with values rounded to `prec` (single or double).
+int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int prec, int num_sms,
+               cudaStream_t s, SellMat* out, int* launches)
+{
+    const int64_t nsl = (n + 31) >> 5;
+    int32_t* w32 = nullptr;
+    int rc = dev_alloc((void**)&w32, sizeof(int32_t) * nsl, s);
+    if (rc) return rc;
+    rc = dev_alloc((void**)&out->off, sizeof(int64_t) * (nsl + 1), s);
+    if (rc) { dev_free(w32, s); return rc; }
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((nsl * 32 + tb - 1) / tb, (int64_t)num_sms * 16));
+    k_sell_width<<<gb, tb, 0, s>>>(n, rp, w32);
+    rc = scan_counts(nsl, w32, out->off, s);
+    *launches += 4;
+    int64_t total = 0;
+    if (!rc && cudaMemcpyAsync(&total, out->off + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    dev_free(w32, s);
+    if (rc) return rc;
+    out->prec = prec;
+    out->nnz = total;
+    if ((rc = dev_alloc((void**)&out->col, sizeof(int32_t) * std::max<int64_t>(total, 1), s))) return rc;
+    if ((rc = dev_alloc(&out->val, (size_t)prec_bytes(prec) * std::max<int64_t>(total, 1), s))) return rc;
+    if (prec == SPAI_SINGLE) k_sell_fill<float><<<gb, tb, 0, s>>>(n, rp, ci, val, out->off, out->col, (float*)out->val);
+    else k_sell_fill<double><<<gb, tb, 0, s>>>(n, rp, ci, val, out->off, out->col, (double*)out->val);
+    *launches += 1;
+    SPAI_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+void sell_free(SellMat* m, cudaStream_t s)
+{
+    dev_free(m->off, s);
+    dev_free(m->col, s);
+    dev_free(m->val, s);
+    m->off = nullptr;
+    m->col = nullptr;
+    m->val = nullptr;
+}
+
 int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
                  const double* b, double* xout, const ir_opts* o, ir_stats* st)
 {
-    (void)device;
     const int64_t n = A.n;
     if (!o) return SPAI_ERR_INVALID_ARG;
     if (o->u != SPAI_SINGLE && o->u != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
@@ -483,15 +733,16 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     SPAI_CUDA_TRY(cudaEventCreate(&ek1));
     int nl = 0;  // kernels launched
     const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
-    void *x = nullptr, *r = nullptr, *wbuf = nullptr, *tbuf = nullptr, *V = nullptr, *aval_p = nullptr;
-    double *R = nullptr, *part = nullptr, *nbe = nullptr;
+    void *x = nullptr, *r = nullptr, *wbuf = nullptr, *tbuf = nullptr, *V = nullptr;
+    double *R = nullptr, *nbe = nullptr;
     int *its = nullptr, *outv = nullptr, *err = nullptr;
-    unsigned* bar = nullptr;
+    unsigned long long* msg = nullptr;
     unsigned long long* norms = nullptr;
     unsigned long long h_norms[3] = {0, 0, 0};
     int h_out[2] = {0, 0}, h_err = 0;
     int grid = 0;
-    const void* pval_p = nullptr;
+    SellMat As;
+    const SellMat* Ps = nullptr;
     int64_t ldv = (n + 31) & ~int64_t(31);
     const int tb = 256;
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
@@ -506,37 +757,24 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     TRY(dev_alloc(&tbuf, (size_t)sp * n, s));
     TRY(dev_alloc(&V, (size_t)sg * ldv * (kmax + 1), s));
     TRY(dev_alloc((void**)&R, sizeof(double) * (size_t)(kmax + 1) * kmax, s));
-    TRY(dev_alloc((void**)&part, sizeof(double) * 2 * 2 * 4096, s));
+    TRY(dev_alloc((void**)&msg, sizeof(unsigned long long) * 2 * MAX_GRID * 4, s));
     TRY(dev_alloc((void**)&nbe, sizeof(double) * (imax + 1), s));
     TRY(dev_alloc((void**)&its, sizeof(int) * (imax + 1), s));
     TRY(dev_alloc((void**)&outv, sizeof(int) * 2, s));
     TRY(dev_alloc((void**)&err, sizeof(int) * 2, s));
-    TRY(dev_alloc((void**)&bar, sizeof(unsigned) * 2, s));
     TRY(dev_alloc((void**)&norms, sizeof(unsigned long long) * 3, s));
     CTRY(cudaMemsetAsync(norms, 0, sizeof(unsigned long long) * 3, s));
     CTRY(cudaMemsetAsync(its, 0, sizeof(int) * (imax + 1), s));
     CTRY(cudaMemsetAsync(outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, s));
+    CTRY(cudaMemsetAsync(msg, 0, sizeof(unsigned long long) * 2 * MAX_GRID * 4, s));
     CTRY(cudaEventRecord(e0, s));
-    // A in u_p
-    if (o->up == SPAI_SINGLE) {
-        TRY(dev_alloc(&aval_p, sizeof(float) * (A.nnz > 0 ? A.nnz : 1), s));
-        k_to_float<<<gb, tb, 0, s>>>(A.nnz, A.val, (float*)aval_p);
-        nl++;
-    }
-    // P in u_p
+    // A and P in u_p, SELL-32 (P's copy is cached on the preconditioner)
+    TRY(sell_build(n, A.rowptr, A.col, A.val, o->up, num_sms, s, &As, &nl));
     if (P) {
-        if (o->up == SPAI_SINGLE) {
-            if (!P->val_f32) {
-                TRY(dev_alloc((void**)&P->val_f32, sizeof(float) * (P->nnz > 0 ? P->nnz : 1), s));
-                k_to_float<<<gb, tb, 0, s>>>(P->nnz, P->val, P->val_f32);
-                nl++;
-            }
-            pval_p = P->val_f32;
-        } else {
-            pval_p = P->val;
-        }
+        SellMat* cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
+        if (!cache->off) TRY(sell_build(n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, &nl));
+        Ps = cache;
     }
     k_norms<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, b, norms);
     nl++;
@@ -569,22 +807,18 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         const int q = (int)h_norms[2];
         const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
         a.n = n;
+        a.A.off = As.off; a.A.col = As.col; a.A.val = As.val;
+        if (Ps) { a.P.off = Ps->off; a.P.col = Ps->col; a.P.val = Ps->val; }
         a.arp = A.rowptr; a.aci = A.col; a.aval = A.val;
-        a.aval_p = o->up == SPAI_SINGLE ? aval_p : (const void*)A.val;
-        a.prp = P ? P->rowptr : nullptr;
-        a.pci = P ? P->col : nullptr;
-        a.pval_p = pval_p;
-        a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.part = part;
-        a.gb.count = bar; a.gb.err = err;
+        a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
+        a.err = err;
         int clk_khz = 0;
         cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, device);
         if (clk_khz <= 0) clk_khz = 2000000;
-        a.gb.limit = (long long)clk_khz * 1000LL * 4;  // about four seconds per wait
+        a.limit = (long long)clk_khz * 1000LL * 4;  // about four seconds per wait
         a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
         a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
         a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
-        a.la = lanes_for(n > 0 ? (double)A.nnz / n : 1.0);
-        a.lp = P ? lanes_for(n > 0 ? (double)P->nnz / n : 1.0) : 1;
         a.its = its; a.nbe = nbe; a.out = outv;
         const int rm = o->ur == SPAI_QUAD ? 2 : 1;
         CTRY(cudaEventRecord(ek0, s));
@@ -644,9 +878,11 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
 done:
 #undef TRY
 #undef CTRY
-    dev_free(x, s); dev_free(r, s); dev_free(wbuf, s); dev_free(tbuf, s); dev_free(V, s); dev_free(aval_p, s);
-    dev_free(R, s); dev_free(part, s); dev_free(nbe, s); dev_free(its, s); dev_free(outv, s); dev_free(err, s);
-    dev_free(bar, s); dev_free(norms, s);
+    (void)sp;
+    sell_free(&As, s);
+    dev_free(x, s); dev_free(r, s); dev_free(wbuf, s); dev_free(tbuf, s); dev_free(V, s);
+    dev_free(R, s); dev_free(msg, s); dev_free(nbe, s); dev_free(its, s); dev_free(outv, s); dev_free(err, s);
+    dev_free(norms, s);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ek0) cudaEventDestroy(ek0);

@@ -24,13 +24,22 @@ struct DevCsr {
     bool owned = false;
 };
 
+// A matrix in SELL-32 layout (see gmres_ir.cu) with values in one precision.
+struct SellMat {
+    int64_t* off = nullptr;   // slice offsets, (n + 31) / 32 + 1
+    int32_t* col = nullptr;
+    void* val = nullptr;
+    int64_t nnz = 0;          // stored entries, padding included
+    int prec = SPAI_DOUBLE;
+};
+
 struct spai_precond_s {
     int device = 0;
     int64_t n = 0, nnz = 0;
     int64_t* rowptr = nullptr;   // n + 1
     int32_t* col = nullptr;      // nnz
     double* val = nullptr;       // nnz, unrounded mbar_k * d(J_k)
-    float* val_f32 = nullptr;    // lazily made copy rounded to single (u_p = single)
+    SellMat sell_f32, sell_f64;  // lazily made SELL-32 copies in u_p = single / double
     void* val_uf = nullptr;      // copy rounded to u_f (used by x0 = P b)
     int uf = SPAI_DOUBLE;
     cudaStream_t stream = nullptr;
@@ -71,6 +80,11 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
                    spai_precond* P_out, spai_stats* st);
 int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
                  const double* b_dev, double* x_dev, const ir_opts* o, ir_stats* st);
+
+int scan_counts(int64_t n, const int32_t* in, int64_t* out, cudaStream_t s);
+int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int prec, int num_sms,
+               cudaStream_t s, SellMat* out, int* launches);
+void sell_free(SellMat* m, cudaStream_t s);
 
 // bytes the solve of an n x n system with nnz nonzeros may hold on the device
 size_t estimate_footprint(int64_t n, int64_t nnz, const spai_opts* so, const ir_opts* io);

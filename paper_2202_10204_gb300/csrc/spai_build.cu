@@ -7,12 +7,10 @@
 //   k_col_count / k_col_fill / k_col_sort
 //                  structure of A^T (column lists of A) for pattern(A), pattern(A^2)
 //                  and the candidate sets N_l of the adaptive step
-//   k_pattern      initial J_k (identity, pattern(A), pattern(A^2)) with the fill cap
-//   k_shadow_count |I_k| for sizing the per-column tiles
-//   k_spai         one warp per column: gather B(I_k, J_k) (sorted warp merge of the
-//                  rows j in J_k), Householder QR, back substitution, explicit
-//                  residual s = B(I,J) m - e_k and ||s||, and (adaptive) the rho_jk
-//                  scores, mean acceptance and up-to-beta augmentation, looping
+//   k_pattern      initial J_k (identity, pattern(A), pattern(A^2)) with the fill cap,
+//                  and |I_k| for sizing the per-column tiles
+//   k_spai         (spai_column.cuh) one warp per column: gather, Householder QR,
+//                  back substitution, explicit residual, adaptive augmentation
 //   k_assemble     P row k = m_k * d(J_k) in CSR (column k of M is row k of P)
 #include <climits>
 #include <cstdio>
@@ -20,14 +18,14 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "spai_column.cuh"
 
 using namespace spai;
 
 namespace {
 
-constexpr int LD = 33;          // row stride of the per-column tile (32 columns + pad)
-constexpr int MAX_FILL = 31;    // |J_k| <= 31 so that [B(I,J) | e] fits 32 lanes
-constexpr int MMAX_LIMIT = 512; // largest |I_k| handled by the warp kernel
+constexpr int MAX_FILL = SPAI_MAX_FILL;
+constexpr int MMAX_LIMIT = SPAI_MMAX_LIMIT;
 
 // ---------------------------------------------------------------- scaling
 
@@ -142,6 +140,8 @@ __global__ void k_scan_chunks(int64_t n, const int32_t* __restrict__ in, const i
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[gridDim.x];
 }
 
+}  // namespace
+
 int scan_counts(int64_t n, const int32_t* in, int64_t* out, cudaStream_t s)
 {
     const int64_t chunk = 1 << 16;
@@ -158,63 +158,97 @@ int scan_counts(int64_t n, const int32_t* in, int64_t* out, cudaStream_t s)
     return 0;
 }
 
-// ---------------------------------------------------------------- warp merge
-// Sorted union of up to 32 sorted index lists, one per lane.  Each lane
-// holds the head of its list; the warp repeatedly takes the minimum head
-// (one REDUX), and every lane whose head equals it advances.  `emit(p, idx,
-// has)` runs on all lanes for output position p.
+namespace {
 
-struct ListCursor {
-    int64_t q, e;
-    int head;
-};
-
-__device__ __forceinline__ void cursor_load(ListCursor& c, const int32_t* __restrict__ idx,
-                                            const double* __restrict__ val)
+// ---------------------------------------------------------------- sorted unions
+// Sorted union of up to 32 sorted index lists held in shared memory, one per
+// lane (lane l: lst[l*stride .. l*stride + len)), plus the single index
+// `extra` carried by lane `extra_lane` (-1: none).  The warp repeatedly
+// takes the minimum head (one REDUX) and every lane holding it advances.
+// Writes the union to out[0..cap) when out != nullptr; returns its size.
+__device__ int warp_union(const int32_t* lst, int stride, int len, int extra_lane, int extra, int32_t* out, int cap)
 {
-    // skip stored zeros when values are given (the shadow counts |a_ij| != 0)
-    if (val) while (c.q < c.e && val[c.q] == 0.0) c.q++;
-    c.head = c.q < c.e ? idx[c.q] : INT_MAX;
+    const int lane = threadIdx.x & 31;
+    const int32_t* l = lst + lane * stride;
+    int q = 0;
+    int head = lane == extra_lane ? extra : (len > 0 ? l[0] : INT_MAX);
+    int cnt = 0;
+    while (true) {
+        const int mn = __reduce_min_sync(0xffffffffu, head);
+        if (mn == INT_MAX) break;
+        if (out && lane == 0 && cnt < cap) out[cnt] = mn;
+        cnt++;
+        if (head == mn) {
+            q++;
+            head = (lane != extra_lane && q < len) ? l[q] : INT_MAX;
+        }
+    }
+    __syncwarp();
+    return cnt;
+}
+
+// Load list `lane` = idx[b..e) (entries with val == 0 skipped when val is
+// given) into lst + lane*stride; returns its length.
+__device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, const double* __restrict__ val, int64_t b,
+                                         int64_t e, int32_t* lst, int stride)
+{
+    const int lane = threadIdx.x & 31;
+    int32_t* l = lst + lane * stride;
+    int len = 0;
+    for (int64_t q = b; q < e; q += 4) {
+        int cc[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            cc[u] = q + u < e ? idx[q + u] : 0;
+            ok[u] = q + u < e && (!val || val[q + u] != 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (ok[u] && len < stride) l[len++] = cc[u];
+    }
+    return len;
 }
 
 // ---------------------------------------------------------------- pattern
 
-// Initial pattern J_k, capped at F keeping k and then the nearest indices
-// (ties to the smaller index).  One warp per column; `buf` is a per-warp
-// shared buffer of `cap` ints for the uncapped union.
-__global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                          int32_t* __restrict__ Jidx, int32_t* __restrict__ Jcnt, int cap, int* __restrict__ err)
+// Initial pattern J_k (identity, pattern(A), pattern(A^2)), capped at F
+// keeping k and then the nearest indices (ties to the smaller index), and
+// the shadow size |I_k| = |union of the nonzero columns of rows j in J_k,
+// plus k|.  One warp per column.  Per-warp shared memory: buf[cap] for the
+// uncapped pattern and 32 lists of `stride` ints.
+__global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const int64_t* __restrict__ cp,
+                          const int32_t* __restrict__ ri, int32_t* __restrict__ Jidx, int32_t* __restrict__ Jcnt,
+                          int32_t* __restrict__ Icnt, int cap, int stride, int* __restrict__ err,
+                          int* __restrict__ maxI)
 {
     extern __shared__ int32_t pbuf[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    int32_t* buf = pbuf + wib * cap;
+    int32_t* buf = pbuf + (size_t)wib * (cap + 32 * stride);
+    int32_t* lst = buf + cap;
     for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < n; k += (int64_t)gridDim.x * wpb) {
         int cnt = 0;
         if (init == SPAI_PAT_IDENTITY) {
             if (lane == 0) buf[0] = (int32_t)k;
             cnt = 1;
         } else if (init == SPAI_PAT_A) {
-            int64_t b = cp[k], e = cp[k + 1];
+            const int64_t b = cp[k], e = cp[k + 1];
             cnt = (int)(e - b);
             if (cnt > cap) { if (lane == 0) atomicCAS(err, 0, SPAI_ERR_UNSUPPORTED); cnt = cap; }
             for (int t = lane; t < cnt; t += 32) buf[t] = ri[b + t];
         } else {
-            // union over i in column k of A of column i of A (column k of A^2)
-            int64_t b = cp[k], e = cp[k + 1];
+            // column k of A^2: union over i in column k of A of column i of A
+            const int64_t b = cp[k];
+            int64_t e = cp[k + 1];
             if (e - b > 32) { if (lane == 0) atomicCAS(err, 0, SPAI_ERR_UNSUPPORTED); e = b + 32; }
-            ListCursor c;
+            int len = 0;
             if (lane < e - b) {
-                int i = ri[b + lane];
-                c.q = cp[i]; c.e = cp[i + 1];
-            } else { c.q = 0; c.e = 0; }
-            cursor_load(c, ri, nullptr);
-            while (true) {
-                int mn = __reduce_min_sync(0xffffffffu, c.head);
-                if (mn == INT_MAX) break;
-                if (lane == 0 && cnt < cap) buf[cnt] = mn;
-                cnt++;
-                if (c.head == mn) { c.q++; cursor_load(c, ri, nullptr); }
+                const int i = ri[b + lane];
+                len = load_list(ri, nullptr, cp[i], cp[i + 1], lst, stride);
             }
+            __syncwarp();
+            cnt = warp_union(lst, stride, len, -1, 0, buf, cap);
             if (cnt > cap) { if (lane == 0) atomicCAS(err, 0, SPAI_ERR_UNSUPPORTED); cnt = cap; }
         }
         __syncwarp();
@@ -227,9 +261,9 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
                 lo = pk; hi = pk;
                 if (pk < cnt && buf[pk] == k) hi = pk + 1;
                 while (hi - lo < F) {
-                    bool can_l = lo > 0, can_r = hi < cnt;
+                    const bool can_l = lo > 0, can_r = hi < cnt;
                     if (can_l && can_r) {
-                        long dl = (long)k - buf[lo - 1], dr = (long)buf[hi] - k;
+                        const long dl = (long)k - buf[lo - 1], dr = (long)buf[hi] - k;
                         if (dl <= dr) lo--; else hi++;
                     } else if (can_l) lo--;
                     else hi++;
@@ -238,395 +272,19 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
             lo = __shfl_sync(0xffffffffu, lo, 0);
             hi = __shfl_sync(0xffffffffu, hi, 0);
         }
-        int nj = hi - lo;
+        const int nj = hi - lo;
+        const int jl = lane < nj ? buf[lo + lane] : -1;
         for (int t = lane; t < F; t += 32) Jidx[k * F + t] = t < nj ? buf[lo + t] : -1;
         if (lane == 0) Jcnt[k] = nj;
         __syncwarp();
-    }
-}
-
-// |I_k| = |union of the nonzero columns of rows j in J_k, plus k|
-__global__ void k_shadow_count(int64_t n, int F, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                               const double* __restrict__ val, const int32_t* __restrict__ Jidx,
-                               const int32_t* __restrict__ Jcnt, int32_t* __restrict__ Icnt, int* __restrict__ maxI)
-{
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < n; k += (int64_t)gridDim.x * wpb) {
-        int nj = Jcnt[k];
-        ListCursor c;
-        if (lane < nj) {
-            int j = Jidx[k * F + lane];
-            c.q = rp[j]; c.e = rp[j + 1];
-            cursor_load(c, col, val);
-        } else if (lane == nj) {
-            c.q = 0; c.e = 1; c.head = (int)k;
-        } else {
-            c.q = 0; c.e = 0; c.head = INT_MAX;
-        }
-        int cnt = 0;
-        while (true) {
-            int mn = __reduce_min_sync(0xffffffffu, c.head);
-            if (mn == INT_MAX) break;
-            cnt++;
-            if (c.head == mn) {
-                c.q++;
-                if (lane < nj) cursor_load(c, col, val);
-                else c.head = INT_MAX;
-            }
-        }
-        if (lane == 0) {
-            Icnt[k] = cnt;
-            atomicMax(maxI, cnt);
-        }
-    }
-}
-
-// ---------------------------------------------------------------- the column kernel
-
-struct SpaiArgs {
-    int64_t n;
-    int F;
-    const int64_t* rp;
-    const int32_t* col;
-    const double* val;
-    const int64_t* cp;   // A^T structure (adaptive)
-    const int32_t* ri;
-    const double* d;
-    int32_t* Jidx;       // n * F, in: initial pattern, out: final pattern
-    int32_t* Jcnt;       // n
-    double* Praw;        // n * F: mbar * d(J)
-    void* mval;          // n * F in storage precision
-    double* colres;      // n
-    int32_t* flags;      // n
-    int32_t* Icnt;       // n
-    int32_t* nsolve;     // n
-    double eps;
-    int alpha, beta, rho_restricted;
-    int mmax, cmax;      // per-warp tile rows and candidate capacity
-    int warp_bytes;
-    int* err;
-};
-
-__device__ __forceinline__ int bsearch_smem(const int32_t* a, int len, int key)
-{
-    int lo = 0, hi = len - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int v = a[mid];
-        if (v == key) return mid;
-        if (v < key) lo = mid + 1; else hi = mid - 1;
-    }
-    return -1;
-}
-
-// warp bitonic sort of a[0..len2) in shared memory, len2 a power of two
-__device__ void warp_bitonic_sort(int32_t* a, int len2)
-{
-    const int lane = threadIdx.x & 31;
-    for (int size = 2; size <= len2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < len2 / 2; t += 32) {
-                int i = 2 * t - (t & (stride - 1));
-                int j = i + stride;
-                bool up = ((i & size) == 0);
-                int32_t x = a[i], y = a[j];
-                if ((x > y) == up) { a[i] = y; a[j] = x; }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-#define CF_CONVERGED 1
-#define CF_FILLCAP 2
-#define CF_ALPHA 4
-#define CF_NOCAND 8
-#define CF_SINGULAR 16
-#define CF_NONFINITE 32
-#define CF_TOOBIG 64   // the augmented shadow exceeded the tile: previous solve kept
-
-template <class S, bool ADAPTIVE>
-__global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
-{
-    typedef typename Compute<S>::T C;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int MM = a.mmax;
-    unsigned char* base = smem + (size_t)wib * a.warp_bytes;
-    int32_t* Iidx = (int32_t*)base;
-    size_t off = ((size_t)MM * 4 + 15) & ~size_t(15);
-    C* W = (C*)(base + off);
-    off += ((size_t)MM * LD * sizeof(C) + 15) & ~size_t(15);
-    C* s = (C*)(base + off);
-    off += ((size_t)MM * sizeof(C) + 15) & ~size_t(15);
-    C* mb = (C*)(base + off);
-    off += 32 * sizeof(C);
-    int32_t* Jl = (int32_t*)(base + off);
-    off += 32 * 4;
-    int32_t* Jprev = (int32_t*)(base + off);
-    off += 32 * 4;
-    int32_t* cand = (int32_t*)(base + off);
-    off += (size_t)a.cmax * 4;
-    C* rho = (C*)(base + off);
-    const unsigned FULL = 0xffffffffu;
-    const int F = a.F;
-
-    for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < a.n; k += (int64_t)gridDim.x * wpb) {
-        int nj = a.Jcnt[k];
-        if (lane < nj) Jl[lane] = a.Jidx[k * F + lane];
+        // shadow size of the (initial) pattern
+        int len = 0;
+        if (lane < nj) len = load_list(col, val, rp[jl], rp[jl + 1], lst, stride);
         __syncwarp();
-        int fl = 0, m = 0, ns = 0, nj_prev = nj, m_prev = 0;
-        C snorm = 0;
-        for (int step = 0;; step++) {
-            // ---- gather Abar = B(I_k, J_k), ebar = e_k(I_k) by a sorted merge
-            ListCursor cur;
-            double dj = 0.0;
-            if (lane < nj) {
-                int j = Jl[lane];
-                dj = a.d[j];
-                cur.q = a.rp[j]; cur.e = a.rp[j + 1];
-                cursor_load(cur, a.col, a.val);
-            } else if (lane == nj) {
-                cur.q = 0; cur.e = 1; cur.head = (int)k;
-            } else {
-                cur.q = 0; cur.e = 0; cur.head = INT_MAX;
-            }
-            m = 0;
-            while (true) {
-                int mn = __reduce_min_sync(FULL, cur.head);
-                if (mn == INT_MAX) break;
-                bool has = cur.head == mn;
-                if (m < MM) {
-                    if (lane == 0) Iidx[m] = mn;
-                    if (lane <= nj) {
-                        C v = C(0);
-                        if (has) v = lane < nj ? to_c(from_d<S>(a.val[cur.q] * dj)) : C(1);
-                        W[m * LD + lane] = v;
-                    }
-                }
-                m++;
-                if (has) {
-                    cur.q++;
-                    if (lane < nj) cursor_load(cur, a.col, a.val);
-                    else cur.head = INT_MAX;
-                }
-            }
-            __syncwarp();
-            if (m > MM) {
-                fl |= CF_TOOBIG;
-                if (step == 0) {
-                    if (lane == 0) atomicCAS(a.err, 0, SPAI_ERR_UNSUPPORTED);
-                } else {
-                    // the augmented shadow does not fit the tile: keep the previous solve
-                    nj = nj_prev;
-                    m = m_prev;
-                    if (lane < nj) Jl[lane] = Jprev[lane];
-                    __syncwarp();
-                }
-                break;
-            }
-            // ---- Householder QR of [Abar | ebar]; lane t owns column t
-            const int steps = nj < m ? nj : m;
-            for (int c = 0; c < steps; c++) {
-                C g0 = 0, g1 = 0;
-                if (lane <= nj) {
-                    int i = c;
-                    for (; i + 1 < m; i += 2) {
-                        g0 = fma(W[i * LD + c], W[i * LD + lane], g0);
-                        g1 = fma(W[(i + 1) * LD + c], W[(i + 1) * LD + lane], g1);
-                    }
-                    if (i < m) g0 = fma(W[i * LD + c], W[i * LD + lane], g0);
-                }
-                C g = g0 + g1;
-                C sig2 = __shfl_sync(FULL, g, c);
-                C nrm = rnd<S>(sqrt(sig2));
-                if (nrm == C(0)) continue;
-                C x0 = W[c * LD + c];
-                C alpha = x0 >= C(0) ? -nrm : nrm;
-                C v0 = rnd<S>(x0 - alpha);
-                C vtv = C(2) * nrm * (nrm + fabs(x0));
-                __syncwarp();
-                if (lane > c && lane <= nj) {
-                    C act = W[c * LD + lane];
-                    C sv = g + (v0 - x0) * act;
-                    C f = rnd<S>((sv + sv) / vtv);
-                    W[c * LD + lane] = rnd<S>(act - f * v0);
-                    for (int i = c + 1; i < m; i++) W[i * LD + lane] = rnd<S>(W[i * LD + lane] - f * W[i * LD + c]);
-                }
-                __syncwarp();
-                if (lane == c) W[c * LD + c] = alpha;
-                __syncwarp();
-            }
-            // ---- back substitution R mbar = (Q^T ebar)(1:nj); lane t ends with mbar_t
-            {
-                C y = lane < nj ? W[lane * LD + nj] : C(0);
-                C mv = 0;
-                for (int c = nj - 1; c >= 0; c--) {
-                    C mc = 0;
-                    if (lane == c) {
-                        C rcc = c < m ? W[c * LD + c] : C(0);
-                        if (rcc != C(0)) mc = rnd<S>(rnd<S>(y) / rcc);
-                        else fl |= CF_SINGULAR;
-                        mv = mc;
-                    }
-                    mc = __shfl_sync(FULL, mc, c);
-                    if (lane < c) y = y - W[lane * LD + c] * mc;
-                }
-                fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
-                if (lane < nj) mb[lane] = mv;
-            }
-            __syncwarp();
-            // ---- explicit residual s = Abar mbar - ebar, re-gathered from A
-            for (int p = lane; p < m; p += 32) s[p] = C(0);
-            __syncwarp();
-            for (int c = 0; c < nj; c++) {
-                int j = Jl[c];
-                double djc = a.d[j];
-                C mc = mb[c];
-                for (int64_t q = a.rp[j] + lane; q < a.rp[j + 1]; q += 32) {
-                    double av = a.val[q];
-                    if (av != 0.0) {
-                        int p = bsearch_smem(Iidx, m, a.col[q]);
-                        s[p] = fma(to_c(from_d<S>(av * djc)), mc, s[p]);
-                    }
-                }
-                __syncwarp();
-            }
-            C part = 0;
-            for (int p = lane; p < m; p += 32) {
-                C e = Iidx[p] == (int)k ? C(1) : C(0);
-                C sp = rnd<S>(rnd<S>(s[p]) - e);
-                s[p] = sp;
-                part = fma(sp, sp, part);
-            }
-            C s2 = warp_sum(part);
-            snorm = rnd<S>(sqrt(s2));
-            ns++;
-            __syncwarp();
-            if (!isfinite((double)snorm)) fl |= CF_NONFINITE;
-            if (snorm <= (C)a.eps) { fl |= CF_CONVERGED; break; }
-            if (!ADAPTIVE) break;
-            if (step >= a.alpha) { fl |= CF_ALPHA; break; }
-            if (nj >= F) { fl |= CF_FILLCAP; break; }
-            // ---- candidates: J~ = union over l in I with s_l != 0 of {j : a_jl != 0} \ J
-            int cnt = 0;
-            bool over = false;
-            for (int p = 0; p < m; p++) {
-                if (s[p] == C(0)) continue;
-                int l = Iidx[p];
-                int64_t b = a.cp[l], e = a.cp[l + 1];
-                for (int64_t q0 = b; q0 < e; q0 += 32) {
-                    int64_t q = q0 + lane;
-                    bool ok = false;
-                    int j = 0;
-                    if (q < e) {
-                        j = a.ri[q];
-                        ok = bsearch_smem(Jl, nj, j) < 0;
-                    }
-                    unsigned bal = __ballot_sync(FULL, ok);
-                    int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                    if (ok && pos < a.cmax) cand[pos] = j;
-                    cnt += __popc(bal);
-                }
-            }
-            if (cnt > a.cmax) { over = true; cnt = a.cmax; }
-            if (over && lane == 0) atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
-            int len2 = 1;
-            while (len2 < cnt) len2 <<= 1;
-            if (len2 > a.cmax) len2 = a.cmax; // cmax is a power of two
-            for (int t = cnt + lane; t < len2; t += 32) cand[t] = INT_MAX;
-            __syncwarp();
-            warp_bitonic_sort(cand, len2);
-            // unique, in order
-            int u = 0;
-            for (int t0 = 0; t0 < cnt; t0 += 32) {
-                int t = t0 + lane;
-                int v = t < cnt ? cand[t] : INT_MAX;
-                bool keep = t < cnt && (t == 0 || cand[t - 1] != v);
-                unsigned bal = __ballot_sync(FULL, keep);
-                __syncwarp();
-                if (keep) cand[u + __popc(bal & ((1u << lane) - 1u))] = v;
-                u += __popc(bal);
-                __syncwarp();
-            }
-            if (u == 0) { fl |= CF_NOCAND; break; }
-            // ---- rho_j^2 = ||s||^2 - (s^T b_j)^2 / ||b_j||^2 (statistics in float, or double)
-            for (int t = lane; t < u; t += 32) {
-                int j = cand[t];
-                double djj = a.d[j];
-                C num = 0, den = 0;
-                for (int64_t q = a.rp[j]; q < a.rp[j + 1]; q++) {
-                    C bij = to_c(from_d<S>(a.val[q] * djj));
-                    int p = bsearch_smem(Iidx, m, a.col[q]);
-                    if (p >= 0) num = fma(s[p], bij, num);
-                    if (!a.rho_restricted || p >= 0) den = fma(bij, bij, den);
-                }
-                C r2 = s2;
-                if (den > C(0)) r2 = s2 - num * num / den;
-                rho[t] = sqrt(r2 > C(0) ? r2 : C(0));
-            }
-            __syncwarp();
-            C rs = 0;
-            for (int t = lane; t < u; t += 32) rs += rho[t];
-            C mean = warp_sum(rs) / (C)u;
-            // ---- take up to min(beta, F - nj) acceptable indices with the smallest rho
-            if (lane < nj) Jprev[lane] = Jl[lane];
-            __syncwarp();
-            int room = F - nj;
-            int want = a.beta < room ? a.beta : room;
-            int nadd = 0;
-            for (int it = 0; it < want; it++) {
-                C br = C(0);
-                int bj = INT_MAX, bt = -1;
-                for (int t = lane; t < u; t += 32) {
-                    C r = rho[t];
-                    int j = cand[t];
-                    if (j < 0 || !(r <= mean)) continue;
-                    if (bt < 0 || r < br || (r == br && j < bj)) { br = r; bj = j; bt = t; }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    C ob = __shfl_xor_sync(FULL, br, o);
-                    int oj = __shfl_xor_sync(FULL, bj, o);
-                    int ot = __shfl_xor_sync(FULL, bt, o);
-                    bool take = ot >= 0 && (bt < 0 || ob < br || (ob == br && oj < bj));
-                    if (take) { br = ob; bj = oj; bt = ot; }
-                }
-                if (bt < 0) break;
-                if (lane == 0) {
-                    cand[bt] = -1;
-                    // sorted insert into J
-                    int pos = nj + nadd;
-                    while (pos > 0 && Jl[pos - 1] > bj) { Jl[pos] = Jl[pos - 1]; pos--; }
-                    Jl[pos] = bj;
-                }
-                nadd++;
-                __syncwarp();
-            }
-            if (nadd == 0) { fl |= CF_NOCAND; break; }
-            nj_prev = nj;
-            m_prev = m;
-            nj += nadd;
-            __syncwarp();
-        }
-        fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
-        // ---- outputs: row k of P = mbar_k * d(J_k)
-        for (int t = lane; t < F; t += 32) {
-            bool in = t < nj;
-            int j = in ? Jl[t] : -1;
-            C mv = in ? mb[t] : C(0);
-            a.Jidx[k * F + t] = j;
-            ((S*)a.mval)[k * F + t] = from_d<S>((double)mv);
-            a.Praw[k * F + t] = in ? (double)mv * a.d[j] : 0.0;
-            if (in && !isfinite((double)mv)) fl |= CF_NONFINITE;
-        }
-        fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
+        const int mI = warp_union(lst, stride, len, nj, (int)k, nullptr, 0);
         if (lane == 0) {
-            a.Jcnt[k] = nj;
-            a.colres[k] = (double)snorm;
-            a.flags[k] = fl;
-            a.Icnt[k] = m;
-            a.nsolve[k] = ns;
+            Icnt[k] = mI;
+            atomicMax(maxI, mI);
         }
         __syncwarp();
     }
@@ -682,48 +340,11 @@ __global__ void k_max_row(int64_t n, const int64_t* __restrict__ rp, int* __rest
     if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
-template <class S>
-size_t warp_bytes_for(int mmax, int cmax)
-{
-    typedef typename Compute<S>::T C;
-    size_t b = ((size_t)mmax * 4 + 15) & ~size_t(15);
-    b += ((size_t)mmax * LD * sizeof(C) + 15) & ~size_t(15);
-    b += ((size_t)mmax * sizeof(C) + 15) & ~size_t(15);
-    b += 32 * sizeof(C) + 64 * 4;
-    b += (size_t)cmax * 4 + (size_t)cmax * sizeof(C);
-    return (b + 15) & ~size_t(15);
-}
-
-template <class S>
-int launch_spai(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
-{
-    SpaiArgs a = a0;
-    if (!adaptive) a.cmax = 0;
-    // candidate capacity: halve until one warp's tile fits
-    while (adaptive && a.cmax > 256 && warp_bytes_for<S>(a.mmax, a.cmax) > smem_cap) a.cmax >>= 1;
-    size_t wb = warp_bytes_for<S>(a.mmax, a.cmax);
-    a.warp_bytes = (int)wb;
-    int wpb = (int)(smem_cap / wb);
-    if (wpb > 8) wpb = 8;
-    if (wpb < 1) return SPAI_ERR_UNSUPPORTED;
-    size_t smem = wb * wpb;
-    auto kern = adaptive ? k_spai<S, true> : k_spai<S, false>;
-    SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int64_t blocks = (a.n + wpb - 1) / wpb;
-    int64_t cap = (int64_t)num_sms * 64;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, wpb * 32, smem, s>>>(a);
-    SPAI_CUDA_TRY(cudaGetLastError());
-    return 0;
-}
-
 }  // namespace
 
 int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
                    spai_precond* P_out, spai_stats* st)
 {
-    (void)device;
     const int64_t n = A.n, nnz = A.nnz;
     if (!o || !P_out) return SPAI_ERR_INVALID_ARG;
     if (o->max_fill < 1 || o->max_fill > MAX_FILL) return SPAI_ERR_UNSUPPORTED;
@@ -795,24 +416,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         nl += 2;
     }
     {
-        // the pattern: buffer for the uncapped union of pattern(A^2)
-        const int cap = 1024;
-        const int wpb = 4;
-        size_t sm = (size_t)cap * 4 * wpb;
-        SPAI_CUDA_TRY(cudaFuncSetAttribute(k_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms * 64);
-        if (blocks < 1) blocks = 1;
-        k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, cp, ri, Jidx, Jcnt, cap, err);
-        k_shadow_count<<<(unsigned)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms * 64), 256, 0, s>>>(
-            n, F, A.rowptr, A.col, A.val, Jidx, Jcnt, Icnt, err + 1);
-        nl += 2;
-        if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (h_err[0]) { rc = h_err[0]; goto done; }
-    }
-    {
-        // largest row nonzero count: bounds |I_k| <= max_fill * maxrow + 1 when adaptive
+        // longest row and column of A: list capacities, and |I_k| <= max_fill * maxrow + 1
         int* mr = err + 3;
         k_max_row<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8) + 1, 256, 0, s>>>(n, A.rowptr, mr);
         k_max_row<<<(unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8) + 1, 256, 0, s>>>(n, cp, mr + 1);
@@ -820,6 +424,27 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         if (cudaMemcpyAsync(&maxrow, mr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaMemcpyAsync(&maxcol, mr + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (maxrow < 1) maxrow = 1;
+        if (maxcol < 1) maxcol = 1;
+    }
+    {
+        // the pattern and its shadow sizes: per warp a buffer for the uncapped
+        // union of pattern(A^2) and 32 lists
+        const int cap = 1024;
+        const int stride = std::max(maxrow, maxcol);
+        const int wpb = 4;
+        const size_t sm = (size_t)(cap + 32 * stride) * 4 * wpb;
+        if (sm > smem_cap) { rc = SPAI_ERR_UNSUPPORTED; goto done; }
+        SPAI_CUDA_TRY(cudaFuncSetAttribute(k_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms * 64);
+        if (blocks < 1) blocks = 1;
+        k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, A.rowptr, A.col, A.val, cp, ri, Jidx, Jcnt,
+                                                        Icnt, cap, stride, err, err + 1);
+        nl += 1;
+        if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (h_err[0]) { rc = h_err[0]; goto done; }
     }
     {
         SpaiArgs a;
@@ -829,6 +454,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         a.Icnt = Icnt; a.nsolve = nsolve; a.eps = o->eps;
         a.alpha = o->alpha < 0 ? (int)((n + o->beta - 1) / std::max(o->beta, 1)) : o->alpha;
         a.beta = o->beta; a.rho_restricted = o->rho_restricted; a.err = err;
+        a.rl = maxrow;
         // adaptive: the tile holds up to MMAX_LIMIT shadow rows; a column whose
         // augmented shadow would exceed it keeps its previous solve (flag 64)
         int mneed = o->adaptive ? (int)std::min<int64_t>((int64_t)F * maxrow + 1, (int64_t)MMAX_LIMIT) : h_err[1];
@@ -840,9 +466,9 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         while (cmax < (int64_t)a.mmax * maxcol) cmax <<= 1;
         a.cmax = cmax > 8192 ? 8192 : (cmax < 256 ? 256 : cmax);
         if (cudaEventRecord(ek0, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (o->uf == SPAI_HALF) TRY(launch_spai<__half>(a, o->adaptive != 0, num_sms, smem_cap, s));
-        else if (o->uf == SPAI_SINGLE) TRY(launch_spai<float>(a, o->adaptive != 0, num_sms, smem_cap, s));
-        else TRY(launch_spai<double>(a, o->adaptive != 0, num_sms, smem_cap, s));
+        if (o->uf == SPAI_HALF) TRY(launch_spai_half(a, o->adaptive != 0, num_sms, smem_cap, s));
+        else if (o->uf == SPAI_SINGLE) TRY(launch_spai_single(a, o->adaptive != 0, num_sms, smem_cap, s));
+        else TRY(launch_spai_double(a, o->adaptive != 0, num_sms, smem_cap, s));
         if (cudaEventRecord(ek1, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         nl++;
     }

@@ -1,0 +1,595 @@
+// The SPAI column kernel: Algorithm 1 for one column k of M per warp,
+// on B = A^T D (column j of B is row j of A times d_j).
+//
+// Per column:
+//   1. load the rows j in J_k of A (nonzeros only, scaled by d_j and rounded
+//      to u_f) into shared memory, one list per lane (all loads in flight);
+//   2. gather: a sorted warp merge of those lists (plus the list {k}) gives
+//      the shadow I_k and the dense tile [B(I_k,J_k) | e_k(I_k)] (row-major,
+//      shared memory);
+//   3. Householder QR of the tile and back substitution, either
+//        - register path (MM = 32/64): lane t keeps column t of the tile
+//          in registers; each step the pivot lane writes its column to
+//          shared memory, every lane forms its dot product with it (the
+//          pivot lane's own dot is ||x||^2), and the trailing lanes apply
+//          the reflector to their registers; back substitution is row
+//          oriented, m_c = (y_c - sum_t R(c,t) m_t) / R(c,c), one warp sum
+//          per row; or
+//        - shared-memory path (MM = 0, any |I_k| up to the tile height):
+//          the same steps in place on the tile in shared memory;
+//   4. explicit residual s = B(I,J) m - e and ||s||_2 from the original
+//      tile (register path) or from the row lists (shared-memory path);
+//   5. adaptive: candidates J~ (column lists of A for l in I with s_l != 0,
+//      minus J), rho_j, mean acceptance, up to beta additions, loop.
+// Arithmetic: values are stored in u_f (S) and every inner product and
+// update runs in the compute type (float for half/single, double for
+// double) with each stored result rounded to S -- the FP16-storage /
+// FP32-accumulate model at u_f = half.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace spai {
+
+constexpr int SPAI_LD = 33;       // row stride of the tile (32 columns + pad)
+constexpr int SPAI_MAX_FILL = 31; // |J_k| <= 31 so that [B(I,J) | e] fits 32 lanes
+constexpr int SPAI_MMAX_LIMIT = 512;
+
+#define CF_CONVERGED 1
+#define CF_FILLCAP 2
+#define CF_ALPHA 4
+#define CF_NOCAND 8
+#define CF_SINGULAR 16
+#define CF_NONFINITE 32
+#define CF_TOOBIG 64  // the augmented shadow exceeded the tile: previous solve kept
+
+struct SpaiArgs {
+    int64_t n;
+    int F;
+    const int64_t* rp;
+    const int32_t* col;
+    const double* val;
+    const int64_t* cp;   // A^T structure (adaptive)
+    const int32_t* ri;
+    const double* d;
+    int32_t* Jidx;       // n * F, in: initial pattern, out: final pattern
+    int32_t* Jcnt;       // n
+    double* Praw;        // n * F: mbar * d(J)
+    void* mval;          // n * F in storage precision
+    double* colres;      // n
+    int32_t* flags;      // n
+    int32_t* Icnt;       // n
+    int32_t* nsolve;     // n
+    double eps;
+    int alpha, beta, rho_restricted;
+    int mmax, cmax;      // per-warp tile rows and candidate capacity
+    int rl;              // longest row of A (list capacity per lane)
+    int warp_bytes;
+    int* err;
+};
+
+__device__ __forceinline__ int bsearch_smem(const int32_t* a, int len, int key)
+{
+    int lo = 0, hi = len - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = a[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+// warp bitonic sort of a[0..len2) in shared memory, len2 a power of two
+__device__ inline void warp_bitonic_sort(int32_t* a, int len2)
+{
+    const int lane = threadIdx.x & 31;
+    for (int size = 2; size <= len2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < len2 / 2; t += 32) {
+                int i = 2 * t - (t & (stride - 1));
+                int j = i + stride;
+                bool up = ((i & size) == 0);
+                int32_t x = a[i], y = a[j];
+                if ((x > y) == up) { a[i] = y; a[j] = x; }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// per-warp shared-memory layout
+template <class C>
+struct Tile {
+    int32_t* I;     // mm
+    C* W;           // mm * LD: [B(I,J) | e] (the shared-memory path factors it in place)
+    C* v;           // mm: pivot column / residual
+    C* mb;          // 32
+    int32_t* J;     // 32
+    int32_t* Jp;    // 32
+    int32_t* lcol;  // 32 * rl
+    C* lval;        // 32 * rl
+    int32_t* lcnt;  // 32
+    int32_t* cand;  // cmax
+    C* rho;         // cmax
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <class C>
+__host__ __device__ inline size_t tile_bytes(int mm, int rl, int cmax)
+{
+    size_t b = align16((size_t)mm * 4);
+    b += align16((size_t)mm * SPAI_LD * sizeof(C));
+    b += align16((size_t)mm * sizeof(C));
+    b += align16(32 * sizeof(C)) + 3 * 32 * 4;
+    b += align16((size_t)32 * rl * 4) + align16((size_t)32 * rl * sizeof(C));
+    b += align16((size_t)cmax * 4) + align16((size_t)cmax * sizeof(C));
+    return align16(b);
+}
+
+template <class C>
+__device__ inline Tile<C> carve(unsigned char* base, int mm, int rl, int cmax)
+{
+    Tile<C> t;
+    size_t off = 0;
+    t.I = (int32_t*)(base + off); off += align16((size_t)mm * 4);
+    t.W = (C*)(base + off); off += align16((size_t)mm * SPAI_LD * sizeof(C));
+    t.v = (C*)(base + off); off += align16((size_t)mm * sizeof(C));
+    t.mb = (C*)(base + off); off += align16(32 * sizeof(C));
+    t.J = (int32_t*)(base + off); off += 32 * 4;
+    t.Jp = (int32_t*)(base + off); off += 32 * 4;
+    t.lcnt = (int32_t*)(base + off); off += 32 * 4;
+    t.lcol = (int32_t*)(base + off); off += align16((size_t)32 * rl * 4);
+    t.lval = (C*)(base + off); off += align16((size_t)32 * rl * sizeof(C));
+    t.cand = (int32_t*)(base + off); off += align16((size_t)cmax * 4);
+    t.rho = (C*)(base + off);
+    return t;
+}
+
+// Steps 1-2: lists of the rows in J, then the sorted merge.  Returns |I_k|
+// (which may exceed mm; then only the first mm rows were written).
+template <class S, class C>
+__device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64_t k, int nj, int mm)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    int len = 0;
+    if (lane < nj) {
+        const int j = T.J[lane];
+        const double dj = a.d[j];
+        const int64_t b = a.rp[j], e = a.rp[j + 1];
+        int32_t* lc = T.lcol + lane * a.rl;
+        C* lv = T.lval + lane * a.rl;
+        for (int64_t q = b; q < e; q += 4) {
+            double vv[4];
+            int cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                vv[u] = q + u < e ? a.val[q + u] : 0.0;
+                cc[u] = q + u < e ? a.col[q + u] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (vv[u] != 0.0) {  // the shadow counts |a_ij| != 0
+                    lc[len] = cc[u];
+                    lv[len] = to_c(from_d<S>(vv[u] * dj));
+                    len++;
+                }
+            }
+        }
+    }
+    T.lcnt[lane] = len;
+    __syncwarp();
+    // merge; lane nj carries the list {k} with value 1 (the e_k column)
+    int q = 0;
+    const int32_t* lc = T.lcol + lane * a.rl;
+    const C* lv = T.lval + lane * a.rl;
+    int head = lane < nj ? (len > 0 ? lc[0] : INT_MAX) : (lane == nj ? (int)k : INT_MAX);
+    int m = 0;
+    while (true) {
+        const int mn = __reduce_min_sync(FULL, head);
+        if (mn == INT_MAX) break;
+        const bool has = head == mn;
+        if (m < mm) {
+            if (lane == 0) T.I[m] = mn;
+            if (lane <= nj) T.W[m * SPAI_LD + lane] = has ? (lane < nj ? lv[q] : C(1)) : C(0);
+        }
+        m++;
+        if (has) {
+            q++;
+            head = (lane < nj && q < len) ? lc[q] : INT_MAX;
+        }
+    }
+    __syncwarp();
+    return m;
+}
+
+// Step 3, register path.  Returns flags (CF_SINGULAR); writes mbar to T.mb.
+template <class S, class C, int MM>
+__device__ __forceinline__ int qr_solve_reg(const Tile<C>& T, int m, int nj)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    C col[MM];
+#pragma unroll
+    for (int i = 0; i < MM; i++) col[i] = (i < m && lane <= nj) ? T.W[i * SPAI_LD + lane] : C(0);
+    const int steps = nj < m ? nj : m;
+#pragma unroll
+    for (int c = 0; c < SPAI_MAX_FILL; c++) {
+        if (c < steps) {
+            // the pivot lane publishes x = column c, rows >= c
+            if (lane == c) {
+#pragma unroll
+                for (int i = 0; i < MM; i++) T.v[i] = i >= c ? col[i] : C(0);
+            }
+            __syncwarp();
+            C g0 = 0, g1 = 0;
+#pragma unroll
+            for (int i = 0; i < MM; i += 2) {
+                if (i + 1 >= c) {
+                    g0 = fma(T.v[i], col[i], g0);
+                    g1 = fma(T.v[i + 1], col[i + 1], g1);
+                }
+            }
+            const C g = g0 + g1;
+            const C sig2 = __shfl_sync(FULL, g, c);
+            const C x0 = __shfl_sync(FULL, col[c], c);
+            const C nrm = rnd<S>(sqrt(sig2));
+            if (nrm != C(0)) {
+                const C alpha = x0 >= C(0) ? -nrm : nrm;
+                const C v0 = rnd<S>(x0 - alpha);
+                const C vtv = C(2) * nrm * (nrm + fabs(x0));
+                if (lane > c && lane <= nj) {
+                    const C act = col[c];
+                    const C sv = g + (v0 - x0) * act;
+                    const C f = rnd<S>((sv + sv) / vtv);
+                    col[c] = rnd<S>(act - f * v0);
+#pragma unroll
+                    for (int i = c + 1; i < MM; i++) col[i] = rnd<S>(col[i] - f * T.v[i]);
+                }
+                if (lane == c) col[c] = alpha;
+            }
+            __syncwarp();
+        }
+    }
+    // back substitution, row oriented: R(c, t) is lane t's col[c]
+    int fl = 0;
+    C mv = 0;
+#pragma unroll
+    for (int c = SPAI_MAX_FILL - 1; c >= 0; c--) {
+        if (c < nj) {
+            C part = (lane > c && lane < nj) ? col[c] * mv : C(0);
+            part = warp_sum(part);
+            const C yc = __shfl_sync(FULL, col[c], nj);
+            const C rcc = __shfl_sync(FULL, col[c], c);
+            C mc = 0;
+            if (c < m && rcc != C(0)) mc = rnd<S>(rnd<S>(yc - part) / rcc);
+            else fl = CF_SINGULAR;
+            if (lane == c) mv = mc;
+        }
+    }
+    if (lane < nj) T.mb[lane] = mv;
+    __syncwarp();
+    return fl;
+}
+
+// Step 3, shared-memory path, in place on the tile.
+template <class S, class C>
+__device__ __forceinline__ int qr_solve_smem(const Tile<C>& T, int m, int nj)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    C* W = T.W;
+    const int steps = nj < m ? nj : m;
+    for (int c = 0; c < steps; c++) {
+        C g0 = 0, g1 = 0;
+        if (lane <= nj) {
+            int i = c;
+            for (; i + 1 < m; i += 2) {
+                g0 = fma(W[i * SPAI_LD + c], W[i * SPAI_LD + lane], g0);
+                g1 = fma(W[(i + 1) * SPAI_LD + c], W[(i + 1) * SPAI_LD + lane], g1);
+            }
+            if (i < m) g0 = fma(W[i * SPAI_LD + c], W[i * SPAI_LD + lane], g0);
+        }
+        const C g = g0 + g1;
+        const C sig2 = __shfl_sync(FULL, g, c);
+        const C nrm = rnd<S>(sqrt(sig2));
+        if (nrm == C(0)) continue;
+        const C x0 = W[c * SPAI_LD + c];
+        const C alpha = x0 >= C(0) ? -nrm : nrm;
+        const C v0 = rnd<S>(x0 - alpha);
+        const C vtv = C(2) * nrm * (nrm + fabs(x0));
+        __syncwarp();
+        if (lane > c && lane <= nj) {
+            const C act = W[c * SPAI_LD + lane];
+            const C sv = g + (v0 - x0) * act;
+            const C f = rnd<S>((sv + sv) / vtv);
+            W[c * SPAI_LD + lane] = rnd<S>(act - f * v0);
+            for (int i = c + 1; i < m; i++) W[i * SPAI_LD + lane] = rnd<S>(W[i * SPAI_LD + lane] - f * W[i * SPAI_LD + c]);
+        }
+        __syncwarp();
+        if (lane == c) W[c * SPAI_LD + c] = alpha;
+        __syncwarp();
+    }
+    int fl = 0;
+    C mv = 0;
+    for (int c = nj - 1; c >= 0; c--) {
+        C part = (lane > c && lane < nj) ? W[c * SPAI_LD + lane] * mv : C(0);
+        part = warp_sum(part);
+        const C yc = W[c * SPAI_LD + nj];
+        const C rcc = c < m ? W[c * SPAI_LD + c] : C(0);
+        C mc = 0;
+        if (rcc != C(0)) mc = rnd<S>(rnd<S>(yc - part) / rcc);
+        else fl = CF_SINGULAR;
+        if (lane == c) mv = mc;
+    }
+    if (lane < nj) T.mb[lane] = mv;
+    __syncwarp();
+    return fl;
+}
+
+// Step 4 (shared-memory path): s = B(I,J) mbar - e from the row lists, one
+// column at a time in order (lane-parallel over the column's entries, which
+// hit distinct rows); returns ||s||^2 (all lanes)
+template <class S, class C>
+__device__ __forceinline__ C residual_lists(const SpaiArgs& a, const Tile<C>& T, int64_t k, int m, int nj)
+{
+    const int lane = threadIdx.x & 31;
+    for (int p = lane; p < m; p += 32) T.v[p] = C(0);
+    __syncwarp();
+    for (int c = 0; c < nj; c++) {
+        const int len = T.lcnt[c];
+        const int32_t* lc = T.lcol + c * a.rl;
+        const C* lv = T.lval + c * a.rl;
+        const C mc = T.mb[c];
+        for (int q = lane; q < len; q += 32) {
+            const int p = bsearch_smem(T.I, m, lc[q]);
+            T.v[p] = fma(lv[q], mc, T.v[p]);
+        }
+        __syncwarp();
+    }
+    C part = 0;
+    for (int p = lane; p < m; p += 32) {
+        const C e = T.I[p] == (int)k ? C(1) : C(0);
+        const C sp = rnd<S>(rnd<S>(T.v[p]) - e);
+        T.v[p] = sp;
+        part = fma(sp, sp, part);
+    }
+    __syncwarp();
+    return warp_sum(part);
+}
+
+// Step 4 (register path): s = B(I,J) mbar - e from the unmodified tile
+template <class S, class C>
+__device__ __forceinline__ C residual(const Tile<C>& T, int m, int nj)
+{
+    const int lane = threadIdx.x & 31;
+    C part = 0;
+    for (int p = lane; p < m; p += 32) {
+        C acc = 0;
+        for (int c = 0; c < nj; c++) acc = fma(T.W[p * SPAI_LD + c], T.mb[c], acc);
+        const C sp = rnd<S>(rnd<S>(acc) - T.W[p * SPAI_LD + nj]);
+        T.v[p] = sp;
+        part = fma(sp, sp, part);
+    }
+    __syncwarp();
+    return warp_sum(part);
+}
+
+template <class S, bool ADAPTIVE, int MM>
+__global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
+{
+    typedef typename Compute<S>::T C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const Tile<C> T = carve<C>(smem + (size_t)wib * a.warp_bytes, a.mmax, a.rl, a.cmax);
+    const unsigned FULL = 0xffffffffu;
+    const int F = a.F;
+    const int mm = a.mmax;
+
+    for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < a.n; k += (int64_t)gridDim.x * wpb) {
+        int nj = a.Jcnt[k];
+        if (lane < nj) T.J[lane] = a.Jidx[k * F + lane];
+        __syncwarp();
+        int fl = 0, m = 0, ns = 0, nj_prev = nj, m_prev = 0;
+        C snorm = 0;
+        for (int step = 0;; step++) {
+            m = gather<S, C>(a, T, k, nj, mm);
+            if (m > mm) {
+                fl |= CF_TOOBIG;
+                if (step == 0) {
+                    if (lane == 0) atomicCAS(a.err, 0, SPAI_ERR_UNSUPPORTED);
+                } else {
+                    // the augmented shadow does not fit the tile: keep the previous solve
+                    nj = nj_prev;
+                    m = m_prev;
+                    if (lane < nj) T.J[lane] = T.Jp[lane];
+                    __syncwarp();
+                }
+                break;
+            }
+            C s2;
+            if (MM > 0) {
+                fl |= qr_solve_reg<S, C, (MM > 0 ? MM : 32)>(T, m, nj);
+                s2 = residual<S, C>(T, m, nj);
+            } else {
+                fl |= qr_solve_smem<S, C>(T, m, nj);
+                s2 = residual_lists<S, C>(a, T, k, m, nj);
+            }
+            snorm = rnd<S>(sqrt(s2));
+            ns++;
+            if (!isfinite((double)snorm)) fl |= CF_NONFINITE;
+            if (snorm <= (C)a.eps) { fl |= CF_CONVERGED; break; }
+            if (!ADAPTIVE) break;
+            if (step >= a.alpha) { fl |= CF_ALPHA; break; }
+            if (nj >= F) { fl |= CF_FILLCAP; break; }
+            // ---- candidates: J~ = union over l in I with s_l != 0 of {j : a_jl != 0} \ J
+            int cnt = 0;
+            for (int p = 0; p < m; p++) {
+                if (T.v[p] == C(0)) continue;
+                const int l = T.I[p];
+                const int64_t b = a.cp[l], e = a.cp[l + 1];
+                for (int64_t q0 = b; q0 < e; q0 += 32) {
+                    const int64_t q = q0 + lane;
+                    bool ok = false;
+                    int j = 0;
+                    if (q < e) {
+                        j = a.ri[q];
+                        ok = bsearch_smem(T.J, nj, j) < 0;
+                    }
+                    const unsigned bal = __ballot_sync(FULL, ok);
+                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                    if (ok && pos < a.cmax) T.cand[pos] = j;
+                    cnt += __popc(bal);
+                }
+            }
+            if (cnt > a.cmax) {
+                if (lane == 0) atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
+                cnt = a.cmax;
+            }
+            int len2 = 1;
+            while (len2 < cnt) len2 <<= 1;
+            for (int t = cnt + lane; t < len2; t += 32) T.cand[t] = INT_MAX;
+            __syncwarp();
+            warp_bitonic_sort(T.cand, len2);
+            int u = 0;
+            for (int t0 = 0; t0 < cnt; t0 += 32) {
+                const int t = t0 + lane;
+                const int v = t < cnt ? T.cand[t] : INT_MAX;
+                const bool keep = t < cnt && (t == 0 || T.cand[t - 1] != v);
+                const unsigned bal = __ballot_sync(FULL, keep);
+                __syncwarp();
+                if (keep) T.cand[u + __popc(bal & ((1u << lane) - 1u))] = v;
+                u += __popc(bal);
+                __syncwarp();
+            }
+            if (u == 0) { fl |= CF_NOCAND; break; }
+            // ---- rho_j^2 = ||s||^2 - (s^T b_j)^2 / ||b_j||^2
+            for (int t = lane; t < u; t += 32) {
+                const int j = T.cand[t];
+                const double djj = a.d[j];
+                C num = 0, den = 0;
+                for (int64_t q = a.rp[j]; q < a.rp[j + 1]; q++) {
+                    const C bij = to_c(from_d<S>(a.val[q] * djj));
+                    const int p = bsearch_smem(T.I, m, a.col[q]);
+                    if (p >= 0) num = fma(T.v[p], bij, num);
+                    if (!a.rho_restricted || p >= 0) den = fma(bij, bij, den);
+                }
+                C r2 = s2;
+                if (den > C(0)) r2 = s2 - num * num / den;
+                T.rho[t] = sqrt(r2 > C(0) ? r2 : C(0));
+            }
+            __syncwarp();
+            C rs = 0;
+            for (int t = lane; t < u; t += 32) rs += T.rho[t];
+            const C mean = warp_sum(rs) / (C)u;
+            // ---- up to min(beta, F - nj) acceptable indices with the smallest rho
+            if (lane < nj) T.Jp[lane] = T.J[lane];
+            __syncwarp();
+            const int room = F - nj;
+            const int want = a.beta < room ? a.beta : room;
+            int nadd = 0;
+            for (int it = 0; it < want; it++) {
+                C br = C(0);
+                int bj = INT_MAX, bt = -1;
+                for (int t = lane; t < u; t += 32) {
+                    const C r = T.rho[t];
+                    const int j = T.cand[t];
+                    if (j < 0 || !(r <= mean)) continue;
+                    if (bt < 0 || r < br || (r == br && j < bj)) { br = r; bj = j; bt = t; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const C ob = __shfl_xor_sync(FULL, br, o);
+                    const int oj = __shfl_xor_sync(FULL, bj, o);
+                    const int ot = __shfl_xor_sync(FULL, bt, o);
+                    const bool take = ot >= 0 && (bt < 0 || ob < br || (ob == br && oj < bj));
+                    if (take) { br = ob; bj = oj; bt = ot; }
+                }
+                if (bt < 0) break;
+                if (lane == 0) {
+                    T.cand[bt] = -1;
+                    int pos = nj + nadd;
+                    while (pos > 0 && T.J[pos - 1] > bj) { T.J[pos] = T.J[pos - 1]; pos--; }
+                    T.J[pos] = bj;
+                }
+                nadd++;
+                __syncwarp();
+            }
+            if (nadd == 0) { fl |= CF_NOCAND; break; }
+            nj_prev = nj;
+            m_prev = m;
+            nj += nadd;
+            __syncwarp();
+        }
+        fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
+        // ---- outputs: row k of P = mbar_k * d(J_k)
+        for (int t = lane; t < F; t += 32) {
+            const bool in = t < nj;
+            const int j = in ? T.J[t] : -1;
+            const C mv = in ? T.mb[t] : C(0);
+            a.Jidx[k * F + t] = j;
+            ((S*)a.mval)[k * F + t] = from_d<S>((double)mv);
+            a.Praw[k * F + t] = in ? (double)mv * a.d[j] : 0.0;
+            if (in && !isfinite((double)mv)) fl |= CF_NONFINITE;
+        }
+        fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
+        if (lane == 0) {
+            a.Jcnt[k] = nj;
+            a.colres[k] = (double)snorm;
+            a.flags[k] = fl;
+            a.Icnt[k] = m;
+            a.nsolve[k] = ns;
+        }
+        __syncwarp();
+    }
+}
+
+// Launch for storage type S: the register path when the tile height fits
+// (32 or 64 rows), otherwise the shared-memory path.
+template <class S>
+int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    typedef typename Compute<S>::T C;
+    SpaiArgs a = a0;
+    if (!adaptive) a.cmax = 0;
+    int MMsel = 0;
+    if (a.mmax <= 32) MMsel = 32;
+    else if (a.mmax <= 64) MMsel = 64;
+    if (MMsel) a.mmax = MMsel;
+    while (adaptive && a.cmax > 256 && tile_bytes<C>(a.mmax, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
+    const size_t wb = tile_bytes<C>(a.mmax, a.rl, a.cmax);
+    a.warp_bytes = (int)wb;
+    int wpb = (int)(smem_cap / wb);
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) return SPAI_ERR_UNSUPPORTED;
+    const size_t smem = wb * wpb;
+    void (*kern)(SpaiArgs) = nullptr;
+    if (adaptive) {
+        if (MMsel == 32) kern = k_spai<S, true, 32>;
+        else if (MMsel == 64) kern = k_spai<S, true, 64>;
+        else kern = k_spai<S, true, 0>;
+    } else {
+        if (MMsel == 32) kern = k_spai<S, false, 32>;
+        else if (MMsel == 64) kern = k_spai<S, false, 64>;
+        else kern = k_spai<S, false, 0>;
+    }
+    SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int64_t blocks = (a.n + wpb - 1) / wpb;
+    const int64_t cap = (int64_t)num_sms * 64;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, wpb * 32, smem, s>>>(a);
+    SPAI_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace spai
+
+int launch_spai_half(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
+int launch_spai_single(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
+int launch_spai_double(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);

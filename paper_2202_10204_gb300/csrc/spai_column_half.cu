@@ -1,0 +1,7 @@
+// Instantiation of the SPAI column kernel for u_f = half.
+#include "spai_column.cuh"
+
+int launch_spai_half(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    return spai::launch_spai_t<__half>(a, adaptive, num_sms, smem_cap, s);
+}
