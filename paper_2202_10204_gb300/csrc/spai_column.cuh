@@ -28,6 +28,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -277,6 +278,130 @@ __device__ __forceinline__ int qr_solve_reg(const Tile<C>& T, int m, int nj)
     return fl;
 }
 
+// d = a * b + c with f16 operands and an f32 accumulator, one rounding
+// (the FP16-operand / FP32-accumulate product of the u_f = half model)
+__device__ __forceinline__ float fma_f32_f16(__half a, __half b, float c)
+{
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(b)), "f"(c));
+    return d;
+}
+
+// Step 3, register path for u_f = half: lane t keeps column t as MM/2
+// packed half2 registers.  Dot products use f16 x f16 -> f32 FMAs; the
+// reflector update a - f v is one packed f16 FMA per row pair, i.e. the
+// exact value rounded once to half (the stored trailing matrix lives in u_f).
+template <int MM>
+__device__ __forceinline__ int qr_solve_reg_half(const Tile<float>& T, int m, int nj)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    constexpr int NP = MM / 2;
+    __half2 col[NP];
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        const int i0 = 2 * p, i1 = 2 * p + 1;
+        const float a0 = (i0 < m && lane <= nj) ? T.W[i0 * SPAI_LD + lane] : 0.f;
+        const float a1 = (i1 < m && lane <= nj) ? T.W[i1 * SPAI_LD + lane] : 0.f;
+        col[p] = __floats2half2_rn(a0, a1);  // exact: the tile holds half values
+    }
+    __half2* v2 = reinterpret_cast<__half2*>(T.v);  // NP packed pivot entries (16-byte aligned)
+    const int steps = nj < m ? nj : m;
+#pragma unroll
+    for (int c = 0; c < SPAI_MAX_FILL; c++) {
+        if (c < steps) {
+            if (lane == c) {
+#pragma unroll
+                for (int p = 0; p < NP; p += 4) {
+                    __half2 q[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int i0 = 2 * (p + u);
+                        __half2 x = col[p + u];
+                        if (i0 + 1 < c) x = __float2half2_rn(0.f);
+                        else if (i0 < c) x = __halves2half2(__float2half_rn(0.f), __high2half(x));
+                        q[u] = x;
+                    }
+                    *reinterpret_cast<uint4*>(v2 + p) = *reinterpret_cast<uint4*>(q);
+                }
+            }
+            __syncwarp();
+            float g0 = 0.f, g1 = 0.f;
+#pragma unroll
+            for (int p = 0; p < NP; p += 4) {
+                if (2 * (p + 4) > c) {
+                    uint4 raw = *reinterpret_cast<const uint4*>(v2 + p);
+                    const __half2* q = reinterpret_cast<const __half2*>(&raw);
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        g0 = fma_f32_f16(__low2half(q[u]), __low2half(col[p + u]), g0);
+                        g1 = fma_f32_f16(__high2half(q[u]), __high2half(col[p + u]), g1);
+                    }
+                }
+            }
+            const float g = g0 + g1;
+            const float sig2 = __shfl_sync(FULL, g, c);
+            const float xc_own = (c & 1) ? __high2float(col[c / 2]) : __low2float(col[c / 2]);
+            const float x0 = __shfl_sync(FULL, xc_own, c);
+            const float nrm = rnd<__half>(sqrtf(sig2));
+            if (nrm != 0.f) {
+                const float alpha = x0 >= 0.f ? -nrm : nrm;
+                const float v0 = rnd<__half>(x0 - alpha);
+                const float vtv = 2.f * nrm * (nrm + fabsf(x0));
+                if (lane > c && lane <= nj) {
+                    const float act = xc_own;
+                    const float sv = g + (v0 - x0) * act;
+                    const __half f = __float2half_rn((sv + sv) / vtv);
+                    const __half2 nf = __halves2half2(__hneg(f), __hneg(f));
+#pragma unroll
+                    for (int p = 0; p < NP; p += 4) {
+                        if (2 * (p + 4) > c) {
+                            uint4 raw = *reinterpret_cast<const uint4*>(v2 + p);
+                            __half2* q = reinterpret_cast<__half2*>(&raw);
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                const int i0 = 2 * (p + u);
+                                if (i0 + 1 < c) continue;  // rows above the pivot are final
+                                __half2 vv = q[u];
+                                // row c uses v0 instead of x0
+                                if (i0 == c) vv = __halves2half2(__float2half_rn(v0), __high2half(vv));
+                                else if (i0 + 1 == c) vv = __halves2half2(__low2half(vv), __float2half_rn(v0));
+                                col[p + u] = __hfma2(nf, vv, col[p + u]);
+                            }
+                        }
+                    }
+                }
+                if (lane == c) {
+                    const __half al = __float2half_rn(alpha);
+                    if (c & 1) col[c / 2] = __halves2half2(__low2half(col[c / 2]), al);
+                    else col[c / 2] = __halves2half2(al, __high2half(col[c / 2]));
+                }
+            }
+            __syncwarp();
+        }
+    }
+    // back substitution, row oriented: R(c, t) is element c of lane t's column
+    int fl = 0;
+    float mv = 0.f;
+#pragma unroll
+    for (int c = SPAI_MAX_FILL - 1; c >= 0; c--) {
+        if (c < nj) {
+            const float rc = (c & 1) ? __high2float(col[c / 2]) : __low2float(col[c / 2]);
+            float part = (lane > c && lane < nj) ? rc * mv : 0.f;
+            part = warp_sum(part);
+            const float yc = __shfl_sync(FULL, rc, nj);
+            const float rcc = __shfl_sync(FULL, rc, c);
+            float mc = 0.f;
+            if (c < m && rcc != 0.f) mc = rnd<__half>(rnd<__half>(yc - part) / rcc);
+            else fl = CF_SINGULAR;
+            if (lane == c) mv = mc;
+        }
+    }
+    if (lane < nj) T.mb[lane] = mv;
+    __syncwarp();
+    return fl;
+}
+
 // Step 3, shared-memory path, in place on the tile.
 template <class S, class C>
 __device__ __forceinline__ int qr_solve_smem(const Tile<C>& T, int m, int nj)
@@ -414,7 +539,8 @@ __global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
             }
             C s2;
             if (MM > 0) {
-                fl |= qr_solve_reg<S, C, (MM > 0 ? MM : 32)>(T, m, nj);
+                if constexpr (std::is_same<S, __half>::value) fl |= qr_solve_reg_half<(MM > 0 ? MM : 32)>(T, m, nj);
+                else fl |= qr_solve_reg<S, C, (MM > 0 ? MM : 32)>(T, m, nj);
                 s2 = residual<S, C>(T, m, nj);
             } else {
                 fl |= qr_solve_smem<S, C>(T, m, nj);
@@ -565,7 +691,9 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
     const size_t wb = tile_bytes<C>(a.mmax, a.rl, a.cmax);
     a.warp_bytes = (int)wb;
     int wpb = (int)(smem_cap / wb);
-    if (wpb > 8) wpb = 8;
+    // register-path warps hold their tile in registers: small blocks keep the
+    // occupancy granularity fine
+    if (wpb > (MMsel ? 2 : 8)) wpb = MMsel ? 2 : 8;
     if (wpb < 1) return SPAI_ERR_UNSUPPORTED;
     const size_t smem = wb * wpb;
     void (*kern)(SpaiArgs) = nullptr;
