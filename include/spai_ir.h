@@ -185,6 +185,31 @@ int solver_poll(spai_ctx ctx, uint64_t ticket, double* x, ir_stats* st);
 
 const char* spai_strerror(int code);
 
+/* ---- allocation-free refinement solve --------------------------------
+ * No counterpart in the paper: an engineering entry point for callers that
+ * cannot call the CUDA allocator -- code running inside a stream capture,
+ * allocation-free real-time or embedded runtimes, and hosts that own the
+ * GPU memory budget exactly.  It runs the same refinement kernels as
+ * gmres_ir_solve with a given preconditioner, but every scratch buffer lives
+ * in one fixed device array of SPAI_NOALLOC_SCRATCH_BYTES that each GPU
+ * loading this library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   A, P : device CSR (on_device = 1); P holds the float64 entries of the
+ *          left preconditioner (for instance spai_precond_export's output);
+ *          P == NULL solves unpreconditioned.
+ *   b, x : device float64 arrays of length n; x is output only.
+ *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * Returns SPAI_ERR_UNSUPPORTED when the problem (n, nonzeros, gmres_max_it,
+ * precisions) needs more than SPAI_NOALLOC_SCRATCH_BYTES, and the other
+ * codes as gmres_ir_solve.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps
+ * on the GPU (other threads or streams) race and must be serialised by the
+ * caller.  ir_stats' timing fields are left 0. */
+#define SPAI_NOALLOC_SCRATCH_BYTES (32u << 20)
+int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, const double* b, double* x,
+                           const ir_opts* opts, void* cuda_stream, ir_stats* st);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,8 @@ ERR_INVALID_ARG, ERR_ZERO_ROW, ERR_NONFINITE, ERR_NO_MEMORY = -1, -2, -3, -4
 ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND, ERR_INTERNAL = -5, -6, -7, -8, -9, -10
 
 EXPORTED = ("spai_ctx_create", "spai_ctx_destroy", "spai_build", "spai_precond_info", "spai_precond_export",
-            "spai_precond_free", "gmres_ir_solve", "solver_submit", "solver_poll", "spai_strerror")
+            "spai_precond_free", "gmres_ir_solve", "solver_submit", "solver_poll", "spai_strerror",
+            "gmres_ir_solve_noalloc")
 
 
 class spai_csr(C.Structure):
@@ -88,6 +89,8 @@ def lib():
             L.solver_submit.argtypes = [vp, C.POINTER(spai_csr), vp, C.POINTER(spai_opts), C.POINTER(ir_opts),
                                         C.POINTER(C.c_uint64)]
             L.solver_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(ir_stats)]
+            L.gmres_ir_solve_noalloc.argtypes = [C.POINTER(spai_csr), C.POINTER(spai_csr), vp, vp,
+                                                 C.POINTER(ir_opts), vp, C.POINTER(ir_stats)]
             L.spai_strerror.argtypes = [C.c_int]
             L.spai_strerror.restype = C.c_char_p
             _lib = L
@@ -253,4 +256,18 @@ def solver_poll(ctx: Context, ticket: int, x=None):
     if rc == PENDING:
         return None
     _check(rc, "solver_poll")
+    return _ir_dict(st, rc)
+
+
+def gmres_ir_solve_noalloc(A, b, x, P=None, opts: ir_opts | None = None, stream=None):
+    """Allocation-free refinement solve; A, P (CSR triples), b and x are CUDA tensors."""
+    csr = make_csr(A, on_device=True)
+    pcsr = make_csr(P, on_device=True) if P is not None else None
+    st = ir_stats()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib().gmres_ir_solve_noalloc(C.byref(csr), C.byref(pcsr) if pcsr is not None else None, _ptr(b),
+                                      _ptr(x), C.byref(opts), s, C.byref(st))
+    _check(rc, "gmres_ir_solve_noalloc")
     return _ir_dict(st, rc)

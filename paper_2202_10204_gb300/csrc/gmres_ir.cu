@@ -24,6 +24,7 @@
 #include <climits>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -889,4 +890,298 @@ done:
     if (ek1) cudaEventDestroy(ek1);
     if (rc < 0) cudaStreamSynchronize(s);
     return rc;
+}
+
+// ====================================================================
+// Allocation-free refinement solve (gmres_ir_solve_noalloc).
+//
+// For callers that must not allocate device memory: code running inside a
+// CUDA graph capture, callers that own their memory budget exactly, or
+// runtimes that forbid the CUDA allocator after start-up.  The refinement
+// scratch (SELL copies of A and P, the Krylov basis, the residual and
+// iterate, the exchange slots) lives in one file-scope device array of
+// SPAI_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
+// until exit.  Host code never passes the array's name to a kernel (on the
+// host it is only a stand-in symbol): its device address is looked up once
+// per device with cudaGetSymbolAddress, on the first call made on that
+// device.
+// ====================================================================
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SPAI_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_base[128] = {nullptr};
+
+int noalloc_base(int dev, unsigned char** out)
+{
+    if (dev < 0 || dev >= 128) return SPAI_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            spai_set_last_cuda_error(e);
+            return SPAI_ERR_CUDA;
+        }
+        g_noalloc_base[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_base[dev];
+    return 0;
+}
+
+// exclusive scan of ns counts into out[0..ns], one block
+__global__ void k_scan_one_block(int64_t ns, const int32_t* __restrict__ in, int64_t* __restrict__ out)
+{
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ns; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < ns ? in[i] : 0;
+        int64_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int64_t t = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < nw) wsum[lane] = t;
+        }
+        __syncthreads();
+        const int64_t pre = carry + (w > 0 ? wsum[w - 1] : 0) + x - v;
+        if (i < ns) out[i] = pre;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = pre + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[ns] = carry;
+}
+
+// x0 = P b in u_f with P's float64 values rounded to u_f on the fly
+template <class S, class TU>
+__global__ void k_x0_dbl(int64_t n, const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                         const double* __restrict__ pv, const double* __restrict__ b, TU* __restrict__ x)
+{
+    typedef typename Compute<S>::T C;
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+        C acc = C(0);
+        if (prp) {
+            for (int64_t q = prp[row]; q < prp[row + 1]; q++)
+                acc = fma(to_c(from_d<S>(pv[q])), to_c(from_d<S>(b[pci[q]])), acc);
+        } else {
+            acc = to_c(from_d<S>(b[row]));
+        }
+        x[row] = (TU)to_c(from_d<S>((double)acc));
+    }
+}
+
+struct Carve {
+    unsigned char* base;
+    size_t off, cap;
+    void* take(size_t bytes)
+    {
+        off = (off + 255) & ~size_t(255);
+        if (off + bytes > cap) return nullptr;
+        void* p = base + off;
+        off += bytes;
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, const double* b, double* xout,
+                                      const ir_opts* o, void* cuda_stream, ir_stats* st)
+{
+    if (!A || !b || !xout || !o) return SPAI_ERR_INVALID_ARG;
+    if (!A->on_device || (P && !P->on_device)) return SPAI_ERR_INVALID_ARG;
+    if (A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
+    if (P && (P->n != A->n || P->nnz < 0 || !P->rowptr || !P->col || !P->val)) return SPAI_ERR_INVALID_ARG;
+    if (A->n > INT32_MAX) return SPAI_ERR_UNSUPPORTED;
+    if (o->u != SPAI_SINGLE && o->u != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    if (o->ug != SPAI_SINGLE && o->ug != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    if (o->up != SPAI_SINGLE && o->up != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    if (o->ur != SPAI_DOUBLE && o->ur != SPAI_QUAD) return SPAI_ERR_UNSUPPORTED;
+    if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
+    if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
+    const int64_t n = A->n;
+    int kmax = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
+    if (kmax > n) kmax = (int)n;
+    if (kmax > KMAX_LIMIT) return SPAI_ERR_UNSUPPORTED;
+    if (kmax < 1) kmax = 1;
+    const int imax = o->ir_max_steps;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int device = 0, num_sms = 0;
+    SPAI_CUDA_TRY(cudaGetDevice(&device));
+    SPAI_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
+    unsigned char* base = nullptr;
+    int rc = noalloc_base(device, &base);
+    if (rc) return rc;
+
+    const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
+    const int64_t ldv = (n + 31) & ~int64_t(31);
+    const int64_t nsl = (n + 31) >> 5;
+    Carve cv{base, 0, (size_t)SPAI_NOALLOC_SCRATCH_BYTES};
+    const size_t msg_bytes = sizeof(unsigned long long) * 2 * MAX_GRID * 4;
+    const size_t ctrl_bytes = sizeof(int) * 4 + sizeof(int) * (imax + 1) + sizeof(double) * (imax + 1) +
+                              sizeof(unsigned long long) * 3 + 64;
+    unsigned long long* msg = (unsigned long long*)cv.take(msg_bytes);
+    unsigned char* ctrl = (unsigned char*)cv.take(ctrl_bytes);
+    void* x = cv.take((size_t)su * n);
+    void* r = cv.take((size_t)su * n);
+    void* wbuf = cv.take((size_t)sg * n);
+    void* tbuf = cv.take((size_t)sp * n);
+    void* V = cv.take((size_t)sg * ldv * (kmax + 1));
+    double* R = (double*)cv.take(sizeof(double) * (size_t)(kmax + 1) * kmax);
+    int64_t* aoff = (int64_t*)cv.take(sizeof(int64_t) * (nsl + 1));
+    int32_t* aw = (int32_t*)cv.take(sizeof(int32_t) * nsl);
+    int64_t* poff = P ? (int64_t*)cv.take(sizeof(int64_t) * (nsl + 1)) : nullptr;
+    int32_t* pw = P ? (int32_t*)cv.take(sizeof(int32_t) * nsl) : nullptr;
+    if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)))
+        return SPAI_ERR_UNSUPPORTED;  // the problem does not fit the fixed scratch
+    int* err = (int*)ctrl;
+    int* outv = err + 2;
+    int* its = outv + 2;
+    double* nbe = (double*)(((uintptr_t)(its + imax + 1) + 7) & ~uintptr_t(7));
+    unsigned long long* norms = (unsigned long long*)(nbe + imax + 1);
+    // the array keeps the previous call's contents: clear what must start at zero
+    SPAI_CUDA_TRY(cudaMemsetAsync(msg, 0, msg_bytes, s));
+    SPAI_CUDA_TRY(cudaMemsetAsync(ctrl, 0, ctrl_bytes, s));
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
+    const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((nsl * 32 + tb - 1) / tb, (int64_t)num_sms * 16));
+    int nl = 0;
+    k_sell_width<<<gs, tb, 0, s>>>(n, A->rowptr, aw);
+    k_scan_one_block<<<1, 1024, 0, s>>>(nsl, aw, aoff);
+    nl += 2;
+    if (P) {
+        k_sell_width<<<gs, tb, 0, s>>>(n, P->rowptr, pw);
+        k_scan_one_block<<<1, 1024, 0, s>>>(nsl, pw, poff);
+        nl += 2;
+    }
+    int64_t tot[2] = {0, 0};
+    SPAI_CUDA_TRY(cudaMemcpyAsync(&tot[0], aoff + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (P) SPAI_CUDA_TRY(cudaMemcpyAsync(&tot[1], poff + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA_TRY(cudaStreamSynchronize(s));
+    int32_t* acol = (int32_t*)cv.take(sizeof(int32_t) * std::max<int64_t>(tot[0], 1));
+    void* aval = cv.take((size_t)sp * std::max<int64_t>(tot[0], 1));
+    int32_t* pcol = P ? (int32_t*)cv.take(sizeof(int32_t) * std::max<int64_t>(tot[1], 1)) : nullptr;
+    void* pval = P ? cv.take((size_t)sp * std::max<int64_t>(tot[1], 1)) : nullptr;
+    if (!acol || !aval || (P && (!pcol || !pval))) return SPAI_ERR_UNSUPPORTED;
+    if (o->up == SPAI_SINGLE) {
+        k_sell_fill<float><<<gs, tb, 0, s>>>(n, A->rowptr, A->col, A->val, aoff, acol, (float*)aval);
+        if (P) k_sell_fill<float><<<gs, tb, 0, s>>>(n, P->rowptr, P->col, P->val, poff, pcol, (float*)pval);
+    } else {
+        k_sell_fill<double><<<gs, tb, 0, s>>>(n, A->rowptr, A->col, A->val, aoff, acol, (double*)aval);
+        if (P) k_sell_fill<double><<<gs, tb, 0, s>>>(n, P->rowptr, P->col, P->val, poff, pcol, (double*)pval);
+    }
+    nl += P ? 2 : 1;
+    k_norms<<<gb, tb, 0, s>>>(n, A->rowptr, A->val, b, norms);
+    nl++;
+    {
+        const int64_t* prp = P ? P->rowptr : nullptr;
+        const int32_t* pci = P ? P->col : nullptr;
+        const double* pvd = P ? P->val : nullptr;
+#define X0D(S, TU) k_x0_dbl<S, TU><<<gb, tb, 0, s>>>(n, prp, pci, pvd, b, (TU*)x)
+        if (o->u == SPAI_SINGLE) {
+            if (o->uf == SPAI_HALF) X0D(__half, float);
+            else if (o->uf == SPAI_SINGLE) X0D(float, float);
+            else X0D(double, float);
+        } else {
+            if (o->uf == SPAI_HALF) X0D(__half, double);
+            else if (o->uf == SPAI_SINGLE) X0D(float, double);
+            else X0D(double, double);
+        }
+#undef X0D
+        nl++;
+    }
+    SPAI_CUDA_TRY(cudaGetLastError());
+    unsigned long long h_norms[3] = {0, 0, 0};
+    SPAI_CUDA_TRY(cudaMemcpyAsync(h_norms, norms, sizeof(h_norms), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA_TRY(cudaStreamSynchronize(s));
+    IrArgs a;
+    memset(&a, 0, sizeof(a));
+    double anorm, bnorm;
+    {
+        long long t0 = (long long)h_norms[0], t1 = (long long)h_norms[1];
+        memcpy(&anorm, &t0, 8);
+        memcpy(&bnorm, &t1, 8);
+    }
+    const int q = (int)h_norms[2];
+    const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    a.n = n;
+    a.A.off = aoff; a.A.col = acol; a.A.val = aval;
+    if (P) { a.P.off = poff; a.P.col = pcol; a.P.val = pval; }
+    a.arp = A->rowptr; a.aci = A->col; a.aval = A->val;
+    a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
+    a.err = err;
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, device);
+    if (clk_khz <= 0) clk_khz = 2000000;
+    a.limit = (long long)clk_khz * 1000LL * 4;
+    a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
+    a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
+    a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
+    a.its = its; a.nbe = nbe; a.out = outv;
+    const int rm = o->ur == SPAI_QUAD ? 2 : 1;
+    int grid = 0;
+    if (o->u == SPAI_DOUBLE) {
+        if (o->ug == SPAI_DOUBLE) {
+            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<double, double, double>(a, rm, num_sms, s, &grid);
+            else rc = launch_ir_rm<double, double, float>(a, rm, num_sms, s, &grid);
+        } else {
+            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<double, float, double>(a, rm, num_sms, s, &grid);
+            else rc = launch_ir_rm<double, float, float>(a, rm, num_sms, s, &grid);
+        }
+    } else {
+        if (o->ug == SPAI_DOUBLE) {
+            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<float, double, double>(a, rm, num_sms, s, &grid);
+            else rc = launch_ir_rm<float, double, float>(a, rm, num_sms, s, &grid);
+        } else {
+            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<float, float, double>(a, rm, num_sms, s, &grid);
+            else rc = launch_ir_rm<float, float, float>(a, rm, num_sms, s, &grid);
+        }
+    }
+    if (rc) return rc;
+    nl++;
+    if (o->u == SPAI_SINGLE) k_to_double<float><<<gb, tb, 0, s>>>(n, (const float*)x, xout);
+    else k_to_double<double><<<gb, tb, 0, s>>>(n, (const double*)x, xout);
+    nl++;
+    SPAI_CUDA_TRY(cudaGetLastError());
+    int h_out[2] = {0, 0}, h_err = 0;
+    SPAI_CUDA_TRY(cudaMemcpyAsync(h_out, outv, sizeof(h_out), cudaMemcpyDeviceToHost, s));
+    SPAI_CUDA_TRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (st) {
+        memset(st, 0, sizeof(*st));
+        SPAI_CUDA_TRY(cudaMemcpyAsync(st->its, its, sizeof(int) * imax, cudaMemcpyDeviceToHost, s));
+        SPAI_CUDA_TRY(cudaMemcpyAsync(st->nbe, nbe, sizeof(double) * (imax + 1), cudaMemcpyDeviceToHost, s));
+    }
+    SPAI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err) return h_err;
+    if (st) {
+        st->steps = h_out[0];
+        st->flags = h_out[1];
+        for (int i = 0; i < st->steps; i++) st->total_its += st->its[i];
+        for (int i = st->steps + 1; i <= SPAI_IR_MAX_STEPS; i++) st->nbe[i] = 0.0;
+        st->final_nbe = st->nbe[st->steps];
+        st->launches = nl;
+        st->grid = grid;
+        st->nnz_P = P ? P->nnz : 0;
+    }
+    if (h_out[1] & 8) return SPAI_ERR_NONFINITE;
+    if (!(h_out[1] & 1) && o->stop == IR_STOP_BACKWARD) return SPAI_WARN_NOT_CONVERGED;
+    return 0;
 }
