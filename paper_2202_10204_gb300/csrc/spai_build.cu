@@ -144,7 +144,8 @@ __global__ void k_scan_chunks(int64_t n, const int32_t* __restrict__ in, const i
 
 int scan_counts(int64_t n, const int32_t* in, int64_t* out, cudaStream_t s)
 {
-    const int64_t chunk = 1 << 16;
+    // chunks of 4096 counts: one 1024-thread block scans a chunk in 4 passes
+    const int64_t chunk = 4096;
     int nb = (int)((n + chunk - 1) / chunk);
     if (nb < 1) nb = 1;
     int64_t* sums = nullptr;
@@ -152,7 +153,7 @@ int scan_counts(int64_t n, const int32_t* in, int64_t* out, cudaStream_t s)
     if (rc) return rc;
     k_block_sums<<<nb, 256, 0, s>>>(n, in, sums, chunk);
     k_scan_sums<<<1, 32, 0, s>>>(nb, sums);
-    k_scan_chunks<<<nb, 256, 0, s>>>(n, in, sums, out, chunk);
+    k_scan_chunks<<<nb, 1024, 0, s>>>(n, in, sums, out, chunk);
     dev_free(sums, s);
     SPAI_CUDA_TRY(cudaGetLastError());
     return 0;
