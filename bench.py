@@ -169,6 +169,22 @@ def ir_kernel_bytes(n, nnz_a, nnz_p, its, s_u=4, s_g=4, s_p=4):
     return total
 
 
+# ---------------------------------------------------------------- multi-rank aggregation
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """Largest value over all ranks (the slowest rank's time); identity at N = 1."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, max_ms):
+    """Whole-job solves/s: every rank solves `steps` systems; time is the slowest rank's."""
+    return world * steps / (max_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def main():
@@ -230,12 +246,10 @@ def main():
         torch.cuda.synchronize()
     per = [e0.elapsed_time(e1) for e0, e1 in ev]
     tot_ms = float(sum(per))
-    t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
     if world > 1:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tot_max = float(t.item())
-    value = world * args.steps / (tot_max / 1000.0)
+    tot_max = max_over_ranks(tot_ms, dist if world > 1 else None, dev)
+    value = job_throughput(world, args.steps, tot_max)
 
     # correctness of the timed solves (the metric counts solves meeting the accuracy bar)
     x = xd.cpu().numpy()
@@ -276,11 +290,9 @@ def main():
             S.gmres_ir_solve(ctx, Ah, bh, xh, sopts=so, opts=io)
         e1.record(stream)
         torch.cuda.synchronize()
-        te = torch.tensor([e0.elapsed_time(e1)], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        te = max_over_ranks(e0.elapsed_time(e1), dist if world > 1 else None, dev)
         h2d = sum(a.numel() * a.element_size() for a in Ah) + bh.numel() * 8
-        e2e = dict(value=world * ke / (float(te.item()) / 1000.0), unit=UNIT, h2d_bytes_per_step=int(h2d),
+        e2e = dict(value=job_throughput(world, ke, te), unit=UNIT, h2d_bytes_per_step=int(h2d),
                    d2h_bytes_per_step=int(n * 8 + 4 * 2), steps=ke)
 
     cpu = None

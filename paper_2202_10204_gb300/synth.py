@@ -100,11 +100,16 @@ def random_sparse(n: int, nnz_per_col: int = 16, seed: int = 6, shift: float | N
     k = nnz_per_col - 1
     if shift is None:
         shift = 2.0 * np.sqrt(max(k, 1))
-    rows = np.empty((n, k), dtype=np.int64)
-    for j in range(n):
-        r = rng.choice(n - 1, size=k, replace=False)
-        r[r >= j] += 1  # skip the diagonal
-        rows[j] = r
+    # k distinct off-diagonal rows per column: draw, then redraw the columns
+    # that got a repeat until none is left
+    rows = rng.integers(0, n - 1, size=(n, k), dtype=np.int64)
+    while True:
+        srt = np.sort(rows, axis=1)
+        bad = np.nonzero(np.any(srt[:, 1:] == srt[:, :-1], axis=1))[0]
+        if len(bad) == 0:
+            break
+        rows[bad] = rng.integers(0, n - 1, size=(len(bad), k), dtype=np.int64)
+    rows[rows >= np.arange(n)[:, None]] += 1  # skip the diagonal
     colsj = np.repeat(np.arange(n), k)
     vals = rng.normal(0.0, 1.0, size=n * k)
     dg = rng.normal(0.0, 1.0, size=n)

@@ -1,0 +1,191 @@
+"""GPU parity at full workload sizes (sampled against the oracle) and the
+serving queue.
+
+* The 64^3 bench workload, in the launch configuration bench.py times:
+  the pattern of every column is checked against pattern(A^2) with the cap
+  (from scipy), a seeded sample of columns against the oracle's own column
+  computation, and the refinement against properties that hold at any size
+  (backward error at the stop tolerance, bounded steps).
+* An adaptive (Grote-Huckle) build on a 100,000-column random nonsymmetric
+  matrix, 16 nonzeros per column, condition raised by row/column scaling:
+  sampled columns against the oracle.
+* Serving: requests of different sizes and precisions submitted together
+  give bitwise the same solution as the same request solved alone.
+"""
+import time
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_2202_10204_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2202_10204_gb300 as S  # noqa: E402
+
+RES_TOL = {"half": 1e-3, "single": 1e-6, "double": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = S.Context(0, stream=torch.cuda.current_stream())
+    yield c
+    c.close()
+
+
+def col_residuals(A, d, cols, J_list, m_list):
+    """float64 ||B(:,J_k) m_k - e_k|| and || |B(:,J_k)| |m_k| || for the sampled columns."""
+    Ms = synth.to_scipy(A)
+    n = Ms.shape[0]
+    B = (Ms.T @ sp.diags(d)).tocsc()
+    res, absbm = [], []
+    for k, J, m in zip(cols, J_list, m_list):
+        BJ = B[:, J]
+        r = BJ @ m
+        r[k] -= 1.0
+        res.append(np.linalg.norm(r))
+        absbm.append(np.linalg.norm(abs(BJ) @ np.abs(m)))
+    return np.array(res), np.array(absbm)
+
+
+def check_sampled_columns(A, P_csr, ref, cols, uf, allow_mismatch=0.0):
+    rp, ci, va = P_csr
+    d = ref["d"]
+    same, Jg, mg, Jo, mo = [], [], [], [], []
+    for k in cols:
+        J = ci[rp[k]:rp[k + 1]]
+        Jr = ref["Jidx"][k][: ref["Jcnt"][k]]
+        same.append(np.array_equal(J, Jr))
+        Jg.append(J); mg.append(va[rp[k]:rp[k + 1]] / d[J])
+        Jo.append(Jr); mo.append(ref["mbar"][k][: ref["Jcnt"][k]])
+    same = np.array(same)
+    assert same.mean() >= 1.0 - allow_mismatch, same.mean()
+    cols = np.asarray(cols)
+    rg, ag = col_residuals(A, d, cols, Jg, mg)
+    ro, _ = col_residuals(A, d, cols, Jo, mo)
+    u = O.UNIT_ROUNDOFF[O.prec(uf)]
+    diff = np.abs(rg - ro)[same]
+    bound = RES_TOL[uf] * ro[same] + (4 * u + 64 * 2.0 ** -53) * ag[same]
+    assert np.all(diff <= bound), np.max(diff - bound)
+    assert np.mean(diff <= RES_TOL[uf] * ro[same]) >= 0.99
+
+
+def test_bench_workload_full_size(ctx):
+    A, b, x_true = synth.cfg_large_3d(N=64)
+    n = len(A[0]) - 1
+    Ad = tuple(torch.from_numpy(a).cuda() for a in A)
+    so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3)
+    P, st = S.spai_build(ctx, Ad, so, per_column=True)
+    Pc = P.export()
+    # every column's pattern: column k of pattern(A^2), at most 25 (interior columns have exactly 25)
+    Ms = synth.to_scipy(A)
+    A2 = (abs(Ms) @ abs(Ms)).tocsc()
+    A2.sort_indices()
+    assert np.array_equal(np.diff(Pc[0]), np.diff(A2.indptr))
+    assert np.array_equal(Pc[1], A2.indices)
+    assert st["max_I"] == 63 and st["max_J"] == 25
+    # sampled columns against the oracle
+    cols = np.sort(np.random.default_rng(7).choice(n, size=384, replace=False))
+    cols = np.unique(np.concatenate([cols, [0, 1, n // 2, n - 1]]))
+    ref = O.spai(A, init=O.PAT_A2, max_fill=25, uf="half", eps=0.3, cols=cols)
+    check_sampled_columns(A, Pc, ref, cols, "half")
+    assert np.array_equal(st["nI"][cols], ref["Icnt"][cols])
+    # the refinement: stops at the backward-error tolerance within i_max
+    io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    r = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io)
+    x = xd.cpu().numpy()
+    assert r["flags"] & 1 and 1 <= r["steps"] <= 10
+    q = 7
+    nbe = np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b)))
+    assert nbe <= q * 2.0 ** -24
+    assert abs(r["final_nbe"] - nbe) <= 0.5 * nbe  # the kernel's own estimate (single-precision iterate)
+    assert np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)) < 1e-4
+    P.free()
+
+
+def test_adaptive_100k_sampled(ctx):
+    A = synth.random_sparse(100_000, 16, seed=6, log10_scale=6.0)
+    n = len(A[0]) - 1
+    so = S.make_spai_opts(init=0, adaptive=True, eps=0.5, beta=8, max_fill=30, uf="single")
+    t0 = time.time()
+    P, st = S.spai_build(ctx, A, so, per_column=True)
+    assert time.time() - t0 < 120
+    Pc = P.export()
+    cols = np.sort(np.random.default_rng(11).choice(n, size=48, replace=False))
+    ref = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=0.5, beta=8, max_fill=30, uf="single", cols=cols)
+    # near-ties of rho may select differently on a small fraction of columns
+    check_sampled_columns(A, Pc, ref, cols, "single", allow_mismatch=0.05)
+    conv = (st["flags"][cols] & 1) != 0
+    assert np.mean(conv == ((ref["flags"][cols] & 1) != 0)) >= 0.95
+    P.free()
+
+
+def _requests():
+    reqs = []
+    A, b, _ = synth.cfg_small_2d()
+    reqs.append((A, b, S.make_spai_opts(init=1, max_fill=30, uf="single"),
+                 S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)))
+    for N, seed in ((12, 3), (16, 5), (20, 9)):
+        A3 = synth.conv_diff_3d(N, 50.0, seed=seed)
+        b3, _ = synth.rhs(A3, seed=seed + 1)
+        reqs.append((A3, b3, S.make_spai_opts(init=2, max_fill=25, uf="half"),
+                     S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4)))
+    Ar = synth.random_sparse(3000, 8, seed=4, log10_scale=2.0)
+    br, _ = synth.rhs(Ar, seed=1)
+    reqs.append((Ar, br, S.make_spai_opts(init=0, adaptive=True, eps=0.4, max_fill=20, uf="single"),
+                 S.make_ir_opts(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4)))
+    A2, b2, _ = synth.cfg_small_2d(seed_mat=5, seed_rhs=6)
+    reqs.append((A2, b2, None, S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="double",
+                                              tau=1e-8)))
+    return reqs
+
+
+def test_serving_mix_matches_standalone():
+    reqs = _requests()
+    alone = []
+    c1 = S.Context(0)
+    for A, b, so, io in reqs:
+        x = np.zeros_like(b)
+        st = S.gmres_ir_solve(c1, A, b, x, sopts=so, opts=io)
+        alone.append((x, st))
+    c1.close()
+    c2 = S.Context(0, hbm_budget=8 << 30)
+    tickets = [S.solver_submit(c2, A, b, so, io) for (A, b, so, io) in reqs]
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets):
+        assert time.time() - t0 < 300
+        for i, t in enumerate(tickets):
+            if i in results:
+                continue
+            x = np.zeros_like(reqs[i][1])
+            st = S.solver_poll(c2, t, x)
+            if st is not None:
+                results[i] = (x, st)
+        time.sleep(0.01)
+    for i in range(len(reqs)):
+        xa, sa = alone[i]
+        xm, sm = results[i]
+        assert sm["steps"] == sa["steps"] and sm["its"] == sa["its"], i
+        assert np.array_equal(xm, xa), i  # deterministic kernels: the same bits alone and in the mix
+    c2.close()
+
+
+def test_serving_admission_budget():
+    A, b, _ = synth.cfg_small_2d()
+    c = S.Context(0, hbm_budget=1 << 20)
+    with pytest.raises(S.SpaiError) as e:
+        S.solver_submit(c, A, b, S.make_spai_opts(init=1), S.make_ir_opts())
+    assert e.value.code == -5
+    with pytest.raises(S.SpaiError) as e:
+        S.solver_poll(c, 12345)
+    assert e.value.code == -9
+    c.close()
