@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
     IrShared* sh = &shs;
     const int kmax = a.kmax;
     const int tid = threadIdx.x, BT = blockDim.x;
+    const int GT = BT > 32 ? 32 : 0;  // the Givens thread: lane 0 of warp 1 (warp 0 polls)
     const int64_t r0 = (int64_t)blockIdx.x * a.rb;
     const int64_t r1 = min(a.n, r0 + a.rb);
     const int nsl = (int)((a.rb + 31) >> 5);
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
         int k = 0;
         if (beta > TG(0)) {
             for (int64_t row = r0 + tid; row < r1; row += BT) V[row] = ws[row - r0] / beta;
-            if (tid == 0) g[0] = (double)beta;
+            if (tid == GT) g[0] = (double)beta;
             TG hdiv = beta;
             bool done = false;
             for (int j = 0; j < kmax && !done; j++) {
@@ -440,7 +441,17 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
                     }
                     TG h;
                     if (!xsum<false>(a, sh, redg, part, h)) return;
-                    if (tid == 0) hc[i] = (double)h;
+                    if (tid == GT) {
+                        // Givens, pipelined with the rounds: rotation i-1 needs h_i
+                        hc[i] = (double)h;
+                        if (i >= 1) {
+                            const int q = i - 1;
+                            const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
+                            hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
+                            hc[q] = t0;
+                            if (blockIdx.x == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
+                        }
+                    }
                     const TG* Vi = V + (int64_t)i * a.ldv;
                     part = TG(0);
                     if (i < j) {
@@ -486,14 +497,10 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
                     TG* Vn = V + (int64_t)(j + 1) * a.ldv;
                     for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ws[row - r0] / hn;
                 }
-                // ---- Givens rotations in double (identical in every block)
-                if (tid == 0) {
+                // ---- the new Givens rotation in double (identical in every block);
+                // rotations 0..j-1 were applied to this column during the rounds
+                if (tid == GT) {
                     hc[j + 1] = (double)hn;
-                    for (int i = 0; i < j; i++) {
-                        double t0 = cs[i] * hc[i] + sn[i] * hc[i + 1];
-                        hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
-                        hc[i] = t0;
-                    }
                     double dn = sqrt(hc[j] * hc[j] + hc[j + 1] * hc[j + 1]);
                     if (dn == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
                     else { cs[j] = hc[j] / dn; sn[j] = hc[j + 1] / dn; }
@@ -501,8 +508,7 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
                     g[j + 1] = -sn[j] * g[j];
                     g[j] = cs[j] * g[j];
                     sh->resid = fabs(g[j + 1]) / (double)beta;
-                    if (blockIdx.x == 0)
-                        for (int i = 0; i <= j; i++) a.R[(size_t)j * (kmax + 1) + i] = hc[i];
+                    if (blockIdx.x == 0) a.R[(size_t)j * (kmax + 1) + j] = hc[j];
                 }
                 __syncthreads();
                 k = j + 1;
@@ -823,23 +829,25 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         a.its = its; a.nbe = nbe; a.out = outv;
         const int rm = o->ur == SPAI_QUAD ? 2 : 1;
         CTRY(cudaEventRecord(ek0, s));
+#define LAUNCH(TU, TG, TP) TRY((launch_ir_rm<TU, TG, TP>(a, rm, num_sms, s, &grid)))
         if (o->u == SPAI_DOUBLE) {
             if (o->ug == SPAI_DOUBLE) {
-                if (o->up == SPAI_DOUBLE) TRY((launch_ir_rm<double, double, double>(a, rm, num_sms, s, &grid)));
-                else TRY((launch_ir_rm<double, double, float>(a, rm, num_sms, s, &grid)));
+                if (o->up == SPAI_DOUBLE) LAUNCH(double, double, double);
+                else LAUNCH(double, double, float);
             } else {
-                if (o->up == SPAI_DOUBLE) TRY((launch_ir_rm<double, float, double>(a, rm, num_sms, s, &grid)));
-                else TRY((launch_ir_rm<double, float, float>(a, rm, num_sms, s, &grid)));
+                if (o->up == SPAI_DOUBLE) LAUNCH(double, float, double);
+                else LAUNCH(double, float, float);
             }
         } else {
             if (o->ug == SPAI_DOUBLE) {
-                if (o->up == SPAI_DOUBLE) TRY((launch_ir_rm<float, double, double>(a, rm, num_sms, s, &grid)));
-                else TRY((launch_ir_rm<float, double, float>(a, rm, num_sms, s, &grid)));
+                if (o->up == SPAI_DOUBLE) LAUNCH(float, double, double);
+                else LAUNCH(float, double, float);
             } else {
-                if (o->up == SPAI_DOUBLE) TRY((launch_ir_rm<float, float, double>(a, rm, num_sms, s, &grid)));
-                else TRY((launch_ir_rm<float, float, float>(a, rm, num_sms, s, &grid)));
+                if (o->up == SPAI_DOUBLE) LAUNCH(float, float, double);
+                else LAUNCH(float, float, float);
             }
         }
+#undef LAUNCH
     }
     CTRY(cudaEventRecord(ek1, s));
     nl++;
