@@ -102,6 +102,10 @@ typedef struct {
     int ir_max_steps;            /* i_max (1..64)                                      */
     ir_stop_rule stop;
     double stop_tol;             /* <= 0: q*u, q the largest row nonzero count of A    */
+    int orth;                    /* Arnoldi orthogonalisation: 0 modified Gram-Schmidt (the
+                                    paper's MGS-GMRES), 1 classical Gram-Schmidt applied
+                                    twice (CGS2: two vector reductions per iteration instead
+                                    of j+1 scalar ones) */
 } ir_opts;
 
 #define SPAI_IR_MAX_STEPS 64

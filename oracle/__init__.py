@@ -54,13 +54,13 @@ class SpaiOpts(C.Structure):
 
 
 class GmresOpts(C.Structure):
-    _fields_ = [("ug", C.c_int), ("up", C.c_int), ("tau", C.c_double), ("maxit", C.c_int)]
+    _fields_ = [("ug", C.c_int), ("up", C.c_int), ("tau", C.c_double), ("maxit", C.c_int), ("orth", C.c_int)]
 
 
 class IrOpts(C.Structure):
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int),
                 ("ur", C.c_int), ("mode", C.c_int), ("tau", C.c_double),
-                ("gmres_maxit", C.c_int), ("imax", C.c_int), ("stop_tol", C.c_double)]
+                ("gmres_maxit", C.c_int), ("imax", C.c_int), ("stop_tol", C.c_double), ("orth", C.c_int)]
 
 
 def lib():
@@ -221,15 +221,18 @@ def residual(A, b, x, ur="double", u="double"):
     return r
 
 
-def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None):
-    """One left-preconditioned MGS-GMRES solve of (P A) d = P r from d = 0."""
+ORTH_MGS, ORTH_CGS2 = 0, 1
+
+
+def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORTH_MGS):
+    """One left-preconditioned GMRES solve of (P A) d = P r from d = 0 (MGS or CGS2)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     r = np.ascontiguousarray(r, dtype=np.float64)
     d = np.zeros(n)
     bd = C.c_int(0)
     rr = C.c_double(0.0)
-    o = GmresOpts(prec(ug), prec(up), float(tau), int(maxit if maxit is not None else min(n, 500)))
+    o = GmresOpts(prec(ug), prec(up), float(tau), int(maxit if maxit is not None else min(n, 500)), int(orth))
     if P is None:
         pp = (None, None, None)
     else:
@@ -248,7 +251,7 @@ def default_stop_tol(A, u) -> float:
 
 
 def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur="quad",
-             tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32):
+             tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32, orth=ORTH_MGS):
     """SPAI-GMRES-IR (Algorithm 3) given P = (rowptr, col, val_up, val_uf) or None."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
@@ -256,7 +259,7 @@ def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur
     if stop_tol is None:
         stop_tol = default_stop_tol(A, u)
     o = IrOpts(prec(uf), prec(u), prec(ug), prec(up), prec(ur), int(mode), float(tau),
-               int(gmres_maxit if gmres_maxit is not None else min(n, 500)), int(imax), float(stop_tol))
+               int(gmres_maxit if gmres_maxit is not None else min(n, 500)), int(imax), float(stop_tol), int(orth))
     x = np.zeros(n)
     its = np.zeros(imax + 1, dtype=np.int32)
     nbe = np.full(imax + 1, np.nan)
@@ -276,3 +279,21 @@ def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur
     s = steps.value
     return dict(x=x, steps=s, its=its[:s].copy(), nbe=nbe[:s + 1].copy(), status=status,
                 total_its=int(its[:s].sum()))
+
+
+def arnoldi(A, r, P=None, k=10, ug="double", up="double", orth=ORTH_MGS):
+    """k Arnoldi steps on (P A); returns (V n x (m), H (k+1) x k) with m columns produced."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    V = np.zeros((k + 1, n))
+    H = np.zeros((k, k + 1))
+    if P is None:
+        pp = (None, None, None)
+    else:
+        prp, pci, pva = _csr(P)
+        pp = (_p(prp, C.c_int64), _p(pci, C.c_int32), _p(pva, C.c_double))
+    m = lib().orc_arnoldi(C.c_int(n), _p(rp, C.c_int64), _p(ci, C.c_int32), _p(va, C.c_double), pp[0], pp[1],
+                          pp[2], _p(r, C.c_double), C.c_int(prec(ug)), C.c_int(prec(up)), C.c_int(int(orth)),
+                          C.c_int(k), _p(V, C.c_double), _p(H, C.c_double))
+    return V[:m].T.copy(), H.T.copy()

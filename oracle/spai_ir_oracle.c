@@ -46,7 +46,8 @@
  *   R6  |J_k| <= max_fill; an initial pattern larger than the cap keeps k,
  *       then the indices nearest to k (ties: smaller index).
  *   R7  MGS-GMRES, x0 = 0, no restart, stop when |g_{j+1}| / beta <= tau;
- *       Givens rotations, H, g and y in double.
+ *       Givens rotations, H, g and y in double.  Option: classical
+ *       Gram-Schmidt applied twice (CGS2) instead of MGS.
  *   R8  IR stop: before step i, nbe_i = ||r_i||_inf / (||A||_inf ||x_i||_inf
  *       + ||b||_inf) <= stop_tol; at most i_max GMRES solves.
  *   R10 pattern(A) / pattern(A^2) initial patterns: J_k = nonzero rows of
@@ -561,6 +562,8 @@ typedef struct {
     int ug, up;      /* GMRES working precision, product precision */
     double tau;      /* relative tolerance on the preconditioned residual */
     int maxit;       /* iteration cap */
+    int orth;        /* 0: modified Gram-Schmidt (the paper's MGS-GMRES);
+                        1: classical Gram-Schmidt applied twice (CGS2) */
 } orc_gmres_opts;
 
 /*
@@ -602,12 +605,28 @@ int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
         if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
         else for (int i = 0; i < n; i++) w[i] = t[i];
         for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
-        /* modified Gram-Schmidt in u_g */
         double* h = (double*)calloc((size_t)j + 2, sizeof(double));
-        for (int i = 0; i <= j; i++) {
-            double hij = dot_p(V[i], 1, w, 1, n, ug, MODE_PEROP);
-            h[i] = hij;
-            for (int q = 0; q < n; q++) w[q] = rnd(w[q] - rnd(hij * V[i][q], ug), ug);
+        if (o->orth == 0) {
+            /* modified Gram-Schmidt in u_g: project against v_i one at a time */
+            for (int i = 0; i <= j; i++) {
+                double hij = dot_p(V[i], 1, w, 1, n, ug, MODE_PEROP);
+                h[i] = hij;
+                for (int q = 0; q < n; q++) w[q] = rnd(w[q] - rnd(hij * V[i][q], ug), ug);
+            }
+        } else {
+            /* classical Gram-Schmidt twice in u_g: all projections of a pass
+             * use the same w; the second pass re-orthogonalises */
+            double* c = (double*)calloc((size_t)j + 2, sizeof(double));
+            for (int pass = 0; pass < 2; pass++) {
+                for (int i = 0; i <= j; i++) c[i] = dot_p(V[i], 1, w, 1, n, ug, MODE_PEROP);
+                for (int q = 0; q < n; q++) {
+                    double acc = w[q];
+                    for (int i = 0; i <= j; i++) acc = rnd(acc - rnd(c[i] * V[i][q], ug), ug);
+                    w[q] = acc;
+                }
+                for (int i = 0; i <= j; i++) h[i] = rnd(h[i] + c[i], ug);
+            }
+            free(c);
         }
         h[j + 1] = rnd(sqrt(dot_p(w, 1, w, 1, n, ug, MODE_PEROP)), ug);
         double hnext = h[j + 1];
@@ -661,6 +680,7 @@ typedef struct {
     int gmres_maxit;        /* per GMRES solve */
     int imax;               /* maximum number of refinement steps */
     double stop_tol;        /* R8 backward-error threshold */
+    int orth;               /* 0 MGS, 1 CGS2 */
 } orc_ir_opts;
 
 /*
@@ -690,7 +710,7 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
     if (prp) spmv_p(n, prp, pci, pv_uf, b, o->uf, o->mode, x);
     else for (int i = 0; i < n; i++) x[i] = rnd(b[i], o->uf);
     for (int i = 0; i < n; i++) x[i] = rnd(x[i], o->u);
-    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit };
+    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit, o->orth };
     int i;
     *steps = 0;
     for (i = 0; i <= o->imax; i++) {
@@ -741,4 +761,56 @@ void orc_half_ops(int cnt, const double* a, const double* b, int op, double* out
         }
         out[i] = orc_chop_half(z);
     }
+}
+
+/* Arnoldi only (for the oracle's pins): k steps of the Gram-Schmidt variant
+ * on (P A) from v_1 = P r / ||P r||, in u_g / u_p.  Writes V (n x (k+1),
+ * column-major) and H ((k+1) x k, column-major, unrotated).  Returns the
+ * number of columns produced (less than k+1 on breakdown). */
+int orc_arnoldi(int n, const int64_t* arp, const int* aci, const double* av,
+                const int64_t* prp, const int* pci, const double* pv,
+                const double* r, int ug, int up, int orth, int k, double* Vout, double* Hout)
+{
+    double* t = (double*)malloc(sizeof(double) * (size_t)n);
+    double* w = (double*)malloc(sizeof(double) * (size_t)n);
+    double* c = (double*)malloc(sizeof(double) * (size_t)(k + 2));
+    if (prp) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, w);
+    else for (int i = 0; i < n; i++) w[i] = rnd(r[i], up);
+    for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
+    double beta = rnd(sqrt(dot_p(w, 1, w, 1, n, ug, MODE_PEROP)), ug);
+    int cols = 1;
+    for (int i = 0; i < n; i++) Vout[i] = rnd(w[i] / beta, ug);
+    for (int z = 0; z < (k + 1) * k; z++) Hout[z] = 0.0;
+    for (int j = 0; j < k; j++) {
+        const double* vj = Vout + (size_t)j * n;
+        spmv_p(n, arp, aci, av, vj, up, MODE_PEROP, t);
+        if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
+        else for (int i = 0; i < n; i++) w[i] = t[i];
+        for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
+        double* h = Hout + (size_t)j * (k + 1);
+        if (orth == 0) {
+            for (int i = 0; i <= j; i++) {
+                double hij = dot_p(Vout + (size_t)i * n, 1, w, 1, n, ug, MODE_PEROP);
+                h[i] = hij;
+                for (int q = 0; q < n; q++) w[q] = rnd(w[q] - rnd(hij * Vout[(size_t)i * n + q], ug), ug);
+            }
+        } else {
+            for (int pass = 0; pass < 2; pass++) {
+                for (int i = 0; i <= j; i++) c[i] = dot_p(Vout + (size_t)i * n, 1, w, 1, n, ug, MODE_PEROP);
+                for (int q = 0; q < n; q++) {
+                    double acc = w[q];
+                    for (int i = 0; i <= j; i++) acc = rnd(acc - rnd(c[i] * Vout[(size_t)i * n + q], ug), ug);
+                    w[q] = acc;
+                }
+                for (int i = 0; i <= j; i++) h[i] = rnd(h[i] + c[i], ug);
+            }
+        }
+        double hn = rnd(sqrt(dot_p(w, 1, w, 1, n, ug, MODE_PEROP)), ug);
+        h[j + 1] = hn;
+        if (hn == 0.0) break;
+        for (int i = 0; i < n; i++) Vout[(size_t)(j + 1) * n + i] = rnd(w[i] / hn, ug);
+        cols = j + 2;
+    }
+    free(t); free(w); free(c);
+    return cols;
 }

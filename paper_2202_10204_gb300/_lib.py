@@ -44,7 +44,7 @@ class spai_opts(C.Structure):
 class ir_opts(C.Structure):
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int), ("ur", C.c_int),
                 ("tau", C.c_double), ("gmres_max_it", C.c_int), ("ir_max_steps", C.c_int), ("stop", C.c_int),
-                ("stop_tol", C.c_double)]
+                ("stop_tol", C.c_double), ("orth", C.c_int)]
 
 
 class spai_stats(C.Structure):
@@ -144,9 +144,10 @@ def make_spai_opts(init=PAT_A, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fi
 
 
 def make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8, gmres_max_it=0,
-                 ir_max_steps=10, stop=IR_STOP_BACKWARD, stop_tol=0.0):
+                 ir_max_steps=10, stop=IR_STOP_BACKWARD, stop_tol=0.0, orth=0):
+    """orth: 0 modified Gram-Schmidt (default, the paper's), 1 classical Gram-Schmidt twice."""
     return ir_opts(_prec(uf), _prec(u), _prec(ug), _prec(up), _prec(ur), float(tau), int(gmres_max_it),
-                   int(ir_max_steps), int(stop), float(stop_tol))
+                   int(ir_max_steps), int(stop), float(stop_tol), int(orth))
 
 
 class Context:

@@ -72,10 +72,14 @@ struct IrArgs {
     int* its;                   // imax
     double* nbe;                // imax + 1
     int* out;                   // [0] steps, [1] flags
+    int orth;                   // 0 modified Gram-Schmidt, 1 classical Gram-Schmidt twice (CGS2)
+    void* pvec;                 // CGS2: 2 parities x gridDim.x x (kmax + 1) partial dot products (u_g)
+    unsigned* gcount;           // CGS2: counter of the barrier that publishes them (zeroed)
 };
 
 struct IrShared {
     unsigned epoch;
+    unsigned gepoch;  // CGS2 barrier count
     int ok;
     double bcast[2];
     double resid;
@@ -349,8 +353,10 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
         soa[i] = a.A.off[sg];
         sop[i] = hasP ? a.P.off[sg] : 0;
     }
-    if (tid == 0) { sh->epoch = 0; sh->ok = 1; }
+    if (tid == 0) { sh->epoch = 0; sh->gepoch = 0; sh->ok = 1; }
     __syncthreads();
+    const GridBarrier gbar{a.gcount, a.err, a.limit};
+    unsigned vx = 0;  // CGS2 exchanges so far (identical in every block)
 
     int steps = 0, flags = 0;
     for (int it = 0; it <= a.imax; it++) {
@@ -419,6 +425,55 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
                 } else {
                     for (int64_t row = r0 + tid; row < r1; row += BT) ws[row - r0] = (TG)ldcg(&tbuf[row]);
                 }
+                if (a.orth) {
+                    // ---- classical Gram-Schmidt applied twice in u_g: each pass forms all
+                    // j+1 projections of the same w (one vector exchange), then subtracts them
+                    TG* cvec = reinterpret_cast<TG*>(yv);  // free until the back substitution
+                    const int lane = tid & 31, wid = tid >> 5, nwp = BT >> 5;
+                    __syncthreads();
+                    for (int pass = 0; pass < 2; pass++) {
+                        TG* pbase = (TG*)a.pvec + (size_t)(vx & 1u) * gridDim.x * (kmax + 1);
+                        for (int i = wid; i <= j; i += nwp) {
+                            const TG* Vi = V + (int64_t)i * a.ldv;
+                            TG acc = TG(0);
+                            for (int64_t row = r0 + lane; row < r1; row += 32) acc = fma(Vi[row], ws[row - r0], acc);
+                            acc = warp_sum(acc);
+                            if (lane == 0) pbase[(size_t)blockIdx.x * (kmax + 1) + i] = acc;
+                        }
+                        if (!grid_sync(gbar, &sh->gepoch, &sh->ok)) return;
+                        for (int i = wid; i <= j; i += nwp) {
+                            TG acc = TG(0);
+                            for (unsigned b = lane; b < gridDim.x; b += 32) acc += ldcg(&pbase[(size_t)b * (kmax + 1) + i]);
+                            acc = warp_sum(acc);
+                            if (lane == 0) cvec[i] = acc;
+                        }
+                        vx++;
+                        __syncthreads();
+                        if (tid == GT)
+                            for (int i = 0; i <= j; i++) hc[i] = pass == 0 ? (double)cvec[i] : (double)((TG)hc[i] + cvec[i]);
+                        for (int64_t row = r0 + tid; row < r1; row += BT) {
+                            TG acc = ws[row - r0];
+                            for (int i = 0; i <= j; i++) acc = fma(-cvec[i], V[(int64_t)i * a.ldv + row], acc);
+                            ws[row - r0] = acc;
+                        }
+                        __syncthreads();
+                    }
+                    part = TG(0);
+                    for (int64_t row = r0 + tid; row < r1; row += BT) {
+                        const TG wv = ws[row - r0];
+                        wbuf[row] = wv;
+                        part = fma(wv, wv, part);
+                    }
+                    if (tid == GT) {
+                        // rotations 0..j-1 on the new column
+                        for (int q = 0; q < j; q++) {
+                            const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
+                            hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
+                            hc[q] = t0;
+                            if (blockIdx.x == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
+                        }
+                    }
+                } else {
                 // sell_rows and the copy give thread tid the rows r0 + tid + u*BT, so
                 // the partial needs no __syncthreads
 #pragma unroll
@@ -488,6 +543,7 @@ __global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
                             part = fma(wv, wv, part);
                         }
                     }
+                }
                 }
                 TG hsq;
                 if (!xsum<true>(a, sh, redg, part, hsq)) return;
@@ -726,6 +782,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     if (P && P->uf != o->uf) return SPAI_ERR_INVALID_ARG;
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
+    if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
     int kmax = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
     if (kmax > n) kmax = (int)n;
     if (kmax > KMAX_LIMIT) return SPAI_ERR_UNSUPPORTED;
@@ -748,6 +805,8 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     unsigned long long h_norms[3] = {0, 0, 0};
     int h_out[2] = {0, 0}, h_err = 0;
     int grid = 0;
+    void* pvec = nullptr;
+    unsigned* gcount = nullptr;
     SellMat As;
     const SellMat* Ps = nullptr;
     int64_t ldv = (n + 31) & ~int64_t(31);
@@ -771,6 +830,11 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     TRY(dev_alloc((void**)&err, sizeof(int) * 2, s));
     TRY(dev_alloc((void**)&norms, sizeof(unsigned long long) * 3, s));
     CTRY(cudaMemsetAsync(norms, 0, sizeof(unsigned long long) * 3, s));
+    if (o->orth) {
+        TRY(dev_alloc(&pvec, (size_t)sg * 2 * MAX_GRID * (kmax + 1), s));
+        TRY(dev_alloc((void**)&gcount, sizeof(unsigned), s));
+        CTRY(cudaMemsetAsync(gcount, 0, sizeof(unsigned), s));
+    }
     CTRY(cudaMemsetAsync(its, 0, sizeof(int) * (imax + 1), s));
     CTRY(cudaMemsetAsync(outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, s));
@@ -827,6 +891,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
         a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
         a.its = its; a.nbe = nbe; a.out = outv;
+        a.orth = o->orth; a.pvec = pvec; a.gcount = gcount;
         const int rm = o->ur == SPAI_QUAD ? 2 : 1;
         CTRY(cudaEventRecord(ek0, s));
 #define LAUNCH(TU, TG, TP) TRY((launch_ir_rm<TU, TG, TP>(a, rm, num_sms, s, &grid)))
@@ -892,6 +957,8 @@ done:
     dev_free(x, s); dev_free(r, s); dev_free(wbuf, s); dev_free(tbuf, s); dev_free(V, s);
     dev_free(R, s); dev_free(msg, s); dev_free(nbe, s); dev_free(its, s); dev_free(outv, s); dev_free(err, s);
     dev_free(norms, s);
+    dev_free(pvec, s);
+    dev_free(gcount, s);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ek0) cudaEventDestroy(ek0);

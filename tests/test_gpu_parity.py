@@ -254,3 +254,26 @@ def test_edge_cases(ctx):
     with pytest.raises(S.SpaiError) as e:
         S.spai_build(ctx, A, S.make_spai_opts(init=1, max_fill=40))
     assert e.value.code == -8
+
+
+@pytest.mark.parametrize("tup", [("half", "single", "single", "single", "double"),
+                                 ("single", "double", "double", "double", "quad"),
+                                 ("single", "double", "single", "single", "double")])
+def test_ir_cgs2_against_oracle(ctx, tup):
+    """The classical-Gram-Schmidt-twice Arnoldi option against the oracle's CGS2."""
+    uf, u, ug, up, ur = tup
+    if u == "single":
+        A, b, x_true = synth.cfg_large_3d(N=16)
+        init, F = O.PAT_A2, 25
+    else:
+        A = synth.conv_diff_2d(40, 20.0, 1.0, 0.1, seed=11)
+        b, x_true = synth.rhs(A, seed=12)
+        init, F = O.PAT_A, 30
+    tau = 1e-4 if ug == "single" else 1e-8
+    so = S.make_spai_opts(init=init, max_fill=F, uf=uf)
+    io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=1)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    Sr = O.spai(A, init=init, max_fill=F, uf=uf)
+    ref = O.gmres_ir(A, b, O.assemble_P(Sr, up, uf), uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=O.ORTH_CGS2)
+    check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])

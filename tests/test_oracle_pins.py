@@ -453,3 +453,49 @@ def test_gmres_single_precision_converges_to_tau():
     assert rr <= 1e-4
     assert np.linalg.norm(Ad @ d - r) / np.linalg.norm(r) <= 1e-3
     assert np.array_equal(d, O.round_to(d, "single"))
+
+
+# ---------------------------------------------------------------- Gram-Schmidt variants
+
+
+@pytest.mark.parametrize("orth", [O.ORTH_MGS, O.ORTH_CGS2])
+def test_arnoldi_matches_krylov_qr(orth):
+    # Arnoldi builds an orthonormal basis of the Krylov space K_k(A, r) with
+    # A V_k = V_{k+1} H; compare with numpy's QR of the explicit Krylov matrix
+    rng = np.random.default_rng(5)
+    n, k = 12, 6
+    Ad = rng.normal(size=(n, n)) + 3 * np.eye(n)
+    r = rng.normal(size=n)
+    V, H = O.arnoldi(dense_to_csr(Ad), r, None, k=k, orth=orth)
+    K = np.column_stack([np.linalg.matrix_power(Ad, i) @ r for i in range(k + 1)])
+    Q, _ = np.linalg.qr(K)
+    # same subspace column by column (up to signs)
+    for c in range(k + 1):
+        assert abs(abs(Q[:, c] @ V[:, c]) - 1.0) < 1e-9
+    np.testing.assert_allclose(Ad @ V[:, :k], V @ H, atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(k + 1), atol=1e-13)
+
+
+def test_cgs2_keeps_orthogonality_in_single():
+    # twice is enough: CGS2's basis is orthogonal to O(u) even where MGS
+    # drifts (loss of orthogonality ~ u * cond); single precision, 60 steps
+    A, b, x = synth.cfg_small_2d()
+    r = np.random.default_rng(2).normal(size=1024)
+    V2, _ = O.arnoldi(A, r, None, k=60, ug="single", up="single", orth=O.ORTH_CGS2)
+    Vm, _ = O.arnoldi(A, r, None, k=60, ug="single", up="single", orth=O.ORTH_MGS)
+    e2 = np.linalg.norm(V2.T @ V2 - np.eye(V2.shape[1]))
+    em = np.linalg.norm(Vm.T @ Vm - np.eye(Vm.shape[1]))
+    assert e2 <= 100 * 2.0 ** -24 * np.sqrt(V2.shape[1])
+    assert e2 <= em
+
+
+def test_gmres_ir_cgs2_matches_mgs_solution():
+    A, b, x_true = synth.cfg_small_2d()
+    S = O.spai(A, init=O.PAT_A, uf="single", max_fill=30)
+    P = O.assemble_P(S, "double", "single")
+    Rm = O.gmres_ir(A, b, P, tau=1e-4, orth=O.ORTH_MGS)
+    Rc = O.gmres_ir(A, b, P, tau=1e-4, orth=O.ORTH_CGS2)
+    assert Rc["status"] & O.IR_CONVERGED
+    assert Rc["steps"] == Rm["steps"]
+    assert abs(Rc["total_its"] - Rm["total_its"]) <= 1
+    assert np.max(np.abs(Rc["x"] - Rm["x"])) <= 4 * 2.0 ** -53 * np.max(np.abs(Rm["x"]))
