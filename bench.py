@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cgs2", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the double-precision, adaptive and serving lines")
     return p.parse_args()
 
 
@@ -184,6 +185,112 @@ def max_over_ranks(value, dist=None, device="cpu"):
 def job_throughput(world, steps, max_ms):
     """Whole-job solves/s: every rank solves `steps` systems; time is the slowest rank's."""
     return world * steps / (max_ms / 1000.0)
+
+
+# ---------------------------------------------------------------- other workloads (reported beside the headline)
+
+def extra_workloads(S, synth, torch, dev):
+    """Three secondary lines, each bounded to a few seconds:
+    * u = double: the 32x32 2D system with (single, double, double, double, quad), the
+      configuration whose backward error must reach 1e-15;
+    * adaptive: Grote-Huckle SPAI from the identity on a 100,000-column random nonsymmetric
+      matrix (16 nonzeros per column, row/column scaling 1e6), eps 0.5, beta 8, fill cap 30,
+      u_f single, then the solve with (single, double, double, double, quad);
+    * serving: 48 requests of 3D systems (grids 10^3..46^3, log-uniform) arriving as a
+      Poisson stream at 200 requests/s into a context with a 120 GB admission budget;
+      latency = completion - arrival."""
+    import numpy as np
+    out = {}
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(dev.index or 0, stream=stream)
+    # ---- u = double
+    A, b, xt = synth.cfg_small_2d()
+    Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+    for _ in range(3):
+        S.gmres_ir_solve(ctx, Ad, bd, xd, sopts=so, opts=io)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(stream)
+    for _ in range(reps):
+        st = S.gmres_ir_solve(ctx, Ad, bd, xd, sopts=so, opts=io)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    Ms = synth.to_scipy(A)
+    x = xd.cpu().numpy()
+    nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+    out["double_2d"] = dict(workload="2D conv-diff 32x32 (n=1024), Peclet 10, pattern(A), "
+                                     "(single,double,double,double,quad), tau 1e-4",
+                            solves_per_s=reps / (e0.elapsed_time(e1) / 1000.0), backward_error=nbe,
+                            its=st["its"], steps=st["steps"])
+    # ---- adaptive
+    A = synth.random_sparse(100_000, 16, seed=6, log10_scale=6.0)
+    b, xt = synth.rhs(A, seed=7)
+    Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    so = S.make_spai_opts(init=0, adaptive=True, eps=0.5, beta=8, max_fill=30, uf="single")
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8)
+    P, sst = S.spai_build(ctx, Ad, so)
+    P.free()
+    P, sst = S.spai_build(ctx, Ad, so)
+    torch.cuda.synchronize()
+    st = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io)
+    x = xd.cpu().numpy()
+    Ms = synth.to_scipy(A)
+    nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+    out["adaptive_100k"] = dict(workload="random nonsymmetric n=100000, 16 nnz/col, scaling 1e6; adaptive "
+                                          "SPAI eps 0.5, beta 8, cap 30, u_f single; (single,double,double,double,quad)",
+                                spai_ms=sst["ms"], spai_cols_per_s=100_000 / (sst["ms"] / 1000.0),
+                                nnz_P=sst["nnz_P"], cols_converged=sst["cols_converged"],
+                                cols_fillcap=sst["cols_fillcap"], ir_ms=st["ms_ir"], its=st["its"],
+                                steps=st["steps"], backward_error=nbe)
+    P.free()
+    ctx.close()
+    # ---- serving
+    rng = np.random.default_rng(5)
+    R, rate = 48, 200.0
+    grids = np.round(np.exp(rng.uniform(np.log(10), np.log(46), size=R))).astype(int)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=R))
+    reqs = []
+    for i, N in enumerate(grids):
+        A3 = synth.conv_diff_3d(int(N), 50.0, seed=100 + i)
+        b3, _ = synth.rhs(A3, seed=200 + i)
+        reqs.append((A3, b3))
+    so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3)
+    io = S.make_ir_opts(uf="half", u="single", ug="single", up="double", ur="double", tau=1e-4)
+    sctx = S.Context(dev.index or 0, hbm_budget=120 << 30)
+    # warm the workers and kernels
+    t = S.solver_submit(sctx, reqs[0][0], reqs[0][1], so, io)
+    while S.solver_poll(sctx, t) is None:
+        time.sleep(0.001)
+    pending = {}
+    lat = [None] * R
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < R or pending:
+        now = time.perf_counter() - t0
+        while nxt < R and arrivals[nxt] <= now:
+            pending[nxt] = S.solver_submit(sctx, reqs[nxt][0], reqs[nxt][1], so, io)
+            nxt += 1
+        for i in list(pending):
+            stt = S.solver_poll(sctx, pending[i], np.zeros(len(reqs[i][1])))
+            if stt is not None:
+                lat[i] = (time.perf_counter() - t0) - arrivals[i]
+                del pending[i]
+        time.sleep(0.0002)
+    makespan = time.perf_counter() - t0
+    sctx.close()
+    lat = np.array(lat) * 1000.0
+    out["serving"] = dict(workload="48 requests, 3D conv-diff grids 10^3..46^3 (log-uniform), Poisson 200/s, "
+                                   "(half,single,single,double,double), budget 120 GB, host inputs",
+                          requests=R, solves_per_s=R / makespan, p50_ms=float(np.percentile(lat, 50)),
+                          p99_ms=float(np.percentile(lat, 99)), sum_n=int(sum(int(g) ** 3 for g in grids)))
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -327,6 +434,10 @@ def main():
                     ir_kernel_ms=float(np.mean([s["ms_kernel"] for s in st2])), its=st2[-1]["its"],
                     backward_error=nbe2)
 
+    extra = {}
+    if world == 1 and not args.no_extra:
+        extra = extra_workloads(S, synth, torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -361,6 +472,7 @@ def main():
                           peak_source=peak_src, algorithmic_bytes_per_launch=float(np.mean(ir_bytes))),
             gpu_launches=launches,
             arnoldi_cgs2=cgs2,
+            **extra,
             clocks=clocks,
             e2e=e2e,
             cpu_baseline=cpu,
