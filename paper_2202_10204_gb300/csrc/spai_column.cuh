@@ -154,17 +154,18 @@ __device__ inline Tile<C> carve(unsigned char* base, int mm, int rl, int cmax)
 // Steps 1-2: lists of the rows in J, then the sorted merge.  Returns |I_k|
 // (which may exceed mm; then only the first mm rows were written).
 template <class S, class C>
-__device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64_t k, int nj, int mm)
+__device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, C* TW, const int32_t* TJ, int32_t* tlcol,
+                                           C* tlval, int32_t* tlcnt, int64_t k, int nj, int mm)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
     int len = 0;
     if (lane < nj) {
-        const int j = T.J[lane];
+        const int j = TJ[lane];
         const double dj = a.d[j];
         const int64_t b = a.rp[j], e = a.rp[j + 1];
-        int32_t* lc = T.lcol + lane * a.rl;
-        C* lv = T.lval + lane * a.rl;
+        int32_t* lc = tlcol + lane * a.rl;
+        C* lv = tlval + lane * a.rl;
         for (int64_t q = b; q < e; q += 4) {
             double vv[4];
             int cc[4];
@@ -183,12 +184,12 @@ __device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64
             }
         }
     }
-    T.lcnt[lane] = len;
+    tlcnt[lane] = len;
     __syncwarp();
     // merge; lane nj carries the list {k} with value 1 (the e_k column)
     int q = 0;
-    const int32_t* lc = T.lcol + lane * a.rl;
-    const C* lv = T.lval + lane * a.rl;
+    const int32_t* lc = tlcol + lane * a.rl;
+    const C* lv = tlval + lane * a.rl;
     int head = lane < nj ? (len > 0 ? lc[0] : INT_MAX) : (lane == nj ? (int)k : INT_MAX);
     int m = 0;
     while (true) {
@@ -196,8 +197,8 @@ __device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64
         if (mn == INT_MAX) break;
         const bool has = head == mn;
         if (m < mm) {
-            if (lane == 0) T.I[m] = mn;
-            if (lane <= nj) T.W[m * SPAI_LD + lane] = has ? (lane < nj ? lv[q] : C(1)) : C(0);
+            if (lane == 0) TI[m] = mn;
+            if (lane <= nj) TW[m * SPAI_LD + lane] = has ? (lane < nj ? lv[q] : C(1)) : C(0);
         }
         m++;
         if (has) {
@@ -207,6 +208,12 @@ __device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64
     }
     __syncwarp();
     return m;
+}
+
+template <class S, class C>
+__device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64_t k, int nj, int mm)
+{
+    return gather_ptrs<S, C>(a, T.I, T.W, T.J, T.lcol, T.lval, T.lcnt, k, nj, mm);
 }
 
 // Step 3, register path.  Returns flags (CF_SINGULAR); writes mbar to T.mb.
@@ -675,6 +682,9 @@ __global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
     }
 }
 
+template <class S>
+int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
+
 // Launch for storage type S: the register path when the tile height fits
 // (32 or 64 rows), otherwise the shared-memory path.
 template <class S>
@@ -686,6 +696,7 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
     int MMsel = 0;
     if (a.mmax <= 32) MMsel = 32;
     else if (a.mmax <= 64) MMsel = 64;
+    else if (a.mmax <= 512) return launch_spai_cta_t<S>(a0, adaptive, num_sms, smem_cap, s);
     if (MMsel) a.mmax = MMsel;
     while (adaptive && a.cmax > 256 && tile_bytes<C>(a.mmax, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
     const size_t wb = tile_bytes<C>(a.mmax, a.rl, a.cmax);
