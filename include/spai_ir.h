@@ -149,6 +149,9 @@ typedef struct spai_precond_s* spai_precond;
  * NULL: the context creates its own).  hbm_budget_bytes bounds the device
  * memory the serving queue admits (0: 90% of free memory at creation). */
 int spai_ctx_create(spai_ctx* out, int device, void* cuda_stream, size_t hbm_budget_bytes);
+/* Waits for the context's work, stops its serving workers and releases its
+ * stream (if it created it).  Preconditioners it built stay valid and may be
+ * freed later (on the default stream). */
 void spai_ctx_destroy(spai_ctx ctx);
 
 /* Algorithm 1 on A^T D (Section 2.2, Algorithm 1; Section 4 scaling), giving

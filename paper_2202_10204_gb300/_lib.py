@@ -174,8 +174,9 @@ class Context:
 
 
 class Precond:
-    def __init__(self, h):
+    def __init__(self, h, ctx=None):
         self.h = h
+        self.ctx = ctx  # keeps the building context alive while the handle lives
 
     def info(self):
         n = C.c_int64()
@@ -220,7 +221,7 @@ def spai_build(ctx: Context, A, opts: spai_opts, per_column=False):
                cols_nonfinite=st.cols_nonfinite, max_I=st.max_I, max_J=st.max_J, ms=st.ms,
                ms_kernel=st.ms_kernel, launches=st.launches, rc=rc)
     out.update(cols)
-    return Precond(h), out
+    return Precond(h, ctx), out
 
 
 def _ir_dict(st, rc):

@@ -37,6 +37,7 @@ constexpr int IR_THREADS = 1024;
 constexpr int KMAX_LIMIT = 1024;
 constexpr int MAX_GRID = 160;   // exchange slots are polled by one warp, SPL slots per lane
 constexpr int SPL = (MAX_GRID + 31) / 32;
+constexpr int SLOT_WORDS = 16;  // one 128-byte line per block and parity (up to 4 words used)
 constexpr int PF = 4;           // rows per thread whose next basis entries are prefetched
 
 // SELL-32: rows in slices of 32; slice s stores its entries column-major
@@ -64,7 +65,7 @@ struct IrArgs {
     void* V;                    // ldv x (kmax + 1), precision u_g; a block reads back only its own rows
     int64_t ldv;
     double* R;                  // (kmax + 1) x kmax column-major, written by block 0
-    unsigned long long* msg;    // [2 parities][gridDim.x][4] epoch-tagged words
+    unsigned long long* msg;    // [2 parities][gridDim.x][SLOT_WORDS] epoch-tagged words
     int* err;
     long long limit;            // clock64 cycles a wait may take
     double anorm, bnorm, tau, stop_tol;
@@ -100,7 +101,10 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 // publishes NW 32-bit payload words, each tagged with the round's epoch in
 // the upper 32 bits (one single-copy-atomic 64-bit store per word) after a
 // fence that orders everything the block wrote before the preceding
-// __syncthreads.  Warp 0 then polls every block's words of that epoch (lane
+// __syncthreads.  Each block's slot is a 128-byte line of its own: blocks
+// sharing a line made every round measurably slower (the polls of all blocks
+// and the stores of the line's owners queue on the same L2 line), while more
+// polling warps or a denser layout made it slower still.  Warp 0 then polls every block's words of that epoch (lane
 // l owns blocks l, l+32, ...), feeding them to `acc` in that fixed order,
 // until one pass sees every word carry the epoch; it then fences (acquire)
 // and `acc.finish` combines the lanes and publishes to shared memory.  Slots
@@ -114,12 +118,12 @@ __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const ui
     const unsigned G = gridDim.x;
     if (threadIdx.x < 32) {
         const unsigned ep = sh->epoch + 1u;
-        unsigned long long* base = a.msg + (size_t)(ep & 1u) * G * 4;
+        unsigned long long* base = a.msg + (size_t)(ep & 1u) * G * SLOT_WORDS;
         if (threadIdx.x == 0) {
             if (DATA) __threadfence();
 #pragma unroll
             for (int k = 0; k < NW; k++)
-                st_relaxed_u64(base + (size_t)blockIdx.x * 4 + k, ((unsigned long long)ep << 32) | pay[k]);
+                st_relaxed_u64(base + (size_t)blockIdx.x * SLOT_WORDS + k, ((unsigned long long)ep << 32) | pay[k]);
         }
         const unsigned lane = threadIdx.x;
         const long long t0 = clock64();
@@ -134,7 +138,7 @@ __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const ui
                     uint32_t wv[NW];
 #pragma unroll
                     for (int k = 0; k < NW; k++) {
-                        unsigned long long w = ld_relaxed_u64(base + (size_t)i * 4 + k);
+                        unsigned long long w = ld_relaxed_u64(base + (size_t)i * SLOT_WORDS + k);
                         all = all && (unsigned)(w >> 32) == ep;
                         wv[k] = (uint32_t)w;
                     }
@@ -316,8 +320,18 @@ __device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t*
     }
 }
 
+// Threads per block of the refinement kernel: 1024 when the basis and the
+// preconditioner products are single precision; 512 when either is double,
+// because the 1024-thread build of those spills registers (64 per thread),
+// which puts the basis prefetch behind HBM latency every Gram-Schmidt round.
+template <class TG, class TP>
+constexpr int ir_threads()
+{
+    return (sizeof(TG) == 8 || sizeof(TP) == 8) ? IR_THREADS / 2 : IR_THREADS;
+}
+
 template <class TU, class TG, class TP, int RM>
-__global__ void __launch_bounds__(IR_THREADS, 1) k_ir(IrArgs a)
+__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ IrShared shs;
@@ -699,7 +713,7 @@ template <class TU, class TG, class TP, int RM>
 int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, int* grid_out)
 {
     auto kern = k_ir<TU, TG, TP, RM>;
-    // one block per SM (1024 threads), at least 256 rows per block, rows per
+    // one block per SM, at least 256 rows per block, rows per
     // block a multiple of 32 so that blocks own whole SELL slices
     int64_t G = std::min<int64_t>((a.n + 255) / 256, std::min(num_sms, MAX_GRID));
     if (G < 1) G = 1;
@@ -709,10 +723,11 @@ int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, int* grid_out)
     const size_t smem = sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + a.rb * sizeof(TG) + 64;
     SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, IR_THREADS, smem));
+    constexpr int threads = ir_threads<TG, TP>();
+    SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
     if ((int64_t)occ * num_sms < G) return SPAI_ERR_UNSUPPORTED;
     void* args[] = {(void*)&a};
-    SPAI_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)G), dim3(IR_THREADS), args, smem, s));
+    SPAI_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)G), dim3(threads), args, smem, s));
     *grid_out = (int)G;
     return 0;
 }
@@ -823,7 +838,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     TRY(dev_alloc(&tbuf, (size_t)sp * n, s));
     TRY(dev_alloc(&V, (size_t)sg * ldv * (kmax + 1), s));
     TRY(dev_alloc((void**)&R, sizeof(double) * (size_t)(kmax + 1) * kmax, s));
-    TRY(dev_alloc((void**)&msg, sizeof(unsigned long long) * 2 * MAX_GRID * 4, s));
+    TRY(dev_alloc((void**)&msg, sizeof(unsigned long long) * 2 * MAX_GRID * SLOT_WORDS, s));
     TRY(dev_alloc((void**)&nbe, sizeof(double) * (imax + 1), s));
     TRY(dev_alloc((void**)&its, sizeof(int) * (imax + 1), s));
     TRY(dev_alloc((void**)&outv, sizeof(int) * 2, s));
@@ -838,7 +853,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     CTRY(cudaMemsetAsync(its, 0, sizeof(int) * (imax + 1), s));
     CTRY(cudaMemsetAsync(outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(msg, 0, sizeof(unsigned long long) * 2 * MAX_GRID * 4, s));
+    CTRY(cudaMemsetAsync(msg, 0, sizeof(unsigned long long) * 2 * MAX_GRID * SLOT_WORDS, s));
     CTRY(cudaEventRecord(e0, s));
     // A and P in u_p, SELL-32 (P's copy is cached on the preconditioner)
     TRY(sell_build(n, A.rowptr, A.col, A.val, o->up, num_sms, s, &As, &nl));
@@ -1110,7 +1125,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     const int64_t ldv = (n + 31) & ~int64_t(31);
     const int64_t nsl = (n + 31) >> 5;
     Carve cv{base, 0, (size_t)SPAI_NOALLOC_SCRATCH_BYTES};
-    const size_t msg_bytes = sizeof(unsigned long long) * 2 * MAX_GRID * 4;
+    const size_t msg_bytes = sizeof(unsigned long long) * 2 * MAX_GRID * SLOT_WORDS;
     const size_t ctrl_bytes = sizeof(int) * 4 + sizeof(int) * (imax + 1) + sizeof(double) * (imax + 1) +
                               sizeof(unsigned long long) * 3 + 64;
     unsigned long long* msg = (unsigned long long*)cv.take(msg_bytes);

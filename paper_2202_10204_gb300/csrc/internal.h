@@ -9,6 +9,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <thread>
 #include <vector>
 
@@ -42,7 +43,8 @@ struct spai_precond_s {
     SellMat sell_f32, sell_f64;  // lazily made SELL-32 copies in u_p = single / double
     void* val_uf = nullptr;      // copy rounded to u_f (used by x0 = P b)
     int uf = SPAI_DOUBLE;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;  // the building context's stream (the default stream once it is gone)
+    spai_ctx_s* owner = nullptr;    // the context that built it through spai_build, while it lives
 };
 
 struct ServeRequest;
@@ -64,6 +66,7 @@ struct spai_ctx_s {
     size_t in_use = 0;
     uint64_t next_ticket = 1;
     bool stopping = false;
+    std::set<spai_precond_s*> live;  // preconditioners built by spai_build and not yet freed
 };
 
 // stream-ordered device allocation helpers

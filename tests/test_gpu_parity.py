@@ -256,6 +256,24 @@ def test_edge_cases(ctx):
     assert e.value.code == -8
 
 
+def test_precond_outlives_its_context():
+    # a preconditioner stays usable after the context that built it is destroyed
+    A, b, _ = synth.cfg_small_2d()
+    c = S.Context(0)
+    P, _ = S.spai_build(c, A, S.make_spai_opts(init=1, max_fill=30, uf="single"))
+    before = P.export()
+    c.close()
+    after = P.export()
+    for u, v in zip(before, after):
+        assert np.array_equal(u, v)
+    c2 = S.Context(0)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(c2, A, b, x, P=P, opts=S.make_ir_opts(tau=1e-8))
+    assert st["flags"] & 1
+    P.free()
+    c2.close()
+
+
 @pytest.mark.parametrize("tup", [("half", "single", "single", "single", "double"),
                                  ("single", "double", "double", "double", "quad"),
                                  ("single", "double", "single", "single", "double")])
