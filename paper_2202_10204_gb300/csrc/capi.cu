@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -50,6 +51,26 @@ static void trim_device_pool(int dev)
     if (dev < 0 || dev >= 64) return;
     std::lock_guard<std::mutex> lk(g_pool_mu);
     if (g_pool[dev]) cudaMemPoolTrimTo(g_pool[dev], 0);
+}
+
+// Device attributes are fixed for the life of the process; some queries
+// (the SM clock rate) cost ~0.6 ms each on this driver, so they are asked
+// once per device and attribute.
+int device_attr_cached(cudaDeviceAttr attr, int device)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair((int)attr, device);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, attr, device) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cache[key] = v;
+    return v;
 }
 
 int dev_alloc(void** p, size_t bytes, cudaStream_t s)

@@ -684,10 +684,13 @@ __global__ void k_to_double(int64_t n, const TU* __restrict__ x, double* __restr
 }
 
 
-// ||A||_inf, ||b||_inf, and the largest row count q
+// ||A||_inf, ||b||_inf, and the largest row count q: per-block maxima, then
+// one atomic per block and value
 __global__ void k_norms(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ val,
                         const double* __restrict__ b, unsigned long long* __restrict__ out)
 {
+    __shared__ double sa[32], sb[32];
+    __shared__ int sq[32];
     double an = 0.0, bn = 0.0;
     int q = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -697,15 +700,27 @@ __global__ void k_norms(int64_t n, const int64_t* __restrict__ rp, const double*
         bn = fmax(bn, fabs(b[i]));
         q = max(q, (int)(rp[i + 1] - rp[i]));
     }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     an = warp_max(an);
     bn = warp_max(bn);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q = max(q, __shfl_xor_sync(0xffffffffu, q, o));
-    if ((threadIdx.x & 31) == 0) {
-        // non-negative doubles order like their bit patterns
-        atomicMax(&out[0], (unsigned long long)__double_as_longlong(an));
-        atomicMax(&out[1], (unsigned long long)__double_as_longlong(bn));
-        atomicMax(&out[2], (unsigned long long)q);
+    if (lane == 0) { sa[wid] = an; sb[wid] = bn; sq[wid] = q; }
+    __syncthreads();
+    if (wid == 0) {
+        an = lane < nw ? sa[lane] : 0.0;
+        bn = lane < nw ? sb[lane] : 0.0;
+        q = lane < nw ? sq[lane] : 0;
+        an = warp_max(an);
+        bn = warp_max(bn);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q = max(q, __shfl_xor_sync(0xffffffffu, q, o));
+        if (lane == 0) {
+            // non-negative doubles order like their bit patterns
+            atomicMax(&out[0], (unsigned long long)__double_as_longlong(an));
+            atomicMax(&out[1], (unsigned long long)__double_as_longlong(bn));
+            atomicMax(&out[2], (unsigned long long)q);
+        }
     }
 }
 
@@ -898,8 +913,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         a.arp = A.rowptr; a.aci = A.col; a.aval = A.val;
         a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
         a.err = err;
-        int clk_khz = 0;
-        cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, device);
+        int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
         if (clk_khz <= 0) clk_khz = 2000000;
         a.limit = (long long)clk_khz * 1000LL * 4;  // about four seconds per wait
         a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
@@ -1218,8 +1232,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     a.arp = A->rowptr; a.aci = A->col; a.aval = A->val;
     a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
     a.err = err;
-    int clk_khz = 0;
-    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, device);
+    int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
     if (clk_khz <= 0) clk_khz = 2000000;
     a.limit = (long long)clk_khz * 1000LL * 4;
     a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;

@@ -69,6 +69,9 @@ struct spai_ctx_s {
     std::set<spai_precond_s*> live;  // preconditioners built by spai_build and not yet freed
 };
 
+// cudaDeviceGetAttribute, asked once per process for each (attribute, device); 0 on failure
+int device_attr_cached(cudaDeviceAttr attr, int device);
+
 // stream-ordered device allocation helpers
 int dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);

@@ -291,20 +291,23 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
     }
 }
 
-// P in CSR from the padded per-column results
+// P in CSR from the padded per-column results: one thread per padded slot
+// (k, c), so that the reads of the n x F arrays are coalesced
 template <class S>
 __global__ void k_assemble(int64_t n, int F, const int32_t* __restrict__ Jidx, const int32_t* __restrict__ Jcnt,
                            const double* __restrict__ Praw, const int64_t* __restrict__ prp,
                            int32_t* __restrict__ pcol, double* __restrict__ pval, S* __restrict__ pval_uf)
 {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        int64_t o = prp[k];
-        int nj = Jcnt[k];
-        for (int c = 0; c < nj; c++) {
-            double v = Praw[k * F + c];
-            pcol[o + c] = Jidx[k * F + c];
-            pval[o + c] = v;
-            pval_uf[o + c] = from_d<S>(v);
+    const int64_t total = n * F;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / F;
+        const int c = (int)(t - k * F);
+        if (c < Jcnt[k]) {
+            const int64_t o = prp[k] + c;
+            const double v = Praw[t];
+            pcol[o] = Jidx[t];
+            pval[o] = v;
+            pval_uf[o] = from_d<S>(v);
         }
     }
 }
@@ -378,8 +381,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
     int h_err[3] = {0, 0, 0};
     unsigned long long h_fstat[3] = {0, 0, 0};
     int maxrow = 0, maxcol = 0;
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const int optin = device_attr_cached(cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     const size_t smem_cap = optin > 0 ? (size_t)optin : (size_t)(100 * 1024);
 
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
