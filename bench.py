@@ -190,7 +190,7 @@ def job_throughput(world, steps, max_ms):
 # ---------------------------------------------------------------- other workloads (reported beside the headline)
 
 def extra_workloads(S, synth, torch, dev):
-    """Three secondary lines, each bounded to a few seconds:
+    """Four secondary lines, each bounded to a few seconds:
     * u = double: the 32x32 2D system with (single, double, double, double, quad), the
       configuration whose backward error must reach 1e-15;
     * adaptive: Grote-Huckle SPAI from the identity on a 100,000-column random nonsymmetric
@@ -198,7 +198,9 @@ def extra_workloads(S, synth, torch, dev):
       u_f single, then the solve with (single, double, double, double, quad);
     * serving: 48 requests of 3D systems (grids 10^3..46^3, log-uniform) arriving as a
       Poisson stream at 200 requests/s into a context with a 120 GB admission budget;
-      latency = completion - arrival."""
+      latency = completion - arrival;
+    * batched: 512 independent systems (half 2D convection-diffusion, half random sparse,
+      n log-uniform in [2e3, 5e4]) submitted at once; solves/s and columns/s over the makespan."""
     import numpy as np
     out = {}
     stream = torch.cuda.current_stream()
@@ -290,6 +292,48 @@ def extra_workloads(S, synth, torch, dev):
                                    "(half,single,single,double,double), budget 120 GB, host inputs",
                           requests=R, solves_per_s=R / makespan, p50_ms=float(np.percentile(lat, 50)),
                           p99_ms=float(np.percentile(lat, 99)), sum_n=int(sum(int(g) ** 3 for g in grids)))
+    # ---- batched: 512 independent systems through the queue at once
+    rng = np.random.default_rng(4)
+    R = 512
+    ns = np.exp(rng.uniform(np.log(2e3), np.log(5e4), size=R))
+    batch = []
+    for i in range(R):
+        if i % 2 == 0:
+            N = max(8, int(round(np.sqrt(ns[i]))))
+            A2 = synth.conv_diff_2d(N, float(rng.uniform(0.0, 50.0)), 1.0, 0.1, seed=1000 + i)
+        else:
+            A2 = synth.random_sparse(int(ns[i]), int(rng.integers(8, 17)), seed=2000 + i,
+                                     log10_scale=float(rng.uniform(1.0, 3.0)))
+        b2, _ = synth.rhs(A2, seed=3000 + i)
+        batch.append((A2, b2))
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    io = S.make_ir_opts(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4)
+    bctx = S.Context(dev.index or 0, hbm_budget=120 << 30)
+    t = S.solver_submit(bctx, batch[0][0], batch[0][1], so, io)
+    while S.solver_poll(bctx, t) is None:
+        time.sleep(0.001)
+    t0 = time.perf_counter()
+    tickets = [S.solver_submit(bctx, A2, b2, so, io) for A2, b2 in batch]
+    done, conv, its = {}, 0, 0
+    while len(done) < R:
+        for i, tk in enumerate(tickets):
+            if i in done:
+                continue
+            stt = S.solver_poll(bctx, tk, np.zeros(len(batch[i][1])))
+            if stt is not None:
+                done[i] = time.perf_counter() - t0
+                conv += int(stt["flags"] & 1)
+                its += stt["total_its"]
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t0
+    bctx.close()
+    sum_n = int(sum(len(a[0]) - 1 for a, _ in batch))
+    out["batched_512"] = dict(workload="512 systems, n log-uniform in [2e3, 5e4]: even = 2D conv-diff (Peclet "
+                                       "U(0,50)), odd = random sparse 8-16 nnz/col with row/column scaling "
+                                       "10^U(1,3) (cond_1 ~1e2-5e3); pattern(A), (single,double,single,single,double), tau 1e-4, "
+                                       "all submitted at once, host inputs",
+                              systems=R, solves_per_s=R / makespan, cols_per_s=sum_n / makespan, sum_n=sum_n,
+                              makespan_s=makespan, converged=conv, total_its=its)
     return out
 
 

@@ -73,6 +73,34 @@ int device_attr_cached(cudaDeviceAttr attr, int device)
     return v;
 }
 
+cudaError_t allow_max_dynamic_smem_ptr(const void* kernel, size_t* dyn)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(kernel, dev);
+    auto it = done.find(key);
+    if (it != done.end()) {
+        *dyn = it->second;
+        return cudaSuccess;
+    }
+    const int optin = device_attr_cached(cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    // static and dynamic shared memory together may not exceed the opt-in limit
+    const int d = optin - (int)fa.sharedSizeBytes;
+    if (d <= 0) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, d);
+    if (e != cudaSuccess) return e;
+    done[key] = (size_t)d;
+    *dyn = (size_t)d;
+    return cudaSuccess;
+}
+
 int dev_alloc(void** p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
@@ -210,6 +238,11 @@ static void run_request(spai_ctx ctx, cudaStream_t s, ServeRequest* r)
     dev_free(dx, s);
     csr_release(&dA, s);
     cudaStreamSynchronize(s);
+    if (rc == SPAI_ERR_CUDA) {
+        // the status code alone does not say which call failed
+        const cudaError_t e = cudaGetLastError();
+        fprintf(stderr, "spai serving: request of order %lld failed: %s\n", (long long)r->n, cudaGetErrorString(e));
+    }
     r->status = rc < 0 ? rc : wrc;
 }
 

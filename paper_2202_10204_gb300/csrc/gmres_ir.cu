@@ -39,6 +39,7 @@ constexpr int MAX_GRID = 160;   // exchange slots are polled by one warp, SPL sl
 constexpr int SPL = (MAX_GRID + 31) / 32;
 constexpr int SLOT_WORDS = 16;  // one 128-byte line per block and parity (up to 4 words used)
 constexpr int PF = 4;           // rows per thread whose next basis entries are prefetched
+constexpr int MGS_GROUP_MIN_GRID = 64;  // grids from this size run the Gram-Schmidt rounds in a group
 
 // SELL-32: rows in slices of 32; slice s stores its entries column-major
 // (entry c of row 32s+l at off[s] + 32c + l), padded to the slice's longest
@@ -66,6 +67,9 @@ struct IrArgs {
     int64_t ldv;
     double* R;                  // (kmax + 1) x kmax column-major, written by block 0
     unsigned long long* msg;    // [2 parities][gridDim.x][SLOT_WORDS] epoch-tagged words
+    unsigned long long* msg2;   // the same for the Gram-Schmidt group's rounds
+    int g2;                     // Gram-Schmidt group: blocks 0..g2-1, each over the rows of two
+                                // blocks (0: every block runs the rounds on its own rows)
     int* err;
     long long limit;            // clock64 cycles a wait may take
     double anorm, bnorm, tau, stop_tol;
@@ -80,6 +84,7 @@ struct IrArgs {
 
 struct IrShared {
     unsigned epoch;
+    unsigned epoch2;  // rounds of the Gram-Schmidt group
     unsigned gepoch;  // CGS2 barrier count
     int ok;
     double bcast[2];
@@ -112,13 +117,16 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 // every block has read it.  The wait is bounded: on expiry SPAI_ERR_TIMEOUT
 // goes to *err and every block leaves.  Must be called by all threads after
 // a __syncthreads that follows the block's writes.
-template <int NW, bool DATA, class Acc>
+template <int NW, bool DATA, class Acc, bool GRP = false>
 __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const uint32_t* pay, Acc& acc)
 {
-    const unsigned G = gridDim.x;
+    // GRP: a round of the Gram-Schmidt group (blocks 0..g2-1), with its own
+    // slots and epoch; only the group's blocks may call it
+    const unsigned G = GRP ? (unsigned)a.g2 : gridDim.x;
+    unsigned* epoch = GRP ? &sh->epoch2 : &sh->epoch;
     if (threadIdx.x < 32) {
-        const unsigned ep = sh->epoch + 1u;
-        unsigned long long* base = a.msg + (size_t)(ep & 1u) * G * SLOT_WORDS;
+        const unsigned ep = *epoch + 1u;
+        unsigned long long* base = (GRP ? a.msg2 : a.msg) + (size_t)(ep & 1u) * G * SLOT_WORDS;
         if (threadIdx.x == 0) {
             if (DATA) __threadfence();
 #pragma unroll
@@ -158,7 +166,7 @@ __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const ui
         if (DATA) __threadfence();
         if (ok) acc.finish(lane, sh);
         __syncwarp();
-        if (lane == 0) { sh->ok = ok; sh->epoch = ep; }
+        if (lane == 0) { sh->ok = ok; *epoch = ep; }
     }
     __syncthreads();
     return sh->ok != 0;
@@ -204,7 +212,7 @@ struct NoAcc {
 // is identical in every block.  DATA: the round also publishes the global
 // writes made before it (release/acquire); without it only the scalar
 // travels, in the same single-copy-atomic word as its epoch.
-template <bool DATA, class T>
+template <bool DATA, class T, bool GRP = false>
 __device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -225,7 +233,7 @@ __device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out)
         }
     }
     SumAcc<T> acc;
-    bool good = exchange<NW, DATA>(a, sh, pay, acc);
+    bool good = exchange<NW, DATA, SumAcc<T>, GRP>(a, sh, pay, acc);
     out = (T)sh->bcast[0];
     return good;
 }
@@ -343,6 +351,12 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
     const int GT = BT > 32 ? 32 : 0;  // the Givens thread: lane 0 of warp 1 (warp 0 polls)
     const int64_t r0 = (int64_t)blockIdx.x * a.rb;
     const int64_t r1 = min(a.n, r0 + a.rb);
+    // modified Gram-Schmidt rows [m0, m1): the block's own rows, or with a
+    // Gram-Schmidt group the rows of blocks 2b and 2b+1 (empty outside it)
+    const bool sub = a.g2 > 0;
+    const bool gs = !sub || (int)blockIdx.x < a.g2;
+    const int64_t m0 = sub ? min(a.n, (int64_t)blockIdx.x * 2 * a.rb) : r0;
+    const int64_t m1 = sub ? (gs ? min(a.n, m0 + 2 * a.rb) : m0) : r1;
     const int nsl = (int)((a.rb + 31) >> 5);
     double* cs = (double*)smem;            // kmax + 2
     double* sn = cs + (kmax + 2);          // kmax + 2
@@ -351,7 +365,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
     double* yv = hc + (kmax + 2);          // kmax + 2
     int64_t* soa = (int64_t*)(yv + (kmax + 2));  // nsl + 1 slice offsets of A
     int64_t* sop = soa + (nsl + 1);        // nsl + 1 slice offsets of P
-    TG* ws = (TG*)(sop + (nsl + 1));       // rb: w for the block's rows
+    TG* ws = (TG*)(sop + (nsl + 1));       // w for rows [m0, m1) (rb, or 2 rb with a group)
     TU* x = (TU*)a.x;
     TU* r = (TU*)a.r;
     TG* wbuf = (TG*)a.wbuf;
@@ -367,7 +381,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
         soa[i] = a.A.off[sg];
         sop[i] = hasP ? a.P.off[sg] : 0;
     }
-    if (tid == 0) { sh->epoch = 0; sh->gepoch = 0; sh->ok = 1; }
+    if (tid == 0) { sh->epoch = 0; sh->epoch2 = 0; sh->gepoch = 0; sh->ok = 1; }
     __syncthreads();
     const GridBarrier gbar{a.gcount, a.err, a.limit};
     unsigned vx = 0;  // CGS2 exchanges so far (identical in every block)
@@ -424,16 +438,37 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                 sell_rows<TP>(r0, r1, soa, a.A.col, av, [&](int c) { return (TP)(ldcg(&wbuf[c]) / hdiv); },
                               [&](int64_t row, TP v) { tbuf[row] = v; });
                 // prefetch v_0 for the first Gram-Schmidt dot while the barrier runs
+                // (with a group the range holds other blocks' rows of v_0, which are
+                // published by this barrier when j = 0: the load waits for it)
                 TG vc[PF];
+                if (!sub) {
 #pragma unroll
-                for (int u = 0; u < PF; u++) {
-                    int64_t row = r0 + tid + (int64_t)u * BT;
-                    vc[u] = row < r1 ? V[row] : TG(0);
+                    for (int u = 0; u < PF; u++) {
+                        int64_t row = m0 + tid + (int64_t)u * BT;
+                        vc[u] = row < m1 ? V[row] : TG(0);
+                    }
                 }
                 if (!xbar(a, sh)) return;
+                if (sub) {
+#pragma unroll
+                    for (int u = 0; u < PF; u++) {
+                        int64_t row = m0 + tid + (int64_t)u * BT;
+                        vc[u] = row < m1 ? ldcg(&V[row]) : TG(0);
+                    }
+                }
                 // ---- w = P t in u_p, stored in u_g (own rows, shared memory); first MGS partial
                 part = TG(0);
-                if (hasP) {
+                if (sub) {
+                    // publish w = P t; the group's blocks then read their double range
+                    if (hasP) {
+                        sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return ldcg(&tbuf[c]); },
+                                      [&](int64_t row, TP v) { wbuf[row] = (TG)v; });
+                    } else {
+                        for (int64_t row = r0 + tid; row < r1; row += BT) wbuf[row] = (TG)ldcg(&tbuf[row]);
+                    }
+                    if (!xbar(a, sh)) return;
+                    for (int64_t row = m0 + tid; row < m1; row += BT) ws[row - m0] = ldcg(&wbuf[row]);
+                } else if (hasP) {
                     sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return ldcg(&tbuf[c]); },
                                   [&](int64_t row, TP v) { ws[row - r0] = (TG)v; });
                 } else {
@@ -488,28 +523,30 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                         }
                     }
                 } else {
-                // sell_rows and the copy give thread tid the rows r0 + tid + u*BT, so
-                // the partial needs no __syncthreads
+                // sell_rows, the copy and the group's load give thread tid the rows
+                // m0 + tid + u*BT, so the partial needs no __syncthreads.  Basis
+                // entries are read through L2 (ld.cg): with a group they include
+                // rows that other blocks wrote
 #pragma unroll
                 for (int u = 0; u < PF; u++) {
-                    int64_t row = r0 + tid + (int64_t)u * BT;
-                    if (row < r1) part = fma(vc[u], ws[row - r0], part);
+                    int64_t row = m0 + tid + (int64_t)u * BT;
+                    if (row < m1) part = fma(vc[u], ws[row - m0], part);
                 }
-                for (int64_t row = r0 + tid + (int64_t)PF * BT; row < r1; row += BT) part = fma(V[row], ws[row - r0], part);
-                // ---- modified Gram-Schmidt in u_g
-                for (int i = 0; i <= j; i++) {
-                    // prefetch v_{i+1} (own rows) before waiting for h_{i,j}
+                for (int64_t row = m0 + tid + (int64_t)PF * BT; row < m1; row += BT) part = fma(ldcg(&V[row]), ws[row - m0], part);
+                // ---- modified Gram-Schmidt in u_g (blocks outside the group skip it)
+                for (int i = 0; i <= j && gs; i++) {
+                    // prefetch v_{i+1} (rows [m0, m1)) before waiting for h_{i,j}
                     const TG* Vn = V + (int64_t)(i + 1) * a.ldv;
                     TG vn[PF];
                     if (i < j) {
 #pragma unroll
                         for (int u = 0; u < PF; u++) {
-                            int64_t row = r0 + tid + (int64_t)u * BT;
-                            vn[u] = row < r1 ? Vn[row] : TG(0);
+                            int64_t row = m0 + tid + (int64_t)u * BT;
+                            vn[u] = row < m1 ? ldcg(&Vn[row]) : TG(0);
                         }
                     }
                     TG h;
-                    if (!xsum<false>(a, sh, redg, part, h)) return;
+                    if (sub ? !xsum<false, TG, true>(a, sh, redg, part, h) : !xsum<false>(a, sh, redg, part, h)) return;
                     if (tid == GT) {
                         // Givens, pipelined with the rounds: rotation i-1 needs h_i
                         hc[i] = (double)h;
@@ -526,46 +563,56 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                     if (i < j) {
 #pragma unroll
                         for (int u = 0; u < PF; u++) {
-                            int64_t row = r0 + tid + (int64_t)u * BT;
-                            if (row < r1) {
-                                TG wv = fma(-h, vc[u], ws[row - r0]);
-                                ws[row - r0] = wv;
+                            int64_t row = m0 + tid + (int64_t)u * BT;
+                            if (row < m1) {
+                                TG wv = fma(-h, vc[u], ws[row - m0]);
+                                ws[row - m0] = wv;
                                 part = fma(vn[u], wv, part);
                             }
                             vc[u] = vn[u];
                         }
-                        for (int64_t row = r0 + tid + (int64_t)PF * BT; row < r1; row += BT) {
-                            TG wv = fma(-h, Vi[row], ws[row - r0]);
-                            ws[row - r0] = wv;
-                            part = fma(Vn[row], wv, part);
+                        for (int64_t row = m0 + tid + (int64_t)PF * BT; row < m1; row += BT) {
+                            TG wv = fma(-h, ldcg(&Vi[row]), ws[row - m0]);
+                            ws[row - m0] = wv;
+                            part = fma(ldcg(&Vn[row]), wv, part);
                         }
                     } else {
 #pragma unroll
                         for (int u = 0; u < PF; u++) {
-                            int64_t row = r0 + tid + (int64_t)u * BT;
-                            if (row < r1) {
-                                TG wv = fma(-h, vc[u], ws[row - r0]);
-                                ws[row - r0] = wv;
+                            int64_t row = m0 + tid + (int64_t)u * BT;
+                            if (row < m1) {
+                                TG wv = fma(-h, vc[u], ws[row - m0]);
+                                ws[row - m0] = wv;
                                 wbuf[row] = wv;
                                 part = fma(wv, wv, part);
                             }
                         }
-                        for (int64_t row = r0 + tid + (int64_t)PF * BT; row < r1; row += BT) {
-                            TG wv = fma(-h, Vi[row], ws[row - r0]);
-                            ws[row - r0] = wv;
+                        for (int64_t row = m0 + tid + (int64_t)PF * BT; row < m1; row += BT) {
+                            TG wv = fma(-h, ldcg(&Vi[row]), ws[row - m0]);
+                            ws[row - m0] = wv;
                             wbuf[row] = wv;
                             part = fma(wv, wv, part);
                         }
                     }
                 }
                 }
+                // outside the group part is 0; block 0 stores the rotated diagonal
+                // entry h_jj (rotations 0..j-1 applied) in the unused last row of R's
+                // column j for the blocks outside the group
+                if (!gs) part = TG(0);
+                if (sub && !a.orth && blockIdx.x == 0 && tid == GT) a.R[(size_t)j * (kmax + 1) + kmax] = hc[j];
                 TG hsq;
                 if (!xsum<true>(a, sh, redg, part, hsq)) return;
                 const TG hn = sqrt(hsq);
-                // ---- v_{j+1} = w / h_{j+1,j} (own rows)
+                if (sub && !a.orth && !gs && tid == GT) hc[j] = __ldcg(&a.R[(size_t)j * (kmax + 1) + kmax]);
+                // ---- v_{j+1} = w / h_{j+1,j} (own rows; with a group from the published w)
                 if (hn > TG(0)) {
                     TG* Vn = V + (int64_t)(j + 1) * a.ldv;
-                    for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ws[row - r0] / hn;
+                    if (sub) {
+                        for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ldcg(&wbuf[row]) / hn;
+                    } else {
+                        for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ws[row - r0] / hn;
+                    }
                 }
                 // ---- the new Givens rotation in double (identical in every block);
                 // rotations 0..j-1 were applied to this column during the rounds
@@ -735,8 +782,19 @@ int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, int* grid_out)
     a.rb = ((a.n + G - 1) / G + 31) & ~int64_t(31);
     G = (a.n + a.rb - 1) / a.rb;
     const int64_t nsl = (a.rb + 31) >> 5;
-    const size_t smem = sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + a.rb * sizeof(TG) + 64;
-    SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // Gram-Schmidt group: on large grids the scalar rounds run among half the
+    // blocks (each over two blocks' rows); a round among 76 blocks took
+    // ~1.2 us against ~1.7 us among 152, which outweighs the extra barrier
+    // that publishes w once per iteration.  CGS2 has no scalar rounds.
+    a.g2 = (!a.orth && G >= MGS_GROUP_MIN_GRID) ? (int)((G + 1) / 2) : 0;
+    auto smem_for = [&](int g2) {
+        return sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + (g2 ? 2 : 1) * a.rb * sizeof(TG) + 64;
+    };
+    size_t dyn_max = 0;
+    SPAI_CUDA_TRY(allow_max_dynamic_smem(kern, &dyn_max));
+    if (a.g2 && smem_for(a.g2) > dyn_max) a.g2 = 0;  // the doubled row range does not fit
+    const size_t smem = smem_for(a.g2);
+    if (smem > dyn_max) return SPAI_ERR_UNSUPPORTED;
     int occ = 0;
     constexpr int threads = ir_threads<TG, TP>();
     SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
@@ -853,7 +911,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     TRY(dev_alloc(&tbuf, (size_t)sp * n, s));
     TRY(dev_alloc(&V, (size_t)sg * ldv * (kmax + 1), s));
     TRY(dev_alloc((void**)&R, sizeof(double) * (size_t)(kmax + 1) * kmax, s));
-    TRY(dev_alloc((void**)&msg, sizeof(unsigned long long) * 2 * MAX_GRID * SLOT_WORDS, s));
+    TRY(dev_alloc((void**)&msg, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
     TRY(dev_alloc((void**)&nbe, sizeof(double) * (imax + 1), s));
     TRY(dev_alloc((void**)&its, sizeof(int) * (imax + 1), s));
     TRY(dev_alloc((void**)&outv, sizeof(int) * 2, s));
@@ -868,7 +926,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     CTRY(cudaMemsetAsync(its, 0, sizeof(int) * (imax + 1), s));
     CTRY(cudaMemsetAsync(outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(msg, 0, sizeof(unsigned long long) * 2 * MAX_GRID * SLOT_WORDS, s));
+    CTRY(cudaMemsetAsync(msg, 0, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
     CTRY(cudaEventRecord(e0, s));
     // A and P in u_p, SELL-32 (P's copy is cached on the preconditioner)
     TRY(sell_build(n, A.rowptr, A.col, A.val, o->up, num_sms, s, &As, &nl));
@@ -912,6 +970,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         if (Ps) { a.P.off = Ps->off; a.P.col = Ps->col; a.P.val = Ps->val; }
         a.arp = A.rowptr; a.aci = A.col; a.aval = A.val;
         a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
+        a.msg2 = msg + 2 * MAX_GRID * SLOT_WORDS;
         a.err = err;
         int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
         if (clk_khz <= 0) clk_khz = 2000000;
@@ -1139,7 +1198,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     const int64_t ldv = (n + 31) & ~int64_t(31);
     const int64_t nsl = (n + 31) >> 5;
     Carve cv{base, 0, (size_t)SPAI_NOALLOC_SCRATCH_BYTES};
-    const size_t msg_bytes = sizeof(unsigned long long) * 2 * MAX_GRID * SLOT_WORDS;
+    const size_t msg_bytes = sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS;
     const size_t ctrl_bytes = sizeof(int) * 4 + sizeof(int) * (imax + 1) + sizeof(double) * (imax + 1) +
                               sizeof(unsigned long long) * 3 + 64;
     unsigned long long* msg = (unsigned long long*)cv.take(msg_bytes);
@@ -1231,6 +1290,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     if (P) { a.P.off = poff; a.P.col = pcol; a.P.val = pval; }
     a.arp = A->rowptr; a.aci = A->col; a.aval = A->val;
     a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
+    a.msg2 = msg + 2 * MAX_GRID * SLOT_WORDS;
     a.err = err;
     int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
     if (clk_khz <= 0) clk_khz = 2000000;

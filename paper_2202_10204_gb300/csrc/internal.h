@@ -72,6 +72,23 @@ struct spai_ctx_s {
 // cudaDeviceGetAttribute, asked once per process for each (attribute, device); 0 on failure
 int device_attr_cached(cudaDeviceAttr attr, int device);
 
+// Let `kernel` launch with as much dynamic shared memory as the device's
+// opt-in limit leaves beside its static shared memory; *dyn gets that size.
+// The attribute is global to the kernel, so it is set to the maximum (once
+// per kernel and device) rather than to one launch's size: with serving
+// workers launching the same kernel from several threads, a per-launch value
+// set by one thread could be lowered by another between its
+// cudaFuncSetAttribute and its launch.
+cudaError_t allow_max_dynamic_smem_ptr(const void* kernel, size_t* dyn);
+template <class K>
+inline cudaError_t allow_max_dynamic_smem(K* kernel, size_t* dyn = nullptr)
+{
+    size_t d = 0;
+    cudaError_t e = allow_max_dynamic_smem_ptr((const void*)kernel, &d);
+    if (dyn) *dyn = d;
+    return e;
+}
+
 // stream-ordered device allocation helpers
 int dev_alloc(void** p, size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);

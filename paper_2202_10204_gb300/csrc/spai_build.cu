@@ -438,7 +438,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
         const int wpb = 4;
         const size_t sm = (size_t)(cap + 32 * stride) * 4 * wpb;
         if (sm > smem_cap) { rc = SPAI_ERR_UNSUPPORTED; goto done; }
-        SPAI_CUDA_TRY(cudaFuncSetAttribute(k_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        SPAI_CUDA_TRY(allow_max_dynamic_smem(k_pattern));
         int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms * 64);
         if (blocks < 1) blocks = 1;
         k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, A.rowptr, A.col, A.val, cp, ri, Jidx, Jcnt,

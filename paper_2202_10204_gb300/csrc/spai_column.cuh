@@ -717,7 +717,7 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
         else if (MMsel == 64) kern = k_spai<S, false, 64>;
         else kern = k_spai<S, false, 0>;
     }
-    SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SPAI_CUDA_TRY(allow_max_dynamic_smem(kern));
     int64_t blocks = (a.n + wpb - 1) / wpb;
     const int64_t cap = (int64_t)num_sms * 64;
     if (blocks > cap) blocks = cap;

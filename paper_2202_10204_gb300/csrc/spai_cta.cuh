@@ -431,7 +431,7 @@ int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t sme
     if (smem > smem_cap) return SPAI_ERR_UNSUPPORTED;
     a.warp_bytes = (int)smem;
     void (*kern)(SpaiArgs) = adaptive ? k_spai_cta<S, true, NW> : k_spai_cta<S, false, NW>;
-    SPAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SPAI_CUDA_TRY(allow_max_dynamic_smem(kern));
     int occ = 0;
     SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * NW, smem));
     if (occ < 1) return SPAI_ERR_UNSUPPORTED;

@@ -176,6 +176,20 @@ def test_ir_3d_half_single(ctx):
     check_ir(A, b, x_true, x, st, ref, 2.0 ** -24)
 
 
+@pytest.mark.parametrize("tup", [("half", "single", "single", "single", "double"),
+                                 ("single", "double", "double", "double", "double")])
+def test_ir_gram_schmidt_group(ctx, tup):
+    # n = 27^3 = 19683: 77 blocks of 256 rows, so the Gram-Schmidt rounds run among
+    # 39 blocks that each hold two blocks' rows (the last one a single, ragged block)
+    uf, u, ug, up, ur = tup
+    A = synth.conv_diff_3d(27, 50.0, seed=11)
+    b, x_true = synth.rhs(A, seed=12)
+    tau = 1e-4 if ug == "single" else 1e-8
+    x, st, ref = run_pair(ctx, A, b, O.PAT_A2, 25, uf, u, ug, up, ur, tau)
+    assert st["grid"] >= 64
+    check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
+
+
 @pytest.mark.parametrize("tup", [("single", "double", "single", "single", "double"),
                                  ("half", "single", "single", "double", "double"),
                                  ("double", "double", "double", "double", "double"),
