@@ -149,6 +149,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- algorithmic bytes
 
+# DRAM bytes (read + write) of one k_ir launch on the 64^3 workload, from one ncu capture of this
+# kernel build (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the timed launch): the
+# algorithmic bytes are 13.6 GB; A, P and the recent basis vectors stay in L2.
+K_IR_DRAM_BYTES_64CUBE = 5.129e9
+
+
 def ir_kernel_bytes(n, nnz_a, nnz_p, its, s_u=4, s_g=4, s_p=4):
     """Algorithmic HBM bytes of one refinement-kernel launch.
 
@@ -512,7 +518,8 @@ def main():
             ir=dict(steps=last["steps"], its=last["its"], total_its=last["total_its"], grid=last["grid"],
                     backward_error=nbe, forward_error=fe, nbe_trace=last["nbe"]),
             roofline=dict(kernel="k_ir (persistent refinement kernel)", bound="hbm", achieved=achieved,
-                          peak=hbm_peak, unit="GB/s", frac=achieved / hbm_peak, traffic=None,
+                          peak=hbm_peak, unit="GB/s", frac=achieved / hbm_peak,
+                          traffic=K_IR_DRAM_BYTES_64CUBE if args.grid == 64 else None,
                           peak_source=peak_src, algorithmic_bytes_per_launch=float(np.mean(ir_bytes))),
             gpu_launches=launches,
             arnoldi_cgs2=cgs2,

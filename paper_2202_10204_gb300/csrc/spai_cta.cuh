@@ -192,7 +192,11 @@ __global__ void __launch_bounds__(32 * NW, 1) k_spai_cta(SpaiArgs a)
                 __syncthreads();
                 break;
             }
-            // ---- Householder QR, tile in registers: warp w rows [32w, 32w+32), lane t column t
+            // ---- Householder QR, tile in registers: warp w rows [32w, 32w+32), lane t column t.
+            // Warps whose rows all lie beyond |I_k| hold zeros: they skip the
+            // arithmetic and only take part in the barriers.
+            const int nwa = (m + 31) >> 5;
+            const bool wact = wid < nwa;
             C col[32];
 #pragma unroll
             for (int r = 0; r < 32; r++) {
@@ -202,23 +206,27 @@ __global__ void __launch_bounds__(32 * NW, 1) k_spai_cta(SpaiArgs a)
             const int steps = nj < m ? nj : m;
             for (int c = 0; c < steps; c++) {
                 // publish the pivot column (rows >= c) and the pivot row
+                if (wact) {
 #pragma unroll
-                for (int r = 0; r < 32; r++) {
-                    const int row = 32 * wid + r;
-                    if (lane == c) T.v[row] = row >= c ? col[r] : C(0);
-                    if (wid == 0 && r == c && lane <= nj) T.arow[lane] = col[r];
+                    for (int r = 0; r < 32; r++) {
+                        const int row = 32 * wid + r;
+                        if (lane == c) T.v[row] = row >= c ? col[r] : C(0);
+                        if (wid == 0 && r == c && lane <= nj) T.arow[lane] = col[r];
+                    }
                 }
                 __syncthreads();
-                C g0 = 0, g1 = 0;
+                if (wact) {
+                    C g0 = 0, g1 = 0;
 #pragma unroll
-                for (int r = 0; r < 32; r += 2) {
-                    g0 = fma(T.v[32 * wid + r], col[r], g0);
-                    g1 = fma(T.v[32 * wid + r + 1], col[r + 1], g1);
+                    for (int r = 0; r < 32; r += 2) {
+                        g0 = fma(T.v[32 * wid + r], col[r], g0);
+                        g1 = fma(T.v[32 * wid + r + 1], col[r + 1], g1);
+                    }
+                    T.P[wid * 33 + lane] = g0 + g1;
                 }
-                T.P[wid * 33 + lane] = g0 + g1;
                 __syncthreads();
                 C g = 0, sig2 = 0;
-                for (int w = 0; w < NW; w++) {
+                for (int w = 0; w < nwa; w++) {
                     g += T.P[w * 33 + lane];
                     sig2 += T.P[w * 33 + c];
                 }
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(32 * NW, 1) k_spai_cta(SpaiArgs a)
                     const C alpha = x0 >= C(0) ? -nrm : nrm;
                     const C v0 = rnd<S>(x0 - alpha);
                     const C vtv = C(2) * nrm * (nrm + fabs(x0));
-                    if (lane > c && lane <= nj) {
+                    if (wact && lane > c && lane <= nj) {
                         const C act = T.arow[lane];
                         const C sv = g + (v0 - x0) * act;
                         const C f = rnd<S>((sv + sv) / vtv);
