@@ -47,6 +47,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cgs2", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the double-precision, adaptive and serving lines")
+    p.add_argument("--sweep", action="store_true",
+                   help="instead of the bench line: the eps trade-off of adaptive SPAI against fixed patterns "
+                        "and no preconditioner (one JSON line)")
     return p.parse_args()
 
 
@@ -343,12 +346,71 @@ def extra_workloads(S, synth, torch, dev):
     return out
 
 
+def run_sweep(args):
+    """The paper's trade-off between the SPAI stopping tolerance eps, the fill of P and the GMRES
+    iterations (its Section 5 discussion and figures), on two synthetic stand-ins: adaptive SPAI
+    from the identity for eps in 0.1..0.9 against the fixed patterns pattern(A), pattern(A^2) and
+    against no preconditioner.  Per run: nnz(P)/n, the refinement steps and GMRES iterations, the
+    final backward error, SPAI and refinement milliseconds (CUDA events of the library)."""
+    import numpy as np
+    import torch
+
+    import paper_2202_10204_gb300 as S
+    from paper_2202_10204_gb300 import synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(0, stream=stream)
+    cases = [
+        ("3D conv-diff 32^3 (n=32768), Peclet 50, (half,single,single,single,double), tau 1e-4",
+         synth.conv_diff_3d(32, 50.0, seed=3), dict(uf="half", u="single", ug="single", up="single", ur="double",
+                                                    tau=1e-4), "half"),
+        ("random nonsymmetric n=20000, 12 nnz/col, scaling 1e3, (single,double,single,single,double), tau 1e-4",
+         synth.random_sparse(20000, 12, seed=31, log10_scale=3.0),
+         dict(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4), "single"),
+    ]
+    out = []
+    for name, A, io_kw, uf in cases:
+        b, xt = synth.rhs(A, seed=5)
+        n = len(A[0]) - 1
+        Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+        bd = torch.from_numpy(b).to(dev)
+        io = S.make_ir_opts(**io_kw)
+        Ms = synth.to_scipy(A)
+        runs = []
+        configs = [("none", None)]
+        configs += [("pattern(A)", S.make_spai_opts(init=1, max_fill=30, uf=uf))]
+        configs += [("pattern(A^2)", S.make_spai_opts(init=2, max_fill=30, uf=uf))]
+        for eps in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9):
+            configs.append(("adaptive eps=%.1f" % eps,
+                            S.make_spai_opts(init=0, adaptive=True, eps=eps, beta=8, max_fill=30, uf=uf)))
+        for label, so in configs:
+            P, sst = (None, None)
+            if so is not None:
+                P, sst = S.spai_build(ctx, Ad, so)
+            xd = torch.zeros_like(bd)
+            st = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io)
+            x = xd.cpu().numpy()
+            nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+            runs.append(dict(precond=label, nnz_P_per_n=(sst["nnz_P"] / n) if sst else 0.0,
+                             cols_converged=sst["cols_converged"] if sst else None,
+                             steps=st["steps"], its=st["its"], total_its=st["total_its"], backward_error=nbe,
+                             spai_ms=sst["ms"] if sst else 0.0, ir_ms=st["ms_ir"]))
+            if P is not None:
+                P.free()
+        out.append(dict(workload=name, n=n, runs=runs))
+    ctx.close()
+    print(json.dumps(dict(sweep="eps trade-off", data="synthetic", cases=out)))
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     import torch
     import torch.distributed as dist
 

@@ -16,6 +16,7 @@ import subprocess
 import threading
 
 import numpy as np
+import scipy.sparse as sp
 
 HALF, SINGLE, DOUBLE, QUAD = 0, 1, 2, 3
 PREC_NAMES = {"half": HALF, "single": SINGLE, "double": DOUBLE, "quad": QUAD}
@@ -54,13 +55,15 @@ class SpaiOpts(C.Structure):
 
 
 class GmresOpts(C.Structure):
-    _fields_ = [("ug", C.c_int), ("up", C.c_int), ("tau", C.c_double), ("maxit", C.c_int), ("orth", C.c_int)]
+    _fields_ = [("ug", C.c_int), ("up", C.c_int), ("tau", C.c_double), ("maxit", C.c_int), ("orth", C.c_int),
+                ("side", C.c_int)]
 
 
 class IrOpts(C.Structure):
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int),
                 ("ur", C.c_int), ("mode", C.c_int), ("tau", C.c_double),
-                ("gmres_maxit", C.c_int), ("imax", C.c_int), ("stop_tol", C.c_double), ("orth", C.c_int)]
+                ("gmres_maxit", C.c_int), ("imax", C.c_int), ("stop_tol", C.c_double), ("orth", C.c_int),
+                ("side", C.c_int)]
 
 
 def lib():
@@ -199,6 +202,34 @@ def assemble_P(S, up="double", uf=None):
     return rowptr, col, val_up, val_uf
 
 
+def transpose_csr(A):
+    """CSR of A^T (sorted column indices); a library transpose, no arithmetic."""
+    rp, ci, va = _csr(A)
+    n = len(rp) - 1
+    M = sp.csr_matrix((va, ci, rp), shape=(n, n)).T.tocsr()
+    M.sort_indices()
+    return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
+
+
+def spai_right(A, up="double", uf=None, **kw):
+    """Right SPAI (A P ~ I, reading R14): the transpose of the left SPAI of A^T.
+
+    Algorithm 1 run on (A^T)^T D = A D with D scaling the columns of A gives
+    M ~ (A D)^{-1}; the left assembly of that run is M^T D, whose transpose
+    D M satisfies A (D M) ~ I.  Returns (S, P) with S the run's dict (per
+    column of M, i.e. per row of P^T) and P = (rowptr, col, val_up, val_uf).
+    """
+    S = spai(transpose_csr(A), **kw)
+    rp, ci, vup, vuf = assemble_P(S, up, uf)
+    n = S["n"]
+    perm = sp.csr_matrix((np.arange(len(ci), dtype=np.float64) + 1.0, ci, rp), shape=(n, n)).T.tocsr()
+    perm.sort_indices()
+    idx = perm.data.astype(np.int64) - 1
+    P = (perm.indptr.astype(np.int64), perm.indices.astype(np.int32), vup[idx],
+         None if vuf is None else vuf[idx])
+    return S, P
+
+
 def spmv(A, x, p="double", mode=MODE_PEROP):
     rp, ci, va = _csr(A)
     n = len(rp) - 1
@@ -222,17 +253,19 @@ def residual(A, b, x, ur="double", u="double"):
 
 
 ORTH_MGS, ORTH_CGS2 = 0, 1
+SIDE_LEFT, SIDE_RIGHT = 0, 1
 
 
-def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORTH_MGS):
-    """One left-preconditioned GMRES solve of (P A) d = P r from d = 0 (MGS or CGS2)."""
+def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORTH_MGS, side=SIDE_LEFT):
+    """One GMRES solve from d = 0 (MGS or CGS2): left, (P A) d = P r; right, (A P) u = r and d = P u."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     r = np.ascontiguousarray(r, dtype=np.float64)
     d = np.zeros(n)
     bd = C.c_int(0)
     rr = C.c_double(0.0)
-    o = GmresOpts(prec(ug), prec(up), float(tau), int(maxit if maxit is not None else min(n, 500)), int(orth))
+    o = GmresOpts(prec(ug), prec(up), float(tau), int(maxit if maxit is not None else min(n, 500)), int(orth),
+                  int(side))
     if P is None:
         pp = (None, None, None)
     else:
@@ -251,15 +284,17 @@ def default_stop_tol(A, u) -> float:
 
 
 def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur="quad",
-             tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32, orth=ORTH_MGS):
-    """SPAI-GMRES-IR (Algorithm 3) given P = (rowptr, col, val_up, val_uf) or None."""
+             tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32, orth=ORTH_MGS, side=SIDE_LEFT):
+    """SPAI-GMRES-IR (Algorithm 3) given P = (rowptr, col, val_up, val_uf) or None; side selects left
+    (Algorithm 3) or right preconditioning of the GMRES solves (reading R14)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
     if stop_tol is None:
         stop_tol = default_stop_tol(A, u)
     o = IrOpts(prec(uf), prec(u), prec(ug), prec(up), prec(ur), int(mode), float(tau),
-               int(gmres_maxit if gmres_maxit is not None else min(n, 500)), int(imax), float(stop_tol), int(orth))
+               int(gmres_maxit if gmres_maxit is not None else min(n, 500)), int(imax), float(stop_tol), int(orth),
+               int(side))
     x = np.zeros(n)
     its = np.zeros(imax + 1, dtype=np.int32)
     nbe = np.full(imax + 1, np.nan)

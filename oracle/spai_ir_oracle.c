@@ -55,6 +55,12 @@
  *   R11 an augmentation whose new shadow |I_k| exceeds max_shadow (the
  *       CUDA tile height, 512 rows) is undone and the column keeps its
  *       previous pattern and solve (flag CF_TOOBIG).
+ *   R14 right preconditioning (the paper leaves it as future work at the
+ *       end of Section 3): GMRES on (A P) u = r from u = 0, w = A (P v_j)
+ *       with both products in u_p, the initial vector r rounded to u_p and
+ *       u_g (as with P = I), and the correction d = P (V_k y) in u_p,
+ *       stored in u_g.  The right SPAI (A P ~ I) is the transpose of the
+ *       left SPAI of A^T (Algorithm 1 run on A D, D scaling the columns of A).
  */
 #include <math.h>
 #include <stdint.h>
@@ -564,10 +570,16 @@ typedef struct {
     int maxit;       /* iteration cap */
     int orth;        /* 0: modified Gram-Schmidt (the paper's MGS-GMRES);
                         1: classical Gram-Schmidt applied twice (CGS2) */
+    int side;        /* 0: left preconditioning (Algorithm 3);
+                        1: right preconditioning, the variant the paper leaves
+                        as future work at the end of Section 3 */
 } orc_gmres_opts;
 
 /*
- * Solve (P A) d = P r from d0 = 0.  P may be NULL (P = I).  The result d is
+ * Left (side 0): solve (P A) d = P r from d0 = 0.  Right (side 1): solve
+ * (A P) u = r from u0 = 0 and return d = P u; the Givens estimate |g_k|/beta
+ * is then the unpreconditioned relative residual ||r - A d|| / ||r|| of exact
+ * arithmetic.  P may be NULL (P = I, both sides coincide).  The result d is
  * in u_g precision values.  Returns the number of iterations; *breakdown is
  * set when h_{j+1,j} = 0.  relres receives |g_k| / beta (or 0).
  */
@@ -584,8 +596,9 @@ int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
     double* sn = (double*)calloc((size_t)K + 1, sizeof(double));
     double* g = (double*)calloc((size_t)K + 2, sizeof(double));
     *breakdown = 0;
-    /* z = P r in u_p, stored in u_g */
-    if (prp) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, w);
+    const int right = o->side == 1;
+    /* left: z = P r in u_p; right: z = r; stored in u_g */
+    if (prp && !right) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, w);
     else for (int i = 0; i < n; i++) w[i] = rnd(r[i], up);
     for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
     double beta = rnd(sqrt(dot_p(w, 1, w, 1, n, ug, MODE_PEROP)), ug);
@@ -600,10 +613,15 @@ int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
     g[0] = beta;
     int k = 0;
     for (int j = 0; j < K; j++) {
-        /* w = P (A v_j), both products in u_p */
-        spmv_p(n, arp, aci, av, V[j], up, MODE_PEROP, t);
-        if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
-        else for (int i = 0; i < n; i++) w[i] = t[i];
+        /* left: w = P (A v_j); right: w = A (P v_j); both products in u_p */
+        if (right && prp) {
+            spmv_p(n, prp, pci, pv, V[j], up, MODE_PEROP, t);
+            spmv_p(n, arp, aci, av, t, up, MODE_PEROP, w);
+        } else {
+            spmv_p(n, arp, aci, av, V[j], up, MODE_PEROP, t);
+            if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
+            else for (int i = 0; i < n; i++) w[i] = t[i];
+        }
         for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
         double* h = (double*)calloc((size_t)j + 2, sizeof(double));
         if (o->orth == 0) {
@@ -664,6 +682,11 @@ int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
         for (int i = 0; i < k; i++) acc = rnd(acc + rnd(V[i][q] * rnd(y[i], ug), ug), ug);
         d[q] = acc;
     }
+    if (right && prp) {
+        /* right preconditioning: d = P (V_k y) in u_p, stored in u_g */
+        spmv_p(n, prp, pci, pv, d, up, MODE_PEROP, t);
+        for (int q = 0; q < n; q++) d[q] = rnd(t[q], ug);
+    }
     for (int i = 0; i <= K; i++) free(V[i]);
     free(y); free(t); free(w); free(V); free(H); free(cs); free(sn); free(g);
     return k;
@@ -681,6 +704,7 @@ typedef struct {
     int imax;               /* maximum number of refinement steps */
     double stop_tol;        /* R8 backward-error threshold */
     int orth;               /* 0 MGS, 1 CGS2 */
+    int side;               /* 0 left, 1 right preconditioning */
 } orc_ir_opts;
 
 /*
@@ -710,7 +734,7 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
     if (prp) spmv_p(n, prp, pci, pv_uf, b, o->uf, o->mode, x);
     else for (int i = 0; i < n; i++) x[i] = rnd(b[i], o->uf);
     for (int i = 0; i < n; i++) x[i] = rnd(x[i], o->u);
-    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit, o->orth };
+    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit, o->orth, o->side };
     int i;
     *steps = 0;
     for (i = 0; i <= o->imax; i++) {

@@ -499,3 +499,90 @@ def test_gmres_ir_cgs2_matches_mgs_solution():
     assert Rc["steps"] == Rm["steps"]
     assert abs(Rc["total_its"] - Rm["total_its"]) <= 1
     assert np.max(np.abs(Rc["x"] - Rm["x"])) <= 4 * 2.0 ** -53 * np.max(np.abs(Rm["x"]))
+
+
+# ---------------------------------------------------------------- right preconditioning (reading R14)
+
+
+def test_right_gmres_equals_unpreconditioned_on_AP():
+    # right preconditioning: GMRES on (A, P) from the right is GMRES on the product A P, and
+    # its correction is d = P u
+    rng = np.random.default_rng(18)
+    n = 20
+    Ad = rng.normal(size=(n, n)) + 5 * np.eye(n)
+    Pd = np.diag(1.0 / np.diag(Ad)) + 0.01 * rng.normal(size=(n, n))
+    r = rng.normal(size=n)
+    d1, k1, _, _ = O.gmres(dense_to_csr(Ad), r, dense_to_csr(Pd), tau=1e-10, side=O.SIDE_RIGHT)
+    u2, k2, _, _ = O.gmres(dense_to_csr(Ad @ Pd), r, None, tau=1e-10)
+    assert k1 == k2
+    np.testing.assert_allclose(d1, Pd @ u2, rtol=1e-8, atol=1e-10)
+
+
+def test_right_gmres_estimate_is_the_true_residual():
+    # the Givens estimate of right-preconditioned GMRES is ||r - A d|| / ||r|| (exact arithmetic);
+    # the left one is the preconditioned residual ||P (r - A d)|| / ||P r||
+    rng = np.random.default_rng(19)
+    n = 40
+    Ad = rng.normal(size=(n, n)) + 8 * np.eye(n)
+    Pd = np.linalg.inv(Ad + 0.5 * rng.normal(size=(n, n)))
+    r = rng.normal(size=n)
+    for side in (O.SIDE_LEFT, O.SIDE_RIGHT):
+        d, k, _, rr = O.gmres(dense_to_csr(Ad), r, dense_to_csr(Pd), tau=1e-6, side=side)
+        if side == O.SIDE_RIGHT:
+            true = np.linalg.norm(r - Ad @ d) / np.linalg.norm(r)
+        else:
+            true = np.linalg.norm(Pd @ (r - Ad @ d)) / np.linalg.norm(Pd @ r)
+        assert rr <= 1e-6 and abs(true - rr) <= 1e-9, (side, k, rr, true)
+
+
+def test_right_gmres_without_preconditioner_is_left():
+    A = synth.conv_diff_2d(10, 20.0, 1.0, 0.1, seed=3)
+    r = np.random.default_rng(2).normal(size=100)
+    d1, k1, _, _ = O.gmres(A, r, None, ug="single", up="single", tau=1e-4)
+    d2, k2, _, _ = O.gmres(A, r, None, ug="single", up="single", tau=1e-4, side=O.SIDE_RIGHT)
+    assert k1 == k2 and np.array_equal(d1, d2)
+
+
+def test_spai_right_full_pattern_gives_inverse_from_the_right():
+    rng = np.random.default_rng(21)
+    n = 10
+    Ad = rng.normal(size=(n, n)) + 4 * np.eye(n)
+    A = dense_to_csr(Ad)
+    S, (rp, col, val, _) = O.spai_right(A, up="double", init=O.PAT_A, uf="double", max_fill=n, eps=1e-12)
+    P = sp.csr_matrix((val, col, rp), shape=(n, n)).toarray()
+    np.testing.assert_allclose(Ad @ P, np.eye(n), atol=1e-12 * np.linalg.cond(Ad))
+    # and right-preconditioned GMRES on A P = I converges in one iteration
+    b = rng.normal(size=n)
+    d, k, bd, rr = O.gmres(A, b, (rp, col, val), tau=1e-10, side=O.SIDE_RIGHT)
+    assert k == 1
+    np.testing.assert_allclose(Ad @ d, b, atol=1e-10)
+
+
+def test_spai_right_columns_minimise_the_right_residual():
+    # the right SPAI's column k minimises ||A D m - e_k|| over its pattern (Algorithm 1 on A D):
+    # check against numpy lstsq on the columns of A D for a random sparse matrix
+    A = synth.random_sparse(60, 4, seed=9)
+    Ms = synth.to_scipy(A).toarray()
+    S, (rp, col, val, _) = O.spai_right(A, up="double", init=O.PAT_A, uf="double", max_fill=10, eps=0.0)
+    dcol = 1.0 / np.max(np.abs(Ms), axis=0)
+    B = Ms * dcol[None, :]
+    P = sp.csr_matrix((val, col, rp), shape=(60, 60)).toarray()
+    for k in (0, 7, 33, 59):
+        J = S["Jidx"][k][: S["Jcnt"][k]]
+        e = np.zeros(60); e[k] = 1.0
+        m, *_ = np.linalg.lstsq(B[:, J], e, rcond=None)
+        # column k of P = D m (rows J)
+        np.testing.assert_allclose(P[J, k], dcol[J] * m, rtol=1e-10, atol=1e-14)
+        assert np.count_nonzero(P[:, k]) == len(J)
+
+
+def test_ir_right_reaches_working_accuracy():
+    A, b, x_true = synth.cfg_small_2d()
+    S, P = O.spai_right(A, up="double", uf="single", init=O.PAT_A, max_fill=30)
+    r = O.gmres_ir(A, b, P, uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4,
+                   side=O.SIDE_RIGHT)
+    Ms = synth.to_scipy(A)
+    x = r["x"]
+    nbe = np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b)))
+    assert r["steps"] >= 1 and nbe <= 5 * 2.0 ** -53
+    assert np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)) < 1e-12
