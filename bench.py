@@ -199,9 +199,10 @@ def job_throughput(world, steps, max_ms):
 # ---------------------------------------------------------------- other workloads (reported beside the headline)
 
 def extra_workloads(S, synth, torch, dev):
-    """Four secondary lines, each bounded to a few seconds:
+    """Five secondary lines, each bounded to a few seconds:
     * u = double: the 32x32 2D system with (single, double, double, double, quad), the
       configuration whose backward error must reach 1e-15;
+    * right: the 64^3 workload with the right SPAI (A P ~ I) and right-preconditioned GMRES;
     * adaptive: Grote-Huckle SPAI from the identity on a 100,000-column random nonsymmetric
       matrix (16 nonzeros per column, row/column scaling 1e6), eps 0.5, beta 8, fill cap 30,
       u_f single, then the solve with (single, double, double, double, quad);
@@ -238,6 +239,30 @@ def extra_workloads(S, synth, torch, dev):
                                      "(single,double,double,double,quad), tau 1e-4",
                             solves_per_s=reps / (e0.elapsed_time(e1) / 1000.0), backward_error=nbe,
                             its=st["its"], steps=st["steps"])
+    # ---- right preconditioning on the 64^3 workload (SPAI with A P ~ I, GMRES on A P)
+    A, b, xt = synth.cfg_large_3d(N=64)
+    Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros_like(bd)
+    so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3, side=S.SIDE_RIGHT)
+    io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4, side=S.SIDE_RIGHT)
+    for _ in range(2):
+        S.gmres_ir_solve(ctx, Ad, bd, xd, sopts=so, opts=io)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        st = S.gmres_ir_solve(ctx, Ad, bd, xd, sopts=so, opts=io)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    Ms = synth.to_scipy(A)
+    x = xd.cpu().numpy()
+    nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+    out["right_64cube"] = dict(workload="the 64^3 workload with the right SPAI (A P ~ I) and right-preconditioned "
+                                        "GMRES; spai_build + solve per step, device inputs",
+                               solves_per_s=reps / (e0.elapsed_time(e1) / 1000.0), its=st["its"], steps=st["steps"],
+                               backward_error=nbe, ms_spai=st["ms_spai"], ms_ir=st["ms_ir"])
     # ---- adaptive
     A = synth.random_sparse(100_000, 16, seed=6, log10_scale=6.0)
     b, xt = synth.rhs(A, seed=7)

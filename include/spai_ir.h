@@ -91,6 +91,14 @@ typedef struct {
     spai_prec uf;           /* precision of the construction (half/single/double) */
     int scale;              /* 1: run on A^T D (recommended), 0: on A^T           */
     int rho_restricted;     /* 1: rho_jk uses ||b_j(I_k)|| (literal Algorithm 1)  */
+    int side;               /* 0: left preconditioner P ~ A^{-1} with P A ~ I (the
+                               paper's Section 3: Algorithm 1 on A^T D, P = M^T D);
+                               1: right preconditioner with A P ~ I (Algorithm 1 on
+                               A D, D scaling the columns of A, P = D M; the variant
+                               the paper leaves as future work at the end of
+                               Section 3).  Patterns then refer to A^T: pattern(A)
+                               gives pattern(P) = pattern(A).  Per-column stats
+                               describe the columns of M, i.e. the columns of P.  */
 } spai_opts;
 
 /* Algorithm 3 parameters: the five precisions, tau, i_max and the stop rule. */
@@ -106,6 +114,11 @@ typedef struct {
                                     paper's MGS-GMRES), 1 classical Gram-Schmidt applied
                                     twice (CGS2: two vector reductions per iteration instead
                                     of j+1 scalar ones) */
+    int side;                    /* 0: left preconditioning (Algorithm 3: GMRES on P A d = P r,
+                                    tau bounds ||P(r - A d)||/||P r||); 1: right preconditioning
+                                    (GMRES on A P u = r, d = P u, tau bounds ||r - A d||/||r||;
+                                    future work in the paper's Section 3).  Ignored when P is
+                                    NULL. */
 } ir_opts;
 
 #define SPAI_IR_MAX_STEPS 64

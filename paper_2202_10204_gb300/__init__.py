@@ -6,8 +6,8 @@ The numerical work lives in the CUDA library (``csrc/``, C ABI in
 ``include/spai_ir.h``); ``_lib`` is its ctypes binding and ``synth`` builds
 seeded test systems.
 """
-from ._lib import (Context, Precond, SpaiError, gmres_ir_solve, make_ir_opts, make_spai_opts, solver_poll,
-                   solver_submit, spai_build, strerror)
+from ._lib import (SIDE_LEFT, SIDE_RIGHT, Context, Precond, SpaiError, gmres_ir_solve, make_ir_opts, make_spai_opts,
+                   solver_poll, solver_submit, spai_build, strerror)
 
-__all__ = ["Context", "Precond", "SpaiError", "gmres_ir_solve", "make_ir_opts", "make_spai_opts", "solver_poll",
-           "solver_submit", "spai_build", "strerror"]
+__all__ = ["SIDE_LEFT", "SIDE_RIGHT", "Context", "Precond", "SpaiError", "gmres_ir_solve", "make_ir_opts",
+           "make_spai_opts", "solver_poll", "solver_submit", "spai_build", "strerror"]

@@ -35,16 +35,19 @@ class spai_csr(C.Structure):
                 ("val", C.c_void_p), ("on_device", C.c_int)]
 
 
+SIDE_LEFT, SIDE_RIGHT = 0, 1
+
+
 class spai_opts(C.Structure):
     _fields_ = [("init", C.c_int), ("adaptive", C.c_int), ("eps", C.c_double), ("alpha", C.c_int),
                 ("beta", C.c_int), ("max_fill", C.c_int), ("uf", C.c_int), ("scale", C.c_int),
-                ("rho_restricted", C.c_int)]
+                ("rho_restricted", C.c_int), ("side", C.c_int)]
 
 
 class ir_opts(C.Structure):
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int), ("ur", C.c_int),
                 ("tau", C.c_double), ("gmres_max_it", C.c_int), ("ir_max_steps", C.c_int), ("stop", C.c_int),
-                ("stop_tol", C.c_double), ("orth", C.c_int)]
+                ("stop_tol", C.c_double), ("orth", C.c_int), ("side", C.c_int)]
 
 
 class spai_stats(C.Structure):
@@ -138,16 +141,18 @@ def make_csr(A, on_device=None):
 
 
 def make_spai_opts(init=PAT_A, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fill=30, uf="single", scale=True,
-                   rho_restricted=False):
+                   rho_restricted=False, side=SIDE_LEFT):
+    """side: SIDE_LEFT (P A ~ I, the paper's) or SIDE_RIGHT (A P ~ I)."""
     return spai_opts(int(init), int(bool(adaptive)), float(eps), int(alpha), int(beta), int(max_fill), _prec(uf),
-                     int(bool(scale)), int(bool(rho_restricted)))
+                     int(bool(scale)), int(bool(rho_restricted)), int(side))
 
 
 def make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8, gmres_max_it=0,
-                 ir_max_steps=10, stop=IR_STOP_BACKWARD, stop_tol=0.0, orth=0):
-    """orth: 0 modified Gram-Schmidt (default, the paper's), 1 classical Gram-Schmidt twice."""
+                 ir_max_steps=10, stop=IR_STOP_BACKWARD, stop_tol=0.0, orth=0, side=SIDE_LEFT):
+    """orth: 0 modified Gram-Schmidt (default, the paper's), 1 classical Gram-Schmidt twice.
+    side: SIDE_LEFT (Algorithm 3) or SIDE_RIGHT (GMRES on A P u = r, d = P u)."""
     return ir_opts(_prec(uf), _prec(u), _prec(ug), _prec(up), _prec(ur), float(tau), int(gmres_max_it),
-                   int(ir_max_steps), int(stop), float(stop_tol), int(orth))
+                   int(ir_max_steps), int(stop), float(stop_tol), int(orth), int(side))
 
 
 class Context:

@@ -78,6 +78,7 @@ struct IrArgs {
     double* nbe;                // imax + 1
     int* out;                   // [0] steps, [1] flags
     int orth;                   // 0 modified Gram-Schmidt, 1 classical Gram-Schmidt twice (CGS2)
+    int side;                   // 0 left preconditioning (P A d = P r), 1 right (A P u = r, d = P u)
     void* pvec;                 // CGS2: 2 parities x gridDim.x x (kmax + 1) partial dot products (u_g)
     unsigned* gcount;           // CGS2: counter of the barrier that publishes them (zeroed)
 };
@@ -374,6 +375,8 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
     const TP* av = (const TP*)a.A.val;
     const TP* pv = (const TP*)a.P.val;
     const bool hasP = a.P.off != nullptr;
+    // the Arnoldi product w = second(first(v)): left P (A v), right A (P v)
+    const bool rightP = hasP && a.side == 1;
     const int64_t s0 = r0 >> 5;
     const int64_t nslg = (a.n + 31) >> 5;
     for (int i = tid; i <= nsl; i += BT) {
@@ -411,9 +414,9 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
         if (a.stop_rule == IR_STOP_BACKWARD && nb <= a.stop_tol) { flags |= 1; break; }
         if (it == a.imax) { flags |= 2; break; }
 
-        // ---------------- z = P r in u_p, stored in u_g; beta = ||z||
+        // ---------------- z = P r (left) or r (right) in u_p, stored in u_g; beta = ||z||
         TG part = TG(0);
-        if (hasP) {
+        if (hasP && !rightP) {
             sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&r[c]); },
                           [&](int64_t row, TP v) { TG z = (TG)v; ws[row - r0] = z; wbuf[row] = z; part = fma(z, z, part); });
         } else {
@@ -434,8 +437,10 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
             TG hdiv = beta;
             bool done = false;
             for (int j = 0; j < kmax && !done; j++) {
-                // ---- t = A v_j in u_p; v_j formed from the published w: fl(w / h)
-                sell_rows<TP>(r0, r1, soa, a.A.col, av, [&](int c) { return (TP)(ldcg(&wbuf[c]) / hdiv); },
+                // ---- t = A v_j (left) or P v_j (right) in u_p; v_j formed from the
+                // published w: fl(w / h)
+                sell_rows<TP>(r0, r1, rightP ? sop : soa, rightP ? a.P.col : a.A.col, rightP ? pv : av,
+                              [&](int c) { return (TP)(ldcg(&wbuf[c]) / hdiv); },
                               [&](int64_t row, TP v) { tbuf[row] = v; });
                 // prefetch v_0 for the first Gram-Schmidt dot while the barrier runs
                 // (with a group the range holds other blocks' rows of v_0, which are
@@ -456,12 +461,14 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                         vc[u] = row < m1 ? ldcg(&V[row]) : TG(0);
                     }
                 }
-                // ---- w = P t in u_p, stored in u_g (own rows, shared memory); first MGS partial
+                // ---- w = P t (left) or A t (right) in u_p, stored in u_g (own rows, shared
+                // memory); first MGS partial
                 part = TG(0);
                 if (sub) {
                     // publish w = P t; the group's blocks then read their double range
                     if (hasP) {
-                        sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return ldcg(&tbuf[c]); },
+                        sell_rows<TP>(r0, r1, rightP ? soa : sop, rightP ? a.A.col : a.P.col, rightP ? av : pv,
+                                      [&](int c) { return ldcg(&tbuf[c]); },
                                       [&](int64_t row, TP v) { wbuf[row] = (TG)v; });
                     } else {
                         for (int64_t row = r0 + tid; row < r1; row += BT) wbuf[row] = (TG)ldcg(&tbuf[row]);
@@ -469,7 +476,8 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                     if (!xbar(a, sh)) return;
                     for (int64_t row = m0 + tid; row < m1; row += BT) ws[row - m0] = ldcg(&wbuf[row]);
                 } else if (hasP) {
-                    sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return ldcg(&tbuf[c]); },
+                    sell_rows<TP>(r0, r1, rightP ? soa : sop, rightP ? a.A.col : a.P.col, rightP ? av : pv,
+                                  [&](int c) { return ldcg(&tbuf[c]); },
                                   [&](int64_t row, TP v) { ws[row - r0] = (TG)v; });
                 } else {
                     for (int64_t row = r0 + tid; row < r1; row += BT) ws[row - r0] = (TG)ldcg(&tbuf[row]);
@@ -650,10 +658,22 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                 }
             }
             __syncthreads();
-            for (int64_t row = r0 + tid; row < r1; row += BT) {
-                TG dsum = TG(0);
-                for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
-                x[row] = (TU)((TU)x[row] + (TU)dsum);
+            if (rightP) {
+                // right preconditioning: d = P (V_k y), the product in u_p stored in u_g
+                for (int64_t row = r0 + tid; row < r1; row += BT) {
+                    TG dsum = TG(0);
+                    for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
+                    wbuf[row] = dsum;
+                }
+                if (!xbar(a, sh)) return;
+                sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&wbuf[c]); },
+                              [&](int64_t row, TP v) { x[row] = (TU)((TU)x[row] + (TU)(TG)v); });
+            } else {
+                for (int64_t row = r0 + tid; row < r1; row += BT) {
+                    TG dsum = TG(0);
+                    for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
+                    x[row] = (TU)((TU)x[row] + (TU)dsum);
+                }
             }
         }
         if (blockIdx.x == 0 && tid == 0) a.its[it] = k;
@@ -871,6 +891,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
     if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
+    if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
     int kmax = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
     if (kmax > n) kmax = (int)n;
     if (kmax > KMAX_LIMIT) return SPAI_ERR_UNSUPPORTED;
@@ -979,7 +1000,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
         a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
         a.its = its; a.nbe = nbe; a.out = outv;
-        a.orth = o->orth; a.pvec = pvec; a.gcount = gcount;
+        a.orth = o->orth; a.pvec = pvec; a.gcount = gcount; a.side = o->side;
         const int rm = o->ur == SPAI_QUAD ? 2 : 1;
         CTRY(cudaEventRecord(ek0, s));
 #define LAUNCH(TU, TG, TP) TRY((launch_ir_rm<TU, TG, TP>(a, rm, num_sms, s, &grid)))
@@ -1171,6 +1192,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     if (!A || !b || !xout || !o) return SPAI_ERR_INVALID_ARG;
     if (!A->on_device || (P && !P->on_device)) return SPAI_ERR_INVALID_ARG;
     if (A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
+    if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
     if (P && (P->n != A->n || P->nnz < 0 || !P->rowptr || !P->col || !P->val)) return SPAI_ERR_INVALID_ARG;
     if (A->n > INT32_MAX) return SPAI_ERR_UNSUPPORTED;
     if (o->u != SPAI_SINGLE && o->u != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
@@ -1299,6 +1321,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
     a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
     a.its = its; a.nbe = nbe; a.out = outv;
+    a.side = o->side;
     const int rm = o->ur == SPAI_QUAD ? 2 : 1;
     int grid = 0;
     if (o->u == SPAI_DOUBLE) {

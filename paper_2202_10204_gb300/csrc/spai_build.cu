@@ -344,10 +344,157 @@ __global__ void k_max_row(int64_t n, const int64_t* __restrict__ rp, int* __rest
     if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
 
+// ---------------------------------------------------------------- CSR transpose (right SPAI)
+
+// entries of row i go to row col[q] of the transpose, at a slot taken from
+// that row's cursor (order within a row fixed afterwards by k_tr_sort)
+__global__ void k_tr_fill(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const double* __restrict__ val, const int64_t* __restrict__ rpT, int32_t* __restrict__ cursor,
+                          int32_t* __restrict__ colT, double* __restrict__ valT)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t q = rp[i]; q < rp[i + 1]; q++) {
+            const int j = col[q];
+            const int slot = atomicAdd(&cursor[j], 1);
+            colT[rpT[j] + slot] = (int32_t)i;
+            valT[rpT[j] + slot] = val[q];
+        }
+}
+
+// insertion sort of each row by column index, carrying the values
+__global__ void k_tr_sort(int64_t n, const int64_t* __restrict__ rp, int32_t* __restrict__ col, double* __restrict__ val)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        for (int64_t x = b + 1; x < e; x++) {
+            const int32_t c = col[x];
+            const double v = val[x];
+            int64_t y = x - 1;
+            while (y >= b && col[y] > c) { col[y + 1] = col[y]; val[y + 1] = val[y]; y--; }
+            col[y + 1] = c;
+            val[y + 1] = v;
+        }
+    }
+}
+
+template <class S>
+__global__ void k_round_to(int64_t m, const double* __restrict__ v, S* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = from_d<S>(v[i]);
+}
+
+// CSR (rowptr, col, val) of the transpose of an n x n CSR, in new device
+// arrays (sorted column indices, deterministic whatever the atomic order)
+int csr_transpose(int num_sms, cudaStream_t s, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* col,
+                  const double* val, int64_t** rpT, int32_t** colT, double** valT, int* nl)
+{
+    *rpT = nullptr; *colT = nullptr; *valT = nullptr;
+    int32_t* cnt = nullptr;
+    int rc = dev_alloc((void**)&cnt, sizeof(int32_t) * (n + 1), s);
+    if (!rc) rc = dev_alloc((void**)rpT, sizeof(int64_t) * (n + 1), s);
+    if (!rc) rc = dev_alloc((void**)colT, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s);
+    if (!rc) rc = dev_alloc((void**)valT, sizeof(double) * (nnz > 0 ? nnz : 1), s);
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(n, nnz) + tb - 1) / tb, (int64_t)num_sms * 32));
+    if (!rc && cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    if (!rc) {
+        k_col_count<<<gb, tb, 0, s>>>(nnz, col, cnt);
+        rc = scan_counts(n, cnt, *rpT, s);
+        *nl += 4;
+    }
+    if (!rc && cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    if (!rc) {
+        k_tr_fill<<<gb, tb, 0, s>>>(n, rp, col, val, *rpT, cnt, *colT, *valT);
+        k_tr_sort<<<gb, tb, 0, s>>>(n, *rpT, *colT, *valT);
+        *nl += 2;
+        if (cudaGetLastError() != cudaSuccess) rc = SPAI_ERR_CUDA;
+    }
+    dev_free(cnt, s);
+    if (rc) {
+        dev_free(*rpT, s); dev_free(*colT, s); dev_free(*valT, s);
+        *rpT = nullptr; *colT = nullptr; *valT = nullptr;
+    }
+    return rc;
+}
+
+int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
+                    spai_precond* P_out, spai_stats* st);
+
 }  // namespace
 
+// Algorithm 1 on A^T D (left, P = M^T D) or, with side = 1, on A D with P = D M
+// (right).  The right construction is the left one run on A^T, transposed:
+// the left run on A^T computes M ~ (A D)^{-1} column by column and assembles
+// M^T D, whose transpose D M is the right preconditioner.
 int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
                    spai_precond* P_out, spai_stats* st)
+{
+    if (!o || !P_out) return SPAI_ERR_INVALID_ARG;
+    if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
+    if (o->side == 0) return spai_build_left(device, num_sms, s, A, o, P_out, st);
+    *P_out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPAI_CUDA_TRY(cudaEventCreate(&e0));
+    SPAI_CUDA_TRY(cudaEventCreate(&e1));
+    int nl = 0, rc = 0;
+    DevCsr At;
+    At.n = A.n;
+    At.nnz = A.nnz;
+    At.owned = true;
+    spai_opts ol = *o;
+    ol.side = 0;
+    spai_precond P = nullptr;
+    int64_t* rpT = nullptr;
+    int32_t* colT = nullptr;
+    double* valT = nullptr;
+    if (cudaEventRecord(e0, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    if (!rc) rc = csr_transpose(num_sms, s, A.n, A.nnz, A.rowptr, A.col, A.val, &At.rowptr, &At.col, &At.val, &nl);
+    if (!rc) rc = spai_build_left(device, num_sms, s, At, &ol, &P, st);
+    csr_release(&At, s);
+    if (rc >= 0 && P) {
+        const int wrc = rc;
+        rc = csr_transpose(num_sms, s, P->n, P->nnz, P->rowptr, P->col, P->val, &rpT, &colT, &valT, &nl);
+        if (!rc) {
+            dev_free(P->rowptr, s);
+            dev_free(P->col, s);
+            dev_free(P->val, s);
+            P->rowptr = rpT;
+            P->col = colT;
+            P->val = valT;
+            // the u_f copy: the same values rounded to u_f
+            const int tb = 256;
+            const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((P->nnz + tb - 1) / tb, (int64_t)num_sms * 32));
+            if (P->nnz > 0) {
+                if (P->uf == SPAI_HALF) k_round_to<__half><<<gb, tb, 0, s>>>(P->nnz, P->val, (__half*)P->val_uf);
+                else if (P->uf == SPAI_SINGLE) k_round_to<float><<<gb, tb, 0, s>>>(P->nnz, P->val, (float*)P->val_uf);
+                else k_round_to<double><<<gb, tb, 0, s>>>(P->nnz, P->val, (double*)P->val_uf);
+                nl++;
+            }
+            if (cudaGetLastError() != cudaSuccess) rc = SPAI_ERR_CUDA;
+            if (!rc) rc = wrc;
+        }
+    }
+    if (rc >= 0 && cudaEventRecord(e1, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess && st) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        st->ms = ms;  // the whole right construction, transposes included
+        st->launches += nl;
+    }
+    if (rc < 0 && P) {
+        spai_precond_free(P);
+        P = nullptr;
+    }
+    *P_out = P;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+namespace {
+
+int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
+                    spai_precond* P_out, spai_stats* st)
 {
     const int64_t n = A.n, nnz = A.nnz;
     if (!o || !P_out) return SPAI_ERR_INVALID_ARG;
@@ -546,3 +693,5 @@ done:
     *P_out = P;
     return rc;
 }
+
+}  // namespace

@@ -309,3 +309,80 @@ def test_ir_cgs2_against_oracle(ctx, tup):
     Sr = O.spai(A, init=init, max_fill=F, uf=uf)
     ref = O.gmres_ir(A, b, O.assemble_P(Sr, up, uf), uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=O.ORTH_CGS2)
     check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
+
+
+# ---------------------------------------------------------------- right preconditioning (reading R14)
+
+
+def _transpose(rp, ci, va):
+    n = len(rp) - 1
+    M = sp.csr_matrix((va, ci, rp), shape=(n, n)).T.tocsr()
+    M.sort_indices()
+    return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data
+
+
+@pytest.mark.parametrize("uf", ["half", "single"])
+@pytest.mark.parametrize("name,make,init,F", [SPAI_CASES[0], SPAI_CASES[2]])
+def test_spai_right_parity(ctx, name, make, init, F, uf):
+    # the right SPAI is the transpose of Algorithm 1 run on A^T: compare P^T with the oracle's
+    # left run on A^T column by column (pattern bit-exact, residuals as for the left SPAI)
+    A = make()
+    P, st, (rp, ci, va) = gpu_spai(ctx, A, init=init, max_fill=F, uf=uf, eps=0.0, side=S.SIDE_RIGHT)
+    At = O.transpose_csr(A)
+    ref = O.spai(At, init=init, max_fill=F, uf=uf, eps=0.0)
+    n = ref["n"]
+    tp, tc, tv = _transpose(rp, ci, va)
+    assert np.array_equal(np.diff(tp), ref["Jcnt"])
+    for k in range(n):
+        assert np.array_equal(tc[tp[k]:tp[k + 1]], ref["Jidx"][k][: ref["Jcnt"][k]])
+    J, cnt, M = split_rows(tp, tc, tv, ref["d"])
+    res_gpu, absbm = true_colres(At, ref["d"], J, cnt, M, floor=True)
+    assert_colres(res_gpu, ref["colres64"], absbm, uf)
+    # column k of A P - I is A D m_k - e_k, the residual just compared
+    Ms = synth.to_scipy(A)
+    Pm = sp.csr_matrix((va, ci, rp), shape=(n, n))
+    R = (Ms @ Pm - sp.identity(n)).tocsc()
+    colres = np.sqrt(np.asarray(R.multiply(R).sum(axis=0)).ravel())
+    np.testing.assert_allclose(colres, res_gpu, rtol=1e-9, atol=1e-13)
+    P.free()
+
+
+@pytest.mark.parametrize("tup", [("single", "double", "double", "double", "quad"),
+                                 ("half", "single", "single", "single", "double")])
+def test_ir_right_preconditioned(ctx, tup):
+    uf, u, ug, up, ur = tup
+    if uf == "half":
+        A, b, x_true = synth.cfg_large_3d(N=16)
+        init, F = O.PAT_A2, 25
+    else:
+        A, b, x_true = synth.cfg_small_2d()
+        init, F = O.PAT_A, 30
+    tau = 1e-4
+    so = S.make_spai_opts(init=init, max_fill=F, uf=uf, side=S.SIDE_RIGHT)
+    io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, side=S.SIDE_RIGHT)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    _, Pr = O.spai_right(A, up=up, uf=uf, init=init, max_fill=F)
+    ref = O.gmres_ir(A, b, Pr, uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, side=O.SIDE_RIGHT)
+    check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
+    assert st["flags"] & 1
+
+
+def test_ir_right_group_and_left_agree():
+    # a grid large enough for the Gram-Schmidt group (77 blocks): the right-preconditioned solve
+    # reaches the same accuracy as the left one
+    c = S.Context(0)
+    A = synth.conv_diff_3d(27, 50.0, seed=11)
+    b, x_true = synth.rhs(A, seed=12)
+    res = {}
+    for side in (S.SIDE_LEFT, S.SIDE_RIGHT):
+        so = S.make_spai_opts(init=O.PAT_A2, max_fill=25, uf="half", side=side)
+        io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4, side=side)
+        x = np.zeros_like(b)
+        st = S.gmres_ir_solve(c, A, b, x, sopts=so, opts=io)
+        nbe, fe = errors(A, b, x, x_true)
+        res[side] = (st, nbe, fe)
+        assert st["flags"] & 1 and st["grid"] >= 64
+    for side in res:
+        assert res[side][1] <= 7 * 2.0 ** -24 and res[side][2] <= 1e-4
+    c.close()
