@@ -190,6 +190,22 @@ void spai_precond_free(spai_precond P);
 int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_opts* sopts,
                    const double* b, double* x, const ir_opts* opts, ir_stats* st);
 
+/* Algorithm 3 for `count` independent systems with the same options (a batch
+ * of the paper's solve; the batching is this library's).  As many systems as
+ * fit the GPU's co-resident grid share one cooperative launch of the
+ * refinement kernel, each on its own blocks (about 2048 rows per block);
+ * further systems follow in later launches, larger systems first.  A[i] is a
+ * host or device CSR and b[i], x[i] follow A[i].on_device.  P may be NULL or
+ * hold NULL entries (that system is unpreconditioned); preconditioners come
+ * from spai_build with the same u_f as opts->uf.  st (count entries, may be
+ * NULL) receives each system's steps, iterations and backward errors, while
+ * ms_ir, ms_kernel and launches describe the whole batch.  status (count
+ * entries, may be NULL) receives each system's return code.  Returns the
+ * first error, else the first warning, else SPAI_OK. */
+int gmres_ir_solve_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_precond* P,
+                         const double* const* b, double* const* x, const ir_opts* opts,
+                         ir_stats* st, int* status);
+
 /* Serving queue.  solver_submit copies A and b (host or device, as
  * A->on_device says) into the context and returns a ticket at once; requests
  * are admitted to the GPU while their estimated device footprint fits the

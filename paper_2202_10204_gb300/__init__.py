@@ -6,8 +6,9 @@ The numerical work lives in the CUDA library (``csrc/``, C ABI in
 ``include/spai_ir.h``); ``_lib`` is its ctypes binding and ``synth`` builds
 seeded test systems.
 """
-from ._lib import (SIDE_LEFT, SIDE_RIGHT, Context, Precond, SpaiError, gmres_ir_solve, make_ir_opts, make_spai_opts,
-                   solver_poll, solver_submit, spai_build, strerror)
+from ._lib import (SIDE_LEFT, SIDE_RIGHT, Context, Precond, SpaiError, gmres_ir_solve, gmres_ir_solve_batch,
+                   make_ir_opts, make_spai_opts, solver_poll, solver_submit, spai_build, strerror)
 
-__all__ = ["SIDE_LEFT", "SIDE_RIGHT", "Context", "Precond", "SpaiError", "gmres_ir_solve", "make_ir_opts",
+__all__ = ["SIDE_LEFT", "SIDE_RIGHT", "Context", "Precond", "SpaiError", "gmres_ir_solve", "gmres_ir_solve_batch",
+           "make_ir_opts",
            "make_spai_opts", "solver_poll", "solver_submit", "spai_build", "strerror"]

@@ -27,7 +27,7 @@ ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND, ERR_INTERN
 
 EXPORTED = ("spai_ctx_create", "spai_ctx_destroy", "spai_build", "spai_precond_info", "spai_precond_export",
             "spai_precond_free", "gmres_ir_solve", "solver_submit", "solver_poll", "spai_strerror",
-            "gmres_ir_solve_noalloc")
+            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch")
 
 
 class spai_csr(C.Structure):
@@ -94,6 +94,9 @@ def lib():
             L.solver_poll.argtypes = [vp, C.c_uint64, vp, C.POINTER(ir_stats)]
             L.gmres_ir_solve_noalloc.argtypes = [C.POINTER(spai_csr), C.POINTER(spai_csr), vp, vp,
                                                  C.POINTER(ir_opts), vp, C.POINTER(ir_stats)]
+            L.gmres_ir_solve_batch.argtypes = [vp, C.c_int, C.POINTER(spai_csr), C.POINTER(vp), C.POINTER(vp),
+                                               C.POINTER(vp), C.POINTER(ir_opts), C.POINTER(ir_stats),
+                                               C.POINTER(C.c_int)]
             L.spai_strerror.argtypes = [C.c_int]
             L.spai_strerror.restype = C.c_char_p
             _lib = L
@@ -246,6 +249,27 @@ def gmres_ir_solve(ctx: Context, A, b, x, P: Precond | None = None, sopts: spai_
                               C.byref(st))
     _check(rc, "gmres_ir_solve")
     return _ir_dict(st, rc)
+
+
+def gmres_ir_solve_batch(ctx: Context, As, bs, xs, Ps=None, opts: ir_opts | None = None):
+    """Algorithm 3 for many systems with the same options in shared launches.
+
+    As: list of CSR triples (numpy or CUDA tensors); bs, xs: matching float64
+    vectors; Ps: None or a list of Precond / None.  Returns (stats list,
+    status list); raises on the first error."""
+    k = len(As)
+    csrs = (spai_csr * max(k, 1))(*[make_csr(A) for A in As])
+    vp = C.c_void_p
+    bp = (vp * max(k, 1))(*[_ptr(b) for b in bs])
+    xp = (vp * max(k, 1))(*[_ptr(x) for x in xs])
+    pp = None
+    if Ps is not None:
+        pp = (vp * max(k, 1))(*[(P.h if P is not None else None) for P in Ps])
+    sts = (ir_stats * max(k, 1))()
+    status = (C.c_int * max(k, 1))()
+    rc = lib().gmres_ir_solve_batch(ctx.h, k, csrs, pp, bp, xp, C.byref(opts), sts, status)
+    _check(rc, "gmres_ir_solve_batch")
+    return [_ir_dict(sts[i], status[i]) for i in range(k)], [status[i] for i in range(k)]
 
 
 def solver_submit(ctx: Context, A, b, sopts: spai_opts | None, opts: ir_opts) -> int:

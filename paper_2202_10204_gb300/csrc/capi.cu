@@ -443,6 +443,57 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
     return rc ? rc : wrc;
 }
 
+int gmres_ir_solve_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_precond* P,
+                         const double* const* b, double* const* x, const ir_opts* opts, ir_stats* st,
+                         int* status)
+{
+    if (!ctx || !opts || count < 0) return SPAI_ERR_INVALID_ARG;
+    if (count == 0) return 0;
+    if (!A || !b || !x) return SPAI_ERR_INVALID_ARG;
+    for (int i = 0; i < count; i++) {
+        int rc = csr_validate_host(&A[i]);
+        if (rc) return rc;
+        if (!b[i] || !x[i]) return SPAI_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    if (st) memset(st, 0, sizeof(ir_stats) * (size_t)count);
+    std::vector<DevCsr> dA(count);
+    std::vector<const double*> db(count, nullptr);
+    std::vector<double*> dx(count, nullptr);
+    int rc = 0;
+    for (int i = 0; i < count && !rc; i++) {
+        rc = csr_to_device(&A[i], &dA[i], s);
+        if (rc) break;
+        if (A[i].on_device) {
+            db[i] = b[i];
+            dx[i] = x[i];
+        } else {
+            double* t = nullptr;
+            rc = dev_alloc((void**)&t, sizeof(double) * A[i].n, s);
+            if (!rc && cudaMemcpyAsync(t, b[i], sizeof(double) * A[i].n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+                rc = SPAI_ERR_CUDA;
+            db[i] = t;
+            if (!rc) rc = dev_alloc((void**)&dx[i], sizeof(double) * A[i].n, s);
+        }
+    }
+    if (!rc) rc = gmres_ir_batch_dev(ctx->device, ctx->num_sms, s, count, dA.data(), P, db.data(), dx.data(), opts,
+                                     st, status);
+    for (int i = 0; i < count; i++) {
+        if (!A[i].on_device) {
+            if (rc >= 0 && dx[i] &&
+                cudaMemcpyAsync(x[i], dx[i], sizeof(double) * A[i].n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                rc = SPAI_ERR_CUDA;
+            dev_free(const_cast<double*>(db[i]), s);
+            dev_free(dx[i], s);
+        }
+        csr_release(&dA[i], s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
+    return rc;
+}
+
 int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_opts* sopts, const ir_opts* opts,
                   uint64_t* ticket)
 {

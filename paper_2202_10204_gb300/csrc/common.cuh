@@ -165,6 +165,7 @@ struct GridBarrier {
     unsigned* count;   // zeroed before the launch
     int* err;          // zeroed before the launch
     long long limit;   // clock64 cycles before a wait gives up
+    unsigned nblocks;  // blocks taking part (the grid, or one system's blocks of a batch)
 };
 
 // `epoch` is a per-block counter kept in shared memory by the caller and
@@ -175,7 +176,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch
     if (threadIdx.x == 0) {
         unsigned e = *epoch + 1u;
         *epoch = e;
-        const unsigned target = e * gridDim.x;
+        const unsigned target = e * gb.nblocks;
         // release: the bar.sync above orders the block's writes before it
         red_release_add_u32(gb.count, 1u);
         int ok = 1;

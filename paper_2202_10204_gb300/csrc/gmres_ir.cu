@@ -21,10 +21,12 @@
 // MGS dots, one for ||w||.  v_{j+1} = w / h_{j+1,j} is never re-published:
 // readers form fl(w_c / h) from the published w themselves, which is the
 // same correctly rounded quotient the owner stores into V.
+#include <algorithm>
 #include <climits>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -79,11 +81,15 @@ struct IrArgs {
     int* out;                   // [0] steps, [1] flags
     int orth;                   // 0 modified Gram-Schmidt, 1 classical Gram-Schmidt twice (CGS2)
     int side;                   // 0 left preconditioning (P A d = P r), 1 right (A P u = r, d = P u)
+    int G;                      // blocks of this system
+    int block0;                 // its first block in a batched launch (0 alone)
     void* pvec;                 // CGS2: 2 parities x gridDim.x x (kmax + 1) partial dot products (u_g)
     unsigned* gcount;           // CGS2: counter of the barrier that publishes them (zeroed)
 };
 
 struct IrShared {
+    int bid;          // the block's rank within its system
+    int G;            // the system's block count
     unsigned epoch;
     unsigned epoch2;  // rounds of the Gram-Schmidt group
     unsigned gepoch;  // CGS2 barrier count
@@ -123,7 +129,7 @@ __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const ui
 {
     // GRP: a round of the Gram-Schmidt group (blocks 0..g2-1), with its own
     // slots and epoch; only the group's blocks may call it
-    const unsigned G = GRP ? (unsigned)a.g2 : gridDim.x;
+    const unsigned G = GRP ? (unsigned)a.g2 : (unsigned)sh->G;
     unsigned* epoch = GRP ? &sh->epoch2 : &sh->epoch;
     if (threadIdx.x < 32) {
         const unsigned ep = *epoch + 1u;
@@ -132,7 +138,7 @@ __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const ui
             if (DATA) __threadfence();
 #pragma unroll
             for (int k = 0; k < NW; k++)
-                st_relaxed_u64(base + (size_t)blockIdx.x * SLOT_WORDS + k, ((unsigned long long)ep << 32) | pay[k]);
+                st_relaxed_u64(base + (size_t)sh->bid * SLOT_WORDS + k, ((unsigned long long)ep << 32) | pay[k]);
         }
         const unsigned lane = threadIdx.x;
         const long long t0 = clock64();
@@ -339,8 +345,9 @@ constexpr int ir_threads()
     return (sizeof(TG) == 8 || sizeof(TP) == 8) ? IR_THREADS / 2 : IR_THREADS;
 }
 
+// The refinement of one system by its G blocks; `bid` is this block's rank.
 template <class TU, class TG, class TP, int RM>
-__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
+__device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const int G)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ IrShared shs;
@@ -350,13 +357,13 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
     const int kmax = a.kmax;
     const int tid = threadIdx.x, BT = blockDim.x;
     const int GT = BT > 32 ? 32 : 0;  // the Givens thread: lane 0 of warp 1 (warp 0 polls)
-    const int64_t r0 = (int64_t)blockIdx.x * a.rb;
+    const int64_t r0 = (int64_t)bid * a.rb;
     const int64_t r1 = min(a.n, r0 + a.rb);
     // modified Gram-Schmidt rows [m0, m1): the block's own rows, or with a
     // Gram-Schmidt group the rows of blocks 2b and 2b+1 (empty outside it)
     const bool sub = a.g2 > 0;
-    const bool gs = !sub || (int)blockIdx.x < a.g2;
-    const int64_t m0 = sub ? min(a.n, (int64_t)blockIdx.x * 2 * a.rb) : r0;
+    const bool gs = !sub || (int)bid < a.g2;
+    const int64_t m0 = sub ? min(a.n, (int64_t)bid * 2 * a.rb) : r0;
     const int64_t m1 = sub ? (gs ? min(a.n, m0 + 2 * a.rb) : m0) : r1;
     const int nsl = (int)((a.rb + 31) >> 5);
     double* cs = (double*)smem;            // kmax + 2
@@ -384,9 +391,9 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
         soa[i] = a.A.off[sg];
         sop[i] = hasP ? a.P.off[sg] : 0;
     }
-    if (tid == 0) { sh->epoch = 0; sh->epoch2 = 0; sh->gepoch = 0; sh->ok = 1; }
+    if (tid == 0) { sh->bid = bid; sh->G = G; sh->epoch = 0; sh->epoch2 = 0; sh->gepoch = 0; sh->ok = 1; }
     __syncthreads();
-    const GridBarrier gbar{a.gcount, a.err, a.limit};
+    const GridBarrier gbar{a.gcount, a.err, a.limit, (unsigned)G};
     unsigned vx = 0;  // CGS2 exchanges so far (identical in every block)
 
     int steps = 0, flags = 0;
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
         if (!xmax2(a, sh, redd, rmax, xmax, rn, xn)) return;
         const double den = a.anorm * xn + a.bnorm;
         const double nb = den > 0.0 ? rn / den : 0.0;
-        if (blockIdx.x == 0 && tid == 0) a.nbe[it] = nb;
+        if (bid == 0 && tid == 0) a.nbe[it] = nb;
         if (!isfinite(nb)) { flags |= 8; break; }
         if (a.stop_rule == IR_STOP_BACKWARD && nb <= a.stop_tol) { flags |= 1; break; }
         if (it == a.imax) { flags |= 2; break; }
@@ -489,18 +496,18 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                     const int lane = tid & 31, wid = tid >> 5, nwp = BT >> 5;
                     __syncthreads();
                     for (int pass = 0; pass < 2; pass++) {
-                        TG* pbase = (TG*)a.pvec + (size_t)(vx & 1u) * gridDim.x * (kmax + 1);
+                        TG* pbase = (TG*)a.pvec + (size_t)(vx & 1u) * G * (kmax + 1);
                         for (int i = wid; i <= j; i += nwp) {
                             const TG* Vi = V + (int64_t)i * a.ldv;
                             TG acc = TG(0);
                             for (int64_t row = r0 + lane; row < r1; row += 32) acc = fma(Vi[row], ws[row - r0], acc);
                             acc = warp_sum(acc);
-                            if (lane == 0) pbase[(size_t)blockIdx.x * (kmax + 1) + i] = acc;
+                            if (lane == 0) pbase[(size_t)bid * (kmax + 1) + i] = acc;
                         }
                         if (!grid_sync(gbar, &sh->gepoch, &sh->ok)) return;
                         for (int i = wid; i <= j; i += nwp) {
                             TG acc = TG(0);
-                            for (unsigned b = lane; b < gridDim.x; b += 32) acc += ldcg(&pbase[(size_t)b * (kmax + 1) + i]);
+                            for (unsigned b = lane; b < G; b += 32) acc += ldcg(&pbase[(size_t)b * (kmax + 1) + i]);
                             acc = warp_sum(acc);
                             if (lane == 0) cvec[i] = acc;
                         }
@@ -527,7 +534,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                             const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
                             hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
                             hc[q] = t0;
-                            if (blockIdx.x == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
+                            if (bid == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
                         }
                     }
                 } else {
@@ -563,7 +570,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                             const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
                             hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
                             hc[q] = t0;
-                            if (blockIdx.x == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
+                            if (bid == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
                         }
                     }
                     const TG* Vi = V + (int64_t)i * a.ldv;
@@ -608,7 +615,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                 // entry h_jj (rotations 0..j-1 applied) in the unused last row of R's
                 // column j for the blocks outside the group
                 if (!gs) part = TG(0);
-                if (sub && !a.orth && blockIdx.x == 0 && tid == GT) a.R[(size_t)j * (kmax + 1) + kmax] = hc[j];
+                if (sub && !a.orth && bid == 0 && tid == GT) a.R[(size_t)j * (kmax + 1) + kmax] = hc[j];
                 TG hsq;
                 if (!xsum<true>(a, sh, redg, part, hsq)) return;
                 const TG hn = sqrt(hsq);
@@ -633,7 +640,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                     g[j + 1] = -sn[j] * g[j];
                     g[j] = cs[j] * g[j];
                     sh->resid = fabs(g[j + 1]) / (double)beta;
-                    if (blockIdx.x == 0) a.R[(size_t)j * (kmax + 1) + j] = hc[j];
+                    if (bid == 0) a.R[(size_t)j * (kmax + 1) + j] = hc[j];
                 }
                 __syncthreads();
                 k = j + 1;
@@ -676,15 +683,33 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
                 }
             }
         }
-        if (blockIdx.x == 0 && tid == 0) a.its[it] = k;
+        if (bid == 0 && tid == 0) a.its[it] = k;
         steps = it + 1;
         // x must be complete before the next residual
         if (!xbar(a, sh)) return;
     }
-    if (blockIdx.x == 0 && tid == 0) {
+    if (bid == 0 && tid == 0) {
         a.out[0] = steps;
         a.out[1] = flags;
     }
+}
+
+template <class TU, class TG, class TP, int RM>
+__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
+{
+    ir_body<TU, TG, TP, RM>(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Many systems in one cooperative launch: block b runs system sys[b] (each
+// system owns the contiguous blocks block0 .. block0 + G - 1, with its own
+// arguments, exchange slots and error word).  Systems do not wait on one
+// another; a system's blocks leave when its refinement ends.
+template <class TU, class TG, class TP, int RM>
+__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrArgs* __restrict__ args,
+                                                                     const int* __restrict__ sys)
+{
+    const IrArgs& a = args[sys[blockIdx.x]];
+    ir_body<TU, TG, TP, RM>(a, (int)blockIdx.x - a.block0, a.G);
 }
 
 // ---------------------------------------------------------------- SELL-32 conversion
@@ -877,176 +902,275 @@ void sell_free(SellMat* m, cudaStream_t s)
     m->val = nullptr;
 }
 
-int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
-                 const double* b, double* xout, const ir_opts* o, ir_stats* st)
+namespace {
+
+// One system's refinement: buffers, the host copies of its results, and the
+// kernel arguments.  gmres_ir_dev runs one job; gmres_ir_batch_dev runs many
+// jobs per cooperative launch.
+struct IrJob {
+    const DevCsr* A = nullptr;
+    spai_precond P = nullptr;
+    const double* b = nullptr;
+    double* xout = nullptr;
+    int64_t n = 0;
+    int kmax = 0, imax = 0;
+    void *x = nullptr, *r = nullptr, *wbuf = nullptr, *tbuf = nullptr, *V = nullptr;
+    double *R = nullptr, *nbe = nullptr;
+    int *its = nullptr, *outv = nullptr, *err = nullptr;
+    unsigned long long* msg = nullptr;
+    unsigned long long* norms = nullptr;
+    void* pvec = nullptr;
+    unsigned* gcount = nullptr;
+    SellMat As;
+    const SellMat* Ps = nullptr;
+    unsigned long long h_norms[3] = {0, 0, 0};
+    int h_out[2] = {0, 0}, h_err = 0;
+    int h_its[SPAI_IR_MAX_STEPS + 1] = {0};
+    double h_nbe[SPAI_IR_MAX_STEPS + 1] = {0.0};
+    IrArgs a;
+};
+
+int ir_check_opts(const ir_opts* o)
 {
-    const int64_t n = A.n;
     if (!o) return SPAI_ERR_INVALID_ARG;
     if (o->u != SPAI_SINGLE && o->u != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->ug != SPAI_SINGLE && o->ug != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->up != SPAI_SINGLE && o->up != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->ur != SPAI_DOUBLE && o->ur != SPAI_QUAD) return SPAI_ERR_UNSUPPORTED;
     if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (P && P->uf != o->uf) return SPAI_ERR_INVALID_ARG;
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
     if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
     if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
-    int kmax = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
-    if (kmax > n) kmax = (int)n;
-    if (kmax > KMAX_LIMIT) return SPAI_ERR_UNSUPPORTED;
-    if (kmax < 1) kmax = 1;
-    const int imax = o->ir_max_steps;
+    return 0;
+}
 
-    int rc = 0;
+int ir_job_kmax(int64_t n, const ir_opts* o, int* kmax)
+{
+    int k = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
+    if (k > n) k = (int)n;
+    if (k > KMAX_LIMIT) return SPAI_ERR_UNSUPPORTED;
+    if (k < 1) k = 1;
+    *kmax = k;
+    return 0;
+}
+
+// Allocations, SELL-32 copies of A (and of P, cached on the handle), the norms
+// and x0 = P b, all enqueued on s (the SELL builds synchronise s once each).
+int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int* nl)
+{
+#define TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
+#define CTRY(x) do { if ((x) != cudaSuccess) return SPAI_ERR_CUDA; } while (0)
+    const int64_t n = J.n;
+    const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
+    const int64_t ldv = (n + 31) & ~int64_t(31);
+    const int kmax = J.kmax, imax = J.imax;
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
+    TRY(dev_alloc(&J.x, (size_t)su * n, s));
+    TRY(dev_alloc(&J.r, (size_t)su * n, s));
+    TRY(dev_alloc(&J.wbuf, (size_t)sg * n, s));
+    TRY(dev_alloc(&J.tbuf, (size_t)sp * n, s));
+    TRY(dev_alloc(&J.V, (size_t)sg * ldv * (kmax + 1), s));
+    TRY(dev_alloc((void**)&J.R, sizeof(double) * (size_t)(kmax + 1) * kmax, s));
+    TRY(dev_alloc((void**)&J.msg, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
+    TRY(dev_alloc((void**)&J.nbe, sizeof(double) * (imax + 1), s));
+    TRY(dev_alloc((void**)&J.its, sizeof(int) * (imax + 1), s));
+    TRY(dev_alloc((void**)&J.outv, sizeof(int) * 2, s));
+    TRY(dev_alloc((void**)&J.err, sizeof(int) * 2, s));
+    TRY(dev_alloc((void**)&J.norms, sizeof(unsigned long long) * 3, s));
+    CTRY(cudaMemsetAsync(J.norms, 0, sizeof(unsigned long long) * 3, s));
+    if (o->orth) {
+        TRY(dev_alloc(&J.pvec, (size_t)sg * 2 * MAX_GRID * (kmax + 1), s));
+        TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
+        CTRY(cudaMemsetAsync(J.gcount, 0, sizeof(unsigned), s));
+    }
+    CTRY(cudaMemsetAsync(J.its, 0, sizeof(int) * (imax + 1), s));
+    CTRY(cudaMemsetAsync(J.outv, 0, sizeof(int) * 2, s));
+    CTRY(cudaMemsetAsync(J.err, 0, sizeof(int) * 2, s));
+    CTRY(cudaMemsetAsync(J.msg, 0, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
+    // A and P in u_p, SELL-32 (P's copy is cached on the preconditioner)
+    const DevCsr& A = *J.A;
+    spai_precond P = J.P;
+    TRY(sell_build(n, A.rowptr, A.col, A.val, o->up, num_sms, s, &J.As, nl));
+    if (P) {
+        SellMat* cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
+        if (!cache->off) TRY(sell_build(n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, nl));
+        J.Ps = cache;
+    }
+    k_norms<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, J.b, J.norms);
+    (*nl)++;
+    CTRY(cudaMemcpyAsync(J.h_norms, J.norms, sizeof(J.h_norms), cudaMemcpyDeviceToHost, s));
+    // x0 = P b in u_f, stored in u
+    const int64_t* prp = P ? P->rowptr : nullptr;
+    const int32_t* pci = P ? P->col : nullptr;
+    const void* pvf = P ? P->val_uf : nullptr;
+#define X0(S, TU) k_x0<S, TU><<<gb, tb, 0, s>>>(n, prp, pci, (const S*)pvf, J.b, (TU*)J.x)
+    if (o->u == SPAI_SINGLE) {
+        if (o->uf == SPAI_HALF) X0(__half, float);
+        else if (o->uf == SPAI_SINGLE) X0(float, float);
+        else X0(double, float);
+    } else {
+        if (o->uf == SPAI_HALF) X0(__half, double);
+        else if (o->uf == SPAI_SINGLE) X0(float, double);
+        else X0(double, double);
+    }
+#undef X0
+    (*nl)++;
+    CTRY(cudaGetLastError());
+    return 0;
+#undef TRY
+#undef CTRY
+}
+
+// The kernel arguments, once the norms have reached the host (after a sync).
+void ir_job_args(IrJob& J, int device, const ir_opts* o)
+{
+    IrArgs& a = J.a;
+    memset(&a, 0, sizeof(a));
+    double anorm, bnorm;
+    long long t0 = (long long)J.h_norms[0], t1 = (long long)J.h_norms[1];
+    memcpy(&anorm, &t0, 8);
+    memcpy(&bnorm, &t1, 8);
+    const int q = (int)J.h_norms[2];
+    const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    const DevCsr& A = *J.A;
+    a.n = J.n;
+    a.A.off = J.As.off; a.A.col = J.As.col; a.A.val = J.As.val;
+    if (J.Ps) { a.P.off = J.Ps->off; a.P.col = J.Ps->col; a.P.val = J.Ps->val; }
+    a.arp = A.rowptr; a.aci = A.col; a.aval = A.val;
+    a.b = J.b; a.x = J.x; a.r = J.r; a.wbuf = J.wbuf; a.tbuf = J.tbuf; a.V = J.V;
+    a.ldv = (J.n + 31) & ~int64_t(31); a.R = J.R; a.msg = J.msg;
+    a.msg2 = J.msg + 2 * MAX_GRID * SLOT_WORDS;
+    a.err = J.err;
+    int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
+    if (clk_khz <= 0) clk_khz = 2000000;
+    a.limit = (long long)clk_khz * 1000LL * 4;  // about four seconds per wait
+    a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
+    a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
+    a.kmax = J.kmax; a.imax = J.imax; a.stop_rule = o->stop;
+    a.its = J.its; a.nbe = J.nbe; a.out = J.outv;
+    a.orth = o->orth; a.pvec = J.pvec; a.gcount = J.gcount; a.side = o->side;
+}
+
+// x in double and the result copies, enqueued on s.
+int ir_job_collect(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int* nl)
+{
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((J.n + tb - 1) / tb, (int64_t)num_sms * 32));
+    if (o->u == SPAI_SINGLE) k_to_double<float><<<gb, tb, 0, s>>>(J.n, (const float*)J.x, J.xout);
+    else k_to_double<double><<<gb, tb, 0, s>>>(J.n, (const double*)J.x, J.xout);
+    (*nl)++;
+    if (cudaGetLastError() != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaMemcpyAsync(J.h_out, J.outv, sizeof(J.h_out), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaMemcpyAsync(&J.h_err, J.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaMemcpyAsync(J.h_its, J.its, sizeof(int) * J.imax, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaMemcpyAsync(J.h_nbe, J.nbe, sizeof(double) * (J.imax + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SPAI_ERR_CUDA;
+    return 0;
+}
+
+// After a sync: the statistics (timings and launch counts are the caller's)
+// and the return code of the job.
+int ir_job_result(const IrJob& J, const ir_opts* o, ir_stats* st)
+{
+    if (J.h_err) return J.h_err;
+    if (st) {
+        memset(st->its, 0, sizeof(st->its));
+        for (int i = 0; i < J.imax; i++) st->its[i] = J.h_its[i];
+        for (int i = 0; i <= SPAI_IR_MAX_STEPS; i++) st->nbe[i] = 0.0;
+        st->steps = J.h_out[0];
+        st->flags = J.h_out[1];
+        for (int i = 0; i <= st->steps && i <= J.imax; i++) st->nbe[i] = J.h_nbe[i];
+        st->total_its = 0;
+        for (int i = 0; i < st->steps; i++) st->total_its += st->its[i];
+        st->final_nbe = st->nbe[st->steps];
+        st->nnz_P = J.P ? J.P->nnz : 0;
+    }
+    if (J.h_out[1] & 8) return SPAI_ERR_NONFINITE;
+    if (!(J.h_out[1] & 1) && o->stop == IR_STOP_BACKWARD) return SPAI_WARN_NOT_CONVERGED;
+    return 0;
+}
+
+void ir_job_free(IrJob& J, cudaStream_t s)
+{
+    sell_free(&J.As, s);
+    dev_free(J.x, s); dev_free(J.r, s); dev_free(J.wbuf, s); dev_free(J.tbuf, s); dev_free(J.V, s);
+    dev_free(J.R, s); dev_free(J.msg, s); dev_free(J.nbe, s); dev_free(J.its, s); dev_free(J.outv, s);
+    dev_free(J.err, s); dev_free(J.norms, s); dev_free(J.pvec, s); dev_free(J.gcount, s);
+    J.x = J.r = J.wbuf = J.tbuf = J.V = J.pvec = nullptr;
+    J.R = J.nbe = nullptr;
+    J.its = J.outv = J.err = nullptr;
+    J.msg = J.norms = nullptr;
+    J.gcount = nullptr;
+}
+
+// Instantiate F<TU, TG, TP> for the run-time precisions and call it.
+template <class F>
+int dispatch_tuple(const ir_opts* o, F&& f)
+{
+    if (o->u == SPAI_DOUBLE) {
+        if (o->ug == SPAI_DOUBLE) {
+            if (o->up == SPAI_DOUBLE) return f.template run<double, double, double>();
+            return f.template run<double, double, float>();
+        }
+        if (o->up == SPAI_DOUBLE) return f.template run<double, float, double>();
+        return f.template run<double, float, float>();
+    }
+    if (o->ug == SPAI_DOUBLE) {
+        if (o->up == SPAI_DOUBLE) return f.template run<float, double, double>();
+        return f.template run<float, double, float>();
+    }
+    if (o->up == SPAI_DOUBLE) return f.template run<float, float, double>();
+    return f.template run<float, float, float>();
+}
+
+struct LaunchOne {
+    IrArgs* a;
+    int rm, num_sms;
+    cudaStream_t s;
+    int* grid;
+    template <class TU, class TG, class TP>
+    int run() { return launch_ir_rm<TU, TG, TP>(*a, rm, num_sms, s, grid); }
+};
+
+}  // namespace
+
+int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
+                 const double* b, double* xout, const ir_opts* o, ir_stats* st)
+{
+    int rc = ir_check_opts(o);
+    if (rc) return rc;
+    if (P && P->uf != o->uf) return SPAI_ERR_INVALID_ARG;
+    IrJob J;
+    J.A = &A; J.P = P; J.b = b; J.xout = xout; J.n = A.n; J.imax = o->ir_max_steps;
+    rc = ir_job_kmax(A.n, o, &J.kmax);
+    if (rc) return rc;
     cudaEvent_t e0 = nullptr, e1 = nullptr, ek0 = nullptr, ek1 = nullptr;
     SPAI_CUDA_TRY(cudaEventCreate(&e0));
     SPAI_CUDA_TRY(cudaEventCreate(&e1));
     SPAI_CUDA_TRY(cudaEventCreate(&ek0));
     SPAI_CUDA_TRY(cudaEventCreate(&ek1));
     int nl = 0;  // kernels launched
-    const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
-    void *x = nullptr, *r = nullptr, *wbuf = nullptr, *tbuf = nullptr, *V = nullptr;
-    double *R = nullptr, *nbe = nullptr;
-    int *its = nullptr, *outv = nullptr, *err = nullptr;
-    unsigned long long* msg = nullptr;
-    unsigned long long* norms = nullptr;
-    unsigned long long h_norms[3] = {0, 0, 0};
-    int h_out[2] = {0, 0}, h_err = 0;
     int grid = 0;
-    void* pvec = nullptr;
-    unsigned* gcount = nullptr;
-    SellMat As;
-    const SellMat* Ps = nullptr;
-    int64_t ldv = (n + 31) & ~int64_t(31);
-    const int tb = 256;
-    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
-    IrArgs a;
-    memset(&a, 0, sizeof(a));
-
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
 #define CTRY(x) do { if ((x) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; } } while (0)
-    TRY(dev_alloc(&x, (size_t)su * n, s));
-    TRY(dev_alloc(&r, (size_t)su * n, s));
-    TRY(dev_alloc(&wbuf, (size_t)sg * n, s));
-    TRY(dev_alloc(&tbuf, (size_t)sp * n, s));
-    TRY(dev_alloc(&V, (size_t)sg * ldv * (kmax + 1), s));
-    TRY(dev_alloc((void**)&R, sizeof(double) * (size_t)(kmax + 1) * kmax, s));
-    TRY(dev_alloc((void**)&msg, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
-    TRY(dev_alloc((void**)&nbe, sizeof(double) * (imax + 1), s));
-    TRY(dev_alloc((void**)&its, sizeof(int) * (imax + 1), s));
-    TRY(dev_alloc((void**)&outv, sizeof(int) * 2, s));
-    TRY(dev_alloc((void**)&err, sizeof(int) * 2, s));
-    TRY(dev_alloc((void**)&norms, sizeof(unsigned long long) * 3, s));
-    CTRY(cudaMemsetAsync(norms, 0, sizeof(unsigned long long) * 3, s));
-    if (o->orth) {
-        TRY(dev_alloc(&pvec, (size_t)sg * 2 * MAX_GRID * (kmax + 1), s));
-        TRY(dev_alloc((void**)&gcount, sizeof(unsigned), s));
-        CTRY(cudaMemsetAsync(gcount, 0, sizeof(unsigned), s));
-    }
-    CTRY(cudaMemsetAsync(its, 0, sizeof(int) * (imax + 1), s));
-    CTRY(cudaMemsetAsync(outv, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(err, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(msg, 0, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
     CTRY(cudaEventRecord(e0, s));
-    // A and P in u_p, SELL-32 (P's copy is cached on the preconditioner)
-    TRY(sell_build(n, A.rowptr, A.col, A.val, o->up, num_sms, s, &As, &nl));
-    if (P) {
-        SellMat* cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
-        if (!cache->off) TRY(sell_build(n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, &nl));
-        Ps = cache;
-    }
-    k_norms<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, b, norms);
-    nl++;
-    CTRY(cudaMemcpyAsync(h_norms, norms, sizeof(h_norms), cudaMemcpyDeviceToHost, s));
-    // x0 = P b in u_f, stored in u
-    {
-        const int64_t* prp = P ? P->rowptr : nullptr;
-        const int32_t* pci = P ? P->col : nullptr;
-        const void* pvf = P ? P->val_uf : nullptr;
-#define X0(S, TU) k_x0<S, TU><<<gb, tb, 0, s>>>(n, prp, pci, (const S*)pvf, b, (TU*)x)
-        if (o->u == SPAI_SINGLE) {
-            if (o->uf == SPAI_HALF) X0(__half, float);
-            else if (o->uf == SPAI_SINGLE) X0(float, float);
-            else X0(double, float);
-        } else {
-            if (o->uf == SPAI_HALF) X0(__half, double);
-            else if (o->uf == SPAI_SINGLE) X0(float, double);
-            else X0(double, double);
-        }
-#undef X0
-        nl++;
-        CTRY(cudaGetLastError());
-    }
+    TRY(ir_job_prepare(J, num_sms, s, o, &nl));
     CTRY(cudaStreamSynchronize(s));
+    ir_job_args(J, device, o);
+    CTRY(cudaEventRecord(ek0, s));
     {
-        double anorm, bnorm;
-        long long t0 = (long long)h_norms[0], t1 = (long long)h_norms[1];
-        memcpy(&anorm, &t0, 8);
-        memcpy(&bnorm, &t1, 8);
-        const int q = (int)h_norms[2];
-        const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
-        a.n = n;
-        a.A.off = As.off; a.A.col = As.col; a.A.val = As.val;
-        if (Ps) { a.P.off = Ps->off; a.P.col = Ps->col; a.P.val = Ps->val; }
-        a.arp = A.rowptr; a.aci = A.col; a.aval = A.val;
-        a.b = b; a.x = x; a.r = r; a.wbuf = wbuf; a.tbuf = tbuf; a.V = V; a.ldv = ldv; a.R = R; a.msg = msg;
-        a.msg2 = msg + 2 * MAX_GRID * SLOT_WORDS;
-        a.err = err;
-        int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
-        if (clk_khz <= 0) clk_khz = 2000000;
-        a.limit = (long long)clk_khz * 1000LL * 4;  // about four seconds per wait
-        a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
-        a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
-        a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
-        a.its = its; a.nbe = nbe; a.out = outv;
-        a.orth = o->orth; a.pvec = pvec; a.gcount = gcount; a.side = o->side;
-        const int rm = o->ur == SPAI_QUAD ? 2 : 1;
-        CTRY(cudaEventRecord(ek0, s));
-#define LAUNCH(TU, TG, TP) TRY((launch_ir_rm<TU, TG, TP>(a, rm, num_sms, s, &grid)))
-        if (o->u == SPAI_DOUBLE) {
-            if (o->ug == SPAI_DOUBLE) {
-                if (o->up == SPAI_DOUBLE) LAUNCH(double, double, double);
-                else LAUNCH(double, double, float);
-            } else {
-                if (o->up == SPAI_DOUBLE) LAUNCH(double, float, double);
-                else LAUNCH(double, float, float);
-            }
-        } else {
-            if (o->ug == SPAI_DOUBLE) {
-                if (o->up == SPAI_DOUBLE) LAUNCH(float, double, double);
-                else LAUNCH(float, double, float);
-            } else {
-                if (o->up == SPAI_DOUBLE) LAUNCH(float, float, double);
-                else LAUNCH(float, float, float);
-            }
-        }
-#undef LAUNCH
+        LaunchOne L{&J.a, o->ur == SPAI_QUAD ? 2 : 1, num_sms, s, &grid};
+        TRY(dispatch_tuple(o, L));
     }
     CTRY(cudaEventRecord(ek1, s));
     nl++;
-    if (o->u == SPAI_SINGLE) k_to_double<float><<<gb, tb, 0, s>>>(n, (const float*)x, xout);
-    else k_to_double<double><<<gb, tb, 0, s>>>(n, (const double*)x, xout);
-    nl++;
-    CTRY(cudaGetLastError());
+    TRY(ir_job_collect(J, num_sms, s, o, &nl));
     CTRY(cudaEventRecord(e1, s));
-    CTRY(cudaMemcpyAsync(h_out, outv, sizeof(h_out), cudaMemcpyDeviceToHost, s));
-    CTRY(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (st) {
-        memset(st->its, 0, sizeof(st->its));
-        CTRY(cudaMemcpyAsync(st->its, its, sizeof(int) * imax, cudaMemcpyDeviceToHost, s));
-        for (int i = 0; i <= SPAI_IR_MAX_STEPS; i++) st->nbe[i] = 0.0;
-        CTRY(cudaMemcpyAsync(st->nbe, nbe, sizeof(double) * (imax + 1), cudaMemcpyDeviceToHost, s));
-    }
     CTRY(cudaStreamSynchronize(s));
-    if (h_err) { rc = h_err; goto done; }
-    if (st) {
-        st->steps = h_out[0];
-        st->flags = h_out[1];
-        st->total_its = 0;
-        for (int i = 0; i < st->steps; i++) st->total_its += st->its[i];
-        for (int i = st->steps + 1; i <= SPAI_IR_MAX_STEPS; i++) st->nbe[i] = 0.0;
-        st->final_nbe = st->nbe[st->steps];
+    rc = ir_job_result(J, o, st);
+    if (rc >= 0 && st) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         st->ms_ir = ms;
@@ -1054,26 +1178,232 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
         st->ms_kernel = ms;
         st->launches += nl;
         st->grid = grid;
-        st->nnz_P = P ? P->nnz : 0;
     }
-    if (h_out[1] & 8) rc = SPAI_ERR_NONFINITE;
-    else if (!(h_out[1] & 1) && o->stop == IR_STOP_BACKWARD) rc = SPAI_WARN_NOT_CONVERGED;
 done:
 #undef TRY
 #undef CTRY
-    (void)sp;
-    sell_free(&As, s);
-    dev_free(x, s); dev_free(r, s); dev_free(wbuf, s); dev_free(tbuf, s); dev_free(V, s);
-    dev_free(R, s); dev_free(msg, s); dev_free(nbe, s); dev_free(its, s); dev_free(outv, s); dev_free(err, s);
-    dev_free(norms, s);
-    dev_free(pvec, s);
-    dev_free(gcount, s);
+    ir_job_free(J, s);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (ek0) cudaEventDestroy(ek0);
     if (ek1) cudaEventDestroy(ek1);
     if (rc < 0) cudaStreamSynchronize(s);
     return rc;
+}
+
+// ====================================================================
+// Batched refinement (gmres_ir_solve_batch): many independent systems per
+// cooperative launch.  Cooperative launches of separate systems hardly
+// overlap on the GPU (16 solves of an n = 4096 system: 111 ms one after
+// another, 66-70 ms from 2 or 4 host threads), while one such system keeps
+// only 16 of 152 SMs busy.  A batch gives every system about
+// BATCH_ROWS_PER_BLOCK rows per block (fewer blocks per system also make
+// its exchange rounds cheaper), packs as many systems as fit the co-resident
+// grid into one launch of k_ir_batch, and runs the waves one after another.
+// ====================================================================
+
+namespace {
+
+constexpr int64_t BATCH_ROWS_PER_BLOCK = 2048;
+
+struct BatchPlan {
+    int G;          // blocks
+    int64_t rb;     // rows per block
+};
+
+BatchPlan batch_geometry(int64_t n, int num_sms)
+{
+    int64_t G = (n + BATCH_ROWS_PER_BLOCK - 1) / BATCH_ROWS_PER_BLOCK;
+    G = std::max<int64_t>(1, std::min<int64_t>(G, std::min(num_sms, MAX_GRID)));
+    int64_t rb = ((n + G - 1) / G + 31) & ~int64_t(31);
+    G = (n + rb - 1) / rb;
+    return BatchPlan{(int)G, rb};
+}
+
+template <class TU, class TG, class TP, int RM>
+struct BatchRun {
+    int device, num_sms;
+    cudaStream_t s;
+    const ir_opts* o;
+    std::vector<IrJob>* jobs;
+    std::vector<int>* order;   // systems by decreasing order n
+    int* nl;
+    float* ms_kernel;
+
+    size_t smem_for(const IrArgs& a) const
+    {
+        const int64_t nsl = (a.rb + 31) >> 5;
+        return sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + (a.g2 ? 2 : 1) * a.rb * sizeof(TG) + 64;
+    }
+
+    int run()
+    {
+        auto kern = k_ir_batch<TU, TG, TP, RM>;
+        constexpr int threads = ir_threads<TG, TP>();
+        size_t dyn_max = 0;
+        SPAI_CUDA_TRY(allow_max_dynamic_smem(kern, &dyn_max));
+        std::vector<IrJob>& J = *jobs;
+        const int count = (int)J.size();
+        // geometry of every system, and the largest shared-memory need
+        size_t smem_all = 0;
+        std::vector<BatchPlan> plan(count);
+        for (int i = 0; i < count; i++) {
+            plan[i] = batch_geometry(J[i].n, num_sms);
+            IrArgs probe;
+            memset(&probe, 0, sizeof(probe));
+            probe.kmax = J[i].kmax;
+            probe.rb = plan[i].rb;
+            probe.g2 = (!o->orth && plan[i].G >= MGS_GROUP_MIN_GRID) ? (plan[i].G + 1) / 2 : 0;
+            if (probe.g2 && smem_for(probe) > dyn_max) probe.g2 = 0;
+            const size_t sm = smem_for(probe);
+            if (sm > dyn_max) return SPAI_ERR_UNSUPPORTED;
+            smem_all = std::max(smem_all, sm);
+        }
+        int occ = 0;
+        SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem_all));
+        const int cap = occ * num_sms;
+        if (cap < 1) return SPAI_ERR_UNSUPPORTED;
+        int rc = 0;
+        size_t pos = 0;
+        while (pos < order->size() && rc >= 0) {
+            // the next wave: systems in order while their blocks fit the grid
+            std::vector<int> wave;
+            int blocks = 0;
+            while (pos < order->size() && blocks + plan[(*order)[pos]].G <= cap) {
+                wave.push_back((*order)[pos]);
+                blocks += plan[(*order)[pos]].G;
+                pos++;
+            }
+            if (wave.empty()) return SPAI_ERR_UNSUPPORTED;
+            for (int i : wave) {
+                rc = ir_job_prepare(J[i], num_sms, s, o, nl);
+                if (rc) return rc;
+            }
+            if (cudaStreamSynchronize(s) != cudaSuccess) return SPAI_ERR_CUDA;
+            std::vector<IrArgs> h(wave.size());
+            std::vector<int> sys(blocks);
+            int b0 = 0;
+            size_t smem = 0;
+            for (size_t w = 0; w < wave.size(); w++) {
+                IrJob& jb = J[wave[w]];
+                ir_job_args(jb, device, o);
+                IrArgs& a = jb.a;
+                a.G = plan[wave[w]].G;
+                a.rb = plan[wave[w]].rb;
+                a.g2 = (!o->orth && a.G >= MGS_GROUP_MIN_GRID) ? (a.G + 1) / 2 : 0;
+                if (a.g2 && smem_for(a) > dyn_max) a.g2 = 0;
+                a.block0 = b0;
+                smem = std::max(smem, smem_for(a));
+                for (int k = 0; k < a.G; k++) sys[b0 + k] = (int)w;
+                b0 += a.G;
+                h[w] = a;
+            }
+            IrArgs* d_args = nullptr;
+            int* d_sys = nullptr;
+            rc = dev_alloc((void**)&d_args, sizeof(IrArgs) * h.size(), s);
+            if (!rc) rc = dev_alloc((void**)&d_sys, sizeof(int) * sys.size(), s);
+            if (!rc && cudaMemcpyAsync(d_args, h.data(), sizeof(IrArgs) * h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                rc = SPAI_ERR_CUDA;
+            if (!rc && cudaMemcpyAsync(d_sys, sys.data(), sizeof(int) * sys.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                rc = SPAI_ERR_CUDA;
+            cudaEvent_t k0 = nullptr, k1 = nullptr;
+            if (!rc && (cudaEventCreate(&k0) != cudaSuccess || cudaEventCreate(&k1) != cudaSuccess)) rc = SPAI_ERR_CUDA;
+            if (!rc) {
+                const IrArgs* pa = d_args;
+                const int* ps = d_sys;
+                void* args[] = {(void*)&pa, (void*)&ps};
+                cudaEventRecord(k0, s);
+                if (cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, smem, s) != cudaSuccess)
+                    rc = SPAI_ERR_CUDA;
+                cudaEventRecord(k1, s);
+                (*nl)++;
+            }
+            for (int i : wave)
+                if (!rc) rc = ir_job_collect(J[i], num_sms, s, o, nl);
+            if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
+            if (!rc) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, k0, k1);
+                *ms_kernel += ms;
+            }
+            if (k0) cudaEventDestroy(k0);
+            if (k1) cudaEventDestroy(k1);
+            dev_free(d_args, s);
+            dev_free(d_sys, s);
+            // the wave's results are on the host: its scratch goes back to the
+            // pool before the next wave
+            for (int i : wave) ir_job_free(J[i], s);
+        }
+        return rc;
+    }
+};
+
+struct LaunchBatch {
+    int device, num_sms;
+    cudaStream_t s;
+    const ir_opts* o;
+    std::vector<IrJob>* jobs;
+    std::vector<int>* order;
+    int* nl;
+    float* ms_kernel;
+    template <class TU, class TG, class TP>
+    int run()
+    {
+        if (o->ur == SPAI_QUAD) return BatchRun<TU, TG, TP, 2>{device, num_sms, s, o, jobs, order, nl, ms_kernel}.run();
+        return BatchRun<TU, TG, TP, 1>{device, num_sms, s, o, jobs, order, nl, ms_kernel}.run();
+    }
+};
+
+}  // namespace
+
+int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const DevCsr* A, const spai_precond* P,
+                       const double* const* b, double* const* xout, const ir_opts* o, ir_stats* st, int* status)
+{
+    int rc = ir_check_opts(o);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!A || !b || !xout))) return SPAI_ERR_INVALID_ARG;
+    std::vector<IrJob> jobs(count);
+    for (int i = 0; i < count; i++) {
+        spai_precond Pi = P ? P[i] : nullptr;
+        if (Pi && (Pi->uf != o->uf || Pi->n != A[i].n)) return SPAI_ERR_INVALID_ARG;
+        IrJob& J = jobs[i];
+        J.A = &A[i]; J.P = Pi; J.b = b[i]; J.xout = xout[i]; J.n = A[i].n; J.imax = o->ir_max_steps;
+        rc = ir_job_kmax(A[i].n, o, &J.kmax);
+        if (rc) return rc;
+    }
+    std::vector<int> order(count);
+    for (int i = 0; i < count; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jobs[x].n > jobs[y].n; });
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SPAI_CUDA_TRY(cudaEventCreate(&e0));
+    SPAI_CUDA_TRY(cudaEventCreate(&e1));
+    int nl = 0;
+    float ms_kernel = 0.f;
+    cudaEventRecord(e0, s);
+    LaunchBatch L{device, num_sms, s, o, &jobs, &order, &nl, &ms_kernel};
+    rc = dispatch_tuple(o, L);
+    cudaEventRecord(e1, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
+    float ms_all = 0.f;
+    if (rc >= 0) cudaEventElapsedTime(&ms_all, e0, e1);
+    int worst = 0;
+    for (int i = 0; i < count; i++) {
+        int ri = rc < 0 ? rc : ir_job_result(jobs[i], o, st ? &st[i] : nullptr);
+        if (status) status[i] = ri;
+        if (ri < 0 && worst >= 0) worst = ri;
+        else if (ri > 0 && worst == 0) worst = ri;
+        if (st && rc >= 0) {
+            st[i].ms_ir = ms_all;
+            st[i].ms_kernel = ms_kernel;
+            st[i].launches = nl;
+            st[i].grid = batch_geometry(jobs[i].n, num_sms).G;
+        }
+        ir_job_free(jobs[i], s);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    return rc < 0 ? rc : worst;
 }
 
 // ====================================================================

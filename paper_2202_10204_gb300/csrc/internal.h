@@ -103,6 +103,11 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
                    spai_precond* P_out, spai_stats* st);
 int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
                  const double* b_dev, double* x_dev, const ir_opts* o, ir_stats* st);
+// Many systems with the same options (see gmres_ir_solve_batch); status[i]
+// receives each system's code (may be NULL).
+int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const DevCsr* A, const spai_precond* P,
+                       const double* const* b_dev, double* const* x_dev, const ir_opts* o, ir_stats* st,
+                       int* status);
 
 int scan_counts(int64_t n, const int32_t* in, int64_t* out, cudaStream_t s);
 int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int prec, int num_sms,

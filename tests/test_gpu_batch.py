@@ -1,0 +1,138 @@
+"""GPU: the batched refinement entry point (gmres_ir_solve_batch).
+
+Systems solved together in shared cooperative launches run on fewer blocks
+each than alone (about 2048 rows per block), so their reductions round
+differently; the bar is the GMRES-IR one of the other tests: the same number
+of refinement steps as the same system solved alone (or by the oracle),
+GMRES iterations within 10%, backward and forward errors within 10x.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2202_10204_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2202_10204_gb300 as S  # noqa: E402
+
+TUPLE = dict(uf="single", u="double", ug="single", up="single", ur="double")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = S.Context(0)
+    yield c
+    c.close()
+
+
+def errors(A, b, x, x_true):
+    Ms = synth.to_scipy(A)
+    nbe = np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b)))
+    return nbe, np.max(np.abs(x - x_true)) / np.max(np.abs(x_true))
+
+
+def mixed_systems():
+    out = []
+    for i, N in enumerate((20, 45, 64, 100, 130)):
+        A = synth.conv_diff_2d(N, 10.0 + 8 * i, 1.0, 0.1, seed=40 + i)
+        out.append(A)
+    for i, n in enumerate((3000, 9000, 20000)):
+        out.append(synth.random_sparse(n, 8 + 2 * i, seed=50 + i, log10_scale=2.0))
+    out.append(synth.conv_diff_3d(18, 50.0, seed=60))
+    return out
+
+
+def test_batch_matches_single_solves(ctx):
+    As = mixed_systems()
+    io = S.make_ir_opts(tau=1e-4, **TUPLE)
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    Ps = [S.spai_build(ctx, A, so)[0] for A in As]
+    Ps[3] = None  # one system without a preconditioner
+    bs, xts = zip(*[synth.rhs(A, seed=70 + i) for i, A in enumerate(As)])
+    xs = [np.zeros_like(b) for b in bs]
+    sts, status = S.gmres_ir_solve_batch(ctx, As, list(bs), xs, Ps, io)
+    assert all(s_ >= 0 for s_ in status)
+    for i, A in enumerate(As):
+        x1 = np.zeros_like(bs[i])
+        st1 = S.gmres_ir_solve(ctx, A, bs[i], x1, P=Ps[i], opts=io)
+        assert sts[i]["steps"] == st1["steps"], (i, sts[i]["its"], st1["its"])
+        assert abs(sts[i]["total_its"] - st1["total_its"]) <= max(1, 0.1 * st1["total_its"]), (i, sts[i]["its"],
+                                                                                          st1["its"])
+        nb_b, fe_b = errors(A, bs[i], xs[i], xts[i])
+        nb_s, fe_s = errors(A, bs[i], x1, xts[i])
+        u = 2.0 ** -53
+        assert nb_b <= 10 * max(nb_s, u) and fe_b <= 10 * max(fe_s, u), (i, nb_b, nb_s, fe_b, fe_s)
+        assert sts[i]["flags"] & 1
+    for P in Ps:
+        if P is not None:
+            P.free()
+
+
+def test_batch_against_oracle(ctx):
+    As = [synth.conv_diff_2d(24, 20.0, 1.0, 0.1, seed=7), synth.random_sparse(1500, 8, seed=3, log10_scale=2.0)]
+    io = S.make_ir_opts(tau=1e-4, **TUPLE)
+    Ps, refs, bs, xts = [], [], [], []
+    for i, A in enumerate(As):
+        b, xt = synth.rhs(A, seed=90 + i)
+        bs.append(b); xts.append(xt)
+        P, _ = S.spai_build(ctx, A, S.make_spai_opts(init=1, max_fill=30, uf="single"))
+        Ps.append(P)
+        Sr = O.spai(A, init=O.PAT_A, max_fill=30, uf="single")
+        refs.append(O.gmres_ir(A, b, O.assemble_P(Sr, "single", "single"), tau=1e-4, **TUPLE))
+    xs = [np.zeros_like(b) for b in bs]
+    sts, _ = S.gmres_ir_solve_batch(ctx, As, bs, xs, Ps, io)
+    for i, A in enumerate(As):
+        ref = refs[i]
+        assert sts[i]["steps"] == ref["steps"], (sts[i]["its"], list(ref["its"]))
+        assert abs(sts[i]["total_its"] - ref["total_its"]) <= max(1, 0.1 * ref["total_its"])
+        nb_g, fe_g = errors(A, bs[i], xs[i], xts[i])
+        nb_o, fe_o = errors(A, bs[i], ref["x"], xts[i])
+        assert nb_g <= 10 * max(nb_o, 2.0 ** -53) and fe_g <= 10 * max(fe_o, 2.0 ** -53)
+        Ps[i].free()
+
+
+def test_batch_over_several_launches_device_inputs(ctx):
+    # 24 systems of n = 36864 take 18 blocks each: more than one co-resident grid,
+    # so the batch runs in several launches; inputs and outputs on the device
+    dev = torch.device("cuda", 0)
+    io = S.make_ir_opts(tau=1e-4, **TUPLE)
+    As, bs, xts, Ps = [], [], [], []
+    for i in range(24):
+        A = synth.conv_diff_2d(192, 5.0 + i, 1.0, 0.1, seed=100 + i)
+        b, xt = synth.rhs(A, seed=200 + i)
+        Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+        As.append(Ad); bs.append(torch.from_numpy(b).to(dev)); xts.append((A, b, xt))
+        Ps.append(S.spai_build(ctx, Ad, S.make_spai_opts(init=1, max_fill=30, uf="single"))[0])
+    xs = [torch.zeros_like(b) for b in bs]
+    sts, status = S.gmres_ir_solve_batch(ctx, As, bs, xs, Ps, io)
+    assert all(s_ == 0 for s_ in status)
+    assert sts[0]["launches"] >= 3 + 24  # at least 2 batched launches + per-system kernels
+    for i in range(24):
+        A, b, xt = xts[i]
+        nbe, fe = errors(A, b, xs[i].cpu().numpy(), xt)
+        assert nbe <= 20 * 2.0 ** -53 and fe <= 1e-10, (i, nbe, fe)
+        assert sts[i]["grid"] == 18
+        Ps[i].free()
+
+
+def test_batch_edge_cases(ctx):
+    io = S.make_ir_opts(tau=1e-4, **TUPLE)
+    assert S.gmres_ir_solve_batch(ctx, [], [], [], None, io) == ([], [])
+    A = synth.conv_diff_2d(16, 10.0, 1.0, 0.1, seed=1)
+    b, _ = synth.rhs(A, seed=2)
+    P, _ = S.spai_build(ctx, A, S.make_spai_opts(init=1, uf="half"))
+    with pytest.raises(S.SpaiError) as e:  # P built with another u_f
+        S.gmres_ir_solve_batch(ctx, [A], [b], [np.zeros_like(b)], [P], io)
+    assert e.value.code == -1
+    P.free()
+    # a zero right-hand side among others: x = 0 with no GMRES work
+    A2 = synth.conv_diff_2d(30, 10.0, 1.0, 0.1, seed=3)
+    b2, _ = synth.rhs(A2, seed=4)
+    xs = [np.ones(256), np.zeros_like(b2)]
+    sts, status = S.gmres_ir_solve_batch(ctx, [A, A2], [np.zeros(256), b2], xs, None, io)
+    assert np.all(xs[0] == 0) and sts[0]["steps"] == 0 and sts[1]["flags"] & 1
