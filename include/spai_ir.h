@@ -173,6 +173,19 @@ void spai_ctx_destroy(spai_ctx ctx);
 int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_precond* P_out,
                spai_stats* st);
 
+/* spai_build for `count` matrices with the same options.  The builds run
+ * concurrently on streams of their own (small builds are bound by launch
+ * gaps and host synchronisations, not by the GPU), after the work already
+ * queued on the context's stream; on return every preconditioner belongs to
+ * the context's stream like one from spai_build.  P_out[count] receives the
+ * handles (NULL where a build failed); st (count entries, may be NULL) and
+ * status (count entries, may be NULL) receive each build's statistics and
+ * return code.  Returns the first error, else the first warning, else
+ * SPAI_OK; handles that were built must be freed even when an error is
+ * returned. */
+int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts* opts,
+                     spai_precond* P_out, spai_stats* st, int* status);
+
 /* Size of P: *n and *nnz (either may be NULL). */
 int spai_precond_info(spai_precond P, int64_t* n, int64_t* nnz);
 
@@ -191,10 +204,12 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
                    const double* b, double* x, const ir_opts* opts, ir_stats* st);
 
 /* Algorithm 3 for `count` independent systems with the same options (a batch
- * of the paper's solve; the batching is this library's).  As many systems as
- * fit the GPU's co-resident grid share one cooperative launch of the
- * refinement kernel, each on its own blocks (about 2048 rows per block);
- * further systems follow in later launches, larger systems first.  A[i] is a
+ * of the paper's solve; the batching is this library's).  All systems share
+ * one persistent cooperative launch of the refinement kernel: the grid is
+ * split into teams of equal size (about 2048 rows per block at the median
+ * order, at most 16 blocks), and each team solves one system after another,
+ * larger systems first.  Every system's buffers are allocated before the
+ * launch.  A[i] is a
  * host or device CSR and b[i], x[i] follow A[i].on_device.  P may be NULL or
  * hold NULL entries (that system is unpreconditioned); preconditioners come
  * from spai_build with the same u_f as opts->uf.  st (count entries, may be

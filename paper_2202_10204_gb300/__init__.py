@@ -7,8 +7,8 @@ The numerical work lives in the CUDA library (``csrc/``, C ABI in
 seeded test systems.
 """
 from ._lib import (SIDE_LEFT, SIDE_RIGHT, Context, Precond, SpaiError, gmres_ir_solve, gmres_ir_solve_batch,
-                   make_ir_opts, make_spai_opts, solver_poll, solver_submit, spai_build, strerror)
+                   make_ir_opts, make_spai_opts, solver_poll, solver_submit, spai_build, spai_build_batch, strerror)
 
 __all__ = ["SIDE_LEFT", "SIDE_RIGHT", "Context", "Precond", "SpaiError", "gmres_ir_solve", "gmres_ir_solve_batch",
            "make_ir_opts",
-           "make_spai_opts", "solver_poll", "solver_submit", "spai_build", "strerror"]
+           "make_spai_opts", "solver_poll", "solver_submit", "spai_build", "spai_build_batch", "strerror"]

@@ -27,7 +27,7 @@ ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND, ERR_INTERN
 
 EXPORTED = ("spai_ctx_create", "spai_ctx_destroy", "spai_build", "spai_precond_info", "spai_precond_export",
             "spai_precond_free", "gmres_ir_solve", "solver_submit", "solver_poll", "spai_strerror",
-            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch")
+            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch", "spai_build_batch")
 
 
 class spai_csr(C.Structure):
@@ -97,6 +97,8 @@ def lib():
             L.gmres_ir_solve_batch.argtypes = [vp, C.c_int, C.POINTER(spai_csr), C.POINTER(vp), C.POINTER(vp),
                                                C.POINTER(vp), C.POINTER(ir_opts), C.POINTER(ir_stats),
                                                C.POINTER(C.c_int)]
+            L.spai_build_batch.argtypes = [vp, C.c_int, C.POINTER(spai_csr), C.POINTER(spai_opts), C.POINTER(vp),
+                                           C.POINTER(spai_stats), C.POINTER(C.c_int)]
             L.spai_strerror.argtypes = [C.c_int]
             L.spai_strerror.restype = C.c_char_p
             _lib = L
@@ -249,6 +251,28 @@ def gmres_ir_solve(ctx: Context, A, b, x, P: Precond | None = None, sopts: spai_
                               C.byref(st))
     _check(rc, "gmres_ir_solve")
     return _ir_dict(st, rc)
+
+
+def spai_build_batch(ctx: Context, As, opts: spai_opts):
+    """spai_build for many matrices with the same options (concurrent builds).
+    Returns (list of Precond, list of stats dicts); raises on the first error
+    after freeing the handles that were built."""
+    k = len(As)
+    csrs = (spai_csr * max(k, 1))(*[make_csr(A) for A in As])
+    hs = (C.c_void_p * max(k, 1))()
+    sts = (spai_stats * max(k, 1))()
+    status = (C.c_int * max(k, 1))()
+    rc = lib().spai_build_batch(ctx.h, k, csrs, C.byref(opts), hs, sts, status)
+    Ps = [Precond(C.c_void_p(hs[i]), ctx) if hs[i] else None for i in range(k)]
+    if rc < 0:
+        for P in Ps:
+            if P is not None:
+                P.free()
+        _check(rc, "spai_build_batch")
+    out = [dict(n=sts[i].n, nnz_P=sts[i].nnz_P, cols_converged=sts[i].cols_converged, max_I=sts[i].max_I,
+                max_J=sts[i].max_J, ms=sts[i].ms, ms_kernel=sts[i].ms_kernel, launches=sts[i].launches,
+                rc=status[i]) for i in range(k)]
+    return Ps, out
 
 
 def gmres_ir_solve_batch(ctx: Context, As, bs, xs, Ps=None, opts: ir_opts | None = None):

@@ -2,10 +2,12 @@
 // device marshalling and the serving queue.  All numerical work is done by
 // the kernels in spai_build.cu and gmres_ir.cu.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -19,6 +21,8 @@ void spai_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
 // them to the driver at every synchronisation: re-mapping the Krylov basis
 // and the SPAI work arrays on every solve cost about 2 ms per solve at
 // n = 262144.  spai_ctx_destroy trims the pool back to what is in use.
+constexpr int SPAI_BATCH_STREAMS = 8;  // concurrent builds in spai_build_batch
+
 static std::mutex g_pool_mu;
 static std::mutex g_live_mu;  // guards spai_ctx_s::live and spai_precond_s::owner / stream
 static cudaMemPool_t g_pool[64];
@@ -41,6 +45,12 @@ static cudaMemPool_t device_pool(int dev)
         }
         unsigned long long thr = ~0ull;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        // no reuse across streams through inserted dependencies: concurrent
+        // builds and serving requests on different streams would otherwise
+        // wait on one another's frees
+        int no = 0;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseFollowEventDependencies, &no);
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
         g_pool[dev] = pool;
     }
     return g_pool[dev];
@@ -348,6 +358,71 @@ int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_prec
         (*P_out)->owner = ctx;
         ctx->live.insert(*P_out);
     }
+    return rc;
+}
+
+int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts* opts, spai_precond* P_out,
+                     spai_stats* st, int* status)
+{
+    if (!ctx || !opts || count < 0) return SPAI_ERR_INVALID_ARG;
+    if (count == 0) return 0;
+    if (!A || !P_out) return SPAI_ERR_INVALID_ARG;
+    for (int i = 0; i < count; i++) P_out[i] = nullptr;
+    for (int i = 0; i < count; i++) {
+        const int rc = csr_validate_host(&A[i]);
+        if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
+    // builds of small matrices are bound by launch gaps and host synchronisations,
+    // so several run at once, each on a stream of its own
+    const int nt = std::min(count, SPAI_BATCH_STREAMS);
+    cudaEvent_t ready = nullptr;
+    SPAI_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    std::vector<cudaStream_t> ss(nt, nullptr);
+    int rc = 0;
+    if (cudaEventRecord(ready, ctx->stream) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    for (int t = 0; t < nt && !rc; t++) {
+        if (cudaStreamCreateWithFlags(&ss[t], cudaStreamNonBlocking) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        else if (cudaStreamWaitEvent(ss[t], ready, 0) != cudaSuccess) rc = SPAI_ERR_CUDA;  // after the caller's work
+    }
+    std::vector<int> rcs(count, 0);
+    if (!rc) {
+        std::atomic<int> next{0};
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; t++) {
+            th.emplace_back([&, t] {
+                cudaSetDevice(ctx->device);
+                cudaStream_t s = ss[t];
+                for (int i = next++; i < count; i = next++) {
+                    DevCsr dA;
+                    int r = csr_to_device(&A[i], &dA, s);
+                    if (!r) r = spai_build_dev(ctx->device, ctx->num_sms, s, dA, opts, &P_out[i], st ? &st[i] : nullptr);
+                    csr_release(&dA, s);
+                    if (cudaStreamSynchronize(s) != cudaSuccess && r >= 0) r = SPAI_ERR_CUDA;
+                    rcs[i] = r;
+                }
+            });
+        }
+        for (auto& t : th) t.join();
+    }
+    for (int i = 0; i < count; i++) {
+        if (P_out[i]) {
+            // the handle belongs to the context from now on: its frees go to the context's stream
+            std::lock_guard<std::mutex> lk2(g_live_mu);
+            P_out[i]->stream = ctx->stream;
+            P_out[i]->owner = ctx;
+            ctx->live.insert(P_out[i]);
+        }
+        if (status) status[i] = rcs[i];
+        if (!rc && rcs[i] < 0) rc = rcs[i];
+    }
+    if (!rc)
+        for (int i = 0; i < count && !rc; i++)
+            if (rcs[i] > 0) rc = rcs[i];
+    for (auto s : ss)
+        if (s) cudaStreamDestroy(s);
+    cudaEventDestroy(ready);
     return rc;
 }
 

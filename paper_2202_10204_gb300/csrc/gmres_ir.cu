@@ -700,16 +700,44 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
     ir_body<TU, TG, TP, RM>(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
-// Many systems in one cooperative launch: block b runs system sys[b] (each
-// system owns the contiguous blocks block0 .. block0 + G - 1, with its own
-// arguments, exchange slots and error word).  Systems do not wait on one
-// another; a system's blocks leave when its refinement ends.
+// Many systems in one cooperative launch, scheduled dynamically: the grid is
+// split into teams of T blocks; the first block of a team claims the next
+// system from *next (an atomic counter) and hands its index to the team
+// through the team's word in `claim`, tagged with the team's claim count, and
+// the team runs that system (with its own arguments, exchange slots and error
+// word) as a grid of T blocks.  Teams never wait on one another, so a system
+// with many iterations holds only its own team's SMs.  Waits are bounded like
+// every other wait of the refinement: a team that gives up leaves.
 template <class TU, class TG, class TP, int RM>
-__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrArgs* __restrict__ args,
-                                                                     const int* __restrict__ sys)
+__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrArgs* __restrict__ args, int count,
+                                                                     int T, unsigned* next,
+                                                                     unsigned long long* claim, long long limit)
 {
-    const IrArgs& a = args[sys[blockIdx.x]];
-    ir_body<TU, TG, TP, RM>(a, (int)blockIdx.x - a.block0, a.G);
+    __shared__ int s_sys;
+    const int team = (int)blockIdx.x / T, rank = (int)blockIdx.x % T;
+    for (unsigned round = 1;; round++) {
+        if (threadIdx.x == 0) {
+            int sys = -1;
+            if (rank == 0) {
+                sys = (int)atomicAdd(next, 1u);
+                st_relaxed_u64(&claim[team], ((unsigned long long)round << 32) | (unsigned)sys);
+            } else {
+                const long long t0 = clock64();
+                for (;;) {
+                    const unsigned long long w = ld_relaxed_u64(&claim[team]);
+                    if ((unsigned)(w >> 32) == round) { sys = (int)(unsigned)w; break; }
+                    if (clock64() - t0 > limit) break;  // the leader is gone: leave
+                }
+            }
+            s_sys = sys;
+        }
+        __syncthreads();
+        const int sys = s_sys;
+        __syncthreads();
+        if (sys < 0 || sys >= count) return;
+        ir_body<TU, TG, TP, RM>(args[sys], rank, T);
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- SELL-32 conversion
@@ -1192,33 +1220,21 @@ done:
 }
 
 // ====================================================================
-// Batched refinement (gmres_ir_solve_batch): many independent systems per
-// cooperative launch.  Cooperative launches of separate systems hardly
-// overlap on the GPU (16 solves of an n = 4096 system: 111 ms one after
-// another, 66-70 ms from 2 or 4 host threads), while one such system keeps
-// only 16 of 152 SMs busy.  A batch gives every system about
-// BATCH_ROWS_PER_BLOCK rows per block (fewer blocks per system also make
-// its exchange rounds cheaper), packs as many systems as fit the co-resident
-// grid into one launch of k_ir_batch, and runs the waves one after another.
+// Batched refinement (gmres_ir_solve_batch): many independent systems in one
+// persistent cooperative launch.  Cooperative launches of separate systems
+// hardly overlap on the GPU (16 solves of an n = 4096 system: 111 ms one
+// after another, 66-70 ms from 2 or 4 host threads), while one such system
+// keeps only 16 of 152 SMs busy.  The batch splits the co-resident grid into
+// teams of T blocks (T from the median order, about BATCH_ROWS_PER_BLOCK rows
+// per block, at most 16); each team takes the next system (larger first) as
+// soon as it is done with its last one, so systems with many GMRES iterations
+// do not hold up the others' SMs.  All systems are prepared before the launch
+// (their buffers coexist).
 // ====================================================================
 
 namespace {
 
 constexpr int64_t BATCH_ROWS_PER_BLOCK = 2048;
-
-struct BatchPlan {
-    int G;          // blocks
-    int64_t rb;     // rows per block
-};
-
-BatchPlan batch_geometry(int64_t n, int num_sms)
-{
-    int64_t G = (n + BATCH_ROWS_PER_BLOCK - 1) / BATCH_ROWS_PER_BLOCK;
-    G = std::max<int64_t>(1, std::min<int64_t>(G, std::min(num_sms, MAX_GRID)));
-    int64_t rb = ((n + G - 1) / G + 31) & ~int64_t(31);
-    G = (n + rb - 1) / rb;
-    return BatchPlan{(int)G, rb};
-}
 
 template <class TU, class TG, class TP, int RM>
 struct BatchRun {
@@ -1229,6 +1245,7 @@ struct BatchRun {
     std::vector<int>* order;   // systems by decreasing order n
     int* nl;
     float* ms_kernel;
+    int* team_size;
 
     size_t smem_for(const IrArgs& a) const
     {
@@ -1244,96 +1261,75 @@ struct BatchRun {
         SPAI_CUDA_TRY(allow_max_dynamic_smem(kern, &dyn_max));
         std::vector<IrJob>& J = *jobs;
         const int count = (int)J.size();
-        // geometry of every system, and the largest shared-memory need
-        size_t smem_all = 0;
-        std::vector<BatchPlan> plan(count);
-        for (int i = 0; i < count; i++) {
-            plan[i] = batch_geometry(J[i].n, num_sms);
-            IrArgs probe;
-            memset(&probe, 0, sizeof(probe));
-            probe.kmax = J[i].kmax;
-            probe.rb = plan[i].rb;
-            probe.g2 = (!o->orth && plan[i].G >= MGS_GROUP_MIN_GRID) ? (plan[i].G + 1) / 2 : 0;
-            if (probe.g2 && smem_for(probe) > dyn_max) probe.g2 = 0;
-            const size_t sm = smem_for(probe);
-            if (sm > dyn_max) return SPAI_ERR_UNSUPPORTED;
-            smem_all = std::max(smem_all, sm);
-        }
-        int occ = 0;
-        SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem_all));
-        const int cap = occ * num_sms;
-        if (cap < 1) return SPAI_ERR_UNSUPPORTED;
+        // team size from the median order: about BATCH_ROWS_PER_BLOCK rows per block
+        std::vector<int64_t> ns(count);
+        for (int i = 0; i < count; i++) ns[i] = J[i].n;
+        std::nth_element(ns.begin(), ns.begin() + count / 2, ns.end());
+        const int64_t med = ns[count / 2];
+        const int T = (int)std::max<int64_t>(1, std::min<int64_t>(16, (med + BATCH_ROWS_PER_BLOCK / 2) / BATCH_ROWS_PER_BLOCK));
         int rc = 0;
-        size_t pos = 0;
-        while (pos < order->size() && rc >= 0) {
-            // the next wave: systems in order while their blocks fit the grid
-            std::vector<int> wave;
-            int blocks = 0;
-            while (pos < order->size() && blocks + plan[(*order)[pos]].G <= cap) {
-                wave.push_back((*order)[pos]);
-                blocks += plan[(*order)[pos]].G;
-                pos++;
-            }
-            if (wave.empty()) return SPAI_ERR_UNSUPPORTED;
-            for (int i : wave) {
-                rc = ir_job_prepare(J[i], num_sms, s, o, nl);
-                if (rc) return rc;
-            }
-            if (cudaStreamSynchronize(s) != cudaSuccess) return SPAI_ERR_CUDA;
-            std::vector<IrArgs> h(wave.size());
-            std::vector<int> sys(blocks);
-            int b0 = 0;
-            size_t smem = 0;
-            for (size_t w = 0; w < wave.size(); w++) {
-                IrJob& jb = J[wave[w]];
-                ir_job_args(jb, device, o);
-                IrArgs& a = jb.a;
-                a.G = plan[wave[w]].G;
-                a.rb = plan[wave[w]].rb;
-                a.g2 = (!o->orth && a.G >= MGS_GROUP_MIN_GRID) ? (a.G + 1) / 2 : 0;
-                if (a.g2 && smem_for(a) > dyn_max) a.g2 = 0;
-                a.block0 = b0;
-                smem = std::max(smem, smem_for(a));
-                for (int k = 0; k < a.G; k++) sys[b0 + k] = (int)w;
-                b0 += a.G;
-                h[w] = a;
-            }
-            IrArgs* d_args = nullptr;
-            int* d_sys = nullptr;
-            rc = dev_alloc((void**)&d_args, sizeof(IrArgs) * h.size(), s);
-            if (!rc) rc = dev_alloc((void**)&d_sys, sizeof(int) * sys.size(), s);
-            if (!rc && cudaMemcpyAsync(d_args, h.data(), sizeof(IrArgs) * h.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-                rc = SPAI_ERR_CUDA;
-            if (!rc && cudaMemcpyAsync(d_sys, sys.data(), sizeof(int) * sys.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-                rc = SPAI_ERR_CUDA;
-            cudaEvent_t k0 = nullptr, k1 = nullptr;
-            if (!rc && (cudaEventCreate(&k0) != cudaSuccess || cudaEventCreate(&k1) != cudaSuccess)) rc = SPAI_ERR_CUDA;
-            if (!rc) {
-                const IrArgs* pa = d_args;
-                const int* ps = d_sys;
-                void* args[] = {(void*)&pa, (void*)&ps};
-                cudaEventRecord(k0, s);
-                if (cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)blocks), dim3(threads), args, smem, s) != cudaSuccess)
-                    rc = SPAI_ERR_CUDA;
-                cudaEventRecord(k1, s);
-                (*nl)++;
-            }
-            for (int i : wave)
-                if (!rc) rc = ir_job_collect(J[i], num_sms, s, o, nl);
-            if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
-            if (!rc) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, k0, k1);
-                *ms_kernel += ms;
-            }
-            if (k0) cudaEventDestroy(k0);
-            if (k1) cudaEventDestroy(k1);
-            dev_free(d_args, s);
-            dev_free(d_sys, s);
-            // the wave's results are on the host: its scratch goes back to the
-            // pool before the next wave
-            for (int i : wave) ir_job_free(J[i], s);
+        for (int i : *order) {
+            rc = ir_job_prepare(J[i], num_sms, s, o, nl);
+            if (rc) return rc;
         }
+        if (cudaStreamSynchronize(s) != cudaSuccess) return SPAI_ERR_CUDA;
+        // arguments in claim order (larger systems first), every system on T blocks
+        std::vector<IrArgs> h(count);
+        size_t smem = 0;
+        for (int q = 0; q < count; q++) {
+            IrJob& jb = J[(*order)[q]];
+            ir_job_args(jb, device, o);
+            IrArgs& a = jb.a;
+            a.G = T;
+            a.rb = std::max<int64_t>(32, ((jb.n + T - 1) / T + 31) & ~int64_t(31));
+            a.g2 = 0;
+            a.block0 = 0;
+            smem = std::max(smem, smem_for(a));
+            h[q] = a;
+        }
+        if (smem > dyn_max) return SPAI_ERR_UNSUPPORTED;
+        int occ = 0;
+        SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+        const int teams = (occ * num_sms) / T;
+        if (teams < 1) return SPAI_ERR_UNSUPPORTED;
+        *team_size = T;
+        IrArgs* d_args = nullptr;
+        unsigned* d_next = nullptr;
+        unsigned long long* d_claim = nullptr;
+        rc = dev_alloc((void**)&d_args, sizeof(IrArgs) * count, s);
+        if (!rc) rc = dev_alloc((void**)&d_next, sizeof(unsigned), s);
+        if (!rc) rc = dev_alloc((void**)&d_claim, sizeof(unsigned long long) * teams, s);
+        if (!rc && cudaMemcpyAsync(d_args, h.data(), sizeof(IrArgs) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = SPAI_ERR_CUDA;
+        if (!rc && cudaMemsetAsync(d_next, 0, sizeof(unsigned), s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        if (!rc && cudaMemsetAsync(d_claim, 0, sizeof(unsigned long long) * teams, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        cudaEvent_t k0 = nullptr, k1 = nullptr;
+        if (!rc && (cudaEventCreate(&k0) != cudaSuccess || cudaEventCreate(&k1) != cudaSuccess)) rc = SPAI_ERR_CUDA;
+        if (!rc) {
+            const IrArgs* pa = d_args;
+            int cnt = count, tt = T;
+            long long limit = h[0].limit;
+            void* args[] = {(void*)&pa, (void*)&cnt, (void*)&tt, (void*)&d_next, (void*)&d_claim, (void*)&limit};
+            cudaEventRecord(k0, s);
+            if (cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)(teams * T)), dim3(threads), args, smem, s) !=
+                cudaSuccess)
+                rc = SPAI_ERR_CUDA;
+            cudaEventRecord(k1, s);
+            (*nl)++;
+        }
+        for (int i = 0; i < count; i++)
+            if (!rc) rc = ir_job_collect(J[i], num_sms, s, o, nl);
+        if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
+        if (!rc) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, k0, k1);
+            *ms_kernel += ms;
+        }
+        if (k0) cudaEventDestroy(k0);
+        if (k1) cudaEventDestroy(k1);
+        dev_free(d_args, s);
+        dev_free(d_next, s);
+        dev_free(d_claim, s);
         return rc;
     }
 };
@@ -1346,11 +1342,13 @@ struct LaunchBatch {
     std::vector<int>* order;
     int* nl;
     float* ms_kernel;
+    int* team_size;
     template <class TU, class TG, class TP>
     int run()
     {
-        if (o->ur == SPAI_QUAD) return BatchRun<TU, TG, TP, 2>{device, num_sms, s, o, jobs, order, nl, ms_kernel}.run();
-        return BatchRun<TU, TG, TP, 1>{device, num_sms, s, o, jobs, order, nl, ms_kernel}.run();
+        if (o->ur == SPAI_QUAD)
+            return BatchRun<TU, TG, TP, 2>{device, num_sms, s, o, jobs, order, nl, ms_kernel, team_size}.run();
+        return BatchRun<TU, TG, TP, 1>{device, num_sms, s, o, jobs, order, nl, ms_kernel, team_size}.run();
     }
 };
 
@@ -1380,7 +1378,8 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
     int nl = 0;
     float ms_kernel = 0.f;
     cudaEventRecord(e0, s);
-    LaunchBatch L{device, num_sms, s, o, &jobs, &order, &nl, &ms_kernel};
+    int team = 0;
+    LaunchBatch L{device, num_sms, s, o, &jobs, &order, &nl, &ms_kernel, &team};
     rc = dispatch_tuple(o, L);
     cudaEventRecord(e1, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
@@ -1396,7 +1395,7 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
             st[i].ms_ir = ms_all;
             st[i].ms_kernel = ms_kernel;
             st[i].launches = nl;
-            st[i].grid = batch_geometry(jobs[i].n, num_sms).G;
+            st[i].grid = team;
         }
         ir_job_free(jobs[i], s);
     }
