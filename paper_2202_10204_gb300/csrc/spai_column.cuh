@@ -69,6 +69,7 @@ struct SpaiArgs {
     int mmax, cmax;      // per-warp tile rows and candidate capacity
     int rl;              // longest row of A (list capacity per lane)
     int warp_bytes;
+    int ilo, ihi;        // CTA kernel: only columns with ilo < |I_k| <= ihi (from k_pattern); ihi = 0: all
     int* err;
 };
 

@@ -153,7 +153,7 @@ __device__ __forceinline__ C block_sum_det(C v, C* red)
 }
 
 template <class S, bool ADAPTIVE, int NW>
-__global__ void __launch_bounds__(32 * NW, 1) k_spai_cta(SpaiArgs a)
+__global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs a)
 {
     typedef typename Compute<S>::T C;
     constexpr int MM = 32 * NW;
@@ -165,6 +165,11 @@ __global__ void __launch_bounds__(32 * NW, 1) k_spai_cta(SpaiArgs a)
     int* sc = T.sc;  // [0] nj, [1] m, [2] flags from warp 0, [3] nadd
 
     for (int64_t k = blockIdx.x; k < a.n; k += gridDim.x) {
+        if (a.ihi > 0) {
+            // fixed patterns: this pass takes only the columns of its shadow-size range
+            const int ic = a.Icnt[k];
+            if (ic <= a.ilo || ic > a.ihi) continue;
+        }
         if (tid == 0) { sc[0] = a.Jcnt[k]; sc[2] = 0; }
         __syncthreads();
         int nj = sc[0];
@@ -426,14 +431,16 @@ __global__ void __launch_bounds__(32 * NW, 1) k_spai_cta(SpaiArgs a)
     }
 }
 
-template <class S>
-int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
+template <class S, int NW>
+int launch_spai_cta_nw(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s, int ilo,
+                       int ihi)
 {
     typedef typename Compute<S>::T C;
-    constexpr int NW = 16;
     SpaiArgs a = a0;
     if (!adaptive) a.cmax = 0;
     a.mmax = 32 * NW;
+    a.ilo = ilo;
+    a.ihi = ihi;
     while (adaptive && a.cmax > 512 && cta_tile_bytes<C>(a.mmax, NW, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
     const size_t smem = cta_tile_bytes<C>(a.mmax, NW, a.rl, a.cmax);
     if (smem > smem_cap) return SPAI_ERR_UNSUPPORTED;
@@ -448,6 +455,20 @@ int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t sme
     kern<<<(unsigned)blocks, 32 * NW, smem, s>>>(a);
     SPAI_CUDA_TRY(cudaGetLastError());
     return 0;
+}
+
+// Adaptive patterns grow, so they run 16 warps per column (tiles of 512
+// rows).  Fixed patterns know every column's shadow size from k_pattern:
+// columns of at most 256 rows run 8 warps per column, which fits two CTAs per
+// SM (the 16-warp kernel holds one), and larger ones follow in a 16-warp pass.
+template <class S>
+int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    if (adaptive) return launch_spai_cta_nw<S, 16>(a0, true, num_sms, smem_cap, s, 0, 0);
+    if (a0.mmax <= 256) return launch_spai_cta_nw<S, 8>(a0, false, num_sms, smem_cap, s, 0, 0);
+    const int rc = launch_spai_cta_nw<S, 8>(a0, false, num_sms, smem_cap, s, 0, 256);
+    if (rc) return rc;
+    return launch_spai_cta_nw<S, 16>(a0, false, num_sms, smem_cap, s, 256, 512);
 }
 
 }  // namespace spai

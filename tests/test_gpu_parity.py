@@ -91,6 +91,9 @@ SPAI_CASES = [
     ("3d-patA2", lambda: synth.conv_diff_3d(9, 50.0, seed=3), O.PAT_A2, 25),
     ("rand-patA", lambda: synth.random_sparse(700, 9, seed=5), O.PAT_A, 12),
     ("3d-capped", lambda: synth.conv_diff_3d((7, 6, 5), 50.0, seed=8), O.PAT_A2, 9),
+    # shadows of 208-301 rows: the 8-warp CTA pass takes the columns up to 256 rows, the
+    # 16-warp pass the rest
+    ("rand-patA-wide", lambda: synth.random_sparse(1000, 17, seed=13), O.PAT_A, 30),
 ]
 
 
