@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "common.cuh"
@@ -889,9 +890,11 @@ int prec_bytes(int p) { return p == SPAI_HALF ? 2 : (p == SPAI_SINGLE ? 4 : 8); 
 
 }  // namespace
 
-// SELL-32 copy of a CSR matrix with values rounded to `prec` (single or double).
-int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int prec, int num_sms,
-               cudaStream_t s, SellMat* out, int* launches)
+// SELL-32 copy of a CSR matrix with values rounded to `prec` (single or double),
+// in two halves: sell_begin computes the slice offsets (the entry count stays
+// on the device at off[nslices]); sell_finish allocates and fills once that
+// count is known on the host.
+int sell_begin(int64_t n, const int64_t* rp, int num_sms, cudaStream_t s, SellMat* out, int* launches)
 {
     const int64_t nsl = (n + 31) >> 5;
     int32_t* w32 = nullptr;
@@ -904,11 +907,17 @@ int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* va
     k_sell_width<<<gb, tb, 0, s>>>(n, rp, w32);
     rc = scan_counts(nsl, w32, out->off, s);
     *launches += 4;
-    int64_t total = 0;
-    if (!rc && cudaMemcpyAsync(&total, out->off + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
-    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = SPAI_ERR_CUDA;
     dev_free(w32, s);
-    if (rc) return rc;
+    return rc;
+}
+
+int sell_finish(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int prec, int num_sms,
+                cudaStream_t s, SellMat* out, int64_t total, int* launches)
+{
+    const int64_t nsl = (n + 31) >> 5;
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((nsl * 32 + tb - 1) / tb, (int64_t)num_sms * 16));
+    int rc;
     out->prec = prec;
     out->nnz = total;
     if ((rc = dev_alloc((void**)&out->col, sizeof(int32_t) * std::max<int64_t>(total, 1), s))) return rc;
@@ -918,6 +927,18 @@ int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* va
     *launches += 1;
     SPAI_CUDA_TRY(cudaGetLastError());
     return 0;
+}
+
+int sell_build(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int prec, int num_sms,
+               cudaStream_t s, SellMat* out, int* launches)
+{
+    int rc = sell_begin(n, rp, num_sms, s, out, launches);
+    if (rc) return rc;
+    const int64_t nsl = (n + 31) >> 5;
+    int64_t total = 0;
+    if (cudaMemcpyAsync(&total, out->off + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPAI_ERR_CUDA;
+    return sell_finish(n, rp, ci, val, prec, num_sms, s, out, total, launches);
 }
 
 void sell_free(SellMat* m, cudaStream_t s)
@@ -983,9 +1004,8 @@ int ir_job_kmax(int64_t n, const ir_opts* o, int* kmax)
     return 0;
 }
 
-// Allocations, SELL-32 copies of A (and of P, cached on the handle), the norms
-// and x0 = P b, all enqueued on s (the SELL builds synchronise s once each).
-int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int* nl)
+// The job's buffers (allocated and cleared on s).
+int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
 {
 #define TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
 #define CTRY(x) do { if ((x) != cudaSuccess) return SPAI_ERR_CUDA; } while (0)
@@ -993,8 +1013,6 @@ int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int*
     const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
     const int64_t ldv = (n + 31) & ~int64_t(31);
     const int kmax = J.kmax, imax = J.imax;
-    const int tb = 256;
-    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
     TRY(dev_alloc(&J.x, (size_t)su * n, s));
     TRY(dev_alloc(&J.r, (size_t)su * n, s));
     TRY(dev_alloc(&J.wbuf, (size_t)sg * n, s));
@@ -1017,18 +1035,22 @@ int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int*
     CTRY(cudaMemsetAsync(J.outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(J.err, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(J.msg, 0, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
-    // A and P in u_p, SELL-32 (P's copy is cached on the preconditioner)
+    return 0;
+#undef TRY
+#undef CTRY
+}
+
+// ||A||_inf, ||b||_inf, the longest row into J.norms, and x0 = P b in u_f
+// stored in u, enqueued on s.
+int ir_job_norms_x0(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int* nl)
+{
+    const int64_t n = J.n;
+    const int tb = 256;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
     const DevCsr& A = *J.A;
     spai_precond P = J.P;
-    TRY(sell_build(n, A.rowptr, A.col, A.val, o->up, num_sms, s, &J.As, nl));
-    if (P) {
-        SellMat* cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
-        if (!cache->off) TRY(sell_build(n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, nl));
-        J.Ps = cache;
-    }
     k_norms<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, J.b, J.norms);
     (*nl)++;
-    CTRY(cudaMemcpyAsync(J.h_norms, J.norms, sizeof(J.h_norms), cudaMemcpyDeviceToHost, s));
     // x0 = P b in u_f, stored in u
     const int64_t* prp = P ? P->rowptr : nullptr;
     const int32_t* pci = P ? P->col : nullptr;
@@ -1045,10 +1067,31 @@ int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int*
     }
 #undef X0
     (*nl)++;
-    CTRY(cudaGetLastError());
+    if (cudaGetLastError() != cudaSuccess) return SPAI_ERR_CUDA;
     return 0;
-#undef TRY
-#undef CTRY
+}
+
+// Allocations, SELL-32 copies of A (and of P, cached on the handle), the norms
+// and x0 = P b, all enqueued on s (the SELL builds synchronise s once each).
+int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int* nl)
+{
+    int rc = ir_job_alloc(J, s, o);
+    if (rc) return rc;
+    const DevCsr& A = *J.A;
+    spai_precond P = J.P;
+    rc = sell_build(J.n, A.rowptr, A.col, A.val, o->up, num_sms, s, &J.As, nl);
+    if (rc) return rc;
+    if (P) {
+        SellMat* cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
+        if (!cache->off) rc = sell_build(J.n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, nl);
+        if (rc) return rc;
+        J.Ps = cache;
+    }
+    rc = ir_job_norms_x0(J, num_sms, s, o, nl);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(J.h_norms, J.norms, sizeof(J.h_norms), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SPAI_ERR_CUDA;
+    return 0;
 }
 
 // The kernel arguments, once the norms have reached the host (after a sync).
@@ -1268,11 +1311,58 @@ struct BatchRun {
         const int64_t med = ns[count / 2];
         const int T = (int)std::max<int64_t>(1, std::min<int64_t>(16, (med + BATCH_ROWS_PER_BLOCK / 2) / BATCH_ROWS_PER_BLOCK));
         int rc = 0;
+        // preparation without a wait per system: buffers, SELL offsets, norms and x0
+        // for all systems, then one copy of every SELL size and norm to the host,
+        // then the SELL fills
+        std::vector<char> pbuild(count, 0);
+        std::set<spai_precond> building;
+        unsigned long long* d_slots = nullptr;
+        rc = dev_alloc((void**)&d_slots, sizeof(unsigned long long) * 5 * count, s);
+        if (rc) return rc;
         for (int i : *order) {
-            rc = ir_job_prepare(J[i], num_sms, s, o, nl);
-            if (rc) return rc;
+            IrJob& jb = J[i];
+            if (!rc) rc = ir_job_alloc(jb, s, o);
+            if (!rc) rc = sell_begin(jb.n, jb.A->rowptr, num_sms, s, &jb.As, nl);
+            const int64_t nsl = (jb.n + 31) >> 5;
+            unsigned long long* slot = d_slots + 5 * (size_t)i;
+            if (!rc && jb.P) {
+                SellMat* cache = o->up == SPAI_SINGLE ? &jb.P->sell_f32 : &jb.P->sell_f64;
+                if (!cache->off && !building.count(jb.P)) {
+                    rc = sell_begin(jb.n, jb.P->rowptr, num_sms, s, cache, nl);
+                    building.insert(jb.P);
+                    pbuild[i] = 1;
+                    if (!rc && cudaMemcpyAsync(slot + 4, cache->off + nsl, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                        rc = SPAI_ERR_CUDA;
+                }
+                jb.Ps = cache;
+            }
+            if (!rc) rc = ir_job_norms_x0(jb, num_sms, s, o, nl);
+            if (!rc && cudaMemcpyAsync(slot, jb.norms, 24, cudaMemcpyDeviceToDevice, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+            if (!rc && cudaMemcpyAsync(slot + 3, jb.As.off + nsl, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                rc = SPAI_ERR_CUDA;
         }
-        if (cudaStreamSynchronize(s) != cudaSuccess) return SPAI_ERR_CUDA;
+        // a preconditioner's SELL copy counts as built once its offsets exist: on
+        // failure the copies this batch started are dropped again
+        auto drop_started = [&]() {
+            for (spai_precond P : building) sell_free(o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64, s);
+        };
+        std::vector<unsigned long long> hs(5 * (size_t)count, 0);
+        if (!rc && cudaMemcpyAsync(hs.data(), d_slots, sizeof(unsigned long long) * hs.size(), cudaMemcpyDeviceToHost, s) !=
+                       cudaSuccess)
+            rc = SPAI_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
+        dev_free(d_slots, s);
+        if (rc) { drop_started(); return rc; }
+        for (int i : *order) {
+            IrJob& jb = J[i];
+            const unsigned long long* h = hs.data() + 5 * (size_t)i;
+            for (int k = 0; k < 3; k++) jb.h_norms[k] = h[k];
+            rc = sell_finish(jb.n, jb.A->rowptr, jb.A->col, jb.A->val, o->up, num_sms, s, &jb.As, (int64_t)h[3], nl);
+            if (!rc && pbuild[i])
+                rc = sell_finish(jb.n, jb.P->rowptr, jb.P->col, jb.P->val, o->up, num_sms, s,
+                                 o->up == SPAI_SINGLE ? &jb.P->sell_f32 : &jb.P->sell_f64, (int64_t)h[4], nl);
+            if (rc) { drop_started(); return rc; }
+        }
         // arguments in claim order (larger systems first), every system on T blocks
         std::vector<IrArgs> h(count);
         size_t smem = 0;

@@ -153,3 +153,23 @@ def test_spai_build_batch_matches_single_builds(ctx, adaptive):
         assert sts[i]["nnz_P"] == st1["nnz_P"] and sts[i]["cols_converged"] == st1["cols_converged"]
         P1.free()
         Ps[i].free()
+
+
+@pytest.mark.parametrize("orth,side", [(1, 0), (0, 1)])
+def test_batch_cgs2_and_right_preconditioning(ctx, orth, side):
+    As = mixed_systems()[:6]
+    io = S.make_ir_opts(tau=1e-4, orth=orth, side=side, **TUPLE)
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single", side=side)
+    Ps, _ = S.spai_build_batch(ctx, As, so)
+    bs, xts = zip(*[synth.rhs(A, seed=300 + i) for i, A in enumerate(As)])
+    xs = [np.zeros_like(b) for b in bs]
+    sts, status = S.gmres_ir_solve_batch(ctx, As, list(bs), xs, Ps, io)
+    for i, A in enumerate(As):
+        x1 = np.zeros_like(bs[i])
+        st1 = S.gmres_ir_solve(ctx, A, bs[i], x1, P=Ps[i], opts=io)
+        assert sts[i]["steps"] == st1["steps"], (i, sts[i]["its"], st1["its"])
+        assert abs(sts[i]["total_its"] - st1["total_its"]) <= max(1, 0.1 * st1["total_its"])
+        nb_b, fe_b = errors(A, bs[i], xs[i], xts[i])
+        nb_s, fe_s = errors(A, bs[i], x1, xts[i])
+        assert nb_b <= 10 * max(nb_s, 2.0 ** -53) and fe_b <= 10 * max(fe_s, 2.0 ** -53)
+        Ps[i].free()
