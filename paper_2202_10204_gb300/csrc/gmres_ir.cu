@@ -125,8 +125,16 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 // every block has read it.  The wait is bounded: on expiry SPAI_ERR_TIMEOUT
 // goes to *err and every block leaves.  Must be called by all threads after
 // a __syncthreads that follows the block's writes.
-template <int NW, bool DATA, class Acc, bool GRP = false>
-__device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const uint32_t* pay, Acc& acc)
+struct NoWork {
+    __device__ void operator()() const {}
+};
+
+// `work` runs on thread 0 after it has published the block's words and before
+// warp 0 starts polling: the other blocks' words take about a microsecond to
+// arrive, which hides short serial work there.
+template <int NW, bool DATA, class Acc, bool GRP = false, class Work = NoWork>
+__device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const uint32_t* pay, Acc& acc,
+                                         const Work& work = Work())
 {
     // GRP: a round of the Gram-Schmidt group (blocks 0..g2-1), with its own
     // slots and epoch; only the group's blocks may call it
@@ -140,6 +148,7 @@ __device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const ui
 #pragma unroll
             for (int k = 0; k < NW; k++)
                 st_relaxed_u64(base + (size_t)sh->bid * SLOT_WORDS + k, ((unsigned long long)ep << 32) | pay[k]);
+            work();
         }
         const unsigned lane = threadIdx.x;
         const long long t0 = clock64();
@@ -220,8 +229,8 @@ struct NoAcc {
 // is identical in every block.  DATA: the round also publishes the global
 // writes made before it (release/acquire); without it only the scalar
 // travels, in the same single-copy-atomic word as its epoch.
-template <bool DATA, class T, bool GRP = false>
-__device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out)
+template <bool DATA, class T, bool GRP = false, class Work = NoWork>
+__device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out, const Work& work = Work())
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_sum(v);
@@ -241,7 +250,7 @@ __device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out)
         }
     }
     SumAcc<T> acc;
-    bool good = exchange<NW, DATA, SumAcc<T>, GRP>(a, sh, pay, acc);
+    bool good = exchange<NW, DATA, SumAcc<T>, GRP>(a, sh, pay, acc, work);
     out = (T)sh->bcast[0];
     return good;
 }
@@ -357,7 +366,10 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
     IrShared* sh = &shs;
     const int kmax = a.kmax;
     const int tid = threadIdx.x, BT = blockDim.x;
-    const int GT = BT > 32 ? 32 : 0;  // the Givens thread: lane 0 of warp 1 (warp 0 polls)
+    // the Givens thread: thread 0, which also publishes the block's words, so that
+    // the rotations of the Gram-Schmidt rounds run while its warp waits for the
+    // other blocks
+    const int GT = 0;
     const int64_t r0 = (int64_t)bid * a.rb;
     const int64_t r1 = min(a.n, r0 + a.rb);
     // modified Gram-Schmidt rows [m0, m1): the block's own rows, or with a
@@ -562,18 +574,22 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         }
                     }
                     TG h;
-                    if (sub ? !xsum<false, TG, true>(a, sh, redg, part, h) : !xsum<false>(a, sh, redg, part, h)) return;
-                    if (tid == GT) {
-                        // Givens, pipelined with the rounds: rotation i-1 needs h_i
-                        hc[i] = (double)h;
-                        if (i >= 1) {
-                            const int q = i - 1;
-                            const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
-                            hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
-                            hc[q] = t0;
-                            if (bid == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
+                    // Givens, pipelined with the rounds: rotation q needs h_{q+1}, known
+                    // after round q+1; thread 0 applies it during round q+2, between
+                    // publishing and polling
+                    const int pq = i - 2;
+                    auto rot = [&]() {
+                        if (pq >= 0) {
+                            const double t0 = cs[pq] * hc[pq] + sn[pq] * hc[pq + 1];
+                            hc[pq + 1] = -sn[pq] * hc[pq] + cs[pq] * hc[pq + 1];
+                            hc[pq] = t0;
+                            if (bid == 0) a.R[(size_t)j * (kmax + 1) + pq] = hc[pq];
                         }
-                    }
+                    };
+                    if (sub ? !xsum<false, TG, true>(a, sh, redg, part, h, rot)
+                            : !xsum<false, TG, false>(a, sh, redg, part, h, rot))
+                        return;
+                    if (tid == GT) hc[i] = (double)h;
                     const TG* Vi = V + (int64_t)i * a.ldv;
                     part = TG(0);
                     if (i < j) {
@@ -611,6 +627,14 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         }
                     }
                 }
+                }
+                // the last rotation of the rounds, j-1 (the CGS2 branch applied all)
+                if (!a.orth && gs && tid == GT && j >= 1) {
+                    const int q = j - 1;
+                    const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
+                    hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
+                    hc[q] = t0;
+                    if (bid == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
                 }
                 // outside the group part is 0; block 0 stores the rotated diagonal
                 // entry h_jj (rotations 0..j-1 applied) in the unused last row of R's
