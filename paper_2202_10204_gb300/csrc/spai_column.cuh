@@ -7,18 +7,14 @@
 //   2. gather: a sorted warp merge of those lists (plus the list {k}) gives
 //      the shadow I_k and the dense tile [B(I_k,J_k) | e_k(I_k)] (row-major,
 //      shared memory);
-//   3. Householder QR of the tile and back substitution, either
-//        - register path (MM = 32/64): lane t keeps column t of the tile
-//          in registers; each step the pivot lane writes its column to
-//          shared memory, every lane forms its dot product with it (the
-//          pivot lane's own dot is ||x||^2), and the trailing lanes apply
-//          the reflector to their registers; back substitution is row
-//          oriented, m_c = (y_c - sum_t R(c,t) m_t) / R(c,c), one warp sum
-//          per row; or
-//        - shared-memory path (MM = 0, any |I_k| up to the tile height):
-//          the same steps in place on the tile in shared memory;
-//   4. explicit residual s = B(I,J) m - e and ||s||_2 from the original
-//      tile (register path) or from the row lists (shared-memory path);
+//   3. Householder QR of the tile and back substitution with the tile in
+//      registers (MM = 32/64 rows): lane t keeps column t; each step the
+//      pivot lane writes its column to shared memory, every lane forms its
+//      dot product with it (the pivot lane's own dot is ||x||^2), and the
+//      trailing lanes apply the reflector to their registers; back
+//      substitution is row oriented, m_c = (y_c - sum_t R(c,t) m_t) / R(c,c),
+//      one warp sum per row (larger shadows: spai_cta.cuh);
+//   4. explicit residual s = B(I,J) m - e and ||s||_2 from the original tile;
 //   5. adaptive: candidates J~ (column lists of A for l in I with s_l != 0,
 //      minus J), rho_j, mean acceptance, up to beta additions, loop.
 // Arithmetic: values are stored in u_f (S) and every inner product and
@@ -103,11 +99,13 @@ __device__ inline void warp_bitonic_sort(int32_t* a, int len2)
     }
 }
 
-// per-warp shared-memory layout
-template <class C>
+// per-warp shared-memory layout; the original tile W is kept in WT (u_f
+// itself at half: its entries are half values, and the smaller tile lets more
+// warps share an SM)
+template <class C, class WT = C>
 struct Tile {
     int32_t* I;     // mm
-    C* W;           // mm * LD: [B(I,J) | e] (the shared-memory path factors it in place)
+    WT* W;          // mm * LD: [B(I,J) | e]
     C* v;           // mm: pivot column / residual
     C* mb;          // 32
     int32_t* J;     // 32
@@ -121,11 +119,11 @@ struct Tile {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-template <class C>
+template <class C, class WT = C>
 __host__ __device__ inline size_t tile_bytes(int mm, int rl, int cmax)
 {
     size_t b = align16((size_t)mm * 4);
-    b += align16((size_t)mm * SPAI_LD * sizeof(C));
+    b += align16((size_t)mm * SPAI_LD * sizeof(WT));
     b += align16((size_t)mm * sizeof(C));
     b += align16(32 * sizeof(C)) + 3 * 32 * 4;
     b += align16((size_t)32 * rl * 4) + align16((size_t)32 * rl * sizeof(C));
@@ -133,13 +131,13 @@ __host__ __device__ inline size_t tile_bytes(int mm, int rl, int cmax)
     return align16(b);
 }
 
-template <class C>
-__device__ inline Tile<C> carve(unsigned char* base, int mm, int rl, int cmax)
+template <class C, class WT = C>
+__device__ inline Tile<C, WT> carve(unsigned char* base, int mm, int rl, int cmax)
 {
-    Tile<C> t;
+    Tile<C, WT> t;
     size_t off = 0;
     t.I = (int32_t*)(base + off); off += align16((size_t)mm * 4);
-    t.W = (C*)(base + off); off += align16((size_t)mm * SPAI_LD * sizeof(C));
+    t.W = (WT*)(base + off); off += align16((size_t)mm * SPAI_LD * sizeof(WT));
     t.v = (C*)(base + off); off += align16((size_t)mm * sizeof(C));
     t.mb = (C*)(base + off); off += align16(32 * sizeof(C));
     t.J = (int32_t*)(base + off); off += 32 * 4;
@@ -154,8 +152,13 @@ __device__ inline Tile<C> carve(unsigned char* base, int mm, int rl, int cmax)
 
 // Steps 1-2: lists of the rows in J, then the sorted merge.  Returns |I_k|
 // (which may exceed mm; then only the first mm rows were written).
-template <class S, class C>
-__device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, C* TW, const int32_t* TJ, int32_t* tlcol,
+template <class WT> __device__ __forceinline__ WT to_w(float v);
+template <> __device__ __forceinline__ __half to_w<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ float to_w<float>(float v) { return v; }
+template <class WT> __device__ __forceinline__ WT to_w(double v) { return (WT)v; }
+
+template <class S, class C, class WT>
+__device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, WT* TW, const int32_t* TJ, int32_t* tlcol,
                                            C* tlval, int32_t* tlcnt, int64_t k, int nj, int mm)
 {
     const int lane = threadIdx.x & 31;
@@ -199,7 +202,7 @@ __device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, C* TW
         const bool has = head == mn;
         if (m < mm) {
             if (lane == 0) TI[m] = mn;
-            if (lane <= nj) TW[m * SPAI_LD + lane] = has ? (lane < nj ? lv[q] : C(1)) : C(0);
+            if (lane <= nj) TW[m * SPAI_LD + lane] = to_w<WT>(has ? (lane < nj ? lv[q] : C(1)) : C(0));
         }
         m++;
         if (has) {
@@ -211,10 +214,10 @@ __device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, C* TW
     return m;
 }
 
-template <class S, class C>
-__device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C>& T, int64_t k, int nj, int mm)
+template <class S, class C, class WT>
+__device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C, WT>& T, int64_t k, int nj, int mm)
 {
-    return gather_ptrs<S, C>(a, T.I, T.W, T.J, T.lcol, T.lval, T.lcnt, k, nj, mm);
+    return gather_ptrs<S, C, WT>(a, T.I, T.W, T.J, T.lcol, T.lval, T.lcnt, k, nj, mm);
 }
 
 // Step 3, register path.  Returns flags (CF_SINGULAR); writes mbar to T.mb.
@@ -300,7 +303,7 @@ __device__ __forceinline__ float fma_f32_f16(__half a, __half b, float c)
 // reflector update a - f v is one packed f16 FMA per row pair, i.e. the
 // exact value rounded once to half (the stored trailing matrix lives in u_f).
 template <int MM>
-__device__ __forceinline__ int qr_solve_reg_half(const Tile<float>& T, int m, int nj)
+__device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, int m, int nj)
 {
     const int lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
@@ -309,9 +312,10 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float>& T, int m, in
 #pragma unroll
     for (int p = 0; p < NP; p++) {
         const int i0 = 2 * p, i1 = 2 * p + 1;
-        const float a0 = (i0 < m && lane <= nj) ? T.W[i0 * SPAI_LD + lane] : 0.f;
-        const float a1 = (i1 < m && lane <= nj) ? T.W[i1 * SPAI_LD + lane] : 0.f;
-        col[p] = __floats2half2_rn(a0, a1);  // exact: the tile holds half values
+        const __half zero = __float2half_rn(0.f);
+        const __half a0 = (i0 < m && lane <= nj) ? T.W[i0 * SPAI_LD + lane] : zero;
+        const __half a1 = (i1 < m && lane <= nj) ? T.W[i1 * SPAI_LD + lane] : zero;
+        col[p] = __halves2half2(a0, a1);
     }
     __half2* v2 = reinterpret_cast<__half2*>(T.v);  // NP packed pivot entries (16-byte aligned)
     const int steps = nj < m ? nj : m;
@@ -410,102 +414,16 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float>& T, int m, in
     return fl;
 }
 
-// Step 3, shared-memory path, in place on the tile.
-template <class S, class C>
-__device__ __forceinline__ int qr_solve_smem(const Tile<C>& T, int m, int nj)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
-    C* W = T.W;
-    const int steps = nj < m ? nj : m;
-    for (int c = 0; c < steps; c++) {
-        C g0 = 0, g1 = 0;
-        if (lane <= nj) {
-            int i = c;
-            for (; i + 1 < m; i += 2) {
-                g0 = fma(W[i * SPAI_LD + c], W[i * SPAI_LD + lane], g0);
-                g1 = fma(W[(i + 1) * SPAI_LD + c], W[(i + 1) * SPAI_LD + lane], g1);
-            }
-            if (i < m) g0 = fma(W[i * SPAI_LD + c], W[i * SPAI_LD + lane], g0);
-        }
-        const C g = g0 + g1;
-        const C sig2 = __shfl_sync(FULL, g, c);
-        const C nrm = rnd<S>(sqrt(sig2));
-        if (nrm == C(0)) continue;
-        const C x0 = W[c * SPAI_LD + c];
-        const C alpha = x0 >= C(0) ? -nrm : nrm;
-        const C v0 = rnd<S>(x0 - alpha);
-        const C vtv = C(2) * nrm * (nrm + fabs(x0));
-        __syncwarp();
-        if (lane > c && lane <= nj) {
-            const C act = W[c * SPAI_LD + lane];
-            const C sv = g + (v0 - x0) * act;
-            const C f = rnd<S>((sv + sv) / vtv);
-            W[c * SPAI_LD + lane] = rnd<S>(act - f * v0);
-            for (int i = c + 1; i < m; i++) W[i * SPAI_LD + lane] = rnd<S>(W[i * SPAI_LD + lane] - f * W[i * SPAI_LD + c]);
-        }
-        __syncwarp();
-        if (lane == c) W[c * SPAI_LD + c] = alpha;
-        __syncwarp();
-    }
-    int fl = 0;
-    C mv = 0;
-    for (int c = nj - 1; c >= 0; c--) {
-        C part = (lane > c && lane < nj) ? W[c * SPAI_LD + lane] * mv : C(0);
-        part = warp_sum(part);
-        const C yc = W[c * SPAI_LD + nj];
-        const C rcc = c < m ? W[c * SPAI_LD + c] : C(0);
-        C mc = 0;
-        if (rcc != C(0)) mc = rnd<S>(rnd<S>(yc - part) / rcc);
-        else fl = CF_SINGULAR;
-        if (lane == c) mv = mc;
-    }
-    if (lane < nj) T.mb[lane] = mv;
-    __syncwarp();
-    return fl;
-}
-
-// Step 4 (shared-memory path): s = B(I,J) mbar - e from the row lists, one
-// column at a time in order (lane-parallel over the column's entries, which
-// hit distinct rows); returns ||s||^2 (all lanes)
-template <class S, class C>
-__device__ __forceinline__ C residual_lists(const SpaiArgs& a, const Tile<C>& T, int64_t k, int m, int nj)
-{
-    const int lane = threadIdx.x & 31;
-    for (int p = lane; p < m; p += 32) T.v[p] = C(0);
-    __syncwarp();
-    for (int c = 0; c < nj; c++) {
-        const int len = T.lcnt[c];
-        const int32_t* lc = T.lcol + c * a.rl;
-        const C* lv = T.lval + c * a.rl;
-        const C mc = T.mb[c];
-        for (int q = lane; q < len; q += 32) {
-            const int p = bsearch_smem(T.I, m, lc[q]);
-            T.v[p] = fma(lv[q], mc, T.v[p]);
-        }
-        __syncwarp();
-    }
-    C part = 0;
-    for (int p = lane; p < m; p += 32) {
-        const C e = T.I[p] == (int)k ? C(1) : C(0);
-        const C sp = rnd<S>(rnd<S>(T.v[p]) - e);
-        T.v[p] = sp;
-        part = fma(sp, sp, part);
-    }
-    __syncwarp();
-    return warp_sum(part);
-}
-
-// Step 4 (register path): s = B(I,J) mbar - e from the unmodified tile
-template <class S, class C>
-__device__ __forceinline__ C residual(const Tile<C>& T, int m, int nj)
+// Step 4: s = B(I,J) mbar - e from the unmodified tile
+template <class S, class C, class WT>
+__device__ __forceinline__ C residual(const Tile<C, WT>& T, int m, int nj)
 {
     const int lane = threadIdx.x & 31;
     C part = 0;
     for (int p = lane; p < m; p += 32) {
         C acc = 0;
-        for (int c = 0; c < nj; c++) acc = fma(T.W[p * SPAI_LD + c], T.mb[c], acc);
-        const C sp = rnd<S>(rnd<S>(acc) - T.W[p * SPAI_LD + nj]);
+        for (int c = 0; c < nj; c++) acc = fma((C)to_c(T.W[p * SPAI_LD + c]), T.mb[c], acc);
+        const C sp = rnd<S>(rnd<S>(acc) - (C)to_c(T.W[p * SPAI_LD + nj]));
         T.v[p] = sp;
         part = fma(sp, sp, part);
     }
@@ -513,13 +431,25 @@ __device__ __forceinline__ C residual(const Tile<C>& T, int m, int nj)
     return warp_sum(part);
 }
 
+template <class S>
+struct TileStore {
+    typedef typename std::conditional<std::is_same<S, __half>::value, __half, typename Compute<S>::T>::type T;
+};
+
+// Launched with 64-thread blocks (two columns).  At u_f = half the bound lets
+// ten blocks share an SM (92-95 registers, no spills); single and double tiles
+// need more registers per lane and keep the compiler's choice.
+template <class S>
+constexpr int spai_min_blocks() { return std::is_same<S, __half>::value ? 10 : 1; }
+
 template <class S, bool ADAPTIVE, int MM>
-__global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
+__global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
 {
     typedef typename Compute<S>::T C;
+    typedef typename TileStore<S>::T WT;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const Tile<C> T = carve<C>(smem + (size_t)wib * a.warp_bytes, a.mmax, a.rl, a.cmax);
+    const Tile<C, WT> T = carve<C, WT>(smem + (size_t)wib * a.warp_bytes, a.mmax, a.rl, a.cmax);
     const unsigned FULL = 0xffffffffu;
     const int F = a.F;
     const int mm = a.mmax;
@@ -531,7 +461,7 @@ __global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
         int fl = 0, m = 0, ns = 0, nj_prev = nj, m_prev = 0;
         C snorm = 0;
         for (int step = 0;; step++) {
-            m = gather<S, C>(a, T, k, nj, mm);
+            m = gather<S, C, WT>(a, T, k, nj, mm);
             if (m > mm) {
                 fl |= CF_TOOBIG;
                 if (step == 0) {
@@ -545,15 +475,9 @@ __global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
                 }
                 break;
             }
-            C s2;
-            if (MM > 0) {
-                if constexpr (std::is_same<S, __half>::value) fl |= qr_solve_reg_half<(MM > 0 ? MM : 32)>(T, m, nj);
-                else fl |= qr_solve_reg<S, C, (MM > 0 ? MM : 32)>(T, m, nj);
-                s2 = residual<S, C>(T, m, nj);
-            } else {
-                fl |= qr_solve_smem<S, C>(T, m, nj);
-                s2 = residual_lists<S, C>(a, T, k, m, nj);
-            }
+            if constexpr (std::is_same<S, __half>::value) fl |= qr_solve_reg_half<MM>(T, m, nj);
+            else fl |= qr_solve_reg<S, C, MM>(T, m, nj);
+            const C s2 = residual<S, C, WT>(T, m, nj);
             snorm = rnd<S>(sqrt(s2));
             ns++;
             if (!isfinite((double)snorm)) fl |= CF_NONFINITE;
@@ -686,38 +610,29 @@ __global__ void __launch_bounds__(256) k_spai(SpaiArgs a)
 template <class S>
 int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
 
-// Launch for storage type S: the register path when the tile height fits
-// (32 or 64 rows), otherwise the shared-memory path.
+// Launch for storage type S: the warp kernel with its register tile for
+// shadows of up to 64 rows, the CTA kernel (spai_cta.cuh) for up to 512.
 template <class S>
 int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
 {
     typedef typename Compute<S>::T C;
+    typedef typename TileStore<S>::T WT;
     SpaiArgs a = a0;
     if (!adaptive) a.cmax = 0;
-    int MMsel = 0;
-    if (a.mmax <= 32) MMsel = 32;
-    else if (a.mmax <= 64) MMsel = 64;
-    else if (a.mmax <= 512) return launch_spai_cta_t<S>(a0, adaptive, num_sms, smem_cap, s);
-    if (MMsel) a.mmax = MMsel;
-    while (adaptive && a.cmax > 256 && tile_bytes<C>(a.mmax, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
-    const size_t wb = tile_bytes<C>(a.mmax, a.rl, a.cmax);
+    if (a.mmax > 64) return launch_spai_cta_t<S>(a0, adaptive, num_sms, smem_cap, s);
+    const int MMsel = a.mmax <= 32 ? 32 : 64;
+    a.mmax = MMsel;
+    while (adaptive && a.cmax > 256 && tile_bytes<C, WT>(a.mmax, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
+    const size_t wb = tile_bytes<C, WT>(a.mmax, a.rl, a.cmax);
     a.warp_bytes = (int)wb;
-    int wpb = (int)(smem_cap / wb);
-    // register-path warps hold their tile in registers: small blocks keep the
-    // occupancy granularity fine
-    if (wpb > (MMsel ? 2 : 8)) wpb = MMsel ? 2 : 8;
-    if (wpb < 1) return SPAI_ERR_UNSUPPORTED;
+    // two warps (columns) per block: register-tile warps gain nothing from
+    // sharing a larger block, and small blocks keep the occupancy granularity fine
+    const int wpb = 2;
+    if (wb * wpb > smem_cap) return SPAI_ERR_UNSUPPORTED;
     const size_t smem = wb * wpb;
     void (*kern)(SpaiArgs) = nullptr;
-    if (adaptive) {
-        if (MMsel == 32) kern = k_spai<S, true, 32>;
-        else if (MMsel == 64) kern = k_spai<S, true, 64>;
-        else kern = k_spai<S, true, 0>;
-    } else {
-        if (MMsel == 32) kern = k_spai<S, false, 32>;
-        else if (MMsel == 64) kern = k_spai<S, false, 64>;
-        else kern = k_spai<S, false, 0>;
-    }
+    if (adaptive) kern = MMsel == 32 ? k_spai<S, true, 32> : k_spai<S, true, 64>;
+    else kern = MMsel == 32 ? k_spai<S, false, 32> : k_spai<S, false, 64>;
     SPAI_CUDA_TRY(allow_max_dynamic_smem(kern));
     int64_t blocks = (a.n + wpb - 1) / wpb;
     const int64_t cap = (int64_t)num_sms * 64;
