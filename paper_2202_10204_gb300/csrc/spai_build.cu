@@ -213,21 +213,43 @@ __device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, const 
 
 // ---------------------------------------------------------------- pattern
 
+// Insert `key` into the shared-memory hash set `tab` (mask + 1 = 2^(32 -
+// shift) slots, empty = -1, linear probing from the top bits of Knuth's
+// multiplicative hash); returns 1 if it was not there yet.  The set is sized
+// to at least twice the keys it receives, so a probe always ends.
+__device__ __forceinline__ int hash_insert(int32_t* tab, unsigned mask, int shift, int key)
+{
+    unsigned h = ((unsigned)key * 2654435761u) >> shift;
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int old = atomicCAS(&tab[h], -1, key);
+        if (old == -1) return 1;
+        if (old == key) return 0;
+        h = (h + 1u) & mask;
+    }
+    return 0;
+}
+
 // Initial pattern J_k (identity, pattern(A), pattern(A^2)), capped at F
 // keeping k and then the nearest indices (ties to the smaller index), and
 // the shadow size |I_k| = |union of the nonzero columns of rows j in J_k,
 // plus k|.  One warp per column.  Per-warp shared memory: buf[cap] for the
-// uncapped pattern and 32 lists of `stride` ints.
+// uncapped pattern, 32 lists of `stride` ints, and a hash set of tsz slots
+// that counts the shadow (its size only is needed, so no sorted merge).
 __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                           const double* __restrict__ val, const int64_t* __restrict__ cp,
                           const int32_t* __restrict__ ri, int32_t* __restrict__ Jidx, int32_t* __restrict__ Jcnt,
-                          int32_t* __restrict__ Icnt, int cap, int stride, int* __restrict__ err,
+                          int32_t* __restrict__ Icnt, int cap, int stride, int tsz, int* __restrict__ err,
                           int* __restrict__ maxI)
 {
     extern __shared__ int32_t pbuf[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    int32_t* buf = pbuf + (size_t)wib * (cap + 32 * stride);
+    int32_t* buf = pbuf + (size_t)wib * (cap + 32 * stride + tsz);
     int32_t* lst = buf + cap;
+    int32_t* tab = lst + 32 * stride;
+    const unsigned tmask = (unsigned)tsz - 1u;
+    const int tshift = __clz(tsz) + 1;  // tsz = 2^(31 - clz)
+    for (int t = lane; t < tsz; t += 32) tab[t] = -1;
+    __syncwarp();
     for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < n; k += (int64_t)gridDim.x * wpb) {
         int cnt = 0;
         if (init == SPAI_PAT_IDENTITY) {
@@ -278,15 +300,22 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         for (int t = lane; t < F; t += 32) Jidx[k * F + t] = t < nj ? buf[lo + t] : -1;
         if (lane == 0) Jcnt[k] = nj;
         __syncwarp();
-        // shadow size of the (initial) pattern
-        int len = 0;
-        if (lane < nj) len = load_list(col, val, rp[jl], rp[jl + 1], lst, stride);
-        __syncwarp();
-        const int mI = warp_union(lst, stride, len, nj, (int)k, nullptr, 0);
+        // shadow size of the (initial) pattern: |{k} and the nonzero columns of rows J_k|
+        int mine = lane == 0 ? hash_insert(tab, tmask, tshift, (int)k) : 0;
+        if (lane < nj) {
+            const int64_t b = rp[jl], e = rp[jl + 1];
+            for (int64_t q = b; q < e; q++)
+                if (val[q] != 0.0) mine += hash_insert(tab, tmask, tshift, col[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        const int mI = mine;
         if (lane == 0) {
             Icnt[k] = mI;
             atomicMax(maxI, mI);
         }
+        __syncwarp();
+        for (int t = lane; t < tsz; t += 32) tab[t] = -1;
         __syncwarp();
     }
 }
@@ -579,17 +608,21 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     }
     {
         // the pattern and its shadow sizes: per warp a buffer for the uncapped
-        // union of pattern(A^2) and 32 lists
-        const int cap = 1024;
+        // pattern (pattern(A^2): at most maxcol^2 entries), 32 lists, and a hash
+        // set of at least twice the shadow entries a column can bring
+        const int cap = o->init == SPAI_PAT_A2 ? (int)std::min<int64_t>(1024, std::max<int64_t>(32, (int64_t)maxcol * maxcol))
+                                               : std::max(32, maxcol);
         const int stride = std::max(maxrow, maxcol);
+        int tsz = 64;
+        while (tsz < 2 * ((int64_t)F * maxrow + 1)) tsz <<= 1;
         const int wpb = 4;
-        const size_t sm = (size_t)(cap + 32 * stride) * 4 * wpb;
+        const size_t sm = (size_t)(cap + 32 * stride + tsz) * 4 * wpb;
         if (sm > smem_cap) { rc = SPAI_ERR_UNSUPPORTED; goto done; }
         SPAI_CUDA_TRY(allow_max_dynamic_smem(k_pattern));
         int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms * 64);
         if (blocks < 1) blocks = 1;
         k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, A.rowptr, A.col, A.val, cp, ri, Jidx, Jcnt,
-                                                        Icnt, cap, stride, err, err + 1);
+                                                        Icnt, cap, stride, tsz, err, err + 1);
         nl += 1;
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaMemcpyAsync(h_err, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
