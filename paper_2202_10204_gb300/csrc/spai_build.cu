@@ -4,6 +4,7 @@
 //
 // Steps (each a kernel):
 //   k_scale        d_j = 1 / max_i |a_ji|: every column of A^T (row of A) to max-abs 1
+//   k_bvals        b = fl(a_ij d_j) in u_f, once per nonzero of A (the gather reads these)
 //   k_col_count / k_col_fill / k_col_sort
 //                  structure of A^T (column lists of A) for pattern(A), pattern(A^2)
 //                  and the candidate sets N_l of the adaptive step
@@ -43,6 +44,21 @@ __global__ void k_scale(int64_t n, const int64_t* __restrict__ rp, const double*
         if (!fin) atomicCAS(err, 0, SPAI_ERR_NONFINITE);
         if (mx == 0.0) atomicCAS(err, 0, SPAI_ERR_ZERO_ROW);
         d[i] = scale ? (mx > 0.0 ? 1.0 / mx : 1.0) : 1.0;
+    }
+}
+
+// b = fl_S(a_ij d_j) for every nonzero of row j of A, once, in the storage
+// precision the column kernels read; explicit zeros get the marker pattern
+template <class S>
+__global__ void k_bvals(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ val,
+                        const double* __restrict__ d, S* __restrict__ bv)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double dj = d[j];
+        for (int64_t q = rp[j]; q < rp[j + 1]; q++) {
+            const double a = val[q];
+            bv[q] = a != 0.0 ? from_d<S>(a * dj) : bmark<S>();
+        }
     }
 }
 
@@ -551,6 +567,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     int32_t *Jidx = nullptr, *Jcnt = nullptr, *Icnt = nullptr, *flags = nullptr, *nsolve = nullptr;
     double *Praw = nullptr, *colres = nullptr;
     void* mval = nullptr;
+    void* bval = nullptr;
     unsigned long long* fstat = nullptr;
     size_t ssz = o->uf == SPAI_HALF ? 2 : (o->uf == SPAI_SINGLE ? 4 : 8);
     spai_precond P = nullptr;
@@ -574,6 +591,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     TRY(dev_alloc((void**)&Praw, sizeof(double) * n * F, s));
     TRY(dev_alloc((void**)&colres, sizeof(double) * n, s));
     TRY(dev_alloc(&mval, ssz * n * F, s));
+    TRY(dev_alloc(&bval, ssz * (nnz > 0 ? nnz : 1), s));
     TRY(dev_alloc((void**)&fstat, sizeof(unsigned long long) * 3, s));
     if (cudaMemsetAsync(err, 0, sizeof(int) * 5, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -583,7 +601,10 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         int gb = (int)std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32);
         if (gb < 1) gb = 1;
         k_scale<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, o->scale, d, err);
-        nl++;
+        if (o->uf == SPAI_HALF) k_bvals<__half><<<gb, tb, 0, s>>>(n, A.rowptr, A.val, d, (__half*)bval);
+        else if (o->uf == SPAI_SINGLE) k_bvals<float><<<gb, tb, 0, s>>>(n, A.rowptr, A.val, d, (float*)bval);
+        else k_bvals<double><<<gb, tb, 0, s>>>(n, A.rowptr, A.val, d, (double*)bval);
+        nl += 2;
         int gq = (int)std::min<int64_t>((nnz + tb - 1) / tb, (int64_t)num_sms * 32);
         if (gq < 1) gq = 1;
         k_col_count<<<gq, tb, 0, s>>>(nnz, A.col, ccount);
@@ -632,7 +653,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     {
         SpaiArgs a;
         memset(&a, 0, sizeof(a));
-        a.n = n; a.F = F; a.rp = A.rowptr; a.col = A.col; a.val = A.val; a.cp = cp; a.ri = ri; a.d = d;
+        a.n = n; a.F = F; a.rp = A.rowptr; a.col = A.col; a.val = A.val; a.cp = cp; a.ri = ri; a.d = d; a.bval = bval;
         a.Jidx = Jidx; a.Jcnt = Jcnt; a.Praw = Praw; a.mval = mval; a.colres = colres; a.flags = flags;
         a.Icnt = Icnt; a.nsolve = nsolve; a.eps = o->eps;
         a.alpha = o->alpha < 0 ? (int)((n + o->beta - 1) / std::max(o->beta, 1)) : o->alpha;
@@ -712,7 +733,7 @@ done:
 #undef TRY
     dev_free(d, s); dev_free(err, s); dev_free(ccount, s); dev_free(cp, s); dev_free(ri, s);
     dev_free(Jidx, s); dev_free(Jcnt, s); dev_free(Icnt, s); dev_free(flags, s); dev_free(nsolve, s);
-    dev_free(Praw, s); dev_free(colres, s); dev_free(mval, s); dev_free(fstat, s);
+    dev_free(Praw, s); dev_free(colres, s); dev_free(mval, s); dev_free(bval, s); dev_free(fstat, s);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(ek0);

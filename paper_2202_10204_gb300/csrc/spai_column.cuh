@@ -8,12 +8,15 @@
 //      the shadow I_k and the dense tile [B(I_k,J_k) | e_k(I_k)] (row-major,
 //      shared memory);
 //   3. Householder QR of the tile and back substitution with the tile in
-//      registers (MM = 32/64 rows): lane t keeps column t; each step the
-//      pivot lane writes its column to shared memory, every lane forms its
-//      dot product with it (the pivot lane's own dot is ||x||^2), and the
-//      trailing lanes apply the reflector to their registers; back
-//      substitution is row oriented, m_c = (y_c - sum_t R(c,t) m_t) / R(c,c),
-//      one warp sum per row (larger shadows: spai_cta.cuh);
+//      registers (MM = 32/64 rows).  Single and double: lane t keeps column
+//      t; each step the pivot lane writes its column to shared memory, every
+//      lane forms its dot product with it (the pivot lane's own dot is
+//      ||x||^2), and the trailing lanes apply the reflector to their
+//      registers.  Half: the tile is held in the A-operand layout of
+//      m16n8k16 MMAs and each step's 32 dot products are one tensor-core
+//      matrix-vector product.  Back substitution is row oriented,
+//      m_c = (y_c - sum_t R(c,t) m_t) / R(c,c), one warp sum per row
+//      (larger shadows: spai_cta.cuh);
 //   4. explicit residual s = B(I,J) m - e and ||s||_2 from the original tile;
 //   5. adaptive: candidates J~ (column lists of A for l in I with s_l != 0,
 //      minus J), rho_j, mean acceptance, up to beta additions, loop.
@@ -34,6 +37,7 @@ namespace spai {
 constexpr int SPAI_LD = 33;       // row stride of the tile (32 columns + pad)
 constexpr int SPAI_MAX_FILL = 31; // |J_k| <= 31 so that [B(I,J) | e] fits 32 lanes
 constexpr int SPAI_MMAX_LIMIT = 512;
+constexpr int SPAI_LDR = 40;      // column stride of R (rows 0..31) in shared memory, half path
 
 #define CF_CONVERGED 1
 #define CF_FILLCAP 2
@@ -52,6 +56,7 @@ struct SpaiArgs {
     const int64_t* cp;   // A^T structure (adaptive)
     const int32_t* ri;
     const double* d;
+    const void* bval;    // nnz of A in u_f: b = fl(a_ij d_j), explicit zeros marked (bmark)
     int32_t* Jidx;       // n * F, in: initial pattern, out: final pattern
     int32_t* Jcnt;       // n
     double* Praw;        // n * F: mbar * d(J)
@@ -99,6 +104,26 @@ __device__ inline void warp_bitonic_sort(int32_t* a, int len2)
     }
 }
 
+// The entries of B = A^T D in the storage precision S, one per nonzero of A
+// in its CSR order: b = fl_S(a_ij d_j), rounded once from the exact double
+// product.  An explicit zero of A is stored as the all-ones bit pattern (a
+// NaN, which no finite product rounds to), so the structural test a_ij != 0
+// of the shadow needs no second array.
+template <class S> __device__ __forceinline__ bool bmarked(S v);
+template <> __device__ __forceinline__ bool bmarked<__half>(__half v) { return __half_as_ushort(v) == 0xffffu; }
+template <> __device__ __forceinline__ bool bmarked<float>(float v) { return __float_as_uint(v) == 0xffffffffu; }
+template <> __device__ __forceinline__ bool bmarked<double>(double v) { return __double_as_longlong(v) == -1LL; }
+template <class S> __device__ __forceinline__ S bmark();
+template <> __device__ __forceinline__ __half bmark<__half>() { return __ushort_as_half((unsigned short)0xffffu); }
+template <> __device__ __forceinline__ float bmark<float>() { return __uint_as_float(0xffffffffu); }
+template <> __device__ __forceinline__ double bmark<double>() { return __longlong_as_double(-1LL); }
+// b as a compute-type value, explicit zeros as 0
+template <class S> __device__ __forceinline__ typename Compute<S>::T bvalue(S v)
+{
+    typedef typename Compute<S>::T C;
+    return bmarked<S>(v) ? C(0) : (C)to_c(v);
+}
+
 // per-warp shared-memory layout; the original tile W is kept in WT (u_f
 // itself at half: its entries are half values, and the smaller tile lets more
 // warps share an SM)
@@ -115,6 +140,7 @@ struct Tile {
     int32_t* lcnt;  // 32
     int32_t* cand;  // cmax
     C* rho;         // cmax
+    WT* R;          // 32 * SPAI_LDR, column-major R(0:31, 0:31) (half path only)
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -128,6 +154,7 @@ __host__ __device__ inline size_t tile_bytes(int mm, int rl, int cmax)
     b += align16(32 * sizeof(C)) + 3 * 32 * 4;
     b += align16((size_t)32 * rl * 4) + align16((size_t)32 * rl * sizeof(C));
     b += align16((size_t)cmax * 4) + align16((size_t)cmax * sizeof(C));
+    if (std::is_same<WT, __half>::value) b += align16((size_t)32 * SPAI_LDR * sizeof(WT));
     return align16(b);
 }
 
@@ -146,7 +173,8 @@ __device__ inline Tile<C, WT> carve(unsigned char* base, int mm, int rl, int cma
     t.lcol = (int32_t*)(base + off); off += align16((size_t)32 * rl * 4);
     t.lval = (C*)(base + off); off += align16((size_t)32 * rl * sizeof(C));
     t.cand = (int32_t*)(base + off); off += align16((size_t)cmax * 4);
-    t.rho = (C*)(base + off);
+    t.rho = (C*)(base + off); off += align16((size_t)cmax * sizeof(C));
+    t.R = std::is_same<WT, __half>::value ? (WT*)(base + off) : nullptr;
     return t;
 }
 
@@ -166,23 +194,23 @@ __device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, WT* T
     int len = 0;
     if (lane < nj) {
         const int j = TJ[lane];
-        const double dj = a.d[j];
+        const S* bv = (const S*)a.bval;
         const int64_t b = a.rp[j], e = a.rp[j + 1];
         int32_t* lc = tlcol + lane * a.rl;
         C* lv = tlval + lane * a.rl;
         for (int64_t q = b; q < e; q += 4) {
-            double vv[4];
+            S vv[4];
             int cc[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                vv[u] = q + u < e ? a.val[q + u] : 0.0;
+                vv[u] = q + u < e ? bv[q + u] : bmark<S>();
                 cc[u] = q + u < e ? a.col[q + u] : 0;
             }
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                if (vv[u] != 0.0) {  // the shadow counts |a_ij| != 0
+                if (!bmarked<S>(vv[u])) {  // the shadow counts |a_ij| != 0
                     lc[len] = cc[u];
-                    lv[len] = to_c(from_d<S>(vv[u] * dj));
+                    lv[len] = to_c(vv[u]);
                     len++;
                 }
             }
@@ -289,124 +317,185 @@ __device__ __forceinline__ int qr_solve_reg(const Tile<C>& T, int m, int nj)
     return fl;
 }
 
-// d = a * b + c with f16 operands and an f32 accumulator, one rounding
-// (the FP16-operand / FP32-accumulate product of the u_f = half model)
-__device__ __forceinline__ float fma_f32_f16(__half a, __half b, float c)
+// d += a b on the tensor cores: one m16n8k16 tile, f16 operands, f32
+// accumulators (a: 16 x 16 row-major fragment, b: 16 x 8 column-major)
+__device__ __forceinline__ void mma_f16_f32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
 {
-    float d;
-    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(__half_as_ushort(a)), "h"(__half_as_ushort(b)), "f"(c));
-    return d;
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Step 3, register path for u_f = half: lane t keeps column t as MM/2
-// packed half2 registers.  Dot products use f16 x f16 -> f32 FMAs; the
-// reflector update a - f v is one packed f16 FMA per row pair, i.e. the
-// exact value rounded once to half (the stored trailing matrix lives in u_f).
+__device__ __forceinline__ unsigned h2_bits(__half2 v) { return *reinterpret_cast<unsigned*>(&v); }
+__device__ __forceinline__ __half2 bits_h2(unsigned v) { return *reinterpret_cast<__half2*>(&v); }
+// element h (0 = low = the even row, 1 = high) of a packed pair
+__device__ __forceinline__ float pair_elem(unsigned v, int h)
+{
+    return __half2float(__ushort_as_half((unsigned short)(h ? v >> 16 : v & 0xffffu)));
+}
+__device__ __forceinline__ unsigned pair_set(unsigned v, int h, __half x)
+{
+    const unsigned b = __half_as_ushort(x);
+    return h ? ((v & 0xffffu) | (b << 16)) : ((v & 0xffff0000u) | b);
+}
+
+// Step 3, register path for u_f = half, on the tensor cores.  The tile X
+// (rows r < MM, columns t < 32) is held in the A-operand layout of
+// m16n8k16 MMAs that compute X^T v: with g = lane / 4 and q = lane % 4, the
+// lane holds columns t = g + 8s (slots s = 0..3) at rows 16 ks + 2q + {0, 1,
+// 8, 9} as packed half pairs, X[ks][s / 2][s % 2 (+ 2 for rows 8, 9)].  Per
+// reflector step the pivot column is shuffled into the B operand (every
+// lane q needs the rows its A fragment holds, from the lane of the pivot's
+// group with the same q), and the MMAs give all 32 dot products v^T x_t
+// with f16 x f16 products accumulated in f32; the lane of slot q then
+// forms the reflector scalar f of column g + 8q, the quad exchanges them,
+// and the update a - f v is one packed f16 FMA per row pair (the exact
+// value rounded once to half: the trailing matrix is stored in u_f).
 template <int MM>
 __device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, int m, int nj)
 {
+    static_assert(MM % 16 == 0, "tile height is a multiple of the MMA k-step");
+    constexpr int KS = MM / 16;
     const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, q = lane & 3;
     const unsigned FULL = 0xffffffffu;
-    constexpr int NP = MM / 2;
-    __half2 col[NP];
+    unsigned X[KS][2][4];
 #pragma unroll
-    for (int p = 0; p < NP; p++) {
-        const int i0 = 2 * p, i1 = 2 * p + 1;
-        const __half zero = __float2half_rn(0.f);
-        const __half a0 = (i0 < m && lane <= nj) ? T.W[i0 * SPAI_LD + lane] : zero;
-        const __half a1 = (i1 < m && lane <= nj) ? T.W[i1 * SPAI_LD + lane] : zero;
-        col[p] = __halves2half2(a0, a1);
-    }
-    __half2* v2 = reinterpret_cast<__half2*>(T.v);  // NP packed pivot entries (16-byte aligned)
+    for (int ks = 0; ks < KS; ks++)
+#pragma unroll
+        for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+            for (int rg = 0; rg < 4; rg++) {
+                const int t = 16 * mt + g + ((rg & 1) ? 8 : 0);
+                const int r0 = 16 * ks + 2 * q + ((rg & 2) ? 8 : 0);
+                const __half zero = __float2half_rn(0.f);
+                const __half a0 = (r0 < m && t <= nj) ? T.W[r0 * SPAI_LD + t] : zero;
+                const __half a1 = (r0 + 1 < m && t <= nj) ? T.W[(r0 + 1) * SPAI_LD + t] : zero;
+                X[ks][mt][rg] = h2_bits(__halves2half2(a0, a1));
+            }
     const int steps = nj < m ? nj : m;
 #pragma unroll
     for (int c = 0; c < SPAI_MAX_FILL; c++) {
         if (c < steps) {
-            if (lane == c) {
+            // where column c and row c live
+            const int sc = c >> 3, gc = c & 7;          // slot and group of column c
+            const int ksc = c >> 4, rrc = c & 15;
+            const int rh = rrc >= 8 ? 2 : 0;              // register pair of row c (+0 or +2)
+            const int qc = (rrc & 7) >> 1, hc = rrc & 1;  // lane q and half of row c
+            const int mt0 = c >= 16 ? 1 : 0;              // columns below 16 mt0 are done
+            // B operand: the pivot column with rows above c zeroed
+            unsigned Bv[KS][2];
 #pragma unroll
-                for (int p = 0; p < NP; p += 4) {
-                    __half2 q[4];
+            for (int ks = 0; ks < KS; ks++) {
+                if (ks < ksc) continue;
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const int i0 = 2 * (p + u);
-                        __half2 x = col[p + u];
-                        if (i0 + 1 < c) x = __float2half2_rn(0.f);
-                        else if (i0 < c) x = __halves2half2(__float2half_rn(0.f), __high2half(x));
-                        q[u] = x;
+                for (int u = 0; u < 2; u++) {
+                    unsigned v = __shfl_sync(FULL, X[ks][sc >> 1][(sc & 1) + 2 * u], gc * 4 + q);
+                    if (ks == ksc) {
+                        const int r = 16 * ks + 2 * q + 8 * u;
+                        if (r + 1 < c) v = 0u;
+                        else if (r < c) v &= 0xffff0000u;
                     }
-                    *reinterpret_cast<uint4*>(v2 + p) = *reinterpret_cast<uint4*>(q);
+                    Bv[ks][u] = v;
                 }
             }
-            __syncwarp();
-            float g0 = 0.f, g1 = 0.f;
+            float D[2][4];
 #pragma unroll
-            for (int p = 0; p < NP; p += 4) {
-                if (2 * (p + 4) > c) {
-                    uint4 raw = *reinterpret_cast<const uint4*>(v2 + p);
-                    const __half2* q = reinterpret_cast<const __half2*>(&raw);
+            for (int mt = 0; mt < 2; mt++) {
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        g0 = fma_f32_f16(__low2half(q[u]), __low2half(col[p + u]), g0);
-                        g1 = fma_f32_f16(__high2half(q[u]), __high2half(col[p + u]), g1);
-                    }
-                }
+                for (int e = 0; e < 4; e++) D[mt][e] = 0.f;
+                if (mt < mt0) continue;
+#pragma unroll
+                for (int ks = 0; ks < KS; ks++)
+                    if (ks >= ksc) mma_f16_f32(D[mt], X[ks][mt], Bv[ks][0], Bv[ks][1]);
             }
-            const float g = g0 + g1;
-            const float sig2 = __shfl_sync(FULL, g, c);
-            const float xc_own = (c & 1) ? __high2float(col[c / 2]) : __low2float(col[c / 2]);
-            const float x0 = __shfl_sync(FULL, xc_own, c);
+            // slot s's dot product: D[s / 2][2 (s % 2)] (every column of B is v)
+            const float sig2 = __shfl_sync(FULL, D[sc >> 1][2 * (sc & 1)], gc * 4);
+            // row c of this lane's four columns (meaningful in the lanes q == qc)
+            const unsigned rc01 = (hc ? (X[ksc][0][rh] >> 16) | (X[ksc][0][rh + 1] & 0xffff0000u)
+                                      : (X[ksc][0][rh] & 0xffffu) | (X[ksc][0][rh + 1] << 16));
+            const unsigned rc23 = (hc ? (X[ksc][1][rh] >> 16) | (X[ksc][1][rh + 1] & 0xffff0000u)
+                                      : (X[ksc][1][rh] & 0xffffu) | (X[ksc][1][rh + 1] << 16));
+            const float x0 = __shfl_sync(FULL, pair_elem(sc < 2 ? rc01 : rc23, sc & 1), gc * 4 + qc);
             const float nrm = rnd<__half>(sqrtf(sig2));
             if (nrm != 0.f) {
                 const float alpha = x0 >= 0.f ? -nrm : nrm;
                 const float v0 = rnd<__half>(x0 - alpha);
                 const float vtv = 2.f * nrm * (nrm + fabsf(x0));
-                if (lane > c && lane <= nj) {
-                    const float act = xc_own;
-                    const float sv = g + (v0 - x0) * act;
-                    const __half f = __float2half_rn((sv + sv) / vtv);
-                    const __half2 nf = __halves2half2(__hneg(f), __hneg(f));
+                // the lane of slot q forms f for column g + 8q
+                const unsigned a01 = __shfl_sync(FULL, rc01, g * 4 + qc);
+                const unsigned a23 = __shfl_sync(FULL, rc23, g * 4 + qc);
+                const int tq = g + 8 * q;
+                const float gq = q == 0 ? D[0][0] : q == 1 ? D[0][2] : q == 2 ? D[1][0] : D[1][2];
+                const float act = pair_elem(q < 2 ? a01 : a23, q & 1);
+                __half f = __float2half_rn(0.f);
+                if (tq > c && tq <= nj) {
+                    const float sv = gq + (v0 - x0) * act;
+                    f = __float2half_rn((sv + sv) / vtv);
+                }
+                // quad exchange: pair (f of slots 0, 1) and pair (slots 2, 3)
+                const unsigned fb = __half_as_ushort(f);
+                const unsigned fo = __shfl_xor_sync(FULL, fb, 1);
+                const unsigned pr = (q & 1) ? (fo | (fb << 16)) : (fb | (fo << 16));
+                const unsigned po = __shfl_xor_sync(FULL, pr, 2);
+                const unsigned f01 = (q & 2) ? po : pr, f23 = (q & 2) ? pr : po;
+                // update operand: v with row c = v0
+                if (q == qc) Bv[ksc][rh >> 1] = pair_set(Bv[ksc][rh >> 1], hc, __float2half_rn(v0));
 #pragma unroll
-                    for (int p = 0; p < NP; p += 4) {
-                        if (2 * (p + 4) > c) {
-                            uint4 raw = *reinterpret_cast<const uint4*>(v2 + p);
-                            __half2* q = reinterpret_cast<__half2*>(&raw);
+                for (int s = 0; s < 4; s++) {
+                    const int t = g + 8 * s;
+                    if (8 * s + 7 <= c) continue;  // every column of this slot is final
+                    if (t > c && t <= nj) {
+                        const unsigned fp = s < 2 ? f01 : f23;
+                        const unsigned fs = (s & 1) ? (fp >> 16) : (fp & 0xffffu);
+                        const __half2 nf = __hneg2(bits_h2(fs | (fs << 16)));
 #pragma unroll
-                            for (int u = 0; u < 4; u++) {
-                                const int i0 = 2 * (p + u);
-                                if (i0 + 1 < c) continue;  // rows above the pivot are final
-                                __half2 vv = q[u];
-                                // row c uses v0 instead of x0
-                                if (i0 == c) vv = __halves2half2(__float2half_rn(v0), __high2half(vv));
-                                else if (i0 + 1 == c) vv = __halves2half2(__low2half(vv), __float2half_rn(v0));
-                                col[p + u] = __hfma2(nf, vv, col[p + u]);
+                        for (int ks = 0; ks < KS; ks++) {
+                            if (ks < ksc) continue;
+#pragma unroll
+                            for (int u = 0; u < 2; u++) {
+                                unsigned& x = X[ks][s >> 1][(s & 1) + 2 * u];
+                                x = h2_bits(__hfma2(nf, bits_h2(Bv[ks][u]), bits_h2(x)));
                             }
                         }
                     }
                 }
-                if (lane == c) {
-                    const __half al = __float2half_rn(alpha);
-                    if (c & 1) col[c / 2] = __halves2half2(__low2half(col[c / 2]), al);
-                    else col[c / 2] = __halves2half2(al, __high2half(col[c / 2]));
+                // the pivot column's row c becomes alpha
+                if (g == gc && q == qc) {
+                    unsigned& x = X[ksc][sc >> 1][(sc & 1) + rh];
+                    x = pair_set(x, hc, __float2half_rn(alpha));
                 }
             }
-            __syncwarp();
         }
     }
-    // back substitution, row oriented: R(c, t) is element c of lane t's column
+    // back substitution, column oriented: R (rows and columns 0..31) goes to
+    // shared memory column-major; lane t keeps y_t = R(t, nj) minus the
+    // products R(t, c) m_c of the solved rows (f32 FMAs), and m_c =
+    // fl_h(fl_h(y_c) / R(c, c)) leaves a chain of one shuffle and one division
+    // per row
+    __half* Rs = T.R;
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int ks = 0; ks < (KS < 2 ? KS : 2); ks++)
+#pragma unroll
+            for (int u = 0; u < 2; u++)
+                *reinterpret_cast<unsigned*>(Rs + (g + 8 * s) * SPAI_LDR + 16 * ks + 2 * q + 8 * u) = X[ks][s >> 1][(s & 1) + 2 * u];
+    __syncwarp();
     int fl = 0;
+    float y = lane < nj ? __half2float(Rs[nj * SPAI_LDR + lane]) : 0.f;
     float mv = 0.f;
 #pragma unroll
     for (int c = SPAI_MAX_FILL - 1; c >= 0; c--) {
         if (c < nj) {
-            const float rc = (c & 1) ? __high2float(col[c / 2]) : __low2float(col[c / 2]);
-            float part = (lane > c && lane < nj) ? rc * mv : 0.f;
-            part = warp_sum(part);
-            const float yc = __shfl_sync(FULL, rc, nj);
-            const float rcc = __shfl_sync(FULL, rc, c);
+            const float rcc = __half2float(Rs[c * SPAI_LDR + c]);
+            const float rtc = __half2float(Rs[c * SPAI_LDR + lane]);
+            const float yc = __shfl_sync(FULL, y, c);
             float mc = 0.f;
-            if (c < m && rcc != 0.f) mc = rnd<__half>(rnd<__half>(yc - part) / rcc);
+            if (c < m && rcc != 0.f) mc = rnd<__half>(rnd<__half>(yc) / rcc);
             else fl = CF_SINGULAR;
             if (lane == c) mv = mc;
+            if (lane < c) y = fmaf(-rtc, mc, y);
         }
     }
     if (lane < nj) T.mb[lane] = mv;
@@ -529,10 +618,9 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
             // ---- rho_j^2 = ||s||^2 - (s^T b_j)^2 / ||b_j||^2
             for (int t = lane; t < u; t += 32) {
                 const int j = T.cand[t];
-                const double djj = a.d[j];
                 C num = 0, den = 0;
                 for (int64_t q = a.rp[j]; q < a.rp[j + 1]; q++) {
-                    const C bij = to_c(from_d<S>(a.val[q] * djj));
+                    const C bij = bvalue<S>(((const S*)a.bval)[q]);
                     const int p = bsearch_smem(T.I, m, a.col[q]);
                     if (p >= 0) num = fma(T.v[p], bij, num);
                     if (!a.rho_restricted || p >= 0) den = fma(bij, bij, den);

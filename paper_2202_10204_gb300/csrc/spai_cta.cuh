@@ -338,10 +338,9 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
             // ---- rho_j for every candidate
             for (int t = tid; t < u; t += BT) {
                 const int j = T.cand[t];
-                const double djj = a.d[j];
                 C num = 0, den = 0;
                 for (int64_t q = a.rp[j]; q < a.rp[j + 1]; q++) {
-                    const C bij = to_c(from_d<S>(a.val[q] * djj));
+                    const C bij = bvalue<S>(((const S*)a.bval)[q]);
                     const int p = bsearch_smem(T.I, m, a.col[q]);
                     if (p >= 0) num = fma(T.v[p], bij, num);
                     if (!a.rho_restricted || p >= 0) den = fma(bij, bij, den);
