@@ -229,22 +229,6 @@ __device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, const 
 
 // ---------------------------------------------------------------- pattern
 
-// Insert `key` into the shared-memory hash set `tab` (mask + 1 = 2^(32 -
-// shift) slots, empty = -1, linear probing from the top bits of Knuth's
-// multiplicative hash); returns 1 if it was not there yet.  The set is sized
-// to at least twice the keys it receives, so a probe always ends.
-__device__ __forceinline__ int hash_insert(int32_t* tab, unsigned mask, int shift, int key)
-{
-    unsigned h = ((unsigned)key * 2654435761u) >> shift;
-    for (unsigned probe = 0; probe <= mask; probe++) {
-        const int old = atomicCAS(&tab[h], -1, key);
-        if (old == -1) return 1;
-        if (old == key) return 0;
-        h = (h + 1u) & mask;
-    }
-    return 0;
-}
-
 // Initial pattern J_k (identity, pattern(A), pattern(A^2)), capped at F
 // keeping k and then the nearest indices (ties to the smaller index), and
 // the shadow size |I_k| = |union of the nonzero columns of rows j in J_k,
@@ -317,11 +301,11 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         if (lane == 0) Jcnt[k] = nj;
         __syncwarp();
         // shadow size of the (initial) pattern: |{k} and the nonzero columns of rows J_k|
-        int mine = lane == 0 ? hash_insert(tab, tmask, tshift, (int)k) : 0;
+        int mine = lane == 0 ? hset_insert(tab, tmask, tshift, (int)k) : 0;
         if (lane < nj) {
             const int64_t b = rp[jl], e = rp[jl + 1];
             for (int64_t q = b; q < e; q++)
-                if (val[q] != 0.0) mine += hash_insert(tab, tmask, tshift, col[q]);
+                if (val[q] != 0.0) mine += hset_insert(tab, tmask, tshift, col[q]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);

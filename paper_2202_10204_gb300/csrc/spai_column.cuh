@@ -4,9 +4,10 @@
 // Per column:
 //   1. load the rows j in J_k of A (nonzeros only, scaled by d_j and rounded
 //      to u_f) into shared memory, one list per lane (all loads in flight);
-//   2. gather: a sorted warp merge of those lists (plus the list {k}) gives
-//      the shadow I_k and the dense tile [B(I_k,J_k) | e_k(I_k)] (row-major,
-//      shared memory);
+//   2. gather: the union of those lists (plus the list {k}) is the shadow
+//      I_k, sorted, and gives the dense tile [B(I_k,J_k) | e_k(I_k)]
+//      (row-major, shared memory): through a hash set and a register sort
+//      when the lists hold at most 256 entries, else a sorted warp merge;
 //   3. Householder QR of the tile and back substitution with the tile in
 //      registers (MM = 32/64 rows).  Single and double: lane t keeps column
 //      t; each step the pivot lane writes its column to shared memory, every
@@ -38,6 +39,9 @@ constexpr int SPAI_LD = 33;       // row stride of the tile (32 columns + pad)
 constexpr int SPAI_MAX_FILL = 31; // |J_k| <= 31 so that [B(I,J) | e] fits 32 lanes
 constexpr int SPAI_MMAX_LIMIT = 512;
 constexpr int SPAI_LDR = 40;      // column stride of R (rows 0..31) in shared memory, half path
+constexpr int SPAI_HASH = 512;    // slots of the gather's hash set (at most 256 keys)
+constexpr int SPAI_AUX_BYTES = 2560;  // per warp: the hash set and its ranks, later R (half path)
+static_assert(SPAI_HASH * 5 <= SPAI_AUX_BYTES && 32 * SPAI_LDR * 2 <= SPAI_AUX_BYTES, "aux region");
 
 #define CF_CONVERGED 1
 #define CF_FILLCAP 2
@@ -140,7 +144,9 @@ struct Tile {
     int32_t* lcnt;  // 32
     int32_t* cand;  // cmax
     C* rho;         // cmax
-    WT* R;          // 32 * SPAI_LDR, column-major R(0:31, 0:31) (half path only)
+    WT* R;          // aux: 32 * SPAI_LDR, column-major R(0:31, 0:31) (half path, after the QR)
+    int32_t* hkey;  // aux: SPAI_HASH keys of the gather's hash set (during the gather)
+    unsigned char* hrank;  // aux: the rank in I_k of each slot's key
 };
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -154,7 +160,7 @@ __host__ __device__ inline size_t tile_bytes(int mm, int rl, int cmax)
     b += align16(32 * sizeof(C)) + 3 * 32 * 4;
     b += align16((size_t)32 * rl * 4) + align16((size_t)32 * rl * sizeof(C));
     b += align16((size_t)cmax * 4) + align16((size_t)cmax * sizeof(C));
-    if (std::is_same<WT, __half>::value) b += align16((size_t)32 * SPAI_LDR * sizeof(WT));
+    b += SPAI_AUX_BYTES;
     return align16(b);
 }
 
@@ -175,6 +181,8 @@ __device__ inline Tile<C, WT> carve(unsigned char* base, int mm, int rl, int cma
     t.cand = (int32_t*)(base + off); off += align16((size_t)cmax * 4);
     t.rho = (C*)(base + off); off += align16((size_t)cmax * sizeof(C));
     t.R = std::is_same<WT, __half>::value ? (WT*)(base + off) : nullptr;
+    t.hkey = (int32_t*)(base + off);
+    t.hrank = (unsigned char*)(base + off + SPAI_HASH * 4);
     return t;
 }
 
@@ -185,12 +193,12 @@ template <> __device__ __forceinline__ __half to_w<__half>(float v) { return __f
 template <> __device__ __forceinline__ float to_w<float>(float v) { return v; }
 template <class WT> __device__ __forceinline__ WT to_w(double v) { return (WT)v; }
 
-template <class S, class C, class WT>
-__device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, WT* TW, const int32_t* TJ, int32_t* tlcol,
-                                           C* tlval, int32_t* tlcnt, int64_t k, int nj, int mm)
+// Step 1: lane l < nj copies the nonzeros of row J[l] of A (column of B) to
+// its list in shared memory; returns the list's length.
+template <class S, class C>
+__device__ __forceinline__ int load_lists(const SpaiArgs& a, const int32_t* TJ, int32_t* tlcol, C* tlval, int nj)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned FULL = 0xffffffffu;
     int len = 0;
     if (lane < nj) {
         const int j = TJ[lane];
@@ -216,6 +224,16 @@ __device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, WT* T
             }
         }
     }
+    return len;
+}
+
+template <class S, class C, class WT>
+__device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, WT* TW, const int32_t* TJ, int32_t* tlcol,
+                                           C* tlval, int32_t* tlcnt, int64_t k, int nj, int mm)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    const int len = load_lists<S, C>(a, TJ, tlcol, tlval, nj);
     tlcnt[lane] = len;
     __syncwarp();
     // merge; lane nj carries the list {k} with value 1 (the e_k column)
@@ -242,9 +260,123 @@ __device__ __forceinline__ int gather_ptrs(const SpaiArgs& a, int32_t* TI, WT* T
     return m;
 }
 
+// A shared-memory hash set of int keys >= 0: 2^(32 - shift) slots (mask =
+// slots - 1), empty = -1, linear probing from the top bits of Knuth's
+// multiplicative hash.  Callers keep the load at most one half, so every
+// probe sequence ends.
+__device__ __forceinline__ unsigned hset_slot(int key, int shift) { return ((unsigned)key * 2654435761u) >> shift; }
+// inserts key; returns 1 if it was not there yet
+__device__ __forceinline__ int hset_insert(int32_t* tab, unsigned mask, int shift, int key)
+{
+    unsigned h = hset_slot(key, shift);
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int old = atomicCAS(&tab[h], -1, key);
+        if (old == -1) return 1;
+        if (old == key) return 0;
+        h = (h + 1u) & mask;
+    }
+    return 0;
+}
+// slot of a key that is in the set
+__device__ __forceinline__ unsigned hset_find(const int32_t* tab, unsigned mask, int shift, int key)
+{
+    unsigned h = hset_slot(key, shift);
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        if (tab[h] == key) break;
+        h = (h + 1u) & mask;
+    }
+    return h;
+}
+
+// bitonic sort of 64 keys held two per lane (element 2 lane + i in x_i),
+// ascending
+__device__ __forceinline__ void warp_sort64(int& x0, int& x1)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+        const bool asc = ((2 * lane) & k) == 0;
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 1) {
+                const int lo = min(x0, x1), hi = max(x0, x1);
+                x0 = asc ? lo : hi;
+                x1 = asc ? hi : lo;
+            } else {
+                const int lm = j >> 1;
+                const int y0 = __shfl_xor_sync(FULL, x0, lm), y1 = __shfl_xor_sync(FULL, x1, lm);
+                const bool keep_min = ((lane & lm) == 0) == asc;
+                x0 = keep_min ? min(x0, y0) : max(x0, y0);
+                x1 = keep_min ? min(x1, y1) : max(x1, y1);
+            }
+        }
+    }
+}
+
+// Steps 1-2 with a hash set (warp kernel, mm <= 64, at most 256 keys): the
+// distinct row indices of the lists and k are collected in the hash set
+// (new keys appended to I in arrival order), I is sorted in registers, each
+// slot records its key's rank, and every list entry is written to its rank's
+// row of the zeroed tile.  Same I_k and tile as the sorted merge.
+template <class S, class C, class WT>
+__device__ __forceinline__ int gather_hash(const SpaiArgs& a, const Tile<C, WT>& T, int64_t k, int nj, int mm)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    constexpr unsigned mask = SPAI_HASH - 1;
+    constexpr int shift = 23;  // 32 - log2(SPAI_HASH)
+    static_assert((1 << (32 - shift)) == SPAI_HASH, "hash set size");
+    int32_t* hk = T.hkey;
+    for (int t = lane; t < SPAI_HASH / 4; t += 32) reinterpret_cast<int4*>(hk)[t] = make_int4(-1, -1, -1, -1);
+    const int len = load_lists<S, C>(a, T.J, T.lcol, T.lval, nj);
+    __syncwarp();
+    const int32_t* lc = T.lcol + lane * a.rl;
+    const C* lv = T.lval + lane * a.rl;
+    // lane nj carries the list {k} (the e_k column)
+    const int mylen = lane < nj ? len : (lane == nj ? 1 : 0);
+    int m = 0;
+    for (int t = 0; t < a.rl; t++) {
+        int key = -1;
+        if (t < mylen) key = lane < nj ? lc[t] : (int)k;
+        const bool isnew = key >= 0 && hset_insert(hk, mask, shift, key);
+        const unsigned bal = __ballot_sync(FULL, isnew);
+        if (isnew) {
+            const int pos = m + __popc(bal & ((1u << lane) - 1u));
+            if (pos < mm) T.I[pos] = key;
+        }
+        m += __popc(bal);
+    }
+    __syncwarp();
+    if (m > mm) return m;
+    int x0 = 2 * lane < m ? T.I[2 * lane] : INT_MAX;
+    int x1 = 2 * lane + 1 < m ? T.I[2 * lane + 1] : INT_MAX;
+    warp_sort64(x0, x1);
+    __syncwarp();
+    if (2 * lane < m) {
+        T.I[2 * lane] = x0;
+        T.hrank[hset_find(hk, mask, shift, x0)] = (unsigned char)(2 * lane);
+    }
+    if (2 * lane + 1 < m) {
+        T.I[2 * lane + 1] = x1;
+        T.hrank[hset_find(hk, mask, shift, x1)] = (unsigned char)(2 * lane + 1);
+    }
+    const int n16 = (int)((m * SPAI_LD * sizeof(WT) + 15) / 16);
+    for (int t = lane; t < n16; t += 32) reinterpret_cast<int4*>(T.W)[t] = make_int4(0, 0, 0, 0);
+    __syncwarp();
+    for (int t = 0; t < mylen; t++) {
+        const int key = lane < nj ? lc[t] : (int)k;
+        const int r = T.hrank[hset_find(hk, mask, shift, key)];
+        T.W[r * SPAI_LD + lane] = to_w<WT>(lane < nj ? lv[t] : C(1));
+    }
+    __syncwarp();
+    return m;
+}
+
 template <class S, class C, class WT>
 __device__ __forceinline__ int gather(const SpaiArgs& a, const Tile<C, WT>& T, int64_t k, int nj, int mm)
 {
+    if (nj * a.rl < SPAI_HASH / 2) return gather_hash<S, C, WT>(a, T, k, nj, mm);
     return gather_ptrs<S, C, WT>(a, T.I, T.W, T.J, T.lcol, T.lval, T.lcnt, k, nj, mm);
 }
 
