@@ -30,6 +30,9 @@ constexpr int MMAX_LIMIT = SPAI_MMAX_LIMIT;
 
 // ---------------------------------------------------------------- scaling
 
+// a != 0.0 on the bits (every value but +0 and -0), off the slow FP64 pipe
+__device__ __forceinline__ bool nonzero_bits(double a) { return (__double_as_longlong(a) << 1) != 0; }
+
 __global__ void k_scale(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ val,
                         int scale, double* __restrict__ d, int* __restrict__ err)
 {
@@ -218,7 +221,7 @@ __device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, const 
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             cc[u] = q + u < e ? idx[q + u] : 0;
-            ok[u] = q + u < e && (!val || val[q + u] != 0.0);
+            ok[u] = q + u < e && (!val || nonzero_bits(val[q + u]));
         }
 #pragma unroll
         for (int u = 0; u < 4; u++)
@@ -305,7 +308,7 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         if (lane < nj) {
             const int64_t b = rp[jl], e = rp[jl + 1];
             for (int64_t q = b; q < e; q++)
-                if (val[q] != 0.0) mine += hset_insert(tab, tmask, tshift, col[q]);
+                if (nonzero_bits(val[q])) mine += hset_insert(tab, tmask, tshift, col[q]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);

@@ -506,15 +506,22 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, i
                 X[ks][mt][rg] = h2_bits(__halves2half2(a0, a1));
             }
     const int steps = nj < m ? nj : m;
+    // Pivot steps c = 8 sc + (0..7).  The slot sc of column c and the k-step
+    // and register pair of row c are fixed within a slot: the loop over the
+    // four slots is unrolled (register indices are compile-time), the steps
+    // within a slot are not (the kernel's code stays small enough for the
+    // instruction caches).
 #pragma unroll
-    for (int c = 0; c < SPAI_MAX_FILL; c++) {
-        if (c < steps) {
-            // where column c and row c live
-            const int sc = c >> 3, gc = c & 7;          // slot and group of column c
-            const int ksc = c >> 4, rrc = c & 15;
-            const int rh = rrc >= 8 ? 2 : 0;              // register pair of row c (+0 or +2)
-            const int qc = (rrc & 7) >> 1, hc = rrc & 1;  // lane q and half of row c
-            const int mt0 = c >= 16 ? 1 : 0;              // columns below 16 mt0 are done
+    for (int sc = 0; sc < 4; sc++) {
+        const int ksc = sc >> 1;              // k-step of rows 8 sc .. 8 sc + 7
+        const int rh = (sc & 1) ? 2 : 0;      // register pair of those rows (+0 or +2)
+        const int mt0 = sc >= 2 ? 1 : 0;      // columns below 16 mt0 are done
+        const int cend = steps < 8 * sc + 8 ? steps : 8 * sc + 8;
+#pragma unroll 1
+        for (int c = 8 * sc; c < cend; c++) {
+            const int gc = c & 7;                        // group of column c
+            const int qc = (c & 7) >> 1, hc = c & 1;     // lane q and half of row c
+            const unsigned hsel = hc ? 0x7632u : 0x5410u;  // byte_perm: element hc of two pairs
             // B operand: the pivot column with rows above c zeroed
             unsigned Bv[KS][2];
 #pragma unroll
@@ -544,10 +551,8 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, i
             // slot s's dot product: D[s / 2][2 (s % 2)] (every column of B is v)
             const float sig2 = __shfl_sync(FULL, D[sc >> 1][2 * (sc & 1)], gc * 4);
             // row c of this lane's four columns (meaningful in the lanes q == qc)
-            const unsigned rc01 = (hc ? (X[ksc][0][rh] >> 16) | (X[ksc][0][rh + 1] & 0xffff0000u)
-                                      : (X[ksc][0][rh] & 0xffffu) | (X[ksc][0][rh + 1] << 16));
-            const unsigned rc23 = (hc ? (X[ksc][1][rh] >> 16) | (X[ksc][1][rh + 1] & 0xffff0000u)
-                                      : (X[ksc][1][rh] & 0xffffu) | (X[ksc][1][rh + 1] << 16));
+            const unsigned rc01 = __byte_perm(X[ksc][0][rh], X[ksc][0][rh + 1], hsel);
+            const unsigned rc23 = __byte_perm(X[ksc][1][rh], X[ksc][1][rh + 1], hsel);
             const float x0 = __shfl_sync(FULL, pair_elem(sc < 2 ? rc01 : rc23, sc & 1), gc * 4 + qc);
             const float nrm = rnd<__half>(sqrtf(sig2));
             if (nrm != 0.f) {
@@ -576,7 +581,7 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, i
 #pragma unroll
                 for (int s = 0; s < 4; s++) {
                     const int t = g + 8 * s;
-                    if (8 * s + 7 <= c) continue;  // every column of this slot is final
+                    if (s < sc) continue;  // every column of this slot is final
                     if (t > c && t <= nj) {
                         const unsigned fp = s < 2 ? f01 : f23;
                         const unsigned fs = (s & 1) ? (fp >> 16) : (fp & 0xffffu);
@@ -617,18 +622,16 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, i
     int fl = 0;
     float y = lane < nj ? __half2float(Rs[nj * SPAI_LDR + lane]) : 0.f;
     float mv = 0.f;
-#pragma unroll
-    for (int c = SPAI_MAX_FILL - 1; c >= 0; c--) {
-        if (c < nj) {
-            const float rcc = __half2float(Rs[c * SPAI_LDR + c]);
-            const float rtc = __half2float(Rs[c * SPAI_LDR + lane]);
-            const float yc = __shfl_sync(FULL, y, c);
-            float mc = 0.f;
-            if (c < m && rcc != 0.f) mc = rnd<__half>(rnd<__half>(yc) / rcc);
-            else fl = CF_SINGULAR;
-            if (lane == c) mv = mc;
-            if (lane < c) y = fmaf(-rtc, mc, y);
-        }
+#pragma unroll 1
+    for (int c = nj - 1; c >= 0; c--) {
+        const float rcc = __half2float(Rs[c * SPAI_LDR + c]);
+        const float rtc = __half2float(Rs[c * SPAI_LDR + lane]);
+        const float yc = __shfl_sync(FULL, y, c);
+        float mc = 0.f;
+        if (c < m && rcc != 0.f) mc = rnd<__half>(rnd<__half>(yc) / rcc);
+        else fl = CF_SINGULAR;
+        if (lane == c) mv = mc;
+        if (lane < c) y = fmaf(-rtc, mc, y);
     }
     if (lane < nj) T.mb[lane] = mv;
     __syncwarp();
