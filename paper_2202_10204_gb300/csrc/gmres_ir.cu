@@ -386,7 +386,29 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
     double* yv = hc + (kmax + 2);          // kmax + 2
     int64_t* soa = (int64_t*)(yv + (kmax + 2));  // nsl + 1 slice offsets of A
     int64_t* sop = soa + (nsl + 1);        // nsl + 1 slice offsets of P
-    TG* ws = (TG*)(sop + (nsl + 1));       // w for rows [m0, m1) (rb, or 2 rb with a group)
+    // w for rows [m0, m1) (rb, or 2 rb with a group), 16-byte aligned
+    TG* ws = (TG*)(((uintptr_t)(sop + (nsl + 1)) + 15) & ~(uintptr_t)15);
+    // Gram-Schmidt rows of this thread: PF rows as UV vectors of VN consecutive
+    // rows, vector u = rows [vrow(u), vrow(u) + VN), then rows m0 + PF BT + tid
+    // (step BT); the group's load, the first partial and every round use it
+    constexpr int VN = 16 / (int)sizeof(TG);
+    constexpr int UV = PF / VN;
+    typedef typename std::conditional<sizeof(TG) == 4, float4, double2>::type TV;
+    auto vrow = [&](int u) -> int64_t { return m0 + (int64_t)VN * (tid + u * BT); };
+    // the prefetch set of basis vector Vb: out[u VN + e] = Vb[vrow(u) + e] (0 beyond m1)
+    auto vload = [&](const TG* Vb, TG* out) {
+#pragma unroll
+        for (int u = 0; u < UV; u++) {
+            const int64_t s0 = vrow(u);
+            if (s0 + VN <= m1) {
+                const TV t = __ldcg(reinterpret_cast<const TV*>(Vb + s0));
+                memcpy(out + u * VN, &t, sizeof(TV));
+            } else {
+#pragma unroll
+                for (int e = 0; e < VN; e++) out[u * VN + e] = s0 + e < m1 ? ldcg(&Vb[s0 + e]) : TG(0);
+            }
+        }
+    };
     TU* x = (TU*)a.x;
     TU* r = (TU*)a.r;
     TG* wbuf = (TG*)a.wbuf;
@@ -466,21 +488,9 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 // (with a group the range holds other blocks' rows of v_0, which are
                 // published by this barrier when j = 0: the load waits for it)
                 TG vc[PF];
-                if (!sub) {
-#pragma unroll
-                    for (int u = 0; u < PF; u++) {
-                        int64_t row = m0 + tid + (int64_t)u * BT;
-                        vc[u] = row < m1 ? V[row] : TG(0);
-                    }
-                }
+                if (!sub) vload(V, vc);
                 if (!xbar(a, sh)) return;
-                if (sub) {
-#pragma unroll
-                    for (int u = 0; u < PF; u++) {
-                        int64_t row = m0 + tid + (int64_t)u * BT;
-                        vc[u] = row < m1 ? ldcg(&V[row]) : TG(0);
-                    }
-                }
+                if (sub) vload(V, vc);
                 // ---- w = P t (left) or A t (right) in u_p, stored in u_g (own rows, shared
                 // memory); first MGS partial
                 part = TG(0);
@@ -494,7 +504,18 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         for (int64_t row = r0 + tid; row < r1; row += BT) wbuf[row] = (TG)ldcg(&tbuf[row]);
                     }
                     if (!xbar(a, sh)) return;
-                    for (int64_t row = m0 + tid; row < m1; row += BT) ws[row - m0] = ldcg(&wbuf[row]);
+#pragma unroll
+                    for (int u = 0; u < UV; u++) {
+                        const int64_t s0 = vrow(u);
+                        if (s0 + VN <= m1) {
+                            *reinterpret_cast<TV*>(ws + (s0 - m0)) = __ldcg(reinterpret_cast<const TV*>(wbuf + s0));
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < VN; e++)
+                                if (s0 + e < m1) ws[s0 + e - m0] = ldcg(&wbuf[s0 + e]);
+                        }
+                    }
+                    for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) ws[row - m0] = ldcg(&wbuf[row]);
                 } else if (hasP) {
                     sell_rows<TP>(r0, r1, rightP ? soa : sop, rightP ? a.A.col : a.P.col, rightP ? av : pv,
                                   [&](int c) { return ldcg(&tbuf[c]); },
@@ -551,28 +572,25 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         }
                     }
                 } else {
-                // sell_rows, the copy and the group's load give thread tid the rows
-                // m0 + tid + u*BT, so the partial needs no __syncthreads.  Basis
-                // entries are read through L2 (ld.cg): with a group they include
-                // rows that other blocks wrote
+                // the group's load gives each thread its Gram-Schmidt rows; without a
+                // group sell_rows wrote w in its own row order.  Basis entries are read
+                // through L2 (ld.cg): with a group they include rows that other blocks
+                // wrote
+                if (!sub) __syncthreads();
 #pragma unroll
-                for (int u = 0; u < PF; u++) {
-                    int64_t row = m0 + tid + (int64_t)u * BT;
-                    if (row < m1) part = fma(vc[u], ws[row - m0], part);
+                for (int u = 0; u < UV; u++) {
+                    const int64_t s0 = vrow(u);
+#pragma unroll
+                    for (int e = 0; e < VN; e++)
+                        if (s0 + e < m1) part = fma(vc[u * VN + e], ws[s0 + e - m0], part);
                 }
-                for (int64_t row = m0 + tid + (int64_t)PF * BT; row < m1; row += BT) part = fma(ldcg(&V[row]), ws[row - m0], part);
+                for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) part = fma(ldcg(&V[row]), ws[row - m0], part);
                 // ---- modified Gram-Schmidt in u_g (blocks outside the group skip it)
                 for (int i = 0; i <= j && gs; i++) {
                     // prefetch v_{i+1} (rows [m0, m1)) before waiting for h_{i,j}
                     const TG* Vn = V + (int64_t)(i + 1) * a.ldv;
                     TG vn[PF];
-                    if (i < j) {
-#pragma unroll
-                        for (int u = 0; u < PF; u++) {
-                            int64_t row = m0 + tid + (int64_t)u * BT;
-                            vn[u] = row < m1 ? ldcg(&Vn[row]) : TG(0);
-                        }
-                    }
+                    if (i < j) vload(Vn, vn);
                     TG h;
                     // Givens, pipelined with the rounds: rotation q needs h_{q+1}, known
                     // after round q+1; thread 0 applies it during round q+2, between
@@ -594,32 +612,66 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     part = TG(0);
                     if (i < j) {
 #pragma unroll
-                        for (int u = 0; u < PF; u++) {
-                            int64_t row = m0 + tid + (int64_t)u * BT;
-                            if (row < m1) {
-                                TG wv = fma(-h, vc[u], ws[row - m0]);
-                                ws[row - m0] = wv;
-                                part = fma(vn[u], wv, part);
+                        for (int u = 0; u < UV; u++) {
+                            const int64_t s0 = vrow(u);
+                            TG* wp = ws + (s0 - m0);
+                            if (s0 + VN <= m1) {
+                                TV t = *reinterpret_cast<const TV*>(wp);
+                                TG wv[VN];
+                                memcpy(wv, &t, sizeof(TV));
+#pragma unroll
+                                for (int e = 0; e < VN; e++) {
+                                    wv[e] = fma(-h, vc[u * VN + e], wv[e]);
+                                    part = fma(vn[u * VN + e], wv[e], part);
+                                }
+                                memcpy(&t, wv, sizeof(TV));
+                                *reinterpret_cast<TV*>(wp) = t;
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < VN; e++)
+                                    if (s0 + e < m1) {
+                                        const TG wv = fma(-h, vc[u * VN + e], wp[e]);
+                                        wp[e] = wv;
+                                        part = fma(vn[u * VN + e], wv, part);
+                                    }
                             }
-                            vc[u] = vn[u];
                         }
-                        for (int64_t row = m0 + tid + (int64_t)PF * BT; row < m1; row += BT) {
+#pragma unroll
+                        for (int e = 0; e < PF; e++) vc[e] = vn[e];
+                        for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) {
                             TG wv = fma(-h, ldcg(&Vi[row]), ws[row - m0]);
                             ws[row - m0] = wv;
                             part = fma(ldcg(&Vn[row]), wv, part);
                         }
                     } else {
 #pragma unroll
-                        for (int u = 0; u < PF; u++) {
-                            int64_t row = m0 + tid + (int64_t)u * BT;
-                            if (row < m1) {
-                                TG wv = fma(-h, vc[u], ws[row - m0]);
-                                ws[row - m0] = wv;
-                                wbuf[row] = wv;
-                                part = fma(wv, wv, part);
+                        for (int u = 0; u < UV; u++) {
+                            const int64_t s0 = vrow(u);
+                            TG* wp = ws + (s0 - m0);
+                            if (s0 + VN <= m1) {
+                                TV t = *reinterpret_cast<const TV*>(wp);
+                                TG wv[VN];
+                                memcpy(wv, &t, sizeof(TV));
+#pragma unroll
+                                for (int e = 0; e < VN; e++) {
+                                    wv[e] = fma(-h, vc[u * VN + e], wv[e]);
+                                    part = fma(wv[e], wv[e], part);
+                                }
+                                memcpy(&t, wv, sizeof(TV));
+                                *reinterpret_cast<TV*>(wp) = t;
+                                *reinterpret_cast<TV*>(wbuf + s0) = t;
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < VN; e++)
+                                    if (s0 + e < m1) {
+                                        const TG wv = fma(-h, vc[u * VN + e], wp[e]);
+                                        wp[e] = wv;
+                                        wbuf[s0 + e] = wv;
+                                        part = fma(wv, wv, part);
+                                    }
                             }
                         }
-                        for (int64_t row = m0 + tid + (int64_t)PF * BT; row < m1; row += BT) {
+                        for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) {
                             TG wv = fma(-h, ldcg(&Vi[row]), ws[row - m0]);
                             ws[row - m0] = wv;
                             wbuf[row] = wv;
