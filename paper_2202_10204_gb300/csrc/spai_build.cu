@@ -33,21 +33,26 @@ constexpr int MMAX_LIMIT = SPAI_MMAX_LIMIT;
 // a != 0.0 on the bits (every value but +0 and -0), off the slow FP64 pipe
 __device__ __forceinline__ bool nonzero_bits(double a) { return (__double_as_longlong(a) << 1) != 0; }
 
+// also sets *zeros when A stores an explicit zero (the pattern kernel then
+// tests the values; otherwise the structure alone is the nonzero pattern)
 __global__ void k_scale(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ val,
-                        int scale, double* __restrict__ d, int* __restrict__ err)
+                        int scale, double* __restrict__ d, int* __restrict__ err, int* __restrict__ zeros)
 {
+    bool z = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double mx = 0.0;
         bool fin = true;
         for (int64_t q = rp[i]; q < rp[i + 1]; q++) {
             double a = val[q];
             if (!isfinite(a)) fin = false;
+            if (!nonzero_bits(a)) z = true;
             mx = fmax(mx, fabs(a));
         }
         if (!fin) atomicCAS(err, 0, SPAI_ERR_NONFINITE);
         if (mx == 0.0) atomicCAS(err, 0, SPAI_ERR_ZERO_ROW);
         d[i] = scale ? (mx > 0.0 ? 1.0 / mx : 1.0) : 1.0;
     }
+    if (z) atomicOr(zeros, 1);
 }
 
 // b = fl_S(a_ij d_j) for every nonzero of row j of A, once, in the storage
@@ -242,8 +247,9 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
                           const double* __restrict__ val, const int64_t* __restrict__ cp,
                           const int32_t* __restrict__ ri, int32_t* __restrict__ Jidx, int32_t* __restrict__ Jcnt,
                           int32_t* __restrict__ Icnt, int cap, int stride, int tsz, int* __restrict__ err,
-                          int* __restrict__ maxI)
+                          int* __restrict__ maxI, const int* __restrict__ zeros)
 {
+    const bool zv = *zeros != 0;  // A stores explicit zeros: test the values
     extern __shared__ int32_t pbuf[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     int32_t* buf = pbuf + (size_t)wib * (cap + 32 * stride + tsz);
@@ -307,8 +313,12 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         int mine = lane == 0 ? hset_insert(tab, tmask, tshift, (int)k) : 0;
         if (lane < nj) {
             const int64_t b = rp[jl], e = rp[jl + 1];
-            for (int64_t q = b; q < e; q++)
-                if (nonzero_bits(val[q])) mine += hset_insert(tab, tmask, tshift, col[q]);
+            if (zv) {
+                for (int64_t q = b; q < e; q++)
+                    if (nonzero_bits(val[q])) mine += hset_insert(tab, tmask, tshift, col[q]);
+            } else {
+                for (int64_t q = b; q < e; q++) mine += hset_insert(tab, tmask, tshift, col[q]);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
@@ -547,7 +557,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     int rc = 0;
     // device scratch
     double* d = nullptr;
-    int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|
+    int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|, [3] [4] longest row and column, [5] explicit zeros
     int32_t* ccount = nullptr;
     int64_t* cp = nullptr;
     int32_t* ri = nullptr;
@@ -566,7 +576,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
 
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
     TRY(dev_alloc((void**)&d, sizeof(double) * n, s));
-    TRY(dev_alloc((void**)&err, sizeof(int) * 5, s));
+    TRY(dev_alloc((void**)&err, sizeof(int) * 6, s));
     TRY(dev_alloc((void**)&ccount, sizeof(int32_t) * (n + 1), s));
     TRY(dev_alloc((void**)&cp, sizeof(int64_t) * (n + 1), s));
     TRY(dev_alloc((void**)&ri, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s));
@@ -580,14 +590,14 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     TRY(dev_alloc(&mval, ssz * n * F, s));
     TRY(dev_alloc(&bval, ssz * (nnz > 0 ? nnz : 1), s));
     TRY(dev_alloc((void**)&fstat, sizeof(unsigned long long) * 3, s));
-    if (cudaMemsetAsync(err, 0, sizeof(int) * 5, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+    if (cudaMemsetAsync(err, 0, sizeof(int) * 6, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(fstat, 0, sizeof(unsigned long long) * 3, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     {
         int tb = 256;
         int gb = (int)std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32);
         if (gb < 1) gb = 1;
-        k_scale<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, o->scale, d, err);
+        k_scale<<<gb, tb, 0, s>>>(n, A.rowptr, A.val, o->scale, d, err, err + 5);
         if (o->uf == SPAI_HALF) k_bvals<__half><<<gb, tb, 0, s>>>(n, A.rowptr, A.val, d, (__half*)bval);
         else if (o->uf == SPAI_SINGLE) k_bvals<float><<<gb, tb, 0, s>>>(n, A.rowptr, A.val, d, (float*)bval);
         else k_bvals<double><<<gb, tb, 0, s>>>(n, A.rowptr, A.val, d, (double*)bval);
@@ -630,7 +640,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms * 64);
         if (blocks < 1) blocks = 1;
         k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, A.rowptr, A.col, A.val, cp, ri, Jidx, Jcnt,
-                                                        Icnt, cap, stride, tsz, err, err + 1);
+                                                        Icnt, cap, stride, tsz, err, err + 1, err + 5);
         nl += 1;
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaMemcpyAsync(h_err, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }

@@ -55,7 +55,7 @@ def true_colres(A, d, J_rows, J_cnt, mbar, floor=False):
     return res, np.sqrt(np.asarray(Q.multiply(Q).sum(axis=0)).ravel())
 
 
-def assert_colres(res_gpu, res_orc, absbm, uf, mask=None):
+def assert_colres(res_gpu, res_orc, absbm, uf, mask=None, frac=0.99):
     tol = RES_TOL[uf]
     u = O.UNIT_ROUNDOFF[O.prec(uf)]
     diff = np.abs(res_gpu - res_orc)
@@ -63,7 +63,7 @@ def assert_colres(res_gpu, res_orc, absbm, uf, mask=None):
         diff, res_orc, absbm = diff[mask], res_orc[mask], absbm[mask]
     floor = (4 * u + 64 * 2.0 ** -53) * absbm  # u_f representation + float64 evaluation
     assert np.all(diff <= tol * res_orc + floor), np.max(diff - tol * res_orc - floor)
-    assert np.mean(diff <= tol * res_orc) >= 0.99, np.mean(diff <= tol * res_orc)
+    assert np.mean(diff <= tol * res_orc) >= frac, np.mean(diff <= tol * res_orc)
 
 
 def gpu_spai(ctx, A, **kw):
@@ -84,6 +84,18 @@ def split_rows(rp, ci, va, d):
         J[k, :c] = ci[rp[k]:rp[k + 1]]
         M[k, :c] = va[rp[k]:rp[k + 1]] / d[ci[rp[k]:rp[k + 1]]]
     return J, cnt, M
+
+
+def with_explicit_zeros(A, frac, seed):
+    """A copy of A with a fraction of its off-diagonal values stored as 0.0 (the
+    structure kept): the shadows count only a_ij != 0 (Algorithm 1), the patterns
+    pattern(A), pattern(A^2) the stored structure."""
+    rp, ci, va = A
+    va = va.copy()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    pick = (ci != rows) & (np.random.default_rng(seed).random(len(va)) < frac)
+    va[pick] = 0.0
+    return rp, ci, va
 
 
 SPAI_CASES = [
@@ -115,6 +127,31 @@ def test_spai_fixed_pattern_parity(ctx, name, make, init, F, uf):
     # the u_f-computed norms the kernel reports agree to a few u_f
     u = O.UNIT_ROUNDOFF[O.prec(uf)]
     assert np.all(np.abs(st["colres"] - ref["colres"]) <= 64 * u * ref["colres"] + 8 * u * absbm + 1e-14)
+    P.free()
+
+
+@pytest.mark.parametrize("uf", ["half", "single", "double"])
+def test_spai_explicit_zeros_parity(ctx, uf):
+    """A with explicit zeros (15% of the off-diagonal values stored as 0.0): the
+    pattern pattern(A^2) follows the stored structure and the shadows count only
+    a_ij != 0 (Algorithm 1), both bit-exact against the oracle; every column meets
+    the residual bound with the u_f floor (the u_f term of eq. (rhatbnd)).  At
+    u_f = half 97.9% of this matrix's columns also meet the pure relative
+    tolerance, the same fraction with the warp kernel's earlier FMA arithmetic:
+    with zeros in the tile more columns sit where one half-ulp difference in m_k
+    moves the residual by more than 1e-3 of itself."""
+    A = with_explicit_zeros(synth.conv_diff_3d(9, 50.0, seed=3), 0.15, 21)
+    P, st, (rp, ci, va) = gpu_spai(ctx, A, init=O.PAT_A2, max_fill=25, uf=uf, eps=0.0)
+    ref = O.spai(A, init=O.PAT_A2, max_fill=25, uf=uf, eps=0.0)
+    plain = O.spai(synth.conv_diff_3d(9, 50.0, seed=3), init=O.PAT_A2, max_fill=25, uf=uf, eps=0.0)
+    assert np.sum(ref["Icnt"] != plain["Icnt"]) > 100  # the zeros change many shadows
+    assert np.array_equal(np.diff(rp), ref["Jcnt"])
+    for k in range(ref["n"]):
+        assert np.array_equal(ci[rp[k]:rp[k + 1]], ref["Jidx"][k][: ref["Jcnt"][k]])
+    assert np.array_equal(st["nI"], ref["Icnt"])
+    J, cnt, M = split_rows(rp, ci, va, ref["d"])
+    res_gpu, absbm = true_colres(A, ref["d"], J, cnt, M, floor=True)
+    assert_colres(res_gpu, ref["colres64"], absbm, uf, frac=0.97 if uf == "half" else 0.99)
     P.free()
 
 
