@@ -151,6 +151,58 @@ int csr_validate_host(const spai_csr* A)
     return 0;
 }
 
+// The full structural check of a host CSR once it is on the device: rows
+// with rowptr out of order or past nnz, columns outside [0, n) or not
+// strictly ascending (flag 1), empty rows (flag 2).
+__global__ void k_csr_check(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            int* __restrict__ flags)
+{
+    int f = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        if (b < 0 || e < b || e > nnz) { f |= 1; continue; }
+        if (e == b) { f |= 2; continue; }
+        int prev = -1;
+        for (int64_t q = b; q < e; q++) {
+            const int c = col[q];
+            if (c < 0 || c >= n || c <= prev) { f |= 1; break; }
+            prev = c;
+        }
+    }
+    if (f) atomicOr(flags, f);
+}
+
+// Host inputs: the O(1) checks here, the scan of every row on the device
+// after the copy (csr_check_device); a host loop over a matrix of millions of
+// entries cost milliseconds per call.
+int csr_check_device(const DevCsr& A, int num_sms, cudaStream_t s)
+{
+    int* flags = nullptr;
+    int rc = dev_alloc((void**)&flags, sizeof(int), s);
+    if (rc) return rc;
+    int h = 0;
+    const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + 255) / 256, (int64_t)num_sms * 8));
+    if (cudaMemsetAsync(flags, 0, sizeof(int), s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    if (!rc) {
+        k_csr_check<<<gb, 256, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, flags);
+        if (cudaGetLastError() != cudaSuccess) rc = SPAI_ERR_CUDA;
+    }
+    if (!rc && cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    dev_free(flags, s);
+    if (rc) return rc;
+    return (h & 1) ? SPAI_ERR_INVALID_ARG : ((h & 2) ? SPAI_ERR_ZERO_ROW : 0);
+}
+
+int csr_check_args(const spai_csr* A)
+{
+    if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
+    if (A->n > INT32_MAX) return SPAI_ERR_UNSUPPORTED;
+    if (A->on_device) return 0;
+    if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) return SPAI_ERR_INVALID_ARG;
+    return 0;
+}
+
 int csr_to_device(const spai_csr* A, DevCsr* out, cudaStream_t s)
 {
     out->n = A->n;
@@ -344,12 +396,13 @@ int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_prec
 {
     if (!ctx || !A || !opts || !P_out) return SPAI_ERR_INVALID_ARG;
     *P_out = nullptr;
-    int rc = csr_validate_host(A);
+    int rc = csr_check_args(A);
     if (rc) return rc;
     std::lock_guard<std::mutex> lk(ctx->mu);
     SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
     DevCsr dA;
     rc = csr_to_device(A, &dA, ctx->stream);
+    if (!rc && !A->on_device) rc = csr_check_device(dA, ctx->num_sms, ctx->stream);
     if (!rc) rc = spai_build_dev(ctx->device, ctx->num_sms, ctx->stream, dA, opts, P_out, st);
     csr_release(&dA, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
@@ -471,7 +524,7 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
                    double* x, const ir_opts* opts, ir_stats* st)
 {
     if (!ctx || !A || !b || !x || !opts) return SPAI_ERR_INVALID_ARG;
-    int rc = csr_validate_host(A);
+    int rc = csr_check_args(A);
     if (rc) return rc;
     if (P && P->n != A->n) return SPAI_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -483,6 +536,7 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
     spai_precond own = nullptr;
     int wrc = 0;
     rc = csr_to_device(A, &dA, s);
+    if (!rc && !A->on_device) rc = csr_check_device(dA, ctx->num_sms, s);
     if (!rc) {
         if (A->on_device) {
             db = const_cast<double*>(b);

@@ -304,6 +304,24 @@ def test_edge_cases(ctx):
     with pytest.raises(S.SpaiError) as e:
         S.gmres_ir_solve(ctx, Au, np.ones(2), np.zeros(2), sopts=so, opts=io)
     assert e.value.code == -1
+    # the structural checks of host inputs run on the device: a decreasing rowptr, a
+    # column out of range, a repeated column, in spai_build as well
+    bad = [
+        (np.array([0, 2, 1, 3], dtype=np.int64), np.array([0, 1, 2], dtype=np.int32)),
+        (np.array([0, 1, 2, 3], dtype=np.int64), np.array([0, 3, 2], dtype=np.int32)),
+        (np.array([0, 2, 3, 4], dtype=np.int64), np.array([0, 0, 1, 2], dtype=np.int32)),
+    ]
+    for rp, ci in bad:
+        Ab = (rp, ci, np.ones(len(ci)))
+        with pytest.raises(S.SpaiError) as e:
+            S.gmres_ir_solve(ctx, Ab, np.ones(3), np.zeros(3), sopts=so, opts=io)
+        assert e.value.code == -1
+        with pytest.raises(S.SpaiError) as e:
+            S.spai_build(ctx, Ab, so)
+        assert e.value.code == -1
+    with pytest.raises(S.SpaiError) as e:
+        S.spai_build(ctx, Az, so)
+    assert e.value.code == -2
     # unsupported fill cap
     with pytest.raises(S.SpaiError) as e:
         S.spai_build(ctx, A, S.make_spai_opts(init=1, max_fill=40))
