@@ -20,7 +20,10 @@
  *   - CSR arrays: rowptr[n+1] int64 (rowptr[0] = 0, non-decreasing), col[nnz]
  *     int32 in [0, n) sorted ascending within a row, val[nnz] float64.
  *     With on_device = 1 all three are device pointers on the context's
- *     device, otherwise host pointers.
+ *     device, otherwise host pointers.  Host inputs are checked in full
+ *     (SPAI_ERR_INVALID_ARG for a structural error, which takes precedence
+ *     over SPAI_ERR_ZERO_ROW for an empty row); the scan runs on the device
+ *     after the copy.  Device inputs are not scanned.
  *   - all work runs on the context's CUDA stream on one GPU; every call
  *     returns after its results are complete.
  *   - calls on one context are serialised by the context; distinct contexts
