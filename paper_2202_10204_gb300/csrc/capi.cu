@@ -194,6 +194,26 @@ int csr_check_device(const DevCsr& A, int num_sms, cudaStream_t s)
     return (h & 1) ? SPAI_ERR_INVALID_ARG : ((h & 2) ? SPAI_ERR_ZERO_ROW : 0);
 }
 
+// csr_validate_host over many matrices on several host threads (a batch of
+// hundreds of matrices holds ~1e8 entries); the error of the first failing
+// matrix in index order.
+int csr_validate_many(const spai_csr* A, int count)
+{
+    std::vector<int> rcs(count, 0);
+    const unsigned hc = std::thread::hardware_concurrency();
+    const int nt = std::max(1, std::min<int>(count, (int)std::min<unsigned>(hc ? hc : 1, 16)));
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; t++)
+        th.emplace_back([&] {
+            for (int i = next++; i < count; i = next++) rcs[i] = csr_validate_host(&A[i]);
+        });
+    for (auto& t : th) t.join();
+    for (int i = 0; i < count; i++)
+        if (rcs[i]) return rcs[i];
+    return 0;
+}
+
 int csr_check_args(const spai_csr* A)
 {
     if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
@@ -421,8 +441,8 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
     if (count == 0) return 0;
     if (!A || !P_out) return SPAI_ERR_INVALID_ARG;
     for (int i = 0; i < count; i++) P_out[i] = nullptr;
-    for (int i = 0; i < count; i++) {
-        const int rc = csr_validate_host(&A[i]);
+    {
+        const int rc = csr_validate_many(A, count);
         if (rc) return rc;
     }
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -579,10 +599,11 @@ int gmres_ir_solve_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_
     if (!ctx || !opts || count < 0) return SPAI_ERR_INVALID_ARG;
     if (count == 0) return 0;
     if (!A || !b || !x) return SPAI_ERR_INVALID_ARG;
-    for (int i = 0; i < count; i++) {
-        int rc = csr_validate_host(&A[i]);
-        if (rc) return rc;
+    for (int i = 0; i < count; i++)
         if (!b[i] || !x[i]) return SPAI_ERR_INVALID_ARG;
+    {
+        const int rc = csr_validate_many(A, count);
+        if (rc) return rc;
     }
     std::lock_guard<std::mutex> lk(ctx->mu);
     SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
