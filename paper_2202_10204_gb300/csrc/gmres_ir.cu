@@ -1100,8 +1100,9 @@ int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
     TRY(dev_alloc((void**)&J.its, sizeof(int) * (imax + 1), s));
     TRY(dev_alloc((void**)&J.outv, sizeof(int) * 2, s));
     TRY(dev_alloc((void**)&J.err, sizeof(int) * 2, s));
-    TRY(dev_alloc((void**)&J.norms, sizeof(unsigned long long) * 3, s));
-    CTRY(cudaMemsetAsync(J.norms, 0, sizeof(unsigned long long) * 3, s));
+    // [0..2] the norms and the longest row, [3] [4] SELL entry counts of A and P
+    TRY(dev_alloc((void**)&J.norms, sizeof(unsigned long long) * 5, s));
+    CTRY(cudaMemsetAsync(J.norms, 0, sizeof(unsigned long long) * 5, s));
     if (o->orth) {
         TRY(dev_alloc(&J.pvec, (size_t)sg * 2 * MAX_GRID * (kmax + 1), s));
         TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
@@ -1148,26 +1149,45 @@ int ir_job_norms_x0(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int
 }
 
 // Allocations, SELL-32 copies of A (and of P, cached on the handle), the norms
-// and x0 = P b, all enqueued on s (the SELL builds synchronise s once each).
+// and x0 = P b, enqueued on s with one synchronisation (for the SELL entry
+// counts and the norms, which are on the host when it returns).
 int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int* nl)
 {
     int rc = ir_job_alloc(J, s, o);
     if (rc) return rc;
     const DevCsr& A = *J.A;
     spai_precond P = J.P;
-    rc = sell_build(J.n, A.rowptr, A.col, A.val, o->up, num_sms, s, &J.As, nl);
+    // one host synchronisation for the SELL entry counts and the norms: the
+    // counts join the norms on the device, and one copy brings all five
+    const int64_t nsl = (J.n + 31) >> 5;
+    SellMat* cache = nullptr;
+    rc = sell_begin(J.n, A.rowptr, num_sms, s, &J.As, nl);
     if (rc) return rc;
+    if (cudaMemcpyAsync(J.norms + 3, J.As.off + nsl, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return SPAI_ERR_CUDA;
     if (P) {
-        SellMat* cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
-        if (!cache->off) rc = sell_build(J.n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, nl);
-        if (rc) return rc;
-        J.Ps = cache;
+        cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
+        if (!cache->off) {
+            rc = sell_begin(J.n, P->rowptr, num_sms, s, cache, nl);
+            if (rc) return rc;
+            if (cudaMemcpyAsync(J.norms + 4, cache->off + nsl, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return SPAI_ERR_CUDA;
+        } else {
+            cache = nullptr;  // already made
+        }
+        J.Ps = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
     }
     rc = ir_job_norms_x0(J, num_sms, s, o, nl);
     if (rc) return rc;
-    if (cudaMemcpyAsync(J.h_norms, J.norms, sizeof(J.h_norms), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return SPAI_ERR_CUDA;
-    return 0;
+    unsigned long long h[5] = {0, 0, 0, 0, 0};
+    if (cudaMemcpyAsync(h, J.norms, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SPAI_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPAI_ERR_CUDA;
+    for (int k = 0; k < 3; k++) J.h_norms[k] = h[k];
+    const int64_t tot[2] = {(int64_t)h[3], (int64_t)h[4]};
+    rc = sell_finish(J.n, A.rowptr, A.col, A.val, o->up, num_sms, s, &J.As, tot[0], nl);
+    if (rc) return rc;
+    if (cache) rc = sell_finish(J.n, P->rowptr, P->col, P->val, o->up, num_sms, s, cache, tot[1], nl);
+    return rc;
 }
 
 // The kernel arguments, once the norms have reached the host (after a sync).
@@ -1303,8 +1323,7 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
 #define CTRY(x) do { if ((x) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; } } while (0)
     CTRY(cudaEventRecord(e0, s));
-    TRY(ir_job_prepare(J, num_sms, s, o, &nl));
-    CTRY(cudaStreamSynchronize(s));
+    TRY(ir_job_prepare(J, num_sms, s, o, &nl));  // the norms are on the host when it returns
     ir_job_args(J, device, o);
     CTRY(cudaEventRecord(ek0, s));
     {

@@ -578,22 +578,23 @@ __device__ __forceinline__ int qr_solve_reg_half(const Tile<float, __half>& T, i
                 const unsigned f01 = (q & 2) ? po : pr, f23 = (q & 2) ? pr : po;
                 // update operand: v with row c = v0
                 if (q == qc) Bv[ksc][rh >> 1] = pair_set(Bv[ksc][rh >> 1], hc, __float2half_rn(v0));
+                // without branches: columns that take no update (t <= c, t > nj) get
+                // f = 0, i.e. x + (+-0) = x (at most the sign of a zero changes)
 #pragma unroll
                 for (int s = 0; s < 4; s++) {
                     const int t = g + 8 * s;
                     if (s < sc) continue;  // every column of this slot is final
-                    if (t > c && t <= nj) {
-                        const unsigned fp = s < 2 ? f01 : f23;
-                        const unsigned fs = (s & 1) ? (fp >> 16) : (fp & 0xffffu);
-                        const __half2 nf = __hneg2(bits_h2(fs | (fs << 16)));
+                    const unsigned fp = s < 2 ? f01 : f23;
+                    const unsigned fs = (s & 1) ? (fp >> 16) : (fp & 0xffffu);
+                    const unsigned nfb = (t > c && t <= nj) ? ((fs | (fs << 16)) ^ 0x80008000u) : 0u;
+                    const __half2 nf = bits_h2(nfb);
 #pragma unroll
-                        for (int ks = 0; ks < KS; ks++) {
-                            if (ks < ksc) continue;
+                    for (int ks = 0; ks < KS; ks++) {
+                        if (ks < ksc) continue;
 #pragma unroll
-                            for (int u = 0; u < 2; u++) {
-                                unsigned& x = X[ks][s >> 1][(s & 1) + 2 * u];
-                                x = h2_bits(__hfma2(nf, bits_h2(Bv[ks][u]), bits_h2(x)));
-                            }
+                        for (int u = 0; u < 2; u++) {
+                            unsigned& x = X[ks][s >> 1][(s & 1) + 2 * u];
+                            x = h2_bits(__hfma2(nf, bits_h2(Bv[ks][u]), bits_h2(x)));
                         }
                     }
                 }
