@@ -205,6 +205,40 @@ def test_pattern_A2_matches_scipy():
     assert S["Jcnt"][k] == 25 or k not in range(0, 216, 7)
 
 
+def test_explicit_zeros_pattern_structural_shadow_by_value():
+    """Explicit zeros of A: pattern(A^2) follows the stored structure (a boolean
+    product of the structure, scipy), the shadow I_k counts only rows with a
+    nonzero value in B(:, J_k) (Algorithm 1), and m_k is the library
+    least-squares solution on that shadow."""
+    A = synth.conv_diff_3d(5, 50.0, seed=4)
+    rp, ci, va = A
+    va = va.copy()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    va[(ci != rows) & (np.random.default_rng(7).random(len(va)) < 0.3)] = 0.0
+    Az = (rp, ci, va)
+    n = len(rp) - 1
+    cols = list(range(0, n, 9))
+    S = O.spai(Az, init=O.PAT_A2, uf="double", max_fill=25, cols=cols)
+    Ms = sp.csr_matrix((va, ci, rp), shape=(n, n))  # explicit zeros kept
+    St = sp.csr_matrix((np.ones(len(ci)), ci, rp), shape=(n, n))
+    A2 = (St @ St).tocsc()
+    rowmax = np.array([np.abs(va[rp[i]:rp[i + 1]]).max() for i in range(n)])
+    B = (Ms.T @ sp.diags(1.0 / rowmax)).tocsc()
+    fewer = 0
+    for k in cols:
+        J = S["Jidx"][k][: S["Jcnt"][k]]
+        assert np.array_equal(J, np.sort(A2[:, k].nonzero()[0]))
+        BJ = B[:, J].toarray()
+        I = np.union1d(np.nonzero(np.any(BJ != 0, axis=1))[0], [k])
+        assert S["Icnt"][k] == len(I)
+        Ist = np.union1d(np.nonzero(np.asarray((St.T[:, J]).sum(axis=1)).ravel())[0], [k])
+        fewer += len(I) < len(Ist)
+        e = (I == k).astype(float)
+        m_ref = np.linalg.lstsq(BJ[I], e, rcond=None)[0]
+        np.testing.assert_allclose(S["mbar"][k][: len(J)], m_ref, rtol=1e-10, atol=1e-12)
+    assert fewer > 0  # the zeros shrink some shadows below the structural ones
+
+
 def test_fill_cap_keeps_k_and_nearest():
     A = synth.conv_diff_3d(6, 50.0, seed=3)
     k = 2 * 36 + 3 * 6 + 2
