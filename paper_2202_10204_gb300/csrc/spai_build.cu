@@ -187,50 +187,44 @@ namespace {
 
 // ---------------------------------------------------------------- sorted unions
 // Sorted union of up to 32 sorted index lists held in shared memory, one per
-// lane (lane l: lst[l*stride .. l*stride + len)), plus the single index
-// `extra` carried by lane `extra_lane` (-1: none).  The warp repeatedly
-// takes the minimum head (one REDUX) and every lane holding it advances.
-// Writes the union to out[0..cap) when out != nullptr; returns its size.
-__device__ int warp_union(const int32_t* lst, int stride, int len, int extra_lane, int extra, int32_t* out, int cap)
+// lane (lane l: lst[l*stride .. l*stride + len)).  The warp repeatedly takes
+// the minimum head (one REDUX) and every lane holding it advances.  Writes
+// the union to out[0..cap); returns its size.
+__device__ int warp_union(const int32_t* lst, int stride, int len, int32_t* out, int cap)
 {
     const int lane = threadIdx.x & 31;
     const int32_t* l = lst + lane * stride;
     int q = 0;
-    int head = lane == extra_lane ? extra : (len > 0 ? l[0] : INT_MAX);
+    int head = len > 0 ? l[0] : INT_MAX;
     int cnt = 0;
     while (true) {
         const int mn = __reduce_min_sync(0xffffffffu, head);
         if (mn == INT_MAX) break;
-        if (out && lane == 0 && cnt < cap) out[cnt] = mn;
+        if (lane == 0 && cnt < cap) out[cnt] = mn;
         cnt++;
         if (head == mn) {
             q++;
-            head = (lane != extra_lane && q < len) ? l[q] : INT_MAX;
+            head = q < len ? l[q] : INT_MAX;
         }
     }
     __syncwarp();
     return cnt;
 }
 
-// Load list `lane` = idx[b..e) (entries with val == 0 skipped when val is
-// given) into lst + lane*stride; returns its length.
-__device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, const double* __restrict__ val, int64_t b,
-                                         int64_t e, int32_t* lst, int stride)
+// Load list `lane` = idx[b..e) into lst + lane*stride (at most stride
+// entries); returns its length.
+__device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, int64_t b, int64_t e, int32_t* lst, int stride)
 {
     const int lane = threadIdx.x & 31;
     int32_t* l = lst + lane * stride;
     int len = 0;
     for (int64_t q = b; q < e; q += 4) {
         int cc[4];
-        bool ok[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            cc[u] = q + u < e ? idx[q + u] : 0;
-            ok[u] = q + u < e && (!val || nonzero_bits(val[q + u]));
-        }
+        for (int u = 0; u < 4; u++) cc[u] = q + u < e ? idx[q + u] : 0;
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            if (ok[u] && len < stride) l[len++] = cc[u];
+            if (q + u < e && len < stride) l[len++] = cc[u];
     }
     return len;
 }
@@ -277,10 +271,10 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
             int len = 0;
             if (lane < e - b) {
                 const int i = ri[b + lane];
-                len = load_list(ri, nullptr, cp[i], cp[i + 1], lst, stride);
+                len = load_list(ri, cp[i], cp[i + 1], lst, stride);
             }
             __syncwarp();
-            cnt = warp_union(lst, stride, len, -1, 0, buf, cap);
+            cnt = warp_union(lst, stride, len, buf, cap);
             if (cnt > cap) { if (lane == 0) atomicCAS(err, 0, SPAI_ERR_UNSUPPORTED); cnt = cap; }
         }
         __syncwarp();
