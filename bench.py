@@ -20,6 +20,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -160,7 +161,8 @@ K_IR_DRAM_BYTES_64CUBE = 5.106e9
 
 
 def ir_kernel_bytes(n, nnz_a, nnz_p, its, s_u=4, s_g=4, s_p=4):
-    """Algorithmic HBM bytes of one refinement-kernel launch.
+    """Algorithmic HBM bytes of one refinement-kernel launch: every matrix and
+    vector the method reads or writes, counted once per use.
 
     Per Arnoldi iteration j: SpMV A (values in u_p + int32 cols + int64 rowptr,
     read v, write t), SpMV P (same, read t), MGS (read V(:,0..j) once, write
@@ -502,8 +504,10 @@ def main():
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
-    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank)
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    # nvidia-smi samples during the timed steps; BENCH_CLOCKS_DIR keeps the raw file
+    clk_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+    clk_path = os.path.join(clk_dir, "clocks_rank%d.csv" % rank)
+    os.makedirs(clk_dir, exist_ok=True)
     with ClockSampler(clk_path) as cs:
         time.sleep(0.3)
         for i in range(args.steps):
