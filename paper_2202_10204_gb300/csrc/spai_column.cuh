@@ -2,8 +2,9 @@
 // on B = A^T D (column j of B is row j of A times d_j).
 //
 // Per column:
-//   1. load the rows j in J_k of A (nonzeros only, scaled by d_j and rounded
-//      to u_f) into shared memory, one list per lane (all loads in flight);
+//   1. load the rows j in J_k of A (nonzeros only, as the u_f values of
+//      B = A^T D formed once per nonzero before the kernel) into shared
+//      memory, one list per lane (all loads in flight);
 //   2. gather: the union of those lists (plus the list {k}) is the shadow
 //      I_k, sorted, and gives the dense tile [B(I_k,J_k) | e_k(I_k)]
 //      (row-major, shared memory): through a hash set and a register sort
@@ -15,9 +16,10 @@
 //      ||x||^2), and the trailing lanes apply the reflector to their
 //      registers.  Half: the tile is held in the A-operand layout of
 //      m16n8k16 MMAs and each step's 32 dot products are one tensor-core
-//      matrix-vector product.  Back substitution is row oriented,
-//      m_c = (y_c - sum_t R(c,t) m_t) / R(c,c), one warp sum per row
-//      (larger shadows: spai_cta.cuh);
+//      matrix-vector product.  Back substitution, m_c = (y_c - sum_t R(c,t)
+//      m_t) / R(c,c): row oriented for single and double (one warp sum per
+//      row), column oriented at half (R in shared memory, lane t updating
+//      y_t) (larger shadows: spai_cta.cuh);
 //   4. explicit residual s = B(I,J) m - e and ||s||_2 from the original tile;
 //   5. adaptive: candidates J~ (column lists of A for l in I with s_l != 0,
 //      minus J), rho_j, mean acceptance, up to beta additions, loop.
