@@ -24,10 +24,9 @@ UNIT_ROUNDOFF = {HALF: 2.0 ** -11, SINGLE: 2.0 ** -24, DOUBLE: 2.0 ** -53, QUAD:
 MODE_PEROP, MODE_ACC32 = 0, 1
 PAT_IDENTITY, PAT_A, PAT_A2 = 0, 1, 2
 
-CF_CONVERGED, CF_FILLCAP, CF_ALPHA, CF_NOCAND, CF_SINGULAR, CF_NONFINITE, CF_TOOBIG = 1, 2, 4, 8, 16, 32, 64
-# largest shadow |I_k| an adaptive augmentation may reach (the CUDA tile limit)
-MAX_SHADOW = 512
-IR_CONVERGED, IR_MAXSTEPS, IR_BREAKDOWN, IR_NONFINITE = 1, 2, 4, 8
+CF_CONVERGED, CF_FILLCAP, CF_ALPHA, CF_NOCAND, CF_SINGULAR, CF_NONFINITE = 1, 2, 4, 8, 16, 32
+IR_CONVERGED, IR_MAXSTEPS, IR_BREAKDOWN, IR_NONFINITE, IR_STAGNATED = 1, 2, 4, 8, 16
+STOP_BACKWARD, STOP_FIXED, STOP_CORRECTION = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "spai_ir_oracle.c")
@@ -51,7 +50,7 @@ class SpaiOpts(C.Structure):
     _fields_ = [("init", C.c_int), ("adaptive", C.c_int), ("eps", C.c_double),
                 ("alpha", C.c_int), ("beta", C.c_int), ("max_fill", C.c_int),
                 ("uf", C.c_int), ("mode", C.c_int), ("rho_restricted", C.c_int),
-                ("scale", C.c_int), ("max_shadow", C.c_int)]
+                ("scale", C.c_int)]
 
 
 class GmresOpts(C.Structure):
@@ -63,7 +62,7 @@ class IrOpts(C.Structure):
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int),
                 ("ur", C.c_int), ("mode", C.c_int), ("tau", C.c_double),
                 ("gmres_maxit", C.c_int), ("imax", C.c_int), ("stop_tol", C.c_double), ("orth", C.c_int),
-                ("side", C.c_int)]
+                ("side", C.c_int), ("stop_rule", C.c_int)]
 
 
 def lib():
@@ -151,7 +150,7 @@ def select(cand, rho_vals, nmax, uf="double"):
 
 
 def spai(A, init=PAT_IDENTITY, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fill=30, uf="double",
-         mode=MODE_ACC32, rho_restricted=False, scale=True, cols=None, max_shadow=MAX_SHADOW):
+         mode=MODE_ACC32, rho_restricted=False, scale=True, cols=None):
     """SPAI of Algorithm 1 run on A^T D; returns a dict with P = M^T D pieces.
 
     ``P_rows[k]`` / ``P_vals[k]`` hold row k of P (= column k of M scaled by
@@ -162,7 +161,7 @@ def spai(A, init=PAT_IDENTITY, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fi
     n = len(rp) - 1
     F = int(max_fill)
     o = SpaiOpts(int(init), int(bool(adaptive)), float(eps), int(alpha), int(beta), F, prec(uf), int(mode),
-                 int(bool(rho_restricted)), int(bool(scale)), int(max_shadow))
+                 int(bool(rho_restricted)), int(bool(scale)))
     d = np.zeros(n)
     Jcnt = np.zeros(n, dtype=np.int32)
     Jidx = np.full(n * F, -1, dtype=np.int32)
@@ -284,17 +283,20 @@ def default_stop_tol(A, u) -> float:
 
 
 def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur="quad",
-             tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32, orth=ORTH_MGS, side=SIDE_LEFT):
+             tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32, orth=ORTH_MGS, side=SIDE_LEFT,
+             stop_rule=STOP_BACKWARD):
     """SPAI-GMRES-IR (Algorithm 3) given P = (rowptr, col, val_up, val_uf) or None; side selects left
-    (Algorithm 3) or right preconditioning of the GMRES solves (reading R14)."""
+    (Algorithm 3) or right preconditioning of the GMRES solves (reading R14); stop_rule and stop_tol
+    the stopping rule of reading R8 (default threshold: q u for the backward rule, u for the correction
+    rule)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
     if stop_tol is None:
-        stop_tol = default_stop_tol(A, u)
+        stop_tol = UNIT_ROUNDOFF[prec(u)] if stop_rule == STOP_CORRECTION else default_stop_tol(A, u)
     o = IrOpts(prec(uf), prec(u), prec(ug), prec(up), prec(ur), int(mode), float(tau),
                int(gmres_maxit if gmres_maxit is not None else min(n, 500)), int(imax), float(stop_tol), int(orth),
-               int(side))
+               int(side), int(stop_rule))
     x = np.zeros(n)
     its = np.zeros(imax + 1, dtype=np.int32)
     nbe = np.full(imax + 1, np.nan)

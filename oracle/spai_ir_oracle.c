@@ -48,13 +48,15 @@
  *   R7  MGS-GMRES, x0 = 0, no restart, stop when |g_{j+1}| / beta <= tau;
  *       Givens rotations, H, g and y in double.  Option: classical
  *       Gram-Schmidt applied twice (CGS2) instead of MGS.
- *   R8  IR stop: before step i, nbe_i = ||r_i||_inf / (||A||_inf ||x_i||_inf
- *       + ||b||_inf) <= stop_tol; at most i_max GMRES solves.
+ *   R8  IR stop (the paper fixes only i_max), checked before step i in this
+ *       order: BACKWARD rule: nbe_i = ||r_i||_inf / (||A||_inf ||x_i||_inf
+ *       + ||b||_inf) <= stop_tol; CORRECTION rule: i >= 1 and
+ *       q_i = ||d_{i-1}||_inf / ||x_i||_inf <= stop_tol (the relative size of
+ *       the last correction); i = i_max; then, for both rules, stagnation:
+ *       i >= 2 and q_i >= q_{i-1} / 2 (the correction did not halve), which
+ *       stops without convergence.  The FIXED rule runs i_max solves.
  *   R10 pattern(A) / pattern(A^2) initial patterns: J_k = nonzero rows of
  *       column k of A (resp. A^2).
- *   R11 an augmentation whose new shadow |I_k| exceeds max_shadow (the
- *       CUDA tile height, 512 rows) is undone and the column keeps its
- *       previous pattern and solve (flag CF_TOOBIG).
  *   R14 right preconditioning (the paper leaves it as future work at the
  *       end of Section 3): GMRES on (A P) u = r from u = 0, w = A (P v_j)
  *       with both products in u_p, the initial vector r rounded to u_p and
@@ -86,13 +88,18 @@
 #define CF_NOCAND 8      /* no acceptable candidate to add      */
 #define CF_SINGULAR 16   /* a zero pivot in R                   */
 #define CF_NONFINITE 32  /* Inf/NaN appeared (overflow in u_f)  */
-#define CF_TOOBIG 64     /* augmentation undone: shadow over max_shadow */
 
 /* IR status flags */
 #define IR_CONVERGED 1
 #define IR_MAXSTEPS 2
 #define IR_BREAKDOWN 4
 #define IR_NONFINITE 8
+#define IR_STAGNATED 16
+
+/* IR stopping rules (reading R8) */
+#define STOP_BACKWARD 0
+#define STOP_FIXED 1
+#define STOP_CORRECTION 2
 
 /* ------------------------------------------------------------------ */
 /* Rounding to a precision (Table 1)                                   */
@@ -299,8 +306,6 @@ typedef struct {
     int mode;            /* MODE_PEROP / MODE_ACC32 */
     int rho_restricted;  /* R3 literal reading */
     int scale;           /* 1: run on A^T D (Section 4); 0: on A^T */
-    int max_shadow;      /* adaptive: an augmentation whose shadow |I_k| would
-                            exceed this is undone and the column stops (<= 0: none) */
 } orc_spai_opts;
 
 /* Candidate scores rho_j (Algorithm 1, rho_jk line; reading R3).
@@ -398,8 +403,6 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
     size_t capC = capI * (size_t)(maxcol + 1) + 2;
     int* J = (int*)malloc(sizeof(int) * (capJ0 > (size_t)F ? capJ0 : (size_t)F + 2));
     int* I = (int*)malloc(sizeof(int) * capI);
-    int* Iprev = (int*)malloc(sizeof(int) * capI);
-    int* Jprev = (int*)malloc(sizeof(int) * ((size_t)F + 2));
     int* cand = (int*)malloc(sizeof(int) * capC);
     double* rho = (double*)malloc(sizeof(double) * capC);
     int* sel = (int*)malloc(sizeof(int) * (size_t)(beta + 1));
@@ -423,7 +426,7 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
         }
         nj = sort_unique(J, nj);
         nj = apply_cap(J, nj, k, F);
-        int fl = 0, ns = 0, m = 0, nj_prev = nj, m_prev = 0;
+        int fl = 0, ns = 0, m = 0;
         double snorm = 0.0;
         for (int step = 0; step <= alpha; step++) {
             /* shadow I_k = union of nonzero columns of rows j in J_k, plus k */
@@ -432,15 +435,6 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
                 for (int64_t q = rp[J[c]]; q < rp[J[c] + 1]; q++) if (val[q] != 0.0) I[m++] = ci[q];
             I[m++] = k;
             m = sort_unique(I, m);
-            if (step > 0 && o->max_shadow > 0 && m > o->max_shadow) {
-                /* undo the last augmentation: keep the previous pattern and solve */
-                nj = nj_prev;
-                for (int c = 0; c < nj; c++) J[c] = Jprev[c];
-                m = m_prev;
-                for (int i = 0; i < m; i++) I[i] = Iprev[i];
-                fl |= CF_TOOBIG;
-                break;
-            }
             /* Abar = B(I_k, J_k) in u_f, ebar = e_k(I_k) */
             for (size_t z = 0; z < (size_t)m * nj; z++) Abar[z] = 0.0;
             for (int c = 0; c < nj; c++) {
@@ -475,10 +469,6 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
             int room = F - nj;
             int nadd = orc_select(nc, cand, rho, o->uf, beta < room ? beta : room, sel);
             if (nadd == 0) { fl |= CF_NOCAND; break; }
-            nj_prev = nj;
-            m_prev = m;
-            for (int c = 0; c < nj; c++) Jprev[c] = J[c];
-            for (int i = 0; i < m; i++) Iprev[i] = I[i];
             for (int a = 0; a < nadd; a++) J[nj++] = sel[a];
             nj = sort_unique(J, nj);
         }
@@ -505,7 +495,7 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
         }
         colres64[k] = sqrt(acc);
     }
-    free(cp); free(ri); free(J); free(I); free(Iprev); free(Jprev); free(cand); free(rho); free(sel);
+    free(cp); free(ri); free(J); free(I); free(cand); free(rho); free(sel);
     free(Abar); free(ebar); free(mb); free(sb);
     return 0;
 }
@@ -702,9 +692,10 @@ typedef struct {
     double tau;             /* GMRES tolerance */
     int gmres_maxit;        /* per GMRES solve */
     int imax;               /* maximum number of refinement steps */
-    double stop_tol;        /* R8 backward-error threshold */
+    double stop_tol;        /* R8 threshold of the stopping rule */
     int orth;               /* 0 MGS, 1 CGS2 */
     int side;               /* 0 left, 1 right preconditioning */
+    int stop_rule;          /* STOP_BACKWARD, STOP_FIXED, STOP_CORRECTION */
 } orc_ir_opts;
 
 /*
@@ -736,6 +727,7 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
     for (int i = 0; i < n; i++) x[i] = rnd(x[i], o->u);
     orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit, o->orth, o->side };
     int i;
+    double dn = 0.0, qprev = 0.0; /* ||d_{i-1}||_inf and q_{i-1} (reading R8) */
     *steps = 0;
     for (i = 0; i <= o->imax; i++) {
         residual_ur(n, arp, aci, av, b, x, o->ur, o->u, r);
@@ -743,13 +735,22 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
         double den = anorm * xn + bnorm;
         nbe[i] = den > 0.0 ? rn / den : 0.0;
         if (!isfinite(nbe[i])) { status |= IR_NONFINITE; break; }
-        if (nbe[i] <= o->stop_tol) { status |= IR_CONVERGED; break; }
+        double q = xn > 0.0 ? dn / xn : (dn > 0.0 ? INFINITY : 0.0);
+        if (o->stop_rule == STOP_BACKWARD && nbe[i] <= o->stop_tol) { status |= IR_CONVERGED; break; }
+        if (o->stop_rule == STOP_CORRECTION && i >= 1 && q <= o->stop_tol) { status |= IR_CONVERGED; break; }
         if (i == o->imax) { status |= IR_MAXSTEPS; break; }
+        if (o->stop_rule != STOP_FIXED && i >= 2 && q >= 0.5 * qprev) { status |= IR_STAGNATED; break; }
+        qprev = q;
         int bd = 0;
         double rr;
         its[i] = orc_gmres(n, arp, aci, av, prp, pci, pv_up, r, &go, dd, &bd, &rr);
         if (bd) status |= IR_BREAKDOWN;
-        for (int q = 0; q < n; q++) x[q] = rnd(x[q] + rnd(dd[q], o->u), o->u);
+        dn = 0.0;
+        for (int q2 = 0; q2 < n; q2++) {
+            double dq = rnd(dd[q2], o->u);
+            if (fabs(dq) > dn) dn = fabs(dq);
+            x[q2] = rnd(x[q2] + dq, o->u);
+        }
         *steps = i + 1;
     }
     (void)ur_b;

@@ -190,6 +190,46 @@ def test_spai_column_matches_library_lstsq():
         assert abs(S["colres64"][k] - np.linalg.norm(BJ @ m_ref - np.eye(n)[k])) < 1e-12
 
 
+def _lstsq_column(Ms, d, J, k):
+    """numpy lstsq of min ||B(I, J) m - e_k(I)|| with B = A^T D and I the nonzero
+    rows of B(:, J) plus k; returns (m, I)."""
+    n = Ms.shape[0]
+    B = (Ms.T @ sp.diags(d)).tocsc()
+    BJ = B[:, J].toarray()
+    I = np.union1d(np.nonzero(np.any(BJ != 0, axis=1))[0], [k])
+    e = (I == k).astype(float)
+    return np.linalg.lstsq(BJ[I], e, rcond=None)[0], I
+
+
+def test_spai_large_shadows_match_library_lstsq():
+    # Algorithm 1 has no bound on the shadow |I_k|: fixed pattern(A) columns of a
+    # matrix with 28 nonzeros per column (shadows of 500-700 rows) and adaptive
+    # columns grown to 30 entries are the least-squares solutions on their full
+    # shadows, and the adaptive ones keep augmenting past 512 rows
+    A = synth.random_sparse(1500, 28, seed=31)
+    Ms = synth.to_scipy(A)
+    cols = [0, 101, 333, 1499]
+    S = O.spai(A, init=O.PAT_A, uf="double", max_fill=30, cols=cols)
+    for k in cols:
+        J = S["Jidx"][k][: S["Jcnt"][k]]
+        m_ref, I = _lstsq_column(Ms, S["d"], J, k)
+        assert len(I) == S["Icnt"][k]
+        np.testing.assert_allclose(S["mbar"][k][: len(J)], m_ref, rtol=1e-10, atol=1e-12)
+    assert min(S["Icnt"][k] for k in cols) > 512
+    A = synth.random_sparse(1500, 24, seed=5)
+    Ms = synth.to_scipy(A)
+    cols = list(range(0, 1500, 75))
+    S = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=0.1, beta=8, max_fill=30, uf="double", cols=cols)
+    big = [k for k in cols if S["Icnt"][k] > 512]
+    assert len(big) >= len(cols) // 2
+    for k in big:
+        J = S["Jidx"][k][: S["Jcnt"][k]]
+        assert len(J) == 30 or (S["flags"][k] & O.CF_CONVERGED)
+        m_ref, I = _lstsq_column(Ms, S["d"], J, k)
+        assert len(I) == S["Icnt"][k]
+        np.testing.assert_allclose(S["mbar"][k][: len(J)], m_ref, rtol=1e-9, atol=1e-11)
+
+
 def test_pattern_A2_matches_scipy():
     A = synth.conv_diff_3d(6, 50.0, seed=3)
     Ms = synth.to_scipy(A)
@@ -620,3 +660,43 @@ def test_ir_right_reaches_working_accuracy():
     nbe = np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b)))
     assert r["steps"] >= 1 and nbe <= 5 * 2.0 ** -53
     assert np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)) < 1e-12
+
+
+def _iterates(A, b, P, steps, **kw):
+    """x_0 .. x_steps from runs with the fixed-step rule (reading R8)."""
+    return [O.gmres_ir(A, b, P, imax=s, stop_rule=O.STOP_FIXED, **kw)["x"] for s in range(steps + 1)]
+
+
+def test_ir_correction_rule_stops_at_small_correction():
+    # reading R8, correction rule: stop before step i once ||d_{i-1}|| / ||x_i|| <= stop_tol;
+    # the expected step is read off the iterates of fixed-step runs
+    A = synth.conv_diff_2d(12, 10.0, 1.0, 0.1, seed=3)
+    b, _ = synth.rhs(A, seed=4)
+    P = O.assemble_P(O.spai(A, init=O.PAT_A, max_fill=30, uf="single"), "single", "single")
+    kw = dict(uf="single", u="double", ug="single", up="single", ur="quad", tau=1e-2)
+    X = _iterates(A, b, P, 8, **kw)
+    q = [None] + [np.max(np.abs(X[s] - X[s - 1])) / np.max(np.abs(X[s])) for s in range(1, 9)]
+    want = next(s for s in range(1, 9) if q[s] <= 1e-10)
+    assert all(q[s] < 0.5 * q[s - 1] for s in range(2, want + 1))  # no stagnation on the way
+    R = O.gmres_ir(A, b, P, stop_rule=O.STOP_CORRECTION, stop_tol=1e-10, **kw)
+    assert R["steps"] == want and R["status"] & O.IR_CONVERGED
+    np.testing.assert_array_equal(R["x"], X[want])
+    # the backward rule converges too, without the stagnation flag
+    Rb = O.gmres_ir(A, b, P, **kw)
+    assert Rb["status"] & O.IR_CONVERGED and not Rb["status"] & O.IR_STAGNATED
+
+
+def test_ir_stagnation_stops_without_convergence():
+    # reading R8, stagnation: stop before step i >= 2 once q_i >= q_{i-1} / 2.  One GMRES
+    # iteration per refinement step on an unpreconditioned nonsymmetric system barely
+    # shrinks the corrections
+    A = synth.random_sparse(200, 6, seed=8, log10_scale=2.0)
+    b, _ = synth.rhs(A, seed=9)
+    kw = dict(uf="single", u="double", ug="double", up="double", ur="double", tau=1e-8, gmres_maxit=1)
+    X = _iterates(A, b, None, 6, **kw)
+    q = [None] + [np.max(np.abs(X[s] - X[s - 1])) / np.max(np.abs(X[s])) for s in range(1, 7)]
+    want = next(s for s in range(2, 7) if q[s] >= 0.5 * q[s - 1])
+    R = O.gmres_ir(A, b, None, **kw)
+    assert R["steps"] == want
+    assert R["status"] & O.IR_STAGNATED and not R["status"] & O.IR_CONVERGED
+    np.testing.assert_array_equal(R["x"], X[want])
