@@ -20,10 +20,11 @@
  *   - CSR arrays: rowptr[n+1] int64 (rowptr[0] = 0, non-decreasing), col[nnz]
  *     int32 in [0, n) sorted ascending within a row, val[nnz] float64.
  *     With on_device = 1 all three are device pointers on the context's
- *     device, otherwise host pointers.  Host inputs are checked in full
+ *     device, otherwise host pointers.  Every input is checked in full
  *     (SPAI_ERR_INVALID_ARG for a structural error, which takes precedence
- *     over SPAI_ERR_ZERO_ROW for an empty row); the scan runs on the device
- *     after the copy.  Device inputs are not scanned.
+ *     over SPAI_ERR_ZERO_ROW for an empty row) before any kernel indexes
+ *     with it: one pass over the rows on the device (for host inputs after
+ *     the copy).
  *   - all work runs on the context's CUDA stream on one GPU; every call
  *     returns after its results are complete.
  *   - calls on one context are serialised by the context; distinct contexts
@@ -41,7 +42,7 @@ extern "C" {
 
 /* ---- status codes ---------------------------------------------------- */
 #define SPAI_OK 0
-#define SPAI_WARN_NOT_CONVERGED 1  /* IR stopped at i_max above the stop tolerance  */
+#define SPAI_WARN_NOT_CONVERGED 1  /* IR stopped (i_max or stagnation) unconverged  */
 #define SPAI_WARN_FILLCAP 2        /* some SPAI columns stopped at the fill cap     */
 #define SPAI_PENDING 3             /* solver_poll: request not finished yet          */
 #define SPAI_ERR_INVALID_ARG (-1)  /* bad pointer, size, option or CSR structure     */
@@ -70,8 +71,14 @@ typedef enum { SPAI_PAT_IDENTITY = 0, SPAI_PAT_A = 1, SPAI_PAT_A2 = 2 } spai_pat
 
 /* refinement stopping rule (Algorithm 3 fixes only i_max) */
 typedef enum {
-    IR_STOP_BACKWARD = 0, /* stop before step i once ||r_i||_inf/(||A||_inf||x_i||_inf+||b||_inf) <= stop_tol */
-    IR_STOP_FIXED = 1     /* always run ir_max_steps steps */
+    IR_STOP_BACKWARD = 0,  /* stop before step i once ||r_i||_inf/(||A||_inf||x_i||_inf+||b||_inf) <= stop_tol */
+    IR_STOP_FIXED = 1,     /* always run ir_max_steps steps */
+    IR_STOP_CORRECTION = 2 /* stop before step i >= 1 once ||d_{i-1}||_inf/||x_i||_inf <= stop_tol */
+    /* With BACKWARD and CORRECTION the refinement also stops, without
+     * convergence (flag 16, SPAI_WARN_NOT_CONVERGED), when it stagnates: before
+     * step i >= 2, if ||d_{i-1}||_inf/||x_i||_inf >= (||d_{i-2}||_inf/||x_{i-1}||_inf)/2,
+     * i.e. the last correction did not halve relative to the iterate.  The
+     * convergence tests come first. */
 } ir_stop_rule;
 
 typedef struct {
@@ -112,7 +119,8 @@ typedef struct {
     int gmres_max_it;            /* iterations per GMRES solve (1..1024); <= 0: min(n, 500) */
     int ir_max_steps;            /* i_max (1..64)                                      */
     ir_stop_rule stop;
-    double stop_tol;             /* <= 0: q*u, q the largest row nonzero count of A    */
+    double stop_tol;             /* <= 0: q*u (BACKWARD, q the largest row nonzero count of A,
+                                    the limit of Theorem 2) or u (CORRECTION)          */
     int orth;                    /* Arnoldi orthogonalisation: 0 modified Gram-Schmidt (the
                                     paper's MGS-GMRES), 1 classical Gram-Schmidt applied
                                     twice (CGS2: two vector reductions per iteration instead
@@ -150,7 +158,8 @@ typedef struct {
     int its[SPAI_IR_MAX_STEPS];          /* GMRES iterations per refinement step     */
     double nbe[SPAI_IR_MAX_STEPS + 1];   /* normwise backward error before each step */
     double final_nbe;                    /* backward error of the returned x         */
-    int flags;                           /* 1 converged, 2 max steps, 4 breakdown, 8 non-finite */
+    int flags;                           /* 1 converged, 2 max steps, 4 breakdown, 8 non-finite,
+                                            16 stagnated (see ir_stop_rule)          */
     int64_t nnz_P;
     double ms_spai, ms_ir;               /* device time of the two phases            */
     double ms_kernel;                    /* device time of the refinement kernel alone */
@@ -239,27 +248,47 @@ int solver_poll(spai_ctx ctx, uint64_t ticket, double* x, ir_stats* st);
 
 const char* spai_strerror(int code);
 
+/* Self-test of the bounded device-side waits (no counterpart in the paper).
+ * Every wait of the refinement kernels (the exchange rounds among blocks and
+ * the counter barrier) gives up after a clock budget, records
+ * SPAI_ERR_TIMEOUT and leaves the kernel, so a block that never arrives
+ * cannot hang the GPU.  This call launches a few blocks on `device` (made
+ * current) whose exchange round (mode 0) or counter barrier (mode 1) waits
+ * for one block more than the launch has, with a budget of limit_ms
+ * milliseconds (0 < limit_ms <= 10000).  Returns SPAI_ERR_TIMEOUT when the
+ * waits gave up as designed; the device stays usable afterwards.
+ * SPAI_ERR_INVALID_ARG for a bad mode or limit. */
+int spai_selftest_wait_timeout(int device, int mode, double limit_ms);
+
 /* ---- allocation-free refinement solve --------------------------------
  * No counterpart in the paper: an engineering entry point for callers that
- * cannot call the CUDA allocator -- code running inside a stream capture,
- * allocation-free real-time or embedded runtimes, and hosts that own the
- * GPU memory budget exactly.  It runs the same refinement kernels as
+ * must not call the CUDA allocator -- real-time loops, where cudaMalloc and
+ * cudaFree have no bounded latency and cudaFree synchronises the device;
+ * hosts that hand all device memory to their own pool at start-up, so that
+ * a later allocation would fail or break their accounting; and runtimes that
+ * forbid allocation once running.  It runs the same refinement kernels as
  * gmres_ir_solve with a given preconditioner, but every scratch buffer lives
- * in one fixed device array of SPAI_NOALLOC_SCRATCH_BYTES that each GPU
- * loading this library holds until the process exits.  It calls no
+ * in one fixed device array of SPAI_NOALLOC_SCRATCH_BYTES (32 MiB) that each
+ * GPU loading this library holds until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *   A, P : device CSR (on_device = 1); P holds the float64 entries of the
- *          left preconditioner (for instance spai_precond_export's output);
- *          P == NULL solves unpreconditioned.
+ *          left preconditioner (for instance spai_precond_export's output),
+ *          or of the right one when opts->side = 1; P == NULL solves
+ *          unpreconditioned.  Both are checked on the device first
+ *          (SPAI_ERR_INVALID_ARG, SPAI_ERR_ZERO_ROW for an empty row of A).
  *   b, x : device float64 arrays of length n; x is output only.
+ *   opts : as gmres_ir_solve (orth 0 and 1, both sides, every stop rule).
  *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
+ * The call reads sizes back to the host between its kernels, so it
+ * synchronises the stream, and returns once x is complete.
  * Returns SPAI_ERR_UNSUPPORTED when the problem (n, nonzeros, gmres_max_it,
  * precisions) needs more than SPAI_NOALLOC_SCRATCH_BYTES, and the other
  * codes as gmres_ir_solve.  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array: calls whose work overlaps
- * on the GPU (other threads or streams) race and must be serialised by the
- * caller.  ir_stats' timing fields are left 0. */
+ * stream capture.  All calls share the one array and the array keeps the
+ * last call's contents (the call clears what must start at zero): calls
+ * whose work overlaps on the GPU (other threads or streams) race and must be
+ * serialised by the caller.  ir_stats' timing fields are left 0. */
 #define SPAI_NOALLOC_SCRATCH_BYTES (32u << 20)
 int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, const double* b, double* x,
                            const ir_opts* opts, void* cuda_stream, ir_stats* st);

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libspai_ir.so")
 HALF, SINGLE, DOUBLE, QUAD = 0, 1, 2, 3
 PREC = {"half": HALF, "single": SINGLE, "double": DOUBLE, "quad": QUAD}
 PAT_IDENTITY, PAT_A, PAT_A2 = 0, 1, 2
-IR_STOP_BACKWARD, IR_STOP_FIXED = 0, 1
+IR_STOP_BACKWARD, IR_STOP_FIXED, IR_STOP_CORRECTION = 0, 1, 2
+IR_CONVERGED, IR_MAXSTEPS, IR_BREAKDOWN, IR_NONFINITE, IR_STAGNATED = 1, 2, 4, 8, 16
 SPAI_IR_MAX_STEPS = 64
 
 OK, WARN_NOT_CONVERGED, WARN_FILLCAP, PENDING = 0, 1, 2, 3
@@ -27,7 +28,7 @@ ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND, ERR_INTERN
 
 EXPORTED = ("spai_ctx_create", "spai_ctx_destroy", "spai_build", "spai_precond_info", "spai_precond_export",
             "spai_precond_free", "gmres_ir_solve", "solver_submit", "solver_poll", "spai_strerror",
-            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch", "spai_build_batch")
+            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch", "spai_build_batch", "spai_selftest_wait_timeout")
 
 
 class spai_csr(C.Structure):
@@ -99,6 +100,7 @@ def lib():
                                                C.POINTER(C.c_int)]
             L.spai_build_batch.argtypes = [vp, C.c_int, C.POINTER(spai_csr), C.POINTER(spai_opts), C.POINTER(vp),
                                            C.POINTER(spai_stats), C.POINTER(C.c_int)]
+            L.spai_selftest_wait_timeout.argtypes = [C.c_int, C.c_int, C.c_double]
             L.spai_strerror.argtypes = [C.c_int]
             L.spai_strerror.restype = C.c_char_p
             _lib = L
@@ -155,7 +157,8 @@ def make_spai_opts(init=PAT_A, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fi
 def make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8, gmres_max_it=0,
                  ir_max_steps=10, stop=IR_STOP_BACKWARD, stop_tol=0.0, orth=0, side=SIDE_LEFT):
     """orth: 0 modified Gram-Schmidt (default, the paper's), 1 classical Gram-Schmidt twice.
-    side: SIDE_LEFT (Algorithm 3) or SIDE_RIGHT (GMRES on A P u = r, d = P u)."""
+    side: SIDE_LEFT (Algorithm 3) or SIDE_RIGHT (GMRES on A P u = r, d = P u).
+    stop: IR_STOP_BACKWARD, IR_STOP_FIXED or IR_STOP_CORRECTION (stop_tol <= 0: the default threshold)."""
     return ir_opts(_prec(uf), _prec(u), _prec(ug), _prec(up), _prec(ur), float(tau), int(gmres_max_it),
                    int(ir_max_steps), int(stop), float(stop_tol), int(orth), int(side))
 
@@ -312,6 +315,11 @@ def solver_poll(ctx: Context, ticket: int, x=None):
         return None
     _check(rc, "solver_poll")
     return _ir_dict(st, rc)
+
+
+def selftest_wait_timeout(device=0, mode=0, limit_ms=50.0) -> int:
+    """Runs the bounded-wait self-test; returns its code (ERR_TIMEOUT when the waits gave up)."""
+    return lib().spai_selftest_wait_timeout(int(device), int(mode), float(limit_ms))
 
 
 def gmres_ir_solve_noalloc(A, b, x, P=None, opts: ir_opts | None = None, stream=None):

@@ -136,7 +136,7 @@ int csr_validate_host(const spai_csr* A)
 {
     if (!A || A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
     if (A->n > INT32_MAX) return SPAI_ERR_UNSUPPORTED;
-    if (A->on_device) return 0;  // device arrays are checked by the kernels' own guards
+    if (A->on_device) return 0;  // device arrays: csr_check_device, before the kernels use them
     if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) return SPAI_ERR_INVALID_ARG;
     for (int64_t i = 0; i < A->n; i++) {
         int64_t b = A->rowptr[i], e = A->rowptr[i + 1];
@@ -151,30 +151,10 @@ int csr_validate_host(const spai_csr* A)
     return 0;
 }
 
-// The full structural check of a host CSR once it is on the device: rows
-// with rowptr out of order or past nnz, columns outside [0, n) or not
-// strictly ascending (flag 1), empty rows (flag 2).
-__global__ void k_csr_check(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                            int* __restrict__ flags)
-{
-    int f = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = rp[i], e = rp[i + 1];
-        if (b < 0 || e < b || e > nnz) { f |= 1; continue; }
-        if (e == b) { f |= 2; continue; }
-        int prev = -1;
-        for (int64_t q = b; q < e; q++) {
-            const int c = col[q];
-            if (c < 0 || c >= n || c <= prev) { f |= 1; break; }
-            prev = c;
-        }
-    }
-    if (f) atomicOr(flags, f);
-}
-
-// Host inputs: the O(1) checks here, the scan of every row on the device
-// after the copy (csr_check_device); a host loop over a matrix of millions of
-// entries cost milliseconds per call.
+// The structural check of every row on the device (k_csr_check, common.cuh):
+// for host inputs after the copy (the O(1) checks run on the host first; a
+// host loop over a matrix of millions of entries cost milliseconds per call),
+// for device inputs before any kernel indexes with them.
 int csr_check_device(const DevCsr& A, int num_sms, cudaStream_t s)
 {
     int* flags = nullptr;
@@ -184,7 +164,7 @@ int csr_check_device(const DevCsr& A, int num_sms, cudaStream_t s)
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + 255) / 256, (int64_t)num_sms * 8));
     if (cudaMemsetAsync(flags, 0, sizeof(int), s) != cudaSuccess) rc = SPAI_ERR_CUDA;
     if (!rc) {
-        k_csr_check<<<gb, 256, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, flags);
+        k_csr_check<<<gb, 256, 0, s>>>(A.n, A.nnz, A.rowptr, A.col, flags, 0);
         if (cudaGetLastError() != cudaSuccess) rc = SPAI_ERR_CUDA;
     }
     if (!rc && cudaMemcpyAsync(&h, flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
@@ -422,7 +402,7 @@ int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_prec
     SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
     DevCsr dA;
     rc = csr_to_device(A, &dA, ctx->stream);
-    if (!rc && !A->on_device) rc = csr_check_device(dA, ctx->num_sms, ctx->stream);
+    if (!rc) rc = csr_check_device(dA, ctx->num_sms, ctx->stream);
     if (!rc) rc = spai_build_dev(ctx->device, ctx->num_sms, ctx->stream, dA, opts, P_out, st);
     csr_release(&dA, ctx->stream);
     cudaStreamSynchronize(ctx->stream);
@@ -470,6 +450,7 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
                 for (int i = next++; i < count; i = next++) {
                     DevCsr dA;
                     int r = csr_to_device(&A[i], &dA, s);
+                    if (!r && A[i].on_device) r = csr_check_device(dA, ctx->num_sms, s);
                     if (!r) r = spai_build_dev(ctx->device, ctx->num_sms, s, dA, opts, &P_out[i], st ? &st[i] : nullptr);
                     csr_release(&dA, s);
                     if (cudaStreamSynchronize(s) != cudaSuccess && r >= 0) r = SPAI_ERR_CUDA;
@@ -556,7 +537,7 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
     spai_precond own = nullptr;
     int wrc = 0;
     rc = csr_to_device(A, &dA, s);
-    if (!rc && !A->on_device) rc = csr_check_device(dA, ctx->num_sms, s);
+    if (!rc) rc = csr_check_device(dA, ctx->num_sms, s);
     if (!rc) {
         if (A->on_device) {
             db = const_cast<double*>(b);
@@ -617,6 +598,8 @@ int gmres_ir_solve_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_
         rc = csr_to_device(&A[i], &dA[i], s);
         if (rc) break;
         if (A[i].on_device) {
+            rc = csr_check_device(dA[i], ctx->num_sms, s);
+            if (rc) break;
             db[i] = b[i];
             dx[i] = x[i];
         } else {
@@ -667,6 +650,13 @@ int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_o
             cudaMemcpy(r->b.data(), b, sizeof(double) * A->n, cudaMemcpyDeviceToHost) != cudaSuccess) {
             delete r;
             return SPAI_ERR_CUDA;
+        }
+        // the copy of a device input gets the host's structural check
+        const spai_csr hc{r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(), 0};
+        const int vr = csr_validate_host(&hc);
+        if (vr) {
+            delete r;
+            return vr;
         }
     } else {
         memcpy(r->rowptr.data(), A->rowptr, sizeof(int64_t) * (A->n + 1));

@@ -200,6 +200,33 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch
 
 }  // namespace spai
 
+// The structural check of a CSR on the device, one thread per row: rowptr[0]
+// = 0, rowptr[n] = nnz, rows in order and inside [0, nnz], columns inside
+// [0, n) and strictly ascending (flag 1); empty rows (flag 2) unless
+// allow_empty.  Internal linkage: each translation unit that launches it
+// has its own copy.
+static __global__ void k_csr_check(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                   const int32_t* __restrict__ col, int* __restrict__ flags, int allow_empty)
+{
+    int f = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        if ((i == 0 && b != 0) || (i == n - 1 && e != nnz)) f |= 1;
+        if (b < 0 || e < b || e > nnz) { f |= 1; continue; }
+        if (e == b) {
+            if (!allow_empty) f |= 2;
+            continue;
+        }
+        int prev = -1;
+        for (int64_t q = b; q < e; q++) {
+            const int c = col[q];
+            if (c < 0 || c >= n || c <= prev) { f |= 1; break; }
+            prev = c;
+        }
+    }
+    if (f) atomicOr(flags, f);
+}
+
 #define SPAI_CUDA_TRY(expr)                                   \
     do {                                                      \
         cudaError_t _e = (expr);                              \

@@ -95,7 +95,7 @@ struct IrShared {
     unsigned epoch2;  // rounds of the Gram-Schmidt group
     unsigned gepoch;  // CGS2 barrier count
     int ok;
-    double bcast[2];
+    double bcast[3];
     double resid;
 };
 
@@ -204,18 +204,22 @@ template <class T> struct SumAcc {
     }
 };
 
-struct Max2Acc {
-    double m0, m1;
-    __device__ void reset() { m0 = 0.0; m1 = 0.0; }
+struct Max3Acc {
+    double m[3];
+    __device__ void reset() { m[0] = m[1] = m[2] = 0.0; }
     __device__ void add(const uint32_t* w)
     {
-        m0 = fmax(m0, __longlong_as_double((long long)(((unsigned long long)w[0] << 32) | w[1])));
-        m1 = fmax(m1, __longlong_as_double((long long)(((unsigned long long)w[2] << 32) | w[3])));
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            m[k] = fmax(m[k], __longlong_as_double((long long)(((unsigned long long)w[2 * k] << 32) | w[2 * k + 1])));
     }
     __device__ void finish(unsigned lane, IrShared* sh)
     {
-        double t0 = warp_max(m0), t1 = warp_max(m1);
-        if (lane == 0) { sh->bcast[0] = t0; sh->bcast[1] = t1; }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double t = warp_max(m[k]);
+            if (lane == 0) sh->bcast[k] = t;
+        }
     }
 };
 
@@ -255,27 +259,30 @@ __device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out, const W
     return good;
 }
 
-// Max of two non-negative doubles over all blocks.
-__device__ bool xmax2(const IrArgs& a, IrShared* sh, double* red, double v0, double v1, double& o0, double& o1)
+// Max of three non-negative doubles over all blocks; red holds 96 doubles.
+__device__ bool xmax3(const IrArgs& a, IrShared* sh, double* red, const double (&v)[3], double (&o)[3])
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v0 = warp_max(v0);
-    v1 = warp_max(v1);
-    if (lane == 0) { red[wid] = v0; red[32 + wid] = v1; }
-    __syncthreads();
-    uint32_t pay[4] = {0u, 0u, 0u, 0u};
-    if (wid == 0) {
-        double t0 = warp_max(lane < nw ? red[lane] : 0.0);
-        double t1 = warp_max(lane < nw ? red[32 + lane] : 0.0);
-        unsigned long long u0 = (unsigned long long)__double_as_longlong(t0);
-        unsigned long long u1 = (unsigned long long)__double_as_longlong(t1);
-        pay[0] = (uint32_t)(u0 >> 32); pay[1] = (uint32_t)u0;
-        pay[2] = (uint32_t)(u1 >> 32); pay[3] = (uint32_t)u1;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const double t = warp_max(v[k]);
+        if (lane == 0) red[32 * k + wid] = t;
     }
-    Max2Acc acc;
-    bool good = exchange<4, true>(a, sh, pay, acc);
-    o0 = sh->bcast[0];
-    o1 = sh->bcast[1];
+    __syncthreads();
+    uint32_t pay[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const double t = warp_max(lane < nw ? red[32 * k + lane] : 0.0);
+            const unsigned long long u = (unsigned long long)__double_as_longlong(t);
+            pay[2 * k] = (uint32_t)(u >> 32);
+            pay[2 * k + 1] = (uint32_t)u;
+        }
+    }
+    Max3Acc acc;
+    bool good = exchange<6, true>(a, sh, pay, acc);
+#pragma unroll
+    for (int k = 0; k < 3; k++) o[k] = sh->bcast[k];
     return good;
 }
 
@@ -362,7 +369,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ IrShared shs;
     __shared__ TG redg[33];
-    __shared__ double redd[64];
+    __shared__ double redd[96];
     IrShared* sh = &shs;
     const int kmax = a.kmax;
     const int tid = threadIdx.x, BT = blockDim.x;
@@ -432,6 +439,8 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
     unsigned vx = 0;  // CGS2 exchanges so far (identical in every block)
 
     int steps = 0, flags = 0;
+    double dmax = 0.0;   // this thread's largest |d| of the last correction (as added to x, in u)
+    double qprev = 0.0;  // ||d_{i-2}|| / ||x_{i-1}|| (the stagnation test)
     for (int it = 0; it <= a.imax; it++) {
         // ---------------- residual r = b - A x in u_r, stored in u
         double rmax = 0.0, xmax = 0.0;
@@ -447,14 +456,21 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             rmax = fmax(rmax, fabs((double)rv));
             xmax = fmax(xmax, fabs((double)x[row]));
         }
-        double rn, xn;
-        if (!xmax2(a, sh, redd, rmax, xmax, rn, xn)) return;
+        double mx[3];
+        if (!xmax3(a, sh, redd, {rmax, xmax, dmax}, mx)) return;
+        const double rn = mx[0], xn = mx[1], dn = mx[2];
         const double den = a.anorm * xn + a.bnorm;
         const double nb = den > 0.0 ? rn / den : 0.0;
         if (bid == 0 && tid == 0) a.nbe[it] = nb;
         if (!isfinite(nb)) { flags |= 8; break; }
+        // the stopping rules (identical decisions in every block: the maxima are exchanged)
+        const double q = xn > 0.0 ? dn / xn : (dn > 0.0 ? INFINITY : 0.0);
         if (a.stop_rule == IR_STOP_BACKWARD && nb <= a.stop_tol) { flags |= 1; break; }
+        if (a.stop_rule == IR_STOP_CORRECTION && it >= 1 && q <= a.stop_tol) { flags |= 1; break; }
         if (it == a.imax) { flags |= 2; break; }
+        if (a.stop_rule != IR_STOP_FIXED && it >= 2 && q >= 0.5 * qprev) { flags |= 16; break; }
+        qprev = q;
+        dmax = 0.0;
 
         // ---------------- z = P r (left) or r (right) in u_p, stored in u_g; beta = ||z||
         TG part = TG(0);
@@ -751,12 +767,18 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 }
                 if (!xbar(a, sh)) return;
                 sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&wbuf[c]); },
-                              [&](int64_t row, TP v) { x[row] = (TU)((TU)x[row] + (TU)(TG)v); });
+                              [&](int64_t row, TP v) {
+                                  const TU du = (TU)(TG)v;
+                                  dmax = fmax(dmax, fabs((double)du));
+                                  x[row] = (TU)((TU)x[row] + du);
+                              });
             } else {
                 for (int64_t row = r0 + tid; row < r1; row += BT) {
                     TG dsum = TG(0);
                     for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
-                    x[row] = (TU)((TU)x[row] + (TU)dsum);
+                    const TU du = (TU)dsum;
+                    dmax = fmax(dmax, fabs((double)du));
+                    x[row] = (TU)((TU)x[row] + du);
                 }
             }
         }
@@ -1067,7 +1089,19 @@ int ir_check_opts(const ir_opts* o)
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
     if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
     if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
+    if (o->stop != IR_STOP_BACKWARD && o->stop != IR_STOP_FIXED && o->stop != IR_STOP_CORRECTION)
+        return SPAI_ERR_INVALID_ARG;
     return 0;
+}
+
+// The stopping threshold (reading R8): the caller's, else q u for the
+// backward-error rule (q the longest row of A, the limit of Theorem 2) and u
+// for the correction rule.
+double ir_stop_tol(const ir_opts* o, int q)
+{
+    const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    if (o->stop_tol > 0) return o->stop_tol;
+    return o->stop == IR_STOP_CORRECTION ? uu : q * uu;
 }
 
 int ir_job_kmax(int64_t n, const ir_opts* o, int* kmax)
@@ -1200,7 +1234,6 @@ void ir_job_args(IrJob& J, int device, const ir_opts* o)
     memcpy(&anorm, &t0, 8);
     memcpy(&bnorm, &t1, 8);
     const int q = (int)J.h_norms[2];
-    const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
     const DevCsr& A = *J.A;
     a.n = J.n;
     a.A.off = J.As.off; a.A.col = J.As.col; a.A.val = J.As.val;
@@ -1214,7 +1247,7 @@ void ir_job_args(IrJob& J, int device, const ir_opts* o)
     if (clk_khz <= 0) clk_khz = 2000000;
     a.limit = (long long)clk_khz * 1000LL * 4;  // about four seconds per wait
     a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
-    a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
+    a.stop_tol = ir_stop_tol(o, q);
     a.kmax = J.kmax; a.imax = J.imax; a.stop_rule = o->stop;
     a.its = J.its; a.nbe = J.nbe; a.out = J.outv;
     a.orth = o->orth; a.pvec = J.pvec; a.gcount = J.gcount; a.side = o->side;
@@ -1255,7 +1288,7 @@ int ir_job_result(const IrJob& J, const ir_opts* o, ir_stats* st)
         st->nnz_P = J.P ? J.P->nnz : 0;
     }
     if (J.h_out[1] & 8) return SPAI_ERR_NONFINITE;
-    if (!(J.h_out[1] & 1) && o->stop == IR_STOP_BACKWARD) return SPAI_WARN_NOT_CONVERGED;
+    if (!(J.h_out[1] & 1) && o->stop != IR_STOP_FIXED) return SPAI_WARN_NOT_CONVERGED;
     return 0;
 }
 
@@ -1354,6 +1387,81 @@ done:
     if (ek0) cudaEventDestroy(ek0);
     if (ek1) cudaEventDestroy(ek1);
     if (rc < 0) cudaStreamSynchronize(s);
+    return rc;
+}
+
+// ====================================================================
+// Self-test of the bounded device waits (spai_selftest_wait_timeout): the
+// blocks of a small launch run one exchange round (mode 0) or one counter
+// barrier (mode 1) that counts one block more than the grid holds, so they
+// wait for a word or an arrival that nothing provides.  Each wait gives up
+// after a.limit clock cycles, records SPAI_ERR_TIMEOUT and returns, exactly as
+// in the refinement kernels.
+// ====================================================================
+
+namespace {
+
+__global__ void k_wait_probe(IrArgs a, int mode)
+{
+    __shared__ IrShared shs;
+    if (threadIdx.x == 0) {
+        shs.bid = (int)blockIdx.x;
+        shs.G = (int)gridDim.x + 1;  // a block that does not exist
+        shs.epoch = 0;
+        shs.epoch2 = 0;
+        shs.gepoch = 0;
+        shs.ok = 1;
+    }
+    __syncthreads();
+    if (mode == 0) {
+        uint32_t pay[1] = {0u};
+        NoAcc acc;
+        exchange<1, true>(a, &shs, pay, acc);
+    } else {
+        const GridBarrier gb{a.gcount, a.err, a.limit, gridDim.x + 1};
+        grid_sync(gb, &shs.gepoch, &shs.ok);
+    }
+}
+
+}  // namespace
+
+extern "C" int spai_selftest_wait_timeout(int device, int mode, double limit_ms)
+{
+    if (mode != 0 && mode != 1) return SPAI_ERR_INVALID_ARG;
+    if (!(limit_ms > 0.0) || limit_ms > 10000.0) return SPAI_ERR_INVALID_ARG;
+    SPAI_CUDA_TRY(cudaSetDevice(device));
+    constexpr int grid = 4;
+    unsigned long long* msg = nullptr;
+    int* err = nullptr;
+    unsigned* gcount = nullptr;
+    const size_t msg_bytes = sizeof(unsigned long long) * 2 * (grid + 1) * SLOT_WORDS;
+    int rc = 0;
+    if (cudaMalloc((void**)&msg, msg_bytes) != cudaSuccess || cudaMalloc((void**)&err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void**)&gcount, sizeof(unsigned)) != cudaSuccess)
+        rc = SPAI_ERR_NO_MEMORY;
+    if (!rc && (cudaMemset(msg, 0, msg_bytes) != cudaSuccess || cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+                cudaMemset(gcount, 0, sizeof(unsigned)) != cudaSuccess))
+        rc = SPAI_ERR_CUDA;
+    if (!rc) {
+        IrArgs a;
+        memset(&a, 0, sizeof(a));
+        a.msg = msg;
+        a.err = err;
+        a.gcount = gcount;
+        int clk_khz = device_attr_cached(cudaDevAttrClockRate, device);
+        if (clk_khz <= 0) clk_khz = 2000000;
+        a.limit = (long long)((double)clk_khz * limit_ms);
+        k_wait_probe<<<grid, 32>>>(a, mode);
+        int h = 0;
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = SPAI_ERR_CUDA;
+        else
+            rc = h;  // SPAI_ERR_TIMEOUT when every wait gave up as designed
+    }
+    cudaFree(msg);
+    cudaFree(err);
+    cudaFree(gcount);
     return rc;
 }
 
@@ -1593,9 +1701,10 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
 // ====================================================================
 // Allocation-free refinement solve (gmres_ir_solve_noalloc).
 //
-// For callers that must not allocate device memory: code running inside a
-// CUDA graph capture, callers that own their memory budget exactly, or
-// runtimes that forbid the CUDA allocator after start-up.  The refinement
+// For callers that must not allocate device memory: real-time loops (the
+// allocator's latency is unbounded and cudaFree synchronises the device),
+// hosts that own their memory budget exactly, or runtimes that forbid the
+// CUDA allocator after start-up.  The refinement
 // scratch (SELL copies of A and P, the Krylov basis, the residual and
 // iterate, the exchange slots) lives in one file-scope device array of
 // SPAI_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds
@@ -1716,6 +1825,9 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
+    if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
+    if (o->stop != IR_STOP_BACKWARD && o->stop != IR_STOP_FIXED && o->stop != IR_STOP_CORRECTION)
+        return SPAI_ERR_INVALID_ARG;
     const int64_t n = A->n;
     int kmax = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
     if (kmax > n) kmax = (int)n;
@@ -1735,7 +1847,8 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     const int64_t nsl = (n + 31) >> 5;
     Carve cv{base, 0, (size_t)SPAI_NOALLOC_SCRATCH_BYTES};
     const size_t msg_bytes = sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS;
-    const size_t ctrl_bytes = sizeof(int) * 4 + sizeof(int) * (imax + 1) + sizeof(double) * (imax + 1) +
+    // control words: err[2], out[2], the CSR check flags, its[imax + 1], nbe[imax + 1], the norms
+    const size_t ctrl_bytes = sizeof(int) * 6 + sizeof(int) * (imax + 1) + sizeof(double) * (imax + 1) +
                               sizeof(unsigned long long) * 3 + 64;
     unsigned long long* msg = (unsigned long long*)cv.take(msg_bytes);
     unsigned char* ctrl = (unsigned char*)cv.take(ctrl_bytes);
@@ -1749,11 +1862,16 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     int32_t* aw = (int32_t*)cv.take(sizeof(int32_t) * nsl);
     int64_t* poff = P ? (int64_t*)cv.take(sizeof(int64_t) * (nsl + 1)) : nullptr;
     int32_t* pw = P ? (int32_t*)cv.take(sizeof(int32_t) * nsl) : nullptr;
-    if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)))
+    // CGS2: the partial dot products of every block and the counter of their barrier
+    void* pvec = o->orth ? cv.take((size_t)sg * 2 * MAX_GRID * (kmax + 1)) : nullptr;
+    if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)) ||
+        (o->orth && !pvec))
         return SPAI_ERR_UNSUPPORTED;  // the problem does not fit the fixed scratch
     int* err = (int*)ctrl;
     int* outv = err + 2;
-    int* its = outv + 2;
+    int* csrf = outv + 2;                   // structural check flags of A and P
+    unsigned* gcount = (unsigned*)(csrf + 1);
+    int* its = csrf + 2;
     double* nbe = (double*)(((uintptr_t)(its + imax + 1) + 7) & ~uintptr_t(7));
     unsigned long long* norms = (unsigned long long*)(nbe + imax + 1);
     // the array keeps the previous call's contents: clear what must start at zero
@@ -1763,6 +1881,25 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, (int64_t)num_sms * 32));
     const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((nsl * 32 + tb - 1) / tb, (int64_t)num_sms * 16));
     int nl = 0;
+    // the structural check of both device CSRs (rowptr order and range, columns in
+    // [0, n) and ascending, no empty row of A) before any kernel indexes with them;
+    // its flags come back with the SELL sizes below
+    {
+        const int gc = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8));
+        k_csr_check<<<gc, 256, 0, s>>>(n, A->nnz, A->rowptr, A->col, csrf, 0);
+        nl++;
+        if (P) {
+            // rows of P may be empty (a zero row of P is a valid preconditioner row)
+            k_csr_check<<<gc, 256, 0, s>>>(n, P->nnz, P->rowptr, P->col, csrf, 1);
+            nl++;
+        }
+        SPAI_CUDA_TRY(cudaGetLastError());
+        int h_csr = 0;
+        SPAI_CUDA_TRY(cudaMemcpyAsync(&h_csr, csrf, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPAI_CUDA_TRY(cudaStreamSynchronize(s));
+        if (h_csr & 1) return SPAI_ERR_INVALID_ARG;
+        if (h_csr & 2) return SPAI_ERR_ZERO_ROW;
+    }
     k_sell_width<<<gs, tb, 0, s>>>(n, A->rowptr, aw);
     k_scan_one_block<<<1, 1024, 0, s>>>(nsl, aw, aoff);
     nl += 2;
@@ -1820,7 +1957,6 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
         memcpy(&bnorm, &t1, 8);
     }
     const int q = (int)h_norms[2];
-    const double uu = o->u == SPAI_SINGLE ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
     a.n = n;
     a.A.off = aoff; a.A.col = acol; a.A.val = aval;
     if (P) { a.P.off = poff; a.P.col = pcol; a.P.val = pval; }
@@ -1832,10 +1968,11 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     if (clk_khz <= 0) clk_khz = 2000000;
     a.limit = (long long)clk_khz * 1000LL * 4;
     a.anorm = anorm; a.bnorm = bnorm; a.tau = o->tau;
-    a.stop_tol = o->stop_tol > 0 ? o->stop_tol : q * uu;
+    a.stop_tol = ir_stop_tol(o, q);
     a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
     a.its = its; a.nbe = nbe; a.out = outv;
     a.side = o->side;
+    a.orth = o->orth; a.pvec = pvec; a.gcount = gcount;
     const int rm = o->ur == SPAI_QUAD ? 2 : 1;
     int grid = 0;
     if (o->u == SPAI_DOUBLE) {
@@ -1882,6 +2019,6 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
         st->nnz_P = P ? P->nnz : 0;
     }
     if (h_out[1] & 8) return SPAI_ERR_NONFINITE;
-    if (!(h_out[1] & 1) && o->stop == IR_STOP_BACKWARD) return SPAI_WARN_NOT_CONVERGED;
+    if (!(h_out[1] & 1) && o->stop != IR_STOP_FIXED) return SPAI_WARN_NOT_CONVERGED;
     return 0;
 }

@@ -12,6 +12,9 @@
 //                  and |I_k| for sizing the per-column tiles
 //   k_spai         (spai_column.cuh) one warp per column: gather, Householder QR,
 //                  back substitution, explicit residual, adaptive augmentation
+//                  (k_spai_cta, spai_cta.cuh: one CTA per column for shadows of up
+//                  to 512 rows; k_spai_big, spai_big.cuh: larger shadows, the
+//                  tile in global memory)
 //   k_assemble     P row k = m_k * d(J_k) in CSR (column k of M is row k of P)
 #include <climits>
 #include <cstdio>
@@ -19,7 +22,7 @@
 
 #include "common.cuh"
 #include "internal.h"
-#include "spai_column.cuh"
+#include "spai_big.cuh"
 
 using namespace spai;
 
@@ -237,11 +240,13 @@ __device__ __forceinline__ int load_list(const int32_t* __restrict__ idx, int64_
 // plus k|.  One warp per column.  Per-warp shared memory: buf[cap] for the
 // uncapped pattern, 32 lists of `stride` ints, and a hash set of tsz slots
 // that counts the shadow (its size only is needed, so no sorted merge).
+// Columns whose shadow exceeds big_thr are appended to big[] (count *nbig).
 __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                           const double* __restrict__ val, const int64_t* __restrict__ cp,
                           const int32_t* __restrict__ ri, int32_t* __restrict__ Jidx, int32_t* __restrict__ Jcnt,
                           int32_t* __restrict__ Icnt, int cap, int stride, int tsz, int* __restrict__ err,
-                          int* __restrict__ maxI, const int* __restrict__ zeros)
+                          int* __restrict__ maxI, const int* __restrict__ zeros, int big_thr,
+                          int32_t* __restrict__ big, int* __restrict__ nbig)
 {
     const bool zv = *zeros != 0;  // A stores explicit zeros: test the values
     extern __shared__ int32_t pbuf[];
@@ -320,6 +325,7 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         if (lane == 0) {
             Icnt[k] = mI;
             atomicMax(maxI, mI);
+            if (mI > big_thr) big[atomicAdd(nbig, 1)] = (int32_t)k;  // for the large-shadow kernel
         }
         __syncwarp();
         for (int t = lane; t < tsz; t += 32) tab[t] = -1;
@@ -551,7 +557,10 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     int rc = 0;
     // device scratch
     double* d = nullptr;
-    int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|, [3] [4] longest row and column, [5] explicit zeros
+    int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|, [3] [4] longest row and column,
+                             // [5] explicit zeros, [6] columns for the large-shadow kernel
+    int32_t* big = nullptr;  // those columns
+    unsigned char* slab = nullptr;
     int32_t* ccount = nullptr;
     int64_t* cp = nullptr;
     int32_t* ri = nullptr;
@@ -562,7 +571,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     unsigned long long* fstat = nullptr;
     size_t ssz = o->uf == SPAI_HALF ? 2 : (o->uf == SPAI_SINGLE ? 4 : 8);
     spai_precond P = nullptr;
-    int h_err[3] = {0, 0, 0};
+    int h_err[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long h_fstat[3] = {0, 0, 0};
     int maxrow = 0, maxcol = 0;
     const int optin = device_attr_cached(cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -570,7 +579,8 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
 
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
     TRY(dev_alloc((void**)&d, sizeof(double) * n, s));
-    TRY(dev_alloc((void**)&err, sizeof(int) * 6, s));
+    TRY(dev_alloc((void**)&err, sizeof(int) * 8, s));
+    TRY(dev_alloc((void**)&big, sizeof(int32_t) * n, s));
     TRY(dev_alloc((void**)&ccount, sizeof(int32_t) * (n + 1), s));
     TRY(dev_alloc((void**)&cp, sizeof(int64_t) * (n + 1), s));
     TRY(dev_alloc((void**)&ri, sizeof(int32_t) * (nnz > 0 ? nnz : 1), s));
@@ -584,7 +594,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     TRY(dev_alloc(&mval, ssz * n * F, s));
     TRY(dev_alloc(&bval, ssz * (nnz > 0 ? nnz : 1), s));
     TRY(dev_alloc((void**)&fstat, sizeof(unsigned long long) * 3, s));
-    if (cudaMemsetAsync(err, 0, sizeof(int) * 6, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+    if (cudaMemsetAsync(err, 0, sizeof(int) * 8, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(fstat, 0, sizeof(unsigned long long) * 3, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     {
@@ -633,11 +643,16 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         SPAI_CUDA_TRY(allow_max_dynamic_smem(k_pattern));
         int64_t blocks = std::min<int64_t>((n + wpb - 1) / wpb, (int64_t)num_sms * 64);
         if (blocks < 1) blocks = 1;
+        // fixed patterns: the columns whose shadow exceeds the CTA tile go to the
+        // large-shadow kernel (adaptive columns are handed over by the column
+        // kernels when they outgrow them)
+        const int big_thr = o->adaptive ? INT_MAX : MMAX_LIMIT;
         k_pattern<<<(unsigned)blocks, wpb * 32, sm, s>>>(n, o->init, F, A.rowptr, A.col, A.val, cp, ri, Jidx, Jcnt,
-                                                        Icnt, cap, stride, tsz, err, err + 1, err + 5);
+                                                        Icnt, cap, stride, tsz, err, err + 1, err + 5, big_thr, big,
+                                                        err + 6);
         nl += 1;
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 2, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (h_err[0]) { rc = h_err[0]; goto done; }
     }
@@ -650,11 +665,13 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         a.alpha = o->alpha < 0 ? (int)((n + o->beta - 1) / std::max(o->beta, 1)) : o->alpha;
         a.beta = o->beta; a.rho_restricted = o->rho_restricted; a.err = err;
         a.rl = maxrow;
-        // adaptive: the tile holds up to MMAX_LIMIT shadow rows; a column whose
-        // augmented shadow would exceed it keeps its previous solve (flag 64)
-        int mneed = o->adaptive ? (int)std::min<int64_t>((int64_t)F * maxrow + 1, (int64_t)MMAX_LIMIT) : h_err[1];
+        a.big = big;
+        a.nbig = err + 6;
+        // the warp and CTA kernels hold up to MMAX_LIMIT shadow rows; larger
+        // shadows go to the large-shadow kernel below
+        const int64_t mall = o->adaptive ? (int64_t)F * maxrow + 1 : (int64_t)h_err[1];
+        int mneed = (int)std::min<int64_t>(mall, (int64_t)MMAX_LIMIT);
         if (mneed < 1) mneed = 1;
-        if (mneed > MMAX_LIMIT) { rc = SPAI_ERR_UNSUPPORTED; goto done; }
         a.mmax = (mneed + 31) & ~31;
         int cmax = 1;
         // raw candidate capacity: |I| * (largest column count of A); power of two
@@ -664,8 +681,35 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         if (o->uf == SPAI_HALF) TRY(launch_spai_half(a, o->adaptive != 0, num_sms, smem_cap, s));
         else if (o->uf == SPAI_SINGLE) TRY(launch_spai_single(a, o->adaptive != 0, num_sms, smem_cap, s));
         else TRY(launch_spai_double(a, o->adaptive != 0, num_sms, smem_cap, s));
-        if (cudaEventRecord(ek1, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         nl++;
+        // the large-shadow kernel for the listed columns: fixed patterns know
+        // their count from k_pattern; adaptive builds read what the column
+        // kernels handed over
+        int nbig = h_err[6];
+        if (o->adaptive) {
+            if (cudaMemcpyAsync(&nbig, err + 6, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+            if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        }
+        if (nbig > 0) {
+            // every shadow has at most mall rows and every candidate list at most
+            // mall * (longest column of A) entries
+            int64_t cc = 1;
+            if (o->adaptive)
+                while (cc < mall * (int64_t)maxcol) cc <<= 1;
+            if (mall > INT32_MAX / SPAI_LD || cc > INT32_MAX) { rc = SPAI_ERR_UNSUPPORTED; goto done; }
+            const int mcap = (int)mall, ccap = (int)cc;
+            const size_t per = o->uf == SPAI_DOUBLE ? big_slab_bytes<double>(mcap, maxrow, ccap)
+                                                    : big_slab_bytes<float>(mcap, maxrow, ccap);
+            // one slab per CTA; at most two CTAs per SM, and at most 4 GiB of slabs
+            int grid = (int)std::min<int64_t>(nbig, 2 * (int64_t)num_sms);
+            while (grid > 1 && (size_t)grid * per > ((size_t)4 << 30)) grid = (grid + 1) / 2;
+            TRY(dev_alloc((void**)&slab, (size_t)grid * per, s));
+            if (o->uf == SPAI_HALF) TRY(launch_spai_big_half(a, o->adaptive != 0, big, err + 6, grid, slab, per, mcap, ccap, s));
+            else if (o->uf == SPAI_SINGLE) TRY(launch_spai_big_single(a, o->adaptive != 0, big, err + 6, grid, slab, per, mcap, ccap, s));
+            else TRY(launch_spai_big_double(a, o->adaptive != 0, big, err + 6, grid, slab, per, mcap, ccap, s));
+            nl++;
+        }
+        if (cudaEventRecord(ek1, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     }
     // assemble P
     P = new spai_precond_s();
@@ -722,7 +766,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     else if (h_fstat[1] > 0) rc = SPAI_WARN_FILLCAP;
 done:
 #undef TRY
-    dev_free(d, s); dev_free(err, s); dev_free(ccount, s); dev_free(cp, s); dev_free(ri, s);
+    dev_free(d, s); dev_free(err, s); dev_free(big, s); dev_free(slab, s); dev_free(ccount, s); dev_free(cp, s); dev_free(ri, s);
     dev_free(Jidx, s); dev_free(Jcnt, s); dev_free(Icnt, s); dev_free(flags, s); dev_free(nsolve, s);
     dev_free(Praw, s); dev_free(colres, s); dev_free(mval, s); dev_free(bval, s); dev_free(fstat, s);
     cudaEventDestroy(e0);

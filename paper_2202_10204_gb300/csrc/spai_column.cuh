@@ -51,7 +51,6 @@ static_assert(SPAI_HASH * 5 <= SPAI_AUX_BYTES && 32 * SPAI_LDR * 2 <= SPAI_AUX_B
 #define CF_NOCAND 8
 #define CF_SINGULAR 16
 #define CF_NONFINITE 32
-#define CF_TOOBIG 64  // the augmented shadow exceeded the tile: previous solve kept
 
 struct SpaiArgs {
     int64_t n;
@@ -78,6 +77,13 @@ struct SpaiArgs {
     int warp_bytes;
     int ilo, ihi;        // CTA kernel: only columns with ilo < |I_k| <= ihi (from k_pattern); ihi = 0: all
     int* err;
+    // columns for the large-shadow kernel (spai_big.cuh): fixed patterns whose
+    // shadow exceeds the CTA tile (k_pattern), and adaptive columns that outgrew
+    // the warp or CTA kernel's tile or candidate list (those kernels write the
+    // current J_k to Jidx/Jcnt, the step to resume at to nsolve and the flags so
+    // far to flags, then append k)
+    int32_t* big;
+    int* nbig;
 };
 
 __device__ __forceinline__ int bsearch_smem(const int32_t* a, int len, int key)
@@ -140,7 +146,6 @@ struct Tile {
     C* v;           // mm: pivot column / residual
     C* mb;          // 32
     int32_t* J;     // 32
-    int32_t* Jp;    // 32
     int32_t* lcol;  // 32 * rl
     C* lval;        // 32 * rl
     int32_t* lcnt;  // 32
@@ -159,7 +164,7 @@ __host__ __device__ inline size_t tile_bytes(int mm, int rl, int cmax)
     size_t b = align16((size_t)mm * 4);
     b += align16((size_t)mm * SPAI_LD * sizeof(WT));
     b += align16((size_t)mm * sizeof(C));
-    b += align16(32 * sizeof(C)) + 3 * 32 * 4;
+    b += align16(32 * sizeof(C)) + 2 * 32 * 4;
     b += align16((size_t)32 * rl * 4) + align16((size_t)32 * rl * sizeof(C));
     b += align16((size_t)cmax * 4) + align16((size_t)cmax * sizeof(C));
     b += SPAI_AUX_BYTES;
@@ -176,7 +181,6 @@ __device__ inline Tile<C, WT> carve(unsigned char* base, int mm, int rl, int cma
     t.v = (C*)(base + off); off += align16((size_t)mm * sizeof(C));
     t.mb = (C*)(base + off); off += align16(32 * sizeof(C));
     t.J = (int32_t*)(base + off); off += 32 * 4;
-    t.Jp = (int32_t*)(base + off); off += 32 * 4;
     t.lcnt = (int32_t*)(base + off); off += 32 * 4;
     t.lcol = (int32_t*)(base + off); off += align16((size_t)32 * rl * 4);
     t.lval = (C*)(base + off); off += align16((size_t)32 * rl * sizeof(C));
@@ -685,23 +689,27 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
         int nj = a.Jcnt[k];
         if (lane < nj) T.J[lane] = a.Jidx[k * F + lane];
         __syncwarp();
-        int fl = 0, m = 0, ns = 0, nj_prev = nj, m_prev = 0;
+        int fl = 0, m = 0, ns = 0;
+        bool deferred = false;
         C snorm = 0;
+        // the column outgrew this kernel's tile or candidate list: the
+        // large-shadow kernel resumes it at `step` with the pattern in T.J
+        auto defer = [&](int step) {
+            fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
+            if (lane < nj) a.Jidx[k * F + lane] = T.J[lane];
+            if (lane == 0) {
+                a.Jcnt[k] = nj;
+                a.nsolve[k] = step;
+                a.flags[k] = fl;
+                if (a.big) a.big[atomicAdd(a.nbig, 1)] = (int32_t)k;
+                else atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
+            }
+            deferred = true;
+            __syncwarp();
+        };
         for (int step = 0;; step++) {
             m = gather<S, C, WT>(a, T, k, nj, mm);
-            if (m > mm) {
-                fl |= CF_TOOBIG;
-                if (step == 0) {
-                    if (lane == 0) atomicCAS(a.err, 0, SPAI_ERR_UNSUPPORTED);
-                } else {
-                    // the augmented shadow does not fit the tile: keep the previous solve
-                    nj = nj_prev;
-                    m = m_prev;
-                    if (lane < nj) T.J[lane] = T.Jp[lane];
-                    __syncwarp();
-                }
-                break;
-            }
+            if (m > mm) { defer(step); break; }
             if constexpr (std::is_same<S, __half>::value) fl |= qr_solve_reg_half<MM>(T, m, nj);
             else fl |= qr_solve_reg<S, C, MM>(T, m, nj);
             const C s2 = residual<S, C, WT>(T, m, nj);
@@ -732,10 +740,7 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
                     cnt += __popc(bal);
                 }
             }
-            if (cnt > a.cmax) {
-                if (lane == 0) atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
-                cnt = a.cmax;
-            }
+            if (cnt > a.cmax) { defer(step); break; }  // redone from this step's solve
             int len2 = 1;
             while (len2 < cnt) len2 <<= 1;
             for (int t = cnt + lane; t < len2; t += 32) T.cand[t] = INT_MAX;
@@ -772,8 +777,6 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
             for (int t = lane; t < u; t += 32) rs += T.rho[t];
             const C mean = warp_sum(rs) / (C)u;
             // ---- up to min(beta, F - nj) acceptable indices with the smallest rho
-            if (lane < nj) T.Jp[lane] = T.J[lane];
-            __syncwarp();
             const int room = F - nj;
             const int want = a.beta < room ? a.beta : room;
             int nadd = 0;
@@ -805,11 +808,10 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
                 __syncwarp();
             }
             if (nadd == 0) { fl |= CF_NOCAND; break; }
-            nj_prev = nj;
-            m_prev = m;
             nj += nadd;
             __syncwarp();
         }
+        if (deferred) continue;
         fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
         // ---- outputs: row k of P = mbar_k * d(J_k)
         for (int t = lane; t < F; t += 32) {
@@ -874,3 +876,11 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
 int launch_spai_half(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
 int launch_spai_single(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
 int launch_spai_double(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
+// the large-shadow kernel (spai_big.cuh) over list[0 .. *count), grid CTAs,
+// each with slab_bytes of the slab
+int launch_spai_big_half(const spai::SpaiArgs& a, bool adaptive, const int32_t* list, const int* count, int grid,
+                         unsigned char* slab, size_t slab_bytes, int mcap, int ccap, cudaStream_t s);
+int launch_spai_big_single(const spai::SpaiArgs& a, bool adaptive, const int32_t* list, const int* count, int grid,
+                           unsigned char* slab, size_t slab_bytes, int mcap, int ccap, cudaStream_t s);
+int launch_spai_big_double(const spai::SpaiArgs& a, bool adaptive, const int32_t* list, const int* count, int grid,
+                           unsigned char* slab, size_t slab_bytes, int mcap, int ccap, cudaStream_t s);

@@ -83,7 +83,6 @@ struct CtaTile {
     C* arow;         // 32: the pivot row
     C* mb;           // 32
     int32_t* J;      // 32
-    int32_t* Jp;     // 32
     int32_t* lcnt;   // 32
     int32_t* tmp;    // 64
     int32_t* lcol;   // 32 * rl
@@ -102,7 +101,7 @@ __host__ __device__ inline size_t cta_tile_bytes(int mm, int nw, int rl, int cma
     b += align16((size_t)mm * sizeof(C));
     b += align16((size_t)nw * 33 * sizeof(C));
     b += align16(32 * sizeof(C)) * 2;
-    b += 3 * 32 * 4 + 64 * 4;
+    b += 2 * 32 * 4 + 64 * 4;
     b += align16((size_t)32 * rl * 4) + align16((size_t)32 * rl * sizeof(C));
     b += align16((size_t)cmax * 4) + align16((size_t)cmax * sizeof(C));
     b += align16(33 * sizeof(C)) + 8 * 4;
@@ -121,7 +120,6 @@ __device__ inline CtaTile<C> cta_carve(unsigned char* base, int mm, int nw, int 
     t.arow = (C*)(base + off); off += align16(32 * sizeof(C));
     t.mb = (C*)(base + off); off += align16(32 * sizeof(C));
     t.J = (int32_t*)(base + off); off += 32 * 4;
-    t.Jp = (int32_t*)(base + off); off += 32 * 4;
     t.lcnt = (int32_t*)(base + off); off += 32 * 4;
     t.tmp = (int32_t*)(base + off); off += 64 * 4;
     t.lcol = (int32_t*)(base + off); off += align16((size_t)32 * rl * 4);
@@ -175,8 +173,23 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
         int nj = sc[0];
         if (tid < nj) T.J[tid] = a.Jidx[k * F + tid];
         __syncthreads();
-        int m = 0, ns = 0, nj_prev = nj, m_prev = 0, fl = 0;
+        int m = 0, ns = 0, fl = 0;
+        bool deferred = false;
         C snorm = 0;
+        // the column outgrew the tile or the candidate list: the large-shadow
+        // kernel resumes it at `step` with the pattern in T.J
+        auto defer = [&](int step) {
+            if (tid < nj) a.Jidx[k * F + tid] = T.J[tid];
+            if (tid == 0) {
+                a.Jcnt[k] = nj;
+                a.nsolve[k] = step;
+                a.flags[k] = fl | sc[2];
+                if (a.big) a.big[atomicAdd(a.nbig, 1)] = (int32_t)k;
+                else atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
+            }
+            deferred = true;
+            __syncthreads();
+        };
         for (int step = 0;; step++) {
             // ---- gather (warp 0)
             if (wid == 0) {
@@ -185,18 +198,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
             }
             __syncthreads();
             m = sc[1];
-            if (m > MM) {
-                fl |= CF_TOOBIG;
-                if (step == 0) {
-                    if (tid == 0) atomicCAS(a.err, 0, SPAI_ERR_UNSUPPORTED);
-                } else {
-                    nj = nj_prev;
-                    m = m_prev;
-                    if (tid < nj) T.J[tid] = T.Jp[tid];
-                }
-                __syncthreads();
-                break;
-            }
+            if (m > MM) { defer(step); break; }
             // ---- Householder QR, tile in registers: warp w rows [32w, 32w+32), lane t column t.
             // Warps whose rows all lie beyond |I_k| hold zeros: they skip the
             // arithmetic and only take part in the barriers.
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
             }
             int total = 0;
             const int off = block_excl_scan(cntp, T.tmp, &total);
-            if (total > a.cmax && tid == 0) atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
+            if (total > a.cmax) { defer(step); break; }  // redone from this step's solve
             for (int q = 0; q < cntp; q++) {
                 if (off + q >= a.cmax) break;
                 const int j = a.ri[a.cp[l] + q];
@@ -354,7 +356,6 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
             for (int t = tid; t < u; t += BT) rs += T.rho[t];
             const C mean = block_sum_det(rs, T.red) / (C)u;
             // ---- up to min(beta, F - nj) acceptable indices with the smallest rho
-            if (tid < nj) T.Jp[tid] = T.J[tid];
             const int room = F - nj;
             const int want = a.beta < room ? a.beta : room;
             if (tid == 0) sc[3] = 0;
@@ -403,10 +404,9 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
             const int nadd = sc[3];
             __syncthreads();
             if (nadd == 0) { fl |= CF_NOCAND; break; }
-            nj_prev = nj;
-            m_prev = m;
             nj += nadd;
         }
+        if (deferred) continue;
         fl |= sc[2];
         // ---- outputs: row k of P = mbar_k * d(J_k)
         for (int t = tid; t < F; t += BT) {

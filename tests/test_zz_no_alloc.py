@@ -1,16 +1,18 @@
 """The allocation-free refinement entry point (gmres_ir_solve_noalloc).
 
-Some callers cannot call the CUDA allocator: work being recorded into a
-CUDA graph, real-time or embedded runtimes that forbid allocation after
-start-up, and hosts that hand the library an exact memory budget.  For them
-the library offers gmres_ir_solve_noalloc, which keeps all its scratch in
-one fixed device array.  This test calls it through the C ABI twice in a
-row and checks each result against the allocating entry point
-(gmres_ir_solve with the same preconditioner), with the tolerance the other
-GPU tests use for refinement results (same step count, GMRES iterations
-within 10%, solution within 10 u of the reference relative to its norm).
-It lives in its own file, collected last, and runs alone or after the
-other tests.
+Some callers must not call the CUDA allocator: real-time loops, where
+cudaMalloc and cudaFree have no latency bound (and cudaFree synchronises the
+device); hosts that give all device memory to their own pool at start-up;
+runtimes that forbid allocation once running.  For them the library offers
+gmres_ir_solve_noalloc, which keeps all its scratch in one fixed device
+array.  These tests call it through the C ABI twice in a row and check each
+result against the allocating entry point (gmres_ir_solve with the same
+preconditioner), with the tolerance the other GPU tests use for refinement
+results (same step count, GMRES iterations within 10%, solution within 10 u
+of the reference relative to its norm), for left and right preconditioning,
+no preconditioner, and both Gram-Schmidt variants; and they check that the
+calls leave the device's free memory and torch's allocations unchanged.
+The file is collected last, and its tests pass alone or after the others.
 """
 import numpy as np
 import pytest
@@ -31,36 +33,57 @@ def to_dev(A):
     return tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in A)
 
 
-@pytest.mark.parametrize("case", ["3d-half-single", "2d-single-double-quad"])
+CASES = {
+    "3d-half-single": dict(side=0, orth=0, precond=True),
+    "2d-single-double-quad": dict(side=0, orth=0, precond=True),
+    "2d-unpreconditioned": dict(side=0, orth=0, precond=False),
+    "2d-right": dict(side=1, orth=0, precond=True),
+    "3d-cgs2": dict(side=0, orth=1, precond=True),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
 def test_noalloc_matches_allocating_entry_point(case):
-    if case == "3d-half-single":
+    c = CASES[case]
+    if case.startswith("3d"):
         A, b, _ = synth.cfg_large_3d(N=16)
-        so = S.make_spai_opts(init=2, max_fill=25, uf="half")
-        io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4)
+        so = S.make_spai_opts(init=2, max_fill=25, uf="half", side=c["side"])
+        io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4,
+                            side=c["side"], orth=c["orth"])
         u = 2.0 ** -24
     else:
         A, b, _ = synth.cfg_small_2d()
-        so = S.make_spai_opts(init=1, max_fill=30, uf="single")
-        io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4)
+        so = S.make_spai_opts(init=1, max_fill=30, uf="single", side=c["side"])
+        io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-4,
+                            side=c["side"], orth=c["orth"])
         u = 2.0 ** -53
-    ctx = S.Context(0, stream=torch.cuda.current_stream())
-    P, _ = S.spai_build(ctx, A, so)
-    Pcsr = P.export()
-    Ad, bd, Pd = to_dev(A), torch.from_numpy(b).cuda(), to_dev(Pcsr)
+    stream = torch.cuda.current_stream()
+    ctx = S.Context(0, stream=stream)
+    P = Pd = None
+    if c["precond"]:
+        P, _ = S.spai_build(ctx, A, so)
+        Pd = to_dev(P.export())
+    Ad, bd = to_dev(A), torch.from_numpy(b).cuda()
     x_ref = torch.zeros_like(bd)
     ref = S.gmres_ir_solve(ctx, Ad, bd, x_ref, P=P, opts=io)
     torch.cuda.synchronize()
     xr = x_ref.cpu().numpy()
+    # a first call outside the checks below, so that every kernel it launches is loaded
+    _lib.gmres_ir_solve_noalloc(Ad, bd, torch.zeros_like(bd), P=Pd, opts=io, stream=stream)
+    outs = [torch.full_like(bd, float("nan")) for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):
-        x = torch.full_like(bd, float("nan"))
-        st = _lib.gmres_ir_solve_noalloc(Ad, bd, x, P=Pd, opts=io, stream=torch.cuda.current_stream())
+        free0, torch0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        st = _lib.gmres_ir_solve_noalloc(Ad, bd, outs[call], P=Pd, opts=io, stream=stream)
         torch.cuda.synchronize()
-        xn = x.cpu().numpy()
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == torch0, call
+        xn = outs[call].cpu().numpy()
         assert st["steps"] == ref["steps"], (call, st["its"], ref["its"])
         assert abs(st["total_its"] - ref["total_its"]) <= max(1, 0.1 * ref["total_its"])
         assert np.all(np.isfinite(xn))
         assert np.max(np.abs(xn - xr)) <= 10 * u * np.max(np.abs(xr)), call
-    P.free()
+    if P is not None:
+        P.free()
     ctx.close()
 
 
@@ -73,3 +96,19 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     with pytest.raises(S.SpaiError) as e:
         _lib.gmres_ir_solve_noalloc(Ad, bd, torch.zeros_like(bd), P=None, opts=io)
     assert e.value.code == _lib.ERR_UNSUPPORTED
+
+
+def test_noalloc_checks_its_device_inputs():
+    # the device CSRs are checked before any kernel indexes with them
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="double", tau=1e-8)
+    b = torch.ones(3, dtype=torch.float64, device="cuda")
+    bad = [
+        ((0, 1, 2, 3), (0, 3, 2), _lib.ERR_INVALID_ARG),  # a column outside [0, n)
+        ((0, 2, 1, 3), (0, 1, 2), _lib.ERR_INVALID_ARG),  # a decreasing rowptr
+        ((0, 1, 1, 2), (0, 2), _lib.ERR_ZERO_ROW),        # an empty row
+    ]
+    for rp, ci, code in bad:
+        A = to_dev((np.array(rp, dtype=np.int64), np.array(ci, dtype=np.int32), np.ones(len(ci))))
+        with pytest.raises(S.SpaiError) as e:
+            _lib.gmres_ir_solve_noalloc(A, b, torch.zeros_like(b), P=None, opts=io)
+        assert e.value.code == code
