@@ -251,7 +251,7 @@ def residual(A, b, x, ur="double", u="double"):
     return r
 
 
-ORTH_MGS, ORTH_CGS2 = 0, 1
+ORTH_MGS, ORTH_CGS2, ORTH_MGS_ICWY = 0, 1, 2
 SIDE_LEFT, SIDE_RIGHT = 0, 1
 
 

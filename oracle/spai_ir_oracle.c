@@ -46,8 +46,12 @@
  *   R6  |J_k| <= max_fill; an initial pattern larger than the cap keeps k,
  *       then the indices nearest to k (ties: smaller index).
  *   R7  MGS-GMRES, x0 = 0, no restart, stop when |g_{j+1}| / beta <= tau;
- *       Givens rotations, H, g and y in double.  Option: classical
- *       Gram-Schmidt applied twice (CGS2) instead of MGS.
+ *       Givens rotations, H, g and y in double.  Options: classical
+ *       Gram-Schmidt applied twice (CGS2) instead of MGS; and MGS in its
+ *       inverse compact WY form with one reduction per iteration and lagged
+ *       normalisation (Swirydowicz, Langou, Ananthan, Yang and Thomas, "Low
+ *       synchronization Gram-Schmidt and GMRES algorithms", 2020), which
+ *       equals MGS in exact arithmetic; see orc_gmres.
  *   R8  IR stop (the paper fixes only i_max), checked before step i in this
  *       order: BACKWARD rule: nbe_i = ||r_i||_inf / (||A||_inf ||x_i||_inf
  *       + ||b||_inf) <= stop_tol; CORRECTION rule: i >= 1 and
@@ -559,7 +563,8 @@ typedef struct {
     double tau;      /* relative tolerance on the preconditioned residual */
     int maxit;       /* iteration cap */
     int orth;        /* 0: modified Gram-Schmidt (the paper's MGS-GMRES);
-                        1: classical Gram-Schmidt applied twice (CGS2) */
+                        1: classical Gram-Schmidt applied twice (CGS2);
+                        2: MGS with one reduction per iteration (ICWY form) */
     int side;        /* 0: left preconditioning (Algorithm 3);
                         1: right preconditioning, the variant the paper leaves
                         as future work at the end of Section 3 */
@@ -573,10 +578,175 @@ typedef struct {
  * in u_g precision values.  Returns the number of iterations; *breakdown is
  * set when h_{j+1,j} = 0.  relres receives |g_k| / beta (or 0).
  */
+/* The Arnoldi product w = fl_ug(P (A v)) (left) or fl_ug(A (P v)) (right),
+ * each product in u_p; P = NULL: w = fl_ug(A v).  t: scratch. */
+static void arnoldi_product(int n, const int64_t* arp, const int* aci, const double* av, const int64_t* prp,
+                            const int* pci, const double* pv, int right, int up, int ug, const double* v,
+                            double* t, double* w)
+{
+    if (right && prp) {
+        spmv_p(n, prp, pci, pv, v, up, MODE_PEROP, t);
+        spmv_p(n, arp, aci, av, t, up, MODE_PEROP, w);
+    } else {
+        spmv_p(n, arp, aci, av, v, up, MODE_PEROP, t);
+        if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
+        else for (int i = 0; i < n; i++) w[i] = t[i];
+    }
+    for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
+}
+
+/*
+ * One step of MGS in inverse compact WY form with lagged normalisation
+ * (orth = 2).  With Q_j = [q_0 .. q_{j-1}] and the not yet normalised
+ * u_j, one set of inner products gives everything iteration j needs:
+ *   a = Q_j^T u_j,  nu = u_j^T u_j,  c = Q_j^T w,  delta = u_j^T w,
+ * where w = op(u_j) is the Arnoldi product of u_j.  Then r = sqrt(nu) is
+ * h_{j,j-1} (the subdiagonal of the previous column), q_j = u_j / r, row j
+ * of the strictly lower triangular L = (q_i^T q_k)_{i>k} is a / r, and
+ * b = Q_{j+1}^T (w / r) = [c / r ; delta / r^2].  The MGS coefficients of
+ * column j are h = (I + L)^{-1} b (forward substitution: h_i = b_i -
+ * sum_{k<i} l_ik h_k, which is what projecting against q_0, q_1, ... one
+ * after another gives), and u_{j+1} = w / r - Q_{j+1} h.  In exact
+ * arithmetic L = 0 and h, u_{j+1} are those of MGS.  Every inner product,
+ * quotient and update is rounded to u_g; the subtractions of the update and
+ * of the substitution run in index order, as in MGS.
+ *   V: the basis (V[i] = q_i, allocated here for i <= j); U: u_j on entry,
+ *   u_{j+1} on return; W: w; L: row i at L + i * ldl; h: the coefficients.
+ * Returns r.  For j = 0 there is no previous column and no L row.
+ */
+static double icwy_step(int n, int j, double** V, double* U, const double* W, double* L, int ldl, double* a,
+                        double* c, double* h, int ug, int with_product, double* rnorm_only)
+{
+    double nu = dot_p(U, 1, U, 1, n, ug, MODE_PEROP);
+    double r = rnd(sqrt(nu), ug);
+    if (rnorm_only || !with_product) {
+        if (rnorm_only) *rnorm_only = r;
+        return r;
+    }
+    for (int i = 0; i < j; i++) {
+        a[i] = dot_p(V[i], 1, U, 1, n, ug, MODE_PEROP);
+        c[i] = dot_p(V[i], 1, W, 1, n, ug, MODE_PEROP);
+    }
+    double delta = dot_p(U, 1, W, 1, n, ug, MODE_PEROP);
+    if (r == 0.0) return r;
+    if (!V[j]) V[j] = (double*)malloc(sizeof(double) * (size_t)n);
+    for (int q = 0; q < n; q++) V[j][q] = rnd(U[q] / r, ug);
+    double* Lj = L + (size_t)j * ldl;
+    for (int i = 0; i < j; i++) Lj[i] = rnd(a[i] / r, ug);
+    for (int i = 0; i < j; i++) h[i] = rnd(c[i] / r, ug);
+    h[j] = rnd(rnd(delta / r, ug) / r, ug);
+    for (int i = 0; i <= j; i++) {
+        const double* Li = L + (size_t)i * ldl;
+        double acc = h[i];
+        for (int k = 0; k < i; k++) acc = rnd(acc - rnd(Li[k] * h[k], ug), ug);
+        h[i] = acc;
+    }
+    for (int q = 0; q < n; q++) {
+        double acc = rnd(W[q] / r, ug);
+        for (int i = 0; i <= j; i++) acc = rnd(acc - rnd(h[i] * V[i][q], ug), ug);
+        U[q] = acc;
+    }
+    return r;
+}
+
+/* Apply the rotations 0..j-2 to column j-1 (h[0..j-1], h[j] its subdiagonal),
+ * form rotation j-1 and update g; H receives the rotated column. */
+static void givens_column(int j, double* h, double* cs, double* sn, double* g, double* H, int K)
+{
+    const int c = j - 1;
+    for (int i = 0; i < c; i++) {
+        double tmp = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = tmp;
+    }
+    double den = sqrt(h[c] * h[c] + h[c + 1] * h[c + 1]);
+    if (den == 0.0) { cs[c] = 1.0; sn[c] = 0.0; }
+    else { cs[c] = h[c] / den; sn[c] = h[c + 1] / den; }
+    h[c] = den;
+    h[c + 1] = 0.0;
+    g[c + 1] = -sn[c] * g[c];
+    g[c] = cs[c] * g[c];
+    for (int i = 0; i <= c; i++) H[(size_t)i * K + c] = h[i];
+}
+
+/* GMRES with the one-reduction MGS (orth = 2); arguments as orc_gmres. */
+static int gmres_icwy(int n, const int64_t* arp, const int* aci, const double* av, const int64_t* prp,
+                      const int* pci, const double* pv, const double* r, const orc_gmres_opts* o, double* d,
+                      int* breakdown, double* relres)
+{
+    int ug = o->ug, up = o->up, K = o->maxit;
+    const int right = o->side == 1;
+    double* t = (double*)malloc(sizeof(double) * (size_t)n);
+    double* U = (double*)malloc(sizeof(double) * (size_t)n);
+    double* W = (double*)malloc(sizeof(double) * (size_t)n);
+    double** V = (double**)calloc((size_t)K + 2, sizeof(double*));
+    double* L = (double*)calloc((size_t)(K + 1) * (K + 1), sizeof(double));
+    double* H = (double*)calloc((size_t)(K + 1) * (K + 1), sizeof(double));
+    double* a = (double*)calloc((size_t)K + 2, sizeof(double));
+    double* c = (double*)calloc((size_t)K + 2, sizeof(double));
+    double* h = (double*)calloc((size_t)K + 2, sizeof(double));
+    double* col = (double*)calloc((size_t)K + 2, sizeof(double));
+    double* cs = (double*)calloc((size_t)K + 1, sizeof(double));
+    double* sn = (double*)calloc((size_t)K + 1, sizeof(double));
+    double* g = (double*)calloc((size_t)K + 2, sizeof(double));
+    *breakdown = 0;
+    *relres = 0.0;
+    for (int i = 0; i < n; i++) d[i] = 0.0;
+    /* u_0 = P r (left) or r (right), in u_p then u_g; beta = ||u_0|| comes
+     * from the first reduction */
+    if (prp && !right) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, U);
+    else for (int i = 0; i < n; i++) U[i] = rnd(r[i], up);
+    for (int i = 0; i < n; i++) U[i] = rnd(U[i], ug);
+    double beta = 0.0;
+    int k = 0;
+    for (int j = 0; K > 0; j++) {
+        const int prod = j < K;
+        if (prod) arnoldi_product(n, arp, aci, av, prp, pci, pv, right, up, ug, U, t, W);
+        double rn = 0.0;
+        /* the last pass (j = K) only needs ||u_K|| */
+        double rj = icwy_step(n, j, V, U, W, L, K + 1, a, c, h, ug, prod, prod ? NULL : &rn);
+        if (j == 0) {
+            beta = rj;
+            g[0] = beta;
+            if (beta == 0.0) break;
+        } else {
+            col[j] = rj; /* h_{j,j-1} completes column j-1 */
+            givens_column(j, col, cs, sn, g, H, K + 1);
+            k = j;
+            *relres = fabs(g[j]) / beta;
+            if (rj == 0.0) { *breakdown = 1; break; }
+            if (*relres <= o->tau) break;
+        }
+        if (!prod) break;
+        for (int i = 0; i <= j; i++) col[i] = h[i]; /* column j above its subdiagonal */
+    }
+    /* y = R^{-1} g(0:k) in double, d = V_k y in u_g */
+    double* y = (double*)calloc((size_t)k + 1, sizeof(double));
+    for (int i = k - 1; i >= 0; i--) {
+        double acc = g[i];
+        for (int l = i + 1; l < k; l++) acc -= H[(size_t)i * (K + 1) + l] * y[l];
+        y[i] = H[(size_t)i * (K + 1) + i] != 0.0 ? acc / H[(size_t)i * (K + 1) + i] : 0.0;
+    }
+    for (int q = 0; q < n; q++) {
+        double acc = 0.0;
+        for (int i = 0; i < k; i++) acc = rnd(acc + rnd(V[i][q] * rnd(y[i], ug), ug), ug);
+        d[q] = acc;
+    }
+    if (right && prp) {
+        spmv_p(n, prp, pci, pv, d, up, MODE_PEROP, t);
+        for (int q = 0; q < n; q++) d[q] = rnd(t[q], ug);
+    }
+    for (int i = 0; i <= K + 1; i++) free(V[i]);
+    free(V); free(y); free(t); free(U); free(W); free(L); free(H); free(a); free(c); free(h); free(col);
+    free(cs); free(sn); free(g);
+    return k;
+}
+
 int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
               const int64_t* prp, const int* pci, const double* pv,
               const double* r, const orc_gmres_opts* o, double* d, int* breakdown, double* relres)
 {
+    if (o->orth == 2) return gmres_icwy(n, arp, aci, av, prp, pci, pv, r, o, d, breakdown, relres);
     int ug = o->ug, up = o->up, K = o->maxit;
     double* t = (double*)malloc(sizeof(double) * (size_t)n);
     double* w = (double*)malloc(sizeof(double) * (size_t)n);
@@ -796,6 +966,41 @@ int orc_arnoldi(int n, const int64_t* arp, const int* aci, const double* av,
                 const int64_t* prp, const int* pci, const double* pv,
                 const double* r, int ug, int up, int orth, int k, double* Vout, double* Hout)
 {
+    if (orth == 2) {
+        /* one-reduction MGS: k + 1 passes, the last only for ||u_k|| */
+        double* t = (double*)malloc(sizeof(double) * (size_t)n);
+        double* U = (double*)malloc(sizeof(double) * (size_t)n);
+        double* W = (double*)malloc(sizeof(double) * (size_t)n);
+        double** V = (double**)calloc((size_t)k + 2, sizeof(double*));
+        double* L = (double*)calloc((size_t)(k + 1) * (k + 1), sizeof(double));
+        double* a = (double*)calloc((size_t)k + 2, sizeof(double));
+        double* c = (double*)calloc((size_t)k + 2, sizeof(double));
+        double* h = (double*)calloc((size_t)k + 2, sizeof(double));
+        if (prp) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, U);
+        else for (int i = 0; i < n; i++) U[i] = rnd(r[i], up);
+        for (int i = 0; i < n; i++) U[i] = rnd(U[i], ug);
+        for (int z = 0; z < (k + 1) * k; z++) Hout[z] = 0.0;
+        int cols = 0;
+        for (int j = 0; j <= k; j++) {
+            const int prod = j < k;
+            if (prod) arnoldi_product(n, arp, aci, av, prp, pci, pv, 0, up, ug, U, t, W);
+            double rn = 0.0;
+            double rj = icwy_step(n, j, V, U, W, L, k + 1, a, c, h, ug, prod, prod ? NULL : &rn);
+            if (j > 0) Hout[(size_t)(j - 1) * (k + 1) + j] = rj;
+            if (rj == 0.0) break;
+            if (!prod) {
+                V[j] = (double*)malloc(sizeof(double) * (size_t)n);
+                for (int q = 0; q < n; q++) V[j][q] = rnd(U[q] / rj, ug);
+            }
+            for (int q = 0; q < n; q++) Vout[(size_t)j * n + q] = V[j][q];
+            cols = j + 1;
+            if (!prod) break;
+            for (int i = 0; i <= j; i++) Hout[(size_t)j * (k + 1) + i] = h[i];
+        }
+        for (int i = 0; i <= k + 1; i++) free(V[i]);
+        free(V); free(t); free(U); free(W); free(L); free(a); free(c); free(h);
+        return cols;
+    }
     double* t = (double*)malloc(sizeof(double) * (size_t)n);
     double* w = (double*)malloc(sizeof(double) * (size_t)n);
     double* c = (double*)malloc(sizeof(double) * (size_t)(k + 2));

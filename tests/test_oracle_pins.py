@@ -532,7 +532,7 @@ def test_gmres_single_precision_converges_to_tau():
 # ---------------------------------------------------------------- Gram-Schmidt variants
 
 
-@pytest.mark.parametrize("orth", [O.ORTH_MGS, O.ORTH_CGS2])
+@pytest.mark.parametrize("orth", [O.ORTH_MGS, O.ORTH_CGS2, O.ORTH_MGS_ICWY])
 def test_arnoldi_matches_krylov_qr(orth):
     # Arnoldi builds an orthonormal basis of the Krylov space K_k(A, r) with
     # A V_k = V_{k+1} H; compare with numpy's QR of the explicit Krylov matrix
@@ -561,6 +561,60 @@ def test_cgs2_keeps_orthogonality_in_single():
     em = np.linalg.norm(Vm.T @ Vm - np.eye(Vm.shape[1]))
     assert e2 <= 100 * 2.0 ** -24 * np.sqrt(V2.shape[1])
     assert e2 <= em
+
+
+def test_icwy_mgs_equals_mgs_in_double():
+    # the one-reduction form of MGS (inverse compact WY, lagged normalisation) is
+    # MGS in exact arithmetic: on well-conditioned Krylov bases in double the two
+    # agree to rounding, column by column and coefficient by coefficient
+    rng = np.random.default_rng(5)
+    Ad = rng.normal(size=(40, 40)) + 8 * np.eye(40)
+    r = rng.normal(size=40)
+    Vm, Hm = O.arnoldi(dense_to_csr(Ad), r, None, k=20, orth=O.ORTH_MGS)
+    Vi, Hi = O.arnoldi(dense_to_csr(Ad), r, None, k=20, orth=O.ORTH_MGS_ICWY)
+    assert Vi.shape == Vm.shape
+    np.testing.assert_allclose(Vi, Vm, atol=1e-13)
+    np.testing.assert_allclose(Hi, Hm, atol=1e-12)
+    # with the SPAI preconditioner on the 2D system (P A well conditioned)
+    A, b, x = synth.cfg_small_2d()
+    P = O.assemble_P(O.spai(A, init=O.PAT_A, uf="double", max_fill=30), "double", "double")
+    Pc = (P[0], P[1], P[2])
+    Vm, Hm = O.arnoldi(A, b, Pc, k=20, orth=O.ORTH_MGS)
+    Vi, Hi = O.arnoldi(A, b, Pc, k=20, orth=O.ORTH_MGS_ICWY)
+    np.testing.assert_allclose(Vi, Vm, atol=1e-12)
+    np.testing.assert_allclose(Hi, Hm, atol=1e-12 * np.max(np.abs(Hm)))
+
+
+def test_icwy_mgs_loses_orthogonality_like_mgs_in_single():
+    # MGS-like stability: in single precision the basis of the one-reduction form
+    # loses orthogonality as MGS's does (~ u cond), not more; CGS2 keeps O(u)
+    A = synth.random_sparse(800, 8, seed=3, log10_scale=4.0)
+    r = np.random.default_rng(3).normal(size=800)
+    e = {}
+    for orth in (O.ORTH_MGS, O.ORTH_CGS2, O.ORTH_MGS_ICWY):
+        V, _ = O.arnoldi(A, r, None, k=120, ug="single", up="single", orth=orth)
+        assert V.shape[1] == 121
+        e[orth] = np.linalg.norm(V.T @ V - np.eye(121))
+    assert e[O.ORTH_MGS_ICWY] <= 4 * e[O.ORTH_MGS]
+    assert e[O.ORTH_CGS2] < e[O.ORTH_MGS]
+
+
+def test_gmres_ir_icwy_matches_mgs_solution():
+    A, b, x_true = synth.cfg_small_2d()
+    S = O.spai(A, init=O.PAT_A, uf="single", max_fill=30)
+    P = O.assemble_P(S, "double", "single")
+    Rm = O.gmres_ir(A, b, P, tau=1e-4, orth=O.ORTH_MGS)
+    Ri = O.gmres_ir(A, b, P, tau=1e-4, orth=O.ORTH_MGS_ICWY)
+    assert Ri["status"] & O.IR_CONVERGED
+    assert Ri["steps"] == Rm["steps"] and abs(Ri["total_its"] - Rm["total_its"]) <= 1
+    assert np.max(np.abs(Ri["x"] - Rm["x"])) <= 4 * 2.0 ** -53 * np.max(np.abs(Rm["x"]))
+    # right preconditioning and single-precision Krylov vectors as well
+    _, Pr = O.spai_right(A, up="single", uf="single", init=O.PAT_A, max_fill=30)
+    kw = dict(uf="single", u="double", ug="single", up="single", ur="quad", tau=1e-4, side=O.SIDE_RIGHT)
+    Rm = O.gmres_ir(A, b, Pr, orth=O.ORTH_MGS, **kw)
+    Ri = O.gmres_ir(A, b, Pr, orth=O.ORTH_MGS_ICWY, **kw)
+    assert Ri["status"] & O.IR_CONVERGED and Ri["steps"] == Rm["steps"]
+    assert abs(Ri["total_its"] - Rm["total_its"]) <= max(1, 0.1 * Rm["total_its"])
 
 
 def test_gmres_ir_cgs2_matches_mgs_solution():
