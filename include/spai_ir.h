@@ -122,9 +122,14 @@ typedef struct {
     double stop_tol;             /* <= 0: q*u (BACKWARD, q the largest row nonzero count of A,
                                     the limit of Theorem 2) or u (CORRECTION)          */
     int orth;                    /* Arnoldi orthogonalisation: 0 modified Gram-Schmidt (the
-                                    paper's MGS-GMRES), 1 classical Gram-Schmidt applied
-                                    twice (CGS2: two vector reductions per iteration instead
-                                    of j+1 scalar ones) */
+                                    paper's MGS-GMRES, j+1 scalar reductions in iteration j);
+                                    1 classical Gram-Schmidt applied twice (CGS2: two vector
+                                    reductions per iteration); 2 MGS in its inverse compact WY
+                                    form with lagged normalisation (Swirydowicz, Langou,
+                                    Ananthan, Yang and Thomas, "Low synchronization
+                                    Gram-Schmidt and GMRES algorithms", 2020): one vector
+                                    reduction per iteration, MGS in exact arithmetic and
+                                    MGS-like loss of orthogonality */
     int side;                    /* 0: left preconditioning (Algorithm 3: GMRES on P A d = P r,
                                     tau bounds ||P(r - A d)||/||P r||); 1: right preconditioning
                                     (GMRES on A P u = r, d = P u, tau bounds ||r - A d||/||r||;

@@ -156,7 +156,8 @@ def make_spai_opts(init=PAT_A, adaptive=False, eps=0.5, alpha=-1, beta=8, max_fi
 
 def make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8, gmres_max_it=0,
                  ir_max_steps=10, stop=IR_STOP_BACKWARD, stop_tol=0.0, orth=0, side=SIDE_LEFT):
-    """orth: 0 modified Gram-Schmidt (default, the paper's), 1 classical Gram-Schmidt twice.
+    """orth: 0 modified Gram-Schmidt (default, the paper's), 1 classical Gram-Schmidt twice, 2 MGS with one
+    reduction per iteration (inverse compact WY form, lagged normalisation).
     side: SIDE_LEFT (Algorithm 3) or SIDE_RIGHT (GMRES on A P u = r, d = P u).
     stop: IR_STOP_BACKWARD, IR_STOP_FIXED or IR_STOP_CORRECTION (stop_tol <= 0: the default threshold)."""
     return ir_opts(_prec(uf), _prec(u), _prec(ug), _prec(up), _prec(ur), float(tau), int(gmres_max_it),

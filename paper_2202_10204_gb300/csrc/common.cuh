@@ -168,9 +168,17 @@ struct GridBarrier {
     unsigned nblocks;  // blocks taking part (the grid, or one system's blocks of a batch)
 };
 
+struct NoBarrierWork {
+    __device__ void operator()() const {}
+};
+
 // `epoch` is a per-block counter kept in shared memory by the caller and
-// advanced identically by every block.
-__device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch, int* s_flag)
+// advanced identically by every block.  `work` runs on thread 0 after the
+// block has arrived and before it starts waiting for the others (short
+// serial work hides in the wait); the wait's clock budget starts after it.
+template <class Work = NoBarrierWork>
+__device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch, int* s_flag,
+                                          const Work& work = Work())
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -179,6 +187,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& gb, unsigned* epoch
         const unsigned target = e * gb.nblocks;
         // release: the bar.sync above orders the block's writes before it
         red_release_add_u32(gb.count, 1u);
+        work();
         int ok = 1;
         const long long t0 = clock64();
         unsigned spins = 0;

@@ -31,813 +31,11 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "ir_kernel.cuh"
 
 using namespace spai;
 
 namespace {
-
-constexpr int IR_THREADS = 1024;
-constexpr int KMAX_LIMIT = 1024;
-constexpr int MAX_GRID = 160;   // exchange slots are polled by one warp, SPL slots per lane
-constexpr int SPL = (MAX_GRID + 31) / 32;
-constexpr int SLOT_WORDS = 16;  // one 128-byte line per block and parity (up to 4 words used)
-constexpr int PF = 4;           // rows per thread whose next basis entries are prefetched
-constexpr int MGS_GROUP_MIN_GRID = 64;  // grids from this size run the Gram-Schmidt rounds in a group
-
-// SELL-32: rows in slices of 32; slice s stores its entries column-major
-// (entry c of row 32s+l at off[s] + 32c + l), padded to the slice's longest
-// row with (col = own row, val = 0).  Loads of one entry slot by a warp are
-// one contiguous 128-byte line.
-struct Sell {
-    const int64_t* off;  // nslices + 1 element offsets
-    const int32_t* col;
-    const void* val;     // precision u_p
-};
-
-struct IrArgs {
-    int64_t n;
-    int64_t rb;                 // rows per block (multiple of 32)
-    Sell A, P;                  // P.off == nullptr: P = I
-    const int64_t* arp;         // A in CSR, float64 (residual)
-    const int32_t* aci;
-    const double* aval;
-    const double* b;
-    void* x;                    // n, precision u
-    void* r;                    // n, precision u
-    void* wbuf;                 // n, precision u_g: published w (or z)
-    void* tbuf;                 // n, precision u_p: t = A v
-    void* V;                    // ldv x (kmax + 1), precision u_g; a block reads back only its own rows
-    int64_t ldv;
-    double* R;                  // (kmax + 1) x kmax column-major, written by block 0
-    unsigned long long* msg;    // [2 parities][gridDim.x][SLOT_WORDS] epoch-tagged words
-    unsigned long long* msg2;   // the same for the Gram-Schmidt group's rounds
-    int g2;                     // Gram-Schmidt group: blocks 0..g2-1, each over the rows of two
-                                // blocks (0: every block runs the rounds on its own rows)
-    int* err;
-    long long limit;            // clock64 cycles a wait may take
-    double anorm, bnorm, tau, stop_tol;
-    int kmax, imax, stop_rule;
-    int* its;                   // imax
-    double* nbe;                // imax + 1
-    int* out;                   // [0] steps, [1] flags
-    int orth;                   // 0 modified Gram-Schmidt, 1 classical Gram-Schmidt twice (CGS2)
-    int side;                   // 0 left preconditioning (P A d = P r), 1 right (A P u = r, d = P u)
-    int G;                      // blocks of this system
-    int block0;                 // its first block in a batched launch (0 alone)
-    void* pvec;                 // CGS2: 2 parities x gridDim.x x (kmax + 1) partial dot products (u_g)
-    unsigned* gcount;           // CGS2: counter of the barrier that publishes them (zeroed)
-};
-
-struct IrShared {
-    int bid;          // the block's rank within its system
-    int G;            // the system's block count
-    unsigned epoch;
-    unsigned epoch2;  // rounds of the Gram-Schmidt group
-    unsigned gepoch;  // CGS2 barrier count
-    int ok;
-    double bcast[3];
-    double resid;
-};
-
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// One exchange round among all blocks of the co-resident grid.  Thread 0
-// publishes NW 32-bit payload words, each tagged with the round's epoch in
-// the upper 32 bits (one single-copy-atomic 64-bit store per word) after a
-// fence that orders everything the block wrote before the preceding
-// __syncthreads.  Each block's slot is a 128-byte line of its own: blocks
-// sharing a line made every round measurably slower (the polls of all blocks
-// and the stores of the line's owners queue on the same L2 line), while more
-// polling warps or a denser layout made it slower still.  Warp 0 then polls every block's words of that epoch (lane
-// l owns blocks l, l+32, ...), feeding them to `acc` in that fixed order,
-// until one pass sees every word carry the epoch; it then fences (acquire)
-// and `acc.finish` combines the lanes and publishes to shared memory.  Slots
-// alternate between two parities, so a block can only overwrite a slot after
-// every block has read it.  The wait is bounded: on expiry SPAI_ERR_TIMEOUT
-// goes to *err and every block leaves.  Must be called by all threads after
-// a __syncthreads that follows the block's writes.
-struct NoWork {
-    __device__ void operator()() const {}
-};
-
-// `work` runs on thread 0 after it has published the block's words and before
-// warp 0 starts polling: the other blocks' words take about a microsecond to
-// arrive, which hides short serial work there.
-template <int NW, bool DATA, class Acc, bool GRP = false, class Work = NoWork>
-__device__ __forceinline__ bool exchange(const IrArgs& a, IrShared* sh, const uint32_t* pay, Acc& acc,
-                                         const Work& work = Work())
-{
-    // GRP: a round of the Gram-Schmidt group (blocks 0..g2-1), with its own
-    // slots and epoch; only the group's blocks may call it
-    const unsigned G = GRP ? (unsigned)a.g2 : (unsigned)sh->G;
-    unsigned* epoch = GRP ? &sh->epoch2 : &sh->epoch;
-    if (threadIdx.x < 32) {
-        const unsigned ep = *epoch + 1u;
-        unsigned long long* base = (GRP ? a.msg2 : a.msg) + (size_t)(ep & 1u) * G * SLOT_WORDS;
-        if (threadIdx.x == 0) {
-            if (DATA) __threadfence();
-#pragma unroll
-            for (int k = 0; k < NW; k++)
-                st_relaxed_u64(base + (size_t)sh->bid * SLOT_WORDS + k, ((unsigned long long)ep << 32) | pay[k]);
-            work();
-        }
-        const unsigned lane = threadIdx.x;
-        const long long t0 = clock64();
-        int ok = 1;
-        for (unsigned spins = 1;; spins++) {
-            bool all = true;
-            acc.reset();
-#pragma unroll
-            for (int u = 0; u < SPL; u++) {
-                const unsigned i = lane + 32u * u;
-                if (i < G) {
-                    uint32_t wv[NW];
-#pragma unroll
-                    for (int k = 0; k < NW; k++) {
-                        unsigned long long w = ld_relaxed_u64(base + (size_t)i * SLOT_WORDS + k);
-                        all = all && (unsigned)(w >> 32) == ep;
-                        wv[k] = (uint32_t)w;
-                    }
-                    acc.add(wv);
-                }
-            }
-            if (__all_sync(0xffffffffu, all)) break;
-            if ((spins & 31u) == 0u) {
-                int bad = 0;
-                if (lane == 0) {
-                    if (ld_relaxed_i32(a.err) != 0) bad = 1;
-                    else if (clock64() - t0 > a.limit) { atomicCAS(a.err, 0, SPAI_ERR_TIMEOUT); bad = 1; }
-                }
-                if (__shfl_sync(0xffffffffu, bad, 0)) { ok = 0; break; }
-            }
-        }
-        if (DATA) __threadfence();
-        if (ok) acc.finish(lane, sh);
-        __syncwarp();
-        if (lane == 0) { sh->ok = ok; *epoch = ep; }
-    }
-    __syncthreads();
-    return sh->ok != 0;
-}
-
-template <class T> struct SumAcc {
-    T v;
-    __device__ void reset() { v = T(0); }
-    __device__ void add(const uint32_t* w)
-    {
-        if (sizeof(T) == 8) v += (T)__longlong_as_double((long long)(((unsigned long long)w[0] << 32) | w[1]));
-        else v += (T)__uint_as_float(w[0]);
-    }
-    __device__ void finish(unsigned lane, IrShared* sh)
-    {
-        T t = warp_sum(v);
-        if (lane == 0) sh->bcast[0] = (double)t;
-    }
-};
-
-struct Max3Acc {
-    double m[3];
-    __device__ void reset() { m[0] = m[1] = m[2] = 0.0; }
-    __device__ void add(const uint32_t* w)
-    {
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            m[k] = fmax(m[k], __longlong_as_double((long long)(((unsigned long long)w[2 * k] << 32) | w[2 * k + 1])));
-    }
-    __device__ void finish(unsigned lane, IrShared* sh)
-    {
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const double t = warp_max(m[k]);
-            if (lane == 0) sh->bcast[k] = t;
-        }
-    }
-};
-
-struct NoAcc {
-    __device__ void reset() {}
-    __device__ void add(const uint32_t*) {}
-    __device__ void finish(unsigned, IrShared*) {}
-};
-
-// Sum over all blocks of a per-thread value, in a fixed order; the result
-// is identical in every block.  DATA: the round also publishes the global
-// writes made before it (release/acquire); without it only the scalar
-// travels, in the same single-copy-atomic word as its epoch.
-template <bool DATA, class T, bool GRP = false, class Work = NoWork>
-__device__ bool xsum(const IrArgs& a, IrShared* sh, T* red, T v, T& out, const Work& work = Work())
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    constexpr int NW = sizeof(T) == 8 ? 2 : 1;
-    uint32_t pay[2] = {0u, 0u};
-    if (wid == 0) {
-        T t = lane < nw ? red[lane] : T(0);
-        t = warp_sum(t);
-        if (sizeof(T) == 8) {
-            unsigned long long u = (unsigned long long)__double_as_longlong((double)t);
-            pay[0] = (uint32_t)(u >> 32);
-            pay[1] = (uint32_t)u;
-        } else {
-            pay[0] = __float_as_uint((float)t);
-        }
-    }
-    SumAcc<T> acc;
-    bool good = exchange<NW, DATA, SumAcc<T>, GRP>(a, sh, pay, acc, work);
-    out = (T)sh->bcast[0];
-    return good;
-}
-
-// Max of three non-negative doubles over all blocks; red holds 96 doubles.
-__device__ bool xmax3(const IrArgs& a, IrShared* sh, double* red, const double (&v)[3], double (&o)[3])
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const double t = warp_max(v[k]);
-        if (lane == 0) red[32 * k + wid] = t;
-    }
-    __syncthreads();
-    uint32_t pay[6] = {0u, 0u, 0u, 0u, 0u, 0u};
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const double t = warp_max(lane < nw ? red[32 * k + lane] : 0.0);
-            const unsigned long long u = (unsigned long long)__double_as_longlong(t);
-            pay[2 * k] = (uint32_t)(u >> 32);
-            pay[2 * k + 1] = (uint32_t)u;
-        }
-    }
-    Max3Acc acc;
-    bool good = exchange<6, true>(a, sh, pay, acc);
-#pragma unroll
-    for (int k = 0; k < 3; k++) o[k] = sh->bcast[k];
-    return good;
-}
-
-// plain barrier (no payload)
-__device__ bool xbar(const IrArgs& a, IrShared* sh)
-{
-    __syncthreads();
-    uint32_t pay[1] = {0u};
-    NoAcc acc;
-    return exchange<1, true>(a, sh, pay, acc);
-}
-
-// y = M x for the block's rows (SELL-32), two rows per thread per pass with
-// their loads interleaved; `store(row, value)` receives each result.  The
-// slice offsets of the block live in shared memory (soff[0..nsl]).
-template <class TP, class Load, class Store>
-__device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t* soff, const int32_t* __restrict__ col,
-                                          const TP* __restrict__ val, Load load, Store store)
-{
-    const int tid = threadIdx.x, BT = blockDim.x, lane = tid & 31;
-    constexpr int U = 4;
-    for (int64_t base = r0; base < r1; base += 2 * BT) {
-        const int64_t ra = base + tid, rb = base + BT + tid;
-        const bool va = ra < r1, vb = rb < r1;
-        const int sa = (int)((ra - r0) >> 5), sb = (int)((rb - r0) >> 5);
-        const int64_t oa = va ? soff[sa] + lane : 0, ob = vb ? soff[sb] + lane : 0;
-        const int wa = va ? (int)((soff[sa + 1] - soff[sa]) >> 5) : 0;
-        const int wb = vb ? (int)((soff[sb + 1] - soff[sb]) >> 5) : 0;
-        TP acc_a = TP(0), acc_b = TP(0);
-        const int wmax = wa > wb ? wa : wb;
-        // software pipeline: the entries of chunk c+1 load while chunk c gathers
-        int ca[U], cb[U];
-        TP xa[U], xb[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            ca[u] = u < wa ? __ldg(col + oa + 32 * u) : -1;
-            xa[u] = u < wa ? __ldg(val + oa + 32 * u) : TP(0);
-            cb[u] = u < wb ? __ldg(col + ob + 32 * u) : -1;
-            xb[u] = u < wb ? __ldg(val + ob + 32 * u) : TP(0);
-        }
-        for (int c0 = 0; c0 < wmax; c0 += U) {
-            TP ga[U], gb[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                ga[u] = ca[u] >= 0 ? (TP)load(ca[u]) : TP(0);
-                gb[u] = cb[u] >= 0 ? (TP)load(cb[u]) : TP(0);
-            }
-            TP ya[U], yb[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) { ya[u] = xa[u]; yb[u] = xb[u]; }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const int c = c0 + U + u;
-                ca[u] = c < wa ? __ldg(col + oa + 32 * c) : -1;
-                xa[u] = c < wa ? __ldg(val + oa + 32 * c) : TP(0);
-                cb[u] = c < wb ? __ldg(col + ob + 32 * c) : -1;
-                xb[u] = c < wb ? __ldg(val + ob + 32 * c) : TP(0);
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                acc_a = fma(ya[u], ga[u], acc_a);
-                acc_b = fma(yb[u], gb[u], acc_b);
-            }
-        }
-        if (va) store(ra, acc_a);
-        if (vb) store(rb, acc_b);
-    }
-}
-
-// Threads per block of the refinement kernel: 1024 when the basis and the
-// preconditioner products are single precision; 512 when either is double,
-// because the 1024-thread build of those spills registers (64 per thread),
-// which puts the basis prefetch behind HBM latency every Gram-Schmidt round.
-template <class TG, class TP>
-constexpr int ir_threads()
-{
-    return (sizeof(TG) == 8 || sizeof(TP) == 8) ? IR_THREADS / 2 : IR_THREADS;
-}
-
-// The refinement of one system by its G blocks; `bid` is this block's rank.
-template <class TU, class TG, class TP, int RM>
-__device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const int G)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ IrShared shs;
-    __shared__ TG redg[33];
-    __shared__ double redd[96];
-    IrShared* sh = &shs;
-    const int kmax = a.kmax;
-    const int tid = threadIdx.x, BT = blockDim.x;
-    // the Givens thread: thread 0, which also publishes the block's words, so that
-    // the rotations of the Gram-Schmidt rounds run while its warp waits for the
-    // other blocks
-    const int GT = 0;
-    const int64_t r0 = (int64_t)bid * a.rb;
-    const int64_t r1 = min(a.n, r0 + a.rb);
-    // modified Gram-Schmidt rows [m0, m1): the block's own rows, or with a
-    // Gram-Schmidt group the rows of blocks 2b and 2b+1 (empty outside it)
-    const bool sub = a.g2 > 0;
-    const bool gs = !sub || (int)bid < a.g2;
-    const int64_t m0 = sub ? min(a.n, (int64_t)bid * 2 * a.rb) : r0;
-    const int64_t m1 = sub ? (gs ? min(a.n, m0 + 2 * a.rb) : m0) : r1;
-    const int nsl = (int)((a.rb + 31) >> 5);
-    double* cs = (double*)smem;            // kmax + 2
-    double* sn = cs + (kmax + 2);          // kmax + 2
-    double* g = sn + (kmax + 2);           // kmax + 2
-    double* hc = g + (kmax + 2);           // kmax + 2
-    double* yv = hc + (kmax + 2);          // kmax + 2
-    int64_t* soa = (int64_t*)(yv + (kmax + 2));  // nsl + 1 slice offsets of A
-    int64_t* sop = soa + (nsl + 1);        // nsl + 1 slice offsets of P
-    // w for rows [m0, m1) (rb, or 2 rb with a group), 16-byte aligned
-    TG* ws = (TG*)(((uintptr_t)(sop + (nsl + 1)) + 15) & ~(uintptr_t)15);
-    // Gram-Schmidt rows of this thread: PF rows as UV vectors of VN consecutive
-    // rows, vector u = rows [vrow(u), vrow(u) + VN), then rows m0 + PF BT + tid
-    // (step BT); the group's load, the first partial and every round use it
-    constexpr int VN = 16 / (int)sizeof(TG);
-    constexpr int UV = PF / VN;
-    typedef typename std::conditional<sizeof(TG) == 4, float4, double2>::type TV;
-    auto vrow = [&](int u) -> int64_t { return m0 + (int64_t)VN * (tid + u * BT); };
-    // the prefetch set of basis vector Vb: out[u VN + e] = Vb[vrow(u) + e] (0 beyond m1)
-    auto vload = [&](const TG* Vb, TG* out) {
-#pragma unroll
-        for (int u = 0; u < UV; u++) {
-            const int64_t s0 = vrow(u);
-            if (s0 + VN <= m1) {
-                const TV t = __ldcg(reinterpret_cast<const TV*>(Vb + s0));
-                memcpy(out + u * VN, &t, sizeof(TV));
-            } else {
-#pragma unroll
-                for (int e = 0; e < VN; e++) out[u * VN + e] = s0 + e < m1 ? ldcg(&Vb[s0 + e]) : TG(0);
-            }
-        }
-    };
-    TU* x = (TU*)a.x;
-    TU* r = (TU*)a.r;
-    TG* wbuf = (TG*)a.wbuf;
-    TP* tbuf = (TP*)a.tbuf;
-    TG* V = (TG*)a.V;
-    const TP* av = (const TP*)a.A.val;
-    const TP* pv = (const TP*)a.P.val;
-    const bool hasP = a.P.off != nullptr;
-    // the Arnoldi product w = second(first(v)): left P (A v), right A (P v)
-    const bool rightP = hasP && a.side == 1;
-    const int64_t s0 = r0 >> 5;
-    const int64_t nslg = (a.n + 31) >> 5;
-    for (int i = tid; i <= nsl; i += BT) {
-        int64_t sg = min(s0 + i, nslg);
-        soa[i] = a.A.off[sg];
-        sop[i] = hasP ? a.P.off[sg] : 0;
-    }
-    if (tid == 0) { sh->bid = bid; sh->G = G; sh->epoch = 0; sh->epoch2 = 0; sh->gepoch = 0; sh->ok = 1; }
-    __syncthreads();
-    const GridBarrier gbar{a.gcount, a.err, a.limit, (unsigned)G};
-    unsigned vx = 0;  // CGS2 exchanges so far (identical in every block)
-
-    int steps = 0, flags = 0;
-    double dmax = 0.0;   // this thread's largest |d| of the last correction (as added to x, in u)
-    double qprev = 0.0;  // ||d_{i-2}|| / ||x_{i-1}|| (the stagnation test)
-    for (int it = 0; it <= a.imax; it++) {
-        // ---------------- residual r = b - A x in u_r, stored in u
-        double rmax = 0.0, xmax = 0.0;
-        for (int64_t row = r0 + tid; row < r1; row += BT) {
-            double hi = a.b[row], lo = 0.0;
-            for (int64_t q = a.arp[row]; q < a.arp[row + 1]; q++) {
-                double xv = (double)ldcg(&x[a.aci[q]]);
-                if (RM == 2) dd_sub_prod(hi, lo, a.aval[q], xv);
-                else hi = fma(-a.aval[q], xv, hi);
-            }
-            TU rv = (TU)(hi + lo);
-            r[row] = rv;
-            rmax = fmax(rmax, fabs((double)rv));
-            xmax = fmax(xmax, fabs((double)x[row]));
-        }
-        double mx[3];
-        if (!xmax3(a, sh, redd, {rmax, xmax, dmax}, mx)) return;
-        const double rn = mx[0], xn = mx[1], dn = mx[2];
-        const double den = a.anorm * xn + a.bnorm;
-        const double nb = den > 0.0 ? rn / den : 0.0;
-        if (bid == 0 && tid == 0) a.nbe[it] = nb;
-        if (!isfinite(nb)) { flags |= 8; break; }
-        // the stopping rules (identical decisions in every block: the maxima are exchanged)
-        const double q = xn > 0.0 ? dn / xn : (dn > 0.0 ? INFINITY : 0.0);
-        if (a.stop_rule == IR_STOP_BACKWARD && nb <= a.stop_tol) { flags |= 1; break; }
-        if (a.stop_rule == IR_STOP_CORRECTION && it >= 1 && q <= a.stop_tol) { flags |= 1; break; }
-        if (it == a.imax) { flags |= 2; break; }
-        if (a.stop_rule != IR_STOP_FIXED && it >= 2 && q >= 0.5 * qprev) { flags |= 16; break; }
-        qprev = q;
-        dmax = 0.0;
-
-        // ---------------- z = P r (left) or r (right) in u_p, stored in u_g; beta = ||z||
-        TG part = TG(0);
-        if (hasP && !rightP) {
-            sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&r[c]); },
-                          [&](int64_t row, TP v) { TG z = (TG)v; ws[row - r0] = z; wbuf[row] = z; part = fma(z, z, part); });
-        } else {
-            for (int64_t row = r0 + tid; row < r1; row += BT) {
-                TG z = (TG)(TP)r[row];
-                ws[row - r0] = z;
-                wbuf[row] = z;
-                part = fma(z, z, part);
-            }
-        }
-        TG bsq;
-        if (!xsum<true>(a, sh, redg, part, bsq)) return;
-        const TG beta = sqrt(bsq);
-        int k = 0;
-        if (beta > TG(0)) {
-            for (int64_t row = r0 + tid; row < r1; row += BT) V[row] = ws[row - r0] / beta;
-            if (tid == GT) g[0] = (double)beta;
-            TG hdiv = beta;
-            bool done = false;
-            for (int j = 0; j < kmax && !done; j++) {
-                // ---- t = A v_j (left) or P v_j (right) in u_p; v_j formed from the
-                // published w: fl(w / h)
-                sell_rows<TP>(r0, r1, rightP ? sop : soa, rightP ? a.P.col : a.A.col, rightP ? pv : av,
-                              [&](int c) { return (TP)(ldcg(&wbuf[c]) / hdiv); },
-                              [&](int64_t row, TP v) { tbuf[row] = v; });
-                // prefetch v_0 for the first Gram-Schmidt dot while the barrier runs
-                // (with a group the range holds other blocks' rows of v_0, which are
-                // published by this barrier when j = 0: the load waits for it)
-                TG vc[PF];
-                if (!sub) vload(V, vc);
-                if (!xbar(a, sh)) return;
-                if (sub) vload(V, vc);
-                // ---- w = P t (left) or A t (right) in u_p, stored in u_g (own rows, shared
-                // memory); first MGS partial
-                part = TG(0);
-                if (sub) {
-                    // publish w = P t; the group's blocks then read their double range
-                    if (hasP) {
-                        sell_rows<TP>(r0, r1, rightP ? soa : sop, rightP ? a.A.col : a.P.col, rightP ? av : pv,
-                                      [&](int c) { return ldcg(&tbuf[c]); },
-                                      [&](int64_t row, TP v) { wbuf[row] = (TG)v; });
-                    } else {
-                        for (int64_t row = r0 + tid; row < r1; row += BT) wbuf[row] = (TG)ldcg(&tbuf[row]);
-                    }
-                    if (!xbar(a, sh)) return;
-#pragma unroll
-                    for (int u = 0; u < UV; u++) {
-                        const int64_t s0 = vrow(u);
-                        if (s0 + VN <= m1) {
-                            *reinterpret_cast<TV*>(ws + (s0 - m0)) = __ldcg(reinterpret_cast<const TV*>(wbuf + s0));
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < VN; e++)
-                                if (s0 + e < m1) ws[s0 + e - m0] = ldcg(&wbuf[s0 + e]);
-                        }
-                    }
-                    for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) ws[row - m0] = ldcg(&wbuf[row]);
-                } else if (hasP) {
-                    sell_rows<TP>(r0, r1, rightP ? soa : sop, rightP ? a.A.col : a.P.col, rightP ? av : pv,
-                                  [&](int c) { return ldcg(&tbuf[c]); },
-                                  [&](int64_t row, TP v) { ws[row - r0] = (TG)v; });
-                } else {
-                    for (int64_t row = r0 + tid; row < r1; row += BT) ws[row - r0] = (TG)ldcg(&tbuf[row]);
-                }
-                if (a.orth) {
-                    // ---- classical Gram-Schmidt applied twice in u_g: each pass forms all
-                    // j+1 projections of the same w (one vector exchange), then subtracts them
-                    TG* cvec = reinterpret_cast<TG*>(yv);  // free until the back substitution
-                    const int lane = tid & 31, wid = tid >> 5, nwp = BT >> 5;
-                    __syncthreads();
-                    for (int pass = 0; pass < 2; pass++) {
-                        TG* pbase = (TG*)a.pvec + (size_t)(vx & 1u) * G * (kmax + 1);
-                        for (int i = wid; i <= j; i += nwp) {
-                            const TG* Vi = V + (int64_t)i * a.ldv;
-                            TG acc = TG(0);
-                            for (int64_t row = r0 + lane; row < r1; row += 32) acc = fma(Vi[row], ws[row - r0], acc);
-                            acc = warp_sum(acc);
-                            if (lane == 0) pbase[(size_t)bid * (kmax + 1) + i] = acc;
-                        }
-                        if (!grid_sync(gbar, &sh->gepoch, &sh->ok)) return;
-                        for (int i = wid; i <= j; i += nwp) {
-                            TG acc = TG(0);
-                            for (unsigned b = lane; b < G; b += 32) acc += ldcg(&pbase[(size_t)b * (kmax + 1) + i]);
-                            acc = warp_sum(acc);
-                            if (lane == 0) cvec[i] = acc;
-                        }
-                        vx++;
-                        __syncthreads();
-                        if (tid == GT)
-                            for (int i = 0; i <= j; i++) hc[i] = pass == 0 ? (double)cvec[i] : (double)((TG)hc[i] + cvec[i]);
-                        for (int64_t row = r0 + tid; row < r1; row += BT) {
-                            TG acc = ws[row - r0];
-                            for (int i = 0; i <= j; i++) acc = fma(-cvec[i], V[(int64_t)i * a.ldv + row], acc);
-                            ws[row - r0] = acc;
-                        }
-                        __syncthreads();
-                    }
-                    part = TG(0);
-                    for (int64_t row = r0 + tid; row < r1; row += BT) {
-                        const TG wv = ws[row - r0];
-                        wbuf[row] = wv;
-                        part = fma(wv, wv, part);
-                    }
-                    if (tid == GT) {
-                        // rotations 0..j-1 on the new column
-                        for (int q = 0; q < j; q++) {
-                            const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
-                            hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
-                            hc[q] = t0;
-                            if (bid == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
-                        }
-                    }
-                } else {
-                // the group's load gives each thread its Gram-Schmidt rows; without a
-                // group sell_rows wrote w in its own row order.  Basis entries are read
-                // through L2 (ld.cg): with a group they include rows that other blocks
-                // wrote
-                if (!sub) __syncthreads();
-#pragma unroll
-                for (int u = 0; u < UV; u++) {
-                    const int64_t s0 = vrow(u);
-#pragma unroll
-                    for (int e = 0; e < VN; e++)
-                        if (s0 + e < m1) part = fma(vc[u * VN + e], ws[s0 + e - m0], part);
-                }
-                for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) part = fma(ldcg(&V[row]), ws[row - m0], part);
-                // ---- modified Gram-Schmidt in u_g (blocks outside the group skip it)
-                for (int i = 0; i <= j && gs; i++) {
-                    // prefetch v_{i+1} (rows [m0, m1)) before waiting for h_{i,j}
-                    const TG* Vn = V + (int64_t)(i + 1) * a.ldv;
-                    TG vn[PF];
-                    if (i < j) vload(Vn, vn);
-                    TG h;
-                    // Givens, pipelined with the rounds: rotation q needs h_{q+1}, known
-                    // after round q+1; thread 0 applies it during round q+2, between
-                    // publishing and polling
-                    const int pq = i - 2;
-                    auto rot = [&]() {
-                        if (pq >= 0) {
-                            const double t0 = cs[pq] * hc[pq] + sn[pq] * hc[pq + 1];
-                            hc[pq + 1] = -sn[pq] * hc[pq] + cs[pq] * hc[pq + 1];
-                            hc[pq] = t0;
-                            if (bid == 0) a.R[(size_t)j * (kmax + 1) + pq] = hc[pq];
-                        }
-                    };
-                    if (sub ? !xsum<false, TG, true>(a, sh, redg, part, h, rot)
-                            : !xsum<false, TG, false>(a, sh, redg, part, h, rot))
-                        return;
-                    if (tid == GT) hc[i] = (double)h;
-                    const TG* Vi = V + (int64_t)i * a.ldv;
-                    part = TG(0);
-                    if (i < j) {
-#pragma unroll
-                        for (int u = 0; u < UV; u++) {
-                            const int64_t s0 = vrow(u);
-                            TG* wp = ws + (s0 - m0);
-                            if (s0 + VN <= m1) {
-                                TV t = *reinterpret_cast<const TV*>(wp);
-                                TG wv[VN];
-                                memcpy(wv, &t, sizeof(TV));
-#pragma unroll
-                                for (int e = 0; e < VN; e++) {
-                                    wv[e] = fma(-h, vc[u * VN + e], wv[e]);
-                                    part = fma(vn[u * VN + e], wv[e], part);
-                                }
-                                memcpy(&t, wv, sizeof(TV));
-                                *reinterpret_cast<TV*>(wp) = t;
-                            } else {
-#pragma unroll
-                                for (int e = 0; e < VN; e++)
-                                    if (s0 + e < m1) {
-                                        const TG wv = fma(-h, vc[u * VN + e], wp[e]);
-                                        wp[e] = wv;
-                                        part = fma(vn[u * VN + e], wv, part);
-                                    }
-                            }
-                        }
-#pragma unroll
-                        for (int e = 0; e < PF; e++) vc[e] = vn[e];
-                        for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) {
-                            TG wv = fma(-h, ldcg(&Vi[row]), ws[row - m0]);
-                            ws[row - m0] = wv;
-                            part = fma(ldcg(&Vn[row]), wv, part);
-                        }
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < UV; u++) {
-                            const int64_t s0 = vrow(u);
-                            TG* wp = ws + (s0 - m0);
-                            if (s0 + VN <= m1) {
-                                TV t = *reinterpret_cast<const TV*>(wp);
-                                TG wv[VN];
-                                memcpy(wv, &t, sizeof(TV));
-#pragma unroll
-                                for (int e = 0; e < VN; e++) {
-                                    wv[e] = fma(-h, vc[u * VN + e], wv[e]);
-                                    part = fma(wv[e], wv[e], part);
-                                }
-                                memcpy(&t, wv, sizeof(TV));
-                                *reinterpret_cast<TV*>(wp) = t;
-                                *reinterpret_cast<TV*>(wbuf + s0) = t;
-                            } else {
-#pragma unroll
-                                for (int e = 0; e < VN; e++)
-                                    if (s0 + e < m1) {
-                                        const TG wv = fma(-h, vc[u * VN + e], wp[e]);
-                                        wp[e] = wv;
-                                        wbuf[s0 + e] = wv;
-                                        part = fma(wv, wv, part);
-                                    }
-                            }
-                        }
-                        for (int64_t row = m0 + (int64_t)PF * BT + tid; row < m1; row += BT) {
-                            TG wv = fma(-h, ldcg(&Vi[row]), ws[row - m0]);
-                            ws[row - m0] = wv;
-                            wbuf[row] = wv;
-                            part = fma(wv, wv, part);
-                        }
-                    }
-                }
-                }
-                // the last rotation of the rounds, j-1 (the CGS2 branch applied all)
-                if (!a.orth && gs && tid == GT && j >= 1) {
-                    const int q = j - 1;
-                    const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
-                    hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
-                    hc[q] = t0;
-                    if (bid == 0) a.R[(size_t)j * (kmax + 1) + q] = hc[q];
-                }
-                // outside the group part is 0; block 0 stores the rotated diagonal
-                // entry h_jj (rotations 0..j-1 applied) in the unused last row of R's
-                // column j for the blocks outside the group
-                if (!gs) part = TG(0);
-                if (sub && !a.orth && bid == 0 && tid == GT) a.R[(size_t)j * (kmax + 1) + kmax] = hc[j];
-                TG hsq;
-                if (!xsum<true>(a, sh, redg, part, hsq)) return;
-                const TG hn = sqrt(hsq);
-                if (sub && !a.orth && !gs && tid == GT) hc[j] = __ldcg(&a.R[(size_t)j * (kmax + 1) + kmax]);
-                // ---- v_{j+1} = w / h_{j+1,j} (own rows; with a group from the published w)
-                if (hn > TG(0)) {
-                    TG* Vn = V + (int64_t)(j + 1) * a.ldv;
-                    if (sub) {
-                        for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ldcg(&wbuf[row]) / hn;
-                    } else {
-                        for (int64_t row = r0 + tid; row < r1; row += BT) Vn[row] = ws[row - r0] / hn;
-                    }
-                }
-                // ---- the new Givens rotation in double (identical in every block);
-                // rotations 0..j-1 were applied to this column during the rounds
-                if (tid == GT) {
-                    hc[j + 1] = (double)hn;
-                    double dn = sqrt(hc[j] * hc[j] + hc[j + 1] * hc[j + 1]);
-                    if (dn == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
-                    else { cs[j] = hc[j] / dn; sn[j] = hc[j + 1] / dn; }
-                    hc[j] = dn;
-                    g[j + 1] = -sn[j] * g[j];
-                    g[j] = cs[j] * g[j];
-                    sh->resid = fabs(g[j + 1]) / (double)beta;
-                    if (bid == 0) a.R[(size_t)j * (kmax + 1) + j] = hc[j];
-                }
-                __syncthreads();
-                k = j + 1;
-                hdiv = hn;
-                if (hn == TG(0)) { flags |= 4; done = true; }
-                else if (sh->resid <= a.tau) done = true;
-            }
-            // ---- y = R^{-1} g (double), d = V y in u_g, x = x + d in u
-            if (!xbar(a, sh)) return;  // R columns from block 0
-            if (tid < 32) {
-                for (int t = tid; t < k; t += 32) yv[t] = g[t];
-                __syncwarp();
-                for (int c = k - 1; c >= 0; c--) {
-                    if (tid == 0) {
-                        double rcc = __ldcg(&a.R[(size_t)c * (kmax + 1) + c]);
-                        yv[c] = rcc != 0.0 ? yv[c] / rcc : 0.0;
-                    }
-                    __syncwarp();
-                    double yc = yv[c];
-                    for (int t = tid; t < c; t += 32) yv[t] -= __ldcg(&a.R[(size_t)c * (kmax + 1) + t]) * yc;
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            if (rightP) {
-                // right preconditioning: d = P (V_k y), the product in u_p stored in u_g
-                for (int64_t row = r0 + tid; row < r1; row += BT) {
-                    TG dsum = TG(0);
-                    for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
-                    wbuf[row] = dsum;
-                }
-                if (!xbar(a, sh)) return;
-                sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&wbuf[c]); },
-                              [&](int64_t row, TP v) {
-                                  const TU du = (TU)(TG)v;
-                                  dmax = fmax(dmax, fabs((double)du));
-                                  x[row] = (TU)((TU)x[row] + du);
-                              });
-            } else {
-                for (int64_t row = r0 + tid; row < r1; row += BT) {
-                    TG dsum = TG(0);
-                    for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
-                    const TU du = (TU)dsum;
-                    dmax = fmax(dmax, fabs((double)du));
-                    x[row] = (TU)((TU)x[row] + du);
-                }
-            }
-        }
-        if (bid == 0 && tid == 0) a.its[it] = k;
-        steps = it + 1;
-        // x must be complete before the next residual
-        if (!xbar(a, sh)) return;
-    }
-    if (bid == 0 && tid == 0) {
-        a.out[0] = steps;
-        a.out[1] = flags;
-    }
-}
-
-template <class TU, class TG, class TP, int RM>
-__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
-{
-    ir_body<TU, TG, TP, RM>(a, (int)blockIdx.x, (int)gridDim.x);
-}
-
-// Many systems in one cooperative launch, scheduled dynamically: the grid is
-// split into teams of T blocks; the first block of a team claims the next
-// system from *next (an atomic counter) and hands its index to the team
-// through the team's word in `claim`, tagged with the team's claim count, and
-// the team runs that system (with its own arguments, exchange slots and error
-// word) as a grid of T blocks.  Teams never wait on one another, so a system
-// with many iterations holds only its own team's SMs.  Waits are bounded like
-// every other wait of the refinement: a team that gives up leaves.
-template <class TU, class TG, class TP, int RM>
-__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrArgs* __restrict__ args, int count,
-                                                                     int T, unsigned* next,
-                                                                     unsigned long long* claim, long long limit)
-{
-    __shared__ int s_sys;
-    const int team = (int)blockIdx.x / T, rank = (int)blockIdx.x % T;
-    for (unsigned round = 1;; round++) {
-        if (threadIdx.x == 0) {
-            int sys = -1;
-            if (rank == 0) {
-                sys = (int)atomicAdd(next, 1u);
-                st_relaxed_u64(&claim[team], ((unsigned long long)round << 32) | (unsigned)sys);
-            } else {
-                const long long t0 = clock64();
-                for (;;) {
-                    const unsigned long long w = ld_relaxed_u64(&claim[team]);
-                    if ((unsigned)(w >> 32) == round) { sys = (int)(unsigned)w; break; }
-                    if (clock64() - t0 > limit) break;  // the leader is gone: leave
-                }
-            }
-            s_sys = sys;
-        }
-        __syncthreads();
-        const int sys = s_sys;
-        __syncthreads();
-        if (sys < 0 || sys >= count) return;
-        ir_body<TU, TG, TP, RM>(args[sys], rank, T);
-        __syncthreads();
-    }
-}
 
 // ---------------------------------------------------------------- SELL-32 conversion
 
@@ -943,45 +141,54 @@ __global__ void k_norms(int64_t n, const int64_t* __restrict__ rp, const double*
     }
 }
 
-template <class TU, class TG, class TP, int RM>
-int launch_ir(IrArgs& a, int num_sms, cudaStream_t s, int* grid_out)
+// the kernels of the run-time precision tuple (u, u_g, u_p), u_r and orth
+int ir_kernels(int u, int ug, int up, int ur, int orth, IrKernels* k)
 {
-    auto kern = k_ir<TU, TG, TP, RM>;
-    // one block per SM, at least 256 rows per block, rows per
-    // block a multiple of 32 so that blocks own whole SELL slices
+    const int rm = ur == SPAI_QUAD ? 2 : 1;
+    const bool ls = orth == 2;
+    const int key = (u == SPAI_DOUBLE) * 4 + (ug == SPAI_DOUBLE) * 2 + (up == SPAI_DOUBLE);
+    switch (key) {
+    case 0: ir_kernels_fff(rm, ls, k); break;
+    case 1: ir_kernels_ffd(rm, ls, k); break;
+    case 2: ir_kernels_fdf(rm, ls, k); break;
+    case 3: ir_kernels_fdd(rm, ls, k); break;
+    case 4: ir_kernels_dff(rm, ls, k); break;
+    case 5: ir_kernels_dfd(rm, ls, k); break;
+    case 6: ir_kernels_ddf(rm, ls, k); break;
+    default: ir_kernels_ddd(rm, ls, k); break;
+    }
+    return k->one ? 0 : SPAI_ERR_UNSUPPORTED;
+}
+
+// One system on its own grid: one block per SM, at least 256 rows per
+// block, rows per block a multiple of 32 so that blocks own whole SELL
+// slices.  sg = sizeof(u_g).
+int launch_ir(IrArgs& a, const IrKernels& K, int sg, int num_sms, cudaStream_t s, int* grid_out)
+{
     int64_t G = std::min<int64_t>((a.n + 255) / 256, std::min(num_sms, MAX_GRID));
     if (G < 1) G = 1;
     a.rb = ((a.n + G - 1) / G + 31) & ~int64_t(31);
     G = (a.n + a.rb - 1) / a.rb;
-    const int64_t nsl = (a.rb + 31) >> 5;
     // Gram-Schmidt group: on large grids the scalar rounds run among half the
     // blocks (each over two blocks' rows); a round among 76 blocks took
     // ~1.2 us against ~1.7 us among 152, which outweighs the extra barrier
-    // that publishes w once per iteration.  CGS2 has no scalar rounds.
+    // that publishes w once per iteration.  CGS2 and the one-reduction MGS have
+    // no scalar rounds.
     a.g2 = (!a.orth && G >= MGS_GROUP_MIN_GRID) ? (int)((G + 1) / 2) : 0;
-    auto smem_for = [&](int g2) {
-        return sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + (g2 ? 2 : 1) * a.rb * sizeof(TG) + 64;
-    };
     size_t dyn_max = 0;
-    SPAI_CUDA_TRY(allow_max_dynamic_smem(kern, &dyn_max));
+    SPAI_CUDA_TRY(allow_max_dynamic_smem_ptr(K.one, &dyn_max));
+    a.jl = a.orth == 2 ? ir_pick_jl(a.rb, a.kmax, dyn_max, sg) : 0;
+    auto smem_for = [&](int g2) { return ir_smem_bytes(a.rb, a.kmax, g2, a.orth, a.jl, sg); };
     if (a.g2 && smem_for(a.g2) > dyn_max) a.g2 = 0;  // the doubled row range does not fit
     const size_t smem = smem_for(a.g2);
     if (smem > dyn_max) return SPAI_ERR_UNSUPPORTED;
     int occ = 0;
-    constexpr int threads = ir_threads<TG, TP>();
-    SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+    SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, K.one, K.threads, smem));
     if ((int64_t)occ * num_sms < G) return SPAI_ERR_UNSUPPORTED;
     void* args[] = {(void*)&a};
-    SPAI_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)G), dim3(threads), args, smem, s));
+    SPAI_CUDA_TRY(cudaLaunchCooperativeKernel(K.one, dim3((unsigned)G), dim3(K.threads), args, smem, s));
     *grid_out = (int)G;
     return 0;
-}
-
-template <class TU, class TG, class TP>
-int launch_ir_rm(IrArgs& a, int rm, int num_sms, cudaStream_t s, int* grid)
-{
-    if (rm == 2) return launch_ir<TU, TG, TP, 2>(a, num_sms, s, grid);
-    return launch_ir<TU, TG, TP, 1>(a, num_sms, s, grid);
 }
 
 int prec_bytes(int p) { return p == SPAI_HALF ? 2 : (p == SPAI_SINGLE ? 4 : 8); }
@@ -1068,6 +275,7 @@ struct IrJob {
     unsigned long long* norms = nullptr;
     void* pvec = nullptr;
     unsigned* gcount = nullptr;
+    void* L = nullptr;
     SellMat As;
     const SellMat* Ps = nullptr;
     unsigned long long h_norms[3] = {0, 0, 0};
@@ -1087,7 +295,7 @@ int ir_check_opts(const ir_opts* o)
     if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
-    if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
+    if (o->orth < 0 || o->orth > 2) return SPAI_ERR_INVALID_ARG;
     if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
     if (o->stop != IR_STOP_BACKWARD && o->stop != IR_STOP_FIXED && o->stop != IR_STOP_CORRECTION)
         return SPAI_ERR_INVALID_ARG;
@@ -1142,6 +350,7 @@ int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
         TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
         CTRY(cudaMemsetAsync(J.gcount, 0, sizeof(unsigned), s));
     }
+    if (o->orth == 2) TRY(dev_alloc(&J.L, (size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1), s));
     CTRY(cudaMemsetAsync(J.its, 0, sizeof(int) * (imax + 1), s));
     CTRY(cudaMemsetAsync(J.outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(J.err, 0, sizeof(int) * 2, s));
@@ -1250,7 +459,7 @@ void ir_job_args(IrJob& J, int device, const ir_opts* o)
     a.stop_tol = ir_stop_tol(o, q);
     a.kmax = J.kmax; a.imax = J.imax; a.stop_rule = o->stop;
     a.its = J.its; a.nbe = J.nbe; a.out = J.outv;
-    a.orth = o->orth; a.pvec = J.pvec; a.gcount = J.gcount; a.side = o->side;
+    a.orth = o->orth; a.pvec = J.pvec; a.gcount = J.gcount; a.L = J.L; a.side = o->side;
 }
 
 // x in double and the result copies, enqueued on s.
@@ -1297,42 +506,13 @@ void ir_job_free(IrJob& J, cudaStream_t s)
     sell_free(&J.As, s);
     dev_free(J.x, s); dev_free(J.r, s); dev_free(J.wbuf, s); dev_free(J.tbuf, s); dev_free(J.V, s);
     dev_free(J.R, s); dev_free(J.msg, s); dev_free(J.nbe, s); dev_free(J.its, s); dev_free(J.outv, s);
-    dev_free(J.err, s); dev_free(J.norms, s); dev_free(J.pvec, s); dev_free(J.gcount, s);
-    J.x = J.r = J.wbuf = J.tbuf = J.V = J.pvec = nullptr;
+    dev_free(J.err, s); dev_free(J.norms, s); dev_free(J.pvec, s); dev_free(J.gcount, s); dev_free(J.L, s);
+    J.x = J.r = J.wbuf = J.tbuf = J.V = J.pvec = J.L = nullptr;
     J.R = J.nbe = nullptr;
     J.its = J.outv = J.err = nullptr;
     J.msg = J.norms = nullptr;
     J.gcount = nullptr;
 }
-
-// Instantiate F<TU, TG, TP> for the run-time precisions and call it.
-template <class F>
-int dispatch_tuple(const ir_opts* o, F&& f)
-{
-    if (o->u == SPAI_DOUBLE) {
-        if (o->ug == SPAI_DOUBLE) {
-            if (o->up == SPAI_DOUBLE) return f.template run<double, double, double>();
-            return f.template run<double, double, float>();
-        }
-        if (o->up == SPAI_DOUBLE) return f.template run<double, float, double>();
-        return f.template run<double, float, float>();
-    }
-    if (o->ug == SPAI_DOUBLE) {
-        if (o->up == SPAI_DOUBLE) return f.template run<float, double, double>();
-        return f.template run<float, double, float>();
-    }
-    if (o->up == SPAI_DOUBLE) return f.template run<float, float, double>();
-    return f.template run<float, float, float>();
-}
-
-struct LaunchOne {
-    IrArgs* a;
-    int rm, num_sms;
-    cudaStream_t s;
-    int* grid;
-    template <class TU, class TG, class TP>
-    int run() { return launch_ir_rm<TU, TG, TP>(*a, rm, num_sms, s, grid); }
-};
 
 }  // namespace
 
@@ -1360,8 +540,9 @@ int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_
     ir_job_args(J, device, o);
     CTRY(cudaEventRecord(ek0, s));
     {
-        LaunchOne L{&J.a, o->ur == SPAI_QUAD ? 2 : 1, num_sms, s, &grid};
-        TRY(dispatch_tuple(o, L));
+        IrKernels K;
+        TRY(ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &K));
+        TRY(launch_ir(J.a, K, prec_bytes(o->ug), num_sms, s, &grid));
     }
     CTRY(cudaEventRecord(ek1, s));
     nl++;
@@ -1482,7 +663,6 @@ namespace {
 
 constexpr int64_t BATCH_ROWS_PER_BLOCK = 2048;
 
-template <class TU, class TG, class TP, int RM>
 struct BatchRun {
     int device, num_sms;
     cudaStream_t s;
@@ -1492,19 +672,17 @@ struct BatchRun {
     int* nl;
     float* ms_kernel;
     int* team_size;
+    IrKernels K;
+    int sg;                    // sizeof(u_g)
 
-    size_t smem_for(const IrArgs& a) const
-    {
-        const int64_t nsl = (a.rb + 31) >> 5;
-        return sizeof(double) * 5 * (a.kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + (a.g2 ? 2 : 1) * a.rb * sizeof(TG) + 64;
-    }
+    size_t smem_for(const IrArgs& a) const { return ir_smem_bytes(a.rb, a.kmax, a.g2, a.orth, a.jl, sg); }
 
     int run()
     {
-        auto kern = k_ir_batch<TU, TG, TP, RM>;
-        constexpr int threads = ir_threads<TG, TP>();
+        const void* kern = K.batch;
+        const int threads = K.threads;
         size_t dyn_max = 0;
-        SPAI_CUDA_TRY(allow_max_dynamic_smem(kern, &dyn_max));
+        SPAI_CUDA_TRY(allow_max_dynamic_smem_ptr(kern, &dyn_max));
         std::vector<IrJob>& J = *jobs;
         const int count = (int)J.size();
         // team size from the median order: about BATCH_ROWS_PER_BLOCK rows per block
@@ -1577,6 +755,7 @@ struct BatchRun {
             a.rb = std::max<int64_t>(32, ((jb.n + T - 1) / T + 31) & ~int64_t(31));
             a.g2 = 0;
             a.block0 = 0;
+            a.jl = a.orth == 2 ? ir_pick_jl(a.rb, a.kmax, dyn_max, sg) : 0;
             smem = std::max(smem, smem_for(a));
             h[q] = a;
         }
@@ -1604,7 +783,7 @@ struct BatchRun {
             long long limit = h[0].limit;
             void* args[] = {(void*)&pa, (void*)&cnt, (void*)&tt, (void*)&d_next, (void*)&d_claim, (void*)&limit};
             cudaEventRecord(k0, s);
-            if (cudaLaunchCooperativeKernel((void*)kern, dim3((unsigned)(teams * T)), dim3(threads), args, smem, s) !=
+            if (cudaLaunchCooperativeKernel(kern, dim3((unsigned)(teams * T)), dim3(threads), args, smem, s) !=
                 cudaSuccess)
                 rc = SPAI_ERR_CUDA;
             cudaEventRecord(k1, s);
@@ -1624,24 +803,6 @@ struct BatchRun {
         dev_free(d_next, s);
         dev_free(d_claim, s);
         return rc;
-    }
-};
-
-struct LaunchBatch {
-    int device, num_sms;
-    cudaStream_t s;
-    const ir_opts* o;
-    std::vector<IrJob>* jobs;
-    std::vector<int>* order;
-    int* nl;
-    float* ms_kernel;
-    int* team_size;
-    template <class TU, class TG, class TP>
-    int run()
-    {
-        if (o->ur == SPAI_QUAD)
-            return BatchRun<TU, TG, TP, 2>{device, num_sms, s, o, jobs, order, nl, ms_kernel, team_size}.run();
-        return BatchRun<TU, TG, TP, 1>{device, num_sms, s, o, jobs, order, nl, ms_kernel, team_size}.run();
     }
 };
 
@@ -1672,8 +833,9 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
     float ms_kernel = 0.f;
     cudaEventRecord(e0, s);
     int team = 0;
-    LaunchBatch L{device, num_sms, s, o, &jobs, &order, &nl, &ms_kernel, &team};
-    rc = dispatch_tuple(o, L);
+    BatchRun B{device, num_sms, s, o, &jobs, &order, &nl, &ms_kernel, &team, IrKernels(), prec_bytes(o->ug)};
+    rc = ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &B.K);
+    if (!rc) rc = B.run();
     cudaEventRecord(e1, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
     float ms_all = 0.f;
@@ -1825,7 +987,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
     if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
-    if (o->orth != 0 && o->orth != 1) return SPAI_ERR_INVALID_ARG;
+    if (o->orth < 0 || o->orth > 2) return SPAI_ERR_INVALID_ARG;
     if (o->stop != IR_STOP_BACKWARD && o->stop != IR_STOP_FIXED && o->stop != IR_STOP_CORRECTION)
         return SPAI_ERR_INVALID_ARG;
     const int64_t n = A->n;
@@ -1864,8 +1026,9 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     int32_t* pw = P ? (int32_t*)cv.take(sizeof(int32_t) * nsl) : nullptr;
     // CGS2: the partial dot products of every block and the counter of their barrier
     void* pvec = o->orth ? cv.take((size_t)sg * 2 * MAX_GRID * (kmax + 1)) : nullptr;
+    void* Lrows = o->orth == 2 ? cv.take((size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1)) : nullptr;
     if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)) ||
-        (o->orth && !pvec))
+        (o->orth && !pvec) || (o->orth == 2 && !Lrows))
         return SPAI_ERR_UNSUPPORTED;  // the problem does not fit the fixed scratch
     int* err = (int*)ctrl;
     int* outv = err + 2;
@@ -1972,25 +1135,12 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
     a.its = its; a.nbe = nbe; a.out = outv;
     a.side = o->side;
-    a.orth = o->orth; a.pvec = pvec; a.gcount = gcount;
-    const int rm = o->ur == SPAI_QUAD ? 2 : 1;
+    a.orth = o->orth; a.pvec = pvec; a.gcount = gcount; a.L = Lrows;
     int grid = 0;
-    if (o->u == SPAI_DOUBLE) {
-        if (o->ug == SPAI_DOUBLE) {
-            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<double, double, double>(a, rm, num_sms, s, &grid);
-            else rc = launch_ir_rm<double, double, float>(a, rm, num_sms, s, &grid);
-        } else {
-            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<double, float, double>(a, rm, num_sms, s, &grid);
-            else rc = launch_ir_rm<double, float, float>(a, rm, num_sms, s, &grid);
-        }
-    } else {
-        if (o->ug == SPAI_DOUBLE) {
-            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<float, double, double>(a, rm, num_sms, s, &grid);
-            else rc = launch_ir_rm<float, double, float>(a, rm, num_sms, s, &grid);
-        } else {
-            if (o->up == SPAI_DOUBLE) rc = launch_ir_rm<float, float, double>(a, rm, num_sms, s, &grid);
-            else rc = launch_ir_rm<float, float, float>(a, rm, num_sms, s, &grid);
-        }
+    {
+        IrKernels K;
+        rc = ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &K);
+        if (!rc) rc = launch_ir(a, K, prec_bytes(o->ug), num_sms, s, &grid);
     }
     if (rc) return rc;
     nl++;

@@ -155,7 +155,7 @@ def test_spai_build_batch_matches_single_builds(ctx, adaptive):
         Ps[i].free()
 
 
-@pytest.mark.parametrize("orth,side", [(1, 0), (0, 1)])
+@pytest.mark.parametrize("orth,side", [(1, 0), (0, 1), (2, 0), (2, 1)])
 def test_batch_cgs2_and_right_preconditioning(ctx, orth, side):
     As = mixed_systems()[:6]
     io = S.make_ir_opts(tau=1e-4, orth=orth, side=side, **TUPLE)

@@ -448,6 +448,66 @@ def test_ir_cgs2_against_oracle(ctx, tup):
     check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
 
 
+ICWY_CASES = [
+    # (name, tuple, side, preconditioned, gmres_max_it)
+    ("3d-half-single", ("half", "single", "single", "single", "double"), 0, True, 0),
+    ("2d-single-double-quad", ("single", "double", "double", "double", "quad"), 0, True, 0),
+    ("2d-single-ug-single", ("single", "double", "single", "single", "double"), 0, True, 0),
+    ("2d-right", ("single", "double", "double", "double", "quad"), 1, True, 0),
+    ("2d-unpreconditioned", ("single", "double", "double", "double", "quad"), 0, False, 0),
+    ("2d-capped-iterations", ("single", "double", "double", "double", "quad"), 0, True, 12),
+]
+
+
+@pytest.mark.parametrize("name,tup,side,precond,maxit", ICWY_CASES)
+def test_ir_one_reduction_mgs_against_oracle(ctx, name, tup, side, precond, maxit):
+    """MGS in its one-reduction form (orth 2) against the oracle's: left and right
+    preconditioning, no preconditioner, and a GMRES iteration cap (the last pass
+    then only forms ||u_k||)."""
+    uf, u, ug, up, ur = tup
+    if u == "single":
+        A, b, x_true = synth.cfg_large_3d(N=16)
+        init, F = O.PAT_A2, 25
+    else:
+        A = synth.conv_diff_2d(40, 20.0, 1.0, 0.1, seed=11)
+        b, x_true = synth.rhs(A, seed=12)
+        init, F = O.PAT_A, 30
+    tau = 1e-4 if ug == "single" else 1e-8
+    so = S.make_spai_opts(init=init, max_fill=F, uf=uf, side=side) if precond else None
+    io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=2, side=side, gmres_max_it=maxit)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    Pr = None
+    if precond and side == 0:
+        Pr = O.assemble_P(O.spai(A, init=init, max_fill=F, uf=uf), up, uf)
+    elif precond:
+        _, Pr = O.spai_right(A, up=up, uf=uf, init=init, max_fill=F)
+    ref = O.gmres_ir(A, b, Pr, uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=O.ORTH_MGS_ICWY, side=side,
+                     gmres_maxit=maxit if maxit else None)
+    if maxit:
+        assert max(st["its"]) == maxit
+    check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
+
+
+@pytest.mark.parametrize("tup", [("half", "single", "single", "single", "double"),
+                                 ("single", "double", "double", "double", "double")])
+def test_ir_one_reduction_mgs_large_grid(ctx, tup):
+    # n = 27^3 = 19683: 77 blocks of 256 rows (a ragged last block), the grid size at which
+    # the MGS rounds would run in a Gram-Schmidt group
+    uf, u, ug, up, ur = tup
+    A = synth.conv_diff_3d(27, 50.0, seed=11)
+    b, x_true = synth.rhs(A, seed=12)
+    tau = 1e-4 if ug == "single" else 1e-8
+    so = S.make_spai_opts(init=O.PAT_A2, max_fill=25, uf=uf)
+    io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=2)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    ref = O.gmres_ir(A, b, O.assemble_P(O.spai(A, init=O.PAT_A2, max_fill=25, uf=uf), up, uf), uf=uf, u=u, ug=ug,
+                     up=up, ur=ur, tau=tau, orth=O.ORTH_MGS_ICWY)
+    assert st["grid"] >= 64
+    check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
+
+
 # ---------------------------------------------------------------- right preconditioning (reading R14)
 
 

@@ -39,6 +39,7 @@ CASES = {
     "2d-unpreconditioned": dict(side=0, orth=0, precond=False),
     "2d-right": dict(side=1, orth=0, precond=True),
     "3d-cgs2": dict(side=0, orth=1, precond=True),
+    "3d-one-reduction-mgs": dict(side=0, orth=2, precond=True),
 }
 
 
