@@ -165,10 +165,16 @@ int ir_kernels(int u, int ug, int up, int ur, int orth, IrKernels* k)
 // slices.  sg = sizeof(u_g).
 int launch_ir(IrArgs& a, const IrKernels& K, int sg, int num_sms, cudaStream_t s, int* grid_out)
 {
-    int64_t G = std::min<int64_t>((a.n + 255) / 256, std::min(num_sms, MAX_GRID));
+    // the one-reduction MGS on grids of 8 or more row blocks adds a block without
+    // rows that runs the Givens rotations (FP64 work beside the other blocks'
+    // inner products slowed both)
+    const bool sblock = a.orth == 2 && a.gpub && std::min<int64_t>((a.n + 255) / 256, std::min(num_sms, MAX_GRID)) >= 9;
+    int64_t G = std::min<int64_t>((a.n + 255) / 256, std::min(num_sms, MAX_GRID) - (sblock ? 1 : 0));
     if (G < 1) G = 1;
     a.rb = ((a.n + G - 1) / G + 31) & ~int64_t(31);
     G = (a.n + a.rb - 1) / a.rb;
+    a.sblock = sblock ? 1 : 0;
+    if (sblock) G += 1;
     // Gram-Schmidt group: on large grids the scalar rounds run among half the
     // blocks (each over two blocks' rows); a round among 76 blocks took
     // ~1.2 us against ~1.7 us among 152, which outweighs the extra barrier
@@ -276,6 +282,7 @@ struct IrJob {
     void* pvec = nullptr;
     unsigned* gcount = nullptr;
     void* L = nullptr;
+    double* gpub = nullptr;
     SellMat As;
     const SellMat* Ps = nullptr;
     unsigned long long h_norms[3] = {0, 0, 0};
@@ -350,7 +357,10 @@ int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
         TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
         CTRY(cudaMemsetAsync(J.gcount, 0, sizeof(unsigned), s));
     }
-    if (o->orth == 2) TRY(dev_alloc(&J.L, (size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1), s));
+    if (o->orth == 2) {
+        TRY(dev_alloc(&J.L, (size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1), s));
+        TRY(dev_alloc((void**)&J.gpub, sizeof(double) * (kmax + 2), s));
+    }
     CTRY(cudaMemsetAsync(J.its, 0, sizeof(int) * (imax + 1), s));
     CTRY(cudaMemsetAsync(J.outv, 0, sizeof(int) * 2, s));
     CTRY(cudaMemsetAsync(J.err, 0, sizeof(int) * 2, s));
@@ -459,7 +469,7 @@ void ir_job_args(IrJob& J, int device, const ir_opts* o)
     a.stop_tol = ir_stop_tol(o, q);
     a.kmax = J.kmax; a.imax = J.imax; a.stop_rule = o->stop;
     a.its = J.its; a.nbe = J.nbe; a.out = J.outv;
-    a.orth = o->orth; a.pvec = J.pvec; a.gcount = J.gcount; a.L = J.L; a.side = o->side;
+    a.orth = o->orth; a.pvec = J.pvec; a.gcount = J.gcount; a.L = J.L; a.gpub = J.gpub; a.side = o->side;
 }
 
 // x in double and the result copies, enqueued on s.
@@ -507,6 +517,8 @@ void ir_job_free(IrJob& J, cudaStream_t s)
     dev_free(J.x, s); dev_free(J.r, s); dev_free(J.wbuf, s); dev_free(J.tbuf, s); dev_free(J.V, s);
     dev_free(J.R, s); dev_free(J.msg, s); dev_free(J.nbe, s); dev_free(J.its, s); dev_free(J.outv, s);
     dev_free(J.err, s); dev_free(J.norms, s); dev_free(J.pvec, s); dev_free(J.gcount, s); dev_free(J.L, s);
+    dev_free(J.gpub, s);
+    J.gpub = nullptr;
     J.x = J.r = J.wbuf = J.tbuf = J.V = J.pvec = J.L = nullptr;
     J.R = J.nbe = nullptr;
     J.its = J.outv = J.err = nullptr;
@@ -1027,8 +1039,9 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     // CGS2: the partial dot products of every block and the counter of their barrier
     void* pvec = o->orth ? cv.take((size_t)sg * 2 * MAX_GRID * (kmax + 1)) : nullptr;
     void* Lrows = o->orth == 2 ? cv.take((size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1)) : nullptr;
+    double* gpub = o->orth == 2 ? (double*)cv.take(sizeof(double) * (kmax + 2)) : nullptr;
     if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)) ||
-        (o->orth && !pvec) || (o->orth == 2 && !Lrows))
+        (o->orth && !pvec) || (o->orth == 2 && (!Lrows || !gpub)))
         return SPAI_ERR_UNSUPPORTED;  // the problem does not fit the fixed scratch
     int* err = (int*)ctrl;
     int* outv = err + 2;
@@ -1135,7 +1148,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     a.kmax = kmax; a.imax = imax; a.stop_rule = o->stop;
     a.its = its; a.nbe = nbe; a.out = outv;
     a.side = o->side;
-    a.orth = o->orth; a.pvec = pvec; a.gcount = gcount; a.L = Lrows;
+    a.orth = o->orth; a.pvec = pvec; a.gcount = gcount; a.L = Lrows; a.gpub = gpub;
     int grid = 0;
     {
         IrKernels K;

@@ -78,28 +78,35 @@ struct IrArgs {
     void* pvec;                 // CGS2: 2 parities x gridDim.x x (kmax + 1) partial dot products (u_g);
                                 // one-reduction MGS: [value][block], 2 (kmax + 1) values
     unsigned* gcount;           // CGS2 / one-reduction MGS: counter of the barrier that publishes them (zeroed)
-    void* L;                    // one-reduction MGS: the rows of L = strictly lower part of Q^T Q,
-                                // packed (row i at i (i - 1) / 2), u_g; block 0 writes them
-    int jl;                     // rows 0 .. jl-1 of L are also kept in each block's shared memory
+    void* L;                    // one-reduction MGS: the rows of T = (I + L)^{-1}, L the strictly
+                                // lower part of Q^T Q (row i: its i entries left of the unit
+                                // diagonal, packed at i (i - 1) / 2), u_g; block 0 writes them
+    int jl;                     // rows 0 .. jl-1 of T are also kept in each block's shared memory
+    int sblock;                 // one-reduction MGS: 1 = the system's last block owns no rows and
+                                // runs the Givens rotations alone, publishing R, g (gpub) and the
+                                // residual estimate of column c (R's unused entry (kmax, c))
+    double* gpub;               // kmax + 2: g as that block leaves it
 };
 
 // Dynamic shared memory of the refinement kernel (ir_body's layout), sg =
 // sizeof(u_g): five double arrays of kmax + 2 (Givens, g, the current column,
 // y), the slice offsets of A and P, the block's rows of w (two blocks' rows
 // with a Gram-Schmidt group), and for the one-reduction MGS (orth 2) the rows
-// of w next to those of u, the reduced inner products, b / h, row j of L, the
-// unit partials and rows 0 .. jl-1 of L.
+// of w next to those of u, the reduced inner products, b, row j of L, the
+// unit partials (reused for row j of T and h), rows 0 .. jl-1 of T and the
+// table of segments per vector.
 inline size_t ir_smem_bytes(int64_t rb, int kmax, int g2, int orth, int jl, int sg)
 {
     const int64_t nsl = (rb + 31) >> 5;
     size_t b = sizeof(double) * 5 * (kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + (g2 ? 2 : 1) * rb * sg + 64;
     if (orth == 2)
         b += (size_t)sg * ((size_t)rb + 2 * (kmax + 1) + 2 * (kmax + 1) + 2 * (kmax + 1 + 32) +
-                           (size_t)jl * (jl - 1) / 2);
+                           (size_t)jl * (jl - 1) / 2) +
+             sizeof(int) * (kmax + 2) + 16;  // the unit-count table
     return b;
 }
 
-// rows of L kept in shared memory: as many as fit beside the rest, at most
+// rows of T kept in shared memory: as many as fit beside the rest, at most
 // kmax + 1, within 64 KiB
 inline int ir_pick_jl(int64_t rb, int kmax, size_t dyn_max, int sg)
 {
@@ -402,7 +409,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
     // the rotations of the Gram-Schmidt rounds run while its warp waits for the
     // other blocks
     const int GT = 0;
-    const int64_t r0 = (int64_t)bid * a.rb;
+    const int64_t r0 = min(a.n, (int64_t)bid * a.rb);  // a block past the last row owns none
     const int64_t r1 = min(a.n, r0 + a.rb);
     // modified Gram-Schmidt rows [m0, m1): the block's own rows, or with a
     // Gram-Schmidt group the rows of blocks 2b and 2b+1 (empty outside it)
@@ -525,6 +532,13 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             // column j are h = (I + L)^{-1} [Q_j^T w / r ; u_j^T w / r^2].  Three grid-wide
             // waits per iteration (after the first product, the reduction, and the
             // update that publishes u_{j+1}) instead of j + 3.
+            //
+            // The Givens rotations of column c (complete once iteration c+1 has
+            // r_{c+1} = h_{c+1,c}) run on thread GT during iteration c+2's inner
+            // products, which the other warps compute; the stop test follows them, so a
+            // solve that converges at column c has done one more product and inner-
+            // product pass than it uses.  The columns alternate between two buffers
+            // (hc, and yv until the back substitution).
             const int nwp = BT >> 5, lane = tid & 31, wid = tid >> 5;
             const int64_t rbl = r1 - r0;
             TG* wsm = ws + a.rb;                 // w for the block's rows
@@ -533,17 +547,76 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             TG* lrow = hv + (kmax + 1);          // row j of L (kmax + 1)
             TG* upa = lrow + (kmax + 1);         // unit partials (kmax + 33 each)
             TG* upc = upa + (kmax + 33);
-            TG* ltri = upc + (kmax + 33);        // rows 0 .. jl-1 of L, packed
-            TG* Lg = (TG*)a.L;                   // every row of L, packed (block 0 writes)
+            TG* ttri = upc + (kmax + 33);        // rows 0 .. jl-1 of T = (I + L)^{-1}, packed
+            TG* Tg = (TG*)a.L;                   // every row of T, packed (block 0 writes)
             TG* pv2 = (TG*)a.pvec;               // [value][block] block partials
+            double* colb[2] = {hc, yv};          // column c of H (entries 0..c+1) in colb[c & 1]
             auto tri = [](int i) -> int64_t { return (int64_t)i * (i - 1) / 2; };
-            auto lget = [&](int i, int kk) -> TG { return i < a.jl ? ltri[tri(i) + kk] : ldcg(&Lg[tri(i) + kk]); };
+            // T(i, m) for m < i (row i of T, written in iteration i)
+            auto tget = [&](int i, int m) -> TG { return i < a.jl ? ttri[tri(i) + m] : ldcg(&Tg[tri(i) + m]); };
+            // rotations 0..c-1 and the new rotation c on column c; g, the residual estimate
+            // (the entry that rotation q carries to rotation q+1 stays in a register: one
+            // dependent FP64 FMA per rotation; the rotated entries go to R from block 0)
+            auto givens = [&](int c) {
+                const double* h = colb[c & 1];
+                double x = h[0];
+#pragma unroll 4
+                for (int q = 0; q < c; q++) {
+                    const double csq = cs[q], snq = sn[q], hq1 = h[q + 1];
+                    const double out = fma(csq, x, snq * hq1);
+                    x = fma(-snq, x, csq * hq1);
+                    if (bid == 0 || a.sblock) a.R[(size_t)c * (kmax + 1) + q] = out;
+                }
+                const double hs = h[c + 1];
+                const double dn = sqrt(x * x + hs * hs);
+                if (dn == 0.0) { cs[c] = 1.0; sn[c] = 0.0; }
+                else { cs[c] = x / dn; sn[c] = hs / dn; }
+                g[c + 1] = -sn[c] * g[c];
+                g[c] = cs[c] * g[c];
+                sh->resid = fabs(g[c + 1]) / (double)beta;
+                if (bid == 0) a.R[(size_t)c * (kmax + 1) + c] = dn;
+                if (a.sblock) {
+                    // the rotating block publishes: the other blocks read these after the
+                    // next exchange round
+                    a.R[(size_t)c * (kmax + 1) + c] = dn;
+                    a.gpub[c] = g[c];
+                    a.gpub[c + 1] = g[c + 1];
+                    a.R[(size_t)c * (kmax + 1) + kmax] = sh->resid;
+                }
+            };
+            // with a rotating block (sblock) only it runs the rotations, and the row blocks'
+            // warp 0 joins the inner products
+            const bool rotates = !a.sblock || bid == G - 1;
             if (tid == GT) g[0] = (double)beta;
+            // units of the inner products: S row segments per vector, whole multiples of 32 VN
+            // rows (chunks), S chosen so that the busiest of the nwu warps finishes first, a
+            // unit costing its chunks plus about four chunks for its two warp reductions (at
+            // most kmax + 33 units: the partials' storage).  stab[nv] for nv = 1..kmax+1
+            // vectors, made once per solve (32-bit arithmetic; 64-bit division is slow here).
+            int* stab = reinterpret_cast<int*>(ttri + (size_t)a.jl * (a.jl - 1) / 2);
+            {
+                const int nwu = a.sblock ? nwp : nwp - 1;
+                const int ck = 32 * VN;
+                const int rows = (int)rbl;
+                const int smax = rows > 0 ? (rows + ck - 1) / ck : 1;
+                for (int nv = 1 + tid; nv <= kmax + 1; nv += BT) {
+                    int best = INT_MAX, sb = 1;
+                    for (int s2 = 1; s2 <= smax && nv * s2 <= kmax + 33; s2++) {
+                        const int segc = ((rows + s2 - 1) / s2 + ck - 1) / ck;
+                        const int cost = ((nv * s2 + nwu - 1) / nwu) * (segc + 4);
+                        if (cost < best) { best = cost; sb = s2; }
+                    }
+                    stab[nv] = sb;
+                }
+                __syncthreads();
+            }
             for (int j = 0; j <= kmax; j++) {
                 const bool prod = j < kmax;
+                // w = P (A u_j) (left) or A (P u_j) (right) in u_p, stored in u_g; u_j is read
+                // from the published wbuf (the first u_0 is z).  (Running the second product
+                // on warps 1.. beside the rotations of thread GT slowed both: the FP64
+                // instructions hold up their sub-partition.)
                 if (prod) {
-                    // w = P (A u_j) (left) or A (P u_j) (right) in u_p, stored in u_g; u_j is
-                    // read from the published wbuf (the first u_0 is z)
                     if (hasP) {
                         sell_rows<TP>(r0, r1, rightP ? sop : soa, rightP ? a.P.col : a.A.col, rightP ? pv : av,
                                       [&](int c) { return (TP)ldcg(&wbuf[c]); },
@@ -558,35 +631,64 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     }
                 }
                 __syncthreads();
-                // ---- block partials: units (vector i, row segment), vector j being u_j itself;
-                // a_i = q_i . u_j (a_j = ||u_j||^2) and c_i = q_i . w (c_j = u_j . w)
-                const int nv = j + 1;
-                const int S = nv >= nwp ? 1 : nwp / nv;
-                const int64_t segr = (((rbl + S - 1) / S) + 31) & ~int64_t(31);
-                for (int unit = wid; unit < nv * S; unit += nwp) {
-                    const int i = unit / S, sg = unit - i * S;
-                    const int64_t m0 = r0 + sg * segr, m1 = min(r1, m0 + segr);
-                    const TG* q = V + (int64_t)i * a.ldv;
-                    TG sa = TG(0), sc = TG(0);
-                    if (i < j) {
+                const int nv = j + 1, nwu = a.sblock ? nwp : nwp - 1;
+                const int64_t chunk = 32 * VN;
+                const int S = stab[nv];
+                if (!a.sblock && wid == 0) {
+                    if (tid == GT && j >= 2) givens(j - 2);
+                } else {
+                    if (tid == GT && j >= 2 && rotates) givens(j - 2);
+                    // ---- block partials: units (vector i, row segment), vector j being u_j
+                    // itself; a_i = q_i . u_j (a_j = ||u_j||^2), c_i = q_i . w (c_j = u_j . w).
+                    // Each lane reads VN consecutive rows per 16-byte load
+                    const int64_t segr = (((rbl + S - 1) / S) + chunk - 1) / chunk * chunk;
+                    for (int unit = wid - (a.sblock ? 0 : 1); unit < nv * S; unit += nwu) {
+                        const int i = unit / S, sg = unit - i * S;
+                        const int64_t m0 = r0 + sg * segr, m1 = min(r1, m0 + segr);
+                        const TG* q = V + (int64_t)i * a.ldv;
+                        TG sa = TG(0), sc = TG(0);
+                        if (i < j) {
 #pragma unroll 4
-                        for (int64_t row = m0 + lane; row < m1; row += 32) {
-                            const TG qv = __ldcg(q + row);
-                            sa = fma(qv, ws[row - r0], sa);
-                            sc = fma(qv, wsm[row - r0], sc);
+                            for (int64_t row = m0 + VN * lane; row < m1; row += chunk) {
+                                if (row + VN <= m1) {
+                                    const TV q4 = __ldcg(reinterpret_cast<const TV*>(q + row));
+                                    const TV u4 = *reinterpret_cast<const TV*>(ws + (row - r0));
+                                    const TV w4 = *reinterpret_cast<const TV*>(wsm + (row - r0));
+                                    TG qe[VN], ue[VN], we[VN];
+                                    memcpy(qe, &q4, sizeof(TV));
+                                    memcpy(ue, &u4, sizeof(TV));
+                                    memcpy(we, &w4, sizeof(TV));
+#pragma unroll
+                                    for (int e = 0; e < VN; e++) {
+                                        sa = fma(qe[e], ue[e], sa);
+                                        sc = fma(qe[e], we[e], sc);
+                                    }
+                                } else {
+                                    for (int e = 0; e < VN && row + e < m1; e++) {
+                                        const TG qv = __ldcg(q + row + e);
+                                        sa = fma(qv, ws[row + e - r0], sa);
+                                        sc = fma(qv, wsm[row + e - r0], sc);
+                                    }
+                                }
+                            }
+                        } else {
+                            for (int64_t row = m0 + VN * lane; row < m1; row += chunk) {
+                                for (int e = 0; e < VN && row + e < m1; e++) {
+                                    const TG uv = ws[row + e - r0];
+                                    sa = fma(uv, uv, sa);
+                                    sc = fma(uv, wsm[row + e - r0], sc);
+                                }
+                            }
                         }
-                    } else {
-                        for (int64_t row = m0 + lane; row < m1; row += 32) {
-                            const TG uv = ws[row - r0];
-                            sa = fma(uv, uv, sa);
-                            sc = fma(uv, wsm[row - r0], sc);
-                        }
+                        sa = warp_sum(sa);
+                        sc = warp_sum(sc);
+                        if (lane == 0) { upa[unit] = sa; upc[unit] = sc; }
                     }
-                    sa = warp_sum(sa);
-                    sc = warp_sum(sc);
-                    if (lane == 0) { upa[unit] = sa; upc[unit] = sc; }
                 }
                 __syncthreads();
+                // column j-2 converged: k = j-1 columns (this iteration's products are unused);
+                // with a rotating block the estimate is read after the exchange round below
+                if (!a.sblock && j >= 2 && sh->resid <= a.tau) { k = j - 1; break; }
                 for (int v = tid; v < 2 * nv; v += BT) {
                     const TG* src = v < nv ? upa : upc;
                     const int i = v < nv ? v : v - nv;
@@ -594,93 +696,113 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     for (int sg = 0; sg < S; sg++) acc += src[i * S + sg];
                     pv2[(size_t)v * G + bid] = acc;
                 }
-                // ---- the reduction over blocks; while thread 0 waits it applies the
-                // rotations 0..j-2 to column j-1 (its last rotation needs h_{j,j-1})
-                auto rot = [&]() {
-                    for (int q = 0; q + 1 < j; q++) {
-                        const double t0 = cs[q] * hc[q] + sn[q] * hc[q + 1];
-                        hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
-                        hc[q] = t0;
-                        if (bid == 0) a.R[(size_t)(j - 1) * (kmax + 1) + q] = hc[q];
+                // ---- the reduction over blocks (the partials published by an exchange round)
+                if (!xbar(a, sh)) return;
+                if (a.sblock && j >= 2 && __ldcg(&a.R[(size_t)(j - 2) * (kmax + 1) + kmax]) <= a.tau) {
+                    k = j - 1;
+                    break;
+                }
+                for (int v0 = wid; v0 < 2 * nv; v0 += 2 * nwp) {
+                    const int v1 = v0 + nwp;
+                    const bool two = v1 < 2 * nv;
+                    TG acc0 = TG(0), acc1 = TG(0);
+                    for (int b = lane; b < G; b += 32) {
+                        acc0 += ldcg(&pv2[(size_t)v0 * G + b]);
+                        if (two) acc1 += ldcg(&pv2[(size_t)v1 * G + b]);
                     }
-                };
-                if (!grid_sync(gbar, &sh->gepoch, &sh->ok, rot)) return;
-                for (int v = wid; v < 2 * nv; v += nwp) {
-                    TG acc = TG(0);
-                    for (int b = lane; b < G; b += 32) acc += ldcg(&pv2[(size_t)v * G + b]);
-                    acc = warp_sum(acc);
-                    if (lane == 0) sred[v] = acc;
+                    acc0 = warp_sum(acc0);
+                    acc1 = warp_sum(acc1);
+                    if (lane == 0) {
+                        sred[v0] = acc0;
+                        if (two) sred[v1] = acc1;
+                    }
                 }
                 __syncthreads();
                 const TG rr = j == 0 ? beta : sqrt(sred[j]);
-                bool stop = false;
-                if (j >= 1) {
-                    // column j-1 is complete: its last rotation, g, and the stop test
-                    if (tid == GT) {
-                        const int q = j - 1;
-                        hc[j] = (double)rr;
-                        const double dn = sqrt(hc[q] * hc[q] + hc[j] * hc[j]);
-                        if (dn == 0.0) { cs[q] = 1.0; sn[q] = 0.0; }
-                        else { cs[q] = hc[q] / dn; sn[q] = hc[j] / dn; }
-                        hc[q] = dn;
-                        g[j] = -sn[q] * g[q];
-                        g[q] = cs[q] * g[q];
-                        sh->resid = fabs(g[j]) / (double)beta;
-                        if (bid == 0) a.R[(size_t)q * (kmax + 1) + q] = hc[q];
-                    }
+                if (j >= 1 && tid == GT) colb[(j - 1) & 1][j] = (double)rr;  // h_{j,j-1}
+                if (j >= 1 && (rr == TG(0) || !prod)) {
+                    // breakdown or the iteration cap: column j-1 is the last one
+                    if (tid == GT && rotates) givens(j - 1);
                     __syncthreads();
                     k = j;
-                    if (rr == TG(0)) { flags |= 4; stop = true; }
-                    else if (sh->resid <= a.tau) stop = true;
+                    if (rr == TG(0)) flags |= 4;
+                    break;
                 }
-                if (stop || !prod) break;
-                // ---- row j of L and b = [c / r ; (u_j . w / r) / r]; then (I + L) h = b, the
-                // same in every block: per tile of 32 rows, the columns left of the tile
-                // (one warp per row), then the tile's own triangle (warp 0, column order)
+                if (!prod) break;  // kmax = 0
+                // ---- row j of L and b = [c / r ; (u_j . w / r) / r]; h = (I + L)^{-1} b, the same
+                // in every block.  T = (I + L)^{-1} grows by one row per iteration, t_j =
+                // -l_j^T T (row j of (I + L) T = I), so h = T b is a matrix-vector product (one
+                // warp per entry) instead of a forward substitution; both give MGS's
+                // coefficients.  trow = t_j, hout = h (the unit partials' storage, free here).
+                TG* trow = upa;
+                TG* hout = upc;
                 for (int i = tid; i < j; i += BT) {
-                    const TG l = sred[i] / rr;
-                    lrow[i] = l;
-                    if (j < a.jl) ltri[tri(j) + i] = l;
-                    if (bid == 0) Lg[tri(j) + i] = l;
+                    lrow[i] = sred[i] / rr;
                     hv[i] = sred[nv + i] / rr;
                 }
                 if (tid == 0) hv[j] = (sred[2 * nv - 1] / rr) / rr;
                 __syncthreads();
-                for (int t0 = 0; t0 <= j; t0 += 32) {
-                    if (t0 > 0) {
-                        for (int i = t0 + wid; i <= j && i < t0 + 32; i += nwp) {
-                            TG acc = TG(0);
-                            for (int kk = lane; kk < t0; kk += 32) acc = fma(i == j ? lrow[kk] : lget(i, kk), hv[kk], acc);
-                            acc = warp_sum(acc);
-                            if (lane == 0) hv[i] -= acc;
+                for (int e = wid; e < 2 * j; e += nwp) {
+                    TG acc = TG(0);
+                    if (e < j) {
+                        // t_{j,m} = -sum_{m <= k < j} l_{j,k} T(k, m), T(m, m) = 1
+                        const int m = e;
+                        for (int kk = m + lane; kk < j; kk += 32) acc = fma(lrow[kk], kk == m ? TG(1) : tget(kk, m), acc);
+                        acc = warp_sum(acc);
+                        if (lane == 0) {
+                            trow[m] = -acc;
+                            if (j < a.jl) ttri[tri(j) + m] = -acc;
+                            if (bid == 0) Tg[tri(j) + m] = -acc;
                         }
-                        __syncthreads();
+                    } else {
+                        // h_i = b_i + sum_{m < i} T(i, m) b_m
+                        const int i = e - j;
+                        for (int m = lane; m < i; m += 32) acc = fma(tget(i, m), hv[m], acc);
+                        acc = warp_sum(acc);
+                        if (lane == 0) hout[i] = hv[i] + acc;
                     }
-                    if (wid == 0) {
-                        const int i = t0 + lane;
-                        TG hi = i <= j ? hv[i] : TG(0);
-                        for (int c = 0; c < 32 && t0 + c < j; c++) {
-                            const TG hcol = __shfl_sync(0xffffffffu, hi, c);
-                            if (i > t0 + c && i <= j) hi = fma(-(i == j ? lrow[t0 + c] : lget(i, t0 + c)), hcol, hi);
-                        }
-                        if (i <= j) hv[i] = hi;
-                    }
-                    __syncthreads();
                 }
-                if (tid == GT)
-                    for (int i = 0; i <= j; i++) hc[i] = (double)hv[i];
+                __syncthreads();
+                if (wid == 0) {
+                    TG acc = TG(0);
+                    for (int m = lane; m < j; m += 32) acc = fma(trow[m], hv[m], acc);
+                    acc = warp_sum(acc);
+                    if (lane == 0) hout[j] = hv[j] + acc;
+                }
+                __syncthreads();
+                {
+                    double* hj = colb[j & 1];
+                    for (int i = tid; i <= j; i += BT) hj[i] = (double)hout[i];
+                }
                 // ---- q_j = u_j / r into V, and u_{j+1} = w / r - Q_{j+1} h (the block's rows,
                 // published for the next product)
+                // (a thread's two rows share the loop over the basis: twice the loads in flight)
                 TG* Vj = V + (int64_t)j * a.ldv;
-                for (int64_t row = r0 + tid; row < r1; row += BT) {
-                    const TG qj = ws[row - r0] / rr;
-                    Vj[row] = qj;
-                    TG acc = wsm[row - r0] / rr;
-#pragma unroll 8
-                    for (int i = 0; i < j; i++) acc = fma(-hv[i], __ldcg(V + (int64_t)i * a.ldv + row), acc);
-                    acc = fma(-hv[j], qj, acc);
-                    ws[row - r0] = acc;
-                    wbuf[row] = acc;
+                for (int64_t ra = r0 + tid; ra < r1; ra += 2 * BT) {
+                    const int64_t rb2 = ra + BT;
+                    const bool hb = rb2 < r1;
+                    const TG qa = ws[ra - r0] / rr;
+                    const TG qb = hb ? ws[rb2 - r0] / rr : TG(0);
+                    Vj[ra] = qa;
+                    if (hb) Vj[rb2] = qb;
+                    TG acca = wsm[ra - r0] / rr;
+                    TG accb = hb ? wsm[rb2 - r0] / rr : TG(0);
+                    const int64_t rbx = hb ? rb2 : ra;  // an in-range row for the second load
+#pragma unroll 4
+                    for (int i = 0; i < j; i++) {
+                        const TG* Vi = V + (int64_t)i * a.ldv;
+                        const TG h = hout[i];
+                        acca = fma(-h, __ldcg(Vi + ra), acca);
+                        accb = fma(-h, __ldcg(Vi + rbx), accb);
+                    }
+                    acca = fma(-hout[j], qa, acca);
+                    ws[ra - r0] = acca;
+                    wbuf[ra] = acca;
+                    if (hb) {
+                        accb = fma(-hout[j], qb, accb);
+                        ws[rb2 - r0] = accb;
+                        wbuf[rb2] = accb;
+                    }
                 }
                 if (!xbar(a, sh)) return;
             }
@@ -942,7 +1064,10 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
         }
         if (beta > TG(0)) {
             // ---- y = R^{-1} g (double), d = V y in u_g, x = x + d in u
-            if (!xbar(a, sh)) return;  // R columns from block 0
+            if (!xbar(a, sh)) return;  // R columns from block 0 (or the rotating block)
+            if (LS && a.sblock)
+                for (int t = tid; t <= k; t += BT) g[t] = __ldcg(&a.gpub[t]);
+            __syncthreads();
             if (tid < 32) {
                 for (int t = tid; t < k; t += 32) yv[t] = g[t];
                 __syncwarp();
