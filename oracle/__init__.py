@@ -74,6 +74,7 @@ def lib():
             _lib.orc_chop_half.argtypes = [C.c_double]
             _lib.orc_round.restype = C.c_double
             _lib.orc_round.argtypes = [C.c_double, C.c_int]
+            _lib.orc_dot.restype = C.c_double
         return _lib
 
 
@@ -110,6 +111,13 @@ def half_ops(a, b, op: int):
     out = np.empty_like(a)
     lib().orc_half_ops(C.c_int(a.size), _p(a, C.c_double), _p(b, C.c_double), C.c_int(op), _p(out, C.c_double))
     return out
+
+
+def dot(x, y, p="double", mode=MODE_PEROP):
+    """Inner product in precision p as every step of the oracle forms it."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return lib().orc_dot(C.c_int(len(x)), _p(x, C.c_double), _p(y, C.c_double), C.c_int(prec(p)), C.c_int(mode))
 
 
 def dense_ls(Abar, ebar, uf="double", mode=MODE_ACC32):

@@ -23,6 +23,16 @@
  * single) rounded to p equals the correctly rounded p-result, because 53 >=
  * 2*24 + 2.  The file must be compiled with -ffp-contract=off.
  *
+ * Inner products.  Section 4 runs single and double as the built-in
+ * datatypes, whose vector reductions are library routines rather than one
+ * left-to-right chain; the oracle takes pairwise summation, the textbook
+ * model of such a reduction: sum(a[0..n)) = sum(a[0..n/2)) + sum(a[n/2..n)),
+ * every product and every addition rounded to the precision (error bound
+ * gamma_{ceil(log2 n)+1} sum |x_i y_i|).  Half (the chop simulation) keeps
+ * the per-operation left-to-right chain.  With a strict chain of 262,144
+ * single-precision additions the Arnoldi basis of the 64^3 system lost all
+ * orthogonality within 60 steps, unlike any single-precision library.
+ *
  * Two SPAI arithmetic modes:
  *   MODE_PEROP : every operation rounded to u_f (the paper's model);
  *   MODE_ACC32 : at u_f = half, stored values are rounded to half but every
@@ -144,10 +154,25 @@ double orc_round(double x, int p) { return rnd(x, p); }
 /* Inner products in a precision under a mode                          */
 /* ------------------------------------------------------------------ */
 
-/* sum_i x[i*sx] * y[i*sy] computed in precision p. */
+/* Pairwise sum of the products x[i*sx] * y[i*sy], i in [0, len), each
+ * product and each addition rounded to p. */
+static double dot_pairwise(const double* x, int sx, const double* y, int sy, int len, int p)
+{
+    if (len <= 0) return 0.0;
+    if (len == 1) return rnd(x[0] * y[0], p);
+    int m = len / 2;
+    double a = dot_pairwise(x, sx, y, sy, m, p);
+    double b = dot_pairwise(x + (size_t)m * sx, sx, y + (size_t)m * sy, sy, len - m, p);
+    return rnd(a + b, p);
+}
+
+/* sum_i x[i*sx] * y[i*sy] computed in precision p: pairwise in single and
+ * double, a left-to-right chain in half (per operation, or accumulated in
+ * binary32 and rounded once under MODE_ACC32). */
 static double dot_p(const double* x, int sx, const double* y, int sy, int len, int p, int mode)
 {
-    if (p == PH && mode == MODE_ACC32) {
+    if (p != PH) return dot_pairwise(x, sx, y, sy, len, p);
+    if (mode == MODE_ACC32) {
         float acc = 0.0f;
         for (int i = 0; i < len; i++) {
             float t = (float)x[(size_t)i * sx] * (float)y[(size_t)i * sy];
@@ -929,6 +954,11 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
 }
 
 /* Exported single steps, used by the oracle's own pins. */
+double orc_dot(int len, const double* x, const double* y, int p, int mode)
+{
+    return dot_p(x, 1, y, 1, len, p, mode);
+}
+
 void orc_spmv(int n, const int64_t* rp, const int* ci, const double* mv, const double* x, int p,
               int mode, double* y)
 {

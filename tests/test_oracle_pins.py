@@ -754,3 +754,46 @@ def test_ir_stagnation_stops_without_convergence():
     assert R["steps"] == want
     assert R["status"] & O.IR_STAGNATED and not R["status"] & O.IR_CONVERGED
     np.testing.assert_array_equal(R["x"], X[want])
+
+
+
+def _pairwise_f32(t):
+    # the pairwise order written out with numpy float32 arithmetic (each add rounded)
+    if len(t) == 1:
+        return t[0]
+    m = len(t) // 2
+    return np.float32(_pairwise_f32(t[:m]) + _pairwise_f32(t[m:]))
+
+
+def test_inner_products_single_are_pairwise():
+    # single-precision inner products: rounded products summed pairwise, bit for bit
+    rng = np.random.default_rng(17)
+    for n in (1, 2, 3, 7, 64, 1000, 4097):
+        x = rng.normal(size=n).astype(np.float32).astype(np.float64)
+        y = rng.normal(size=n).astype(np.float32).astype(np.float64)
+        t = (x.astype(np.float32) * y.astype(np.float32)).astype(np.float32)
+        assert O.dot(x, y, "single") == float(_pairwise_f32(list(t))), n
+    # a case where the order matters: 1 + 4 * 2^-25 is 1 left to right, 1 + 2^-23 pairwise
+    x = np.array([1.0, 2.0 ** -25, 2.0 ** -25, 2.0 ** -25, 2.0 ** -25])
+    assert O.dot(x, np.ones(5), "single") == 1.0 + 2.0 ** -23
+
+
+def test_inner_product_error_bounds():
+    # pairwise: |error| <= gamma_{ceil(log2 n)+1} sum |x_i y_i| (Higham, Accuracy and Stability,
+    # eq. (4.6) with the product's rounding); double is checked against the exact (fsum) value
+    import math
+    rng = np.random.default_rng(3)
+    for n, p in ((262144, "single"), (100000, "double"), (5000, "single")):
+        u = O.UNIT_ROUNDOFF[O.prec(p)]
+        x = rng.normal(size=n)
+        y = rng.normal(size=n)
+        if p == "single":
+            x = x.astype(np.float32).astype(np.float64)
+            y = y.astype(np.float32).astype(np.float64)
+        exact = math.fsum(x * y)  # products of single values are exact in double
+        k = math.ceil(math.log2(n)) + 1
+        gamma = k * u / (1 - k * u)
+        bound = gamma * np.sum(np.abs(x * y))
+        if p == "double":
+            bound += 2.0 ** -53 * np.sum(np.abs(x * y))  # x*y themselves rounded in double
+        assert abs(O.dot(x, y, p) - exact) <= bound, (n, p)
