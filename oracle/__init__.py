@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -78,6 +78,11 @@ def lib():
         return _lib
 
 
+def set_threads(n: int = 0) -> int:
+    """Threads of the SPAI column loop (0: keep); returns the number in use."""
+    return int(lib().orc_set_threads(C.c_int(int(n))))
+
+
 def _p(a, ctype):
     return a.ctypes.data_as(C.POINTER(ctype))
 
@@ -100,9 +105,10 @@ def chop_half(x):
 
 
 def round_to(x, p):
-    L = lib()
-    x = np.asarray(x, dtype=np.float64)
-    return np.vectorize(lambda v: L.orc_round(v, prec(p)), otypes=[np.float64])(x)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    lib().orc_round_array(C.c_int64(x.size), _p(x, C.c_double), C.c_int(prec(p)), _p(out, C.c_double))
+    return out
 
 
 def half_ops(a, b, op: int):

@@ -82,6 +82,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define PH 0 /* half,   u = 2^-11  */
 #define PS 1 /* single, u = 2^-24  */
@@ -149,6 +152,12 @@ static double rnd(double x, int p)
 }
 
 double orc_round(double x, int p) { return rnd(x, p); }
+
+/* out[i] = x[i] rounded to p, i < n */
+void orc_round_array(int64_t n, const double* x, int p, double* out)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = rnd(x[i], p);
+}
 
 /* ------------------------------------------------------------------ */
 /* Inner products in a precision under a mode                          */
@@ -430,6 +439,10 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
     size_t capI = (size_t)F * maxrow + 2;
     size_t capJ0 = (size_t)maxcol * maxcol + (size_t)F + 2;
     size_t capC = capI * (size_t)(maxcol + 1) + 2;
+    /* the columns are independent (Section 2.2): with OpenMP they are shared
+     * among threads, each with scratch of its own; no arithmetic changes */
+#pragma omp parallel
+    {
     int* J = (int*)malloc(sizeof(int) * (capJ0 > (size_t)F ? capJ0 : (size_t)F + 2));
     int* I = (int*)malloc(sizeof(int) * capI);
     int* cand = (int*)malloc(sizeof(int) * capC);
@@ -439,6 +452,7 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
     double* ebar = (double*)malloc(sizeof(double) * capI);
     double* mb = (double*)malloc(sizeof(double) * (size_t)F);
     double* sb = (double*)malloc(sizeof(double) * capI);
+#pragma omp for schedule(dynamic, 64)
     for (int t = 0; t < total; t++) {
         int k = (cols && ncols > 0) ? cols[t] : t;
         /* initial pattern J_k (R10), capped (R6) */
@@ -524,8 +538,10 @@ int orc_spai(int n, const int64_t* rp, const int* ci, const double* val, const o
         }
         colres64[k] = sqrt(acc);
     }
-    free(cp); free(ri); free(J); free(I); free(cand); free(rho); free(sel);
+    free(J); free(I); free(cand); free(rho); free(sel);
     free(Abar); free(ebar); free(mb); free(sb);
+    }
+    free(cp); free(ri);
     return 0;
 }
 
@@ -951,6 +967,18 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
     (void)ur_b;
     free(r); free(dd); free(ur_b);
     return status;
+}
+
+/* Threads of the SPAI column loop (OpenMP); returns the number in use. */
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }
 
 /* Exported single steps, used by the oracle's own pins. */

@@ -797,3 +797,23 @@ def test_inner_product_error_bounds():
         if p == "double":
             bound += 2.0 ** -53 * np.sum(np.abs(x * y))  # x*y themselves rounded in double
         assert abs(O.dot(x, y, p) - exact) <= bound, (n, p)
+
+
+def test_spai_threads_do_not_change_results():
+    # the SPAI columns are independent: any number of threads gives the same bits
+    A = synth.random_sparse(600, 8, seed=4, log10_scale=2.0)
+    out = []
+    for th in (1, 4):
+        O.set_threads(th)
+        out.append(O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=0.3, max_fill=20, uf="single"))
+    O.set_threads(0)
+    for key in ("Jcnt", "Jidx", "mbar", "colres", "colres64", "flags", "nsolve", "Icnt"):
+        assert np.array_equal(out[0][key], out[1][key]), key
+
+
+def test_round_to_matches_scalar_rounding():
+    x = np.random.default_rng(1).normal(size=1000) * 10.0 ** np.random.default_rng(2).uniform(-8, 6, size=1000)
+    for p in ("half", "single", "double"):
+        r = O.round_to(x, p)
+        assert all(r[i] == O.lib().orc_round(float(x[i]), O.prec(p)) for i in range(0, 1000, 7))
+    np.testing.assert_array_equal(O.round_to(x, "single"), x.astype(np.float32).astype(np.float64))
