@@ -311,7 +311,7 @@ static void transpose_structure(int n, const int64_t* rp, const int* ci, int64_t
 }
 
 /* order for the fill cap (R6): k first, then by |j-k|, then by j */
-static int g_cap_k;
+static _Thread_local int g_cap_k; /* the column of the qsort in apply_cap (per thread) */
 static int cmp_cap(const void* a, const void* b)
 {
     int x = *(const int*)a, y = *(const int*)b;

@@ -800,15 +800,19 @@ def test_inner_product_error_bounds():
 
 
 def test_spai_threads_do_not_change_results():
-    # the SPAI columns are independent: any number of threads gives the same bits
-    A = synth.random_sparse(600, 8, seed=4, log10_scale=2.0)
-    out = []
-    for th in (1, 4):
-        O.set_threads(th)
-        out.append(O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=0.3, max_fill=20, uf="single"))
-    O.set_threads(0)
-    for key in ("Jcnt", "Jidx", "mbar", "colres", "colres64", "flags", "nsolve", "Icnt"):
-        assert np.array_equal(out[0][key], out[1][key]), key
+    # the SPAI columns are independent: any number of threads gives the same bits, for
+    # adaptive patterns and for fixed patterns cut by the fill cap
+    cases = [(synth.random_sparse(600, 8, seed=4, log10_scale=2.0),
+              dict(init=O.PAT_IDENTITY, adaptive=True, eps=0.3, max_fill=20, uf="single")),
+             (synth.conv_diff_3d((7, 6, 5), 50.0, seed=8), dict(init=O.PAT_A2, max_fill=9, uf="half", eps=0.0))]
+    for A, kw in cases:
+        out = []
+        for th in (1, 4):
+            O.set_threads(th)
+            out.append(O.spai(A, **kw))
+        O.set_threads(0)
+        for key in ("Jcnt", "Jidx", "mbar", "colres", "colres64", "flags", "nsolve", "Icnt"):
+            assert np.array_equal(out[0][key], out[1][key]), key
 
 
 def test_round_to_matches_scalar_rounding():
