@@ -8,9 +8,11 @@ the first step whose additions leave J_g.  There the two runs took a
 different decision on nearly equal scores: the returned gap is the smallest
 distance, relative to the mean rho of that step, between the rho of an index
 the oracle added but the GPU did not and either the rho of an index the GPU
-added instead or the acceptance threshold (the mean).  A path that never
-leaves J_g but stops earlier (the column criterion ||s|| <= eps) returns the
-relative distance of ||s|| to eps.
+added instead or the acceptance threshold (the mean); where the oracle found
+no candidate at or below the mean but the GPU went on, the distance of the
+GPU's additions to the mean.  A path that never leaves J_g but stops earlier
+(the column criterion ||s|| <= eps) returns the relative distance of ||s||
+to eps.
 """
 import numpy as np
 
@@ -65,6 +67,16 @@ def replay_gap(A, d, k, J_gpu, uf, eps, beta, max_fill, alpha=None, colsA=None):
             return None
         rho = O.rho(A, d, I, s, cand, uf)
         sel = O.select(cand, rho, min(beta, max_fill - len(J)), uf)
+        if len(sel) == 0:
+            # no candidate at or below the mean: the oracle stops here; if the GPU went
+            # on, it accepted an index whose rho ties with the mean
+            if set(J) == Jg:
+                return None
+            mean = float(np.mean(rho))
+            r = dict(zip((int(c) for c in cand), rho))
+            ext = [r[j] for j in Jg if j in r]
+            gap = min((abs(v - mean) for v in ext), default=np.inf)
+            return ("threshold", gap / mean if mean > 0 else np.inf)
         if not set(int(x) for x in sel) <= Jg:
             mean = float(np.mean(rho))
             r = dict(zip((int(c) for c in cand), rho))
