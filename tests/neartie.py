@@ -1,18 +1,22 @@
 """Near-tie analysis of adaptive SPAI columns whose patterns differ between
 the CUDA path and the oracle (reading R12 of the selection rule).
 
-For a column k whose GPU pattern J_g differs from the oracle's, the oracle's
-Grote-Huckle path is replayed step by step with the oracle's own exported
-steps (the dense least squares, rho and the selection of Algorithm 1) until
-the first step whose additions leave J_g.  There the two runs took a
-different decision on nearly equal scores: the returned gap is the smallest
-distance, relative to the mean rho of that step, between the rho of an index
-the oracle added but the GPU did not and either the rho of an index the GPU
-added instead or the acceptance threshold (the mean); where the oracle found
-no candidate at or below the mean but the GPU went on, the distance of the
-GPU's additions to the mean.  A path that never leaves J_g but stops earlier
-(the column criterion ||s|| <= eps) returns the relative distance of ||s||
-to eps.
+Both sides score the candidates of a Grote-Huckle step by rho_j computed
+from their own least-squares residual, so the two scores of one candidate
+differ by rounding; where two decisions are that close the sides may take
+different ones, and their patterns differ from then on.  For a column k
+whose GPU pattern J_g differs from the oracle's, the oracle's path is
+replayed step by step with the oracle's own exported steps (the dense least
+squares, rho and the selection of Algorithm 1).  The GPU's intermediate
+patterns are not known, so the replay covers the stretch of the oracle's
+path that is consistent with J_g: from the first step up to and including
+the first step whose additions leave J_g (or the oracle's last step).  On
+that stretch every decision's margin is measured, relative to the step's
+mean rho: the selection boundary (the largest rho taken against the
+smallest acceptable rho left out), the acceptance threshold (the mean
+against the nearest rho on either side) and the column criterion
+(||s|| against eps, relative to eps).  The smallest margin is returned: a
+pattern mismatch is explained by rounding only if it is small.
 """
 import numpy as np
 
@@ -30,6 +34,9 @@ def _col_lists(A):
 
 
 def replay_gap(A, d, k, J_gpu, uf, eps, beta, max_fill, alpha=None, colsA=None):
+    """Smallest decision margin on the oracle's path consistent with J_gpu:
+    (kind, margin, step), kind in {"selection", "threshold", "criterion"};
+    None when the oracle's own pattern equals J_gpu."""
     rp, ci, va = A
     n = len(rp) - 1
     if alpha is None:
@@ -38,6 +45,13 @@ def replay_gap(A, d, k, J_gpu, uf, eps, beta, max_fill, alpha=None, colsA=None):
         colsA = _col_lists(A)
     Jg = set(int(j) for j in J_gpu)
     J = [int(k)]
+    best = None
+
+    def note(kind, margin, step):
+        nonlocal best
+        if best is None or margin < best[1]:
+            best = (kind, float(margin), step)
+
     for step in range(alpha + 1):
         I = set([int(k)])
         for j in J:
@@ -54,39 +68,35 @@ def replay_gap(A, d, k, J_gpu, uf, eps, beta, max_fill, alpha=None, colsA=None):
         Ab = O.round_to(Ab, uf) if O.prec(uf) != O.DOUBLE else Ab
         e = (I == k).astype(float)
         _, s, sn, _ = O.dense_ls(Ab, e, uf)
-        if sn <= eps:
-            return ("converged", abs(sn - eps) / eps) if set(J) != Jg else None
-        if step == alpha or len(J) >= max_fill:
-            return None
+        note("criterion", abs(sn - eps) / eps, step)
+        if sn <= eps or step == alpha or len(J) >= max_fill:
+            break
         cand = set()
         for t, l in enumerate(I):
             if s[t] != 0.0:
                 cand.update(colsA[l])
         cand = np.array(sorted(cand - set(J)), dtype=np.int32)
         if len(cand) == 0:
-            return None
+            break
         rho = O.rho(A, d, I, s, cand, uf)
-        sel = O.select(cand, rho, min(beta, max_fill - len(J)), uf)
-        if len(sel) == 0:
-            # no candidate at or below the mean: the oracle stops here; if the GPU went
-            # on, it accepted an index whose rho ties with the mean
-            if set(J) == Jg:
-                return None
-            mean = float(np.mean(rho))
-            r = dict(zip((int(c) for c in cand), rho))
-            ext = [r[j] for j in Jg if j in r]
-            gap = min((abs(v - mean) for v in ext), default=np.inf)
-            return ("threshold", gap / mean if mean > 0 else np.inf)
-        if not set(int(x) for x in sel) <= Jg:
-            mean = float(np.mean(rho))
-            r = dict(zip((int(c) for c in cand), rho))
-            X = [int(x) for x in sel if int(x) not in Jg]
-            Y = [j for j in Jg if j in r and j not in J and j not in set(int(x) for x in sel)]
-            gap = np.inf
-            for x in X:
-                gap = min(gap, abs(r[x] - mean))
-                for y in Y:
-                    gap = min(gap, abs(r[x] - r[y]))
-            return ("selection", gap / mean if mean > 0 else np.inf)
-        J = sorted(set(J) | set(int(x) for x in sel))
-    return None
+        mean = float(np.mean(rho))
+        scale = mean if mean > 0 else 1.0
+        nmax = min(beta, max_fill - len(J))
+        sel = [int(x) for x in O.select(cand, rho, nmax, uf)]
+        r = dict(zip((int(c) for c in cand), rho))
+        taken = [r[j] for j in sel]
+        left = sorted(r[int(c)] for c in cand if int(c) not in sel and r[int(c)] <= mean)
+        if taken and left and len(sel) == nmax:
+            note("selection", abs(left[0] - max(taken)) / scale, step)
+        below = [v for v in rho if v <= mean]
+        above = [v for v in rho if v > mean]
+        if below:
+            note("threshold", abs(mean - max(below)) / scale, step)
+        if above:
+            note("threshold", abs(min(above) - mean) / scale, step)
+        if not sel or not set(sel) <= Jg:
+            break  # the oracle stops here, or its path leaves J_g
+        J = sorted(set(J) | set(sel))
+    if set(J) == Jg:
+        return None
+    return best

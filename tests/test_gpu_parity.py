@@ -157,13 +157,13 @@ def test_spai_explicit_zeros_parity(ctx, uf):
 
 
 # A column may select a different pattern than the oracle only where the two
-# runs' scores tie to rounding (reading R12): at the first diverging step the
-# rho of an index one side added lies within NEAR_TIE * u_f * (mean rho) of the
-# rho of the index the other side added instead, or of the acceptance
-# threshold.  Both sides compute rho from their own residual s, whose entries
-# differ by the rounding of the QR (a few u_f times the condition of the tile),
-# so the allowance is a few hundred u_f rather than the few u_f of one rho
-# evaluation.
+# runs' scores tie to rounding (reading R12): on the stretch of the oracle's
+# path consistent with the GPU's pattern some decision (the selection boundary,
+# the acceptance threshold or the column criterion) has a margin within
+# NEAR_TIE * u_f of the step's mean rho (tests/neartie.py).  Both sides compute
+# rho from their own residual s, whose entries differ by the rounding of the QR
+# (a few u_f times the condition of the tile), so the allowance is a few
+# hundred u_f rather than the few u_f of one rho evaluation.
 NEAR_TIE = 512
 
 
@@ -178,9 +178,9 @@ def check_mismatches_are_near_ties(A, d, cols, J_gpu, J_orc, uf, eps, beta, F):
         cnt += 1
         r = replay_gap(A, d, int(k), Jg, uf, eps, beta, F)
         assert r is not None, (k, Jg, Jo)
-        kind, gap = r
+        kind, gap, step = r
         if gap > NEAR_TIE * u:
-            bad.append((int(k), kind, gap / u))
+            bad.append((int(k), kind, step, gap / u))
     print("pattern mismatches: %d of %d columns, none beyond %d u_f" % (cnt, len(cols), NEAR_TIE))
     assert not bad, bad
     return cnt

@@ -84,7 +84,7 @@ def check_sampled_columns(A, P_csr, ref, cols, uf, adaptive=None):
             r = replay_gap(A, d, int(k), g, uf, eps, beta, F)
             assert r is not None, (k, g, o)
             if r[1] > NEAR_TIE * u:
-                bad.append((int(k), r[0], r[1] / u))
+                bad.append((int(k), r[0], r[2], r[1] / u))
         print("pattern mismatches: %d of %d sampled columns" % (int((~same).sum()), len(cols)))
         assert not bad, bad
     cols = np.asarray(cols)
@@ -130,6 +130,96 @@ def test_bench_workload_full_size(ctx):
     assert abs(r["final_nbe"] - nbe) <= 0.5 * nbe  # the kernel's own estimate (single-precision iterate)
     assert np.max(np.abs(x - x_true)) / np.max(np.abs(x_true)) < 1e-4
     P.free()
+
+
+def check_ir_against_oracle(A, b, x_true, x, st, ref, u):
+    """Same number of refinement steps, total GMRES iterations within 10%,
+    normwise backward and forward errors within 10x of the oracle's."""
+    Ms = synth.to_scipy(A)
+    assert st["steps"] == ref["steps"], (st["its"], list(ref["its"]))
+    assert abs(st["total_its"] - ref["total_its"]) <= max(1, 0.1 * ref["total_its"]), (st["its"], list(ref["its"]))
+    def errs(xx):
+        nbe = np.max(np.abs(b - Ms @ xx)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(xx)) + np.max(np.abs(b)))
+        return nbe, np.max(np.abs(xx - x_true)) / np.max(np.abs(x_true))
+    nb_g, fe_g = errs(x)
+    nb_o, fe_o = errs(ref["x"])
+    assert nb_g <= 10 * max(nb_o, u) and fe_g <= 10 * max(fe_o, u), (nb_g, nb_o, fe_g, fe_o)
+
+
+@pytest.mark.parametrize("orth", [2, 0])
+def test_bench_workload_refinement_full_size(ctx, orth):
+    """The 64^3 bench workload solved in the launch configuration bench.py times,
+    against a full oracle solve of the same system (every SPAI column, then the
+    refinement): every column's residual within the half-precision tolerance,
+    and the refinement's steps, iterations and errors (one-reduction MGS, the
+    headline's, and the MGS exchange rounds)."""
+    A, b, x_true = synth.cfg_large_3d(N=64)
+    Ad = tuple(torch.from_numpy(a).cuda() for a in A)
+    so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3)
+    P, st = S.spai_build(ctx, Ad, so, per_column=True)
+    Pc = P.export()
+    O.set_threads(0)
+    ref_s = O.spai(A, init=O.PAT_A2, max_fill=25, uf="half", eps=0.3)
+    assert np.array_equal(np.diff(Pc[0]), ref_s["Jcnt"])
+    assert np.array_equal(st["nI"], ref_s["Icnt"])
+    # every column: float64 residuals of both sides' m_k within 1e-3 relative plus the
+    # u_f representation floor, 99% within the pure relative tolerance
+    Ms = synth.to_scipy(A)
+    d = ref_s["d"]
+    n = len(b)
+    B = (Ms.T @ sp.diags(d)).tocsc()
+    rows = np.repeat(np.arange(n), np.diff(Pc[0]))
+    Mg = sp.csr_matrix((Pc[2] / d[Pc[1]], (Pc[1], rows)), shape=(n, n))
+    mask = np.arange(25)[None, :] < ref_s["Jcnt"][:, None]
+    Mo = sp.csr_matrix((ref_s["mbar"][mask], (ref_s["Jidx"][mask], np.repeat(np.arange(n), ref_s["Jcnt"]))),
+                       shape=(n, n))
+    def colnorm(M):
+        return np.sqrt(np.asarray(M.multiply(M).sum(axis=0)).ravel())
+    rg = colnorm((B @ Mg - sp.identity(n)).tocsc())
+    ro = colnorm((B @ Mo - sp.identity(n)).tocsc())
+    ag = colnorm((abs(B) @ abs(Mg)).tocsc())
+    floor = (4 * 2.0 ** -11 + 64 * 2.0 ** -53) * ag
+    diff = np.abs(rg - ro)
+    assert np.all(diff <= RES_TOL["half"] * ro + floor), np.max(diff - RES_TOL["half"] * ro - floor)
+    assert np.mean(diff <= RES_TOL["half"] * ro) >= 0.99
+    # the refinement
+    kw = dict(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4)
+    io = S.make_ir_opts(orth=orth, **kw)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    r = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io)
+    ref = O.gmres_ir(A, b, O.assemble_P(ref_s, "single", "half"), orth=orth, **kw)
+    check_ir_against_oracle(A, b, x_true, xd.cpu().numpy(), r, ref, 2.0 ** -24)
+    P.free()
+
+
+def test_adaptive_ill_conditioned_refinement():
+    """A random nonsymmetric system in the style of the ill-conditioned stress
+    configuration: n = 10,000, 16 nonzeros per column, row and column scalings of
+    up to 10^3 each; Grote-Huckle SPAI from the identity (eps 0.5, beta 8, cap 30,
+    u_f single) and the refinement with (single, double, double, double, quad),
+    whose GMRES solves run to their 500-iteration cap.  Against the oracle: the
+    patterns up to near-ties of rho, and the refinement's steps, iterations and
+    errors (modified Gram-Schmidt, the paper's method)."""
+    c = S.Context(0)
+    A = synth.random_sparse(10000, 16, seed=6, log10_scale=6.0)
+    b, x_true = synth.rhs(A, seed=7)
+    so = S.make_spai_opts(init=0, adaptive=True, eps=0.5, beta=8, max_fill=30, uf="single")
+    P, st = S.spai_build(c, A, so, per_column=True)
+    O.set_threads(0)
+    ref_s = O.spai(A, init=O.PAT_IDENTITY, adaptive=True, eps=0.5, beta=8, max_fill=30, uf="single")
+    Pc = P.export()
+    cols = np.arange(0, 10000, 7)
+    check_sampled_columns(A, Pc, ref_s, cols, "single", adaptive=(0.5, 8, 30))
+    kw = dict(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8)
+    x = np.zeros_like(b)
+    r = S.gmres_ir_solve(c, A, b, x, P=P, opts=S.make_ir_opts(**kw))
+    # the oracle refines with its own preconditioner (near-tie columns may differ)
+    ref = O.gmres_ir(A, b, O.assemble_P(ref_s, "double", "single"), **kw)
+    assert max(ref["its"]) == 500
+    check_ir_against_oracle(A, b, x_true, x, r, ref, 2.0 ** -53)
+    P.free()
+    c.close()
 
 
 def test_adaptive_100k_sampled(ctx):
