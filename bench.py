@@ -5,13 +5,19 @@ plus the whole refinement loop): 3D 7-point convection-diffusion on a 64^3
 grid (n = 262144, 1,810,432 nonzeros), per-cell coefficients lognormal(0,1),
 Peclet 50 upwind; precisions (u_f,u,u_g,u_p,u_r) = (half, single, single,
 single, double); tau = 1e-4; b = A x_true with x_true ~ N(0,1).  Inputs are
-seeded and synthetic.
+seeded and synthetic.  The GMRES solves orthogonalise by modified
+Gram-Schmidt in its one-reduction form (ir_opts.orth = 2: MGS in exact
+arithmetic, one grid-wide reduction per Arnoldi iteration); the same workload
+with the MGS exchange rounds (orth 0) and with CGS2 (orth 1) is reported
+beside it, and so is the all-FP64 form of the method.
 
 N > 1 (torchrun): every rank solves its own copy (independent replicas, weak
 scaling); no collective is on the data path.
 
 ``--impl reference`` times the CPU oracle (the only reference that exists for
-this method) on a bounded sample of the same workload.
+this method) on the same 64^3 system: one full oracle solve, split into K
+bounded steps (SPAI column slices, then the refinement), on all host cores
+(OpenMP over the SPAI columns; the refinement is serial).
 """
 from __future__ import annotations
 
@@ -33,8 +39,10 @@ METRIC = "SPAI-GMRES-IR solves/s (64^3 conv-diff, (half,single,single,single,dou
 UNIT = "solves/s"
 WORKLOAD = "3D 7-point convection-diffusion 64^3, n=262144, lognormal(0,1) cells, Peclet 50, SPAI pattern(A^2)"
 TUPLE = dict(uf="half", u="single", ug="single", up="single", ur="double")
+FP64 = dict(uf="double", u="double", ug="double", up="double", ur="double")
 TAU = 1e-4
 MAX_FILL = 25
+ORTH = 2  # the headline's Arnoldi: MGS in its one-reduction form
 
 
 def parse():
@@ -63,42 +71,68 @@ def nproc():
 
 # ---------------------------------------------------------------- oracle arm
 
-def oracle_sample(grid=20):
-    """One oracle solve of the same generator at grid^3 (single thread)."""
+def oracle_solve_split(grid, parts, threads=0):
+    """One full oracle SPAI-GMRES-IR solve of the grid^3 system, in `parts` pieces:
+    the SPAI columns in parts-1 slices, then the assembly and the refinement.
+    Returns the list of piece durations (s), the refinement result and the
+    number of threads the SPAI used."""
     import oracle as O
     from paper_2202_10204_gb300 import synth
     A, b, x = synth.cfg_large_3d(N=grid)
+    n = len(A[0]) - 1
+    th = O.set_threads(threads)
+    F = MAX_FILL
+    pieces = max(1, parts - 1)
+    bounds = np.linspace(0, n, pieces + 1).astype(np.int64)
+    Jcnt = np.zeros(n, dtype=np.int32)
+    Jidx = np.full((n, F), -1, dtype=np.int32)
+    mbar = np.zeros((n, F))
+    d = None
+    times = []
+    for i in range(pieces):
+        cols = np.arange(bounds[i], bounds[i + 1], dtype=np.int32)
+        t0 = time.perf_counter()
+        if len(cols):
+            S = O.spai(A, init=O.PAT_A2, max_fill=F, uf=TUPLE["uf"], eps=0.3, cols=cols)
+            Jcnt[cols] = S["Jcnt"][cols]
+            Jidx[cols] = S["Jidx"][cols]
+            mbar[cols] = S["mbar"][cols]
+            d = S["d"]
+        times.append(time.perf_counter() - t0)
     t0 = time.perf_counter()
-    S = O.spai(A, init=O.PAT_A2, max_fill=MAX_FILL, uf=TUPLE["uf"], eps=0.3)
-    P = O.assemble_P(S, TUPLE["up"], TUPLE["uf"])
-    R = O.gmres_ir(A, b, P, tau=TAU, **TUPLE)
-    dt = time.perf_counter() - t0
-    return dt, grid ** 3, R
+    Sfull = dict(n=n, max_fill=F, d=d, Jcnt=Jcnt, Jidx=Jidx, mbar=mbar)
+    P = O.assemble_P(Sfull, TUPLE["up"], TUPLE["uf"])
+    R = O.gmres_ir(A, b, P, tau=TAU, orth=ORTH, **TUPLE)
+    times.append(time.perf_counter() - t0)
+    if parts == 1:
+        times = [sum(times)]
+    return times, R, th
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n_full = args.grid ** 3
-    grid = 20
     import oracle as O
     O.build()
+    # warm-up: the same code path on a small system (untimed)
     for _ in range(args.warmup):
-        oracle_sample(grid)
-    times = []
-    for _ in range(args.steps):
-        dt, n_s, R = oracle_sample(grid)
-        times.append(dt * n_full / n_s)  # scaled to the full-size system (linear in n)
-    tot = sum(times)
-    value = args.steps / tot
-    sample = ("oracle SPAI-GMRES-IR of the same generator at %d^3 (n=%d), 1 thread, time scaled by n to %d^3"
-              % (grid, grid ** 3, args.grid))
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=1000 * tot / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, n=n_full, tuple=TUPLE, tau=TAU),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle", sample=sample),
+        oracle_solve_split(12, 2)
+    K = max(1, args.steps)
+    times, R, th = oracle_solve_split(args.grid, K)
+    tot = float(sum(times))
+    value = 1.0 / tot  # exactly one full solve over the K steps
+    n_full = args.grid ** 3
+    sample = ("one full oracle SPAI-GMRES-IR solve of the %d^3 system (n=%d) split into %d steps: SPAI columns in %d "
+              "slices on %d threads (OpenMP), then assembly and the serial refinement (%s iterations); value = 1 / "
+              "total time" % (args.grid, n_full, K, max(1, K - 1), th, list(map(int, R["its"]))))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=K, warmup=args.warmup,
+                ms_per_step=1000 * tot / K, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64 (u_f half, u single, u_g/u_p single, u_r double, simulated)", data="synthetic",
+                impl="reference",
+                config=dict(workload=WORKLOAD, n=n_full, tuple=TUPLE, tau=TAU, orth=ORTH),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=th, kind="oracle", sample=sample,
+                                  nproc=nproc()),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -154,10 +188,9 @@ class ClockSampler:
 # ---------------------------------------------------------------- algorithmic bytes
 
 # DRAM bytes (read + write) of one k_ir launch on the 64^3 workload, from one ncu capture of the
-# current kernel build (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the timed launch):
-# 4.91 GB read + 0.19 GB written against 13.6 GB algorithmic; A, P and the recent basis vectors
-# stay in L2.
-K_IR_DRAM_BYTES_64CUBE = 5.106e9
+# current kernel build (dram__bytes_read.sum + dram__bytes_write.sum, one pass, the timed launch);
+# None until the capture of the current build is taken.
+K_IR_DRAM_BYTES_64CUBE = None
 
 
 def ir_kernel_bytes(n, nnz_a, nnz_p, its, s_u=4, s_g=4, s_p=4):
@@ -200,6 +233,35 @@ def job_throughput(world, steps, max_ms):
 
 
 # ---------------------------------------------------------------- other workloads (reported beside the headline)
+
+def serve_stream(S, dev, reqs, arrivals, so, io, budget=120 << 30):
+    """Submit reqs[i] = (A, b) at arrivals[i] (seconds) to a serving context and poll
+    until all are done; returns (latencies in ms = completion - arrival, makespan s)."""
+    sctx = S.Context(dev.index or 0, hbm_budget=budget)
+    # warm the workers and kernels
+    t = S.solver_submit(sctx, reqs[0][0], reqs[0][1], so, io)
+    while S.solver_poll(sctx, t) is None:
+        time.sleep(0.001)
+    R = len(reqs)
+    pending = {}
+    lat = [None] * R
+    t0 = time.perf_counter()
+    nxt = 0
+    while nxt < R or pending:
+        now = time.perf_counter() - t0
+        while nxt < R and arrivals[nxt] <= now:
+            pending[nxt] = S.solver_submit(sctx, reqs[nxt][0], reqs[nxt][1], so, io)
+            nxt += 1
+        for i in list(pending):
+            stt = S.solver_poll(sctx, pending[i], np.zeros(len(reqs[i][1])))
+            if stt is not None:
+                lat[i] = (time.perf_counter() - t0) - arrivals[i]
+                del pending[i]
+        time.sleep(0.0002)
+    makespan = time.perf_counter() - t0
+    sctx.close()
+    return np.array(lat) * 1000.0, makespan
+
 
 def extra_workloads(S, synth, torch, dev):
     """Five secondary lines, each bounded to a few seconds:
@@ -291,7 +353,7 @@ def extra_workloads(S, synth, torch, dev):
                                 steps=st["steps"], backward_error=nbe)
     P.free()
     ctx.close()
-    # ---- serving
+    # ---- serving: the same Poisson stream with the mixed tuple and in the all-FP64 form
     rng = np.random.default_rng(5)
     R, rate = 48, 200.0
     grids = np.round(np.exp(rng.uniform(np.log(10), np.log(46), size=R))).astype(int)
@@ -303,33 +365,16 @@ def extra_workloads(S, synth, torch, dev):
         reqs.append((A3, b3))
     so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3)
     io = S.make_ir_opts(uf="half", u="single", ug="single", up="double", ur="double", tau=1e-4)
-    sctx = S.Context(dev.index or 0, hbm_budget=120 << 30)
-    # warm the workers and kernels
-    t = S.solver_submit(sctx, reqs[0][0], reqs[0][1], so, io)
-    while S.solver_poll(sctx, t) is None:
-        time.sleep(0.001)
-    pending = {}
-    lat = [None] * R
-    t0 = time.perf_counter()
-    nxt = 0
-    while nxt < R or pending:
-        now = time.perf_counter() - t0
-        while nxt < R and arrivals[nxt] <= now:
-            pending[nxt] = S.solver_submit(sctx, reqs[nxt][0], reqs[nxt][1], so, io)
-            nxt += 1
-        for i in list(pending):
-            stt = S.solver_poll(sctx, pending[i], np.zeros(len(reqs[i][1])))
-            if stt is not None:
-                lat[i] = (time.perf_counter() - t0) - arrivals[i]
-                del pending[i]
-        time.sleep(0.0002)
-    makespan = time.perf_counter() - t0
-    sctx.close()
-    lat = np.array(lat) * 1000.0
+    lat, makespan = serve_stream(S, dev, reqs, arrivals, so, io)
+    so64 = S.make_spai_opts(init=2, max_fill=25, uf="double", eps=0.3)
+    io64 = S.make_ir_opts(uf="double", u="double", ug="double", up="double", ur="double", tau=1e-4)
+    lat64, makespan64 = serve_stream(S, dev, reqs, arrivals, so64, io64)
     out["serving"] = dict(workload="48 requests, 3D conv-diff grids 10^3..46^3 (log-uniform), Poisson 200/s, "
                                    "(half,single,single,double,double), budget 120 GB, host inputs",
                           requests=R, solves_per_s=R / makespan, p50_ms=float(np.percentile(lat, 50)),
-                          p99_ms=float(np.percentile(lat, 99)), sum_n=int(sum(int(g) ** 3 for g in grids)))
+                          p99_ms=float(np.percentile(lat, 99)), sum_n=int(sum(int(g) ** 3 for g in grids)),
+                          fp64=dict(solves_per_s=R / makespan64, p50_ms=float(np.percentile(lat64, 50)),
+                                    p99_ms=float(np.percentile(lat64, 99))))
     # ---- batched: 512 independent systems through the queue at once
     rng = np.random.default_rng(4)
     R = 512
@@ -386,13 +431,31 @@ def extra_workloads(S, synth, torch, dev):
     batch_api = dict(solves_per_s=R / (t2 - t0), makespan_s=t2 - t0, spai_s=t1 - t0, refinement_s=t2 - t1,
                      refinement_launches=int(sts[0]["launches"]), converged=int(sum(int(st_["flags"] & 1) for st_ in sts)),
                      total_its=int(sum(st_["total_its"] for st_ in sts)))
+    # the same systems in the all-FP64 form (every precision double)
+    so64 = S.make_spai_opts(init=1, max_fill=30, uf="double")
+    io64 = S.make_ir_opts(uf="double", u="double", ug="double", up="double", ur="double", tau=1e-4)
+    bctx = S.Context(dev.index or 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Ps, _ = S.spai_build_batch(bctx, [A2 for A2, _ in batch], so64)
+    t1 = time.perf_counter()
+    xs = [np.zeros(len(b2)) for _, b2 in batch]
+    sts64, _ = S.gmres_ir_solve_batch(bctx, [A2 for A2, _ in batch], [b2 for _, b2 in batch], xs, Ps, io64)
+    t2 = time.perf_counter()
+    for P_ in Ps:
+        P_.free()
+    bctx.close()
+    fp64_batch = dict(solves_per_s=R / (t2 - t0), makespan_s=t2 - t0, spai_s=t1 - t0, refinement_s=t2 - t1,
+                      converged=int(sum(int(st_["flags"] & 1) for st_ in sts64)),
+                      total_its=int(sum(st_["total_its"] for st_ in sts64)),
+                      mixed_over_fp64=(R / batch_api["makespan_s"]) / (R / (t2 - t0)))
     out["batched_512"] = dict(workload="512 systems, n log-uniform in [2e3, 5e4]: even = 2D conv-diff (Peclet "
                                        "U(0,50)), odd = random sparse 8-16 nnz/col with row/column scaling "
                                        "10^U(1,3) (cond_1 ~1e2-5e3); pattern(A), (single,double,single,single,double), tau 1e-4, "
                                        "host inputs; value = gmres_ir_solve_batch path, serving_queue = all submitted to the queue at once",
                               systems=R, solves_per_s=batch_api["solves_per_s"],
                               cols_per_s=sum_n / batch_api["makespan_s"], sum_n=sum_n,
-                              batch_api=batch_api, serving_queue=queue)
+                              batch_api=batch_api, serving_queue=queue, fp64_batch_api=fp64_batch)
     return out
 
 
@@ -484,7 +547,7 @@ def main():
     xd = torch.zeros_like(bd)
     ctx = S.Context(local, stream=stream)
     so = S.make_spai_opts(init=2, max_fill=MAX_FILL, uf=TUPLE["uf"], eps=0.3)
-    io = S.make_ir_opts(tau=TAU, **TUPLE)
+    io = S.make_ir_opts(tau=TAU, orth=ORTH, **TUPLE)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def step():
@@ -567,16 +630,21 @@ def main():
         e2e = dict(value=job_throughput(world, ke, te), unit=UNIT, h2d_bytes_per_step=int(h2d),
                    d2h_bytes_per_step=int(n * 8 + 4 * 2), steps=ke)
 
-    # the other Arnoldi options on the same workload (not the headline: the paper's method is
-    # MGS-GMRES): classical Gram-Schmidt twice, and MGS in its one-reduction form
+    # the other Arnoldi options on the same workload: MGS with one exchange round per
+    # projection (orth 0, the library's default), and classical Gram-Schmidt twice (orth 1);
+    # then the all-FP64 form of the method (every precision double) on the same inputs
     variants = {}
-    for name, orth in (("arnoldi_cgs2", 1), ("arnoldi_one_reduction_mgs", 2)):
+    q_row = int(np.max(np.diff(A[0])))
+    for name, orth, tup, stol in (("arnoldi_mgs_rounds", 0, TUPLE, 0.0), ("arnoldi_cgs2", 1, TUPLE, 0.0),
+                                  ("fp64_64cube", ORTH, FP64, 0.0),
+                                  ("fp64_64cube_mixed_stop", ORTH, FP64, q_row * 2.0 ** -24)):
         if args.no_cgs2:
             break
-        io2 = S.make_ir_opts(tau=TAU, orth=orth, **TUPLE)
+        io2 = S.make_ir_opts(tau=TAU, orth=orth, stop_tol=stol, **tup)
+        so2 = so if tup is TUPLE else S.make_spai_opts(init=2, max_fill=MAX_FILL, uf=tup["uf"], eps=0.3)
 
         def step2():
-            P, sst = S.spai_build(ctx, Ad, so)
+            P, sst = S.spai_build(ctx, Ad, so2)
             st = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io2)
             P.free()
             st["ms_spai"] = sst["ms"]
@@ -597,13 +665,23 @@ def main():
         x2 = xd.cpu().numpy()
         nbe2 = float(np.max(np.abs(b - Ms @ x2)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x2)) + np.max(np.abs(b))))
         kms = [s["ms_kernel"] for s in st2]
-        kbytes = [ir_kernel_bytes(n, nnz, s["nnz_P"], s["its"]) for s in st2]
+        sz = dict(s_u=4 if tup["u"] == "single" else 8, s_g=4 if tup["ug"] == "single" else 8,
+                  s_p=4 if tup["up"] == "single" else 8)
+        kbytes = [ir_kernel_bytes(n, nnz, s["nnz_P"], s["its"], **sz) for s in st2]
         ach = float(np.mean([b_ / (m / 1000.0) for b_, m in zip(kbytes, kms)]) / 1e9)
         variants[name] = dict(value=job_throughput(world, args.steps, t2), unit=UNIT, ms_per_step=t2 / args.steps,
-                              ir_kernel_ms=float(np.mean(kms)), its=st2[-1]["its"], backward_error=nbe2,
+                              ir_kernel_ms=float(np.mean(kms)), its=st2[-1]["its"], steps=st2[-1]["steps"],
+                              backward_error=nbe2, tuple=tup, orth=orth,
                               roofline=dict(kernel="k_ir (orth=%d)" % orth, bound="hbm", achieved=ach,
                                             peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
                                             algorithmic_bytes_per_launch=float(np.mean(kbytes))))
+    if "fp64_64cube" in variants:
+        variants["fp64_64cube"]["workload"] = ("the 64^3 workload with every precision double (the all-FP64 form), "
+                                               "same pattern, eps, tau and Arnoldi; stop at q u_double")
+        variants["fp64_64cube"]["mixed_over_fp64"] = value / variants["fp64_64cube"]["value"]
+        variants["fp64_64cube_mixed_stop"]["workload"] = ("the all-FP64 form stopped at the mixed form's backward-error "
+                                                          "tolerance q u_single (the same accuracy target)")
+        variants["fp64_64cube_mixed_stop"]["mixed_over_fp64"] = value / variants["fp64_64cube_mixed_stop"]["value"]
 
     extra = {}
     if world == 1 and not args.no_extra:
@@ -614,13 +692,24 @@ def main():
         try:
             import oracle as O
             O.build()
-            g = 32
-            dt, n_s, R = oracle_sample(g)
-            cpu = dict(value=1.0 / (dt * n / n_s), unit=UNIT, cores=1, kind="oracle",
-                       sample="oracle SPAI-GMRES-IR of the same generator at %d^3 (n=%d) in %.1f s, 1 thread, "
-                              "time scaled by n to %d^3" % (g, n_s, dt, args.grid))
+            # one full oracle solve of this very system on all host cores (OpenMP over the
+            # SPAI columns; the refinement is serial)
+            times, R, th = oracle_solve_split(args.grid, 1)
+            # one thread: the SPAI columns/s on a sample of 8192 columns of the same matrix
+            O.set_threads(1)
+            cols = np.sort(np.random.default_rng(0).choice(n, size=min(n, 8192), replace=False)).astype(np.int32)
+            t0 = time.perf_counter()
+            O.spai(A, init=O.PAT_A2, max_fill=MAX_FILL, uf=TUPLE["uf"], eps=0.3, cols=cols)
+            t1 = time.perf_counter()
+            O.set_threads(0)
+            cpu = dict(value=1.0 / times[0], unit=UNIT, cores=th, kind="oracle", nproc=nproc(),
+                       sample="one full oracle solve of this %d^3 system (n=%d) on %d threads (OpenMP over the SPAI "
+                              "columns, serial refinement): %.1f s, %s iterations" %
+                              (args.grid, n, th, times[0], list(map(int, R["its"]))),
+                       one_thread_spai_cols_per_s=len(cols) / (t1 - t0),
+                       one_thread_sample="SPAI of 8192 sampled columns of the same matrix on 1 thread")
         except Exception as e:  # the baseline is reported, never required
-            cpu = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample="failed: %s" % e)
+            cpu = dict(value=None, unit=UNIT, cores=0, kind="oracle", sample="failed: %s" % e)
 
     clocks = cs.summary(local)
     if rank == 0:
@@ -629,7 +718,8 @@ def main():
             ms_per_step=tot_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f16/f32 (u_f half; u, u_g, u_p single; u_r double)", data="synthetic",
             config=dict(workload=WORKLOAD, n=n, nnz=nnz, nnz_P=int(last["nnz_P"]), tuple=TUPLE, tau=TAU,
-                        max_fill=MAX_FILL, l2="flushed between timed steps (256 MiB write)",
+                        max_fill=MAX_FILL, orth=ORTH, arnoldi="modified Gram-Schmidt, one-reduction form",
+                        l2="flushed between timed steps (256 MiB write)",
                         parallelism="replicas" if world > 1 else "single GPU"),
             latency_ms=dict(p50=float(np.percentile(lat, 50)), p99=float(np.percentile(lat, 99))),
             spai_cols_per_s=n / (spai_ms / 1000.0),
@@ -638,7 +728,7 @@ def main():
                            ir_kernel=float(np.mean(ir_ms))),
             ir=dict(steps=last["steps"], its=last["its"], total_its=last["total_its"], grid=last["grid"],
                     backward_error=nbe, forward_error=fe, nbe_trace=last["nbe"]),
-            roofline=dict(kernel="k_ir (persistent refinement kernel)", bound="hbm", achieved=achieved,
+            roofline=dict(kernel="k_ir (persistent refinement kernel, orth=%d)" % ORTH, bound="hbm", achieved=achieved,
                           peak=hbm_peak, unit="GB/s", frac=achieved / hbm_peak,
                           traffic=K_IR_DRAM_BYTES_64CUBE if args.grid == 64 else None,
                           peak_source=peak_src, algorithmic_bytes_per_launch=float(np.mean(ir_bytes))),
