@@ -190,16 +190,25 @@ void spai_ctx_destroy(spai_ctx ctx);
 int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_precond* P_out,
                spai_stats* st);
 
-/* spai_build for `count` matrices with the same options.  The builds run
- * concurrently on streams of their own (small builds are bound by launch
- * gaps and host synchronisations, not by the GPU), after the work already
- * queued on the context's stream; on return every preconditioner belongs to
- * the context's stream like one from spai_build.  P_out[count] receives the
- * handles (NULL where a build failed); st (count entries, may be NULL) and
- * status (count entries, may be NULL) receive each build's statistics and
- * return code.  Returns the first error, else the first warning, else
- * SPAI_OK; handles that were built must be freed even when an error is
- * returned. */
+/* spai_build for `count` matrices with the same options, after the work
+ * already queued on the context's stream.  Fixed patterns (adaptive = 0):
+ * consecutive matrices are built together as one block-diagonal matrix, so
+ * every kernel of the build runs once for the group instead of once per
+ * matrix (groups are cut where the build would need more than half the free
+ * device memory, 64 GiB at most, or more than 2^31 - 1 rows).  The columns of
+ * Algorithm 1 are independent and each is computed by the kernel its own
+ * shadow size selects, so each preconditioner is bit for bit the one
+ * spai_build gives for its matrix.  A group whose build fails is built again
+ * matrix by matrix, which attributes the error.  Adaptive patterns: the
+ * builds run concurrently on streams of their own.  On return every
+ * preconditioner belongs to the context's stream like one from spai_build.
+ * P_out[count] receives the handles (NULL where a build failed); st (count
+ * entries, may be NULL) and status (count entries, may be NULL) receive each
+ * build's statistics (for a group built together, ms, ms_kernel and
+ * launches are those of the group's build; the per-column arrays are filled
+ * where given) and return code.  Returns the first error, else the first
+ * warning, else SPAI_OK; handles that were built must be freed even when an
+ * error is returned. */
 int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts* opts,
                      spai_precond* P_out, spai_stats* st, int* status);
 

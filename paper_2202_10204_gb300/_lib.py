@@ -257,15 +257,24 @@ def gmres_ir_solve(ctx: Context, A, b, x, P: Precond | None = None, sopts: spai_
     return _ir_dict(st, rc)
 
 
-def spai_build_batch(ctx: Context, As, opts: spai_opts):
-    """spai_build for many matrices with the same options (concurrent builds).
-    Returns (list of Precond, list of stats dicts); raises on the first error
-    after freeing the handles that were built."""
+def spai_build_batch(ctx: Context, As, opts: spai_opts, per_column=False):
+    """spai_build for many matrices with the same options: fixed patterns in
+    one build over the block-diagonal union of the matrices, adaptive ones as
+    concurrent builds.  Returns (list of Precond, list of stats dicts); raises
+    on the first error after freeing the handles that were built."""
     k = len(As)
     csrs = (spai_csr * max(k, 1))(*[make_csr(A) for A in As])
     hs = (C.c_void_p * max(k, 1))()
     sts = (spai_stats * max(k, 1))()
     status = (C.c_int * max(k, 1))()
+    cols = [{} for _ in range(k)]
+    if per_column:
+        for i in range(k):
+            n = csrs[i].n
+            cols[i] = dict(colres=np.zeros(n), nJ=np.zeros(n, dtype=np.int32), nI=np.zeros(n, dtype=np.int32),
+                           flags=np.zeros(n, dtype=np.int32))
+            sts[i].colres, sts[i].nJ, sts[i].nI, sts[i].flags = (_ptr(cols[i]["colres"]), _ptr(cols[i]["nJ"]),
+                                                                 _ptr(cols[i]["nI"]), _ptr(cols[i]["flags"]))
     rc = lib().spai_build_batch(ctx.h, k, csrs, C.byref(opts), hs, sts, status)
     Ps = [Precond(C.c_void_p(hs[i]), ctx) if hs[i] else None for i in range(k)]
     if rc < 0:
@@ -273,9 +282,10 @@ def spai_build_batch(ctx: Context, As, opts: spai_opts):
             if P is not None:
                 P.free()
         _check(rc, "spai_build_batch")
-    out = [dict(n=sts[i].n, nnz_P=sts[i].nnz_P, cols_converged=sts[i].cols_converged, max_I=sts[i].max_I,
+    out = [dict(n=sts[i].n, nnz_P=sts[i].nnz_P, cols_converged=sts[i].cols_converged,
+                cols_fillcap=sts[i].cols_fillcap, cols_nonfinite=sts[i].cols_nonfinite, max_I=sts[i].max_I,
                 max_J=sts[i].max_J, ms=sts[i].ms, ms_kernel=sts[i].ms_kernel, launches=sts[i].launches,
-                rc=status[i]) for i in range(k)]
+                rc=status[i], **cols[i]) for i in range(k)]
     return Ps, out
 
 

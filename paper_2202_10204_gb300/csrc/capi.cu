@@ -414,6 +414,310 @@ int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_prec
     return rc;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched SPAI over a block-diagonal union
+
+// the segment holding position g: the largest i with off[i] <= g
+__device__ __forceinline__ int segment_of(const int64_t* __restrict__ off, int count, int64_t g)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The matrices' rows were copied to their places in the union (rowptr without
+// its last entry); shift row pointers by the matrix's first nonzero and
+// column indices by its first row, and close the row pointers.
+__global__ void k_union_shift(int count, const int64_t* __restrict__ ro, const int64_t* __restrict__ zo, int64_t N,
+                              int64_t nnz, int64_t* __restrict__ rp, int32_t* __restrict__ col)
+{
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = t0; g < N; g += st) rp[g] += zo[segment_of(ro, count, g)];
+    for (int64_t q = t0; q < nnz; q += st) col[q] += (int32_t)ro[segment_of(zo, count, q)];
+    if (t0 == 0) rp[N] = nnz;
+}
+
+struct PartPtrs {
+    int64_t* rp;
+    int32_t* col;
+    double* val;
+    void* vuf;
+};
+
+// P of the union, cut into the matrices' own preconditioners: rows of block
+// i (rows ro[i] .. ro[i+1]-1, nonzeros pz[i] .. pz[i+1]-1) with columns
+// shifted back by ro[i]
+__global__ void k_split_rows(int count, const int64_t* __restrict__ ro, int64_t N, const int64_t* __restrict__ prp,
+                             const PartPtrs* __restrict__ parts)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
+        const int i = segment_of(ro, count, g);
+        const int64_t base = prp[ro[i]], r = g - ro[i];
+        parts[i].rp[r] = prp[g] - base;
+        if (g + 1 == ro[i + 1]) parts[i].rp[r + 1] = prp[g + 1] - base;
+    }
+}
+
+template <class S>
+__global__ void k_split_nz(int count, const int64_t* __restrict__ ro, const int64_t* __restrict__ pz, int64_t nnz,
+                           const int32_t* __restrict__ col, const double* __restrict__ val, const S* __restrict__ vuf,
+                           const PartPtrs* __restrict__ parts)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x) {
+        const int i = segment_of(pz, count, q);
+        const int64_t t = q - pz[i];
+        parts[i].col[t] = col[q] - (int32_t)ro[i];
+        parts[i].val[t] = val[q];
+        ((S*)parts[i].vuf)[t] = vuf[q];
+    }
+}
+
+// Bytes one union build of n rows and nnz nonzeros may hold: the union's A,
+// the build's scratch and P (twice for the right construction's transposes)
+// and the split copies of P.
+static size_t union_footprint(int64_t n, int64_t nnz, const spai_opts* o)
+{
+    const size_t F = (size_t)o->max_fill, N = (size_t)n, Z = (size_t)nnz;
+    size_t b = estimate_footprint(n, nnz, o, nullptr) + N * F * 24 + (N + 1) * 8;
+    if (o->side == 1) b += Z * 12 + N * 8 + N * F * 16;
+    return b;
+}
+
+// Matrices lo .. hi-1 built as one block-diagonal matrix: one pass of every
+// kernel of the build instead of one per matrix.  Columns of a fixed pattern
+// are independent and each is computed by the kernel its own shadow size
+// selects, so every preconditioner is the one spai_build gives for its
+// matrix, bit for bit.  Returns 0 with every handle set, or an error (the
+// caller then builds these matrices one by one, which attributes it).
+static int spai_build_union(spai_ctx ctx, int lo, int hi, const spai_csr* A, const spai_opts* opts,
+                            spai_precond* P_out, spai_stats* st, int* rcs)
+{
+    const int count = hi - lo;
+    cudaStream_t s = ctx->stream;
+    std::vector<int64_t> ro(count + 1, 0), zo(count + 1, 0);
+    for (int i = 0; i < count; i++) {
+        ro[i + 1] = ro[i] + A[lo + i].n;
+        zo[i + 1] = zo[i] + A[lo + i].nnz;
+    }
+    const int64_t N = ro[count], Z = zo[count];
+    int rc = 0;
+    DevCsr U;
+    U.n = N;
+    U.nnz = Z;
+    U.owned = true;
+    int64_t *dro = nullptr, *dzo = nullptr, *dpz = nullptr;
+    int* dflags = nullptr;
+    unsigned long long* dstats = nullptr;
+    PartPtrs* dparts = nullptr;
+    spai_precond PU = nullptr;
+    std::vector<spai_precond> parts(count, nullptr);
+    std::vector<unsigned long long> hs(6 * (size_t)count, 0);
+    std::vector<int> hflags(count, 0);
+    spai_stats su;
+    memset(&su, 0, sizeof(su));
+    bool want_cols = false;
+    std::vector<double> colres;
+    std::vector<int32_t> nJ, nI, fl;
+    const size_t ssz = opts->uf == SPAI_HALF ? 2 : (opts->uf == SPAI_SINGLE ? 4 : 8);
+    const int tb = 256;
+    int nl = 0;
+#define TRYU(x) do { rc = (x); if (rc) goto done; } while (0)
+#define CUDAU(x) do { if ((x) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; } } while (0)
+    TRYU(dev_alloc((void**)&dro, sizeof(int64_t) * (count + 1), s));
+    TRYU(dev_alloc((void**)&dzo, sizeof(int64_t) * (count + 1), s));
+    TRYU(dev_alloc((void**)&dpz, sizeof(int64_t) * (count + 1), s));
+    TRYU(dev_alloc((void**)&dflags, sizeof(int) * count, s));
+    TRYU(dev_alloc((void**)&dstats, sizeof(unsigned long long) * 6 * count, s));
+    TRYU(dev_alloc((void**)&U.rowptr, sizeof(int64_t) * (N + 1), s));
+    TRYU(dev_alloc((void**)&U.col, sizeof(int32_t) * std::max<int64_t>(Z, 1), s));
+    TRYU(dev_alloc((void**)&U.val, sizeof(double) * std::max<int64_t>(Z, 1), s));
+    CUDAU(cudaMemsetAsync(dflags, 0, sizeof(int) * count, s));
+    CUDAU(cudaMemsetAsync(dstats, 0, sizeof(unsigned long long) * 6 * count, s));
+    CUDAU(cudaMemcpyAsync(dro, ro.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    CUDAU(cudaMemcpyAsync(dzo, zo.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+    {
+        // device inputs are checked where they are, before anything reads them by index
+        bool any_dev = false;
+        for (int i = 0; i < count; i++) {
+            const spai_csr& a = A[lo + i];
+            if (!a.on_device) continue;
+            any_dev = true;
+            const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, (int64_t)ctx->num_sms * 8));
+            k_csr_check<<<gb, 256, 0, s>>>(a.n, a.nnz, a.rowptr, a.col, dflags + i, 0);
+            nl++;
+        }
+        if (any_dev) {
+            CUDAU(cudaGetLastError());
+            CUDAU(cudaMemcpyAsync(hflags.data(), dflags, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+            CUDAU(cudaStreamSynchronize(s));
+            for (int i = 0; i < count; i++)
+                if (hflags[i]) { rc = (hflags[i] & 1) ? SPAI_ERR_INVALID_ARG : SPAI_ERR_ZERO_ROW; goto done; }
+        }
+    }
+    for (int i = 0; i < count; i++) {
+        const spai_csr& a = A[lo + i];
+        const cudaMemcpyKind kind = a.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CUDAU(cudaMemcpyAsync(U.rowptr + ro[i], a.rowptr, sizeof(int64_t) * a.n, kind, s));
+        CUDAU(cudaMemcpyAsync(U.col + zo[i], a.col, sizeof(int32_t) * a.nnz, kind, s));
+        CUDAU(cudaMemcpyAsync(U.val + zo[i], a.val, sizeof(double) * a.nnz, kind, s));
+    }
+    {
+        const int gb = (int)std::max<int64_t>(1, std::min<int64_t>((std::max(N, Z) + tb - 1) / tb, (int64_t)ctx->num_sms * 16));
+        k_union_shift<<<gb, tb, 0, s>>>(count, dro, dzo, N, Z, U.rowptr, U.col);
+        nl++;
+        CUDAU(cudaGetLastError());
+    }
+    for (int i = 0; i < count && !want_cols; i++)
+        want_cols = st && (st[lo + i].colres || st[lo + i].nJ || st[lo + i].nI || st[lo + i].flags);
+    if (want_cols) {
+        colres.resize(N); nJ.resize(N); nI.resize(N); fl.resize(N);
+        su.colres = colres.data(); su.nJ = nJ.data(); su.nI = nI.data(); su.flags = fl.data();
+    }
+    {
+        SpaiSegments seg;
+        seg.count = count;
+        seg.ro = dro;
+        seg.stats = dstats;
+        rc = spai_build_dev(ctx->device, ctx->num_sms, s, U, opts, &PU, &su, &seg);
+        if (rc < 0) goto done;
+        rc = 0;
+    }
+    CUDAU(cudaMemcpyAsync(hs.data(), dstats, sizeof(unsigned long long) * 6 * count, cudaMemcpyDeviceToHost, s));
+    CUDAU(cudaStreamSynchronize(s));
+    {
+        std::vector<int64_t> pz(count + 1, 0);
+        for (int i = 0; i < count; i++) pz[i + 1] = pz[i] + (int64_t)hs[6 * (size_t)i + 5];
+        if (pz[count] != PU->nnz) { rc = SPAI_ERR_INTERNAL; goto done; }
+        std::vector<PartPtrs> hp(count);
+        for (int i = 0; i < count; i++) {
+            spai_precond P = new spai_precond_s();
+            parts[i] = P;
+            P->n = A[lo + i].n;
+            P->nnz = pz[i + 1] - pz[i];
+            P->uf = opts->uf;
+            P->stream = s;
+            P->device = ctx->device;
+            const int64_t z = std::max<int64_t>(P->nnz, 1);
+            TRYU(dev_alloc((void**)&P->rowptr, sizeof(int64_t) * (P->n + 1), s));
+            TRYU(dev_alloc((void**)&P->col, sizeof(int32_t) * z, s));
+            TRYU(dev_alloc((void**)&P->val, sizeof(double) * z, s));
+            TRYU(dev_alloc(&P->val_uf, ssz * z, s));
+            hp[i] = PartPtrs{P->rowptr, P->col, P->val, P->val_uf};
+        }
+        TRYU(dev_alloc((void**)&dparts, sizeof(PartPtrs) * count, s));
+        CUDAU(cudaMemcpyAsync(dparts, hp.data(), sizeof(PartPtrs) * count, cudaMemcpyHostToDevice, s));
+        CUDAU(cudaMemcpyAsync(dpz, pz.data(), sizeof(int64_t) * (count + 1), cudaMemcpyHostToDevice, s));
+        const int64_t ZP = PU->nnz;
+        const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((N + tb - 1) / tb, (int64_t)ctx->num_sms * 16));
+        const int gz = (int)std::max<int64_t>(1, std::min<int64_t>((ZP + tb - 1) / tb, (int64_t)ctx->num_sms * 16));
+        k_split_rows<<<gr, tb, 0, s>>>(count, dro, N, PU->rowptr, dparts);
+        if (ZP > 0) {
+            if (opts->uf == SPAI_HALF)
+                k_split_nz<__half><<<gz, tb, 0, s>>>(count, dro, dpz, ZP, PU->col, PU->val, (const __half*)PU->val_uf, dparts);
+            else if (opts->uf == SPAI_SINGLE)
+                k_split_nz<float><<<gz, tb, 0, s>>>(count, dro, dpz, ZP, PU->col, PU->val, (const float*)PU->val_uf, dparts);
+            else
+                k_split_nz<double><<<gz, tb, 0, s>>>(count, dro, dpz, ZP, PU->col, PU->val, (const double*)PU->val_uf, dparts);
+        }
+        nl += 2;
+        CUDAU(cudaGetLastError());
+        CUDAU(cudaStreamSynchronize(s));
+    }
+    for (int i = 0; i < count; i++) {
+        const unsigned long long* h = &hs[6 * (size_t)i];
+        if (st) {
+            spai_stats& o = st[lo + i];
+            const int64_t r0 = ro[i], n = A[lo + i].n;
+            if (o.colres) memcpy(o.colres, colres.data() + r0, sizeof(double) * n);
+            if (o.nJ) memcpy(o.nJ, nJ.data() + r0, sizeof(int32_t) * n);
+            if (o.nI) memcpy(o.nI, nI.data() + r0, sizeof(int32_t) * n);
+            if (o.flags) memcpy(o.flags, fl.data() + r0, sizeof(int32_t) * n);
+            o.n = n;
+            o.nnz_P = (int64_t)h[5];
+            o.cols_converged = (int64_t)h[0];
+            o.cols_fillcap = (int64_t)h[1];
+            o.cols_nonfinite = (int64_t)h[2];
+            o.max_I = (int)h[3];
+            o.max_J = (int)h[4];
+            // one pass built them all: its time and launches
+            o.ms = su.ms;
+            o.ms_kernel = su.ms_kernel;
+            o.launches = su.launches + nl;
+        }
+        rcs[lo + i] = h[2] > 0 ? SPAI_ERR_NONFINITE : (h[1] > 0 ? SPAI_WARN_FILLCAP : 0);
+        P_out[lo + i] = parts[i];
+        parts[i] = nullptr;
+    }
+done:
+#undef TRYU
+#undef CUDAU
+    if (rc) cudaGetLastError();
+    for (auto P : parts)
+        if (P) spai_precond_free(P);
+    if (PU) spai_precond_free(PU);
+    csr_release(&U, s);
+    dev_free(dro, s); dev_free(dzo, s); dev_free(dpz, s); dev_free(dflags, s); dev_free(dstats, s); dev_free(dparts, s);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+extern "C" {
+
+}  // extern "C"
+
+// Matrices lo .. hi-1 built one by one: several at once, each on a stream of
+// its own (builds of small matrices are bound by launch gaps and host
+// synchronisations), after the work already queued on the context's stream.
+static int spai_build_each(spai_ctx ctx, int lo, int hi, const spai_csr* A, const spai_opts* opts,
+                           spai_precond* P_out, spai_stats* st, int* rcs)
+{
+    const int count = hi - lo;
+    const int nt = std::min(count, SPAI_BATCH_STREAMS);
+    cudaEvent_t ready = nullptr;
+    SPAI_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    std::vector<cudaStream_t> ss(nt, nullptr);
+    int rc = 0;
+    if (cudaEventRecord(ready, ctx->stream) != cudaSuccess) rc = SPAI_ERR_CUDA;
+    for (int t = 0; t < nt && !rc; t++) {
+        if (cudaStreamCreateWithFlags(&ss[t], cudaStreamNonBlocking) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        else if (cudaStreamWaitEvent(ss[t], ready, 0) != cudaSuccess) rc = SPAI_ERR_CUDA;  // after the caller's work
+    }
+    if (!rc) {
+        std::atomic<int> next{lo};
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; t++) {
+            th.emplace_back([&, t] {
+                cudaSetDevice(ctx->device);
+                cudaStream_t s = ss[t];
+                for (int i = next++; i < hi; i = next++) {
+                    DevCsr dA;
+                    int r = csr_to_device(&A[i], &dA, s);
+                    if (!r && A[i].on_device) r = csr_check_device(dA, ctx->num_sms, s);
+                    if (!r) r = spai_build_dev(ctx->device, ctx->num_sms, s, dA, opts, &P_out[i], st ? &st[i] : nullptr);
+                    csr_release(&dA, s);
+                    if (cudaStreamSynchronize(s) != cudaSuccess && r >= 0) r = SPAI_ERR_CUDA;
+                    rcs[i] = r;
+                }
+            });
+        }
+        for (auto& t : th) t.join();
+        // the handles' frees go to the context's stream from now on
+        for (int i = lo; i < hi; i++)
+            if (P_out[i]) P_out[i]->stream = ctx->stream;
+    }
+    for (auto s : ss)
+        if (s) cudaStreamDestroy(s);
+    cudaEventDestroy(ready);
+    return rc;
+}
+
+extern "C" {
+
 int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts* opts, spai_precond* P_out,
                      spai_stats* st, int* status)
 {
@@ -427,42 +731,36 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
     }
     std::lock_guard<std::mutex> lk(ctx->mu);
     SPAI_CUDA_TRY(cudaSetDevice(ctx->device));
-    // builds of small matrices are bound by launch gaps and host synchronisations,
-    // so several run at once, each on a stream of its own
-    const int nt = std::min(count, SPAI_BATCH_STREAMS);
-    cudaEvent_t ready = nullptr;
-    SPAI_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    std::vector<cudaStream_t> ss(nt, nullptr);
-    int rc = 0;
-    if (cudaEventRecord(ready, ctx->stream) != cudaSuccess) rc = SPAI_ERR_CUDA;
-    for (int t = 0; t < nt && !rc; t++) {
-        if (cudaStreamCreateWithFlags(&ss[t], cudaStreamNonBlocking) != cudaSuccess) rc = SPAI_ERR_CUDA;
-        else if (cudaStreamWaitEvent(ss[t], ready, 0) != cudaSuccess) rc = SPAI_ERR_CUDA;  // after the caller's work
-    }
     std::vector<int> rcs(count, 0);
-    if (!rc) {
-        std::atomic<int> next{0};
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; t++) {
-            th.emplace_back([&, t] {
-                cudaSetDevice(ctx->device);
-                cudaStream_t s = ss[t];
-                for (int i = next++; i < count; i = next++) {
-                    DevCsr dA;
-                    int r = csr_to_device(&A[i], &dA, s);
-                    if (!r && A[i].on_device) r = csr_check_device(dA, ctx->num_sms, s);
-                    if (!r) r = spai_build_dev(ctx->device, ctx->num_sms, s, dA, opts, &P_out[i], st ? &st[i] : nullptr);
-                    csr_release(&dA, s);
-                    if (cudaStreamSynchronize(s) != cudaSuccess && r >= 0) r = SPAI_ERR_CUDA;
-                    rcs[i] = r;
-                }
-            });
+    int rc = 0;
+    if (!opts->adaptive && count > 1 && (opts->side == 0 || opts->side == 1)) {
+        // fixed patterns: consecutive matrices are built together as one
+        // block-diagonal matrix, in groups whose build fits half the free
+        // device memory (64 GiB at most) and 2^31 - 1 rows; a group whose
+        // build fails is built again matrix by matrix, which attributes the error
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) { cudaGetLastError(); fr = 0; }
+        const size_t cap = std::min<size_t>(fr / 2, (size_t)64 << 30);
+        for (int lo = 0; lo < count && !rc;) {
+            int hi = lo;
+            int64_t n = 0, z = 0;
+            while (hi < count) {
+                const int64_t n2 = n + A[hi].n, z2 = z + A[hi].nnz;
+                if (hi > lo && (n2 > INT32_MAX || union_footprint(n2, z2, opts) > cap)) break;
+                n = n2;
+                z = z2;
+                hi++;
+            }
+            if (hi - lo < 2 || spai_build_union(ctx, lo, hi, A, opts, P_out, st, rcs.data()) != 0)
+                rc = spai_build_each(ctx, lo, hi, A, opts, P_out, st, rcs.data());
+            lo = hi;
         }
-        for (auto& t : th) t.join();
+    } else {
+        rc = spai_build_each(ctx, 0, count, A, opts, P_out, st, rcs.data());
     }
     for (int i = 0; i < count; i++) {
         if (P_out[i]) {
-            // the handle belongs to the context from now on: its frees go to the context's stream
+            // the handle belongs to the context from now on
             std::lock_guard<std::mutex> lk2(g_live_mu);
             P_out[i]->stream = ctx->stream;
             P_out[i]->owner = ctx;
@@ -474,9 +772,6 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
     if (!rc)
         for (int i = 0; i < count && !rc; i++)
             if (rcs[i] > 0) rc = rcs[i];
-    for (auto s : ss)
-        if (s) cudaStreamDestroy(s);
-    cudaEventDestroy(ready);
     return rc;
 }
 

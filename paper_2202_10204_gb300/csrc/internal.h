@@ -98,9 +98,19 @@ int csr_to_device(const spai_csr* A, DevCsr* out, cudaStream_t s);
 void csr_release(DevCsr* d, cudaStream_t s);
 int csr_validate_host(const spai_csr* A);
 
+// A build over the block-diagonal union of several matrices (spai_build_batch):
+// rows ro[i] .. ro[i+1]-1 belong to matrix i.  The build then also writes, per
+// matrix, stats[6 i .. 6 i + 5] = columns converged, columns stopped at the
+// fill cap above eps, non-finite columns, max |I_k|, max |J_k| and nnz(P).
+struct SpaiSegments {
+    int count = 0;
+    const int64_t* ro = nullptr;          // device, count + 1
+    unsigned long long* stats = nullptr;  // device, 6 * count, zeroed by the caller
+};
+
 // phase implementations (spai_build.cu / gmres_ir.cu)
 int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
-                   spai_precond* P_out, spai_stats* st);
+                   spai_precond* P_out, spai_stats* st, const SpaiSegments* seg = nullptr);
 int gmres_ir_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, spai_precond P,
                  const double* b_dev, double* x_dev, const ir_opts* o, ir_stats* st);
 // Many systems with the same options (see gmres_ir_solve_batch); status[i]

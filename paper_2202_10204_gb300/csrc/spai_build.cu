@@ -376,6 +376,86 @@ __global__ void k_flag_stats(int64_t n, const int32_t* __restrict__ flags, const
     }
 }
 
+// Fixed patterns: every column with a shadow of at most MMAX_LIMIT rows
+// goes to the list of its kernel's bin (spai_bin).  k_bin_count counts the
+// bins, the host places them one after another (boff), k_bin_place writes
+// the lists; a column's place within its bin does not matter.  Both take
+// one warp-aggregated atomic per bin present in a warp.
+__device__ __forceinline__ int column_bin(int64_t k, int64_t n, const int32_t* Icnt, const int32_t* Jcnt, bool wide)
+{
+    if (k >= n) return -1;
+    const int m = Icnt[k];
+    return m > MMAX_LIMIT ? -1 : spai_bin(m, Jcnt[k], wide);
+}
+
+__global__ void k_bin_count(int64_t n, const int32_t* __restrict__ Icnt, const int32_t* __restrict__ Jcnt, int wide,
+                            int* __restrict__ cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < n; k0 += stride) {
+        const int b = column_bin(k0 + threadIdx.x, n, Icnt, Jcnt, wide != 0);
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[b], __popc(peers));
+    }
+}
+
+__global__ void k_bin_place(int64_t n, const int32_t* __restrict__ Icnt, const int32_t* __restrict__ Jcnt, int wide,
+                            const int64_t* __restrict__ boff, int* __restrict__ cursor, int32_t* __restrict__ list)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < n; k0 += stride) {
+        const int64_t k = k0 + threadIdx.x;
+        const int b = column_bin(k, n, Icnt, Jcnt, wide != 0);
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (b >= 0 && lane == leader) base = atomicAdd(&cursor[b], __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        if (b >= 0) list[boff[b] + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)k;
+    }
+}
+
+// per matrix of a block-diagonal union: one block per matrix (grid-stride
+// over matrices), the counts of k_flag_stats, max |I_k|, max |J_k|, nnz(P)
+__global__ void k_seg_stats(int count, const int64_t* __restrict__ ro, const int32_t* __restrict__ flags,
+                            const int32_t* __restrict__ Jcnt, const int32_t* __restrict__ Icnt,
+                            const int64_t* __restrict__ prp, unsigned long long* __restrict__ out)
+{
+    __shared__ unsigned long long red[6];
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        if (threadIdx.x < 6) red[threadIdx.x] = 0;
+        __syncthreads();
+        unsigned long long c0 = 0, c1 = 0, c2 = 0;
+        int mi = 0, mj = 0;
+        for (int64_t k = ro[i] + threadIdx.x; k < ro[i + 1]; k += blockDim.x) {
+            const int f = flags[k];
+            c0 += (f & CF_CONVERGED) ? 1 : 0;
+            c1 += ((f & CF_FILLCAP) && !(f & CF_CONVERGED)) ? 1 : 0;
+            c2 += (f & CF_NONFINITE) ? 1 : 0;
+            mi = max(mi, (int)Icnt[k]);
+            mj = max(mj, (int)Jcnt[k]);
+        }
+        c0 = warp_sum(c0); c1 = warp_sum(c1); c2 = warp_sum(c2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mi = max(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+            mj = max(mj, __shfl_xor_sync(0xffffffffu, mj, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&red[0], c0); atomicAdd(&red[1], c1); atomicAdd(&red[2], c2);
+            atomicMax(&red[3], (unsigned long long)mi); atomicMax(&red[4], (unsigned long long)mj);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int t = 0; t < 5; t++) out[6 * (size_t)i + t] = red[t];
+            out[6 * (size_t)i + 5] = (unsigned long long)(prp[ro[i + 1]] - prp[ro[i]]);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_max_row(int64_t n, const int64_t* __restrict__ rp, int* __restrict__ out)
 {
     int mx = 0;
@@ -461,7 +541,7 @@ int csr_transpose(int num_sms, cudaStream_t s, int64_t n, int64_t nnz, const int
 }
 
 int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
-                    spai_precond* P_out, spai_stats* st);
+                    spai_precond* P_out, spai_stats* st, const SpaiSegments* seg);
 
 }  // namespace
 
@@ -470,11 +550,11 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
 // the left run on A^T computes M ~ (A D)^{-1} column by column and assembles
 // M^T D, whose transpose D M is the right preconditioner.
 int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
-                   spai_precond* P_out, spai_stats* st)
+                   spai_precond* P_out, spai_stats* st, const SpaiSegments* seg)
 {
     if (!o || !P_out) return SPAI_ERR_INVALID_ARG;
     if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
-    if (o->side == 0) return spai_build_left(device, num_sms, s, A, o, P_out, st);
+    if (o->side == 0) return spai_build_left(device, num_sms, s, A, o, P_out, st, seg);
     *P_out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SPAI_CUDA_TRY(cudaEventCreate(&e0));
@@ -492,7 +572,8 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
     double* valT = nullptr;
     if (cudaEventRecord(e0, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
     if (!rc) rc = csr_transpose(num_sms, s, A.n, A.nnz, A.rowptr, A.col, A.val, &At.rowptr, &At.col, &At.val, &nl);
-    if (!rc) rc = spai_build_left(device, num_sms, s, At, &ol, &P, st);
+    // (a block-diagonal union transposes block by block: the segments stay)
+    if (!rc) rc = spai_build_left(device, num_sms, s, At, &ol, &P, st, seg);
     csr_release(&At, s);
     if (rc >= 0 && P) {
         const int wrc = rc;
@@ -536,7 +617,7 @@ int spai_build_dev(int device, int num_sms, cudaStream_t s, const DevCsr& A, con
 namespace {
 
 int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, const spai_opts* o,
-                    spai_precond* P_out, spai_stats* st)
+                    spai_precond* P_out, spai_stats* st, const SpaiSegments* seg)
 {
     const int64_t n = A.n, nnz = A.nnz;
     if (!o || !P_out) return SPAI_ERR_INVALID_ARG;
@@ -558,8 +639,12 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     // device scratch
     double* d = nullptr;
     int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|, [3] [4] longest row and column,
-                             // [5] explicit zeros, [6] columns for the large-shadow kernel
+                             // [5] explicit zeros, [6] columns for the large-shadow kernel,
+                             // [8..14] columns per bin of the column kernels (fixed patterns),
+                             // [16..22] the bins' cursors
     int32_t* big = nullptr;  // those columns
+    int32_t* blist = nullptr;  // the bins' column lists
+    int64_t* boff = nullptr;
     unsigned char* slab = nullptr;
     int32_t* ccount = nullptr;
     int64_t* cp = nullptr;
@@ -571,7 +656,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     unsigned long long* fstat = nullptr;
     size_t ssz = o->uf == SPAI_HALF ? 2 : (o->uf == SPAI_SINGLE ? 4 : 8);
     spai_precond P = nullptr;
-    int h_err[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int h_err[16] = {0};
     unsigned long long h_fstat[3] = {0, 0, 0};
     int maxrow = 0, maxcol = 0;
     const int optin = device_attr_cached(cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -579,7 +664,8 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
 
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
     TRY(dev_alloc((void**)&d, sizeof(double) * n, s));
-    TRY(dev_alloc((void**)&err, sizeof(int) * 8, s));
+    TRY(dev_alloc((void**)&err, sizeof(int) * 32, s));
+    TRY(dev_alloc((void**)&boff, sizeof(int64_t) * 8, s));
     TRY(dev_alloc((void**)&big, sizeof(int32_t) * n, s));
     TRY(dev_alloc((void**)&ccount, sizeof(int32_t) * (n + 1), s));
     TRY(dev_alloc((void**)&cp, sizeof(int64_t) * (n + 1), s));
@@ -594,7 +680,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     TRY(dev_alloc(&mval, ssz * n * F, s));
     TRY(dev_alloc(&bval, ssz * (nnz > 0 ? nnz : 1), s));
     TRY(dev_alloc((void**)&fstat, sizeof(unsigned long long) * 3, s));
-    if (cudaMemsetAsync(err, 0, sizeof(int) * 8, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+    if (cudaMemsetAsync(err, 0, sizeof(int) * 32, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(fstat, 0, sizeof(unsigned long long) * 3, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     {
@@ -651,8 +737,13 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
                                                         Icnt, cap, stride, tsz, err, err + 1, err + 5, big_thr, big,
                                                         err + 6);
         nl += 1;
+        if (!o->adaptive) {
+            k_bin_count<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8)), 256, 0, s>>>(
+                n, Icnt, Jcnt, o->uf != SPAI_DOUBLE, err + 8);
+            nl++;
+        }
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (h_err[0]) { rc = h_err[0]; goto done; }
     }
@@ -667,6 +758,22 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         a.rl = maxrow;
         a.big = big;
         a.nbig = err + 6;
+        if (!o->adaptive) {
+            // the bins' lists, one after another
+            int64_t off = 0;
+            for (int b = 0; b < SPAI_NBINS; b++) {
+                a.boff[b] = off;
+                a.bcnt[b] = h_err[8 + b];
+                off += h_err[8 + b];
+            }
+            TRY(dev_alloc((void**)&blist, sizeof(int32_t) * std::max<int64_t>(off, 1), s));
+            if (cudaMemcpyAsync(boff, a.boff, sizeof(int64_t) * SPAI_NBINS, cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+            k_bin_place<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8)), 256, 0, s>>>(
+                n, Icnt, Jcnt, o->uf != SPAI_DOUBLE, boff, err + 16, blist);
+            nl++;
+            if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+            a.blist = blist;
+        }
         // the warp and CTA kernels hold up to MMAX_LIMIT shadow rows; larger
         // shadows go to the large-shadow kernel below
         const int64_t mall = o->adaptive ? (int64_t)F * maxrow + 1 : (int64_t)h_err[1];
@@ -734,6 +841,11 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
             k_assemble<double><<<gb, tb, 0, s>>>(n, F, Jidx, Jcnt, Praw, P->rowptr, P->col, P->val, (double*)P->val_uf);
         k_flag_stats<<<gb, tb, 0, s>>>(n, flags, Jcnt, fstat, err + 2);
         nl += 2;
+        if (seg && seg->count > 0) {
+            k_seg_stats<<<(unsigned)std::min<int64_t>(seg->count, (int64_t)num_sms * 8), 256, 0, s>>>(
+                seg->count, seg->ro, flags, Jcnt, Icnt, P->rowptr, seg->stats);
+            nl++;
+        }
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     }
     if (cudaEventRecord(e1, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -766,7 +878,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     else if (h_fstat[1] > 0) rc = SPAI_WARN_FILLCAP;
 done:
 #undef TRY
-    dev_free(d, s); dev_free(err, s); dev_free(big, s); dev_free(slab, s); dev_free(ccount, s); dev_free(cp, s); dev_free(ri, s);
+    dev_free(d, s); dev_free(err, s); dev_free(big, s); dev_free(blist, s); dev_free(boff, s); dev_free(slab, s); dev_free(ccount, s); dev_free(cp, s); dev_free(ri, s);
     dev_free(Jidx, s); dev_free(Jcnt, s); dev_free(Icnt, s); dev_free(flags, s); dev_free(nsolve, s);
     dev_free(Praw, s); dev_free(colres, s); dev_free(mval, s); dev_free(bval, s); dev_free(fstat, s);
     cudaEventDestroy(e0);

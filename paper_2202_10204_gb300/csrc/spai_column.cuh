@@ -75,7 +75,13 @@ struct SpaiArgs {
     int mmax, cmax;      // per-warp tile rows and candidate capacity
     int rl;              // longest row of A (list capacity per lane)
     int warp_bytes;
-    int ilo, ihi;        // CTA kernel: only columns with ilo < |I_k| <= ihi (from k_pattern); ihi = 0: all
+    // fixed patterns: the kernel of a bin takes the nlist columns of list
+    // (null: all n columns, adaptive); the host side holds every bin's list
+    // (bin b: bcnt[b] columns from blist + boff[b], see spai_bin)
+    const int32_t* list;
+    int64_t nlist;
+    const int32_t* blist;
+    int64_t boff[8], bcnt[8];
     int* err;
     // columns for the large-shadow kernel (spai_big.cuh): fixed patterns whose
     // shadow exceeds the CTA tile (k_pattern), and adaptive columns that outgrew
@@ -85,6 +91,26 @@ struct SpaiArgs {
     int32_t* big;
     int* nbig;
 };
+
+// Fixed patterns: the column kernel of a column with shadow size m = |I_k|
+// (at most SPAI_MMAX_LIMIT; larger shadows go to the large-shadow kernel)
+// and nj = |J_k| columns.  wide: the compute type is float (u_f = half or
+// single), whose row-register kernels hold 256 x 17 tiles.
+//   0: warp kernel, 32-row register tile     1: warp kernel, 64 rows
+//   2: row-register warp kernel, 128 x 16    3: row-register, 256 x 16 (wide)
+//   4: row-register, 128 x 32 (wide)          5: CTA kernel, 8 warps (256 rows)
+//   6: CTA kernel, 16 warps (512 rows)
+constexpr int SPAI_NBINS = 7;
+__host__ __device__ inline int spai_bin(int m, int nj, bool wide)
+{
+    if (m <= 32) return 0;
+    if (m <= 64) return 1;
+    if (m <= 128 && nj <= 16) return 2;
+    if (m <= 256 && nj <= 16 && wide) return 3;
+    if (m <= 128 && wide) return 4;
+    if (m <= 256) return 5;
+    return 6;
+}
 
 __device__ __forceinline__ int bsearch_smem(const int32_t* a, int len, int key)
 {
@@ -685,7 +711,9 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
     const int F = a.F;
     const int mm = a.mmax;
 
-    for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < a.n; k += (int64_t)gridDim.x * wpb) {
+    const int64_t ncols = a.list ? a.nlist : a.n;
+    for (int64_t idx = blockIdx.x * (int64_t)wpb + wib; idx < ncols; idx += (int64_t)gridDim.x * wpb) {
+        const int64_t k = a.list ? (int64_t)a.list[idx] : idx;
         int nj = a.Jcnt[k];
         if (lane < nj) T.J[lane] = a.Jidx[k * F + lane];
         __syncwarp();
@@ -838,17 +866,53 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
 template <class S>
 int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s);
 
-// Launch for storage type S: the warp kernel with its register tile for
-// shadows of up to 64 rows, the CTA kernel (spai_cta.cuh) for up to 512.
+template <class S>
+int launch_spai_cta_nw8(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
+template <class S>
+int launch_spai_cta_nw16(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
+template <class S>
+int launch_spai_mid_bin(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);
+
+// The warp kernel with a register tile of MMsel rows (over a.list when set).
+template <class S>
+int launch_spai_warp(const SpaiArgs& a0, bool adaptive, int MMsel, int num_sms, size_t smem_cap, cudaStream_t s);
+
+// Launch for storage type S.  Fixed patterns run every bin's columns (from
+// k_bin_place) in the bin's kernel (spai_bin), so that a column is computed
+// the same way whatever matrix or batch it belongs to.  Adaptive patterns
+// grow, so they run in the warp kernel when no shadow can exceed 64 rows and
+// in the 16-warp CTA kernel otherwise.
 template <class S>
 int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    if (adaptive) {
+        SpaiArgs a = a0;
+        a.list = nullptr;
+        if (a.mmax > 64) return launch_spai_cta_t<S>(a, true, num_sms, smem_cap, s);
+        return launch_spai_warp<S>(a, true, a.mmax <= 32 ? 32 : 64, num_sms, smem_cap, s);
+    }
+    for (int b = 0; b < SPAI_NBINS; b++) {
+        if (a0.bcnt[b] == 0) continue;
+        SpaiArgs a = a0;
+        a.list = a0.blist + a0.boff[b];
+        a.nlist = a0.bcnt[b];
+        int rc;
+        if (b <= 1) rc = launch_spai_warp<S>(a, false, b == 0 ? 32 : 64, num_sms, smem_cap, s);
+        else if (b <= 4) rc = launch_spai_mid_bin<S>(a, b, num_sms, smem_cap, s);
+        else if (b == 5) rc = launch_spai_cta_nw8<S>(a, num_sms, smem_cap, s);
+        else rc = launch_spai_cta_nw16<S>(a, num_sms, smem_cap, s);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+template <class S>
+int launch_spai_warp(const SpaiArgs& a0, bool adaptive, int MMsel, int num_sms, size_t smem_cap, cudaStream_t s)
 {
     typedef typename Compute<S>::T C;
     typedef typename TileStore<S>::T WT;
     SpaiArgs a = a0;
     if (!adaptive) a.cmax = 0;
-    if (a.mmax > 64) return launch_spai_cta_t<S>(a0, adaptive, num_sms, smem_cap, s);
-    const int MMsel = a.mmax <= 32 ? 32 : 64;
     a.mmax = MMsel;
     while (adaptive && a.cmax > 256 && tile_bytes<C, WT>(a.mmax, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
     const size_t wb = tile_bytes<C, WT>(a.mmax, a.rl, a.cmax);
@@ -862,7 +926,7 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
     if (adaptive) kern = MMsel == 32 ? k_spai<S, true, 32> : k_spai<S, true, 64>;
     else kern = MMsel == 32 ? k_spai<S, false, 32> : k_spai<S, false, 64>;
     SPAI_CUDA_TRY(allow_max_dynamic_smem(kern));
-    int64_t blocks = (a.n + wpb - 1) / wpb;
+    int64_t blocks = ((a.list ? a.nlist : a.n) + wpb - 1) / wpb;
     const int64_t cap = (int64_t)num_sms * 64;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;

@@ -162,12 +162,9 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
     const int F = a.F;
     int* sc = T.sc;  // [0] nj, [1] m, [2] flags from warp 0, [3] nadd
 
-    for (int64_t k = blockIdx.x; k < a.n; k += gridDim.x) {
-        if (a.ihi > 0) {
-            // fixed patterns: this pass takes only the columns of its shadow-size range
-            const int ic = a.Icnt[k];
-            if (ic <= a.ilo || ic > a.ihi) continue;
-        }
+    const int64_t ncols = a.list ? a.nlist : a.n;
+    for (int64_t idx = blockIdx.x; idx < ncols; idx += gridDim.x) {
+        const int64_t k = a.list ? (int64_t)a.list[idx] : idx;
         if (tid == 0) { sc[0] = a.Jcnt[k]; sc[2] = 0; }
         __syncthreads();
         int nj = sc[0];
@@ -431,15 +428,12 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
 }
 
 template <class S, int NW>
-int launch_spai_cta_nw(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s, int ilo,
-                       int ihi)
+int launch_spai_cta_nw(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
 {
     typedef typename Compute<S>::T C;
     SpaiArgs a = a0;
     if (!adaptive) a.cmax = 0;
     a.mmax = 32 * NW;
-    a.ilo = ilo;
-    a.ihi = ihi;
     while (adaptive && a.cmax > 512 && cta_tile_bytes<C>(a.mmax, NW, a.rl, a.cmax) > smem_cap) a.cmax >>= 1;
     const size_t smem = cta_tile_bytes<C>(a.mmax, NW, a.rl, a.cmax);
     if (smem > smem_cap) return SPAI_ERR_UNSUPPORTED;
@@ -449,7 +443,7 @@ int launch_spai_cta_nw(const SpaiArgs& a0, bool adaptive, int num_sms, size_t sm
     int occ = 0;
     SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * NW, smem));
     if (occ < 1) return SPAI_ERR_UNSUPPORTED;
-    int64_t blocks = std::min<int64_t>(a.n, (int64_t)num_sms * occ);
+    int64_t blocks = std::min<int64_t>(a.list ? a.nlist : a.n, (int64_t)num_sms * occ);
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, 32 * NW, smem, s>>>(a);
     SPAI_CUDA_TRY(cudaGetLastError());
@@ -457,17 +451,24 @@ int launch_spai_cta_nw(const SpaiArgs& a0, bool adaptive, int num_sms, size_t sm
 }
 
 // Adaptive patterns grow, so they run 16 warps per column (tiles of 512
-// rows).  Fixed patterns know every column's shadow size from k_pattern:
-// columns of at most 256 rows run 8 warps per column, which fits two CTAs per
-// SM (the 16-warp kernel holds one), and larger ones follow in a 16-warp pass.
+// rows).  Fixed patterns: bins 5 (8 warps per column, up to 256 rows, which
+// fits two CTAs per SM) and 6 (16 warps, up to 512 rows) of spai_bin.
 template <class S>
 int launch_spai_cta_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)
 {
-    if (adaptive) return launch_spai_cta_nw<S, 16>(a0, true, num_sms, smem_cap, s, 0, 0);
-    if (a0.mmax <= 256) return launch_spai_cta_nw<S, 8>(a0, false, num_sms, smem_cap, s, 0, 0);
-    const int rc = launch_spai_cta_nw<S, 8>(a0, false, num_sms, smem_cap, s, 0, 256);
-    if (rc) return rc;
-    return launch_spai_cta_nw<S, 16>(a0, false, num_sms, smem_cap, s, 256, 512);
+    return launch_spai_cta_nw<S, 16>(a0, adaptive, num_sms, smem_cap, s);
+}
+
+template <class S>
+int launch_spai_cta_nw8(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    return launch_spai_cta_nw<S, 8>(a0, false, num_sms, smem_cap, s);
+}
+
+template <class S>
+int launch_spai_cta_nw16(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    return launch_spai_cta_nw<S, 16>(a0, false, num_sms, smem_cap, s);
 }
 
 }  // namespace spai

@@ -6,6 +6,8 @@ differently; the bar is the GMRES-IR one of the other tests: the same number
 of refinement steps as the same system solved alone (or by the oracle),
 GMRES iterations within 10%, backward and forward errors within 10x.
 """
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -138,21 +140,80 @@ def test_batch_edge_cases(ctx):
     assert np.all(xs[0] == 0) and sts[0]["steps"] == 0 and sts[1]["flags"] & 1
 
 
-@pytest.mark.parametrize("adaptive", [False, True])
-def test_spai_build_batch_matches_single_builds(ctx, adaptive):
-    # concurrent builds on separate streams give the same preconditioners bit for bit
+BUILD_CASES = {
+    # fixed patterns: one build over the block-diagonal union of the batch
+    "pattern(A)-half": dict(init=1, max_fill=30, uf="half"),
+    "pattern(A^2)-single-right": dict(init=2, max_fill=25, uf="single", side=1),
+    "pattern(A)-double": dict(init=1, max_fill=30, uf="double"),
+    # adaptive: concurrent builds, one per matrix
+    "adaptive-single": dict(init=0, adaptive=True, eps=0.4, beta=8, max_fill=20, uf="single"),
+}
+
+
+@pytest.mark.parametrize("case", list(BUILD_CASES))
+def test_spai_build_batch_matches_single_builds(ctx, case):
+    # the batched build gives every matrix the preconditioner and statistics of its own build, bit for bit
     As = mixed_systems()
-    so = (S.make_spai_opts(init=0, adaptive=True, eps=0.4, beta=8, max_fill=20, uf="single") if adaptive
-          else S.make_spai_opts(init=1, max_fill=30, uf="half"))
-    Ps, sts = S.spai_build_batch(ctx, As, so)
+    big = BUILD_CASES[case]["init"] == 1
+    if big:
+        # columns of every kernel: shadows above 512 rows (large-shadow kernel) beside small ones
+        As.insert(2, synth.random_sparse(900, 28, seed=31))
+    so = S.make_spai_opts(**BUILD_CASES[case])
+    Ps, sts = S.spai_build_batch(ctx, As, so, per_column=True)
     assert len(Ps) == len(As) and all(P is not None for P in Ps)
     for i, A in enumerate(As):
-        P1, st1 = S.spai_build(ctx, A, so)
+        P1, st1 = S.spai_build(ctx, A, so, per_column=True)
         for u, v in zip(P1.export(), Ps[i].export()):
             assert np.array_equal(u, v), i
-        assert sts[i]["nnz_P"] == st1["nnz_P"] and sts[i]["cols_converged"] == st1["cols_converged"]
+        for key in ("n", "nnz_P", "cols_converged", "cols_fillcap", "cols_nonfinite", "max_I", "max_J", "rc"):
+            assert sts[i][key] == st1[key], (i, key, sts[i][key], st1[key])
+        for key in ("colres", "nJ", "nI", "flags"):
+            assert np.array_equal(sts[i][key], st1[key]), (i, key)
         P1.free()
         Ps[i].free()
+    if big:
+        assert max(st["max_I"] for st in sts) > 512
+    if not BUILD_CASES[case].get("adaptive"):
+        assert len(set(st["launches"] for st in sts)) == 1  # one build for the whole batch
+
+
+def test_spai_build_batch_device_inputs_and_failures(ctx):
+    # device inputs; a matrix with a non-finite value makes its group's build fail, and the
+    # matrices are then built one by one: that matrix alone reports the error
+    dev = torch.device("cuda", 0)
+    As = mixed_systems()[:5]
+    rp, ci, va = As[3]
+    va = va.copy()
+    va[7] = np.inf
+    As[3] = (rp, ci, va)
+    Ad = [tuple(torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in A) for A in As]
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    csrs = (S._lib.spai_csr * len(Ad))(*[S._lib.make_csr(A) for A in Ad])
+    hs = (C.c_void_p * len(Ad))()
+    status = (C.c_int * len(Ad))()
+    rc = S._lib.lib().spai_build_batch(ctx.h, len(Ad), csrs, C.byref(so), hs, None, status)
+    assert rc == S._lib.ERR_NONFINITE
+    assert status[3] == S._lib.ERR_NONFINITE
+    assert not hs[3] and all(hs[i] for i in (0, 1, 2, 4))
+    for i in (0, 1, 2, 4):
+        P = S._lib.Precond(C.c_void_p(hs[i]), ctx)
+        P1, _ = S.spai_build(ctx, As[i], so)
+        for u, v in zip(P1.export(), P.export()):
+            assert np.array_equal(u, v), i
+        assert status[i] >= 0
+        P.free()
+        P1.free()
+    # a device CSR whose last entry names a column beyond its own matrix, inside the
+    # rows of the batch (still sorted: a check of the union alone would pass it)
+    bad = (Ad[0][0], Ad[0][1].clone(), Ad[0][2])
+    bad[1][-1] = int(Ad[0][0].numel() - 1) + 5
+    csrs = (S._lib.spai_csr * 2)(S._lib.make_csr(bad), S._lib.make_csr(Ad[1]))
+    hs = (C.c_void_p * 2)()
+    status = (C.c_int * 2)()
+    rc = S._lib.lib().spai_build_batch(ctx.h, 2, csrs, C.byref(so), hs, None, status)
+    assert rc == S._lib.ERR_INVALID_ARG and status[0] == S._lib.ERR_INVALID_ARG and status[1] >= 0
+    assert not hs[0] and hs[1]
+    S._lib.Precond(C.c_void_p(hs[1]), ctx).free()
 
 
 @pytest.mark.parametrize("orth,side", [(1, 0), (0, 1), (2, 0), (2, 1)])

@@ -107,7 +107,48 @@ SPAI_CASES = [
     # shadows of 208-301 rows: the 8-warp CTA pass takes the columns up to 256 rows, the
     # 16-warp pass the rest
     ("rand-patA-wide", lambda: synth.random_sparse(1000, 17, seed=13), O.PAT_A, 30),
+    # shadows of 65-256 rows with at most 16 pattern columns: the row-register warp kernels
+    # (tiles of 128 x 16 and 256 x 16)
+    ("rand-patA-mid", lambda: synth.random_sparse(2000, 12, seed=17), O.PAT_A, 16),
+    # 22 pattern columns and shadows of at most 101 rows: the 128 x 32 row-register kernel
+    ("band-patA", lambda: banded(600, 25, 22, seed=19), O.PAT_A, 30),
 ]
+
+
+def banded(n, w, per_row, seed):
+    """Rows with the same per_row column offsets in [-w, w] (0 included), values N(0,1)
+    and diagonal 30: every pattern(A) column has per_row entries and a shadow within
+    2 w + 1 rows."""
+    rng = np.random.default_rng(seed)
+    offs = np.sort(np.concatenate([[0], rng.choice(np.setdiff1d(np.arange(-w, w + 1), [0]), per_row - 1,
+                                                   replace=False)]))
+    rows, cols = [], []
+    for i in range(n):
+        c = i + offs
+        c = c[(c >= 0) & (c < n)]
+        rows.extend([i] * len(c)); cols.extend(c)
+    vals = rng.standard_normal(len(rows))
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(n, n)) + 30 * sp.identity(n)
+    M = M.tocsr()
+    M.sort_indices()
+    return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
+
+
+def column_bins(Icnt, Jcnt, uf):
+    """The column kernel each fixed-pattern column runs in (bins of the CUDA path)."""
+    wide = uf != "double"
+    out = []
+    for m, nj in zip(Icnt, Jcnt):
+        if m <= 32: b = 0
+        elif m <= 64: b = 1
+        elif m <= 128 and nj <= 16: b = 2
+        elif m <= 256 and nj <= 16 and wide: b = 3
+        elif m <= 128 and wide: b = 4
+        elif m <= 256: b = 5
+        elif m <= 512: b = 6
+        else: b = 7
+        out.append(b)
+    return np.array(out)
 
 
 @pytest.mark.parametrize("uf", ["half", "single", "double"])
@@ -117,6 +158,11 @@ def test_spai_fixed_pattern_parity(ctx, name, make, init, F, uf):
     P, st, (rp, ci, va) = gpu_spai(ctx, A, init=init, max_fill=F, uf=uf, eps=0.0)
     ref = O.spai(A, init=init, max_fill=F, uf=uf, eps=0.0)
     n = ref["n"]
+    bins = column_bins(ref["Icnt"], ref["Jcnt"], uf)
+    if name == "rand-patA-mid":
+        assert np.sum(bins == 2) > 100 and np.sum(bins == (3 if uf != "double" else 5)) > 100
+    if name == "band-patA":
+        assert np.mean(bins == (4 if uf != "double" else 5)) > 0.9
     # pattern: bit-exact
     assert np.array_equal(np.diff(rp), ref["Jcnt"])
     for k in range(n):
