@@ -381,33 +381,33 @@ __global__ void k_flag_stats(int64_t n, const int32_t* __restrict__ flags, const
 // bins, the host places them one after another (boff), k_bin_place writes
 // the lists; a column's place within its bin does not matter.  Both take
 // one warp-aggregated atomic per bin present in a warp.
-__device__ __forceinline__ int column_bin(int64_t k, int64_t n, const int32_t* Icnt, const int32_t* Jcnt, bool wide)
+__device__ __forceinline__ int column_bin(int64_t k, int64_t n, const int32_t* Icnt, const int32_t* Jcnt)
 {
     if (k >= n) return -1;
     const int m = Icnt[k];
-    return m > MMAX_LIMIT ? -1 : spai_bin(m, Jcnt[k], wide);
+    return m > MMAX_LIMIT ? -1 : spai_bin(m, Jcnt[k]);
 }
 
-__global__ void k_bin_count(int64_t n, const int32_t* __restrict__ Icnt, const int32_t* __restrict__ Jcnt, int wide,
+__global__ void k_bin_count(int64_t n, const int32_t* __restrict__ Icnt, const int32_t* __restrict__ Jcnt,
                             int* __restrict__ cnt)
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < n; k0 += stride) {
-        const int b = column_bin(k0 + threadIdx.x, n, Icnt, Jcnt, wide != 0);
+        const int b = column_bin(k0 + threadIdx.x, n, Icnt, Jcnt);
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[b], __popc(peers));
     }
 }
 
-__global__ void k_bin_place(int64_t n, const int32_t* __restrict__ Icnt, const int32_t* __restrict__ Jcnt, int wide,
+__global__ void k_bin_place(int64_t n, const int32_t* __restrict__ Icnt, const int32_t* __restrict__ Jcnt,
                             const int64_t* __restrict__ boff, int* __restrict__ cursor, int32_t* __restrict__ list)
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x; k0 < n; k0 += stride) {
         const int64_t k = k0 + threadIdx.x;
-        const int b = column_bin(k, n, Icnt, Jcnt, wide != 0);
+        const int b = column_bin(k, n, Icnt, Jcnt);
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(peers) - 1;
         int base = 0;
@@ -640,8 +640,8 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     double* d = nullptr;
     int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|, [3] [4] longest row and column,
                              // [5] explicit zeros, [6] columns for the large-shadow kernel,
-                             // [8..14] columns per bin of the column kernels (fixed patterns),
-                             // [16..22] the bins' cursors
+                             // [8..15] columns per bin of the column kernels (fixed patterns),
+                             // [16..23] the bins' cursors
     int32_t* big = nullptr;  // those columns
     int32_t* blist = nullptr;  // the bins' column lists
     int64_t* boff = nullptr;
@@ -739,7 +739,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         nl += 1;
         if (!o->adaptive) {
             k_bin_count<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8)), 256, 0, s>>>(
-                n, Icnt, Jcnt, o->uf != SPAI_DOUBLE, err + 8);
+                n, Icnt, Jcnt, err + 8);
             nl++;
         }
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -769,7 +769,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
             TRY(dev_alloc((void**)&blist, sizeof(int32_t) * std::max<int64_t>(off, 1), s));
             if (cudaMemcpyAsync(boff, a.boff, sizeof(int64_t) * SPAI_NBINS, cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
             k_bin_place<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8)), 256, 0, s>>>(
-                n, Icnt, Jcnt, o->uf != SPAI_DOUBLE, boff, err + 16, blist);
+                n, Icnt, Jcnt, boff, err + 16, blist);
             nl++;
             if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
             a.blist = blist;

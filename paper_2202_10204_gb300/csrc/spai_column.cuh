@@ -81,7 +81,7 @@ struct SpaiArgs {
     const int32_t* list;
     int64_t nlist;
     const int32_t* blist;
-    int64_t boff[8], bcnt[8];
+    int64_t boff[8], bcnt[8];  // SPAI_NBINS
     int* err;
     // columns for the large-shadow kernel (spai_big.cuh): fixed patterns whose
     // shadow exceeds the CTA tile (k_pattern), and adaptive columns that outgrew
@@ -94,22 +94,19 @@ struct SpaiArgs {
 
 // Fixed patterns: the column kernel of a column with shadow size m = |I_k|
 // (at most SPAI_MMAX_LIMIT; larger shadows go to the large-shadow kernel)
-// and nj = |J_k| columns.  wide: the compute type is float (u_f = half or
-// single), whose row-register kernels hold 256 x 17 tiles.
-//   0: warp kernel, 32-row register tile     1: warp kernel, 64 rows
-//   2: row-register warp kernel, 128 x 16    3: row-register, 256 x 16 (wide)
-//   4: row-register, 128 x 32 (wide)          5: CTA kernel, 8 warps (256 rows)
-//   6: CTA kernel, 16 warps (512 rows)
-constexpr int SPAI_NBINS = 7;
-__host__ __device__ inline int spai_bin(int m, int nj, bool wide)
+// and nj = |J_k| columns:
+//   0: warp kernel, 32-row register tile       1: warp kernel, 64 rows
+//   2..7: warp kernel with the tile in shared memory (spai_mid.cuh), 32 R rows
+//   and NC columns: 2: 128 x 16, 3: 256 x 16, 4: 128 x 32, 5: 256 x 32,
+//   6: 512 x 16, 7: 512 x 32 (at u_f = double the 16-warp CTA kernel)
+constexpr int SPAI_NBINS = 8;
+__host__ __device__ inline int spai_bin(int m, int nj)
 {
     if (m <= 32) return 0;
     if (m <= 64) return 1;
-    if (m <= 128 && nj <= 16) return 2;
-    if (m <= 256 && nj <= 16 && wide) return 3;
-    if (m <= 128 && wide) return 4;
-    if (m <= 256) return 5;
-    return 6;
+    if (m <= 128) return nj <= 16 ? 2 : 4;
+    if (m <= 256) return nj <= 16 ? 3 : 5;
+    return nj <= 16 ? 6 : 7;
 }
 
 __device__ __forceinline__ int bsearch_smem(const int32_t* a, int len, int key)
@@ -898,9 +895,7 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
         a.nlist = a0.bcnt[b];
         int rc;
         if (b <= 1) rc = launch_spai_warp<S>(a, false, b == 0 ? 32 : 64, num_sms, smem_cap, s);
-        else if (b <= 4) rc = launch_spai_mid_bin<S>(a, b, num_sms, smem_cap, s);
-        else if (b == 5) rc = launch_spai_cta_nw8<S>(a, num_sms, smem_cap, s);
-        else rc = launch_spai_cta_nw16<S>(a, num_sms, smem_cap, s);
+        else rc = launch_spai_mid_bin<S>(a, b, num_sms, smem_cap, s);
         if (rc) return rc;
     }
     return 0;

@@ -104,14 +104,16 @@ SPAI_CASES = [
     ("3d-patA2", lambda: synth.conv_diff_3d(9, 50.0, seed=3), O.PAT_A2, 25),
     ("rand-patA", lambda: synth.random_sparse(700, 9, seed=5), O.PAT_A, 12),
     ("3d-capped", lambda: synth.conv_diff_3d((7, 6, 5), 50.0, seed=8), O.PAT_A2, 9),
-    # shadows of 208-301 rows: the 8-warp CTA pass takes the columns up to 256 rows, the
-    # 16-warp pass the rest
+    # 17-30 pattern columns, shadows of 208-301 rows: the 256 x 32 and 512 x 32 tiles (the
+    # 16-warp CTA kernel for the larger ones at u_f = double)
     ("rand-patA-wide", lambda: synth.random_sparse(1000, 17, seed=13), O.PAT_A, 30),
-    # shadows of 65-256 rows with at most 16 pattern columns: the row-register warp kernels
-    # (tiles of 128 x 16 and 256 x 16)
+    # shadows of 65-256 rows with at most 16 pattern columns: the shared-memory tiles of
+    # 128 x 16 and 256 x 16
     ("rand-patA-mid", lambda: synth.random_sparse(2000, 12, seed=17), O.PAT_A, 16),
-    # 22 pattern columns and shadows of at most 101 rows: the 128 x 32 row-register kernel
+    # 22 pattern columns and shadows of at most 101 rows: the 128 x 32 shared-memory tile
     ("band-patA", lambda: banded(600, 25, 22, seed=19), O.PAT_A, 30),
+    # 16 pattern columns, shadows of 129-512 rows: the 256 x 16 and 512 x 16 tiles
+    ("rand-patA-16", lambda: synth.random_sparse(1500, 18, seed=23), O.PAT_A, 16),
 ]
 
 
@@ -134,19 +136,18 @@ def banded(n, w, per_row, seed):
     return M.indptr.astype(np.int64), M.indices.astype(np.int32), M.data.astype(np.float64)
 
 
-def column_bins(Icnt, Jcnt, uf):
-    """The column kernel each fixed-pattern column runs in (bins of the CUDA path)."""
-    wide = uf != "double"
+def column_bins(Icnt, Jcnt):
+    """The column kernel each fixed-pattern column runs in (bins of the CUDA path):
+    0/1 register-tile warp kernel (32/64 rows), 2..7 shared-memory-tile warp kernel
+    (128/256/512 rows by 16/32 columns), 8 the large-shadow kernel."""
     out = []
     for m, nj in zip(Icnt, Jcnt):
         if m <= 32: b = 0
         elif m <= 64: b = 1
-        elif m <= 128 and nj <= 16: b = 2
-        elif m <= 256 and nj <= 16 and wide: b = 3
-        elif m <= 128 and wide: b = 4
-        elif m <= 256: b = 5
-        elif m <= 512: b = 6
-        else: b = 7
+        elif m <= 128: b = 2 if nj <= 16 else 4
+        elif m <= 256: b = 3 if nj <= 16 else 5
+        elif m <= 512: b = 6 if nj <= 16 else 7
+        else: b = 8
         out.append(b)
     return np.array(out)
 
@@ -158,11 +159,15 @@ def test_spai_fixed_pattern_parity(ctx, name, make, init, F, uf):
     P, st, (rp, ci, va) = gpu_spai(ctx, A, init=init, max_fill=F, uf=uf, eps=0.0)
     ref = O.spai(A, init=init, max_fill=F, uf=uf, eps=0.0)
     n = ref["n"]
-    bins = column_bins(ref["Icnt"], ref["Jcnt"], uf)
+    bins = column_bins(ref["Icnt"], ref["Jcnt"])
     if name == "rand-patA-mid":
-        assert np.sum(bins == 2) > 100 and np.sum(bins == (3 if uf != "double" else 5)) > 100
+        assert np.sum(bins == 2) > 100 and np.sum(bins == 3) > 100
     if name == "band-patA":
-        assert np.mean(bins == (4 if uf != "double" else 5)) > 0.9
+        assert np.mean(bins == 4) > 0.9
+    if name == "rand-patA-wide":
+        assert np.sum(bins == 5) > 100 and np.sum(bins == 7) > 100
+    if name == "rand-patA-16":
+        assert np.sum(bins == 3) > 100 and np.sum(bins == 6) > 100
     # pattern: bit-exact
     assert np.array_equal(np.diff(rp), ref["Jcnt"])
     for k in range(n):
