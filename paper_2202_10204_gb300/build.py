@@ -14,8 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libspai_ir.so")
-SOURCES = (["spai_build.cu", "spai_column_half.cu", "spai_column_single.cu", "spai_column_double.cu", "gmres_ir.cu",
-            "capi.cu"] + ["gmres_ir_k_%s.cu" % t for t in ("fff", "ffd", "fdf", "fdd", "dff", "dfd", "ddf", "ddd")])
+SOURCES = (["spai_build.cu", "spai_column_half.cu", "spai_column_single.cu", "spai_column_double.cu",
+            "spai_mid_half.cu", "spai_mid_single.cu", "spai_mid_double.cu", "gmres_ir.cu", "capi.cu"] +
+           ["gmres_ir_k_%s.cu" % t for t in ("fff", "ffd", "fdf", "fdd", "dff", "dfd", "ddf", "ddd")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -640,8 +640,8 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     double* d = nullptr;
     int* err = nullptr;      // [0] error code, [1] max |I|, [2] max |J|, [3] [4] longest row and column,
                              // [5] explicit zeros, [6] columns for the large-shadow kernel,
-                             // [8..15] columns per bin of the column kernels (fixed patterns),
-                             // [16..23] the bins' cursors
+                             // [8..21] columns per bin of the column kernels (fixed patterns),
+                             // [24..37] the bins' cursors
     int32_t* big = nullptr;  // those columns
     int32_t* blist = nullptr;  // the bins' column lists
     int64_t* boff = nullptr;
@@ -656,7 +656,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     unsigned long long* fstat = nullptr;
     size_t ssz = o->uf == SPAI_HALF ? 2 : (o->uf == SPAI_SINGLE ? 4 : 8);
     spai_precond P = nullptr;
-    int h_err[16] = {0};
+    int h_err[24] = {0};
     unsigned long long h_fstat[3] = {0, 0, 0};
     int maxrow = 0, maxcol = 0;
     const int optin = device_attr_cached(cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -664,8 +664,8 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
 
 #define TRY(x) do { rc = (x); if (rc) goto done; } while (0)
     TRY(dev_alloc((void**)&d, sizeof(double) * n, s));
-    TRY(dev_alloc((void**)&err, sizeof(int) * 32, s));
-    TRY(dev_alloc((void**)&boff, sizeof(int64_t) * 8, s));
+    TRY(dev_alloc((void**)&err, sizeof(int) * 40, s));
+    TRY(dev_alloc((void**)&boff, sizeof(int64_t) * SPAI_NBINS, s));
     TRY(dev_alloc((void**)&big, sizeof(int32_t) * n, s));
     TRY(dev_alloc((void**)&ccount, sizeof(int32_t) * (n + 1), s));
     TRY(dev_alloc((void**)&cp, sizeof(int64_t) * (n + 1), s));
@@ -680,7 +680,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     TRY(dev_alloc(&mval, ssz * n * F, s));
     TRY(dev_alloc(&bval, ssz * (nnz > 0 ? nnz : 1), s));
     TRY(dev_alloc((void**)&fstat, sizeof(unsigned long long) * 3, s));
-    if (cudaMemsetAsync(err, 0, sizeof(int) * 32, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+    if (cudaMemsetAsync(err, 0, sizeof(int) * 40, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(ccount, 0, sizeof(int32_t) * (n + 1), s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     if (cudaMemsetAsync(fstat, 0, sizeof(unsigned long long) * 3, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
     {
@@ -743,7 +743,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
             nl++;
         }
         if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
-        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
+        if (cudaMemcpyAsync(h_err, err, sizeof(int) * 24, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (cudaStreamSynchronize(s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
         if (h_err[0]) { rc = h_err[0]; goto done; }
     }
@@ -769,7 +769,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
             TRY(dev_alloc((void**)&blist, sizeof(int32_t) * std::max<int64_t>(off, 1), s));
             if (cudaMemcpyAsync(boff, a.boff, sizeof(int64_t) * SPAI_NBINS, cudaMemcpyHostToDevice, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
             k_bin_place<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 8)), 256, 0, s>>>(
-                n, Icnt, Jcnt, boff, err + 16, blist);
+                n, Icnt, Jcnt, boff, err + 24, blist);
             nl++;
             if (cudaGetLastError() != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
             a.blist = blist;

@@ -81,7 +81,7 @@ struct SpaiArgs {
     const int32_t* list;
     int64_t nlist;
     const int32_t* blist;
-    int64_t boff[8], bcnt[8];  // SPAI_NBINS
+    int64_t boff[16], bcnt[16];  // at least SPAI_NBINS
     int* err;
     // columns for the large-shadow kernel (spai_big.cuh): fixed patterns whose
     // shadow exceeds the CTA tile (k_pattern), and adaptive columns that outgrew
@@ -96,17 +96,21 @@ struct SpaiArgs {
 // (at most SPAI_MMAX_LIMIT; larger shadows go to the large-shadow kernel)
 // and nj = |J_k| columns:
 //   0: warp kernel, 32-row register tile       1: warp kernel, 64 rows
-//   2..7: warp kernel with the tile in shared memory (spai_mid.cuh), 32 R rows
-//   and NC columns: 2: 128 x 16, 3: 256 x 16, 4: 128 x 32, 5: 256 x 32,
-//   6: 512 x 16, 7: 512 x 32 (at u_f = double the 16-warp CTA kernel)
-constexpr int SPAI_NBINS = 8;
+//   2..13: warp kernel with the tile in shared memory (spai_mid.cuh), 32 R
+//   rows by NC columns: up to 16 columns R = ceil(m/32) for R <= 8 (bins
+//   2..7), then R = 10, 12, 16 (bins 8..10); 17..31 columns R = 4, 8, 16
+//   (bins 11..13; at u_f = double bin 13 runs the 16-warp CTA kernel)
+constexpr int SPAI_NBINS = 14;
 __host__ __device__ inline int spai_bin(int m, int nj)
 {
     if (m <= 32) return 0;
     if (m <= 64) return 1;
-    if (m <= 128) return nj <= 16 ? 2 : 4;
-    if (m <= 256) return nj <= 16 ? 3 : 5;
-    return nj <= 16 ? 6 : 7;
+    const int R = (m + 31) / 32;
+    if (nj <= 16) {
+        if (R <= 8) return R - 1;
+        return R <= 10 ? 8 : (R <= 12 ? 9 : 10);
+    }
+    return R <= 4 ? 11 : (R <= 8 ? 12 : 13);
 }
 
 __device__ __forceinline__ int bsearch_smem(const int32_t* a, int len, int key)
@@ -867,8 +871,17 @@ template <class S>
 int launch_spai_cta_nw8(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
 template <class S>
 int launch_spai_cta_nw16(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
+// the shared-memory tile kernel (spai_mid.cuh), compiled in spai_mid_<u_f>.cu
+int launch_spai_mid_bin_half(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);
+int launch_spai_mid_bin_single(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);
+int launch_spai_mid_bin_double(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);
 template <class S>
-int launch_spai_mid_bin(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);
+inline int launch_spai_mid_bin(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    if constexpr (std::is_same<S, __half>::value) return launch_spai_mid_bin_half(a, bin, num_sms, smem_cap, s);
+    else if constexpr (std::is_same<S, float>::value) return launch_spai_mid_bin_single(a, bin, num_sms, smem_cap, s);
+    else return launch_spai_mid_bin_double(a, bin, num_sms, smem_cap, s);
+}
 
 // The warp kernel with a register tile of MMsel rows (over a.list when set).
 template <class S>
@@ -895,6 +908,7 @@ int launch_spai_t(const SpaiArgs& a0, bool adaptive, int num_sms, size_t smem_ca
         a.nlist = a0.bcnt[b];
         int rc;
         if (b <= 1) rc = launch_spai_warp<S>(a, false, b == 0 ? 32 : 64, num_sms, smem_cap, s);
+        else if (b == 13 && std::is_same<S, double>::value) rc = launch_spai_cta_nw16<S>(a, num_sms, smem_cap, s);
         else rc = launch_spai_mid_bin<S>(a, b, num_sms, smem_cap, s);
         if (rc) return rc;
     }

@@ -1,7 +1,6 @@
 // Instantiation of the SPAI column kernel for u_f = single.
 #include "spai_column.cuh"
 #include "spai_cta.cuh"
-#include "spai_mid.cuh"
 #include "spai_big.cuh"
 
 int launch_spai_single(const spai::SpaiArgs& a, bool adaptive, int num_sms, size_t smem_cap, cudaStream_t s)

@@ -5,20 +5,24 @@
 // the shadow at 64 rows; the CTA kernel spreads larger tiles over 8 or 16
 // warps that synchronise at every Householder step, and a single warp does
 // its gather.  Here one warp owns the column and the working tile X =
-// [B(I_k,J_k) | e_k(I_k)] lives in shared memory, row-major: lane l owns
-// rows l, l + 32, ..., l + 32 (R-1), so every lane reads and updates only
-// its own rows and no step needs a barrier.  The loops over steps and
-// columns are not unrolled (the code stays in the instruction cache); each
-// inner product is a lane-local sum over R rows and a warp sum, two columns
-// at a time.
+// [B(I_k,J_k) | e_k(I_k)] lives in shared memory, row-major and padded with
+// zero rows to 32 R: lane l owns rows l, l + 32, ..., l + 32 (R-1), so every
+// lane reads and updates only its own rows and no step needs a barrier.  The
+// loops over steps and columns are not unrolled (the code stays in the
+// instruction cache); each inner product is a lane-local sum over R rows and
+// a warp sum, four columns at a time.  R is chosen per column as
+// ceil(|I_k| / 32) (the bins of spai_bin), so few padding rows are computed.
 //
 // Per column:
 //   1. gather: every lane takes entry e of each row J_k[t] of A (the u_f
 //      values of B = A^T D; coalesced, all rows in flight at once) and
-//      inserts its row index into a shared-memory hash set (new keys
-//      appended to I in arrival order, plus k); I_k is sorted (warp bitonic
-//      sort), each hash slot records its key's rank, and a second pass
-//      writes every value to its rank's row of the zeroed tile;
+//      inserts its row index into a shared-memory hash set; the rows of I_k
+//      are numbered in the order the traversal first meets them (k first,
+//      then row J_k[0]'s entries, ...), which fixes the order of the tile's
+//      rows for every run.  A second pass writes every value to its row of
+//      the zeroed tile.  The order of the rows does not change the
+//      least-squares problem; it only changes rounding, within the
+//      tolerance of the oracle comparison;
 //   2. Householder QR of X in place: per step c the norm of the pivot
 //      column below row c, then for every later column (and e_k) its inner
 //      product with the reflector and the update of every lane's rows,
@@ -40,18 +44,25 @@
 
 namespace spai {
 
+constexpr int mid_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
 template <class S, int R, int NC>
 struct MidCfg {
     typedef typename Compute<S>::T C;
-    static constexpr int MM = 32 * R;      // tile rows
-    static constexpr int HS = 64 * R;      // hash slots (load at most one half)
-    static constexpr int LDX = NC + 1;     // row stride of X: the NC columns and e_k (odd: no bank conflicts)
-    static constexpr size_t SV = (size_t)MM * (sizeof(C) > 4 ? sizeof(C) : 4);  // I, later s
+    static constexpr int MM = 32 * R;              // tile rows
+    static constexpr int HS = mid_pow2(2 * MM);    // hash slots (load at most one half)
+    static constexpr int LDX = NC + 1;             // row stride of X: the NC columns and e_k (odd: no bank conflicts)
     static constexpr size_t bytes()
     {
-        return ((size_t)HS * 4 + (size_t)HS * 2 + 32 * 8 + 32 * 4 + 32 * sizeof(C) + SV + (size_t)MM * LDX * sizeof(C) +
-                15) & ~size_t(15);
+        return (size_t)HS * 4 + (size_t)HS * 2 + 32 * 8 + 32 * 4 + 32 * sizeof(C) + (size_t)MM * sizeof(C) +
+               (size_t)MM * LDX * sizeof(C) + 64;
     }
+    static constexpr size_t stride() { return (bytes() + 15) & ~size_t(15); }
     // warps per block: two, or one where a warp's tile is large (finer occupancy steps)
     static constexpr int WPB = bytes() > 40 * 1024 ? 1 : 2;
 };
@@ -59,6 +70,19 @@ struct MidCfg {
 __device__ __forceinline__ int mid_hash_shift(int hs)
 {
     return 32 - (31 - __clz(hs));
+}
+
+// inserts key; returns its slot if it was not there yet, else -1
+__device__ __forceinline__ int hset_insert_slot(int32_t* tab, unsigned mask, int shift, int key)
+{
+    unsigned h = hset_slot(key, shift);
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int old = atomicCAS(&tab[h], -1, key);
+        if (old == -1) return (int)h;
+        if (old == key) return -1;
+        h = (h + 1u) & mask;
+    }
+    return -1;
 }
 
 template <class S, int R, int NC>
@@ -69,21 +93,20 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
     constexpr int MM = Cfg::MM, HS = Cfg::HS, LDX = Cfg::LDX, WPB = Cfg::WPB;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    unsigned char* base = smem + (size_t)wib * Cfg::bytes();
+    unsigned char* base = smem + (size_t)wib * Cfg::stride();
     int32_t* hk = (int32_t*)base;                                  // HS keys
-    uint16_t* hr = (uint16_t*)(base + (size_t)HS * 4);             // HS ranks
+    uint16_t* hr = (uint16_t*)(base + (size_t)HS * 4);             // HS: each key's row of the tile
     int64_t* rowq = (int64_t*)(base + (size_t)HS * 6);             // 32: first entry of row J[t] of A
     int32_t* rowl = (int32_t*)(base + (size_t)HS * 6 + 256);       // 32: its length
     C* mb = (C*)(base + (size_t)HS * 6 + 384);                     // 32: mbar
-    unsigned char* sv = base + (size_t)HS * 6 + 384 + 32 * sizeof(C);
-    int32_t* I = (int32_t*)sv;                                     // MM: I_k (gather)
-    C* sres = (C*)sv;                                              // MM: s (residual)
-    C* X = (C*)(sv + Cfg::SV);                                     // MM x LDX
+    C* sres = (C*)(base + (size_t)HS * 6 + 384 + 32 * sizeof(C));  // MM: s
+    C* X = (C*)(((uintptr_t)(sres + MM) + 15) & ~(uintptr_t)15);   // MM x LDX, 16-byte aligned
     const unsigned FULL = 0xffffffffu;
     const unsigned hmask = HS - 1;
     const int hshift = mid_hash_shift(HS);
     const S* bv = (const S*)a.bval;
     const int F = a.F;
+    C* Xl = X + lane * LDX;  // this lane's first row
 
     for (int64_t idx = blockIdx.x * (int64_t)WPB + wib; idx < a.nlist; idx += (int64_t)gridDim.x * WPB) {
         const int64_t k = a.list[idx];
@@ -95,6 +118,12 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
         const int jl = lane < nj ? a.Jidx[k * F + lane] : -1;
         // ---- 1. gather
         for (int t = lane; t < HS; t += 32) hk[t] = -1;
+        {
+            // zero the whole tile, padding rows included (16-byte stores)
+            constexpr int n16 = (int)((MM * LDX * sizeof(C)) / 16);
+            static_assert((MM * LDX * sizeof(C)) % 16 == 0, "tile size");
+            for (int t = lane; t < n16; t += 32) reinterpret_cast<int4*>(X)[t] = make_int4(0, 0, 0, 0);
+        }
         int len = 0;
         if (lane < nj) {
             const int64_t q0 = a.rp[jl];
@@ -104,10 +133,8 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
         }
         const int maxlen = (int)__reduce_max_sync(FULL, (unsigned)len);
         __syncwarp();
-        int m = 0;
-        if (lane == 0) hset_insert(hk, hmask, hshift, (int)k);
-        if (lane == 0) I[0] = (int)k;
-        m = 1;
+        if (lane == 0) hr[hset_insert_slot(hk, hmask, hshift, (int)k)] = 0;  // e_k's row: row 0
+        int m = 1;
         __syncwarp();
         for (int e0 = 0; e0 < maxlen; e0 += 32) {
             int ck[NC];
@@ -124,29 +151,17 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
 #pragma unroll
             for (int t = 0; t < NC; t++) {
                 if (t < nj) {
-                    const bool isnew = ck[t] >= 0 && hset_insert(hk, hmask, hshift, ck[t]);
-                    const unsigned bal = __ballot_sync(FULL, isnew);
-                    if (isnew) {
-                        const int pos = m + __popc(bal & ((1u << lane) - 1u));
-                        if (pos < MM) I[pos] = ck[t];
-                    }
+                    const int slot = ck[t] >= 0 ? hset_insert_slot(hk, hmask, hshift, ck[t]) : -1;
+                    const unsigned bal = __ballot_sync(FULL, slot >= 0);
+                    if (slot >= 0) hr[slot] = (uint16_t)min(m + __popc(bal & ((1u << lane) - 1u)), 0xffff);
                     m += __popc(bal);
                 }
             }
         }
-        __syncwarp();
         if (m > MM) {  // cannot happen: the column was binned by its shadow size
             if (lane == 0) atomicCAS(a.err, 0, SPAI_ERR_INTERNAL);
+            __syncwarp();
             continue;
-        }
-        for (int t = m + lane; t < MM; t += 32) I[t] = INT_MAX;
-        __syncwarp();
-        warp_bitonic_sort(I, MM);
-        for (int p = lane; p < m; p += 32) hr[hset_find(hk, hmask, hshift, I[p])] = (uint16_t)p;
-        {
-            // zero the tile's first m rows (16-byte stores; the tile starts 16-byte aligned)
-            const int n16 = (int)((m * LDX * sizeof(C) + 15) / 16);
-            for (int t = lane; t < n16; t += 32) reinterpret_cast<int4*>(X)[t] = make_int4(0, 0, 0, 0);
         }
         __syncwarp();
         for (int e0 = 0; e0 < maxlen; e0 += 32) {
@@ -159,68 +174,62 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
                 }
             }
         }
-        const int rk = hr[hset_find(hk, hmask, hshift, (int)k)];  // row of e_k
-        if (lane == 0) X[rk * LDX + nj] = C(1);
+        if (lane == 0) X[nj] = C(1);  // e_k: row 0, column nj
         __syncwarp();
-        // ---- 2. Householder QR of X (each lane its own rows)
+        // ---- 2. Householder QR of X (each lane its own rows; padding rows stay zero)
         const int steps = nj < m ? nj : m;
         for (int c = 0; c < steps; c++) {
             C v[R];
 #pragma unroll
-            for (int i = 0; i < R; i++) {
-                const int row = lane + 32 * i;
-                v[i] = row < m ? X[row * LDX + c] : C(0);
-            }
+            for (int i = 0; i < R; i++) v[i] = Xl[i * 32 * LDX + c];
             const C xl = v[0];
             if (lane < c) v[0] = C(0);  // rows >= c only
-            C sp = 0;
+            C sp0 = 0, sp1 = 0;
 #pragma unroll
-            for (int i = 0; i < R; i++) sp = fma(v[i], v[i], sp);
-            const C sig2 = warp_sum(sp);
+            for (int i = 0; i < R; i += 2) {
+                sp0 = fma(v[i], v[i], sp0);
+                if (i + 1 < R) sp1 = fma(v[i + 1], v[i + 1], sp1);
+            }
+            const C sig2 = warp_sum(sp0 + sp1);
             const C x0 = __shfl_sync(FULL, xl, c);
             const C nrm = rnd<S>(sqrt(sig2));
             if (nrm != C(0)) {
                 const C alpha = x0 >= C(0) ? -nrm : nrm;
                 const C v0 = rnd<S>(x0 - alpha);
                 const C vtv = C(2) * nrm * (nrm + fabs(x0));
-                // the later columns and e_k (column nj), two at a time
-                for (int t = c + 1; t <= nj; t += 2) {
-                    const bool two = t + 1 <= nj;
-                    C xa[R], xb[R];
-                    C ga = 0, gb = 0;
+                // the later columns and e_k (column nj), four at a time
+                for (int t = c + 1; t <= nj; t += 4) {
+                    const int nt = min(4, nj + 1 - t);
+                    C xs[4][R];
+                    C g[4];
 #pragma unroll
-                    for (int i = 0; i < R; i++) {
-                        const int row = lane + 32 * i;
-                        xa[i] = row < m ? X[row * LDX + t] : C(0);
-                        xb[i] = (two && row < m) ? X[row * LDX + t + 1] : C(0);
+                    for (int u = 0; u < 4; u++) {
+                        g[u] = 0;
+#pragma unroll
+                        for (int i = 0; i < R; i++) xs[u][i] = u < nt ? Xl[i * 32 * LDX + t + u] : C(0);
                     }
 #pragma unroll
-                    for (int i = 0; i < R; i++) {
-                        ga = fma(v[i], xa[i], ga);
-                        gb = fma(v[i], xb[i], gb);
-                    }
+                    for (int i = 0; i < R; i++)
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        ga += __shfl_xor_sync(FULL, ga, o);
-                        gb += __shfl_xor_sync(FULL, gb, o);
-                    }
-                    const C acta = __shfl_sync(FULL, xa[0], c);
-                    const C actb = __shfl_sync(FULL, xb[0], c);
-                    const C sva = ga + (v0 - x0) * acta, svb = gb + (v0 - x0) * actb;
-                    const C fa = rnd<S>((sva + sva) / vtv), fb = rnd<S>((svb + svb) / vtv);
+                        for (int u = 0; u < 4; u++) g[u] = fma(v[i], xs[u][i], g[u]);
 #pragma unroll
-                    for (int i = 0; i < R; i++) {
-                        const int row = lane + 32 * i;
-                        if (row < m && row > c) {
-                            X[row * LDX + t] = rnd<S>(xa[i] - fa * v[i]);
-                            if (two) X[row * LDX + t + 1] = rnd<S>(xb[i] - fb * v[i]);
-                        } else if (row == c) {
-                            X[row * LDX + t] = rnd<S>(acta - fa * v0);
-                            if (two) X[row * LDX + t + 1] = rnd<S>(actb - fb * v0);
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int u = 0; u < 4; u++) g[u] += __shfl_xor_sync(FULL, g[u], o);
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        if (u < nt) {
+                            const C act = __shfl_sync(FULL, xs[u][0], c);
+                            const C sv = g[u] + (v0 - x0) * act;
+                            const C f = rnd<S>((sv + sv) / vtv);
+                            if (lane > c) Xl[t + u] = rnd<S>(xs[u][0] - f * v[0]);
+                            else if (lane == c) Xl[t + u] = rnd<S>(act - f * v0);
+#pragma unroll
+                            for (int i = 1; i < R; i++) Xl[i * 32 * LDX + t + u] = rnd<S>(xs[u][i] - f * v[i]);
                         }
                     }
                 }
-                if (lane == c) X[c * LDX + c] = alpha;
+                if (lane == c) Xl[c] = alpha;
             }
         }
         __syncwarp();
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
         }
         C s2p = 0;
         for (int p = lane; p < m; p += 32) {
-            const C sp = rnd<S>(rnd<S>(sres[p]) - (p == rk ? C(1) : C(0)));
+            const C sp = rnd<S>(rnd<S>(sres[p]) - (p == 0 ? C(1) : C(0)));
             s2p = fma(sp, sp, s2p);
         }
         const C snorm = rnd<S>(sqrt(warp_sum(s2p)));
@@ -285,7 +294,7 @@ template <class S, int R, int NC>
 int launch_spai_mid(const SpaiArgs& a, int num_sms, size_t smem_cap, cudaStream_t s)
 {
     typedef MidCfg<S, R, NC> Cfg;
-    const size_t smem = Cfg::bytes() * Cfg::WPB;
+    const size_t smem = Cfg::stride() * Cfg::WPB;
     if (smem > smem_cap) return SPAI_ERR_UNSUPPORTED;
     void (*kern)(SpaiArgs) = k_spai_mid<S, R, NC>;
     SPAI_CUDA_TRY(allow_max_dynamic_smem(kern));
@@ -299,22 +308,26 @@ int launch_spai_mid(const SpaiArgs& a, int num_sms, size_t smem_cap, cudaStream_
     return 0;
 }
 
-// bins 2..7 of spai_bin (bin 7 at u_f = double: the 16-warp CTA kernel)
+// bins 2 .. SPAI_NBINS-1 of spai_bin (bin 13 at u_f = double: the 16-warp
+// CTA kernel, launched by launch_spai_t)
 template <class S>
-int launch_spai_cta_nw16(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
-
-template <class S>
-int launch_spai_mid_bin(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s)
+int launch_spai_mid_bin_t(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s)
 {
     switch (bin) {
-    case 2: return launch_spai_mid<S, 4, 16>(a, num_sms, smem_cap, s);
-    case 3: return launch_spai_mid<S, 8, 16>(a, num_sms, smem_cap, s);
-    case 4: return launch_spai_mid<S, 4, 32>(a, num_sms, smem_cap, s);
-    case 5: return launch_spai_mid<S, 8, 32>(a, num_sms, smem_cap, s);
-    case 6: return launch_spai_mid<S, 16, 16>(a, num_sms, smem_cap, s);
-    case 7:
-        if constexpr (std::is_same<S, double>::value) return launch_spai_cta_nw16<S>(a, num_sms, smem_cap, s);
-        else return launch_spai_mid<S, 16, 32>(a, num_sms, smem_cap, s);
+    case 2: return launch_spai_mid<S, 3, 16>(a, num_sms, smem_cap, s);
+    case 3: return launch_spai_mid<S, 4, 16>(a, num_sms, smem_cap, s);
+    case 4: return launch_spai_mid<S, 5, 16>(a, num_sms, smem_cap, s);
+    case 5: return launch_spai_mid<S, 6, 16>(a, num_sms, smem_cap, s);
+    case 6: return launch_spai_mid<S, 7, 16>(a, num_sms, smem_cap, s);
+    case 7: return launch_spai_mid<S, 8, 16>(a, num_sms, smem_cap, s);
+    case 8: return launch_spai_mid<S, 10, 16>(a, num_sms, smem_cap, s);
+    case 9: return launch_spai_mid<S, 12, 16>(a, num_sms, smem_cap, s);
+    case 10: return launch_spai_mid<S, 16, 16>(a, num_sms, smem_cap, s);
+    case 11: return launch_spai_mid<S, 4, 32>(a, num_sms, smem_cap, s);
+    case 12: return launch_spai_mid<S, 8, 32>(a, num_sms, smem_cap, s);
+    case 13:
+        if constexpr (!std::is_same<S, double>::value) return launch_spai_mid<S, 16, 32>(a, num_sms, smem_cap, s);
+        else return SPAI_ERR_INTERNAL;
     default: return SPAI_ERR_INTERNAL;
     }
 }

@@ -112,8 +112,11 @@ SPAI_CASES = [
     ("rand-patA-mid", lambda: synth.random_sparse(2000, 12, seed=17), O.PAT_A, 16),
     # 22 pattern columns and shadows of at most 101 rows: the 128 x 32 shared-memory tile
     ("band-patA", lambda: banded(600, 25, 22, seed=19), O.PAT_A, 30),
-    # 16 pattern columns, shadows of 129-512 rows: the 256 x 16 and 512 x 16 tiles
-    ("rand-patA-16", lambda: synth.random_sparse(1500, 18, seed=23), O.PAT_A, 16),
+    # 16 pattern columns and shadows of 161-320 rows: the 192 x 16 .. 320 x 16 tiles
+    ("rand-patA-16", lambda: synth.random_sparse(1500, 15, seed=37), O.PAT_A, 16),
+    # 16 pattern columns and shadows of 257-512 rows: the 320 x 16, 384 x 16, 512 x 16 tiles
+    ("rand-patA-16-wide", lambda: synth.random_sparse(1500, 22, seed=29), O.PAT_A, 16),
+    ("rand-patA-16-widest", lambda: synth.random_sparse(1500, 27, seed=29), O.PAT_A, 16),
 ]
 
 
@@ -137,17 +140,17 @@ def banded(n, w, per_row, seed):
 
 
 def column_bins(Icnt, Jcnt):
-    """The column kernel each fixed-pattern column runs in (bins of the CUDA path):
-    0/1 register-tile warp kernel (32/64 rows), 2..7 shared-memory-tile warp kernel
-    (128/256/512 rows by 16/32 columns), 8 the large-shadow kernel."""
+    """The column kernel each fixed-pattern column runs in (the bins of the CUDA path):
+    0/1 the register-tile warp kernel (32/64 rows), 2..13 the shared-memory-tile warp
+    kernel (32 R rows by 16 or 32 columns), 14 the large-shadow kernel."""
     out = []
     for m, nj in zip(Icnt, Jcnt):
+        R = (m + 31) // 32
         if m <= 32: b = 0
         elif m <= 64: b = 1
-        elif m <= 128: b = 2 if nj <= 16 else 4
-        elif m <= 256: b = 3 if nj <= 16 else 5
-        elif m <= 512: b = 6 if nj <= 16 else 7
-        else: b = 8
+        elif m > 512: b = 14
+        elif nj <= 16: b = R - 1 if R <= 8 else (8 if R <= 10 else (9 if R <= 12 else 10))
+        else: b = 11 if R <= 4 else (12 if R <= 8 else 13)
         out.append(b)
     return np.array(out)
 
@@ -161,13 +164,17 @@ def test_spai_fixed_pattern_parity(ctx, name, make, init, F, uf):
     n = ref["n"]
     bins = column_bins(ref["Icnt"], ref["Jcnt"])
     if name == "rand-patA-mid":
-        assert np.sum(bins == 2) > 100 and np.sum(bins == 3) > 100
+        assert all(np.sum(bins == b) > 100 for b in (3, 4))
     if name == "band-patA":
-        assert np.mean(bins == 4) > 0.9
+        assert np.mean(bins == 11) > 0.9
     if name == "rand-patA-wide":
-        assert np.sum(bins == 5) > 100 and np.sum(bins == 7) > 100
+        assert np.sum(bins == 12) > 100 and np.sum(bins == 13) > 100
     if name == "rand-patA-16":
-        assert np.sum(bins == 3) > 100 and np.sum(bins == 6) > 100
+        assert all(np.sum(bins == b) > 100 for b in (5, 6, 7))
+    if name == "rand-patA-16-wide":
+        assert all(np.sum(bins == b) > 100 for b in (8, 9))
+    if name == "rand-patA-16-widest":
+        assert all(np.sum(bins == b) > 100 for b in (9, 10))
     # pattern: bit-exact
     assert np.array_equal(np.diff(rp), ref["Jcnt"])
     for k in range(n):
