@@ -235,9 +235,20 @@ def job_throughput(world, steps, max_ms):
 
 # ---------------------------------------------------------------- other workloads (reported beside the headline)
 
+def backward_error(A, b, x):
+    """Normwise backward error max|b - A x| / (||A||_inf max|x| + max|b|) in float64."""
+    import scipy.sparse as sp
+    rp, ci, va = A
+    n = len(rp) - 1
+    M = sp.csr_matrix((va, ci, rp), shape=(n, n))
+    r = b - M @ x
+    return float(np.max(np.abs(r)) / (abs(M).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+
+
 def serve_stream(S, dev, reqs, arrivals, so, io, budget=120 << 30):
     """Submit reqs[i] = (A, b) at arrivals[i] (seconds) to a serving context and poll
-    until all are done; returns (latencies in ms = completion - arrival, makespan s)."""
+    until all are done; returns (latencies in ms = completion - arrival, makespan s,
+    largest backward error of the solutions)."""
     sctx = S.Context(dev.index or 0, hbm_budget=budget)
     # warm the workers and kernels
     t = S.solver_submit(sctx, reqs[0][0], reqs[0][1], so, io)
@@ -246,6 +257,7 @@ def serve_stream(S, dev, reqs, arrivals, so, io, budget=120 << 30):
     R = len(reqs)
     pending = {}
     lat = [None] * R
+    xs = [None] * R
     t0 = time.perf_counter()
     nxt = 0
     while nxt < R or pending:
@@ -254,14 +266,16 @@ def serve_stream(S, dev, reqs, arrivals, so, io, budget=120 << 30):
             pending[nxt] = S.solver_submit(sctx, reqs[nxt][0], reqs[nxt][1], so, io)
             nxt += 1
         for i in list(pending):
-            stt = S.solver_poll(sctx, pending[i], np.zeros(len(reqs[i][1])))
+            xs[i] = np.zeros(len(reqs[i][1]))
+            stt = S.solver_poll(sctx, pending[i], xs[i])
             if stt is not None:
                 lat[i] = (time.perf_counter() - t0) - arrivals[i]
                 del pending[i]
         time.sleep(0.0002)
     makespan = time.perf_counter() - t0
     sctx.close()
-    return np.array(lat) * 1000.0, makespan
+    nbe = max(backward_error(A, b, xs[i]) for i, (A, b) in enumerate(reqs))
+    return np.array(lat) * 1000.0, makespan, nbe
 
 
 def extra_workloads(S, synth, torch, dev):
@@ -272,9 +286,9 @@ def extra_workloads(S, synth, torch, dev):
     * adaptive: Grote-Huckle SPAI from the identity on a 100,000-column random nonsymmetric
       matrix (16 nonzeros per column, row/column scaling 1e6), eps 0.5, beta 8, fill cap 30,
       u_f single, then the solve with (single, double, double, double, quad);
-    * serving: 48 requests of 3D systems (grids 10^3..46^3, log-uniform) arriving as a
-      Poisson stream at 200 requests/s into a context with a 120 GB admission budget;
-      latency = completion - arrival;
+    * serving: Poisson streams at 10, 30, 100, 300, 1000 and 2000 requests/s of 3D systems
+      (n log-uniform in [1e3, 1e6]) into a context with a 120 GB admission budget, in the
+      mixed tuple and in the all-FP64 form; latency = completion - arrival;
     * batched: 512 independent systems (half 2D convection-diffusion, half random sparse,
       n log-uniform in [2e3, 5e4]): spai_build_batch and gmres_ir_solve_batch (refinements in shared
       cooperative launches), beside the same systems submitted at once to the serving queue."""
@@ -354,28 +368,42 @@ def extra_workloads(S, synth, torch, dev):
                                 steps=st["steps"], backward_error=nbe)
     P.free()
     ctx.close()
-    # ---- serving: the same Poisson stream with the mixed tuple and in the all-FP64 form
+    # ---- serving: Poisson streams at 10..2000 requests/s of 3D systems with n log-uniform in
+    # [1e3, 1e6], the mixed tuple and the all-FP64 form, 120 GB admission budget
     rng = np.random.default_rng(5)
-    R, rate = 48, 200.0
-    grids = np.round(np.exp(rng.uniform(np.log(10), np.log(46), size=R))).astype(int)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=R))
-    reqs = []
-    for i, N in enumerate(grids):
+    pool = []
+    for i, N in enumerate(np.round(np.exp(rng.uniform(np.log(10), np.log(100), size=32))).astype(int)):
         A3 = synth.conv_diff_3d(int(N), 50.0, seed=100 + i)
         b3, _ = synth.rhs(A3, seed=200 + i)
-        reqs.append((A3, b3))
+        pool.append((A3, b3))
     so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3)
-    io = S.make_ir_opts(uf="half", u="single", ug="single", up="double", ur="double", tau=1e-4)
-    lat, makespan = serve_stream(S, dev, reqs, arrivals, so, io)
+    io = S.make_ir_opts(uf="half", u="single", ug="single", up="double", ur="double", tau=1e-4, orth=2)
     so64 = S.make_spai_opts(init=2, max_fill=25, uf="double", eps=0.3)
-    io64 = S.make_ir_opts(uf="double", u="double", ug="double", up="double", ur="double", tau=1e-4)
-    lat64, makespan64 = serve_stream(S, dev, reqs, arrivals, so64, io64)
-    out["serving"] = dict(workload="48 requests, 3D conv-diff grids 10^3..46^3 (log-uniform), Poisson 200/s, "
-                                   "(half,single,single,double,double), budget 120 GB, host inputs",
-                          requests=R, solves_per_s=R / makespan, p50_ms=float(np.percentile(lat, 50)),
-                          p99_ms=float(np.percentile(lat, 99)), sum_n=int(sum(int(g) ** 3 for g in grids)),
+    io64 = S.make_ir_opts(uf="double", u="double", ug="double", up="double", ur="double", tau=1e-4, orth=2)
+    sweep = []
+    for rate in (10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0):
+        R = int(min(96, max(16, 2.0 * rate)))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=R))
+        reqs = [pool[int(j)] for j in rng.integers(0, len(pool), size=R)]
+        lat, makespan, nbe = serve_stream(S, dev, reqs, arrivals, so, io)
+        lat64, makespan64, nbe64 = serve_stream(S, dev, reqs, arrivals, so64, io64)
+        sweep.append(dict(rate=rate, requests=R, sum_n=int(sum(len(b3) for _, b3 in reqs)),
+                          solves_per_s=R / makespan, p50_ms=float(np.percentile(lat, 50)),
+                          p99_ms=float(np.percentile(lat, 99)), backward_error_max=nbe,
                           fp64=dict(solves_per_s=R / makespan64, p50_ms=float(np.percentile(lat64, 50)),
-                                    p99_ms=float(np.percentile(lat64, 99))))
+                                    p99_ms=float(np.percentile(lat64, 99)), backward_error_max=nbe64),
+                          mixed_over_fp64=makespan64 / makespan))
+    out["serving"] = dict(workload="Poisson streams at 10..2000 requests/s (16..96 requests each), 3D conv-diff "
+                                   "(Peclet 50, lognormal coefficients) grids 10^3..100^3 (n log-uniform in "
+                                   "[1e3, 1e6], 32 distinct systems), pattern(A^2) cap 25, one-reduction MGS, "
+                                   "(half,single,single,double,double) against (double x5), budget 120 GB, "
+                                   "host inputs; latency = completion - arrival",
+                          sweep=sweep)
+    out["fp64_serving"] = dict(workload="the serving sweep's streams in the all-FP64 form (double x5)",
+                               sweep=[dict(rate=w["rate"], solves_per_s=w["fp64"]["solves_per_s"],
+                                           p50_ms=w["fp64"]["p50_ms"], p99_ms=w["fp64"]["p99_ms"],
+                                           backward_error_max=w["fp64"]["backward_error_max"],
+                                           mixed_over_fp64=w["mixed_over_fp64"]) for w in sweep])
     # ---- batched: 512 independent systems through the queue at once
     rng = np.random.default_rng(4)
     R = 512
@@ -391,7 +419,7 @@ def extra_workloads(S, synth, torch, dev):
         b2, _ = synth.rhs(A2, seed=3000 + i)
         batch.append((A2, b2))
     so = S.make_spai_opts(init=1, max_fill=30, uf="single")
-    io = S.make_ir_opts(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4)
+    io = S.make_ir_opts(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4, orth=ORTH)
     bctx = S.Context(dev.index or 0, hbm_budget=120 << 30)
     t = S.solver_submit(bctx, batch[0][0], batch[0][1], so, io)
     while S.solver_poll(bctx, t) is None:
@@ -412,7 +440,9 @@ def extra_workloads(S, synth, torch, dev):
     makespan = time.perf_counter() - t0
     bctx.close()
     sum_n = int(sum(len(a[0]) - 1 for a, _ in batch))
-    queue = dict(solves_per_s=R / makespan, makespan_s=makespan, converged=conv, total_its=its)
+    queue = dict(solves_per_s=R / makespan, makespan_s=makespan, converged=conv, total_its=its,
+                 p50_ms=float(np.percentile(list(done.values()), 50) * 1000.0),
+                 p99_ms=float(np.percentile(list(done.values()), 99) * 1000.0))
     # the same systems through spai_build_batch (concurrent builds) and gmres_ir_solve_batch (all
     # refinements in shared cooperative launches); host inputs and outputs, copies timed
     bctx = S.Context(dev.index or 0)
@@ -430,11 +460,13 @@ def extra_workloads(S, synth, torch, dev):
         P_.free()
     bctx.close()
     batch_api = dict(solves_per_s=R / (t2 - t0), makespan_s=t2 - t0, spai_s=t1 - t0, refinement_s=t2 - t1,
+                     spai_cols_per_s=sum(len(b2) for _, b2 in batch) / (t1 - t0),
                      refinement_launches=int(sts[0]["launches"]), converged=int(sum(int(st_["flags"] & 1) for st_ in sts)),
-                     total_its=int(sum(st_["total_its"] for st_ in sts)))
+                     total_its=int(sum(st_["total_its"] for st_ in sts)),
+                     backward_error_max=max(backward_error(A2, b2, x2) for (A2, b2), x2 in zip(batch, xs)))
     # the same systems in the all-FP64 form (every precision double)
     so64 = S.make_spai_opts(init=1, max_fill=30, uf="double")
-    io64 = S.make_ir_opts(uf="double", u="double", ug="double", up="double", ur="double", tau=1e-4)
+    io64 = S.make_ir_opts(uf="double", u="double", ug="double", up="double", ur="double", tau=1e-4, orth=ORTH)
     bctx = S.Context(dev.index or 0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -449,14 +481,18 @@ def extra_workloads(S, synth, torch, dev):
     fp64_batch = dict(solves_per_s=R / (t2 - t0), makespan_s=t2 - t0, spai_s=t1 - t0, refinement_s=t2 - t1,
                       converged=int(sum(int(st_["flags"] & 1) for st_ in sts64)),
                       total_its=int(sum(st_["total_its"] for st_ in sts64)),
+                      backward_error_max=max(backward_error(A2, b2, x2) for (A2, b2), x2 in zip(batch, xs)),
                       mixed_over_fp64=(R / batch_api["makespan_s"]) / (R / (t2 - t0)))
     out["batched_512"] = dict(workload="512 systems, n log-uniform in [2e3, 5e4]: even = 2D conv-diff (Peclet "
                                        "U(0,50)), odd = random sparse 8-16 nnz/col with row/column scaling "
                                        "10^U(1,3) (cond_1 ~1e2-5e3); pattern(A), (single,double,single,single,double), tau 1e-4, "
+                                       "one-reduction MGS, "
                                        "host inputs; value = gmres_ir_solve_batch path, serving_queue = all submitted to the queue at once",
                               systems=R, solves_per_s=batch_api["solves_per_s"],
                               cols_per_s=sum_n / batch_api["makespan_s"], sum_n=sum_n,
                               batch_api=batch_api, serving_queue=queue, fp64_batch_api=fp64_batch)
+    out["fp64_batched"] = dict(workload="the 512 systems of batched_512 in the all-FP64 form (double x5), "
+                                        "spai_build_batch + gmres_ir_solve_batch", **fp64_batch)
     return out
 
 

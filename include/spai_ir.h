@@ -230,12 +230,14 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
                    const double* b, double* x, const ir_opts* opts, ir_stats* st);
 
 /* Algorithm 3 for `count` independent systems with the same options (a batch
- * of the paper's solve; the batching is this library's).  All systems share
- * one persistent cooperative launch of the refinement kernel: the grid is
- * split into teams of equal size (about 2048 rows per block at the median
- * order, at most 16 blocks), and each team solves one system after another,
- * larger systems first.  Every system's buffers are allocated before the
- * launch.  A[i] is a
+ * of the paper's solve; the batching is this library's).  The systems share
+ * one persistent cooperative launch of the refinement kernel whose grid is
+ * split into teams of blocks; each team solves one system after another,
+ * larger systems first.  A system's team size depends on its order alone
+ * (about 8192 rows per block, at most 16 blocks), so its result is the same
+ * in any batch.  Systems of more than 65536 rows run afterwards, each on a
+ * grid of its own as in gmres_ir_solve.  Every system's buffers are
+ * allocated before the launch.  A[i] is a
  * host or device CSR and b[i], x[i] follow A[i].on_device.  P may be NULL or
  * hold NULL entries (that system is unpreconditioned); preconditioners come
  * from spai_build with the same u_f as opts->uf.  st (count entries, may be
@@ -247,11 +249,21 @@ int gmres_ir_solve_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_
                          const double* const* b, double* const* x, const ir_opts* opts,
                          ir_stats* st, int* status);
 
-/* Serving queue.  solver_submit copies A and b (host or device, as
- * A->on_device says) into the context and returns a ticket at once; requests
- * are admitted to the GPU while their estimated device footprint fits the
- * context's HBM budget, and admitted requests run concurrently.  Returns
- * SPAI_ERR_ADMISSION if the request alone exceeds the budget. */
+/* Serving queue with continuous batching.  solver_submit copies A and b
+ * (host or device, as A->on_device says) into the context and returns a
+ * ticket at once.  An admission thread admits every waiting request whose
+ * estimated device footprint fits what the context's HBM budget has left (a
+ * request passed over for more than 200 ms is admitted before any later
+ * one), uploads the admitted requests and builds their preconditioners
+ * (requests with the same fixed-pattern options: one build over the
+ * block-diagonal union, as spai_build_batch); a refinement thread solves the
+ * prepared requests with the same options together, as gmres_ir_solve_batch
+ * does.  Requests that arrive while others are being solved are admitted
+ * and prepared meanwhile and join the next launch.  A request's result does
+ * not depend on the other requests: alone or in a mix it is the same, bit
+ * for bit.  Each request's A, P, b and x stay on the device until it is
+ * solved.  Returns SPAI_ERR_ADMISSION if the request alone exceeds the
+ * budget. */
 int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_opts* sopts,
                   const ir_opts* opts, uint64_t* ticket);
 

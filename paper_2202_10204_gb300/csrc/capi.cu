@@ -3,6 +3,7 @@
 // the kernels in spai_build.cu and gmres_ir.cu.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -252,6 +253,23 @@ size_t estimate_footprint(int64_t n, int64_t nnz, const spai_opts* so, const ir_
 
 // ------------------------------------------------------------------ serving
 
+// Continuous batching.  solver_submit queues a request and returns; the
+// admission thread admits every waiting request whose estimated footprint
+// fits what the budget has left (a request passed over for longer than
+// SERVE_MAX_BYPASS_MS is then admitted before any later one), uploads the
+// admitted group, builds its preconditioners (fixed patterns: one build over
+// the block-diagonal union, as spai_build_batch) and hands the group to the
+// refinement thread, which solves it with the batched refinement
+// (gmres_ir_batch_dev: teams of blocks sized by each system's order, larger
+// systems on a grid of their own).  Requests that arrive while a group is
+// being solved are admitted and prepared meanwhile (the admission thread's
+// kernels share the GPU with the running refinement) and are solved in the
+// next launch; each request's A, P, b and x stay on the device until its
+// group is done.  A request's result depends only on the request: the union
+// build gives each matrix its single-build preconditioner, and a system's
+// team size is a function of its order.
+constexpr double SERVE_MAX_BYPASS_MS = 200.0;
+
 struct ServeRequest {
     uint64_t ticket = 0;
     int64_t n = 0, nnz = 0;
@@ -262,77 +280,218 @@ struct ServeRequest {
     ir_opts io{};
     bool has_so = false;
     size_t bytes = 0;
+    std::chrono::steady_clock::time_point t_submit;
     bool done = false;
     int status = 0;
     ir_stats st{};
+    // device state while admitted
+    DevCsr dA;
+    double* db = nullptr;
+    double* dx = nullptr;
+    spai_precond P = nullptr;
+    int spai_rc = 0;
 };
 
-static void run_request(spai_ctx ctx, cudaStream_t s, ServeRequest* r)
+static void serve_release(spai_ctx ctx, ServeRequest* r, cudaStream_t s)
 {
-    cudaSetDevice(ctx->device);
-    spai_csr A{r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(), 0};
-    DevCsr dA;
-    double *db = nullptr, *dx = nullptr;
-    spai_precond P = nullptr;
-    int rc = csr_to_device(&A, &dA, s);
-    if (!rc) rc = dev_alloc((void**)&db, sizeof(double) * r->n, s);
-    if (!rc) rc = dev_alloc((void**)&dx, sizeof(double) * r->n, s);
-    if (!rc && cudaMemcpyAsync(db, r->b.data(), sizeof(double) * r->n, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
-    int wrc = 0;
-    if (!rc && r->has_so) {
-        spai_stats sst{};
-        rc = spai_build_dev(ctx->device, ctx->num_sms, s, dA, &r->so, &P, &sst);
-        if (rc > 0) { wrc = rc; rc = 0; }
-        r->st.ms_spai = sst.ms;
-        r->st.launches = sst.launches;
-    }
-    if (rc >= 0 && !(rc < 0)) {
-        int rr = gmres_ir_dev(ctx->device, ctx->num_sms, s, dA, P, db, dx, &r->io, &r->st);
-        if (rr < 0) rc = rr; else if (rr > 0) wrc = rr;
-    }
-    if (rc >= 0) {
-        r->x.resize(r->n);
-        if (cudaMemcpyAsync(r->x.data(), dx, sizeof(double) * r->n, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
-    if (P) spai_precond_free(P);
-    dev_free(db, s);
-    dev_free(dx, s);
-    csr_release(&dA, s);
-    cudaStreamSynchronize(s);
-    if (rc == SPAI_ERR_CUDA) {
-        // the status code alone does not say which call failed
-        const cudaError_t e = cudaGetLastError();
-        fprintf(stderr, "spai serving: request of order %lld failed: %s\n", (long long)r->n, cudaGetErrorString(e));
-    }
-    r->status = rc < 0 ? rc : wrc;
+    if (r->P) spai_precond_free(r->P);
+    r->P = nullptr;
+    dev_free(r->db, s);
+    dev_free(r->dx, s);
+    r->db = r->dx = nullptr;
+    csr_release(&r->dA, s);
 }
 
-static void worker_loop(spai_ctx ctx, int widx)
+// requests of one group share their options (one batched launch)
+static bool same_opts(const ServeRequest* a, const ServeRequest* b)
 {
-    cudaSetDevice(ctx->device);
-    cudaStream_t s = ctx->worker_streams[widx];
-    for (;;) {
-        ServeRequest* r = nullptr;
-        {
-            std::unique_lock<std::mutex> lk(ctx->qmu);
-            // admit the oldest request once its footprint fits the budget
-            ctx->qcv.wait(lk, [&] {
-                return ctx->stopping || (!ctx->pending.empty() && ctx->in_use + ctx->pending.front()->bytes <= ctx->budget);
-            });
-            if (ctx->stopping && ctx->pending.empty()) return;
-            if (ctx->pending.empty()) continue;
-            r = ctx->pending.front();
-            ctx->pending.pop_front();
-            ctx->in_use += r->bytes;
-        }
-        run_request(ctx, s, r);
-        {
-            std::lock_guard<std::mutex> lk(ctx->qmu);
+    if (a->has_so != b->has_so || memcmp(&a->io, &b->io, sizeof(ir_opts)) != 0) return false;
+    return !a->has_so || memcmp(&a->so, &b->so, sizeof(spai_opts)) == 0;
+}
+
+static void serve_finish(spai_ctx ctx, const std::vector<ServeRequest*>& g, cudaStream_t s)
+{
+    cudaStreamSynchronize(s);
+    for (ServeRequest* r : g) serve_release(ctx, r, s);
+    cudaStreamSynchronize(s);
+    {
+        std::lock_guard<std::mutex> lk(ctx->qmu);
+        for (ServeRequest* r : g) {
             ctx->in_use -= r->bytes;
             r->done = true;
         }
-        ctx->qcv.notify_all();
+        ctx->qgen++;
+    }
+    ctx->qcv.notify_all();
+}
+
+static int spai_build_union(spai_ctx ctx, cudaStream_t s, int lo, int hi, const spai_csr* A, const spai_opts* opts,
+                            spai_precond* P_out, spai_stats* st, int* rcs);
+
+// Upload a group and build its preconditioners (admission thread).  Requests
+// that fail are finished at once with their error; the rest go to the
+// refinement thread.
+static void serve_prepare(spai_ctx ctx, std::vector<ServeRequest*>& g, cudaStream_t s)
+{
+    std::vector<ServeRequest*> ok;
+    for (ServeRequest* r : g) {
+        spai_csr A{r->n, r->nnz, r->rowptr.data(), r->col.data(), r->val.data(), 0};
+        int rc = csr_to_device(&A, &r->dA, s);
+        if (!rc) rc = dev_alloc((void**)&r->db, sizeof(double) * r->n, s);
+        if (!rc) rc = dev_alloc((void**)&r->dx, sizeof(double) * r->n, s);
+        if (!rc && cudaMemcpyAsync(r->db, r->b.data(), sizeof(double) * r->n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = SPAI_ERR_CUDA;
+        r->status = rc;
+    }
+    const ServeRequest* g0 = g.front();
+    if (g0->has_so) {
+        std::vector<ServeRequest*> todo;
+        for (ServeRequest* r : g)
+            if (r->status == 0) todo.push_back(r);
+        const int cnt = (int)todo.size();
+        std::vector<spai_csr> As(cnt);
+        std::vector<spai_precond> Ps(cnt, nullptr);
+        std::vector<spai_stats> sts(cnt);
+        std::vector<int> rcs(cnt, 0);
+        for (int i = 0; i < cnt; i++) {
+            const DevCsr& d = todo[i]->dA;
+            As[i] = spai_csr{d.n, d.nnz, d.rowptr, d.col, d.val, 1};
+            memset(&sts[i], 0, sizeof(spai_stats));
+        }
+        bool built = false;
+        if (cnt > 1 && !g0->so.adaptive && (g0->so.side == 0 || g0->so.side == 1))
+            built = spai_build_union(ctx, s, 0, cnt, As.data(), &g0->so, Ps.data(), sts.data(), rcs.data()) == 0;
+        if (!built) {
+            for (int i = 0; i < cnt; i++) {
+                if (Ps[i]) { spai_precond_free(Ps[i]); Ps[i] = nullptr; }
+                memset(&sts[i], 0, sizeof(spai_stats));
+                rcs[i] = spai_build_dev(ctx->device, ctx->num_sms, s, todo[i]->dA, &g0->so, &Ps[i], &sts[i]);
+            }
+        }
+        for (int i = 0; i < cnt; i++) {
+            ServeRequest* r = todo[i];
+            r->P = Ps[i];
+            r->st.ms_spai = sts[i].ms;
+            r->st.launches = sts[i].launches;
+            if (rcs[i] < 0) r->status = rcs[i];
+            else r->spai_rc = rcs[i];
+        }
+    }
+    cudaStreamSynchronize(s);
+    std::vector<ServeRequest*> failed;
+    for (ServeRequest* r : g) (r->status < 0 ? failed : ok).push_back(r);
+    if (!failed.empty()) serve_finish(ctx, failed, s);
+    if (!ok.empty()) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->qmu);
+            ctx->ready.push_back(std::move(ok));
+        }
+        ctx->rcv.notify_all();
+    }
+}
+
+static void serve_admission_loop(spai_ctx ctx)
+{
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->worker_streams[0];
+    uint64_t seen = 0;
+    for (;;) {
+        std::vector<ServeRequest*> take;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->qcv.wait(lk, [&] { return ctx->stopping || (!ctx->pending.empty() && ctx->qgen != seen); });
+            if (ctx->stopping) return;
+            seen = ctx->qgen;
+            const auto now = std::chrono::steady_clock::now();
+            bool head_only = false;
+            for (auto it = ctx->pending.begin(); it != ctx->pending.end();) {
+                ServeRequest* r = *it;
+                if (r->bytes <= ctx->budget - ctx->in_use) {
+                    ctx->in_use += r->bytes;
+                    take.push_back(r);
+                    it = ctx->pending.erase(it);
+                    continue;
+                }
+                // the oldest request that does not fit: after waiting long enough it
+                // keeps the freed budget for itself
+                if (it == ctx->pending.begin() &&
+                    std::chrono::duration<double, std::milli>(now - r->t_submit).count() > SERVE_MAX_BYPASS_MS)
+                    head_only = true;
+                if (head_only) break;
+                ++it;
+            }
+        }
+        // groups of requests with the same options, in arrival order
+        while (!take.empty()) {
+            std::vector<ServeRequest*> g, rest;
+            for (ServeRequest* r : take) (same_opts(take.front(), r) ? g : rest).push_back(r);
+            serve_prepare(ctx, g, s);
+            take.swap(rest);
+        }
+    }
+}
+
+static void serve_refine_loop(spai_ctx ctx)
+{
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = ctx->worker_streams[1];
+    for (;;) {
+        std::vector<ServeRequest*> g;
+        {
+            std::unique_lock<std::mutex> lk(ctx->qmu);
+            ctx->rcv.wait(lk, [&] { return ctx->stopping || !ctx->ready.empty(); });
+            if (ctx->stopping) return;
+            // every prepared group with the same options as the oldest joins its launch
+            g = std::move(ctx->ready.front());
+            ctx->ready.pop_front();
+            for (auto it = ctx->ready.begin(); it != ctx->ready.end();) {
+                if (same_opts(g.front(), it->front())) {
+                    g.insert(g.end(), it->begin(), it->end());
+                    it = ctx->ready.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        const int cnt = (int)g.size();
+        std::vector<DevCsr> As(cnt);
+        std::vector<spai_precond> Ps(cnt);
+        std::vector<const double*> bs(cnt);
+        std::vector<double*> xs(cnt);
+        std::vector<ir_stats> sts(cnt);
+        std::vector<int> status(cnt, 0);
+        for (int i = 0; i < cnt; i++) {
+            As[i] = g[i]->dA;
+            As[i].owned = false;
+            if (g[i]->P) g[i]->P->stream = s;  // its frees and SELL copies go to this thread's stream now
+            Ps[i] = g[i]->P;
+            bs[i] = g[i]->db;
+            xs[i] = g[i]->dx;
+            memset(&sts[i], 0, sizeof(ir_stats));
+        }
+        int rc = gmres_ir_batch_dev(ctx->device, ctx->num_sms, s, cnt, As.data(), Ps.data(), bs.data(), xs.data(),
+                                    &g.front()->io, sts.data(), status.data());
+        for (int i = 0; i < cnt; i++) {
+            ServeRequest* r = g[i];
+            int ri = rc < 0 ? rc : status[i];
+            if (ri >= 0) {
+                r->x.resize(r->n);
+                if (cudaMemcpyAsync(r->x.data(), r->dx, sizeof(double) * r->n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                    ri = SPAI_ERR_CUDA;
+            }
+            const double ms_spai = r->st.ms_spai;
+            const int nl = r->st.launches;
+            r->st = sts[i];
+            r->st.ms_spai = ms_spai;
+            r->st.launches += nl;
+            if (r->P) r->st.nnz_P = r->P->nnz;
+            r->status = ri < 0 ? ri : (ri > 0 ? ri : r->spai_rc);
+        }
+        if (rc == SPAI_ERR_CUDA) {
+            const cudaError_t e = cudaGetLastError();
+            fprintf(stderr, "spai serving: a batch of %d requests failed: %s\n", cnt, cudaGetErrorString(e));
+        }
+        serve_finish(ctx, g, s);
     }
 }
 
@@ -373,7 +532,11 @@ void spai_ctx_destroy(spai_ctx c)
         c->stopping = true;
     }
     c->qcv.notify_all();
+    c->rcv.notify_all();
     for (auto& t : c->workers) t.join();
+    cudaSetDevice(c->device);
+    for (auto& g : c->ready)
+        for (ServeRequest* r : g) serve_release(c, r, c->stream);
     for (auto s : c->worker_streams) cudaStreamDestroy(s);
     for (auto& kv : c->tickets) delete kv.second;
     cudaSetDevice(c->device);
@@ -494,11 +657,10 @@ static size_t union_footprint(int64_t n, int64_t nnz, const spai_opts* o)
 // selects, so every preconditioner is the one spai_build gives for its
 // matrix, bit for bit.  Returns 0 with every handle set, or an error (the
 // caller then builds these matrices one by one, which attributes it).
-static int spai_build_union(spai_ctx ctx, int lo, int hi, const spai_csr* A, const spai_opts* opts,
+static int spai_build_union(spai_ctx ctx, cudaStream_t s, int lo, int hi, const spai_csr* A, const spai_opts* opts,
                             spai_precond* P_out, spai_stats* st, int* rcs)
 {
     const int count = hi - lo;
-    cudaStream_t s = ctx->stream;
     std::vector<int64_t> ro(count + 1, 0), zo(count + 1, 0);
     for (int i = 0; i < count; i++) {
         ro[i + 1] = ro[i] + A[lo + i].n;
@@ -751,7 +913,7 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
                 z = z2;
                 hi++;
             }
-            if (hi - lo < 2 || spai_build_union(ctx, lo, hi, A, opts, P_out, st, rcs.data()) != 0)
+            if (hi - lo < 2 || spai_build_union(ctx, ctx->stream, lo, hi, A, opts, P_out, st, rcs.data()) != 0)
                 rc = spai_build_each(ctx, lo, hi, A, opts, P_out, st, rcs.data());
             lo = hi;
         }
@@ -962,21 +1124,23 @@ int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_o
     if (sopts) { r->so = *sopts; r->has_so = true; }
     r->io = *opts;
     r->bytes = bytes;
+    r->t_submit = std::chrono::steady_clock::now();
     {
         std::lock_guard<std::mutex> lk(ctx->qmu);
         if (ctx->workers.empty()) {
-            const int nw = 4;
             cudaSetDevice(ctx->device);
-            for (int i = 0; i < nw; i++) {
+            for (int i = 0; i < 2; i++) {
                 cudaStream_t s;
                 if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { delete r; return SPAI_ERR_CUDA; }
                 ctx->worker_streams.push_back(s);
             }
-            for (int i = 0; i < nw; i++) ctx->workers.emplace_back(worker_loop, ctx, i);
+            ctx->workers.emplace_back(serve_admission_loop, ctx);
+            ctx->workers.emplace_back(serve_refine_loop, ctx);
         }
         r->ticket = ctx->next_ticket++;
         ctx->tickets[r->ticket] = r;
         ctx->pending.push_back(r);
+        ctx->qgen++;
         *ticket = r->ticket;
     }
     ctx->qcv.notify_all();

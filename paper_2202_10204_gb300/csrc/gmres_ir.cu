@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <map>
 #include <set>
 #include <vector>
 
@@ -659,31 +660,49 @@ extern "C" int spai_selftest_wait_timeout(int device, int mode, double limit_ms)
 }
 
 // ====================================================================
-// Batched refinement (gmres_ir_solve_batch): many independent systems in one
-// persistent cooperative launch.  Cooperative launches of separate systems
+// Batched refinement (gmres_ir_solve_batch): many independent systems in
+// persistent cooperative launches.  Cooperative launches of separate systems
 // hardly overlap on the GPU (16 solves of an n = 4096 system: 111 ms one
 // after another, 66-70 ms from 2 or 4 host threads), while one such system
-// keeps only 16 of 152 SMs busy.  The batch splits the co-resident grid into
-// teams of T blocks (T from the median order, about BATCH_ROWS_PER_BLOCK rows
-// per block, at most 16); each team takes the next system (larger first) as
-// soon as it is done with its last one, so systems with many GMRES iterations
-// do not hold up the others' SMs.  All systems are prepared before the launch
+// keeps only 16 of 152 SMs busy.  One launch splits the co-resident grid
+// into teams; each team takes the next system of its class (larger first) as
+// soon as it is done with its last one, so systems with many GMRES
+// iterations do not hold up the others' SMs.  A system's team size is a
+// function of its order alone (batch_team: about BATCH_ROWS_PER_BLOCK rows
+// per block, at most 16 blocks), so its result is the same whatever batch it
+// is solved in; the systems of one team size form a class, and the classes'
+// teams share the launch (one team per class, then teams given one at a time
+// to the class with the most rows per team; a team whose class is done takes
+// systems of classes with smaller teams).  Systems of more than
+// BATCH_SOLO_N rows, which fill the GPU alone, run on a grid of their own
+// (the single-system path).  All systems of a launch are prepared before it
 // (their buffers coexist).
 // ====================================================================
 
 namespace {
 
-constexpr int64_t BATCH_ROWS_PER_BLOCK = 2048;
+// Rows per block of a batched system.  A batch is bound by the bytes each
+// block streams per iteration, not by its grid-wide waits, so fewer and
+// fuller blocks per system solve more systems at once: the refinement of the
+// 512-system batch (n 2e3..5e4) took 0.41 s of kernel time at 8192 rows per
+// block against 0.69 s at 2048 and 1.39 s at 1024 (MGS: 0.34 s, 0.76 s, 1.39 s).
+constexpr int64_t BATCH_ROWS_PER_BLOCK = 8192;
+constexpr int64_t BATCH_SOLO_N = 65536;
+
+int batch_team(int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, (n + BATCH_ROWS_PER_BLOCK / 2) / BATCH_ROWS_PER_BLOCK));
+}
 
 struct BatchRun {
     int device, num_sms;
     cudaStream_t s;
     const ir_opts* o;
     std::vector<IrJob>* jobs;
-    std::vector<int>* order;   // systems by decreasing order n
+    // classes of one launch: (team size, systems by decreasing order), larger teams first
+    const std::vector<std::pair<int, std::vector<int>>>* classes;
     int* nl;
     float* ms_kernel;
-    int* team_size;
     IrKernels K;
     int sg;                    // sizeof(u_g)
 
@@ -696,13 +715,15 @@ struct BatchRun {
         size_t dyn_max = 0;
         SPAI_CUDA_TRY(allow_max_dynamic_smem_ptr(kern, &dyn_max));
         std::vector<IrJob>& J = *jobs;
-        const int count = (int)J.size();
-        // team size from the median order: about BATCH_ROWS_PER_BLOCK rows per block
-        std::vector<int64_t> ns(count);
-        for (int i = 0; i < count; i++) ns[i] = J[i].n;
-        std::nth_element(ns.begin(), ns.begin() + count / 2, ns.end());
-        const int64_t med = ns[count / 2];
-        const int T = (int)std::max<int64_t>(1, std::min<int64_t>(16, (med + BATCH_ROWS_PER_BLOCK / 2) / BATCH_ROWS_PER_BLOCK));
+        const int ncls = (int)classes->size();
+        std::vector<int> order;        // args order: class by class
+        std::vector<int> cs(ncls + 1, 0);
+        for (int c = 0; c < ncls; c++) {
+            const auto& v = (*classes)[c].second;
+            order.insert(order.end(), v.begin(), v.end());
+            cs[c + 1] = (int)order.size();
+        }
+        const int count = (int)order.size();
         int rc = 0;
         // preparation without a wait per system: buffers, SELL offsets, norms and x0
         // for all systems, then one copy of every SELL size and norm to the host,
@@ -712,8 +733,8 @@ struct BatchRun {
         unsigned long long* d_slots = nullptr;
         rc = dev_alloc((void**)&d_slots, sizeof(unsigned long long) * 5 * count, s);
         if (rc) return rc;
-        for (int i : *order) {
-            IrJob& jb = J[i];
+        for (int i = 0; i < count; i++) {
+            IrJob& jb = J[order[i]];
             if (!rc) rc = ir_job_alloc(jb, s, o);
             if (!rc) rc = sell_begin(jb.n, jb.A->rowptr, num_sms, s, &jb.As, nl);
             const int64_t nsl = (jb.n + 31) >> 5;
@@ -746,8 +767,8 @@ struct BatchRun {
         if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
         dev_free(d_slots, s);
         if (rc) { drop_started(); return rc; }
-        for (int i : *order) {
-            IrJob& jb = J[i];
+        for (int i = 0; i < count; i++) {
+            IrJob& jb = J[order[i]];
             const unsigned long long* h = hs.data() + 5 * (size_t)i;
             for (int k = 0; k < 3; k++) jb.h_norms[k] = h[k];
             rc = sell_finish(jb.n, jb.A->rowptr, jb.A->col, jb.A->val, o->up, num_sms, s, &jb.As, (int64_t)h[3], nl);
@@ -756,53 +777,90 @@ struct BatchRun {
                                  o->up == SPAI_SINGLE ? &jb.P->sell_f32 : &jb.P->sell_f64, (int64_t)h[4], nl);
             if (rc) { drop_started(); return rc; }
         }
-        // arguments in claim order (larger systems first), every system on T blocks
+        // arguments in claim order, every system prepared for its class's team size
         std::vector<IrArgs> h(count);
         size_t smem = 0;
-        for (int q = 0; q < count; q++) {
-            IrJob& jb = J[(*order)[q]];
-            ir_job_args(jb, device, o);
-            IrArgs& a = jb.a;
-            a.G = T;
-            a.rb = std::max<int64_t>(32, ((jb.n + T - 1) / T + 31) & ~int64_t(31));
-            a.g2 = 0;
-            a.block0 = 0;
-            a.jl = a.orth == 2 ? ir_pick_jl(a.rb, a.kmax, dyn_max, sg) : 0;
-            smem = std::max(smem, smem_for(a));
-            h[q] = a;
+        std::vector<double> work(ncls, 0.0);
+        for (int c = 0; c < ncls; c++) {
+            const int T = (*classes)[c].first;
+            for (int q = cs[c]; q < cs[c + 1]; q++) {
+                IrJob& jb = J[order[q]];
+                ir_job_args(jb, device, o);
+                IrArgs& a = jb.a;
+                a.G = T;
+                a.rb = std::max<int64_t>(32, ((jb.n + T - 1) / T + 31) & ~int64_t(31));
+                a.g2 = 0;
+                a.block0 = 0;
+                a.jl = a.orth == 2 ? ir_pick_jl(a.rb, a.kmax, dyn_max, sg) : 0;
+                smem = std::max(smem, smem_for(a));
+                h[q] = a;
+                work[c] += (double)jb.n;
+            }
         }
         if (smem > dyn_max) return SPAI_ERR_UNSUPPORTED;
         int occ = 0;
         SPAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
-        const int teams = (occ * num_sms) / T;
-        if (teams < 1) return SPAI_ERR_UNSUPPORTED;
-        *team_size = T;
+        // teams: one per class, then one more at a time to the class with the most
+        // work per team (rows as the measure), while blocks are left
+        const int gmax = occ * num_sms;
+        std::vector<int> teams(ncls, 1);
+        int used = 0;
+        for (int c = 0; c < ncls; c++) used += (*classes)[c].first;
+        if (used > gmax) return SPAI_ERR_UNSUPPORTED;
+        for (;;) {
+            int best = -1;
+            double bw = 0.0;
+            for (int c = 0; c < ncls; c++) {
+                const int T = (*classes)[c].first;
+                if (teams[c] >= cs[c + 1] - cs[c] || used + T > gmax) continue;
+                const double w = work[c] / teams[c];
+                if (best < 0 || w > bw) { best = c; bw = w; }
+            }
+            if (best < 0) break;
+            teams[best]++;
+            used += (*classes)[best].first;
+        }
+        std::vector<int> tb(1, 0), tc;
+        for (int c = 0; c < ncls; c++)
+            for (int t = 0; t < teams[c]; t++) {
+                tb.push_back(tb.back() + (*classes)[c].first);
+                tc.push_back(c);
+            }
+        const int nteams = (int)tc.size();
         IrArgs* d_args = nullptr;
         unsigned* d_next = nullptr;
         unsigned long long* d_claim = nullptr;
+        int* d_plan = nullptr;
+        const int plan_ints = (nteams + 1) + nteams + (ncls + 1);
+        std::vector<int> hp;
+        hp.insert(hp.end(), tb.begin(), tb.end());
+        hp.insert(hp.end(), tc.begin(), tc.end());
+        hp.insert(hp.end(), cs.begin(), cs.end());
         rc = dev_alloc((void**)&d_args, sizeof(IrArgs) * count, s);
-        if (!rc) rc = dev_alloc((void**)&d_next, sizeof(unsigned), s);
-        if (!rc) rc = dev_alloc((void**)&d_claim, sizeof(unsigned long long) * teams, s);
+        if (!rc) rc = dev_alloc((void**)&d_next, sizeof(unsigned) * ncls, s);
+        if (!rc) rc = dev_alloc((void**)&d_claim, sizeof(unsigned long long) * nteams, s);
+        if (!rc) rc = dev_alloc((void**)&d_plan, sizeof(int) * plan_ints, s);
         if (!rc && cudaMemcpyAsync(d_args, h.data(), sizeof(IrArgs) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
             rc = SPAI_ERR_CUDA;
-        if (!rc && cudaMemsetAsync(d_next, 0, sizeof(unsigned), s) != cudaSuccess) rc = SPAI_ERR_CUDA;
-        if (!rc && cudaMemsetAsync(d_claim, 0, sizeof(unsigned long long) * teams, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        if (!rc && cudaMemcpyAsync(d_plan, hp.data(), sizeof(int) * plan_ints, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            rc = SPAI_ERR_CUDA;
+        if (!rc && cudaMemsetAsync(d_next, 0, sizeof(unsigned) * ncls, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+        if (!rc && cudaMemsetAsync(d_claim, 0, sizeof(unsigned long long) * nteams, s) != cudaSuccess) rc = SPAI_ERR_CUDA;
         cudaEvent_t k0 = nullptr, k1 = nullptr;
         if (!rc && (cudaEventCreate(&k0) != cudaSuccess || cudaEventCreate(&k1) != cudaSuccess)) rc = SPAI_ERR_CUDA;
         if (!rc) {
             const IrArgs* pa = d_args;
-            int cnt = count, tt = T;
+            BatchPlan plan{d_plan, d_plan + nteams + 1, d_plan + 2 * nteams + 1, nteams, ncls};
             long long limit = h[0].limit;
-            void* args[] = {(void*)&pa, (void*)&cnt, (void*)&tt, (void*)&d_next, (void*)&d_claim, (void*)&limit};
+            void* args[] = {(void*)&pa, (void*)&plan, (void*)&d_next, (void*)&d_claim, (void*)&limit};
             cudaEventRecord(k0, s);
-            if (cudaLaunchCooperativeKernel(kern, dim3((unsigned)(teams * T)), dim3(threads), args, smem, s) !=
-                cudaSuccess)
+            if (cudaLaunchCooperativeKernel(kern, dim3((unsigned)tb.back()), dim3(threads), args, smem, s) != cudaSuccess)
                 rc = SPAI_ERR_CUDA;
             cudaEventRecord(k1, s);
             (*nl)++;
         }
         for (int i = 0; i < count; i++)
-            if (!rc) rc = ir_job_collect(J[i], num_sms, s, o, nl);
+            if (!rc) rc = ir_job_collect(J[order[i]], num_sms, s, o, nl);
         if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = SPAI_ERR_CUDA;
         if (!rc) {
             float ms = 0.f;
@@ -814,6 +872,7 @@ struct BatchRun {
         dev_free(d_args, s);
         dev_free(d_next, s);
         dev_free(d_claim, s);
+        dev_free(d_plan, s);
         return rc;
     }
 };
@@ -838,16 +897,55 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
     std::vector<int> order(count);
     for (int i = 0; i < count; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jobs[x].n > jobs[y].n; });
+    // one launch per team size (larger teams first), then the systems that run alone
+    std::map<int, std::vector<int>> byteam;
+    std::vector<int> solo;
+    std::vector<int> grid_of(count, 0);
+    for (int i : order) {
+        if (jobs[i].n > BATCH_SOLO_N) solo.push_back(i);
+        else byteam[batch_team(jobs[i].n)].push_back(i);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SPAI_CUDA_TRY(cudaEventCreate(&e0));
     SPAI_CUDA_TRY(cudaEventCreate(&e1));
     int nl = 0;
     float ms_kernel = 0.f;
     cudaEventRecord(e0, s);
-    int team = 0;
-    BatchRun B{device, num_sms, s, o, &jobs, &order, &nl, &ms_kernel, &team, IrKernels(), prec_bytes(o->ug)};
-    rc = ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &B.K);
-    if (!rc) rc = B.run();
+    IrKernels K;
+    rc = ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &K);
+    if (!rc && !byteam.empty()) {
+        // all team sizes in one launch, larger teams first
+        std::vector<std::pair<int, std::vector<int>>> classes(byteam.rbegin(), byteam.rend());
+        BatchRun B{device, num_sms, s, o, &jobs, &classes, &nl, &ms_kernel, K, prec_bytes(o->ug)};
+        rc = B.run();
+        for (const auto& c : classes)
+            for (int i : c.second) grid_of[i] = c.first;
+    }
+    for (int i : solo) {
+        if (rc) break;
+        IrJob& J = jobs[i];
+        rc = ir_job_prepare(J, num_sms, s, o, &nl);
+        if (!rc) {
+            ir_job_args(J, device, o);
+            cudaEvent_t k0 = nullptr, k1 = nullptr;
+            if (cudaEventCreate(&k0) != cudaSuccess || cudaEventCreate(&k1) != cudaSuccess) rc = SPAI_ERR_CUDA;
+            if (!rc) cudaEventRecord(k0, s);
+            if (!rc) rc = launch_ir(J.a, K, prec_bytes(o->ug), num_sms, s, &grid_of[i]);
+            if (!rc) {
+                cudaEventRecord(k1, s);
+                nl++;
+                rc = ir_job_collect(J, num_sms, s, o, &nl);
+            }
+            if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = SPAI_ERR_CUDA;
+            if (!rc) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, k0, k1);
+                ms_kernel += ms;
+            }
+            if (k0) cudaEventDestroy(k0);
+            if (k1) cudaEventDestroy(k1);
+        }
+    }
     cudaEventRecord(e1, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc >= 0) rc = SPAI_ERR_CUDA;
     float ms_all = 0.f;
@@ -862,7 +960,7 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
             st[i].ms_ir = ms_all;
             st[i].ms_kernel = ms_kernel;
             st[i].launches = nl;
-            st[i].grid = team;
+            st[i].grid = grid_of[i];
         }
         ir_job_free(jobs[i], s);
     }

@@ -56,14 +56,19 @@ struct spai_ctx_s {
     size_t budget = 0;
     int num_sms = 0;
     std::mutex mu;  // serialises the synchronous entry points
-    // serving queue
+    // serving engine (capi.cu): an admission thread that uploads and builds
+    // the preconditioners of every admitted group, a refinement thread that
+    // solves prepared groups in batched launches; each on a stream of its own
     std::mutex qmu;
-    std::condition_variable qcv;
-    std::deque<ServeRequest*> pending;
+    std::condition_variable qcv;               // admission: new requests, freed budget, stop
+    std::condition_variable rcv;               // refinement: prepared groups, stop
+    std::deque<ServeRequest*> pending;         // submitted, not admitted
+    std::deque<std::vector<ServeRequest*>> ready;  // admitted and prepared, not solved
     std::map<uint64_t, ServeRequest*> tickets;
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> worker_streams;
-    size_t in_use = 0;
+    size_t in_use = 0;                         // estimated bytes of the admitted requests
+    uint64_t qgen = 0;                         // bumped at every submission and release
     uint64_t next_ticket = 1;
     bool stopping = false;
     std::set<spai_precond_s*> live;  // preconditioners built by spai_build and not yet freed

@@ -1127,26 +1127,51 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir(IrArgs a)
     ir_body<TU, TG, TP, RM, LS>(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
-// Many systems in one cooperative launch, scheduled dynamically: the grid is
-// split into teams of T blocks; the first block of a team claims the next
-// system from *next (an atomic counter) and hands its index to the team
-// through the team's word in `claim`, tagged with the team's claim count, and
-// the team runs that system (with its own arguments, exchange slots and error
-// word) as a grid of T blocks.  Teams never wait on one another, so a system
-// with many iterations holds only its own team's SMs.  Waits are bounded like
-// every other wait of the refinement: a team that gives up leaves.
+// Many systems in one cooperative launch (gmres_ir_solve_batch).  The grid
+// is cut into teams of contiguous blocks; teams of one class have the same
+// size and solve the systems of that class (args[cs[c] .. cs[c+1]), each
+// prepared for that team size), one after another, taking the next from the
+// class's counter as soon as they are done, so a system with many iterations
+// holds only its own team's SMs.  Classes are in decreasing team size; a
+// team whose class has no system left takes one of a later class (smaller
+// teams), which its first a.G blocks solve exactly as a team of that size
+// would.  Team j: blocks tb[j] .. tb[j+1]-1, class tc[j].  Waits are bounded
+// like every other wait of the refinement: a team that gives up leaves.
+struct BatchPlan {
+    const int* tb;   // nteams + 1 first blocks
+    const int* tc;   // nteams classes
+    const int* cs;   // nclasses + 1 offsets into args
+    int nteams, ncls;
+};
+
 template <class TU, class TG, class TP, int RM, bool LS>
-__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrArgs* __restrict__ args, int count,
-                                                                     int T, unsigned* next,
-                                                                     unsigned long long* claim, long long limit)
+__global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrArgs* __restrict__ args, BatchPlan plan,
+                                                                     unsigned* next, unsigned long long* claim,
+                                                                     long long limit)
 {
-    __shared__ int s_sys;
-    const int team = (int)blockIdx.x / T, rank = (int)blockIdx.x % T;
+    __shared__ int s_sys, s_team;
+    if (threadIdx.x == 0) {
+        // this block's team: the last j with tb[j] <= blockIdx.x
+        int lo = 0, hi = plan.nteams - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (plan.tb[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_team = lo;
+    }
+    __syncthreads();
+    const int team = s_team;
+    const int rank = (int)blockIdx.x - plan.tb[team];
+    const int c = plan.tc[team];
     for (unsigned round = 1;; round++) {
         if (threadIdx.x == 0) {
             int sys = -1;
             if (rank == 0) {
-                sys = (int)atomicAdd(next, 1u);
+                for (int cc = c; cc < plan.ncls && sys < 0; cc++) {
+                    const int q = (int)atomicAdd(&next[cc], 1u);
+                    if (q < plan.cs[cc + 1] - plan.cs[cc]) sys = plan.cs[cc] + q;
+                }
                 st_relaxed_u64(&claim[team], ((unsigned long long)round << 32) | (unsigned)sys);
             } else {
                 const long long t0 = clock64();
@@ -1161,8 +1186,9 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrAr
         __syncthreads();
         const int sys = s_sys;
         __syncthreads();
-        if (sys < 0 || sys >= count) return;
-        ir_body<TU, TG, TP, RM, LS>(args[sys], rank, T);
+        if (sys < 0) return;
+        const int G = args[sys].G;  // T, or a smaller class's team size
+        if (rank < G) ir_body<TU, TG, TP, RM, LS>(args[sys], rank, G);
         __syncthreads();
     }
 }

@@ -254,8 +254,6 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
     int32_t* buf = pbuf + (size_t)wib * (cap + 32 * stride + tsz);
     int32_t* lst = buf + cap;
     int32_t* tab = lst + 32 * stride;
-    const unsigned tmask = (unsigned)tsz - 1u;
-    const int tshift = __clz(tsz) + 1;  // tsz = 2^(31 - clz)
     for (int t = lane; t < tsz; t += 32) tab[t] = -1;
     __syncwarp();
     for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < n; k += (int64_t)gridDim.x * wpb) {
@@ -308,16 +306,35 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         for (int t = lane; t < F; t += 32) Jidx[k * F + t] = t < nj ? buf[lo + t] : -1;
         if (lane == 0) Jcnt[k] = nj;
         __syncwarp();
-        // shadow size of the (initial) pattern: |{k} and the nonzero columns of rows J_k|
-        int mine = lane == 0 ? hset_insert(tab, tmask, tshift, (int)k) : 0;
+        // shadow size of the (initial) pattern: |{k} and the nonzero columns of rows J_k|,
+        // counted in the first ts slots of the table, ts at least twice the entries
+        // (a power of two, at most tsz): only those are cleared afterwards
+        int64_t b = 0, e = 0;
         if (lane < nj) {
-            const int64_t b = rp[jl], e = rp[jl + 1];
-            if (zv) {
-                for (int64_t q = b; q < e; q++)
-                    if (nonzero_bits(val[q])) mine += hset_insert(tab, tmask, tshift, col[q]);
-            } else {
-                for (int64_t q = b; q < e; q++) mine += hset_insert(tab, tmask, tshift, col[q]);
+            b = rp[jl];
+            e = rp[jl + 1];
+        }
+        int ts = 64;
+        {
+            int tot = (int)(e - b);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            while (ts < 2 * (tot + 1) && ts < tsz) ts <<= 1;
+        }
+        const unsigned tmask = (unsigned)ts - 1u;
+        const int tshift = __clz(ts) + 1;  // ts = 2^(31 - clz)
+        int mine = lane == 0 ? hset_insert(tab, tmask, tshift, (int)k) : 0;
+        // (four loads in flight per lane before the inserts)
+        for (int64_t q = b; q < e; q += 4) {
+            int c4[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                c4[u] = -1;
+                if (q + u < e && (!zv || nonzero_bits(val[q + u]))) c4[u] = col[q + u];
             }
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (c4[u] >= 0) mine += hset_insert(tab, tmask, tshift, c4[u]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
@@ -328,7 +345,7 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
             if (mI > big_thr) big[atomicAdd(nbig, 1)] = (int32_t)k;  // for the large-shadow kernel
         }
         __syncwarp();
-        for (int t = lane; t < tsz; t += 32) tab[t] = -1;
+        for (int t = lane; t < ts; t += 32) tab[t] = -1;
         __syncwarp();
     }
 }

@@ -368,8 +368,9 @@ __device__ __forceinline__ int gather_hash(const SpaiArgs& a, const Tile<C, WT>&
     const C* lv = T.lval + lane * a.rl;
     // lane nj carries the list {k} (the e_k column)
     const int mylen = lane < nj ? len : (lane == nj ? 1 : 0);
+    const int maxlen = (int)__reduce_max_sync(FULL, (unsigned)mylen);
     int m = 0;
-    for (int t = 0; t < a.rl; t++) {
+    for (int t = 0; t < maxlen; t++) {
         int key = -1;
         if (t < mylen) key = lane < nj ? lc[t] : (int)k;
         const bool isnew = key >= 0 && hset_insert(hk, mask, shift, key);

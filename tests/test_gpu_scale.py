@@ -261,17 +261,14 @@ def _requests():
     return reqs
 
 
-def test_serving_mix_matches_standalone():
-    reqs = _requests()
-    alone = []
-    c1 = S.Context(0)
-    for A, b, so, io in reqs:
-        x = np.zeros_like(b)
-        st = S.gmres_ir_solve(c1, A, b, x, sopts=so, opts=io)
-        alone.append((x, st))
-    c1.close()
-    c2 = S.Context(0, hbm_budget=8 << 30)
-    tickets = [S.solver_submit(c2, A, b, so, io) for (A, b, so, io) in reqs]
+def _serve(ctx, reqs, stagger=0.0):
+    """Submit reqs (the second half `stagger` seconds after the first) and poll
+    until every request is done; returns [(x, stats)] in submission order."""
+    half = (len(reqs) + 1) // 2 if stagger > 0 else len(reqs)
+    tickets = [S.solver_submit(ctx, A, b, so, io) for (A, b, so, io) in reqs[:half]]
+    if stagger > 0:
+        time.sleep(stagger)
+        tickets += [S.solver_submit(ctx, A, b, so, io) for (A, b, so, io) in reqs[half:]]
     results = {}
     t0 = time.time()
     while len(results) < len(tickets):
@@ -280,16 +277,45 @@ def test_serving_mix_matches_standalone():
             if i in results:
                 continue
             x = np.zeros_like(reqs[i][1])
-            st = S.solver_poll(c2, t, x)
+            st = S.solver_poll(ctx, t, x)
             if st is not None:
                 results[i] = (x, st)
-        time.sleep(0.01)
-    for i in range(len(reqs)):
+        time.sleep(0.002)
+    return [results[i] for i in range(len(reqs))]
+
+
+def test_serving_mix_matches_standalone():
+    # continuous batching: each request gives the same bits alone in the queue, all at once,
+    # and when half of them arrive while the first half is on the GPU
+    reqs = _requests()
+    alone = []
+    for req in reqs:
+        c1 = S.Context(0, hbm_budget=8 << 30)
+        alone.append(_serve(c1, [req])[0])
+        c1.close()
+    for stagger in (0.0, 0.005):
+        c2 = S.Context(0, hbm_budget=8 << 30)
+        mix = _serve(c2, reqs, stagger)
+        c2.close()
+        for i in range(len(reqs)):
+            xa, sa = alone[i]
+            xm, sm = mix[i]
+            assert sm["steps"] == sa["steps"] and sm["its"] == sa["its"], (stagger, i)
+            assert np.array_equal(xm, xa), (stagger, i)  # deterministic kernels: the same bits alone and in the mix
+            if len(reqs[i][1]) <= 65536:
+                assert sm["grid"] <= 16, sm["grid"]  # solved by a team of the batched launch
+    # and within the refinement tolerance of the single-system entry point
+    c3 = S.Context(0)
+    for i, (A, b, so, io) in enumerate(reqs):
+        x = np.zeros_like(b)
+        st = S.gmres_ir_solve(c3, A, b, x, sopts=so, opts=io)
         xa, sa = alone[i]
-        xm, sm = results[i]
-        assert sm["steps"] == sa["steps"] and sm["its"] == sa["its"], i
-        assert np.array_equal(xm, xa), i  # deterministic kernels: the same bits alone and in the mix
-    c2.close()
+        assert sa["steps"] == st["steps"], (i, sa["its"], st["its"])
+        assert abs(sa["total_its"] - st["total_its"]) <= max(1, 0.1 * st["total_its"]), (i, sa["its"], st["its"])
+        Ms = synth.to_scipy(A)
+        nb = lambda y: np.max(np.abs(b - Ms @ y)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(y)) + np.max(np.abs(b)))
+        assert nb(xa) <= 10 * max(nb(x), 2.0 ** -53), (i, nb(xa), nb(x))
+    c3.close()
 
 
 def test_serving_admission_budget():
