@@ -233,8 +233,9 @@ int gmres_ir_solve(spai_ctx ctx, const spai_csr* A, spai_precond P, const spai_o
  * of the paper's solve; the batching is this library's).  The systems share
  * one persistent cooperative launch of the refinement kernel whose grid is
  * split into teams of blocks; each team solves one system after another,
- * larger systems first.  A system's team size depends on its order alone
- * (about 8192 rows per block, at most 16 blocks), so its result is the same
+ * larger systems first.  A system's team size depends on its order and the
+ * options alone (about 8192 rows per block, more blocks where a block's rows
+ * would not fit its shared memory, at most 16), so its result is the same
  * in any batch.  Systems of more than 65536 rows run afterwards, each on a
  * grid of its own as in gmres_ir_solve.  Every system's buffers are
  * allocated before the launch.  A[i] is a

@@ -668,9 +668,10 @@ extern "C" int spai_selftest_wait_timeout(int device, int mode, double limit_ms)
 // into teams; each team takes the next system of its class (larger first) as
 // soon as it is done with its last one, so systems with many GMRES
 // iterations do not hold up the others' SMs.  A system's team size is a
-// function of its order alone (batch_team: about BATCH_ROWS_PER_BLOCK rows
-// per block, at most 16 blocks), so its result is the same whatever batch it
-// is solved in; the systems of one team size form a class, and the classes'
+// function of its order and options alone (batch_team: about
+// BATCH_ROWS_PER_BLOCK rows per block, raised until a block's rows fit its
+// shared memory, at most 16 blocks), so its result is the same whatever
+// batch it is solved in; the systems of one team size form a class, and the classes'
 // teams share the launch (one team per class, then teams given one at a time
 // to the class with the most rows per team; a team whose class is done takes
 // systems of classes with smaller teams).  Systems of more than
@@ -897,13 +898,27 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
     std::vector<int> order(count);
     for (int i = 0; i < count; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return jobs[x].n > jobs[y].n; });
-    // one launch per team size (larger teams first), then the systems that run alone
+    IrKernels K;
+    rc = ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &K);
+    if (rc) return rc;
+    size_t dyn_max = 0;
+    SPAI_CUDA_TRY(allow_max_dynamic_smem_ptr(K.batch, &dyn_max));
+    // the team sizes (the batch_team of the order, raised until a block's rows fit its
+    // shared memory), then the systems that run alone
     std::map<int, std::vector<int>> byteam;
     std::vector<int> solo;
     std::vector<int> grid_of(count, 0);
+    const int sg = prec_bytes(o->ug);
     for (int i : order) {
-        if (jobs[i].n > BATCH_SOLO_N) solo.push_back(i);
-        else byteam[batch_team(jobs[i].n)].push_back(i);
+        const IrJob& jb = jobs[i];
+        int T = jb.n > BATCH_SOLO_N ? 17 : batch_team(jb.n);
+        for (; T <= 16; T++) {
+            const int64_t rb = std::max<int64_t>(32, ((jb.n + T - 1) / T + 31) & ~int64_t(31));
+            const int jl = o->orth == 2 ? ir_pick_jl(rb, jb.kmax, dyn_max, sg) : 0;
+            if (ir_smem_bytes(rb, jb.kmax, 0, o->orth, jl, sg) <= dyn_max) break;
+        }
+        if (T > 16) solo.push_back(i);
+        else byteam[T].push_back(i);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SPAI_CUDA_TRY(cudaEventCreate(&e0));
@@ -911,8 +926,6 @@ int gmres_ir_batch_dev(int device, int num_sms, cudaStream_t s, int count, const
     int nl = 0;
     float ms_kernel = 0.f;
     cudaEventRecord(e0, s);
-    IrKernels K;
-    rc = ir_kernels(o->u, o->ug, o->up, o->ur, o->orth, &K);
     if (!rc && !byteam.empty()) {
         // all team sizes in one launch, larger teams first
         std::vector<std::pair<int, std::vector<int>>> classes(byteam.rbegin(), byteam.rend());
