@@ -685,8 +685,9 @@ namespace {
 // Rows per block of a batched system.  A batch is bound by the bytes each
 // block streams per iteration, not by its grid-wide waits, so fewer and
 // fuller blocks per system solve more systems at once: the refinement of the
-// 512-system batch (n 2e3..5e4) took 0.41 s of kernel time at 8192 rows per
-// block against 0.69 s at 2048 and 1.39 s at 1024 (MGS: 0.34 s, 0.76 s, 1.39 s).
+// 512-system batch (n 2e3..5e4, one-reduction MGS) took 0.31 s of kernel
+// time at 8192 rows per block against 0.41 s at 2048 and 0.69 s at 1024
+// (the textbook MGS: 0.35 s, 0.76 s, 1.39 s).
 constexpr int64_t BATCH_ROWS_PER_BLOCK = 8192;
 constexpr int64_t BATCH_SOLO_N = 65536;
 
