@@ -59,7 +59,51 @@ def parse():
     p.add_argument("--sweep", action="store_true",
                    help="instead of the bench line: the eps trade-off of adaptive SPAI against fixed patterns "
                         "and no preconditioner (one JSON line)")
+    p.add_argument("--case", default=None, choices=["batched_spai"],
+                   help="instead of the bench line, one run of a single case for profiling: batched_spai = "
+                        "one spai_build_batch of the 512 systems of the batched line (one JSON line)")
     return p.parse_args()
+
+
+def batched_512_systems(synth):
+    """The 512 systems of the batched line: n log-uniform in [2e3, 5e4], even ones 2D
+    convection-diffusion (Peclet U(0, 50)), odd ones random sparse with 8-16 nonzeros per column
+    and row/column scaling 10^U(1,3); returns [(A, b)]."""
+    rng = np.random.default_rng(4)
+    R = 512
+    ns = np.exp(rng.uniform(np.log(2e3), np.log(5e4), size=R))
+    batch = []
+    for i in range(R):
+        if i % 2 == 0:
+            N = max(8, int(round(np.sqrt(ns[i]))))
+            A2 = synth.conv_diff_2d(N, float(rng.uniform(0.0, 50.0)), 1.0, 0.1, seed=1000 + i)
+        else:
+            A2 = synth.random_sparse(int(ns[i]), int(rng.integers(8, 17)), seed=2000 + i,
+                                     log10_scale=float(rng.uniform(1.0, 3.0)))
+        b2, _ = synth.rhs(A2, seed=3000 + i)
+        batch.append((A2, b2))
+    return batch
+
+
+def run_case(args):
+    """One run of a single case (for ncu), printing one JSON line."""
+    import paper_2202_10204_gb300 as S
+    from paper_2202_10204_gb300 import synth
+    if args.case == "batched_spai":
+        batch = batched_512_systems(synth)
+        ctx = S.Context(0)
+        so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+        Ps, sts = S.spai_build_batch(ctx, [A for A, _ in batch], so, per_column=True)
+        nI = np.concatenate([st["nI"] for st in sts])
+        out = dict(case=args.case, columns=int(len(nI)), ms=sts[0]["ms"], ms_kernel=sts[0]["ms_kernel"],
+                   launches=sts[0]["launches"],
+                   shadow_rows={"1-32": int(np.sum(nI <= 32)), "33-64": int(np.sum((nI > 32) & (nI <= 64))),
+                                "65-256": int(np.sum((nI > 64) & (nI <= 256))), "257-512": int(np.sum(nI > 256))})
+        for P in Ps:
+            P.free()
+        ctx.close()
+        print(json.dumps(out))
+    return 0
 
 
 def nproc():
@@ -405,19 +449,8 @@ def extra_workloads(S, synth, torch, dev):
                                            backward_error_max=w["fp64"]["backward_error_max"],
                                            mixed_over_fp64=w["mixed_over_fp64"]) for w in sweep])
     # ---- batched: 512 independent systems through the queue at once
-    rng = np.random.default_rng(4)
-    R = 512
-    ns = np.exp(rng.uniform(np.log(2e3), np.log(5e4), size=R))
-    batch = []
-    for i in range(R):
-        if i % 2 == 0:
-            N = max(8, int(round(np.sqrt(ns[i]))))
-            A2 = synth.conv_diff_2d(N, float(rng.uniform(0.0, 50.0)), 1.0, 0.1, seed=1000 + i)
-        else:
-            A2 = synth.random_sparse(int(ns[i]), int(rng.integers(8, 17)), seed=2000 + i,
-                                     log10_scale=float(rng.uniform(1.0, 3.0)))
-        b2, _ = synth.rhs(A2, seed=3000 + i)
-        batch.append((A2, b2))
+    batch = batched_512_systems(synth)
+    R = len(batch)
     so = S.make_spai_opts(init=1, max_fill=30, uf="single")
     io = S.make_ir_opts(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4, orth=ORTH)
     bctx = S.Context(dev.index or 0, hbm_budget=120 << 30)
@@ -559,6 +592,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     if args.sweep:
         return run_sweep(args)
     import torch

@@ -2,9 +2,11 @@
 //
 // The same steps as the warp kernel (spai_column.cuh) for tiles of up to
 // 32*NW rows:
-//   - gather: warp 0 loads the rows j in J_k of A into shared-memory lists
-//     and merges them (sorted union, plus {k}) into I_k and the tile
-//     [B(I_k,J_k) | e_k(I_k)] (row-major, shared memory, kept unmodified);
+//   - gather: the warps take the rows j in J_k of A, collect their row
+//     indices (plus k) in a shared-memory hash set, sort them into I_k and
+//     write the tile [B(I_k,J_k) | e_k(I_k)] (row-major, shared memory, kept
+//     unmodified); the hash set then gives the position of a row in I_k for
+//     rho's inner products;
 //   - Householder QR with the tile in registers: warp w holds rows
 //     [32w, 32w+32), lane t holds column t.  Each step the lanes holding the
 //     pivot column publish it to shared memory together with the pivot row;
@@ -76,6 +78,8 @@ __device__ inline void block_bitonic_sort(int32_t* a, int len2)
 
 template <class C>
 struct CtaTile {
+    int32_t* hk;     // 2 mm: hash set of the shadow's row indices
+    uint16_t* hr;    // 2 mm: each key's position in the sorted I_k
     int32_t* I;      // mm
     C* W;            // mm * LD (original tile)
     C* v;            // mm: pivot column, then the residual
@@ -96,7 +100,8 @@ struct CtaTile {
 template <class C>
 __host__ __device__ inline size_t cta_tile_bytes(int mm, int nw, int rl, int cmax)
 {
-    size_t b = align16((size_t)mm * 4);
+    size_t b = align16((size_t)2 * mm * 4) + align16((size_t)2 * mm * 2);
+    b += align16((size_t)mm * 4);
     b += align16((size_t)mm * SPAI_LD * sizeof(C));
     b += align16((size_t)mm * sizeof(C));
     b += align16((size_t)nw * 33 * sizeof(C));
@@ -113,6 +118,8 @@ __device__ inline CtaTile<C> cta_carve(unsigned char* base, int mm, int nw, int 
 {
     CtaTile<C> t;
     size_t off = 0;
+    t.hk = (int32_t*)(base + off); off += align16((size_t)2 * mm * 4);
+    t.hr = (uint16_t*)(base + off); off += align16((size_t)2 * mm * 2);
     t.I = (int32_t*)(base + off); off += align16((size_t)mm * 4);
     t.W = (C*)(base + off); off += align16((size_t)mm * SPAI_LD * sizeof(C));
     t.v = (C*)(base + off); off += align16((size_t)mm * sizeof(C));
@@ -150,6 +157,78 @@ __device__ __forceinline__ C block_sum_det(C v, C* red)
     return r;
 }
 
+// position of key in the sorted shadow through the hash set (-1: not in I_k)
+__device__ __forceinline__ int cta_find(const int32_t* hk, const uint16_t* hr, unsigned mask, int shift, int key)
+{
+    unsigned h = hset_slot(key, shift);
+    for (unsigned probe = 0; probe <= mask; probe++) {
+        const int v = hk[h];
+        if (v == key) return hr[h];
+        if (v == -1) return -1;
+        h = (h + 1u) & mask;
+    }
+    return -1;
+}
+
+// Steps 1-2 block-parallel: every warp takes rows J[t] of A (t = warp, warp + NW, ...), its
+// lanes the entries, and inserts the row indices into a hash set of 2 MM slots (new keys
+// appended to I in arrival order, plus k); I is then sorted (block bitonic sort), each slot
+// records its key's position, and the entries are written to their rows of the zeroed tile
+// [B(I,J) | e_k].  The same sorted I_k and tile as the sorted merge.  Returns |I_k| (beyond
+// MM: nothing written past the tile).
+template <class S, class C, int NW>
+__device__ int cta_gather_hash(const SpaiArgs& a, const CtaTile<C>& T, int64_t k, int nj, int* cnt)
+{
+    constexpr int MM = 32 * NW, HS = 2 * MM;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, BT = blockDim.x;
+    const unsigned mask = HS - 1;
+    const int shift = 32 - (31 - __clz(HS));
+    const S* bv = (const S*)a.bval;
+    for (int t = tid; t < HS; t += BT) T.hk[t] = -1;
+    if (tid == 0) *cnt = 0;
+    __syncthreads();
+    auto add = [&](int key) {
+        if (hset_insert(T.hk, mask, shift, key)) {
+            const int pos = atomicAdd(cnt, 1);
+            if (pos < MM) T.I[pos] = key;
+        }
+    };
+    if (tid == 0) add((int)k);
+    for (int t = wid; t < nj; t += NW) {
+        const int j = T.J[t];
+        const int64_t b = a.rp[j], e = a.rp[j + 1];
+        for (int64_t q = b + lane; q < e; q += 32)
+            if (!bmarked<S>(bv[q])) add(a.col[q]);
+    }
+    __syncthreads();
+    const int m = *cnt;
+    if (m > MM) return m;
+    int len2 = 1;
+    while (len2 < m) len2 <<= 1;
+    for (int t = m + tid; t < len2; t += BT) T.I[t] = INT_MAX;
+    __syncthreads();
+    block_bitonic_sort(T.I, len2);
+    for (int p = tid; p < m; p += BT) {
+        const int key = T.I[p];
+        unsigned h = hset_slot(key, shift);
+        for (unsigned probe = 0; probe <= mask && T.hk[h] != key; probe++) h = (h + 1u) & mask;
+        T.hr[h] = (uint16_t)p;
+    }
+    for (int t = tid; t < m * SPAI_LD; t += BT) T.W[t] = C(0);
+    __syncthreads();
+    for (int t = wid; t < nj; t += NW) {
+        const int j = T.J[t];
+        const int64_t b = a.rp[j], e = a.rp[j + 1];
+        for (int64_t q = b + lane; q < e; q += 32) {
+            const S v = bv[q];
+            if (!bmarked<S>(v)) T.W[cta_find(T.hk, T.hr, mask, shift, a.col[q]) * SPAI_LD + t] = to_c(v);
+        }
+    }
+    if (tid == 0) T.W[cta_find(T.hk, T.hr, mask, shift, (int)k) * SPAI_LD + nj] = C(1);
+    __syncthreads();
+    return m;
+}
+
 template <class S, bool ADAPTIVE, int NW>
 __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs a)
 {
@@ -160,7 +239,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, BT = blockDim.x;
     const unsigned FULL = 0xffffffffu;
     const int F = a.F;
-    int* sc = T.sc;  // [0] nj, [1] m, [2] flags from warp 0, [3] nadd
+    int* sc = T.sc;  // [0] nj, [1] m, [2] flags from warp 0, [3] nadd, [4] the gather's count
 
     const int64_t ncols = a.list ? a.nlist : a.n;
     for (int64_t idx = blockIdx.x; idx < ncols; idx += gridDim.x) {
@@ -188,13 +267,8 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
             __syncthreads();
         };
         for (int step = 0;; step++) {
-            // ---- gather (warp 0)
-            if (wid == 0) {
-                const int mg = gather_ptrs<S, C>(a, T.I, T.W, T.J, T.lcol, T.lval, T.lcnt, k, nj, MM);
-                if (lane == 0) sc[1] = mg;
-            }
-            __syncthreads();
-            m = sc[1];
+            // ---- gather (every warp)
+            m = cta_gather_hash<S, C, NW>(a, T, k, nj, &sc[4]);
             if (m > MM) { defer(step); break; }
             // ---- Householder QR, tile in registers: warp w rows [32w, 32w+32), lane t column t.
             // Warps whose rows all lie beyond |I_k| hold zeros: they skip the
@@ -340,7 +414,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
                 C num = 0, den = 0;
                 for (int64_t q = a.rp[j]; q < a.rp[j + 1]; q++) {
                     const C bij = bvalue<S>(((const S*)a.bval)[q]);
-                    const int p = bsearch_smem(T.I, m, a.col[q]);
+                    const int p = cta_find(T.hk, T.hr, 2 * MM - 1, 32 - (31 - __clz(2 * MM)), a.col[q]);
                     if (p >= 0) num = fma(T.v[p], bij, num);
                     if (!a.rho_restricted || p >= 0) den = fma(bij, bij, den);
                 }
