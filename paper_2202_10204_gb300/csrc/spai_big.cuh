@@ -301,16 +301,14 @@ __global__ void __launch_bounds__(32 * BIG_NW, 1)
             nj += nadd;
         }
         fl |= sc[1];
-        // ---- outputs: row k of P = mbar_k * d(J_k)
+        // ---- outputs: row k of P = mbar_k * d(J_k) (entries past |J_k| are never read)
         int nf = 0;
-        for (int t = tid; t < F; t += BT) {
-            const bool in = t < nj;
-            const int j = in ? J[t] : -1;
-            const C mv = in ? mb[t] : C(0);
+        for (int t = tid; t < nj; t += BT) {
+            const int j = J[t];
+            const C mv = mb[t];
             a.Jidx[k * F + t] = j;
-            ((S*)a.mval)[k * F + t] = from_d<S>((double)mv);
-            a.Praw[k * F + t] = in ? (double)mv * a.d[j] : 0.0;
-            if (in && !isfinite((double)mv)) nf = CF_NONFINITE;
+            a.Praw[k * F + t] = (double)mv * a.d[j];
+            if (!isfinite((double)mv)) nf = CF_NONFINITE;
         }
         if (nf) atomicOr(&sc[1], nf);
         __syncthreads();

@@ -256,6 +256,7 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
     int32_t* tab = lst + 32 * stride;
     for (int t = lane; t < tsz; t += 32) tab[t] = -1;
     __syncwarp();
+    int wmax = 0;  // the warp's largest shadow
     for (int64_t k = blockIdx.x * (int64_t)wpb + wib; k < n; k += (int64_t)gridDim.x * wpb) {
         int cnt = 0;
         if (init == SPAI_PAT_IDENTITY) {
@@ -303,7 +304,7 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
         }
         const int nj = hi - lo;
         const int jl = lane < nj ? buf[lo + lane] : -1;
-        for (int t = lane; t < F; t += 32) Jidx[k * F + t] = t < nj ? buf[lo + t] : -1;
+        if (lane < nj) Jidx[k * F + lane] = jl;  // entries past |J_k| are never read
         if (lane == 0) Jcnt[k] = nj;
         __syncwarp();
         // shadow size of the (initial) pattern: |{k} and the nonzero columns of rows J_k|,
@@ -339,15 +340,17 @@ __global__ void k_pattern(int64_t n, int init, int F, const int64_t* __restrict_
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
         const int mI = mine;
+        wmax = max(wmax, mI);
         if (lane == 0) {
             Icnt[k] = mI;
-            atomicMax(maxI, mI);
             if (mI > big_thr) big[atomicAdd(nbig, 1)] = (int32_t)k;  // for the large-shadow kernel
         }
         __syncwarp();
         for (int t = lane; t < ts; t += 32) tab[t] = -1;
         __syncwarp();
     }
+    // one atomic per warp (one per column on a single address serialised the kernel)
+    if (lane == 0 && wmax > 0) atomicMax(maxI, wmax);
 }
 
 // P in CSR from the padded per-column results: one thread per padded slot
@@ -668,7 +671,6 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     int32_t* ri = nullptr;
     int32_t *Jidx = nullptr, *Jcnt = nullptr, *Icnt = nullptr, *flags = nullptr, *nsolve = nullptr;
     double *Praw = nullptr, *colres = nullptr;
-    void* mval = nullptr;
     void* bval = nullptr;
     unsigned long long* fstat = nullptr;
     size_t ssz = o->uf == SPAI_HALF ? 2 : (o->uf == SPAI_SINGLE ? 4 : 8);
@@ -694,7 +696,6 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
     TRY(dev_alloc((void**)&nsolve, sizeof(int32_t) * n, s));
     TRY(dev_alloc((void**)&Praw, sizeof(double) * n * F, s));
     TRY(dev_alloc((void**)&colres, sizeof(double) * n, s));
-    TRY(dev_alloc(&mval, ssz * n * F, s));
     TRY(dev_alloc(&bval, ssz * (nnz > 0 ? nnz : 1), s));
     TRY(dev_alloc((void**)&fstat, sizeof(unsigned long long) * 3, s));
     if (cudaMemsetAsync(err, 0, sizeof(int) * 40, s) != cudaSuccess) { rc = SPAI_ERR_CUDA; goto done; }
@@ -768,7 +769,7 @@ int spai_build_left(int device, int num_sms, cudaStream_t s, const DevCsr& A, co
         SpaiArgs a;
         memset(&a, 0, sizeof(a));
         a.n = n; a.F = F; a.rp = A.rowptr; a.col = A.col; a.val = A.val; a.cp = cp; a.ri = ri; a.d = d; a.bval = bval;
-        a.Jidx = Jidx; a.Jcnt = Jcnt; a.Praw = Praw; a.mval = mval; a.colres = colres; a.flags = flags;
+        a.Jidx = Jidx; a.Jcnt = Jcnt; a.Praw = Praw; a.colres = colres; a.flags = flags;
         a.Icnt = Icnt; a.nsolve = nsolve; a.eps = o->eps;
         a.alpha = o->alpha < 0 ? (int)((n + o->beta - 1) / std::max(o->beta, 1)) : o->alpha;
         a.beta = o->beta; a.rho_restricted = o->rho_restricted; a.err = err;
@@ -897,7 +898,7 @@ done:
 #undef TRY
     dev_free(d, s); dev_free(err, s); dev_free(big, s); dev_free(blist, s); dev_free(boff, s); dev_free(slab, s); dev_free(ccount, s); dev_free(cp, s); dev_free(ri, s);
     dev_free(Jidx, s); dev_free(Jcnt, s); dev_free(Icnt, s); dev_free(flags, s); dev_free(nsolve, s);
-    dev_free(Praw, s); dev_free(colres, s); dev_free(mval, s); dev_free(bval, s); dev_free(fstat, s);
+    dev_free(Praw, s); dev_free(colres, s); dev_free(bval, s); dev_free(fstat, s);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(ek0);

@@ -64,8 +64,7 @@ struct SpaiArgs {
     const void* bval;    // nnz of A in u_f: b = fl(a_ij d_j), explicit zeros marked (bmark)
     int32_t* Jidx;       // n * F, in: initial pattern, out: final pattern
     int32_t* Jcnt;       // n
-    double* Praw;        // n * F: mbar * d(J)
-    void* mval;          // n * F in storage precision
+    double* Praw;        // n * F: mbar * d(J) (entries 0 .. |J_k|-1 of row k)
     double* colres;      // n
     int32_t* flags;      // n
     int32_t* Icnt;       // n
@@ -843,15 +842,13 @@ __global__ void __launch_bounds__(64, spai_min_blocks<S>()) k_spai(SpaiArgs a)
         }
         if (deferred) continue;
         fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
-        // ---- outputs: row k of P = mbar_k * d(J_k)
-        for (int t = lane; t < F; t += 32) {
-            const bool in = t < nj;
-            const int j = in ? T.J[t] : -1;
-            const C mv = in ? T.mb[t] : C(0);
+        // ---- outputs: row k of P = mbar_k * d(J_k) (entries past |J_k| are never read)
+        for (int t = lane; t < nj; t += 32) {
+            const int j = T.J[t];
+            const C mv = T.mb[t];
             a.Jidx[k * F + t] = j;
-            ((S*)a.mval)[k * F + t] = from_d<S>((double)mv);
-            a.Praw[k * F + t] = in ? (double)mv * a.d[j] : 0.0;
-            if (in && !isfinite((double)mv)) fl |= CF_NONFINITE;
+            a.Praw[k * F + t] = (double)mv * a.d[j];
+            if (!isfinite((double)mv)) fl |= CF_NONFINITE;
         }
         fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
         if (lane == 0) {

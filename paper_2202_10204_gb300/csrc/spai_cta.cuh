@@ -479,15 +479,13 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 ? 2 : 1) k_spai_cta(SpaiArgs 
         }
         if (deferred) continue;
         fl |= sc[2];
-        // ---- outputs: row k of P = mbar_k * d(J_k)
-        for (int t = tid; t < F; t += BT) {
-            const bool in = t < nj;
-            const int j = in ? T.J[t] : -1;
-            const C mv = in ? T.mb[t] : C(0);
+        // ---- outputs: row k of P = mbar_k * d(J_k) (entries past |J_k| are never read)
+        for (int t = tid; t < nj; t += BT) {
+            const int j = T.J[t];
+            const C mv = T.mb[t];
             a.Jidx[k * F + t] = j;
-            ((S*)a.mval)[k * F + t] = from_d<S>((double)mv);
-            a.Praw[k * F + t] = in ? (double)mv * a.d[j] : 0.0;
-            if (in && !isfinite((double)mv)) atomicOr(&sc[2], CF_NONFINITE);
+            a.Praw[k * F + t] = (double)mv * a.d[j];
+            if (!isfinite((double)mv)) atomicOr(&sc[2], CF_NONFINITE);
         }
         __syncthreads();
         if (tid == 0) {

@@ -270,13 +270,11 @@ __global__ void __launch_bounds__(32 * MidCfg<S, R, NC>::WPB) k_spai_mid(SpaiArg
         const C snorm = rnd<S>(sqrt(warp_sum(s2p)));
         if (!isfinite((double)snorm)) fl |= CF_NONFINITE;
         if (snorm <= (C)a.eps) fl |= CF_CONVERGED;
-        // ---- outputs: row k of P = mbar_k * d(J_k)
-        if (lane < F) {
-            const bool in = lane < nj;
-            a.Jidx[k * F + lane] = in ? jl : -1;
-            ((S*)a.mval)[k * F + lane] = from_d<S>(in ? (double)mv : 0.0);
-            a.Praw[k * F + lane] = in ? (double)mv * a.d[jl] : 0.0;
-            if (in && !isfinite((double)mv)) fl |= CF_NONFINITE;
+        // ---- outputs: row k of P = mbar_k * d(J_k) (entries past |J_k| are never read)
+        if (lane < nj) {
+            a.Jidx[k * F + lane] = jl;
+            a.Praw[k * F + lane] = (double)mv * a.d[jl];
+            if (!isfinite((double)mv)) fl |= CF_NONFINITE;
         }
         fl = (int)__reduce_or_sync(FULL, (unsigned)fl);
         if (lane == 0) {
