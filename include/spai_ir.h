@@ -212,6 +212,22 @@ int spai_build(spai_ctx ctx, const spai_csr* A, const spai_opts* opts, spai_prec
 int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts* opts,
                      spai_precond* P_out, spai_stats* st, int* status);
 
+/* The tile tuner of the SPAI build (fixed patterns).  Columns with shadows of
+ * 65..512 rows run in a warp kernel whose tile in shared memory has 32 R rows
+ * and 16 or 32 columns; any tile that holds a column gives the same result
+ * bit for bit (padding rows are zero and stay zero), so the shape is a cost
+ * choice.  The columns are binned by |I_k| and |J_k| (bins 2..13: up to 16
+ * columns and R = 3, 4, 5, 6, 7, 8, 10, 12, 16 for bins 2..10; 17..31 columns
+ * and R = 4, 8, 16 for bins 11..13).  The first build in which a bin has at
+ * least 8192 columns times the bin's candidate tiles (its own, the next two
+ * larger row counts, a 32-column tile) on 4096 of them and keeps the fastest
+ * for the device, u_f (SPAI_HALF / SPAI_SINGLE / SPAI_DOUBLE) and bin.
+ * spai_tune_get returns the bin's choice (a candidate index 0..3, -1 while
+ * untuned); spai_tune_set forces it (-1: tune again).  Both return
+ * SPAI_ERR_INVALID_ARG for a bad bin, u_f or index. */
+int spai_tune_get(int device, int uf, int bin);
+int spai_tune_set(int device, int uf, int bin, int variant);
+
 /* Size of P: *n and *nnz (either may be NULL). */
 int spai_precond_info(spai_precond P, int64_t* n, int64_t* nnz);
 

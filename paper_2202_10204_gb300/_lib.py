@@ -28,7 +28,8 @@ ERR_ADMISSION, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND, ERR_INTERN
 
 EXPORTED = ("spai_ctx_create", "spai_ctx_destroy", "spai_build", "spai_precond_info", "spai_precond_export",
             "spai_precond_free", "gmres_ir_solve", "solver_submit", "solver_poll", "spai_strerror",
-            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch", "spai_build_batch", "spai_selftest_wait_timeout")
+            "gmres_ir_solve_noalloc", "gmres_ir_solve_batch", "spai_build_batch", "spai_selftest_wait_timeout",
+            "spai_tune_get", "spai_tune_set")
 
 
 class spai_csr(C.Structure):
@@ -326,6 +327,19 @@ def solver_poll(ctx: Context, ticket: int, x=None):
         return None
     _check(rc, "solver_poll")
     return _ir_dict(st, rc)
+
+
+def tune_get(device: int, uf, bin_: int) -> int:
+    """The SPAI tile tuner's choice for a bin (-1 while untuned); see spai_tune_get."""
+    rc = lib().spai_tune_get(int(device), _prec(uf), int(bin_))
+    if rc < -1:
+        _check(rc, "spai_tune_get")
+    return rc
+
+
+def tune_set(device: int, uf, bin_: int, variant: int) -> None:
+    """Force the SPAI tile tuner's choice for a bin (-1: tune again)."""
+    _check(lib().spai_tune_set(int(device), _prec(uf), int(bin_), int(variant)), "spai_tune_set")
 
 
 def selftest_wait_timeout(device=0, mode=0, limit_ms=50.0) -> int:

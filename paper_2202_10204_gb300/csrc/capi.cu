@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -935,6 +936,44 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
         for (int i = 0; i < count && !rc; i++)
             if (rcs[i] > 0) rc = rcs[i];
     return rc;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ the tile tuner's choices
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tune;
+
+namespace spai {
+int mid_tune_get(int device, int uf, int bin)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(std::make_tuple(device, uf, bin));
+    return it == g_tune.end() ? -1 : it->second;
+}
+void mid_tune_put(int device, int uf, int bin, int variant)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (variant < 0) g_tune.erase(std::make_tuple(device, uf, bin));
+    else g_tune[std::make_tuple(device, uf, bin)] = variant;
+}
+}  // namespace spai
+
+extern "C" {
+
+int spai_tune_get(int device, int uf, int bin)
+{
+    if (bin < 2 || bin > 13 || (uf != SPAI_HALF && uf != SPAI_SINGLE && uf != SPAI_DOUBLE)) return SPAI_ERR_INVALID_ARG;
+    return spai::mid_tune_get(device, uf, bin);
+}
+
+int spai_tune_set(int device, int uf, int bin, int variant)
+{
+    if (bin < 2 || bin > 13 || (uf != SPAI_HALF && uf != SPAI_SINGLE && uf != SPAI_DOUBLE)) return SPAI_ERR_INVALID_ARG;
+    if (variant < -1 || variant >= 4) return SPAI_ERR_INVALID_ARG;
+    spai::mid_tune_put(device, uf, bin, variant);
+    return 0;
 }
 
 int spai_precond_info(spai_precond P, int64_t* n, int64_t* nnz)

@@ -869,6 +869,9 @@ template <class S>
 int launch_spai_cta_nw8(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
 template <class S>
 int launch_spai_cta_nw16(const SpaiArgs& a0, int num_sms, size_t smem_cap, cudaStream_t s);
+// the tile tuner's choices (capi.cu)
+int mid_tune_get(int device, int uf, int bin);
+void mid_tune_put(int device, int uf, int bin, int variant);
 // the shared-memory tile kernel (spai_mid.cuh), compiled in spai_mid_<u_f>.cu
 int launch_spai_mid_bin_half(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);
 int launch_spai_mid_bin_single(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s);

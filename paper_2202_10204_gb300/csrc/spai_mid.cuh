@@ -306,28 +306,113 @@ int launch_spai_mid(const SpaiArgs& a, int num_sms, size_t smem_cap, cudaStream_
     return 0;
 }
 
-// bins 2 .. SPAI_NBINS-1 of spai_bin (bin 13 at u_f = double: the 16-warp
-// CTA kernel, launched by launch_spai_t)
+// ---- bins 2 .. SPAI_NBINS-1 of spai_bin, and the tuner of their tile shapes.
+//
+// A column's result does not depend on the tile it runs in as long as the
+// tile holds it (R >= ceil(|I_k|/32), NC >= |J_k|): padding rows are zero and
+// stay zero, so every inner product, update and norm sees the same values in
+// the same order.  The tile shape is therefore only a cost choice.  For each
+// bin the tuner times the candidate shapes (the bin's own tile, the next
+// larger row counts, and a 32-column tile) on a sample of the bin's columns
+// the first time a build has enough of them, and keeps the fastest per device,
+// u_f and bin; later builds use it.  spai_tune_get / spai_tune_set read and
+// force the choice.
+
+constexpr int MID_TUNE_MIN = 8192;   // columns of a bin before it is tuned
+constexpr int MID_TUNE_SAMPLE = 4096;
+constexpr int MID_MAX_VARIANTS = 4;
+
+// the bin's candidate tiles as (R, NC); returns their count
+inline int mid_variants(int bin, int (*rv)[2])
+{
+    static const int R16[] = {3, 4, 5, 6, 7, 8, 10, 12, 16};
+    static const int R32[] = {4, 8, 16};
+    int Rb, nc;
+    if (bin >= 2 && bin <= 10) { Rb = R16[bin - 2]; nc = 16; }
+    else if (bin >= 11 && bin <= 13) { Rb = R32[bin - 11]; nc = 32; }
+    else return 0;
+    int cnt = 0;
+    if (nc == 16) {
+        for (int q = bin - 2; q < 9 && cnt < 3; q++) { rv[cnt][0] = R16[q]; rv[cnt][1] = 16; cnt++; }
+    }
+    for (int q = 0; q < 3 && cnt < MID_MAX_VARIANTS; q++)
+        if (R32[q] >= Rb) { rv[cnt][0] = R32[q]; rv[cnt][1] = 32; cnt++; if (nc == 16) break; }
+    return cnt;
+}
+
+template <class S>
+int launch_spai_mid_shape(const SpaiArgs& a, int R, int NC, int num_sms, size_t smem_cap, cudaStream_t s)
+{
+    if (NC == 16) {
+        switch (R) {
+        case 3: return launch_spai_mid<S, 3, 16>(a, num_sms, smem_cap, s);
+        case 4: return launch_spai_mid<S, 4, 16>(a, num_sms, smem_cap, s);
+        case 5: return launch_spai_mid<S, 5, 16>(a, num_sms, smem_cap, s);
+        case 6: return launch_spai_mid<S, 6, 16>(a, num_sms, smem_cap, s);
+        case 7: return launch_spai_mid<S, 7, 16>(a, num_sms, smem_cap, s);
+        case 8: return launch_spai_mid<S, 8, 16>(a, num_sms, smem_cap, s);
+        case 10: return launch_spai_mid<S, 10, 16>(a, num_sms, smem_cap, s);
+        case 12: return launch_spai_mid<S, 12, 16>(a, num_sms, smem_cap, s);
+        case 16: return launch_spai_mid<S, 16, 16>(a, num_sms, smem_cap, s);
+        }
+    } else {
+        switch (R) {
+        case 4: return launch_spai_mid<S, 4, 32>(a, num_sms, smem_cap, s);
+        case 8: return launch_spai_mid<S, 8, 32>(a, num_sms, smem_cap, s);
+        case 16:
+            if constexpr (!std::is_same<S, double>::value) return launch_spai_mid<S, 16, 32>(a, num_sms, smem_cap, s);
+            break;
+        }
+    }
+    return SPAI_ERR_INTERNAL;
+}
+
+// the tuner's choices: variant index per (device, u_f, bin), -1 until tuned
+int mid_tune_get(int device, int uf, int bin);
+void mid_tune_put(int device, int uf, int bin, int variant);
+
 template <class S>
 int launch_spai_mid_bin_t(const SpaiArgs& a, int bin, int num_sms, size_t smem_cap, cudaStream_t s)
 {
-    switch (bin) {
-    case 2: return launch_spai_mid<S, 3, 16>(a, num_sms, smem_cap, s);
-    case 3: return launch_spai_mid<S, 4, 16>(a, num_sms, smem_cap, s);
-    case 4: return launch_spai_mid<S, 5, 16>(a, num_sms, smem_cap, s);
-    case 5: return launch_spai_mid<S, 6, 16>(a, num_sms, smem_cap, s);
-    case 6: return launch_spai_mid<S, 7, 16>(a, num_sms, smem_cap, s);
-    case 7: return launch_spai_mid<S, 8, 16>(a, num_sms, smem_cap, s);
-    case 8: return launch_spai_mid<S, 10, 16>(a, num_sms, smem_cap, s);
-    case 9: return launch_spai_mid<S, 12, 16>(a, num_sms, smem_cap, s);
-    case 10: return launch_spai_mid<S, 16, 16>(a, num_sms, smem_cap, s);
-    case 11: return launch_spai_mid<S, 4, 32>(a, num_sms, smem_cap, s);
-    case 12: return launch_spai_mid<S, 8, 32>(a, num_sms, smem_cap, s);
-    case 13:
-        if constexpr (!std::is_same<S, double>::value) return launch_spai_mid<S, 16, 32>(a, num_sms, smem_cap, s);
-        else return SPAI_ERR_INTERNAL;
-    default: return SPAI_ERR_INTERNAL;
+    constexpr int uf = std::is_same<S, __half>::value ? SPAI_HALF : (std::is_same<S, float>::value ? SPAI_SINGLE : SPAI_DOUBLE);
+    int rv[MID_MAX_VARIANTS][2];
+    int nv = mid_variants(bin, rv);
+    if (std::is_same<S, double>::value && bin == 13) return SPAI_ERR_INTERNAL;  // the CTA kernel's bin
+    // shapes past what this type can hold (512 x 32 at double) are not candidates
+    if (std::is_same<S, double>::value)
+        while (nv > 1 && rv[nv - 1][0] == 16 && rv[nv - 1][1] == 32) nv--;
+    if (nv == 0) return SPAI_ERR_INTERNAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPAI_ERR_CUDA;
+    int v = mid_tune_get(dev, uf, bin);
+    if (v < 0 && nv > 1 && a.nlist >= MID_TUNE_MIN) {
+        // time every candidate on the bin's first columns (twice each, the second counts);
+        // every candidate writes the same results for them
+        SpaiArgs t = a;
+        t.nlist = std::min<int64_t>(a.nlist, MID_TUNE_SAMPLE);
+        cudaEvent_t e0, e1;
+        SPAI_CUDA_TRY(cudaEventCreate(&e0));
+        SPAI_CUDA_TRY(cudaEventCreate(&e1));
+        float best = 0.f;
+        int rc = 0;
+        for (int q = 0; q < nv && !rc; q++) {
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && !rc; rep++) {
+                cudaEventRecord(e0, s);
+                rc = launch_spai_mid_shape<S>(t, rv[q][0], rv[q][1], num_sms, smem_cap, s);
+                cudaEventRecord(e1, s);
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = SPAI_ERR_CUDA;
+                if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (!rc && (v < 0 || ms < best)) { best = ms; v = q; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        mid_tune_put(dev, uf, bin, v);
     }
+    if (v < 0 || v >= nv) v = 0;
+    return launch_spai_mid_shape<S>(a, rv[v][0], rv[v][1], num_sms, smem_cap, s);
 }
 
 }  // namespace spai

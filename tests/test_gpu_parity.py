@@ -190,6 +190,30 @@ def test_spai_fixed_pattern_parity(ctx, name, make, init, F, uf):
 
 
 @pytest.mark.parametrize("uf", ["half", "single", "double"])
+def test_spai_tile_shapes_give_the_same_result(ctx, uf):
+    """The tile tuner's candidates (shared-memory tiles of more rows or columns than a
+    column needs) give every column the same result bit for bit, so the tuner's choice
+    never changes a preconditioner."""
+    A = synth.random_sparse(20000, 12, seed=17)
+    so = S.make_spai_opts(init=1, max_fill=16, uf=uf)
+    cols = np.arange(0, 20000, 97, dtype=np.int32)
+    ref = O.spai(A, init=O.PAT_A, max_fill=16, uf="single", eps=0.0, cols=cols)
+    assert np.mean(column_bins(ref["Icnt"][cols], ref["Jcnt"][cols]) == 4) > 0.6  # the 160 x 16 bin holds most
+    S.tune_set(0, uf, 4, -1)
+    P0, _ = S.spai_build(ctx, A, so)
+    assert S.tune_get(0, uf, 4) >= 0  # tuned on this build (over 8192 columns in the bin)
+    want = P0.export()
+    P0.free()
+    for variant in range(4):
+        S.tune_set(0, uf, 4, variant)
+        P, _ = S.spai_build(ctx, A, so)
+        for u, v in zip(want, P.export()):
+            assert np.array_equal(u, v), variant
+        P.free()
+    S.tune_set(0, uf, 4, -1)
+
+
+@pytest.mark.parametrize("uf", ["half", "single", "double"])
 def test_spai_explicit_zeros_parity(ctx, uf):
     """A with explicit zeros (15% of the off-diagonal values stored as 0.0): the
     pattern pattern(A^2) follows the stored structure and the shadows count only
