@@ -404,7 +404,9 @@ int launch_spai_mid_bin_t(const SpaiArgs& a, int bin, int num_sms, size_t smem_c
                 if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = SPAI_ERR_CUDA;
                 if (!rc) cudaEventElapsedTime(&ms, e0, e1);
             }
-            if (!rc && (v < 0 || ms < best)) { best = ms; v = q; }
+            // another shape replaces the bin's own tile only when clearly faster (timings
+            // taken under a profiler or beside other work are noisy)
+            if (!rc && (v < 0 || ms < (v == 0 ? 0.95f : 1.0f) * best)) { best = ms; v = q; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -234,3 +234,23 @@ def test_batch_cgs2_and_right_preconditioning(ctx, orth, side):
         nb_s, fe_s = errors(A, bs[i], x1, xts[i])
         assert nb_b <= 10 * max(nb_s, 2.0 ** -53) and fe_b <= 10 * max(fe_s, 2.0 ** -53)
         Ps[i].free()
+
+
+def test_batch_large_system_runs_alone_and_matches_single_solve(ctx):
+    # a system of more than 65536 rows runs on a grid of its own inside the batch, exactly as
+    # gmres_ir_solve runs it: the same bits; the small ones beside it run in the shared launch
+    io = S.make_ir_opts(tau=1e-4, orth=2, **TUPLE)
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    As = [synth.conv_diff_2d(300, 20.0, 1.0, 0.1, seed=11), synth.conv_diff_2d(40, 10.0, 1.0, 0.1, seed=12)]
+    Ps, _ = S.spai_build_batch(ctx, As, so)
+    bs = [synth.rhs(A, seed=20 + i)[0] for i, A in enumerate(As)]
+    xs = [np.zeros_like(b) for b in bs]
+    sts, status = S.gmres_ir_solve_batch(ctx, As, bs, xs, Ps, io)
+    assert all(s_ >= 0 for s_ in status)
+    x1 = np.zeros_like(bs[0])
+    st1 = S.gmres_ir_solve(ctx, As[0], bs[0], x1, P=Ps[0], opts=io)
+    assert sts[0]["grid"] == st1["grid"] and sts[0]["its"] == st1["its"]
+    assert np.array_equal(xs[0], x1)
+    assert sts[1]["grid"] == 1  # 1600 rows: a team of one block
+    for P in Ps:
+        P.free()

@@ -318,6 +318,42 @@ def test_serving_mix_matches_standalone():
     c3.close()
 
 
+def test_serving_failed_request_does_not_affect_others():
+    # a request with a non-finite value fails on its own; the requests admitted with it are
+    # solved as they would be alone
+    reqs = _requests()[1:4]
+    A, b, so, io = reqs[1]
+    rp, ci, va = A
+    va = va.copy()
+    va[3] = np.nan
+    bad = ((rp, ci, va), b, so, io)
+    c1 = S.Context(0, hbm_budget=8 << 30)
+    alone = [_serve(c1, [r])[0] for r in (reqs[0], reqs[2])]
+    c1.close()
+    c2 = S.Context(0, hbm_budget=8 << 30)
+    tickets = [S.solver_submit(c2, A_, b_, so_, io_) for (A_, b_, so_, io_) in (reqs[0], bad, reqs[2])]
+    got = {}
+    t0 = time.time()
+    while len(got) < 3:
+        assert time.time() - t0 < 120
+        for i, t in enumerate(tickets):
+            if i in got:
+                continue
+            x = np.zeros(len(b) if i == 1 else len((reqs[0], bad, reqs[2])[i][1]))
+            try:
+                st = S.solver_poll(c2, t, x)
+            except S.SpaiError as e:
+                got[i] = e.code
+                continue
+            if st is not None:
+                got[i] = (x, st)
+        time.sleep(0.002)
+    c2.close()
+    assert got[1] == S._lib.ERR_NONFINITE
+    for i, j in ((0, 0), (2, 1)):
+        assert np.array_equal(got[i][0], alone[j][0]) and got[i][1]["its"] == alone[j][1]["its"]
+
+
 def test_serving_admission_budget():
     A, b, _ = synth.cfg_small_2d()
     c = S.Context(0, hbm_budget=1 << 20)
