@@ -705,10 +705,22 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 for (int v0 = wid; v0 < 2 * nv; v0 += 2 * nwp) {
                     const int v1 = v0 + nwp;
                     const bool two = v1 < 2 * nv;
+                    // every block's partial loaded first (all loads in flight), then summed
+                    // in block order as before
+                    TG x0[SPL], x1[SPL];
+#pragma unroll
+                    for (int q = 0; q < SPL; q++) {
+                        const int b = lane + 32 * q;
+                        x0[q] = b < G ? ldcg(&pv2[(size_t)v0 * G + b]) : TG(0);
+                        x1[q] = (two && b < G) ? ldcg(&pv2[(size_t)v1 * G + b]) : TG(0);
+                    }
                     TG acc0 = TG(0), acc1 = TG(0);
-                    for (int b = lane; b < G; b += 32) {
-                        acc0 += ldcg(&pv2[(size_t)v0 * G + b]);
-                        if (two) acc1 += ldcg(&pv2[(size_t)v1 * G + b]);
+#pragma unroll
+                    for (int q = 0; q < SPL; q++) {
+                        if (lane + 32 * q < G) {
+                            acc0 += x0[q];
+                            acc1 += x1[q];
+                        }
                     }
                     acc0 = warp_sum(acc0);
                     acc1 = warp_sum(acc1);
@@ -788,7 +800,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     TG acca = wsm[ra - r0] / rr;
                     TG accb = hb ? wsm[rb2 - r0] / rr : TG(0);
                     const int64_t rbx = hb ? rb2 : ra;  // an in-range row for the second load
-#pragma unroll 4
+#pragma unroll 8
                     for (int i = 0; i < j; i++) {
                         const TG* Vi = V + (int64_t)i * a.ldv;
                         const TG h = hout[i];
