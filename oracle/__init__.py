@@ -55,14 +55,14 @@ class SpaiOpts(C.Structure):
 
 class GmresOpts(C.Structure):
     _fields_ = [("ug", C.c_int), ("up", C.c_int), ("tau", C.c_double), ("maxit", C.c_int), ("orth", C.c_int),
-                ("side", C.c_int)]
+                ("side", C.c_int), ("kmode", C.c_int)]
 
 
 class IrOpts(C.Structure):
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int),
                 ("ur", C.c_int), ("mode", C.c_int), ("tau", C.c_double),
                 ("gmres_maxit", C.c_int), ("imax", C.c_int), ("stop_tol", C.c_double), ("orth", C.c_int),
-                ("side", C.c_int), ("stop_rule", C.c_int)]
+                ("side", C.c_int), ("stop_rule", C.c_int), ("kmode", C.c_int)]
 
 
 def lib():
@@ -269,8 +269,11 @@ ORTH_MGS, ORTH_CGS2, ORTH_MGS_ICWY = 0, 1, 2
 SIDE_LEFT, SIDE_RIGHT = 0, 1
 
 
-def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORTH_MGS, side=SIDE_LEFT):
-    """One GMRES solve from d = 0 (MGS or CGS2): left, (P A) d = P r; right, (A P) u = r and d = P u."""
+def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORTH_MGS, side=SIDE_LEFT,
+          kmode=MODE_PEROP):
+    """One GMRES solve from d = 0 (MGS, CGS2 or the one-reduction MGS): left, (P A) d = P r; right,
+    (A P) u = r and d = P u.  kmode: at u_g or u_p = half, MODE_PEROP rounds every operation to half
+    (the paper's chop model), MODE_ACC32 (orth 2 only) stores vectors in half and computes in binary32."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     r = np.ascontiguousarray(r, dtype=np.float64)
@@ -278,7 +281,7 @@ def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORT
     bd = C.c_int(0)
     rr = C.c_double(0.0)
     o = GmresOpts(prec(ug), prec(up), float(tau), int(maxit if maxit is not None else min(n, 500)), int(orth),
-                  int(side))
+                  int(side), int(kmode))
     if P is None:
         pp = (None, None, None)
     else:
@@ -286,6 +289,8 @@ def gmres(A, r, P=None, ug="double", up="double", tau=1e-8, maxit=None, orth=ORT
         pp = (_p(prp, C.c_int64), _p(pci, C.c_int32), _p(pva, C.c_double))
     k = lib().orc_gmres(C.c_int(n), _p(rp, C.c_int64), _p(ci, C.c_int32), _p(va, C.c_double), pp[0], pp[1],
                         pp[2], _p(r, C.c_double), C.byref(o), _p(d, C.c_double), C.byref(bd), C.byref(rr))
+    if k < 0:
+        raise ValueError("kmode MODE_ACC32 at u_g or u_p = half is defined for the one-reduction MGS only")
     return d, k, bool(bd.value), rr.value
 
 
@@ -298,11 +303,13 @@ def default_stop_tol(A, u) -> float:
 
 def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur="quad",
              tau=1e-8, gmres_maxit=None, imax=10, stop_tol=None, mode=MODE_ACC32, orth=ORTH_MGS, side=SIDE_LEFT,
-             stop_rule=STOP_BACKWARD):
+             stop_rule=STOP_BACKWARD, kmode=MODE_PEROP):
     """SPAI-GMRES-IR (Algorithm 3) given P = (rowptr, col, val_up, val_uf) or None; side selects left
     (Algorithm 3) or right preconditioning of the GMRES solves (reading R14); stop_rule and stop_tol
     the stopping rule of reading R8 (default threshold: q u for the backward rule, u for the correction
-    rule)."""
+    rule); kmode the arithmetic of the Krylov part at u_g or u_p = half (see gmres)."""
+    if kmode == MODE_ACC32 and orth != ORTH_MGS_ICWY and (prec(ug) == HALF or prec(up) == HALF):
+        raise ValueError("kmode MODE_ACC32 at u_g or u_p = half is defined for the one-reduction MGS only")
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -310,7 +317,7 @@ def gmres_ir(A, b, P=None, uf="single", u="double", ug="double", up="double", ur
         stop_tol = UNIT_ROUNDOFF[prec(u)] if stop_rule == STOP_CORRECTION else default_stop_tol(A, u)
     o = IrOpts(prec(uf), prec(u), prec(ug), prec(up), prec(ur), int(mode), float(tau),
                int(gmres_maxit if gmres_maxit is not None else min(n, 500)), int(imax), float(stop_tol), int(orth),
-               int(side), int(stop_rule))
+               int(side), int(stop_rule), int(kmode))
     x = np.zeros(n)
     its = np.zeros(imax + 1, dtype=np.int32)
     nbe = np.full(imax + 1, np.nan)

@@ -40,6 +40,17 @@
  *                to half once (the FP16-storage / FP32-accumulate model).  At
  *                u_f = single or double the two modes coincide.
  *
+ * The same two modes for the Krylov part (kmode) when u_g or u_p is half:
+ *   MODE_PEROP : every GMRES operation rounded to u_g / u_p (the paper's chop
+ *                model);
+ *   MODE_ACC32 : (one-reduction MGS only) half is a storage format: the
+ *                basis vectors, u_j and w are stored in half, every scalar,
+ *                inner product, quotient and update is computed in binary32
+ *                and the vectors are rounded to half once when stored; the
+ *                sparse products take half matrix values and inputs,
+ *                multiply and sum in binary32 and round the result to half.
+ *                At u_g, u_p in {single, double} it is MODE_PEROP.
+ *
  * Readings of points where the paper is silent or garbled (each one is a
  * parameter or a documented constant):
  *   R1  L_k = { l in I_k : s_l != 0 }, and I_k always contains k.
@@ -77,6 +88,11 @@
  *       u_g (as with P = I), and the correction d = P (V_k y) in u_p,
  *       stored in u_g.  The right SPAI (A P ~ I) is the transpose of the
  *       left SPAI of A^T (Algorithm 1 run on A D, D scaling the columns of A).
+ *   R17 u_g or u_p = half (Algorithm 3 allows any precision there; the
+ *       paper's runs use u_g = u_p = u): GMRES gets the residual scaled by
+ *       the power of two 2^-e with ||r||_inf = m 2^e, m in [0.5, 1) (exact),
+ *       and the correction is scaled back by 2^e; otherwise the residuals of
+ *       a converging refinement fall below half's range.
  */
 #include <math.h>
 #include <stdint.h>
@@ -609,6 +625,7 @@ typedef struct {
     int side;        /* 0: left preconditioning (Algorithm 3);
                         1: right preconditioning, the variant the paper leaves
                         as future work at the end of Section 3 */
+    int kmode;       /* MODE_PEROP / MODE_ACC32 for u_g, u_p = half */
 } orc_gmres_opts;
 
 /*
@@ -622,15 +639,15 @@ typedef struct {
 /* The Arnoldi product w = fl_ug(P (A v)) (left) or fl_ug(A (P v)) (right),
  * each product in u_p; P = NULL: w = fl_ug(A v).  t: scratch. */
 static void arnoldi_product(int n, const int64_t* arp, const int* aci, const double* av, const int64_t* prp,
-                            const int* pci, const double* pv, int right, int up, int ug, const double* v,
-                            double* t, double* w)
+                            const int* pci, const double* pv, int right, int up, int ug, int pmode,
+                            const double* v, double* t, double* w)
 {
     if (right && prp) {
-        spmv_p(n, prp, pci, pv, v, up, MODE_PEROP, t);
-        spmv_p(n, arp, aci, av, t, up, MODE_PEROP, w);
+        spmv_p(n, prp, pci, pv, v, up, pmode, t);
+        spmv_p(n, arp, aci, av, t, up, pmode, w);
     } else {
-        spmv_p(n, arp, aci, av, v, up, MODE_PEROP, t);
-        if (prp) spmv_p(n, prp, pci, pv, t, up, MODE_PEROP, w);
+        spmv_p(n, arp, aci, av, v, up, pmode, t);
+        if (prp) spmv_p(n, prp, pci, pv, t, up, pmode, w);
         else for (int i = 0; i < n; i++) w[i] = t[i];
     }
     for (int i = 0; i < n; i++) w[i] = rnd(w[i], ug);
@@ -653,39 +670,42 @@ static void arnoldi_product(int n, const int64_t* arp, const int* aci, const dou
  * of the substitution run in index order, as in MGS.
  *   V: the basis (V[i] = q_i, allocated here for i <= j); U: u_j on entry,
  *   u_{j+1} on return; W: w; L: row i at L + i * ldl; h: the coefficients.
+ *   ug: the storage precision of the vectors; ag: the precision of every
+ *   operation (u_g, or binary32 for half storage under MODE_ACC32); each
+ *   vector entry is rounded to ug once it is complete.
  * Returns r.  For j = 0 there is no previous column and no L row.
  */
 static double icwy_step(int n, int j, double** V, double* U, const double* W, double* L, int ldl, double* a,
-                        double* c, double* h, int ug, int with_product, double* rnorm_only)
+                        double* c, double* h, int ug, int ag, int with_product, double* rnorm_only)
 {
-    double nu = dot_p(U, 1, U, 1, n, ug, MODE_PEROP);
-    double r = rnd(sqrt(nu), ug);
+    double nu = dot_p(U, 1, U, 1, n, ag, MODE_PEROP);
+    double r = rnd(sqrt(nu), ag);
     if (rnorm_only || !with_product) {
         if (rnorm_only) *rnorm_only = r;
         return r;
     }
     for (int i = 0; i < j; i++) {
-        a[i] = dot_p(V[i], 1, U, 1, n, ug, MODE_PEROP);
-        c[i] = dot_p(V[i], 1, W, 1, n, ug, MODE_PEROP);
+        a[i] = dot_p(V[i], 1, U, 1, n, ag, MODE_PEROP);
+        c[i] = dot_p(V[i], 1, W, 1, n, ag, MODE_PEROP);
     }
-    double delta = dot_p(U, 1, W, 1, n, ug, MODE_PEROP);
+    double delta = dot_p(U, 1, W, 1, n, ag, MODE_PEROP);
     if (r == 0.0) return r;
     if (!V[j]) V[j] = (double*)malloc(sizeof(double) * (size_t)n);
-    for (int q = 0; q < n; q++) V[j][q] = rnd(U[q] / r, ug);
+    for (int q = 0; q < n; q++) V[j][q] = rnd(rnd(U[q] / r, ag), ug);
     double* Lj = L + (size_t)j * ldl;
-    for (int i = 0; i < j; i++) Lj[i] = rnd(a[i] / r, ug);
-    for (int i = 0; i < j; i++) h[i] = rnd(c[i] / r, ug);
-    h[j] = rnd(rnd(delta / r, ug) / r, ug);
+    for (int i = 0; i < j; i++) Lj[i] = rnd(a[i] / r, ag);
+    for (int i = 0; i < j; i++) h[i] = rnd(c[i] / r, ag);
+    h[j] = rnd(rnd(delta / r, ag) / r, ag);
     for (int i = 0; i <= j; i++) {
         const double* Li = L + (size_t)i * ldl;
         double acc = h[i];
-        for (int k = 0; k < i; k++) acc = rnd(acc - rnd(Li[k] * h[k], ug), ug);
+        for (int k = 0; k < i; k++) acc = rnd(acc - rnd(Li[k] * h[k], ag), ag);
         h[i] = acc;
     }
     for (int q = 0; q < n; q++) {
-        double acc = rnd(W[q] / r, ug);
-        for (int i = 0; i <= j; i++) acc = rnd(acc - rnd(h[i] * V[i][q], ug), ug);
-        U[q] = acc;
+        double acc = rnd(W[q] / r, ag);
+        for (int i = 0; i <= j; i++) acc = rnd(acc - rnd(h[i] * V[i][q], ag), ag);
+        U[q] = rnd(acc, ug);
     }
     return r;
 }
@@ -717,6 +737,9 @@ static int gmres_icwy(int n, const int64_t* arp, const int* aci, const double* a
 {
     int ug = o->ug, up = o->up, K = o->maxit;
     const int right = o->side == 1;
+    /* MODE_ACC32: half is storage only; operations in binary32 */
+    const int ag = (o->kmode == MODE_ACC32 && ug == PH) ? PS : ug;
+    const int pmode = o->kmode == MODE_ACC32 ? MODE_ACC32 : MODE_PEROP;
     double* t = (double*)malloc(sizeof(double) * (size_t)n);
     double* U = (double*)malloc(sizeof(double) * (size_t)n);
     double* W = (double*)malloc(sizeof(double) * (size_t)n);
@@ -735,17 +758,17 @@ static int gmres_icwy(int n, const int64_t* arp, const int* aci, const double* a
     for (int i = 0; i < n; i++) d[i] = 0.0;
     /* u_0 = P r (left) or r (right), in u_p then u_g; beta = ||u_0|| comes
      * from the first reduction */
-    if (prp && !right) spmv_p(n, prp, pci, pv, r, up, MODE_PEROP, U);
+    if (prp && !right) spmv_p(n, prp, pci, pv, r, up, pmode, U);
     else for (int i = 0; i < n; i++) U[i] = rnd(r[i], up);
     for (int i = 0; i < n; i++) U[i] = rnd(U[i], ug);
     double beta = 0.0;
     int k = 0;
     for (int j = 0; K > 0; j++) {
         const int prod = j < K;
-        if (prod) arnoldi_product(n, arp, aci, av, prp, pci, pv, right, up, ug, U, t, W);
+        if (prod) arnoldi_product(n, arp, aci, av, prp, pci, pv, right, up, ug, pmode, U, t, W);
         double rn = 0.0;
         /* the last pass (j = K) only needs ||u_K|| */
-        double rj = icwy_step(n, j, V, U, W, L, K + 1, a, c, h, ug, prod, prod ? NULL : &rn);
+        double rj = icwy_step(n, j, V, U, W, L, K + 1, a, c, h, ug, ag, prod, prod ? NULL : &rn);
         if (j == 0) {
             beta = rj;
             g[0] = beta;
@@ -770,11 +793,11 @@ static int gmres_icwy(int n, const int64_t* arp, const int* aci, const double* a
     }
     for (int q = 0; q < n; q++) {
         double acc = 0.0;
-        for (int i = 0; i < k; i++) acc = rnd(acc + rnd(V[i][q] * rnd(y[i], ug), ug), ug);
+        for (int i = 0; i < k; i++) acc = rnd(acc + rnd(V[i][q] * rnd(y[i], ag), ag), ag);
         d[q] = acc;
     }
     if (right && prp) {
-        spmv_p(n, prp, pci, pv, d, up, MODE_PEROP, t);
+        spmv_p(n, prp, pci, pv, d, up, pmode, t);
         for (int q = 0; q < n; q++) d[q] = rnd(t[q], ug);
     }
     for (int i = 0; i <= K + 1; i++) free(V[i]);
@@ -788,6 +811,7 @@ int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
               const double* r, const orc_gmres_opts* o, double* d, int* breakdown, double* relres)
 {
     if (o->orth == 2) return gmres_icwy(n, arp, aci, av, prp, pci, pv, r, o, d, breakdown, relres);
+    if (o->kmode == MODE_ACC32 && (o->ug == PH || o->up == PH)) return -1; /* defined for orth 2 only */
     int ug = o->ug, up = o->up, K = o->maxit;
     double* t = (double*)malloc(sizeof(double) * (size_t)n);
     double* w = (double*)malloc(sizeof(double) * (size_t)n);
@@ -907,6 +931,7 @@ typedef struct {
     int orth;               /* 0 MGS, 1 CGS2 */
     int side;               /* 0 left, 1 right preconditioning */
     int stop_rule;          /* STOP_BACKWARD, STOP_FIXED, STOP_CORRECTION */
+    int kmode;              /* arithmetic mode of the Krylov part at u_g, u_p = half */
 } orc_ir_opts;
 
 /*
@@ -936,7 +961,7 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
     if (prp) spmv_p(n, prp, pci, pv_uf, b, o->uf, o->mode, x);
     else for (int i = 0; i < n; i++) x[i] = rnd(b[i], o->uf);
     for (int i = 0; i < n; i++) x[i] = rnd(x[i], o->u);
-    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit, o->orth, o->side };
+    orc_gmres_opts go = { o->ug, o->up, o->tau, o->gmres_maxit, o->orth, o->side, o->kmode };
     int i;
     double dn = 0.0, qprev = 0.0; /* ||d_{i-1}||_inf and q_{i-1} (reading R8) */
     *steps = 0;
@@ -954,7 +979,19 @@ int orc_gmres_ir(int n, const int64_t* arp, const int* aci, const double* av,
         qprev = q;
         int bd = 0;
         double rr;
+        /* reading R17: with u_g or u_p = half the residual is scaled by a
+         * power of two, 2^-e with ||r||_inf = m 2^e, m in [0.5, 1), before
+         * GMRES (exact; residuals of a converging refinement would otherwise
+         * fall below half's range), and d is scaled back by 2^e */
+        int e = 0;
+        if ((o->ug == PH || o->up == PH) && rn > 0.0) {
+            frexp(rn, &e);
+            for (int q2 = 0; q2 < n; q2++) r[q2] = ldexp(r[q2], -e);
+        }
         its[i] = orc_gmres(n, arp, aci, av, prp, pci, pv_up, r, &go, dd, &bd, &rr);
+        if (its[i] < 0) { its[i] = 0; status |= IR_NONFINITE; break; } /* unsupported mode */
+        if (e != 0)
+            for (int q2 = 0; q2 < n; q2++) dd[q2] = ldexp(dd[q2], e);
         if (bd) status |= IR_BREAKDOWN;
         dn = 0.0;
         for (int q2 = 0; q2 < n; q2++) {
@@ -1041,9 +1078,9 @@ int orc_arnoldi(int n, const int64_t* arp, const int* aci, const double* av,
         int cols = 0;
         for (int j = 0; j <= k; j++) {
             const int prod = j < k;
-            if (prod) arnoldi_product(n, arp, aci, av, prp, pci, pv, 0, up, ug, U, t, W);
+            if (prod) arnoldi_product(n, arp, aci, av, prp, pci, pv, 0, up, ug, MODE_PEROP, U, t, W);
             double rn = 0.0;
-            double rj = icwy_step(n, j, V, U, W, L, k + 1, a, c, h, ug, prod, prod ? NULL : &rn);
+            double rj = icwy_step(n, j, V, U, W, L, k + 1, a, c, h, ug, ug, prod, prod ? NULL : &rn);
             if (j > 0) Hout[(size_t)(j - 1) * (k + 1) + j] = rj;
             if (rj == 0.0) break;
             if (!prod) {

@@ -821,3 +821,77 @@ def test_round_to_matches_scalar_rounding():
         r = O.round_to(x, p)
         assert all(r[i] == O.lib().orc_round(float(x[i]), O.prec(p)) for i in range(0, 1000, 7))
     np.testing.assert_array_equal(O.round_to(x, "single"), x.astype(np.float32).astype(np.float64))
+
+
+# ---------------------------------------------------------------- half-storage Krylov part (kmode)
+
+
+def test_half_krylov_acc32_is_perop_at_single_and_double():
+    # the Krylov arithmetic mode only concerns half: with u_g, u_p single or
+    # double the two modes give the same bits
+    A, b, x = synth.cfg_small_2d()
+    P = O.assemble_P(O.spai(A, init=O.PAT_A, uf="single", max_fill=30), "single", "single")
+    r = np.random.default_rng(7).normal(size=1024)
+    for ug, up in (("single", "single"), ("double", "single"), ("single", "double")):
+        d0 = O.gmres(A, r, (P[0], P[1], P[2]), ug=ug, up=up, tau=1e-4, orth=O.ORTH_MGS_ICWY)
+        d1 = O.gmres(A, r, (P[0], P[1], P[2]), ug=ug, up=up, tau=1e-4, orth=O.ORTH_MGS_ICWY,
+                     kmode=O.MODE_ACC32)
+        assert d0[1] == d1[1] and np.array_equal(d0[0], d1[0])
+
+
+def test_half_krylov_finite_termination():
+    # textbook: GMRES on a diagonalisable matrix with two distinct eigenvalues
+    # terminates after two iterations; with the vectors stored in half (values
+    # 1 and 2, and a right-hand side of ones, are exact in half) the third
+    # Arnoldi vector is at the level of half's rounding, and d = A^{-1} r to
+    # that level
+    n = 64
+    Ad = np.diag(np.where(np.arange(n) < 40, 1.0, 2.0))
+    r = np.ones(n)
+    d, k, bd, rr = O.gmres(dense_to_csr(Ad), r, None, ug="half", up="half", tau=1e-2,
+                           orth=O.ORTH_MGS_ICWY, kmode=O.MODE_ACC32)
+    assert k <= 2
+    np.testing.assert_allclose(d, r / np.diag(Ad), rtol=8 * 2.0 ** -11)
+
+
+def test_half_krylov_acc32_refinement_reaches_working_accuracy():
+    # Algorithm 3 with u_g = u_p = half (FP16 storage, FP32 operations) on a
+    # well-conditioned SPAI-preconditioned system, tau ~ sqrt(u_half): each GMRES
+    # solve is only accurate to ~u_half, but the refinement (u = double, u_r =
+    # quad) still converges to a backward error of q u (Theorem 2's limit); the
+    # vectors stored in half cost refinement steps, not accuracy.  Without the
+    # power-of-two scaling of the residual (reading R17) the residuals of later
+    # steps fall below half's range and the refinement stagnates near 1e-8.
+    A, b, x_true = synth.cfg_small_2d()
+    P = O.assemble_P(O.spai(A, init=O.PAT_A, uf="single", max_fill=30), "half", "single")
+    R = O.gmres_ir(A, b, P, uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2,
+                   orth=O.ORTH_MGS_ICWY, kmode=O.MODE_ACC32, imax=30)
+    assert R["status"] & O.IR_CONVERGED
+    assert R["nbe"][-1] <= O.default_stop_tol(A, "double")
+    ferr = np.max(np.abs(R["x"] - x_true)) / np.max(np.abs(x_true))
+    assert ferr <= 1e-12
+    # the half-precision Krylov part needs more refinement steps than single's
+    Ps = O.assemble_P(O.spai(A, init=O.PAT_A, uf="single", max_fill=30), "single", "single")
+    S = O.gmres_ir(A, b, Ps, uf="single", u="double", ug="single", up="single", ur="quad", tau=1e-2,
+                   orth=O.ORTH_MGS_ICWY)
+    assert R["steps"] > S["steps"]
+
+
+def test_half_krylov_acc32_beats_per_operation_half():
+    # binary32 operations on half-stored vectors give a more accurate GMRES
+    # solution than rounding every operation to half (the chop model), measured
+    # by the true preconditioned residual of a long solve
+    A, b, x = synth.cfg_small_2d()
+    Ad = synth.to_scipy(A)
+    S = O.spai(A, init=O.PAT_A, uf="single", max_fill=30)
+    P = O.assemble_P(S, "half", "single")
+    Pd = sp.csr_matrix((P[2], P[1], P[0]), shape=(1024, 1024))
+    r = np.random.default_rng(11).normal(size=1024)
+    z = Pd @ r
+    res = {}
+    for km in (O.MODE_PEROP, O.MODE_ACC32):
+        d, k, bd, rr = O.gmres(A, r, (P[0], P[1], P[2]), ug="half", up="half", tau=1e-6, maxit=80,
+                               orth=O.ORTH_MGS_ICWY, kmode=km)
+        res[km] = np.linalg.norm(z - Pd @ (Ad @ d)) / np.linalg.norm(z)
+    assert res[O.MODE_ACC32] < res[O.MODE_PEROP]
+    assert res[O.MODE_ACC32] <= 50 * 2.0 ** -11
