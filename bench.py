@@ -713,13 +713,16 @@ def main():
     # then the all-FP64 form of the method (every precision double) on the same inputs
     variants = {}
     q_row = int(np.max(np.diff(A[0])))
-    for name, orth, tup, stol in (("arnoldi_mgs_rounds", 0, TUPLE, 0.0), ("arnoldi_cgs2", 1, TUPLE, 0.0),
-                                  ("fp64_64cube", ORTH, FP64, 0.0),
-                                  ("fp64_64cube_mixed_stop", ORTH, FP64, q_row * 2.0 ** -24)):
+    # u_g = u_p = half (half storage, binary32 arithmetic; tau ~ sqrt(u_half)) beside them
+    half_k = dict(TUPLE, ug="half", up="half")
+    for name, orth, tup, stol, tau2 in (("arnoldi_mgs_rounds", 0, TUPLE, 0.0, TAU), ("arnoldi_cgs2", 1, TUPLE, 0.0, TAU),
+                                        ("fp64_64cube", ORTH, FP64, 0.0, TAU),
+                                        ("fp64_64cube_mixed_stop", ORTH, FP64, q_row * 2.0 ** -24, TAU),
+                                        ("half_krylov_64cube", 2, half_k, 0.0, 1e-2)):
         if args.no_cgs2:
             break
-        io2 = S.make_ir_opts(tau=TAU, orth=orth, stop_tol=stol, **tup)
-        so2 = so if tup is TUPLE else S.make_spai_opts(init=2, max_fill=MAX_FILL, uf=tup["uf"], eps=0.3)
+        io2 = S.make_ir_opts(tau=tau2, orth=orth, stop_tol=stol, ir_max_steps=30, **tup)
+        so2 = so if tup["uf"] == TUPLE["uf"] else S.make_spai_opts(init=2, max_fill=MAX_FILL, uf=tup["uf"], eps=0.3)
 
         def step2():
             P, sst = S.spai_build(ctx, Ad, so2)
@@ -743,13 +746,13 @@ def main():
         x2 = xd.cpu().numpy()
         nbe2 = float(np.max(np.abs(b - Ms @ x2)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x2)) + np.max(np.abs(b))))
         kms = [s["ms_kernel"] for s in st2]
-        sz = dict(s_u=4 if tup["u"] == "single" else 8, s_g=4 if tup["ug"] == "single" else 8,
-                  s_p=4 if tup["up"] == "single" else 8)
+        nb = {"half": 2, "single": 4, "double": 8}
+        sz = dict(s_u=nb[tup["u"]], s_g=nb[tup["ug"]], s_p=nb[tup["up"]])
         kbytes = [ir_kernel_bytes(n, nnz, s["nnz_P"], s["its"], **sz) for s in st2]
         ach = float(np.mean([b_ / (m / 1000.0) for b_, m in zip(kbytes, kms)]) / 1e9)
         variants[name] = dict(value=job_throughput(world, args.steps, t2), unit=UNIT, ms_per_step=t2 / args.steps,
                               ir_kernel_ms=float(np.mean(kms)), its=st2[-1]["its"], steps=st2[-1]["steps"],
-                              backward_error=nbe2, tuple=tup, orth=orth,
+                              backward_error=nbe2, tuple=tup, orth=orth, tau=tau2,
                               roofline=dict(kernel="k_ir (orth=%d)" % orth, bound="hbm", achieved=ach,
                                             peak=hbm_peak, unit="GB/s", frac=ach / hbm_peak,
                                             algorithmic_bytes_per_launch=float(np.mean(kbytes))))
@@ -760,6 +763,11 @@ def main():
         variants["fp64_64cube_mixed_stop"]["workload"] = ("the all-FP64 form stopped at the mixed form's backward-error "
                                                           "tolerance q u_single (the same accuracy target)")
         variants["fp64_64cube_mixed_stop"]["mixed_over_fp64"] = value / variants["fp64_64cube_mixed_stop"]["value"]
+    if "half_krylov_64cube" in variants:
+        variants["half_krylov_64cube"]["workload"] = (
+            "the 64^3 workload with u_g = u_p = half (Krylov vectors and the SELL copies of A and P in half, "
+            "binary32 arithmetic, residual scaled by a power of two), tau 1e-2, one-reduction MGS; stop at q u_single")
+        variants["half_krylov_64cube"]["over_headline"] = variants["half_krylov_64cube"]["value"] / value
 
     extra = {}
     if world == 1 and not args.no_extra:

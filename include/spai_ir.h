@@ -113,8 +113,14 @@ typedef struct {
 
 /* Algorithm 3 parameters: the five precisions, tau, i_max and the stop rule. */
 typedef struct {
-    spai_prec uf, u, ug, up, ur; /* u in {single,double}; ug,up in {single,double};
-                                    ur in {double,quad}, ur >= u                */
+    spai_prec uf, u, ug, up, ur; /* u in {single,double}; ug,up in {single,double}, or
+                                    half in one or both with single for the other and
+                                    orth = 2 (half storage of the Krylov vectors and of
+                                    the matrices' product copies, binary32 arithmetic;
+                                    GMRES then solves for r scaled by the power of two
+                                    nearest below ||r||_inf, and d is scaled back:
+                                    values beyond half's range give a non-finite
+                                    status); ur in {double,quad}, ur >= u        */
     double tau;                  /* GMRES relative tolerance on ||P(r - A d)||/||P r|| */
     int gmres_max_it;            /* iterations per GMRES solve (1..1024); <= 0: min(n, 500) */
     int ir_max_steps;            /* i_max (1..64)                                      */

@@ -16,7 +16,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libspai_ir.so")
 SOURCES = (["spai_build.cu", "spai_column_half.cu", "spai_column_single.cu", "spai_column_double.cu",
             "spai_mid_half.cu", "spai_mid_single.cu", "spai_mid_double.cu", "gmres_ir.cu", "capi.cu"] +
-           ["gmres_ir_k_%s.cu" % t for t in ("fff", "ffd", "fdf", "fdd", "dff", "dfd", "ddf", "ddd")])
+           ["gmres_ir_k_%s.cu" % t for t in ("fff", "ffd", "fdf", "fdd", "dff", "dfd", "ddf", "ddd",
+                                              "xhh", "xhf", "xfh")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

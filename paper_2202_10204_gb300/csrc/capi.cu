@@ -1010,6 +1010,7 @@ void spai_precond_free(spai_precond P)
     dev_free(P->rowptr, s);
     dev_free(P->col, s);
     dev_free(P->val, s);
+    sell_free(&P->sell_f16, s);
     sell_free(&P->sell_f32, s);
     sell_free(&P->sell_f64, s);
     dev_free(P->val_uf, s);

@@ -70,8 +70,8 @@ __global__ void k_sell_fill(int64_t n, const int64_t* __restrict__ rp, const int
         const int len = row < n ? (int)(rp[row + 1] - b) : 0;
         for (int c = 0; c < w; c++) {
             int64_t o = off[s] + 32 * c + lane;
-            if (c < len) { scol[o] = ci[b + c]; sval[o] = (TP)val[b + c]; }
-            else { scol[o] = row < n ? (int32_t)row : 0; sval[o] = TP(0); }
+            if (c < len) { scol[o] = ci[b + c]; sval[o] = from_d<TP>(val[b + c]); }
+            else { scol[o] = row < n ? (int32_t)row : 0; sval[o] = from_d<TP>(0.0); }
         }
     }
 }
@@ -147,6 +147,14 @@ int ir_kernels(int u, int ug, int up, int ur, int orth, IrKernels* k)
 {
     const int rm = ur == SPAI_QUAD ? 2 : 1;
     const bool ls = orth == 2;
+    const bool ud = u == SPAI_DOUBLE;
+    if (ug == SPAI_HALF || up == SPAI_HALF) {
+        k->one = nullptr;
+        if (ug == SPAI_HALF && up == SPAI_HALF) (ud ? ir_kernels_dhh : ir_kernels_fhh)(rm, ls, k);
+        else if (ug == SPAI_HALF && up == SPAI_SINGLE) (ud ? ir_kernels_dhf : ir_kernels_fhf)(rm, ls, k);
+        else if (ug == SPAI_SINGLE && up == SPAI_HALF) (ud ? ir_kernels_dfh : ir_kernels_ffh)(rm, ls, k);
+        return k->one ? 0 : SPAI_ERR_UNSUPPORTED;
+    }
     const int key = (u == SPAI_DOUBLE) * 4 + (ug == SPAI_DOUBLE) * 2 + (up == SPAI_DOUBLE);
     switch (key) {
     case 0: ir_kernels_fff(rm, ls, k); break;
@@ -200,9 +208,15 @@ int launch_ir(IrArgs& a, const IrKernels& K, int sg, int num_sms, cudaStream_t s
 
 int prec_bytes(int p) { return p == SPAI_HALF ? 2 : (p == SPAI_SINGLE ? 4 : 8); }
 
+// the preconditioner's cached SELL-32 copy in u_p
+SellMat* sell_cache(spai_precond P, int up)
+{
+    return up == SPAI_HALF ? &P->sell_f16 : (up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64);
+}
+
 }  // namespace
 
-// SELL-32 copy of a CSR matrix with values rounded to `prec` (single or double),
+// SELL-32 copy of a CSR matrix with values rounded to `prec` (half, single or double),
 // in two halves: sell_begin computes the slice offsets (the entry count stays
 // on the device at off[nslices]); sell_finish allocates and fills once that
 // count is known on the host.
@@ -234,7 +248,8 @@ int sell_finish(int64_t n, const int64_t* rp, const int32_t* ci, const double* v
     out->nnz = total;
     if ((rc = dev_alloc((void**)&out->col, sizeof(int32_t) * std::max<int64_t>(total, 1), s))) return rc;
     if ((rc = dev_alloc(&out->val, (size_t)prec_bytes(prec) * std::max<int64_t>(total, 1), s))) return rc;
-    if (prec == SPAI_SINGLE) k_sell_fill<float><<<gb, tb, 0, s>>>(n, rp, ci, val, out->off, out->col, (float*)out->val);
+    if (prec == SPAI_HALF) k_sell_fill<__half><<<gb, tb, 0, s>>>(n, rp, ci, val, out->off, out->col, (__half*)out->val);
+    else if (prec == SPAI_SINGLE) k_sell_fill<float><<<gb, tb, 0, s>>>(n, rp, ci, val, out->off, out->col, (float*)out->val);
     else k_sell_fill<double><<<gb, tb, 0, s>>>(n, rp, ci, val, out->off, out->col, (double*)out->val);
     *launches += 1;
     SPAI_CUDA_TRY(cudaGetLastError());
@@ -297,8 +312,12 @@ int ir_check_opts(const ir_opts* o)
 {
     if (!o) return SPAI_ERR_INVALID_ARG;
     if (o->u != SPAI_SINGLE && o->u != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (o->ug != SPAI_SINGLE && o->ug != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (o->up != SPAI_SINGLE && o->up != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    if (o->ug != SPAI_HALF && o->ug != SPAI_SINGLE && o->ug != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    if (o->up != SPAI_HALF && o->up != SPAI_SINGLE && o->up != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
+    // half Krylov storage: with the one-reduction MGS, and beside single only
+    if ((o->ug == SPAI_HALF || o->up == SPAI_HALF) &&
+        (o->orth != 2 || o->ug == SPAI_DOUBLE || o->up == SPAI_DOUBLE))
+        return SPAI_ERR_UNSUPPORTED;
     if (o->ur != SPAI_DOUBLE && o->ur != SPAI_QUAD) return SPAI_ERR_UNSUPPORTED;
     if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
     if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
@@ -354,12 +373,12 @@ int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
     TRY(dev_alloc((void**)&J.norms, sizeof(unsigned long long) * 5, s));
     CTRY(cudaMemsetAsync(J.norms, 0, sizeof(unsigned long long) * 5, s));
     if (o->orth) {
-        TRY(dev_alloc(&J.pvec, (size_t)sg * 2 * MAX_GRID * (kmax + 1), s));
+        TRY(dev_alloc(&J.pvec, (size_t)ir_scalar_bytes(sg) * 2 * MAX_GRID * (kmax + 1), s));
         TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
         CTRY(cudaMemsetAsync(J.gcount, 0, sizeof(unsigned), s));
     }
     if (o->orth == 2) {
-        TRY(dev_alloc(&J.L, (size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1), s));
+        TRY(dev_alloc(&J.L, (size_t)ir_scalar_bytes(sg) * ((size_t)(kmax + 1) * kmax / 2 + 1), s));
         TRY(dev_alloc((void**)&J.gpub, sizeof(double) * (kmax + 2), s));
     }
     CTRY(cudaMemsetAsync(J.its, 0, sizeof(int) * (imax + 1), s));
@@ -420,7 +439,7 @@ int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int*
     if (cudaMemcpyAsync(J.norms + 3, J.As.off + nsl, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return SPAI_ERR_CUDA;
     if (P) {
-        cache = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
+        cache = sell_cache(P, o->up);
         if (!cache->off) {
             rc = sell_begin(J.n, P->rowptr, num_sms, s, cache, nl);
             if (rc) return rc;
@@ -429,7 +448,7 @@ int ir_job_prepare(IrJob& J, int num_sms, cudaStream_t s, const ir_opts* o, int*
         } else {
             cache = nullptr;  // already made
         }
-        J.Ps = o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64;
+        J.Ps = sell_cache(P, o->up);
     }
     rc = ir_job_norms_x0(J, num_sms, s, o, nl);
     if (rc) return rc;
@@ -742,7 +761,7 @@ struct BatchRun {
             const int64_t nsl = (jb.n + 31) >> 5;
             unsigned long long* slot = d_slots + 5 * (size_t)i;
             if (!rc && jb.P) {
-                SellMat* cache = o->up == SPAI_SINGLE ? &jb.P->sell_f32 : &jb.P->sell_f64;
+                SellMat* cache = sell_cache(jb.P, o->up);
                 if (!cache->off && !building.count(jb.P)) {
                     rc = sell_begin(jb.n, jb.P->rowptr, num_sms, s, cache, nl);
                     building.insert(jb.P);
@@ -760,7 +779,7 @@ struct BatchRun {
         // a preconditioner's SELL copy counts as built once its offsets exist: on
         // failure the copies this batch started are dropped again
         auto drop_started = [&]() {
-            for (spai_precond P : building) sell_free(o->up == SPAI_SINGLE ? &P->sell_f32 : &P->sell_f64, s);
+            for (spai_precond P : building) sell_free(sell_cache(P, o->up), s);
         };
         std::vector<unsigned long long> hs(5 * (size_t)count, 0);
         if (!rc && cudaMemcpyAsync(hs.data(), d_slots, sizeof(unsigned long long) * hs.size(), cudaMemcpyDeviceToHost, s) !=
@@ -776,7 +795,7 @@ struct BatchRun {
             rc = sell_finish(jb.n, jb.A->rowptr, jb.A->col, jb.A->val, o->up, num_sms, s, &jb.As, (int64_t)h[3], nl);
             if (!rc && pbuild[i])
                 rc = sell_finish(jb.n, jb.P->rowptr, jb.P->col, jb.P->val, o->up, num_sms, s,
-                                 o->up == SPAI_SINGLE ? &jb.P->sell_f32 : &jb.P->sell_f64, (int64_t)h[4], nl);
+                                 sell_cache(jb.P, o->up), (int64_t)h[4], nl);
             if (rc) { drop_started(); return rc; }
         }
         // arguments in claim order, every system prepared for its class's team size

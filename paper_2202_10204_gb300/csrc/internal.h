@@ -40,7 +40,7 @@ struct spai_precond_s {
     int64_t* rowptr = nullptr;   // n + 1
     int32_t* col = nullptr;      // nnz
     double* val = nullptr;       // nnz, unrounded mbar_k * d(J_k)
-    SellMat sell_f32, sell_f64;  // lazily made SELL-32 copies in u_p = single / double
+    SellMat sell_f16, sell_f32, sell_f64;  // lazily made SELL-32 copies in u_p = half / single / double
     void* val_uf = nullptr;      // copy rounded to u_f (used by x0 = P b)
     int uf = SPAI_DOUBLE;
     cudaStream_t stream = nullptr;  // the building context's stream (the default stream once it is gone)

@@ -11,7 +11,9 @@
 // without another barrier.  The Givens rotations, H, g and y are double
 // precision in every block.
 //
-// Template parameters: TU, TG, TP the storage types of u, u_g, u_p; RM = 2
+// Template parameters: TU, TG, TP the storage types of u, u_g, u_p (u_g and u_p
+// may be half, for the one-reduction MGS only: vectors and matrix values are
+// stored in half, every operation on them is binary32); RM = 2
 // for the double-double residual (u_r = quad); LS selects the one-reduction
 // MGS (orth 2), compiled as its own kernel so that the MGS / CGS2 kernel
 // keeps its register allocation.
@@ -88,6 +90,10 @@ struct IrArgs {
     double* gpub;               // kmax + 2: g as that block leaves it
 };
 
+// Bytes of a Krylov-part scalar for sg = sizeof(u_g): binary32 when the
+// vectors are stored in half.
+inline int ir_scalar_bytes(int sg) { return sg == 2 ? 4 : sg; }
+
 // Dynamic shared memory of the refinement kernel (ir_body's layout), sg =
 // sizeof(u_g): five double arrays of kmax + 2 (Givens, g, the current column,
 // y), the slice offsets of A and P, the block's rows of w (two blocks' rows
@@ -100,8 +106,9 @@ inline size_t ir_smem_bytes(int64_t rb, int kmax, int g2, int orth, int jl, int 
     const int64_t nsl = (rb + 31) >> 5;
     size_t b = sizeof(double) * 5 * (kmax + 2) + sizeof(int64_t) * 2 * (nsl + 1) + (g2 ? 2 : 1) * rb * sg + 64;
     if (orth == 2)
-        b += (size_t)sg * ((size_t)rb + 2 * (kmax + 1) + 2 * (kmax + 1) + 2 * (kmax + 1 + 32) +
-                           (size_t)jl * (jl - 1) / 2) +
+        b += (size_t)sg * rb +
+             (size_t)ir_scalar_bytes(sg) * (2 * (kmax + 1) + 2 * (kmax + 1) + 2 * (kmax + 1 + 32) +
+                                            (size_t)jl * (jl - 1) / 2) +
              sizeof(int) * (kmax + 2) + 16;  // the unit-count table
     return b;
 }
@@ -112,7 +119,7 @@ inline int ir_pick_jl(int64_t rb, int kmax, size_t dyn_max, int sg)
 {
     const size_t base = ir_smem_bytes(rb, kmax, 0, 2, 0, sg);
     if (base + 1024 > dyn_max) return 0;
-    const size_t room = std::min<size_t>(dyn_max - base - 1024, 64 << 10) / sg;
+    const size_t room = std::min<size_t>(dyn_max - base - 1024, 64 << 10) / ir_scalar_bytes(sg);
     int jl = 0;
     while (jl < kmax + 1 && (size_t)(jl + 1) * jl / 2 <= room) jl++;
     return jl;
@@ -329,11 +336,13 @@ __device__ inline bool xbar(const IrArgs& a, IrShared* sh)
 
 // y = M x for the block's rows (SELL-32), two rows per thread per pass with
 // their loads interleaved; `store(row, value)` receives each result.  The
-// slice offsets of the block live in shared memory (soff[0..nsl]).
+// slice offsets of the block live in shared memory (soff[0..nsl]).  Products
+// and sums in the compute type of TP (binary32 for half values and inputs).
 template <class TP, class Load, class Store>
 __device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t* soff, const int32_t* __restrict__ col,
                                           const TP* __restrict__ val, Load load, Store store)
 {
+    typedef typename Compute<TP>::T C;
     const int tid = threadIdx.x, BT = blockDim.x, lane = tid & 31;
     constexpr int U = 4;
     for (int64_t base = r0; base < r1; base += 2 * BT) {
@@ -343,7 +352,7 @@ __device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t*
         const int64_t oa = va ? soff[sa] + lane : 0, ob = vb ? soff[sb] + lane : 0;
         const int wa = va ? (int)((soff[sa + 1] - soff[sa]) >> 5) : 0;
         const int wb = vb ? (int)((soff[sb + 1] - soff[sb]) >> 5) : 0;
-        TP acc_a = TP(0), acc_b = TP(0);
+        C acc_a = C(0), acc_b = C(0);
         const int wmax = wa > wb ? wa : wb;
         // software pipeline: the entries of chunk c+1 load while chunk c gathers
         int ca[U], cb[U];
@@ -356,15 +365,15 @@ __device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t*
             xb[u] = u < wb ? __ldg(val + ob + 32 * u) : TP(0);
         }
         for (int c0 = 0; c0 < wmax; c0 += U) {
-            TP ga[U], gb[U];
+            C ga[U], gb[U];
 #pragma unroll
             for (int u = 0; u < U; u++) {
-                ga[u] = ca[u] >= 0 ? (TP)load(ca[u]) : TP(0);
-                gb[u] = cb[u] >= 0 ? (TP)load(cb[u]) : TP(0);
+                ga[u] = ca[u] >= 0 ? (C)load(ca[u]) : C(0);
+                gb[u] = cb[u] >= 0 ? (C)load(cb[u]) : C(0);
             }
-            TP ya[U], yb[U];
+            C ya[U], yb[U];
 #pragma unroll
-            for (int u = 0; u < U; u++) { ya[u] = xa[u]; yb[u] = xb[u]; }
+            for (int u = 0; u < U; u++) { ya[u] = to_c(xa[u]); yb[u] = to_c(xb[u]); }
 #pragma unroll
             for (int u = 0; u < U; u++) {
                 const int c = c0 + U + u;
@@ -384,6 +393,14 @@ __device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t*
     }
 }
 
+// v 2^e, exact (reading R17: the residual scaling of half-precision Krylov
+// parts); the identity when HK is false
+template <bool HK, class T> __device__ __forceinline__ T scale2(T v, int e)
+{
+    if constexpr (HK) return (T)ldexp((double)v, e);
+    else return v;
+}
+
 // Threads per block of the refinement kernel: 1024 when the basis and the
 // preconditioner products are single precision; 512 when either is double,
 // because the 1024-thread build of those spills registers (64 per thread),
@@ -398,9 +415,14 @@ constexpr int ir_threads()
 template <class TU, class TG, class TP, int RM, bool LS>
 __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const int G)
 {
+    // AG, AP: the arithmetic types of u_g and u_p (binary32 for half storage)
+    typedef typename Compute<TG>::T AG;
+    typedef typename Compute<TP>::T AP;
+    // half storage in the Krylov part: the residual is scaled (reading R17)
+    constexpr bool HK = sizeof(TG) == 2 || sizeof(TP) == 2;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ IrShared shs;
-    __shared__ TG redg[33];
+    __shared__ AG redg[33];
     __shared__ double redd[96];
     IrShared* sh = &shs;
     const int kmax = a.kmax;
@@ -432,7 +454,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
     // (step BT); the group's load, the first partial and every round use it
     constexpr int VN = 16 / (int)sizeof(TG);
     constexpr int UV = PF / VN;
-    typedef typename std::conditional<sizeof(TG) == 4, float4, double2>::type TV;
+    typedef typename std::conditional<sizeof(TG) == 8, double2, float4>::type TV;  // 16 bytes
     auto vrow = [&](int u) -> int64_t { return m0 + (int64_t)VN * (tid + u * BT); };
     // the prefetch set of basis vector Vb: out[u VN + e] = Vb[vrow(u) + e] (0 beyond m1)
     auto vload = [&](const TG* Vb, TG* out) {
@@ -504,26 +526,35 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
         if (a.stop_rule != IR_STOP_FIXED && it >= 2 && q >= 0.5 * sh->qprev) { flags |= 16; break; }
         __syncthreads();  // every thread has read sh->qprev and sh->dmax
         if (tid == 0) { sh->qprev = q; sh->dmax = 0.0; }
+        // R17: GMRES takes r 2^-esc with ||r||_inf = m 2^esc, m in [0.5, 1), and the
+        // correction is scaled back (half storage only)
+        int esc = 0;
+        if (HK && rn > 0.0) frexp(rn, &esc);
 
         // ---------------- z = P r (left) or r (right) in u_p, stored in u_g; beta = ||z||
-        TG part = TG(0);
+        AG part = AG(0);
         if (hasP && !rightP) {
-            sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&r[c]); },
-                          [&](int64_t row, TP v) { TG z = (TG)v; ws[row - r0] = z; wbuf[row] = z; part = fma(z, z, part); });
+            sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)scale2<HK>(ldcg(&r[c]), -esc); },
+                          [&](int64_t row, AP v) {
+                              TG z = (TG)(TP)v;
+                              ws[row - r0] = z;
+                              wbuf[row] = z;
+                              part = fma((AG)z, (AG)z, part);
+                          });
         } else {
             for (int64_t row = r0 + tid; row < r1; row += BT) {
-                TG z = (TG)(TP)r[row];
+                TG z = (TG)(TP)scale2<HK>(r[row], -esc);
                 ws[row - r0] = z;
                 wbuf[row] = z;
-                part = fma(z, z, part);
+                part = fma((AG)z, (AG)z, part);
             }
         }
-        TG bsq;
+        AG bsq;
         if (!xsum<true>(a, sh, redg, part, bsq)) return;
-        const TG beta = sqrt(bsq);
+        const AG beta = sqrt(bsq);
         int k = 0;
         if constexpr (LS) {
-        if (beta > TG(0)) {
+        if (beta > AG(0)) {
             // ---- GMRES with MGS in its one-reduction form (inverse compact WY, lagged
             // normalisation; Swirydowicz et al. 2020): one vector reduction per
             // iteration gives Q_j^T u_j, ||u_j||^2, Q_j^T w and u_j^T w for the not yet
@@ -541,19 +572,20 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             // (hc, and yv until the back substitution).
             const int nwp = BT >> 5, lane = tid & 31, wid = tid >> 5;
             const int64_t rbl = r1 - r0;
+            // (rows in u_g; the scalars, partials and T in its arithmetic type)
             TG* wsm = ws + a.rb;                 // w for the block's rows
-            TG* sred = wsm + a.rb;               // 2 (kmax + 1) inner products, summed over blocks
-            TG* hv = sred + 2 * (kmax + 1);      // the right-hand side b, then h (kmax + 1)
-            TG* lrow = hv + (kmax + 1);          // row j of L (kmax + 1)
-            TG* upa = lrow + (kmax + 1);         // unit partials (kmax + 33 each)
-            TG* upc = upa + (kmax + 33);
-            TG* ttri = upc + (kmax + 33);        // rows 0 .. jl-1 of T = (I + L)^{-1}, packed
-            TG* Tg = (TG*)a.L;                   // every row of T, packed (block 0 writes)
-            TG* pv2 = (TG*)a.pvec;               // [value][block] block partials
+            AG* sred = (AG*)(wsm + a.rb);        // 2 (kmax + 1) inner products, summed over blocks
+            AG* hv = sred + 2 * (kmax + 1);      // the right-hand side b, then h (kmax + 1)
+            AG* lrow = hv + (kmax + 1);          // row j of L (kmax + 1)
+            AG* upa = lrow + (kmax + 1);         // unit partials (kmax + 33 each)
+            AG* upc = upa + (kmax + 33);
+            AG* ttri = upc + (kmax + 33);        // rows 0 .. jl-1 of T = (I + L)^{-1}, packed
+            AG* Tg = (AG*)a.L;                   // every row of T, packed (block 0 writes)
+            AG* pv2 = (AG*)a.pvec;               // [value][block] block partials
             double* colb[2] = {hc, yv};          // column c of H (entries 0..c+1) in colb[c & 1]
             auto tri = [](int i) -> int64_t { return (int64_t)i * (i - 1) / 2; };
             // T(i, m) for m < i (row i of T, written in iteration i)
-            auto tget = [&](int i, int m) -> TG { return i < a.jl ? ttri[tri(i) + m] : ldcg(&Tg[tri(i) + m]); };
+            auto tget = [&](int i, int m) -> AG { return i < a.jl ? ttri[tri(i) + m] : ldcg(&Tg[tri(i) + m]); };
             // rotations 0..c-1 and the new rotation c on column c; g, the residual estimate
             // (the entry that rotation q carries to rotation q+1 stays in a register: one
             // dependent FP64 FMA per rotation; the rotated entries go to R from block 0)
@@ -620,14 +652,14 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     if (hasP) {
                         sell_rows<TP>(r0, r1, rightP ? sop : soa, rightP ? a.P.col : a.A.col, rightP ? pv : av,
                                       [&](int c) { return (TP)ldcg(&wbuf[c]); },
-                                      [&](int64_t row, TP v) { tbuf[row] = v; });
+                                      [&](int64_t row, AP v) { tbuf[row] = (TP)v; });
                         if (!xbar(a, sh)) return;
                         sell_rows<TP>(r0, r1, rightP ? soa : sop, rightP ? a.A.col : a.P.col, rightP ? av : pv,
                                       [&](int c) { return ldcg(&tbuf[c]); },
-                                      [&](int64_t row, TP v) { wsm[row - r0] = (TG)v; });
+                                      [&](int64_t row, AP v) { wsm[row - r0] = (TG)(TP)v; });
                     } else {
                         sell_rows<TP>(r0, r1, soa, a.A.col, av, [&](int c) { return (TP)ldcg(&wbuf[c]); },
-                                      [&](int64_t row, TP v) { wsm[row - r0] = (TG)v; });
+                                      [&](int64_t row, AP v) { wsm[row - r0] = (TG)(TP)v; });
                     }
                 }
                 __syncthreads();
@@ -646,7 +678,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         const int i = unit / S, sg = unit - i * S;
                         const int64_t m0 = r0 + sg * segr, m1 = min(r1, m0 + segr);
                         const TG* q = V + (int64_t)i * a.ldv;
-                        TG sa = TG(0), sc = TG(0);
+                        AG sa = AG(0), sc = AG(0);
                         if (i < j) {
 #pragma unroll 4
                             for (int64_t row = m0 + VN * lane; row < m1; row += chunk) {
@@ -660,23 +692,23 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                                     memcpy(we, &w4, sizeof(TV));
 #pragma unroll
                                     for (int e = 0; e < VN; e++) {
-                                        sa = fma(qe[e], ue[e], sa);
-                                        sc = fma(qe[e], we[e], sc);
+                                        sa = fma((AG)qe[e], (AG)ue[e], sa);
+                                        sc = fma((AG)qe[e], (AG)we[e], sc);
                                     }
                                 } else {
                                     for (int e = 0; e < VN && row + e < m1; e++) {
-                                        const TG qv = __ldcg(q + row + e);
-                                        sa = fma(qv, ws[row + e - r0], sa);
-                                        sc = fma(qv, wsm[row + e - r0], sc);
+                                        const AG qv = (AG)ldcg(q + row + e);
+                                        sa = fma(qv, (AG)ws[row + e - r0], sa);
+                                        sc = fma(qv, (AG)wsm[row + e - r0], sc);
                                     }
                                 }
                             }
                         } else {
                             for (int64_t row = m0 + VN * lane; row < m1; row += chunk) {
                                 for (int e = 0; e < VN && row + e < m1; e++) {
-                                    const TG uv = ws[row + e - r0];
+                                    const AG uv = (AG)ws[row + e - r0];
                                     sa = fma(uv, uv, sa);
-                                    sc = fma(uv, wsm[row + e - r0], sc);
+                                    sc = fma(uv, (AG)wsm[row + e - r0], sc);
                                 }
                             }
                         }
@@ -690,9 +722,9 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 // with a rotating block the estimate is read after the exchange round below
                 if (!a.sblock && j >= 2 && sh->resid <= a.tau) { k = j - 1; break; }
                 for (int v = tid; v < 2 * nv; v += BT) {
-                    const TG* src = v < nv ? upa : upc;
+                    const AG* src = v < nv ? upa : upc;
                     const int i = v < nv ? v : v - nv;
-                    TG acc = TG(0);
+                    AG acc = AG(0);
                     for (int sg = 0; sg < S; sg++) acc += src[i * S + sg];
                     pv2[(size_t)v * G + bid] = acc;
                 }
@@ -707,14 +739,14 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     const bool two = v1 < 2 * nv;
                     // every block's partial loaded first (all loads in flight), then summed
                     // in block order as before
-                    TG x0[SPL], x1[SPL];
+                    AG x0[SPL], x1[SPL];
 #pragma unroll
                     for (int q = 0; q < SPL; q++) {
                         const int b = lane + 32 * q;
-                        x0[q] = b < G ? ldcg(&pv2[(size_t)v0 * G + b]) : TG(0);
-                        x1[q] = (two && b < G) ? ldcg(&pv2[(size_t)v1 * G + b]) : TG(0);
+                        x0[q] = b < G ? ldcg(&pv2[(size_t)v0 * G + b]) : AG(0);
+                        x1[q] = (two && b < G) ? ldcg(&pv2[(size_t)v1 * G + b]) : AG(0);
                     }
-                    TG acc0 = TG(0), acc1 = TG(0);
+                    AG acc0 = AG(0), acc1 = AG(0);
 #pragma unroll
                     for (int q = 0; q < SPL; q++) {
                         if (lane + 32 * q < G) {
@@ -730,14 +762,14 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     }
                 }
                 __syncthreads();
-                const TG rr = j == 0 ? beta : sqrt(sred[j]);
+                const AG rr = j == 0 ? beta : sqrt(sred[j]);
                 if (j >= 1 && tid == GT) colb[(j - 1) & 1][j] = (double)rr;  // h_{j,j-1}
-                if (j >= 1 && (rr == TG(0) || !prod)) {
+                if (j >= 1 && (rr == AG(0) || !prod)) {
                     // breakdown or the iteration cap: column j-1 is the last one
                     if (tid == GT && rotates) givens(j - 1);
                     __syncthreads();
                     k = j;
-                    if (rr == TG(0)) flags |= 4;
+                    if (rr == AG(0)) flags |= 4;
                     break;
                 }
                 if (!prod) break;  // kmax = 0
@@ -746,8 +778,8 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 // -l_j^T T (row j of (I + L) T = I), so h = T b is a matrix-vector product (one
                 // warp per entry) instead of a forward substitution; both give MGS's
                 // coefficients.  trow = t_j, hout = h (the unit partials' storage, free here).
-                TG* trow = upa;
-                TG* hout = upc;
+                AG* trow = upa;
+                AG* hout = upc;
                 for (int i = tid; i < j; i += BT) {
                     lrow[i] = sred[i] / rr;
                     hv[i] = sred[nv + i] / rr;
@@ -755,11 +787,11 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 if (tid == 0) hv[j] = (sred[2 * nv - 1] / rr) / rr;
                 __syncthreads();
                 for (int e = wid; e < 2 * j; e += nwp) {
-                    TG acc = TG(0);
+                    AG acc = AG(0);
                     if (e < j) {
                         // t_{j,m} = -sum_{m <= k < j} l_{j,k} T(k, m), T(m, m) = 1
                         const int m = e;
-                        for (int kk = m + lane; kk < j; kk += 32) acc = fma(lrow[kk], kk == m ? TG(1) : tget(kk, m), acc);
+                        for (int kk = m + lane; kk < j; kk += 32) acc = fma(lrow[kk], kk == m ? AG(1) : tget(kk, m), acc);
                         acc = warp_sum(acc);
                         if (lane == 0) {
                             trow[m] = -acc;
@@ -776,7 +808,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 }
                 __syncthreads();
                 if (wid == 0) {
-                    TG acc = TG(0);
+                    AG acc = AG(0);
                     for (int m = lane; m < j; m += 32) acc = fma(trow[m], hv[m], acc);
                     acc = warp_sum(acc);
                     if (lane == 0) hout[j] = hv[j] + acc;
@@ -793,27 +825,29 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 for (int64_t ra = r0 + tid; ra < r1; ra += 2 * BT) {
                     const int64_t rb2 = ra + BT;
                     const bool hb = rb2 < r1;
-                    const TG qa = ws[ra - r0] / rr;
-                    const TG qb = hb ? ws[rb2 - r0] / rr : TG(0);
-                    Vj[ra] = qa;
-                    if (hb) Vj[rb2] = qb;
-                    TG acca = wsm[ra - r0] / rr;
-                    TG accb = hb ? wsm[rb2 - r0] / rr : TG(0);
+                    // q_j as stored (in u_g) is the vector the update subtracts
+                    const TG qsa = (TG)((AG)ws[ra - r0] / rr);
+                    const TG qsb = hb ? (TG)((AG)ws[rb2 - r0] / rr) : TG(0);
+                    Vj[ra] = qsa;
+                    if (hb) Vj[rb2] = qsb;
+                    const AG qa = (AG)qsa, qb = (AG)qsb;
+                    AG acca = (AG)wsm[ra - r0] / rr;
+                    AG accb = hb ? (AG)wsm[rb2 - r0] / rr : AG(0);
                     const int64_t rbx = hb ? rb2 : ra;  // an in-range row for the second load
 #pragma unroll 8
                     for (int i = 0; i < j; i++) {
                         const TG* Vi = V + (int64_t)i * a.ldv;
-                        const TG h = hout[i];
-                        acca = fma(-h, __ldcg(Vi + ra), acca);
-                        accb = fma(-h, __ldcg(Vi + rbx), accb);
+                        const AG h = hout[i];
+                        acca = fma(-h, (AG)ldcg(Vi + ra), acca);
+                        accb = fma(-h, (AG)ldcg(Vi + rbx), accb);
                     }
                     acca = fma(-hout[j], qa, acca);
-                    ws[ra - r0] = acca;
-                    wbuf[ra] = acca;
+                    ws[ra - r0] = (TG)acca;
+                    wbuf[ra] = (TG)acca;
                     if (hb) {
                         accb = fma(-hout[j], qb, accb);
-                        ws[rb2 - r0] = accb;
-                        wbuf[rb2] = accb;
+                        ws[rb2 - r0] = (TG)accb;
+                        wbuf[rb2] = (TG)accb;
                     }
                 }
                 if (!xbar(a, sh)) return;
@@ -1074,7 +1108,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             }
         }
         }
-        if (beta > TG(0)) {
+        if (beta > AG(0)) {
             // ---- y = R^{-1} g (double), d = V y in u_g, x = x + d in u
             if (!xbar(a, sh)) return;  // R columns from block 0 (or the rotating block)
             if (LS && a.sblock)
@@ -1099,22 +1133,22 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             if (rightP) {
                 // right preconditioning: d = P (V_k y), the product in u_p stored in u_g
                 for (int64_t row = r0 + tid; row < r1; row += BT) {
-                    TG dsum = TG(0);
-                    for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
-                    wbuf[row] = dsum;
+                    AG dsum = AG(0);
+                    for (int i = 0; i < k; i++) dsum = fma((AG)V[(int64_t)i * a.ldv + row], (AG)yv[i], dsum);
+                    wbuf[row] = (TG)dsum;
                 }
                 if (!xbar(a, sh)) return;
                 sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&wbuf[c]); },
-                              [&](int64_t row, TP v) {
-                                  const TU du = (TU)(TG)v;
+                              [&](int64_t row, AP v) {
+                                  const TU du = scale2<HK>((TU)(TG)(TP)v, esc);
                                   dmax = fmax(dmax, fabs((double)du));
                                   x[row] = (TU)((TU)x[row] + du);
                               });
             } else {
                 for (int64_t row = r0 + tid; row < r1; row += BT) {
-                    TG dsum = TG(0);
-                    for (int i = 0; i < k; i++) dsum = fma(V[(int64_t)i * a.ldv + row], (TG)yv[i], dsum);
-                    const TU du = (TU)dsum;
+                    AG dsum = AG(0);
+                    for (int i = 0; i < k; i++) dsum = fma((AG)V[(int64_t)i * a.ldv + row], (AG)yv[i], dsum);
+                    const TU du = scale2<HK>((TU)dsum, esc);
                     dmax = fmax(dmax, fabs((double)du));
                     x[row] = (TU)((TU)x[row] + du);
                 }
@@ -1233,6 +1267,16 @@ void ir_kernels_t(int rm, bool ls, IrKernels* k)
     }
 }
 
+// Half Krylov storage (u_g or u_p = half): the one-reduction MGS only; the
+// other forms are not instantiated (k->one stays null).
+template <class TU, class TG, class TP>
+void ir_kernels_ls(int rm, bool ls, IrKernels* k)
+{
+    if (!ls) return;
+    if (rm == 2) ir_kernels_set<TU, TG, TP, 2, true>(k);
+    else ir_kernels_set<TU, TG, TP, 1, true>(k);
+}
+
 // defined one per (u, u_g, u_p) in gmres_ir_k_<u><u_g><u_p>.cu (f single, d double)
 void ir_kernels_fff(int rm, bool ls, IrKernels* k);
 void ir_kernels_ffd(int rm, bool ls, IrKernels* k);
@@ -1242,5 +1286,12 @@ void ir_kernels_dff(int rm, bool ls, IrKernels* k);
 void ir_kernels_dfd(int rm, bool ls, IrKernels* k);
 void ir_kernels_ddf(int rm, bool ls, IrKernels* k);
 void ir_kernels_ddd(int rm, bool ls, IrKernels* k);
+// half (h) u_g and/or u_p: gmres_ir_k_x<u_g><u_p>.cu, both u in one unit
+void ir_kernels_fhh(int rm, bool ls, IrKernels* k);
+void ir_kernels_dhh(int rm, bool ls, IrKernels* k);
+void ir_kernels_fhf(int rm, bool ls, IrKernels* k);
+void ir_kernels_dhf(int rm, bool ls, IrKernels* k);
+void ir_kernels_ffh(int rm, bool ls, IrKernels* k);
+void ir_kernels_dfh(int rm, bool ls, IrKernels* k);
 
 }  // namespace spai

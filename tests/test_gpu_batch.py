@@ -236,6 +236,44 @@ def test_batch_cgs2_and_right_preconditioning(ctx, orth, side):
         Ps[i].free()
 
 
+def test_batch_half_krylov_matches_single_solves(ctx):
+    # u_g = u_p = half (one-reduction MGS) in the batched launch: each system as solved alone
+    As = mixed_systems()[:6]
+    tup = dict(uf="single", u="double", ug="half", up="half", ur="double")
+    io = S.make_ir_opts(tau=1e-2, orth=2, ir_max_steps=30, **tup)
+    so = S.make_spai_opts(init=1, max_fill=30, uf="single")
+    Ps, _ = S.spai_build_batch(ctx, As, so)
+    bs, xts = zip(*[synth.rhs(A, seed=500 + i) for i, A in enumerate(As)])
+    xs = [np.zeros_like(b) for b in bs]
+    sts, status = S.gmres_ir_solve_batch(ctx, As, list(bs), xs, Ps, io)
+    assert all(s_ >= 0 for s_ in status)
+    for i, A in enumerate(As):
+        x1 = np.zeros_like(bs[i])
+        st1 = S.gmres_ir_solve(ctx, A, bs[i], x1, P=Ps[i], opts=io)
+        assert sts[i]["flags"] & 1 and st1["flags"] & 1
+        # the step counts agree, or differ by one at a near-tie of the stop rule (a
+        # half-precision Krylov step contracts the backward error by only ~1e-2)
+        a, b = sts[i]["steps"], st1["steps"]
+        if a != b:
+            m = min(a, b)
+            longer = sts[i]["nbe"] if a > b else st1["nbe"]
+            assert abs(a - b) == 1 and longer[m] <= 10 * O.default_stop_tol(A, "double"), (i, sts[i], st1)
+        m = min(a, b)
+        assert abs(sum(sts[i]["its"][:m]) - sum(st1["its"][:m])) <= max(1, 0.1 * sum(st1["its"][:m]))
+        xb = xs[i]
+        if a > m:  # errors after the same number of steps
+            xb = np.zeros_like(bs[i])
+            S.gmres_ir_solve_batch(ctx, [A], [bs[i]], [xb], [Ps[i]], S.make_ir_opts(
+                tau=1e-2, orth=2, ir_max_steps=m, **tup))
+        elif b > m:
+            x1 = np.zeros_like(bs[i])
+            S.gmres_ir_solve(ctx, A, bs[i], x1, P=Ps[i], opts=S.make_ir_opts(tau=1e-2, orth=2, ir_max_steps=m, **tup))
+        nb_b, fe_b = errors(A, bs[i], xb, xts[i])
+        nb_s, fe_s = errors(A, bs[i], x1, xts[i])
+        assert nb_b <= 10 * max(nb_s, 2.0 ** -53) and fe_b <= 10 * max(fe_s, 2.0 ** -53)
+        Ps[i].free()
+
+
 def test_batch_large_system_runs_alone_and_matches_single_solve(ctx):
     # a system of more than 65536 rows runs on a grid of its own inside the batch, exactly as
     # gmres_ir_solve runs it: the same bits; the small ones beside it run in the shared launch

@@ -590,6 +590,104 @@ def test_ir_one_reduction_mgs_large_grid(ctx, tup):
     check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
 
 
+# ---------------------------------------------------------------- half Krylov storage (u_g, u_p = half)
+
+HALF_KRYLOV_CASES = [
+    # (name, tuple, tau, side, preconditioned); tau ~ sqrt(u_half) where u_g is half
+    ("2d-hh-double-quad", ("single", "double", "half", "half", "quad"), 1e-2, 0, True),
+    ("3d-hh-single", ("half", "single", "half", "half", "double"), 1e-2, 0, True),
+    ("3d-hf-single", ("half", "single", "half", "single", "double"), 1e-2, 0, True),
+    ("3d-fh-single", ("half", "single", "single", "half", "double"), 1e-4, 0, True),
+    ("2d-hh-right", ("single", "double", "half", "half", "quad"), 1e-2, 1, True),
+    ("2d-hh-unpreconditioned", ("single", "double", "half", "half", "quad"), 1e-2, 0, False),
+]
+
+
+def check_ir_steps_near_stop(st_its, st_nbe, ref_its, ref_nbe, stop_tol):
+    """The step counts agree, or differ by one where the stop rule is a near-tie: with
+    half-precision Krylov vectors a refinement step contracts the backward error by only
+    ~1e-2, so when a step lands within a factor 10 of the threshold q u the two sides may
+    stop one step apart.  Returns the common number of steps."""
+    a, b = len(st_its), len(ref_its)
+    if a != b:
+        m = min(a, b)
+        longer = st_nbe if a > b else ref_nbe
+        assert abs(a - b) == 1 and longer[m] <= 10 * stop_tol, (st_its, list(ref_its), st_nbe, list(ref_nbe))
+        a = b = m
+    tg, to = sum(st_its[:a]), sum(ref_its[:a])
+    assert abs(tg - to) <= max(1, 0.1 * to), (st_its, list(ref_its))
+    return a
+
+
+@pytest.mark.parametrize("name,tup,tau,side,precond", HALF_KRYLOV_CASES)
+def test_ir_half_krylov_against_oracle(ctx, name, tup, tau, side, precond):
+    """u_g and/or u_p = half (Krylov vectors and the products' matrix copies stored in
+    half, binary32 arithmetic; one-reduction MGS) against the oracle's MODE_ACC32 Krylov
+    part, both scaling the residual by a power of two (reading R17)."""
+    uf, u, ug, up, ur = tup
+    if u == "single":
+        A, b, x_true = synth.cfg_large_3d(N=16)
+        init, F = O.PAT_A2, 25
+    else:
+        A = synth.conv_diff_2d(40, 20.0, 1.0, 0.1, seed=11)
+        b, x_true = synth.rhs(A, seed=12)
+        init, F = O.PAT_A, 30
+    so = S.make_spai_opts(init=init, max_fill=F, uf=uf, side=side) if precond else None
+    io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=2, side=side, ir_max_steps=30)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    Pr = None
+    if precond and side == 0:
+        Pr = O.assemble_P(O.spai(A, init=init, max_fill=F, uf=uf), up, uf)
+    elif precond:
+        _, Pr = O.spai_right(A, up=up, uf=uf, init=init, max_fill=F)
+    ref = O.gmres_ir(A, b, Pr, uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=O.ORTH_MGS_ICWY, side=side,
+                     kmode=O.MODE_ACC32, imax=30)
+    assert ref["status"] & O.IR_CONVERGED
+    assert st["flags"] & 1
+    m = check_ir_steps_near_stop(st["its"], st["nbe"], ref["its"], ref["nbe"], O.default_stop_tol(A, u))
+    # at a near-tie the side that took one more step is rerun for m steps, so that the
+    # errors compared are those after the same number of steps
+    if st["steps"] > m:
+        io = S.make_ir_opts(uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=2, side=side, ir_max_steps=m)
+        x = np.zeros_like(b)
+        S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    elif ref["steps"] > m:
+        ref = O.gmres_ir(A, b, Pr, uf=uf, u=u, ug=ug, up=up, ur=ur, tau=tau, orth=O.ORTH_MGS_ICWY, side=side,
+                         kmode=O.MODE_ACC32, imax=m)
+    nb_g, fe_g = errors(A, b, x, x_true)
+    nb_o, fe_o = errors(A, b, ref["x"], x_true)
+    uu = O.UNIT_ROUNDOFF[O.prec(u)]
+    assert nb_g <= 10 * max(nb_o, uu) and fe_g <= 10 * max(fe_o, uu)
+
+
+def test_ir_half_krylov_large_grid(ctx):
+    # n = 27^3 = 19683: 77 row blocks and the block that runs the Givens rotations
+    A = synth.conv_diff_3d(27, 50.0, seed=11)
+    b, x_true = synth.rhs(A, seed=12)
+    tup = dict(uf="half", u="single", ug="half", up="half", ur="double")
+    so = S.make_spai_opts(init=O.PAT_A2, max_fill=25, uf="half")
+    io = S.make_ir_opts(tau=1e-2, orth=2, **tup)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, sopts=so, opts=io)
+    ref = O.gmres_ir(A, b, O.assemble_P(O.spai(A, init=O.PAT_A2, max_fill=25, uf="half"), "half", "half"),
+                     tau=1e-2, orth=O.ORTH_MGS_ICWY, kmode=O.MODE_ACC32, **tup)
+    assert st["grid"] >= 64
+    check_ir(A, b, x_true, x, st, ref, 2.0 ** -24)
+
+
+@pytest.mark.parametrize("ug,up,orth", [("half", "half", 0), ("half", "single", 1), ("half", "double", 2),
+                                        ("double", "half", 2)])
+def test_ir_half_krylov_unsupported_forms(ctx, ug, up, orth):
+    # half Krylov storage is built for the one-reduction MGS beside single only
+    A, b, x_true = synth.cfg_small_2d()
+    io = S.make_ir_opts(uf="single", u="double", ug=ug, up=up, ur="quad", tau=1e-2, orth=orth)
+    x = np.zeros_like(b)
+    with pytest.raises(S.SpaiError) as e:
+        S.gmres_ir_solve(ctx, A, b, x, sopts=S.make_spai_opts(init=1, max_fill=30, uf="single"), opts=io)
+    assert e.value.code == S.ERR_UNSUPPORTED
+
+
 # ---------------------------------------------------------------- right preconditioning (reading R14)
 
 
