@@ -895,3 +895,39 @@ def test_half_krylov_acc32_beats_per_operation_half():
         res[km] = np.linalg.norm(z - Pd @ (Ad @ d)) / np.linalg.norm(z)
     assert res[O.MODE_ACC32] < res[O.MODE_PEROP]
     assert res[O.MODE_ACC32] <= 50 * 2.0 ** -11
+
+
+# ---------------------------------------------------------------- Table 1 (golden fixture)
+
+
+def _table1():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "table1_ieee_precisions.txt")
+    rows = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows[line[0]] = (int(line[1]), int(line[2]), int(line[3]))
+    return rows
+
+
+def test_table1_golden_unit_roundoffs_and_ranges():
+    # the oracle's precisions against the values printed in Table 1: unit
+    # roundoff exactly, storage size, and the order of magnitude of the
+    # largest normalised number of the formats it rounds to
+    rows = _table1()
+    assert set(rows) == {"half", "single", "double", "quad"}
+    for name, (bits, rng, ulog2) in rows.items():
+        assert O.UNIT_ROUNDOFF[O.prec(name)] == 2.0 ** ulog2, name
+    for name, dt in (("half", np.float16), ("single", np.float32), ("double", np.float64)):
+        bits, rng, ulog2 = rows[name]
+        fi = np.finfo(dt)
+        assert fi.bits == bits
+        big, tiny = float(fi.max), float(fi.tiny)
+        assert abs(np.log10(big) - rng) <= 1 and abs(np.log10(tiny) + rng) <= 1
+        if name != "double":
+            # the oracle's rounding keeps the largest finite value and overflows past it
+            assert O.round_to(np.array([big]), name)[0] == big
+            assert np.isinf(O.round_to(np.array([big * (1 + 2.0 ** ulog2)]), name)[0])
+            # and the spacing at 1 is 2u
+            assert O.round_to(np.array([1.0 + 2.0 * 2.0 ** ulog2]), name)[0] == 1.0 + 2.0 * 2.0 ** ulog2
