@@ -376,7 +376,8 @@ def extra_workloads(S, synth, torch, dev):
     bd = torch.from_numpy(b).to(dev)
     xd = torch.zeros_like(bd)
     so = S.make_spai_opts(init=2, max_fill=25, uf="half", eps=0.3, side=S.SIDE_RIGHT)
-    io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4, side=S.SIDE_RIGHT)
+    io = S.make_ir_opts(uf="half", u="single", ug="single", up="single", ur="double", tau=1e-4, side=S.SIDE_RIGHT,
+                        orth=ORTH)
     for _ in range(2):
         S.gmres_ir_solve(ctx, Ad, bd, xd, sopts=so, opts=io)
     torch.cuda.synchronize()
@@ -391,7 +392,7 @@ def extra_workloads(S, synth, torch, dev):
     x = xd.cpu().numpy()
     nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
     out["right_64cube"] = dict(workload="the 64^3 workload with the right SPAI (A P ~ I) and right-preconditioned "
-                                        "GMRES; spai_build + solve per step, device inputs",
+                                        "GMRES (one-reduction MGS); spai_build + solve per step, device inputs",
                                solves_per_s=reps / (e0.elapsed_time(e1) / 1000.0), its=st["its"], steps=st["steps"],
                                backward_error=nbe, ms_spai=st["ms_spai"], ms_ir=st["ms_ir"])
     # ---- adaptive
@@ -401,7 +402,8 @@ def extra_workloads(S, synth, torch, dev):
     bd = torch.from_numpy(b).to(dev)
     xd = torch.zeros_like(bd)
     so = S.make_spai_opts(init=0, adaptive=True, eps=0.5, beta=8, max_fill=30, uf="single")
-    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8)
+    io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8, orth=ORTH)
+    io0 = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="quad", tau=1e-8, orth=0)
     P, sst = S.spai_build(ctx, Ad, so)
     P.free()
     P, sst = S.spai_build(ctx, Ad, so)
@@ -410,12 +412,15 @@ def extra_workloads(S, synth, torch, dev):
     x = xd.cpu().numpy()
     Ms = synth.to_scipy(A)
     nbe = float(np.max(np.abs(b - Ms @ x)) / (abs(Ms).sum(axis=1).max() * np.max(np.abs(x)) + np.max(np.abs(b))))
+    st0 = S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io0)  # the textbook MGS rounds, for context
     out["adaptive_100k"] = dict(workload="random nonsymmetric n=100000, 16 nnz/col, scaling 1e6; adaptive "
-                                          "SPAI eps 0.5, beta 8, cap 30, u_f single; (single,double,double,double,quad)",
+                                          "SPAI eps 0.5, beta 8, cap 30, u_f single; (single,double,double,double,quad), "
+                                          "tau 1e-8, one-reduction MGS (ir_ms_mgs_rounds: the textbook MGS)",
                                 spai_ms=sst["ms"], spai_cols_per_s=100_000 / (sst["ms"] / 1000.0),
                                 nnz_P=sst["nnz_P"], cols_converged=sst["cols_converged"],
                                 cols_fillcap=sst["cols_fillcap"], ir_ms=st["ms_ir"], its=st["its"],
-                                steps=st["steps"], backward_error=nbe)
+                                steps=st["steps"], backward_error=nbe, ir_ms_mgs_rounds=st0["ms_ir"],
+                                its_mgs_rounds=st0["its"])
     P.free()
     ctx.close()
     # ---- serving: Poisson streams at 10..2000 requests/s of 3D systems with n log-uniform in
