@@ -38,6 +38,14 @@ sys.path.insert(0, ROOT)
 METRIC = "SPAI-GMRES-IR solves/s (64^3 conv-diff, (half,single,single,single,double))"
 UNIT = "solves/s"
 WORKLOAD = "3D 7-point convection-diffusion 64^3, n=262144, lognormal(0,1) cells, Peclet 50, SPAI pattern(A^2)"
+
+
+def labels(grid):
+    """METRIC and WORKLOAD for a grid^3 run (the defaults at 64^3; other grids only for profiling)."""
+    if grid == 64:
+        return METRIC, WORKLOAD
+    return (METRIC.replace("64^3", "%d^3" % grid),
+            WORKLOAD.replace("64^3, n=262144", "%d^3, n=%d" % (grid, grid ** 3)))
 TUPLE = dict(uf="half", u="single", ug="single", up="single", ur="double")
 FP64 = dict(uf="double", u="double", ug="double", up="double", ur="double")
 TAU = 1e-4
@@ -820,10 +828,10 @@ def main():
     clocks = cs.summary(local)
     if rank == 0:
         line = dict(
-            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+            metric=labels(args.grid)[0], value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=tot_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f16/f32 (u_f half; u, u_g, u_p single; u_r double)", data="synthetic",
-            config=dict(workload=WORKLOAD, n=n, nnz=nnz, nnz_P=int(last["nnz_P"]), tuple=TUPLE, tau=TAU,
+            config=dict(workload=labels(args.grid)[1], n=n, nnz=nnz, nnz_P=int(last["nnz_P"]), tuple=TUPLE, tau=TAU,
                         max_fill=MAX_FILL, orth=ORTH, arnoldi="modified Gram-Schmidt, one-reduction form",
                         l2="flushed between timed steps (256 MiB write)",
                         parallelism="replicas" if world > 1 else "single GPU"),
