@@ -590,6 +590,36 @@ def test_ir_one_reduction_mgs_large_grid(ctx, tup):
     check_ir(A, b, x_true, x, st, ref, O.UNIT_ROUNDOFF[O.prec(u)])
 
 
+@pytest.mark.parametrize("log10_scale", [4.0, 5.0])
+def test_ir_condition_window(ctx, log10_scale):
+    """Random nonsymmetric systems (n = 2000, 12 nonzeros per column) at the upper end of the
+    batched configuration's condition range, in its tuple (single, double, single, single,
+    double) with the one-reduction MGS: at 1-norm condition ~3e4 the refinement converges after
+    GMRES solves of a few hundred iterations, at ~2e5 it leaves the window where GMRES-IR with
+    u_g = u_p = single converges (Section 3.1) and stagnates near 1e-4 (the stop rule's
+    stagnation test).  The GPU follows the oracle in both, on the same preconditioner."""
+    A = synth.random_sparse(2000, 12, seed=21, log10_scale=log10_scale)
+    b, x_true = synth.rhs(A, seed=22)
+    P, _ = S.spai_build(ctx, A, S.make_spai_opts(init=1, max_fill=30, uf="single"))
+    Pc = P.export()
+    kw = dict(uf="single", u="double", ug="single", up="single", ur="double", tau=1e-4)
+    x = np.zeros_like(b)
+    st = S.gmres_ir_solve(ctx, A, b, x, P=P, opts=S.make_ir_opts(orth=2, **kw))
+    Pv = (Pc[0], Pc[1], O.round_to(Pc[2], "single"), O.round_to(Pc[2], "single"))
+    ref = O.gmres_ir(A, b, Pv, orth=O.ORTH_MGS_ICWY, **kw)
+    assert bool(st["flags"] & 16) == bool(ref["status"] & O.IR_STAGNATED)
+    assert bool(st["flags"] & 1) == bool(ref["status"] & O.IR_CONVERGED)
+    if log10_scale >= 5.0:
+        assert ref["status"] & O.IR_STAGNATED and ref["nbe"][-1] > 1e-8
+        assert st["final_nbe"] <= 10 * ref["nbe"][-1] and ref["nbe"][-1] <= 10 * st["final_nbe"]
+        assert st["steps"] == ref["steps"]
+        assert abs(st["total_its"] - ref["total_its"]) <= max(1, 0.1 * ref["total_its"])
+    else:
+        assert max(ref["its"]) >= 200
+        check_ir(A, b, x_true, x, st, ref, 2.0 ** -53)
+    P.free()
+
+
 # ---------------------------------------------------------------- half Krylov storage (u_g, u_p = half)
 
 HALF_KRYLOV_CASES = [
