@@ -109,7 +109,8 @@ inline size_t ir_smem_bytes(int64_t rb, int kmax, int g2, int orth, int jl, int 
         b += (size_t)sg * rb +
              (size_t)ir_scalar_bytes(sg) * (2 * (kmax + 1) + 2 * (kmax + 1) + 2 * (kmax + 1 + 32) +
                                             (size_t)jl * (jl - 1) / 2) +
-             sizeof(int) * (kmax + 2) + 16;  // the unit-count table
+             sizeof(int) * (kmax + 2) + 16 +  // the unit-count table
+             (size_t)ir_scalar_bytes(sg) * IR_THREADS + 16;  // the T row's group partials
     return b;
 }
 
@@ -626,6 +627,8 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             // most kmax + 33 units: the partials' storage).  stab[nv] for nv = 1..kmax+1
             // vectors, made once per solve (32-bit arithmetic; 64-bit division is slow here).
             int* stab = reinterpret_cast<int*>(ttri + (size_t)a.jl * (a.jl - 1) / 2);
+            // partial sums of the T row's column groups (BT values)
+            AG* tpart = reinterpret_cast<AG*>(((uintptr_t)(stab + kmax + 2) + 15) & ~(uintptr_t)15);
             {
                 const int nwu = a.sblock ? nwp : nwp - 1;
                 const int ck = 32 * VN;
@@ -786,27 +789,64 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 }
                 if (tid == 0) hv[j] = (sred[2 * nv - 1] / rr) / rr;
                 __syncthreads();
-                for (int e = wid; e < 2 * j; e += nwp) {
-                    AG acc = AG(0);
-                    if (e < j) {
-                        // t_{j,m} = -sum_{m <= k < j} l_{j,k} T(k, m), T(m, m) = 1
-                        const int m = e;
-                        for (int kk = m + lane; kk < j; kk += 32) acc = fma(lrow[kk], kk == m ? AG(1) : tget(kk, m), acc);
-                        acc = warp_sum(acc);
-                        if (lane == 0) {
-                            trow[m] = -acc;
-                            if (j < a.jl) ttri[tri(j) + m] = -acc;
-                            if (bid == 0) Tg[tri(j) + m] = -acc;
+                // t_{j,m} = -(l_{j,m} + sum_{m < k < j} l_{j,k} T(k, m)) (T(m, m) = 1), column by
+                // column: thread m of group g sums the rows k of the g-th chunk of (m, j), so the
+                // reads T(k, m) of one row k are consecutive over the threads (coalesced from
+                // global memory, where rows jl.. live), UQ of them in flight per thread; the
+                // groups' partials are added in group order.  Beside it, h_i = b_i + sum_{m < i}
+                // T(i, m) b_m for i < j, a warp per row (lanes over m, four loads in flight).
+                if (j > 0) {
+                    const int JP = (j + 31) & ~31;
+                    const int NG = JP <= BT ? min(BT / JP, 8) : 1;
+                    const int kc = (j + NG - 1) / NG;
+                    constexpr int UQ = 8;
+                    for (int t = tid; t < (JP <= BT ? NG * JP : j); t += BT) {
+                        const int m = JP <= BT ? t % JP : t;
+                        const int g = JP <= BT ? t / JP : 0;
+                        AG acc = AG(0);
+                        if (m < j) {
+                            const int kb = max(m + 1, g * kc), ke = min(j, (g + 1) * kc);
+                            int k = kb;
+                            for (; k + UQ <= ke; k += UQ) {
+                                AG tv[UQ];
+#pragma unroll
+                                for (int u = 0; u < UQ; u++) tv[u] = tget(k + u, m);
+#pragma unroll
+                                for (int u = 0; u < UQ; u++) acc = fma(lrow[k + u], tv[u], acc);
+                            }
+                            for (; k < ke; k++) acc = fma(lrow[k], tget(k, m), acc);
                         }
-                    } else {
-                        // h_i = b_i + sum_{m < i} T(i, m) b_m
-                        const int i = e - j;
-                        for (int m = lane; m < i; m += 32) acc = fma(tget(i, m), hv[m], acc);
+                        if (JP <= BT) tpart[t] = acc;
+                        else trow[m] = -(lrow[m] + acc);
+                    }
+                    for (int i = wid; i < j; i += nwp) {
+                        AG acc = AG(0);
+                        int m = lane;
+                        for (; m + 96 < i; m += 128) {
+                            const AG t0 = tget(i, m), t1 = tget(i, m + 32), t2 = tget(i, m + 64), t3 = tget(i, m + 96);
+                            acc = fma(t0, hv[m], acc);
+                            acc = fma(t1, hv[m + 32], acc);
+                            acc = fma(t2, hv[m + 64], acc);
+                            acc = fma(t3, hv[m + 96], acc);
+                        }
+                        for (; m < i; m += 32) acc = fma(tget(i, m), hv[m], acc);
                         acc = warp_sum(acc);
                         if (lane == 0) hout[i] = hv[i] + acc;
                     }
+                    __syncthreads();
+                    if (JP <= BT) {
+                        for (int m = tid; m < j; m += BT) {
+                            AG acc = AG(0);
+                            for (int g = 0; g < NG; g++) acc += tpart[g * JP + m];
+                            trow[m] = -(lrow[m] + acc);
+                        }
+                        __syncthreads();
+                    }
+                    for (int m = tid; m < j; m += BT) {
+                        if (j < a.jl) ttri[tri(j) + m] = trow[m];
+                        if (bid == 0) Tg[tri(j) + m] = trow[m];
+                    }
                 }
-                __syncthreads();
                 if (wid == 0) {
                     AG acc = AG(0);
                     for (int m = lane; m < j; m += 32) acc = fma(trow[m], hv[m], acc);
