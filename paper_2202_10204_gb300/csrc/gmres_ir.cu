@@ -373,7 +373,9 @@ int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
     TRY(dev_alloc((void**)&J.norms, sizeof(unsigned long long) * 5, s));
     CTRY(cudaMemsetAsync(J.norms, 0, sizeof(unsigned long long) * 5, s));
     if (o->orth) {
-        TRY(dev_alloc(&J.pvec, (size_t)ir_scalar_bytes(sg) * 2 * MAX_GRID * (kmax + 1), s));
+        // CGS2: 2 parities x blocks x (kmax + 1) partials; one-reduction MGS: 2 (kmax + 1) values
+        // x blocks, then the 2 (kmax + 1) sums of the split reduction
+        TRY(dev_alloc(&J.pvec, (size_t)ir_scalar_bytes(sg) * (2 * MAX_GRID + (o->orth == 2 ? 2 : 0)) * (kmax + 1), s));
         TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
         CTRY(cudaMemsetAsync(J.gcount, 0, sizeof(unsigned), s));
     }
@@ -1168,7 +1170,7 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     int64_t* poff = P ? (int64_t*)cv.take(sizeof(int64_t) * (nsl + 1)) : nullptr;
     int32_t* pw = P ? (int32_t*)cv.take(sizeof(int32_t) * nsl) : nullptr;
     // CGS2: the partial dot products of every block and the counter of their barrier
-    void* pvec = o->orth ? cv.take((size_t)sg * 2 * MAX_GRID * (kmax + 1)) : nullptr;
+    void* pvec = o->orth ? cv.take((size_t)sg * (2 * MAX_GRID + (o->orth == 2 ? 2 : 0)) * (kmax + 1)) : nullptr;
     void* Lrows = o->orth == 2 ? cv.take((size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1)) : nullptr;
     double* gpub = o->orth == 2 ? (double*)cv.take(sizeof(double) * (kmax + 2)) : nullptr;
     if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)) ||

@@ -35,7 +35,10 @@ constexpr int MAX_GRID = 160;   // exchange slots are polled by one warp, SPL sl
 constexpr int SPL = (MAX_GRID + 31) / 32;
 constexpr int SLOT_WORDS = 16;  // one 128-byte line per block and parity (up to 4 words used)
 constexpr int PF = 4;           // rows per thread whose next basis entries are prefetched
-constexpr int MGS_GROUP_MIN_GRID = 64;  // grids from this size run the Gram-Schmidt rounds in a group
+constexpr int MGS_GROUP_MIN_GRID = 64;
+// one-reduction MGS: from this many partials (2 (j + 1) values x blocks) the sums over blocks are
+// split among the blocks (one more exchange round) instead of every block reading all of them
+constexpr int IR_DIST_MIN = 32768;  // grids from this size run the Gram-Schmidt rounds in a group
 
 // SELL-32: rows in slices of 32; slice s stores its entries column-major
 // (entry c of row 32s+l at off[s] + 32c + l), padded to the slice's longest
@@ -412,8 +415,9 @@ constexpr int ir_threads()
     return (sizeof(TG) == 8 || sizeof(TP) == 8) ? IR_THREADS / 2 : IR_THREADS;
 }
 
-// The refinement of one system by its G blocks; `bid` is this block's rank.
-template <class TU, class TG, class TP, int RM, bool LS>
+// The refinement of one system by its G blocks; `bid` is this block's rank.  BK: inside
+// the batched kernel, whose claim loop holds more registers (fewer loads in flight).
+template <class TU, class TG, class TP, int RM, bool LS, bool BK = false>
 __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const int G)
 {
     // AG, AP: the arithmetic types of u_g and u_p (binary32 for half storage)
@@ -683,26 +687,41 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         const TG* q = V + (int64_t)i * a.ldv;
                         AG sa = AG(0), sc = AG(0);
                         if (i < j) {
-#pragma unroll 4
-                            for (int64_t row = m0 + VN * lane; row < m1; row += chunk) {
-                                if (row + VN <= m1) {
-                                    const TV q4 = __ldcg(reinterpret_cast<const TV*>(q + row));
-                                    const TV u4 = *reinterpret_cast<const TV*>(ws + (row - r0));
-                                    const TV w4 = *reinterpret_cast<const TV*>(wsm + (row - r0));
-                                    TG qe[VN], ue[VN], we[VN];
-                                    memcpy(qe, &q4, sizeof(TV));
-                                    memcpy(ue, &u4, sizeof(TV));
-                                    memcpy(we, &w4, sizeof(TV));
+                            // IQ 16-byte loads of q issued together, then consumed in row order
+                            // (the sums keep the order of a row-by-row loop); rows relative to r0
+                            // (the double build has 128 registers a thread, the others 64)
+                            constexpr int IQ = sizeof(TG) == 8 ? (BK ? 4 : 8) : 2;
+                            constexpr int CK = 32 * VN;
+                            const TG* qb = q + r0;
+                            const int e0 = (int)(m0 - r0), e1 = (int)(m1 - r0);
+                            for (int rq = e0 + VN * lane; rq < e1; rq += IQ * CK) {
+                                TV q4[IQ];
 #pragma unroll
-                                    for (int e = 0; e < VN; e++) {
-                                        sa = fma((AG)qe[e], (AG)ue[e], sa);
-                                        sc = fma((AG)qe[e], (AG)we[e], sc);
-                                    }
-                                } else {
-                                    for (int e = 0; e < VN && row + e < m1; e++) {
-                                        const AG qv = (AG)ldcg(q + row + e);
-                                        sa = fma(qv, (AG)ws[row + e - r0], sa);
-                                        sc = fma(qv, (AG)wsm[row + e - r0], sc);
+                                for (int uu = 0; uu < IQ; uu++) {
+                                    const int row = rq + uu * CK;
+                                    if (row + VN <= e1) q4[uu] = __ldcg(reinterpret_cast<const TV*>(qb + row));
+                                }
+#pragma unroll
+                                for (int uu = 0; uu < IQ; uu++) {
+                                    const int row = rq + uu * CK;
+                                    if (row + VN <= e1) {
+                                        const TV u4 = *reinterpret_cast<const TV*>(ws + row);
+                                        const TV w4 = *reinterpret_cast<const TV*>(wsm + row);
+                                        TG qe[VN], ue[VN], we[VN];
+                                        memcpy(qe, &q4[uu], sizeof(TV));
+                                        memcpy(ue, &u4, sizeof(TV));
+                                        memcpy(we, &w4, sizeof(TV));
+#pragma unroll
+                                        for (int e = 0; e < VN; e++) {
+                                            sa = fma((AG)qe[e], (AG)ue[e], sa);
+                                            sc = fma((AG)qe[e], (AG)we[e], sc);
+                                        }
+                                    } else if (row < e1) {
+                                        for (int e = 0; e < VN && row + e < e1; e++) {
+                                            const AG qv = (AG)ldcg(qb + row + e);
+                                            sa = fma(qv, (AG)ws[row + e], sa);
+                                            sc = fma(qv, (AG)wsm[row + e], sc);
+                                        }
                                     }
                                 }
                             }
@@ -737,34 +756,60 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     k = j - 1;
                     break;
                 }
-                for (int v0 = wid; v0 < 2 * nv; v0 += 2 * nwp) {
-                    const int v1 = v0 + nwp;
-                    const bool two = v1 < 2 * nv;
-                    // every block's partial loaded first (all loads in flight), then summed
-                    // in block order as before
-                    AG x0[SPL], x1[SPL];
+                // the sums over blocks of the 2 nv partials, each in the same order (lanes over
+                // blocks, then the warp's tree): every block sums them all, or, when that
+                // would read many partials (2 nv G >= IR_DIST_MIN), block b sums the values
+                // b, b + G, ... and publishes them for one more exchange round
+                if (2 * nv * G < IR_DIST_MIN) {
+                    for (int v0 = wid; v0 < 2 * nv; v0 += 2 * nwp) {
+                        const int v1 = v0 + nwp;
+                        const bool two = v1 < 2 * nv;
+                        // every block's partial loaded first (all loads in flight), then summed
+                        // in block order as before
+                        AG x0[SPL], x1[SPL];
 #pragma unroll
-                    for (int q = 0; q < SPL; q++) {
-                        const int b = lane + 32 * q;
-                        x0[q] = b < G ? ldcg(&pv2[(size_t)v0 * G + b]) : AG(0);
-                        x1[q] = (two && b < G) ? ldcg(&pv2[(size_t)v1 * G + b]) : AG(0);
-                    }
-                    AG acc0 = AG(0), acc1 = AG(0);
+                        for (int q = 0; q < SPL; q++) {
+                            const int b = lane + 32 * q;
+                            x0[q] = b < G ? ldcg(&pv2[(size_t)v0 * G + b]) : AG(0);
+                            x1[q] = (two && b < G) ? ldcg(&pv2[(size_t)v1 * G + b]) : AG(0);
+                        }
+                        AG acc0 = AG(0), acc1 = AG(0);
 #pragma unroll
-                    for (int q = 0; q < SPL; q++) {
-                        if (lane + 32 * q < G) {
-                            acc0 += x0[q];
-                            acc1 += x1[q];
+                        for (int q = 0; q < SPL; q++) {
+                            if (lane + 32 * q < G) {
+                                acc0 += x0[q];
+                                acc1 += x1[q];
+                            }
+                        }
+                        acc0 = warp_sum(acc0);
+                        acc1 = warp_sum(acc1);
+                        if (lane == 0) {
+                            sred[v0] = acc0;
+                            if (two) sred[v1] = acc1;
                         }
                     }
-                    acc0 = warp_sum(acc0);
-                    acc1 = warp_sum(acc1);
-                    if (lane == 0) {
-                        sred[v0] = acc0;
-                        if (two) sred[v1] = acc1;
+                    __syncthreads();
+                } else {
+                    AG* tot = (AG*)a.pvec + (size_t)2 * MAX_GRID * (kmax + 1);
+                    for (int t = wid; bid + t * G < 2 * nv; t += nwp) {
+                        const int v0 = bid + t * G;
+                        AG x0[SPL];
+#pragma unroll
+                        for (int q = 0; q < SPL; q++) {
+                            const int b = lane + 32 * q;
+                            x0[q] = b < G ? ldcg(&pv2[(size_t)v0 * G + b]) : AG(0);
+                        }
+                        AG acc0 = AG(0);
+#pragma unroll
+                        for (int q = 0; q < SPL; q++)
+                            if (lane + 32 * q < G) acc0 += x0[q];
+                        acc0 = warp_sum(acc0);
+                        if (lane == 0) tot[v0] = acc0;
                     }
+                    if (!xbar(a, sh)) return;
+                    for (int v = tid; v < 2 * nv; v += BT) sred[v] = ldcg(&tot[v]);
+                    __syncthreads();
                 }
-                __syncthreads();
                 const AG rr = j == 0 ? beta : sqrt(sred[j]);
                 if (j >= 1 && tid == GT) colb[(j - 1) & 1][j] = (double)rr;  // h_{j,j-1}
                 if (j >= 1 && (rr == AG(0) || !prod)) {
@@ -1274,7 +1319,7 @@ __global__ void __launch_bounds__(ir_threads<TG, TP>(), 1) k_ir_batch(const IrAr
         __syncthreads();
         if (sys < 0) return;
         const int G = args[sys].G;  // T, or a smaller class's team size
-        if (rank < G) ir_body<TU, TG, TP, RM, LS>(args[sys], rank, G);
+        if (rank < G) ir_body<TU, TG, TP, RM, LS, true>(args[sys], rank, G);
         __syncthreads();
     }
 }
