@@ -405,14 +405,16 @@ template <bool HK, class T> __device__ __forceinline__ T scale2(T v, int e)
     else return v;
 }
 
-// Threads per block of the refinement kernel: 1024 when the basis and the
-// preconditioner products are single precision; 512 when either is double,
-// because the 1024-thread build of those spills registers (64 per thread),
+// Threads per block of the refinement kernel: 896 (72 registers a thread)
+// when the basis and the preconditioner products are single or half
+// precision, which lets the one-reduction inner products keep four basis
+// loads in flight per lane (1024 threads at 64 registers kept two); 512 when
+// either is double, because the larger builds of those spill registers,
 // which puts the basis prefetch behind HBM latency every Gram-Schmidt round.
 template <class TG, class TP>
 constexpr int ir_threads()
 {
-    return (sizeof(TG) == 8 || sizeof(TP) == 8) ? IR_THREADS / 2 : IR_THREADS;
+    return (sizeof(TG) == 8 || sizeof(TP) == 8) ? IR_THREADS / 2 : 896;
 }
 
 // The refinement of one system by its G blocks; `bid` is this block's rank.  BK: inside
@@ -690,7 +692,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                             // IQ 16-byte loads of q issued together, then consumed in row order
                             // (the sums keep the order of a row-by-row loop); rows relative to r0
                             // (the double build has 128 registers a thread, the others 64)
-                            constexpr int IQ = sizeof(TG) == 8 ? (BK ? 4 : 8) : 2;
+                            constexpr int IQ = sizeof(TG) == 8 ? (BK ? 4 : 8) : (BK ? 2 : 4);
                             constexpr int CK = 32 * VN;
                             const TG* qb = q + r0;
                             const int e0 = (int)(m0 - r0), e1 = (int)(m1 - r0);
