@@ -299,6 +299,7 @@ struct IrJob {
     unsigned* gcount = nullptr;
     void* L = nullptr;
     double* gpub = nullptr;
+    void* arena = nullptr;  // one allocation holding all of the above
     SellMat As;
     const SellMat* Ps = nullptr;
     unsigned long long h_norms[3] = {0, 0, 0};
@@ -349,47 +350,64 @@ int ir_job_kmax(int64_t n, const ir_opts* o, int* kmax)
     return 0;
 }
 
-// The job's buffers (allocated and cleared on s).
+// The job's buffers, carved from one allocation on s (one runtime call instead
+// of one per buffer: a batch prepares hundreds of jobs); the control words
+// (norms, exchange slots, step counts, flags, counters) come first and are
+// cleared together.
 int ir_job_alloc(IrJob& J, cudaStream_t s, const ir_opts* o)
 {
-#define TRY(x) do { int rc_ = (x); if (rc_) return rc_; } while (0)
-#define CTRY(x) do { if ((x) != cudaSuccess) return SPAI_ERR_CUDA; } while (0)
     const int64_t n = J.n;
     const int su = prec_bytes(o->u), sg = prec_bytes(o->ug), sp = prec_bytes(o->up);
     const int64_t ldv = (n + 31) & ~int64_t(31);
     const int kmax = J.kmax, imax = J.imax;
-    TRY(dev_alloc(&J.x, (size_t)su * n, s));
-    TRY(dev_alloc(&J.r, (size_t)su * n, s));
-    TRY(dev_alloc(&J.wbuf, (size_t)sg * n, s));
-    TRY(dev_alloc(&J.tbuf, (size_t)sp * n, s));
-    TRY(dev_alloc(&J.V, (size_t)sg * ldv * (kmax + 1), s));
-    TRY(dev_alloc((void**)&J.R, sizeof(double) * (size_t)(kmax + 1) * kmax, s));
-    TRY(dev_alloc((void**)&J.msg, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
-    TRY(dev_alloc((void**)&J.nbe, sizeof(double) * (imax + 1), s));
-    TRY(dev_alloc((void**)&J.its, sizeof(int) * (imax + 1), s));
-    TRY(dev_alloc((void**)&J.outv, sizeof(int) * 2, s));
-    TRY(dev_alloc((void**)&J.err, sizeof(int) * 2, s));
+    size_t off = 0;
+    auto place = [&](size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        const size_t at = off;
+        off += bytes;
+        return at;
+    };
     // [0..2] the norms and the longest row, [3] [4] SELL entry counts of A and P
-    TRY(dev_alloc((void**)&J.norms, sizeof(unsigned long long) * 5, s));
-    CTRY(cudaMemsetAsync(J.norms, 0, sizeof(unsigned long long) * 5, s));
-    if (o->orth) {
-        // CGS2: 2 parities x blocks x (kmax + 1) partials; one-reduction MGS: 2 (kmax + 1) values
-        // x blocks, then the 2 (kmax + 1) sums of the split reduction
-        TRY(dev_alloc(&J.pvec, (size_t)ir_scalar_bytes(sg) * (2 * MAX_GRID + (o->orth == 2 ? 2 : 0)) * (kmax + 1), s));
-        TRY(dev_alloc((void**)&J.gcount, sizeof(unsigned), s));
-        CTRY(cudaMemsetAsync(J.gcount, 0, sizeof(unsigned), s));
-    }
-    if (o->orth == 2) {
-        TRY(dev_alloc(&J.L, (size_t)ir_scalar_bytes(sg) * ((size_t)(kmax + 1) * kmax / 2 + 1), s));
-        TRY(dev_alloc((void**)&J.gpub, sizeof(double) * (kmax + 2), s));
-    }
-    CTRY(cudaMemsetAsync(J.its, 0, sizeof(int) * (imax + 1), s));
-    CTRY(cudaMemsetAsync(J.outv, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(J.err, 0, sizeof(int) * 2, s));
-    CTRY(cudaMemsetAsync(J.msg, 0, sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS, s));
+    const size_t o_norms = place(sizeof(unsigned long long) * 5);
+    const size_t o_msg = place(sizeof(unsigned long long) * 4 * MAX_GRID * SLOT_WORDS);
+    const size_t o_its = place(sizeof(int) * (imax + 1));
+    const size_t o_outv = place(sizeof(int) * 2);
+    const size_t o_err = place(sizeof(int) * 2);
+    const size_t o_gcount = o->orth ? place(sizeof(unsigned)) : 0;
+    const size_t ctrl = off;
+    const size_t o_x = place((size_t)su * n);
+    const size_t o_r = place((size_t)su * n);
+    const size_t o_wbuf = place((size_t)sg * n);
+    const size_t o_tbuf = place((size_t)sp * n);
+    const size_t o_V = place((size_t)sg * ldv * (kmax + 1));
+    const size_t o_R = place(sizeof(double) * (size_t)(kmax + 1) * kmax);
+    const size_t o_nbe = place(sizeof(double) * (imax + 1));
+    // CGS2: 2 parities x blocks x (kmax + 1) partials; one-reduction MGS: 2 (kmax + 1) values
+    // x blocks, then the 2 (kmax + 1) sums of the split reduction
+    const size_t o_pvec = o->orth ? place((size_t)ir_scalar_bytes(sg) * (2 * MAX_GRID + (o->orth == 2 ? 2 : 0)) * (kmax + 1)) : 0;
+    const size_t o_L = o->orth == 2 ? place((size_t)ir_scalar_bytes(sg) * ((size_t)(kmax + 1) * kmax / 2 + 1)) : 0;
+    const size_t o_gpub = o->orth == 2 ? place(sizeof(double) * (kmax + 2)) : 0;
+    int rc = dev_alloc(&J.arena, off, s);
+    if (rc) return rc;
+    unsigned char* base = (unsigned char*)J.arena;
+    J.norms = (unsigned long long*)(base + o_norms);
+    J.msg = (unsigned long long*)(base + o_msg);
+    J.its = (int*)(base + o_its);
+    J.outv = (int*)(base + o_outv);
+    J.err = (int*)(base + o_err);
+    J.gcount = o->orth ? (unsigned*)(base + o_gcount) : nullptr;
+    J.x = base + o_x;
+    J.r = base + o_r;
+    J.wbuf = base + o_wbuf;
+    J.tbuf = base + o_tbuf;
+    J.V = base + o_V;
+    J.R = (double*)(base + o_R);
+    J.nbe = (double*)(base + o_nbe);
+    J.pvec = o->orth ? base + o_pvec : nullptr;
+    J.L = o->orth == 2 ? base + o_L : nullptr;
+    J.gpub = o->orth == 2 ? (double*)(base + o_gpub) : nullptr;
+    if (cudaMemsetAsync(base, 0, ctrl, s) != cudaSuccess) return SPAI_ERR_CUDA;
     return 0;
-#undef TRY
-#undef CTRY
 }
 
 // ||A||_inf, ||b||_inf, the longest row into J.norms, and x0 = P b in u_f
@@ -536,10 +554,8 @@ int ir_job_result(const IrJob& J, const ir_opts* o, ir_stats* st)
 void ir_job_free(IrJob& J, cudaStream_t s)
 {
     sell_free(&J.As, s);
-    dev_free(J.x, s); dev_free(J.r, s); dev_free(J.wbuf, s); dev_free(J.tbuf, s); dev_free(J.V, s);
-    dev_free(J.R, s); dev_free(J.msg, s); dev_free(J.nbe, s); dev_free(J.its, s); dev_free(J.outv, s);
-    dev_free(J.err, s); dev_free(J.norms, s); dev_free(J.pvec, s); dev_free(J.gcount, s); dev_free(J.L, s);
-    dev_free(J.gpub, s);
+    dev_free(J.arena, s);
+    J.arena = nullptr;
     J.gpub = nullptr;
     J.x = J.r = J.wbuf = J.tbuf = J.V = J.pvec = J.L = nullptr;
     J.R = J.nbe = nullptr;
