@@ -35,10 +35,10 @@ constexpr int MAX_GRID = 160;   // exchange slots are polled by one warp, SPL sl
 constexpr int SPL = (MAX_GRID + 31) / 32;
 constexpr int SLOT_WORDS = 16;  // one 128-byte line per block and parity (up to 4 words used)
 constexpr int PF = 4;           // rows per thread whose next basis entries are prefetched
-constexpr int MGS_GROUP_MIN_GRID = 64;
+constexpr int MGS_GROUP_MIN_GRID = 64;  // grids from this size run the Gram-Schmidt rounds in a group
 // one-reduction MGS: from this many partials (2 (j + 1) values x blocks) the sums over blocks are
 // split among the blocks (one more exchange round) instead of every block reading all of them
-constexpr int IR_DIST_MIN = 32768;  // grids from this size run the Gram-Schmidt rounds in a group
+constexpr int IR_DIST_MIN = 32768;
 
 // SELL-32: rows in slices of 32; slice s stores its entries column-major
 // (entry c of row 32s+l at off[s] + 32c + l), padded to the slice's longest
@@ -691,7 +691,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         if (i < j) {
                             // IQ 16-byte loads of q issued together, then consumed in row order
                             // (the sums keep the order of a row-by-row loop); rows relative to r0
-                            // (the double build has 128 registers a thread, the others 64)
+                            // (the double build has 128 registers a thread, the others 72)
                             constexpr int IQ = sizeof(TG) == 8 ? (BK ? 4 : 8) : (BK ? 2 : 4);
                             constexpr int CK = 32 * VN;
                             const TG* qb = q + r0;
