@@ -200,7 +200,7 @@ def test_adaptive_ill_conditioned_refinement():
     u_f single) and the refinement with (single, double, double, double, quad),
     whose GMRES solves run to their 500-iteration cap.  Against the oracle: the
     patterns up to near-ties of rho, and the refinement's steps, iterations and
-    errors (modified Gram-Schmidt, the paper's method)."""
+    errors (modified Gram-Schmidt, the paper's method, and its one-reduction form)."""
     c = S.Context(0)
     A = synth.random_sparse(10000, 16, seed=6, log10_scale=6.0)
     b, x_true = synth.rhs(A, seed=7)
@@ -220,6 +220,13 @@ def test_adaptive_ill_conditioned_refinement():
     ref = O.gmres_ir(A, b, Pv, **kw)
     assert max(ref["its"]) >= 300
     check_ir_against_oracle(A, b, x_true, x, r, ref, 2.0 ** -53)
+    # the one-reduction MGS on the same system: its GMRES solves run long enough that the
+    # sums over blocks are split among the blocks (2 (j + 1) partials x blocks >= 32768)
+    x2 = np.zeros_like(b)
+    r2 = S.gmres_ir_solve(c, A, b, x2, P=P, opts=S.make_ir_opts(orth=2, **kw))
+    assert 2 * (max(r2["its"]) + 1) * r2["grid"] >= 32768, (r2["its"], r2["grid"])
+    ref2 = O.gmres_ir(A, b, Pv, orth=O.ORTH_MGS_ICWY, **kw)
+    check_ir_against_oracle(A, b, x_true, x2, r2, ref2, 2.0 ** -53)
     P.free()
     c.close()
 
