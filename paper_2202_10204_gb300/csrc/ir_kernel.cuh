@@ -767,7 +767,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                         const int v1 = v0 + nwp;
                         const bool two = v1 < 2 * nv;
                         // every block's partial loaded first (all loads in flight), then summed
-                        // in block order as before
+                        // in block order
                         AG x0[SPL], x1[SPL];
 #pragma unroll
                         for (int q = 0; q < SPL; q++) {
