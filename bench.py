@@ -67,9 +67,10 @@ def parse():
     p.add_argument("--sweep", action="store_true",
                    help="instead of the bench line: the eps trade-off of adaptive SPAI against fixed patterns "
                         "and no preconditioner (one JSON line)")
-    p.add_argument("--case", default=None, choices=["batched_spai"],
+    p.add_argument("--case", default=None, choices=["batched_spai", "half_krylov"],
                    help="instead of the bench line, one run of a single case for profiling: batched_spai = "
-                        "two spai_build_batch calls on the 512 systems of the batched line, the first tuning (one JSON line)")
+                        "two spai_build_batch calls on the 512 systems of the batched line, the first tuning; "
+                        "half_krylov = three solves of the grid^3 system with u_g = u_p = half (one JSON line)")
     return p.parse_args()
 
 
@@ -97,6 +98,29 @@ def run_case(args):
     """One run of a single case (for ncu), printing one JSON line."""
     import paper_2202_10204_gb300 as S
     from paper_2202_10204_gb300 import synth
+    if args.case == "half_krylov":
+        import torch
+        A, b, x_true = synth.cfg_large_3d(N=args.grid)
+        ctx = S.Context(0)
+        dev = torch.device("cuda:0")
+        Ad = tuple(torch.from_numpy(a).to(dev) for a in A)
+        bd = torch.from_numpy(b).to(dev)
+        so = S.make_spai_opts(init=2, max_fill=MAX_FILL, uf=TUPLE["uf"], eps=0.3)
+        io = S.make_ir_opts(tau=1e-2, orth=2, ir_max_steps=30, **dict(TUPLE, ug="half", up="half"))
+        P, _ = S.spai_build(ctx, Ad, so)
+        sts = []
+        for _ in range(3):
+            xd = torch.zeros_like(bd)
+            sts.append(S.gmres_ir_solve(ctx, Ad, bd, xd, P=P, opts=io))
+        torch.cuda.synchronize()
+        n, nnz = len(b), len(A[1])
+        out = dict(case=args.case, n=n, its=sts[-1]["its"], steps=sts[-1]["steps"],
+                   ms_kernel=[s_["ms_kernel"] for s_ in sts],
+                   algorithmic_bytes=ir_kernel_bytes(n, nnz, sts[-1]["nnz_P"], sts[-1]["its"], s_u=4, s_g=2, s_p=2))
+        P.free()
+        ctx.close()
+        print(json.dumps(out))
+        return 0
     if args.case == "batched_spai":
         batch = batched_512_systems(synth)
         ctx = S.Context(0)
