@@ -604,10 +604,15 @@ static void residual_ur(int n, const int64_t* rp, const int* ci, const double* a
     }
 }
 
+/* ||x||_inf; a NaN entry makes it infinite (a non-finite iterate or residual
+ * must not pass for a small one in the stopping rule) */
 static double norm_inf(int n, const double* x)
 {
     double m = 0.0;
-    for (int i = 0; i < n; i++) if (fabs(x[i]) > m) m = fabs(x[i]);
+    for (int i = 0; i < n; i++) {
+        if (isnan(x[i])) return INFINITY;
+        if (fabs(x[i]) > m) m = fabs(x[i]);
+    }
     return m;
 }
 

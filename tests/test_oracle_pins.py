@@ -931,3 +931,14 @@ def test_table1_golden_unit_roundoffs_and_ranges():
             assert np.isinf(O.round_to(np.array([big * (1 + 2.0 ** ulog2)]), name)[0])
             # and the spacing at 1 is 2u
             assert O.round_to(np.array([1.0 + 2.0 * 2.0 ** ulog2]), name)[0] == 1.0 + 2.0 * 2.0 ** ulog2
+
+
+def test_ir_non_finite_iterate_is_reported():
+    # A's half copy overflows (1e6 > 65504): the products are non-finite, so is the
+    # correction, and the refinement must stop with the non-finite status instead of
+    # taking a NaN residual for a zero one
+    Ab = synth._to_csr(sp.diags(np.full(40, 1e6)) + sp.eye(40, k=1))
+    P = O.assemble_P(O.spai(Ab, init=O.PAT_IDENTITY, max_fill=4, uf="single"), "half", "single")
+    R = O.gmres_ir(Ab, np.ones(40), P, uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2,
+                   orth=O.ORTH_MGS_ICWY, kmode=O.MODE_ACC32, imax=30)
+    assert R["status"] & O.IR_NONFINITE and not R["status"] & O.IR_CONVERGED
