@@ -397,6 +397,10 @@ __device__ __forceinline__ void sell_rows(int64_t r0, int64_t r1, const int64_t*
     }
 }
 
+// max(m, |v|) with a NaN taken as infinite: fmax drops NaNs, and a non-finite
+// residual or iterate must not pass for a small one in the stopping rule
+__device__ __forceinline__ double max_abs(double m, double v) { return v != v ? INFINITY : fmax(m, fabs(v)); }
+
 // v 2^e, exact (reading R17: the residual scaling of half-precision Krylov
 // parts); the identity when HK is false
 template <bool HK, class T> __device__ __forceinline__ T scale2(T v, int e)
@@ -515,8 +519,8 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
             }
             TU rv = (TU)(hi + lo);
             r[row] = rv;
-            rmax = fmax(rmax, fabs((double)rv));
-            xmax = fmax(xmax, fabs((double)x[row]));
+            rmax = max_abs(rmax, (double)rv);
+            xmax = max_abs(xmax, (double)x[row]);
         }
         double mx[3];
         if (!xmax3(a, sh, redd, {rmax, xmax, sh->dmax}, mx)) return;
@@ -1228,7 +1232,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                 sell_rows<TP>(r0, r1, sop, a.P.col, pv, [&](int c) { return (TP)ldcg(&wbuf[c]); },
                               [&](int64_t row, AP v) {
                                   const TU du = scale2<HK>((TU)(TG)(TP)v, esc);
-                                  dmax = fmax(dmax, fabs((double)du));
+                                  dmax = max_abs(dmax, (double)du);
                                   x[row] = (TU)((TU)x[row] + du);
                               });
             } else {
@@ -1236,7 +1240,7 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     AG dsum = AG(0);
                     for (int i = 0; i < k; i++) dsum = fma((AG)V[(int64_t)i * a.ldv + row], (AG)yv[i], dsum);
                     const TU du = scale2<HK>((TU)dsum, esc);
-                    dmax = fmax(dmax, fabs((double)du));
+                    dmax = max_abs(dmax, (double)du);
                     x[row] = (TU)((TU)x[row] + du);
                 }
             }

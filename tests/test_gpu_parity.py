@@ -489,6 +489,45 @@ def test_edge_cases(ctx):
     assert e.value.code == -8
 
 
+def test_half_krylov_edge_cases(ctx):
+    # u_g = u_p = half (one-reduction MGS): n = 1, a diagonal system, a zero right-hand side,
+    # a ragged tiny system, and values beyond half's range (a clean non-finite status)
+    io = S.make_ir_opts(uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2, orth=2,
+                        ir_max_steps=30)
+    so = S.make_spai_opts(init=0, max_fill=4, uf="single")
+    A1 = (np.array([0, 1], dtype=np.int64), np.array([0], dtype=np.int32), np.array([4.0]))
+    x = np.zeros(1)
+    S.gmres_ir_solve(ctx, A1, np.array([2.0]), x, sopts=so, opts=io)
+    assert x[0] == 0.5
+    a = np.array([2.0, -3.0, 0.5, 7.0, -0.25])
+    Ad = synth._to_csr(sp.diags(a))
+    b = np.arange(1.0, 6.0)
+    x = np.zeros(5)
+    st = S.gmres_ir_solve(ctx, Ad, b, x, sopts=so, opts=io)
+    np.testing.assert_allclose(x, b / a, rtol=1e-15)
+    assert st["flags"] & 1
+    A, b, x_true = synth.cfg_small_2d()
+    x = np.ones_like(b)
+    st = S.gmres_ir_solve(ctx, A, np.zeros_like(b), x, sopts=S.make_spai_opts(init=1, max_fill=30), opts=io)
+    assert np.all(x == 0) and st["steps"] == 0
+    # ragged: n = 37 (one full 32-row slice and a partial one)
+    Ar = synth.conv_diff_2d(7, 5.0, 1.0, 0.1, seed=3)
+    Ar = synth._to_csr(synth.to_scipy(Ar)[:37, :37] + sp.eye(37))
+    br, xr = synth.rhs(Ar, seed=4)
+    x = np.zeros_like(br)
+    st = S.gmres_ir_solve(ctx, Ar, br, x, sopts=S.make_spai_opts(init=1, max_fill=30), opts=io)
+    ref = O.gmres_ir(Ar, br, O.assemble_P(O.spai(Ar, init=O.PAT_A, max_fill=30, uf="single"), "half", "single"),
+                     uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2, orth=O.ORTH_MGS_ICWY,
+                     kmode=O.MODE_ACC32, imax=30)
+    assert st["flags"] & 1 and ref["status"] & O.IR_CONVERGED
+    assert np.max(np.abs(x - xr)) <= 10 * max(np.max(np.abs(ref["x"] - xr)), 2.0 ** -53) * np.max(np.abs(xr)) + 1e-14
+    # A's half copy overflows: the solve reports a non-finite result instead of a number
+    Ab = synth._to_csr(sp.diags(np.full(40, 1e6)) + sp.eye(40, k=1))
+    with pytest.raises(S.SpaiError) as e:
+        S.gmres_ir_solve(ctx, Ab, np.ones(40), np.zeros(40), sopts=so, opts=io)
+    assert e.value.code == -3  # SPAI_ERR_NONFINITE
+
+
 def test_precond_outlives_its_context():
     # a preconditioner stays usable after the context that built it is destroyed
     A, b, _ = synth.cfg_small_2d()
