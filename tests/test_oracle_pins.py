@@ -942,3 +942,20 @@ def test_ir_non_finite_iterate_is_reported():
     R = O.gmres_ir(Ab, np.ones(40), P, uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2,
                    orth=O.ORTH_MGS_ICWY, kmode=O.MODE_ACC32, imax=30)
     assert R["status"] & O.IR_NONFINITE and not R["status"] & O.IR_CONVERGED
+
+
+@pytest.mark.parametrize("e", [40, -40])
+def test_half_krylov_refinement_is_scale_invariant(e):
+    # binary floating point is invariant under power-of-two scaling while nothing over- or
+    # underflows; with the residual scaled into [0.5, 1) before the half-precision Krylov
+    # part (reading R17), b 2^e gives x 2^e bit for bit even where b 2^e alone would fall
+    # outside half's range
+    A, b, x_true = synth.cfg_small_2d()
+    P = O.assemble_P(O.spai(A, init=O.PAT_A, uf="single", max_fill=30), "half", "single")
+    kw = dict(uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2, orth=O.ORTH_MGS_ICWY,
+              kmode=O.MODE_ACC32, imax=30)
+    R0 = O.gmres_ir(A, b, P, **kw)
+    R1 = O.gmres_ir(A, np.ldexp(b, e), P, **kw)
+    assert R0["status"] & O.IR_CONVERGED and R1["status"] & O.IR_CONVERGED
+    assert list(R0["its"]) == list(R1["its"])
+    assert np.array_equal(np.ldexp(R0["x"], e), R1["x"])
