@@ -527,6 +527,22 @@ def test_half_krylov_edge_cases(ctx):
     assert e.value.code == -3  # SPAI_ERR_NONFINITE
 
 
+@pytest.mark.parametrize("e", [40, -40])
+def test_half_krylov_scale_invariance(ctx, e):
+    # with the residual scaled into [0.5, 1) before the half-precision Krylov part (reading
+    # R17), b 2^e gives x 2^e bit for bit, although b 2^e lies outside half's range
+    A, b, x_true = synth.cfg_small_2d()
+    P, _ = S.spai_build(ctx, A, S.make_spai_opts(init=1, max_fill=30, uf="single"))
+    io = S.make_ir_opts(uf="single", u="double", ug="half", up="half", ur="quad", tau=1e-2, orth=2,
+                        ir_max_steps=30)
+    x0, x1 = np.zeros_like(b), np.zeros_like(b)
+    s0 = S.gmres_ir_solve(ctx, A, b, x0, P=P, opts=io)
+    s1 = S.gmres_ir_solve(ctx, A, np.ldexp(b, e), x1, P=P, opts=io)
+    assert s0["flags"] & 1 and s1["flags"] & 1 and s0["its"] == s1["its"]
+    assert np.array_equal(np.ldexp(x0, e), x1)
+    P.free()
+
+
 def test_precond_outlives_its_context():
     # a preconditioner stays usable after the context that built it is destroyed
     A, b, _ = synth.cfg_small_2d()
