@@ -295,6 +295,9 @@ int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_o
  * and returns the request's own status. */
 int solver_poll(spai_ctx ctx, uint64_t ticket, double* x, ir_stats* st);
 
+/* A static description of a status code; for SPAI_ERR_CUDA it names the last CUDA
+ * error the library saw on the calling thread (a thread-local string, valid until
+ * the thread's next call). */
 const char* spai_strerror(int code);
 
 /* Self-test of the bounded device-side waits (no counterpart in the paper).

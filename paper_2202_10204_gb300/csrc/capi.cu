@@ -1215,11 +1215,17 @@ const char* spai_strerror(int code)
     case SPAI_PENDING: return "request pending";
     case SPAI_ERR_INVALID_ARG: return "invalid argument";
     case SPAI_ERR_ZERO_ROW: return "a row of A has no nonzero entry (A is singular)";
-    case SPAI_ERR_NONFINITE: return "non-finite value (input, or overflow in u_f)";
+    case SPAI_ERR_NONFINITE: return "non-finite value (input, overflow in u_f, or a non-finite refinement iterate)";
     case SPAI_ERR_NO_MEMORY: return "device memory allocation failed";
     case SPAI_ERR_ADMISSION: return "request exceeds the context's HBM budget";
     case SPAI_ERR_TIMEOUT: return "a bounded device-side wait expired";
-    case SPAI_ERR_CUDA: return "CUDA runtime error";
+    case SPAI_ERR_CUDA: {
+        // the last CUDA error the library saw on the calling thread
+        static thread_local char buf[160];
+        if (g_last_cuda == cudaSuccess) return "CUDA runtime error";
+        snprintf(buf, sizeof(buf), "CUDA runtime error (last on this thread: %s)", cudaGetErrorName(g_last_cuda));
+        return buf;
+    }
     case SPAI_ERR_UNSUPPORTED: return "precision tuple or size not supported";
     case SPAI_ERR_NOT_FOUND: return "unknown ticket";
     case SPAI_ERR_INTERNAL: return "device-side consistency check failed";

@@ -64,3 +64,13 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "spai_ir_oracle" not in src, f
+
+
+def test_strerror_names_every_code():
+    import paper_2202_10204_gb300 as S
+    from paper_2202_10204_gb300 import _lib
+    codes = [0, 1, 2, 3] + [-i for i in range(1, 11)]
+    names = [S.strerror(c) for c in codes]
+    assert all(isinstance(n, str) and n and n != "unknown status" for n in names)
+    assert len(set(names)) == len(names)
+    assert S.strerror(-99) == "unknown status"
