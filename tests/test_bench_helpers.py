@@ -35,3 +35,21 @@ def test_ir_kernel_bytes_hand_example():
     b2 = bench.ir_kernel_bytes(10, 30, 40, [4])
     spmv = (30 * 8 + 11 * 8 + 10 * 8) + (40 * 8 + 11 * 8 + 10 * 4)
     assert b2 - b1 == spmv + (3 + 1) * 10 * 4 + 2 * 10 * 4 + 10 * 4
+
+
+def test_ir_kernel_bytes_scale_with_the_precisions():
+    # half-precision u_g and u_p (2 bytes) against single (4): every vector and matrix-value
+    # term halves, the column indices and row pointers do not
+    n, na, npp, its = 1000, 7000, 25000, [30, 20]
+    b4 = bench.ir_kernel_bytes(n, na, npp, its, s_u=4, s_g=4, s_p=4)
+    b2 = bench.ir_kernel_bytes(n, na, npp, its, s_u=4, s_g=2, s_p=2)
+    b8 = bench.ir_kernel_bytes(n, na, npp, its, s_u=4, s_g=8, s_p=8)
+    assert b2 < b4 < b8
+    assert b8 - b4 == 2 * (b4 - b2)  # linear in the element size
+
+
+def test_labels_name_the_grid():
+    m, w = bench.labels(64)
+    assert m == bench.METRIC and w == bench.WORKLOAD
+    m, w = bench.labels(32)
+    assert "32^3" in m and "64^3" not in m and "n=32768" in w
