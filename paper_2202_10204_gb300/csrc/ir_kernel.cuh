@@ -925,7 +925,8 @@ __device__ __forceinline__ void ir_body(const IrArgs& a, const int bid, const in
                     AG acca = (AG)wsm[ra - r0] / rr;
                     AG accb = hb ? (AG)wsm[rb2 - r0] / rr : AG(0);
                     const int64_t rbx = hb ? rb2 : ra;  // an in-range row for the second load
-#pragma unroll 8
+                    // (16 basis vectors unrolled: 32 loads of the two rows in flight)
+#pragma unroll 16
                     for (int i = 0; i < j; i++) {
                         const TG* Vi = V + (int64_t)i * a.ldv;
                         const AG h = hout[i];
