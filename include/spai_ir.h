@@ -329,7 +329,9 @@ int spai_selftest_wait_timeout(int device, int mode, double limit_ms);
  *          unpreconditioned.  Both are checked on the device first
  *          (SPAI_ERR_INVALID_ARG, SPAI_ERR_ZERO_ROW for an empty row of A).
  *   b, x : device float64 arrays of length n; x is output only.
- *   opts : as gmres_ir_solve (orth 0 and 1, both sides, every stop rule).
+ *   opts : as gmres_ir_solve (orth 0, 1 and 2, both sides, every stop rule),
+ *          except that u_g and u_p are single or double: half Krylov storage
+ *          returns SPAI_ERR_UNSUPPORTED here.
  *   cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).
  * The call reads sizes back to the host between its kernels, so it
  * synchronises the stream, and returns once x is complete.

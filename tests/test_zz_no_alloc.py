@@ -10,8 +10,10 @@ result against the allocating entry point (gmres_ir_solve with the same
 preconditioner), with the tolerance the other GPU tests use for refinement
 results (same step count, GMRES iterations within 10%, solution within 10 u
 of the reference relative to its norm), for left and right preconditioning,
-no preconditioner, and both Gram-Schmidt variants; and they check that the
-calls leave the device's free memory and torch's allocations unchanged.
+no preconditioner, and the three Arnoldi forms (MGS rounds, CGS2, one-reduction
+MGS); and they check that the calls leave the device's free memory and torch's
+allocations unchanged.  Half-precision Krylov storage is not offered here and
+is rejected.
 The file is collected last, and its tests pass alone or after the others.
 """
 import numpy as np
@@ -94,6 +96,17 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     Ad, bd = to_dev(A), torch.from_numpy(b).cuda()
     io = S.make_ir_opts(uf="single", u="double", ug="double", up="double", ur="double", tau=1e-8,
                         gmres_max_it=1000)
+    with pytest.raises(S.SpaiError) as e:
+        _lib.gmres_ir_solve_noalloc(Ad, bd, torch.zeros_like(bd), P=None, opts=io)
+    assert e.value.code == _lib.ERR_UNSUPPORTED
+
+
+def test_noalloc_rejects_half_krylov_storage():
+    # u_g = u_p = half is served by gmres_ir_solve only; the options are checked
+    # on the host before any device work
+    A, b, _ = synth.cfg_large_3d(N=8)
+    Ad, bd = to_dev(A), torch.from_numpy(b).cuda()
+    io = S.make_ir_opts(uf="half", u="single", ug="half", up="half", ur="double", tau=1e-2, orth=2)
     with pytest.raises(S.SpaiError) as e:
         _lib.gmres_ir_solve_noalloc(Ad, bd, torch.zeros_like(bd), P=None, opts=io)
     assert e.value.code == _lib.ERR_UNSUPPORTED
