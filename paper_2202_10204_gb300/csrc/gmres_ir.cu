@@ -1138,19 +1138,14 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     if (!A || !b || !xout || !o) return SPAI_ERR_INVALID_ARG;
     if (!A->on_device || (P && !P->on_device)) return SPAI_ERR_INVALID_ARG;
     if (A->n < 1 || A->nnz < 0 || !A->rowptr || !A->col || !A->val) return SPAI_ERR_INVALID_ARG;
-    if (o->side != 0 && o->side != 1) return SPAI_ERR_INVALID_ARG;
     if (P && (P->n != A->n || P->nnz < 0 || !P->rowptr || !P->col || !P->val)) return SPAI_ERR_INVALID_ARG;
     if (A->n > INT32_MAX) return SPAI_ERR_UNSUPPORTED;
-    if (o->u != SPAI_SINGLE && o->u != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (o->ug != SPAI_SINGLE && o->ug != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (o->up != SPAI_SINGLE && o->up != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (o->ur != SPAI_DOUBLE && o->ur != SPAI_QUAD) return SPAI_ERR_UNSUPPORTED;
-    if (o->uf != SPAI_HALF && o->uf != SPAI_SINGLE && o->uf != SPAI_DOUBLE) return SPAI_ERR_UNSUPPORTED;
-    if (o->ir_max_steps < 1 || o->ir_max_steps > SPAI_IR_MAX_STEPS) return SPAI_ERR_INVALID_ARG;
-    if (!(o->tau >= 0.0)) return SPAI_ERR_INVALID_ARG;
-    if (o->orth < 0 || o->orth > 2) return SPAI_ERR_INVALID_ARG;
-    if (o->stop != IR_STOP_BACKWARD && o->stop != IR_STOP_FIXED && o->stop != IR_STOP_CORRECTION)
-        return SPAI_ERR_INVALID_ARG;
+    // the options of gmres_ir_solve, less half Krylov storage
+    if (o->ug == SPAI_HALF || o->up == SPAI_HALF) return SPAI_ERR_UNSUPPORTED;
+    {
+        const int rc = ir_check_opts(o);
+        if (rc) return rc;
+    }
     const int64_t n = A->n;
     int kmax = o->gmres_max_it > 0 ? o->gmres_max_it : (int)std::min<int64_t>(n, 500);
     if (kmax > n) kmax = (int)n;
