@@ -183,7 +183,10 @@ typedef struct spai_precond_s* spai_precond;
 
 /* Create a context on `device` that runs on `cuda_stream` (a cudaStream_t;
  * NULL: the context creates its own).  hbm_budget_bytes bounds the device
- * memory the serving queue admits (0: 90% of free memory at creation). */
+ * memory the serving queue admits (0: 90% of free memory at creation).
+ * This call and every call given the context (or a preconditioner built on
+ * it) make its device current on the calling thread (cudaSetDevice) and leave
+ * it current when they return. */
 int spai_ctx_create(spai_ctx* out, int device, void* cuda_stream, size_t hbm_budget_bytes);
 /* Waits for the context's work, stops its serving workers and releases its
  * stream (if it created it).  Preconditioners it built stay valid and may be
