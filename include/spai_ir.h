@@ -325,7 +325,8 @@ int spai_selftest_wait_timeout(int device, int mode, double limit_ms);
  * gmres_ir_solve with a given preconditioner, but every scratch buffer lives
  * in one fixed device array of SPAI_NOALLOC_SCRATCH_BYTES (32 MiB) that each
  * GPU loading this library holds until the process exits.  It calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * cudaMalloc, cudaFree or other allocating routine.  It runs on the calling
+ * thread's current device, where A, P, b and x must reside.
  *   A, P : device CSR (on_device = 1); P holds the float64 entries of the
  *          left preconditioner (for instance spai_precond_export's output),
  *          or of the right one when opts->side = 1; P == NULL solves
