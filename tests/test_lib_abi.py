@@ -57,6 +57,59 @@ def test_binding_struct_layouts_match_header():
                                                    open(os.path.join(ROOT, "include", "spai_ir.h")).read()).group(1))
 
 
+def header_structs():
+    """{struct name: [field names in order]} of every typedef'd struct in the header."""
+    hdr = open(os.path.join(ROOT, "include", "spai_ir.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*([A-Za-z_]\w*)\s*;", hdr, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            first, *rest = [p.strip() for p in decl.split(",")]
+            fields.append(re.match(r"^.*?([A-Za-z_]\w*)\s*(\[[^\]]*\])?$", first).group(1))
+            fields += [re.match(r"^\**\s*([A-Za-z_]\w*)", p).group(1) for p in rest]
+        out[name] = fields
+    return out
+
+
+def test_binding_field_offsets_match_the_c_compiler(tmp_path):
+    # every field of every struct the header declares, at the offset and size the
+    # C compiler gives it, in the ctypes structure the binding passes across the ABI
+    import ctypes as C
+    import shutil
+    from paper_2202_10204_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = header_structs()
+    assert set(structs) >= {"spai_csr", "spai_opts", "ir_opts", "spai_stats", "ir_stats"}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "spai_ir.h"', "int main(void) {"]
+    for sname, fields in structs.items():
+        lines.append('    printf("%%s __size__ %%zu 0\\n", "%s", sizeof(%s));' % (sname, sname))
+        for f in fields:
+            lines.append('    printf("%%s %%s %%zu %%zu\\n", "%s", "%s", offsetof(%s, %s), sizeof(((%s*)0)->%s));'
+                         % (sname, f, sname, f, sname, f))
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        sname, f, off, size = line.split()
+        got[(sname, f)] = (int(off), int(size))
+    for sname, fields in structs.items():
+        cls = getattr(_lib, sname)
+        assert [f for f, *_ in cls._fields_] == fields, sname
+        assert C.sizeof(cls) == got[(sname, "__size__")][0], sname
+        for f in fields:
+            d = getattr(cls, f)
+            assert (d.offset, d.size) == got[(sname, f)], (sname, f)
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_2202_10204_gb300")
     for dirpath, _, files in os.walk(pkg):
