@@ -110,6 +110,43 @@ def test_binding_field_offsets_match_the_c_compiler(tmp_path):
             assert (d.offset, d.size) == got[(sname, f)], (sname, f)
 
 
+def header_constants():
+    """Names of the header's integer constants: its #defines and enumerators."""
+    hdr = open(os.path.join(ROOT, "include", "spai_ir.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    defines = re.findall(r"^#define[ \t]+([A-Z][A-Z0-9_]*)[ \t]+\S", hdr, flags=re.M)
+    enums = [n for body in re.findall(r"typedef enum\s*\{(.*?)\}", hdr, flags=re.S)
+             for n in re.findall(r"([A-Z][A-Z0-9_]*)\s*=", body)]
+    return defines + enums
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    # every status code, precision, pattern and stop-rule value the header defines has the
+    # same value under its binding name (SPAI_ prefix dropped, except SPAI_IR_MAX_STEPS)
+    import shutil
+    from paper_2202_10204_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = header_constants()
+    assert "SPAI_ERR_TIMEOUT" in names and "SPAI_HALF" in names and "IR_STOP_CORRECTION" in names
+    lines = ["#include <stdio.h>", '#include "spai_ir.h"', "int main(void) {"]
+    lines += ['    printf("%%s %%lld\\n", "%s", (long long)(%s));' % (n, n) for n in names]
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    values = dict((n, int(v)) for n, v in (line.split() for line in subprocess.run(
+        [str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()))
+    no_binding = {"SPAI_NOALLOC_SCRATCH_BYTES"}  # a size, documented in the header only
+    for n, v in values.items():
+        if n in no_binding:
+            continue
+        py = n if n == "SPAI_IR_MAX_STEPS" or not n.startswith("SPAI_") else n[len("SPAI_"):]
+        assert getattr(_lib, py) == v, n
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_2202_10204_gb300")
     for dirpath, _, files in os.walk(pkg):
