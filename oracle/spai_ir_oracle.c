@@ -933,7 +933,7 @@ typedef struct {
     int gmres_maxit;        /* per GMRES solve */
     int imax;               /* maximum number of refinement steps */
     double stop_tol;        /* R8 threshold of the stopping rule */
-    int orth;               /* 0 MGS, 1 CGS2 */
+    int orth;               /* 0 MGS, 1 CGS2, 2 one-reduction MGS */
     int side;               /* 0 left, 1 right preconditioning */
     int stop_rule;          /* STOP_BACKWARD, STOP_FIXED, STOP_CORRECTION */
     int kmode;              /* arithmetic mode of the Krylov part at u_g, u_p = half */
