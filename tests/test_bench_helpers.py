@@ -1,5 +1,6 @@
-"""Host-side helpers of bench.py: the nvidia-smi clock summary and the
-algorithmic-bytes model of the refinement kernel (CPU only)."""
+"""Host-side helpers of bench.py: the nvidia-smi clock summary, the
+algorithmic-bytes model of the refinement kernel, the backward error of the
+bench lines and the recipe of the 512-system batch (CPU only)."""
 import os
 import sys
 
@@ -53,3 +54,42 @@ def test_labels_name_the_grid():
     assert m == bench.METRIC and w == bench.WORKLOAD
     m, w = bench.labels(32)
     assert "32^3" in m and "64^3" not in m and "n=32768" in w
+
+
+def test_backward_error_definition():
+    import numpy as np
+    import scipy.sparse as sp
+    from paper_2202_10204_gb300 import synth
+    A = synth.random_sparse(50, 6, seed=3)
+    M = synth.to_scipy(A).toarray()
+    b = np.random.default_rng(1).normal(size=50)
+    # x = 0 leaves the whole of b: ||b|| / ||b|| = 1
+    assert bench.backward_error(A, b, np.zeros(50)) == 1.0
+    # an exactly representable solution of a diagonal system has no residual
+    D = synth._to_csr(sp.diags(np.full(8, 2.0)))
+    assert bench.backward_error(D, np.full(8, 3.0), np.full(8, 1.5)) == 0.0
+    # the normwise formula with dense numpy, and invariance under power-of-two scaling
+    x = np.linalg.solve(M, b) + 1e-6
+    ref = np.max(np.abs(b - M @ x)) / (np.max(np.abs(M).sum(axis=1)) * np.max(np.abs(x)) + np.max(np.abs(b)))
+    assert abs(bench.backward_error(A, b, x) - ref) <= 1e-12 * ref
+    assert bench.backward_error(A, 8.0 * b, 8.0 * x) == bench.backward_error(A, b, x)
+
+
+def test_batched_512_recipe():
+    # 512 systems, n log-uniform in [2e3, 5e4] (2D grids rounded to a square), even ones the
+    # 5-point convection-diffusion stencil, odd ones 8-16 nonzeros in every column; seeded
+    import numpy as np
+    from paper_2202_10204_gb300 import synth
+    batch = bench.batched_512_systems(synth)
+    assert len(batch) == 512
+    ns = np.array([len(A[0]) - 1 for A, _ in batch])
+    assert ns.min() >= 1900 and ns.max() <= 50000 and ns.sum() == 8336131
+    for i, (A, b) in enumerate(batch):
+        n = len(A[0]) - 1
+        assert len(b) == n
+        if i % 2 == 0:
+            N = int(round(np.sqrt(n)))
+            assert N * N == n and len(A[1]) == 5 * n - 4 * N
+        elif i % 64 == 1:  # column counts of a sample of the random systems
+            per_col = np.bincount(A[1], minlength=n)
+            assert per_col.min() == per_col.max() and 8 <= per_col[0] <= 16
