@@ -220,7 +220,8 @@ class Precond:
 
 
 def spai_build(ctx: Context, A, opts: spai_opts, per_column=False):
-    """Algorithm 1 on A^T D; returns (Precond, stats dict, return code)."""
+    """Algorithm 1 on A^T D; returns (Precond, stats dict), the call's return code under "rc"
+    (0, or SPAI_WARN_FILLCAP when some columns stopped at the fill cap)."""
     csr = make_csr(A)
     st = spai_stats()
     n = csr.n
