@@ -959,3 +959,33 @@ def test_half_krylov_refinement_is_scale_invariant(e):
     assert R0["status"] & O.IR_CONVERGED and R1["status"] & O.IR_CONVERGED
     assert list(R0["its"]) == list(R1["its"])
     assert np.array_equal(np.ldexp(R0["x"], e), R1["x"])
+
+
+@pytest.mark.parametrize("uf,u,tf,tu", [("half", "double", np.float16, np.float64),
+                                        ("single", "double", np.float32, np.float64),
+                                        ("double", "single", np.float64, np.float32),
+                                        ("half", "single", np.float16, np.float32)])
+def test_x0_is_b_rounded_to_u_f_then_u_without_preconditioner(uf, u, tf, tu):
+    # Algorithm 3, line 2 with P = I: x0 = P b computed in u_f and stored in u, which for
+    # A = I is b rounded to u_f and then to u (numpy's IEEE conversions); imax = 0 returns x0
+    n = 64
+    b = np.random.default_rng(3).normal(size=n)
+    eye = synth._to_csr(sp.eye(n, format="csr"))
+    R = O.gmres_ir(eye, b, None, uf=uf, u=u, ug="double", up="double", ur="quad", imax=0)
+    assert R["steps"] == 0
+    assert np.array_equal(R["x"], b.astype(tf).astype(tu).astype(np.float64))
+
+
+def test_x0_uses_the_u_f_copy_of_P():
+    # reading R9: x0 = P b takes P's values in u_f, GMRES its values in u_p.  The two copies
+    # are given different values (powers of two and small integers, so every product is
+    # exact in half), and x0 shows which copy was used
+    rng = np.random.default_rng(4)
+    n = 32
+    a = 2.0 ** rng.integers(-3, 4, size=n)
+    b = rng.integers(-8, 9, size=n).astype(np.float64)
+    A = synth._to_csr(sp.diags(a, format="csr"))
+    rp, ci = np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32)
+    P = (rp, ci, 1.0 / a, 2.0 / a)  # (structure, values in u_p, values in u_f)
+    R = O.gmres_ir(A, b, P, uf="half", u="double", ug="double", up="double", ur="quad", imax=0)
+    assert np.array_equal(R["x"], 2.0 * b / a)
