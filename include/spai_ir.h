@@ -276,8 +276,11 @@ int gmres_ir_solve_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_
                          ir_stats* st, int* status);
 
 /* Serving queue with continuous batching.  solver_submit copies A and b
- * (host or device, as A->on_device says) into the context and returns a
- * ticket at once.  An admission thread admits every waiting request whose
+ * (host or device, as A->on_device says) into host memory the context owns
+ * and returns a ticket; the caller's buffers may be reused once it returns.
+ * Device inputs are copied with synchronous device-to-host copies (so that a
+ * waiting request holds no device memory outside the admission budget) and
+ * checked on the host.  An admission thread admits every waiting request whose
  * estimated device footprint fits what the context's HBM budget has left (a
  * request passed over for more than 200 ms is admitted before any later
  * one), uploads the admitted requests and builds their preconditioners
