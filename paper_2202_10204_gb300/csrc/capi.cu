@@ -1169,11 +1169,15 @@ int solver_submit(spai_ctx ctx, const spai_csr* A, const double* b, const spai_o
         std::lock_guard<std::mutex> lk(ctx->qmu);
         if (ctx->workers.empty()) {
             cudaSetDevice(ctx->device);
+            cudaStream_t ws[2] = {nullptr, nullptr};
             for (int i = 0; i < 2; i++) {
-                cudaStream_t s;
-                if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) { delete r; return SPAI_ERR_CUDA; }
-                ctx->worker_streams.push_back(s);
+                if (cudaStreamCreateWithFlags(&ws[i], cudaStreamNonBlocking) != cudaSuccess) {
+                    for (int k = 0; k < i; k++) cudaStreamDestroy(ws[k]);  // a later submit starts afresh
+                    delete r;
+                    return SPAI_ERR_CUDA;
+                }
             }
+            ctx->worker_streams.assign(ws, ws + 2);
             ctx->workers.emplace_back(serve_admission_loop, ctx);
             ctx->workers.emplace_back(serve_refine_loop, ctx);
         }
