@@ -1181,8 +1181,10 @@ extern "C" int gmres_ir_solve_noalloc(const spai_csr* A, const spai_csr* P, cons
     int64_t* poff = P ? (int64_t*)cv.take(sizeof(int64_t) * (nsl + 1)) : nullptr;
     int32_t* pw = P ? (int32_t*)cv.take(sizeof(int32_t) * nsl) : nullptr;
     // CGS2: the partial dot products of every block and the counter of their barrier
-    void* pvec = o->orth ? cv.take((size_t)sg * (2 * MAX_GRID + (o->orth == 2 ? 2 : 0)) * (kmax + 1)) : nullptr;
-    void* Lrows = o->orth == 2 ? cv.take((size_t)sg * ((size_t)(kmax + 1) * kmax / 2 + 1)) : nullptr;
+    // (scalars in u_g's arithmetic type, as the allocating path sizes them)
+    void* pvec = o->orth ? cv.take((size_t)ir_scalar_bytes(sg) * (2 * MAX_GRID + (o->orth == 2 ? 2 : 0)) * (kmax + 1))
+                         : nullptr;
+    void* Lrows = o->orth == 2 ? cv.take((size_t)ir_scalar_bytes(sg) * ((size_t)(kmax + 1) * kmax / 2 + 1)) : nullptr;
     double* gpub = o->orth == 2 ? (double*)cv.take(sizeof(double) * (kmax + 2)) : nullptr;
     if (!msg || !ctrl || !x || !r || !wbuf || !tbuf || !V || !R || !aoff || !aw || (P && (!poff || !pw)) ||
         (o->orth && !pvec) || (o->orth == 2 && (!Lrows || !gpub)))
