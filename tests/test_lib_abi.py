@@ -147,6 +147,20 @@ def test_binding_constants_match_the_header(tmp_path):
         assert getattr(_lib, py) == v, n
 
 
+def test_package_exports_every_status_code_and_entry_point():
+    import paper_2202_10204_gb300 as S
+    from paper_2202_10204_gb300 import _lib
+    codes = [n for n in header_constants() if n.startswith(("SPAI_ERR_", "SPAI_WARN_")) or n in ("SPAI_OK",
+                                                                                                "SPAI_PENDING")]
+    for n in codes:
+        assert getattr(S, n[len("SPAI_"):]) == getattr(_lib, n[len("SPAI_"):]), n
+    for name in ("gmres_ir_solve", "gmres_ir_solve_batch", "gmres_ir_solve_noalloc", "spai_build",
+                 "spai_build_batch", "solver_submit", "solver_poll", "strerror", "tune_get", "tune_set",
+                 "selftest_wait_timeout", "Context", "Precond"):
+        assert getattr(S, name) is getattr(_lib, name), name
+    assert set(S.__all__) <= set(dir(S))
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_2202_10204_gb300")
     for dirpath, _, files in os.walk(pkg):
