@@ -237,13 +237,18 @@ int spai_build_batch(spai_ctx ctx, int count, const spai_csr* A, const spai_opts
 int spai_tune_get(int device, int uf, int bin);
 int spai_tune_set(int device, int uf, int bin, int variant);
 
-/* Size of P: *n and *nnz (either may be NULL). */
+/* Size of P: *n and *nnz (either may be NULL).  SPAI_ERR_INVALID_ARG for a
+ * NULL P. */
 int spai_precond_info(spai_precond P, int64_t* n, int64_t* nnz);
 
-/* Copy P to host buffers: rowptr[n+1], col[nnz], val[nnz] (float64, the
- * unrounded values mbar_k * d(J_k)); any pointer may be NULL. */
+/* Copy P to host buffers the caller owns: rowptr[n+1], col[nnz], val[nnz]
+ * (float64, the unrounded values mbar_k * d(J_k)); any pointer may be NULL.
+ * Waits for P's stream; SPAI_ERR_INVALID_ARG for a NULL P, SPAI_ERR_CUDA if a
+ * copy fails. */
 int spai_precond_export(spai_precond P, int64_t* rowptr, int32_t* col, double* val);
 
+/* Release P's device memory (after the work queued on its stream); P must not
+ * be used afterwards.  NULL is ignored. */
 void spai_precond_free(spai_precond P);
 
 /* Algorithm 3 (SPAI-GMRES-IR).  P: a preconditioner from spai_build; if NULL
