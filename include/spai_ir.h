@@ -14,9 +14,10 @@
  * Conventions for every entry point:
  *   - return value 0 is success, > 0 a warning, < 0 an error (SPAI_* codes);
  *     spai_strerror() names each code.  No entry point aborts the process.
- *   - the caller owns every buffer it passes; the library never frees or
- *     keeps a caller pointer beyond the call, except solver_submit, which
- *     copies its inputs before returning.
+ *   - the caller owns every buffer it passes; the library never frees a
+ *     caller buffer nor keeps a caller pointer beyond the call (solver_submit
+ *     copies its inputs before it returns, solver_poll writes x during its
+ *     own call).
  *   - CSR arrays: rowptr[n+1] int64 (rowptr[0] = 0, non-decreasing), col[nnz]
  *     int32 in [0, n) sorted ascending within a row, val[nnz] float64.
  *     With on_device = 1 all three are device pointers on the context's
@@ -24,7 +25,7 @@
  *     (SPAI_ERR_INVALID_ARG for a structural error, which takes precedence
  *     over SPAI_ERR_ZERO_ROW for an empty row) before any kernel indexes
  *     with it: one pass over the rows on the device (for host inputs after
- *     the copy).
+ *     the copy; solver_submit checks its host copy on the host).
  *   - all work runs on the context's CUDA stream on one GPU; every call
  *     returns after its results are complete.
  *   - calls on one context are serialised by the context; distinct contexts
