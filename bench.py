@@ -210,11 +210,12 @@ def run_reference(args):
     sample = ("one full oracle SPAI-GMRES-IR solve of the %d^3 system (n=%d) split into %d steps: SPAI columns in %d "
               "slices on %d threads (OpenMP), then assembly and the serial refinement (%s iterations); value = 1 / "
               "total time" % (args.grid, n_full, K, max(1, K - 1), th, list(map(int, R["its"]))))
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=K, warmup=args.warmup,
+    metric, workload = labels(args.grid)
+    line = dict(metric=metric, value=value, unit=UNIT, n_gpus=args.gpus, steps=K, warmup=args.warmup,
                 ms_per_step=1000 * tot / K, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64 (u_f half, u single, u_g/u_p single, u_r double, simulated)", data="synthetic",
                 impl="reference",
-                config=dict(workload=WORKLOAD, n=n_full, tuple=TUPLE, tau=TAU, orth=ORTH),
+                config=dict(workload=workload, n=n_full, tuple=TUPLE, tau=TAU, orth=ORTH),
                 cpu_baseline=dict(value=value, unit=UNIT, cores=th, kind="oracle", sample=sample,
                                   nproc=nproc()),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -273,7 +274,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) of one k_ir launch (one-reduction MGS) on the 64^3 workload, from one
 # ncu capture of the current kernel build (dram__bytes_read.sum + dram__bytes_write.sum, one pass,
-# a timed launch): 4.090 GB read + 0.222 GB written against 13.6 GB algorithmic; A, P and the
+# a timed launch): 4.24 GB read + 0.22 GB written against 13.6 GB algorithmic; A, P and the
 # recent basis vectors are served from L2.
 K_IR_DRAM_BYTES_64CUBE = 4.464e9
 

@@ -93,3 +93,29 @@ def test_batched_512_recipe():
         elif i % 64 == 1:  # column counts of a sample of the random systems
             per_col = np.bincount(A[1], minlength=n)
             assert per_col.min() == per_col.max() and 8 <= per_col[0] <= 16
+
+
+def test_reference_arm_line_contract():
+    # the reference arm times the oracle (CPU): one JSON line with the contract's keys, the
+    # same metric labels as the main arm for the grid, a cpu_baseline describing the run and
+    # an e2e object with no host-device copies; other ranks exit 0 without work
+    import json
+    import subprocess
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--grid", "10", "--steps", "2",
+           "--warmup", "3"]
+    out = subprocess.run(cmd, capture_output=True, text=True, check=True, cwd=ROOT, timeout=600).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert (d["metric"], d["config"]["workload"]) == bench.labels(10) and d["config"]["n"] == 1000
+    assert d["value"] > 0 and abs(d["ms_per_step"] * d["steps"] / 1000.0 - 1.0 / d["value"]) < 1e-9 / d["value"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == dict(value=d["value"], unit=d["unit"], h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
+    assert r.returncode == 0 and not [l for l in r.stdout.splitlines() if l.startswith("{")]
