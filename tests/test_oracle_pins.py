@@ -989,3 +989,15 @@ def test_x0_uses_the_u_f_copy_of_P():
     P = (rp, ci, 1.0 / a, 2.0 / a)  # (structure, values in u_p, values in u_f)
     R = O.gmres_ir(A, b, P, uf="half", u="double", ug="double", up="double", ur="quad", imax=0)
     assert np.array_equal(R["x"], 2.0 * b / a)
+
+
+@pytest.mark.parametrize("orth", [O.ORTH_MGS, O.ORTH_CGS2])
+def test_half_storage_mode_is_refused_outside_the_one_reduction_form(orth):
+    # the binary32-arithmetic model of half Krylov storage (R17) is defined for the
+    # one-reduction MGS only: the other forms must refuse it, not run another model silently
+    A, b, _ = synth.cfg_small_2d()
+    with pytest.raises(ValueError):
+        O.gmres_ir(A, b, None, uf="single", u="double", ug="half", up="single", ur="double", tau=1e-2,
+                   orth=orth, kmode=O.MODE_ACC32)
+    with pytest.raises(ValueError):
+        O.gmres(A, b, None, ug="single", up="half", tau=1e-2, orth=orth, kmode=O.MODE_ACC32)
