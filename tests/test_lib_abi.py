@@ -161,6 +161,37 @@ def test_package_exports_every_status_code_and_entry_point():
     assert set(S.__all__) <= set(dir(S))
 
 
+def test_argument_checks_return_before_any_device_work(built_lib):
+    # NULL handles and out-of-range options are refused with SPAI_ERR_INVALID_ARG before any
+    # CUDA call (so these run without a GPU); the tuner's table is host state
+    import torch  # noqa: F401  (provides the CUDA runtime the library links)
+    from paper_2202_10204_gb300 import _lib
+    L, E = _lib.lib(), _lib.ERR_INVALID_ARG
+    assert L.spai_ctx_create(None, 0, None, 0) == E
+    assert L.spai_build(None, None, None, None, None) == E
+    assert L.spai_build_batch(None, 0, None, None, None, None, None) == E
+    assert L.gmres_ir_solve(None, None, None, None, None, None, None, None) == E
+    assert L.gmres_ir_solve_batch(None, 0, None, None, None, None, None, None, None) == E
+    assert L.gmres_ir_solve_noalloc(None, None, None, None, None, None, None) == E
+    assert L.solver_submit(None, None, None, None, None, None) == E
+    assert L.solver_poll(None, 0, None, None) == E
+    assert L.spai_precond_info(None, None, None) == E
+    assert L.spai_precond_export(None, None, None, None) == E
+    for mode, limit in ((2, 50.0), (0, 0.0), (0, -1.0), (0, 2e4)):
+        assert L.spai_selftest_wait_timeout(0, mode, limit) == E
+    L.spai_ctx_destroy(None)
+    L.spai_precond_free(None)
+    for bad in ((0, 1, 1), (0, 1, 14), (0, 7, 5), (0, _lib.QUAD, 5)):
+        assert L.spai_tune_get(*bad) == E
+        assert L.spai_tune_set(*bad, 0) == E
+    assert L.spai_tune_set(0, _lib.SINGLE, 5, 4) == E and L.spai_tune_set(0, _lib.SINGLE, 5, -2) == E
+    dev = 97  # a device index no test builds on
+    assert L.spai_tune_get(dev, _lib.HALF, 5) == -1
+    assert L.spai_tune_set(dev, _lib.HALF, 5, 2) == 0 and L.spai_tune_get(dev, _lib.HALF, 5) == 2
+    assert L.spai_tune_get(dev, _lib.SINGLE, 5) == -1 and L.spai_tune_get(dev, _lib.HALF, 6) == -1
+    assert L.spai_tune_set(dev, _lib.HALF, 5, -1) == 0 and L.spai_tune_get(dev, _lib.HALF, 5) == -1
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_2202_10204_gb300")
     for dirpath, _, files in os.walk(pkg):
