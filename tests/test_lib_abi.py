@@ -192,6 +192,19 @@ def test_argument_checks_return_before_any_device_work(built_lib):
     assert L.spai_tune_set(dev, _lib.HALF, 5, -1) == 0 and L.spai_tune_get(dev, _lib.HALF, 5) == -1
 
 
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library every entry point raises
+    from paper_2202_10204_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent" / "libspai_ir.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.lib()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.Context(0)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.strerror(0)
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_2202_10204_gb300")
     for dirpath, _, files in os.walk(pkg):
