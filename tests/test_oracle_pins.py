@@ -31,7 +31,8 @@ def test_chop_half_matches_numpy_float16_conversion():
     # exact ties at half precision (odd multiples of half a quantum)
     ties = (rng.integers(0, 2 ** 11, size=5000) * 2 + 1) * 2.0 ** -12
     x = np.concatenate([x, ties, -ties, [65504.0, 65519.99, 65520.0, 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26, 0.0]])
-    ref = x.astype(np.float16).astype(np.float64)
+    with np.errstate(over="ignore"):  # the overflow range is part of the comparison
+        ref = x.astype(np.float16).astype(np.float64)
     got = O.chop_half(x)
     assert np.array_equal(np.isinf(got), np.isinf(ref))
     fin = np.isfinite(ref)
