@@ -66,6 +66,7 @@ class IrOpts(C.Structure):
 
 
 def lib():
+    """The compiled oracle (built on first use)."""
     global _lib
     with _lock:
         if _lib is None:
@@ -95,16 +96,20 @@ def _csr(A):
 
 
 def prec(p) -> int:
+    """Precision code of a name ("half", "single", "double", "quad") or of a code."""
     return PREC_NAMES[p] if isinstance(p, str) else int(p)
 
 
 def chop_half(x):
+    """Round to IEEE binary16, round-to-nearest-even with subnormals and overflow to
+    infinity: the chop model of half precision the paper's experiments use (Section 4)."""
     L = lib()
     x = np.asarray(x, dtype=np.float64)
     return np.vectorize(L.orc_chop_half, otypes=[np.float64])(x) if x.ndim else L.orc_chop_half(float(x))
 
 
 def round_to(x, p):
+    """Round every entry to precision p (Table 1's formats; half by chop_half)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     out = np.empty_like(x)
     lib().orc_round_array(C.c_int64(x.size), _p(x, C.c_double), C.c_int(prec(p)), _p(out, C.c_double))
@@ -112,6 +117,10 @@ def round_to(x, p):
 
 
 def half_ops(a, b, op: int):
+    """One half-precision operation per entry pair (op 0 +, 1 -, 2 *, 3 /, other sqrt|a|):
+    operands rounded to binary16, the result computed in double (exact for + - *, and the
+    second rounding of / and sqrt is innocuous since 53 >= 2 * 11 + 2) and rounded to binary16,
+    the per-operation model of Section 4."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     out = np.empty_like(a)
@@ -141,6 +150,9 @@ def dense_ls(Abar, ebar, uf="double", mode=MODE_ACC32):
 
 
 def rho(A, d, I, s, cand, uf="double", rho_restricted=False):
+    """Candidate scores rho_j of the Grote-Huckle augmentation (Algorithm 1; reading R3):
+    the norm of the residual s after its one-dimensional minimisation along column j of
+    B = A^T D, rho_j^2 = ||s||^2 - (s^T b_j)^2 / ||b_j||^2."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     I = np.ascontiguousarray(I, dtype=np.int32)
@@ -155,6 +167,8 @@ def rho(A, d, I, s, cand, uf="double", rho_restricted=False):
 
 
 def select(cand, rho_vals, nmax, uf="double"):
+    """Indices Algorithm 1 adds (reading R4): of the candidates with rho at most the
+    mean, the nmax smallest rho, ties to the smaller index."""
     cand = np.ascontiguousarray(cand, dtype=np.int32)
     rv = np.ascontiguousarray(rho_vals, dtype=np.float64)
     sel = np.zeros(max(nmax, 1), dtype=np.int32)
@@ -244,6 +258,8 @@ def spai_right(A, up="double", uf=None, **kw):
 
 
 def spmv(A, x, p="double", mode=MODE_PEROP):
+    """y = A x in precision p (the products of Algorithm 3 in u_p; mode selects
+    per-operation rounding or binary32 accumulation for half)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     x = np.ascontiguousarray(x, dtype=np.float64)
@@ -254,6 +270,7 @@ def spmv(A, x, p="double", mode=MODE_PEROP):
 
 
 def residual(A, b, x, ur="double", u="double"):
+    """r = b - A x computed in u_r and stored in u (Algorithm 3, residual line)."""
     rp, ci, va = _csr(A)
     n = len(rp) - 1
     b = np.ascontiguousarray(b, dtype=np.float64)
