@@ -158,6 +158,9 @@ double orc_chop_half(double x)
     return x < 0 ? -q : q;
 }
 
+/* x rounded to precision p (Table 1): half by chop, single by the IEEE
+ * conversion to float (round-to-nearest-even), double and quad unchanged
+ * (quad values are carried as _Float128 where they occur). */
 static double rnd(double x, int p)
 {
     switch (p) {
@@ -167,6 +170,7 @@ static double rnd(double x, int p)
     }
 }
 
+/* rnd, exported for the pins. */
 double orc_round(double x, int p) { return rnd(x, p); }
 
 /* out[i] = x[i] rounded to p, i < n */
@@ -301,6 +305,7 @@ static int sort_unique(int* v, int len)
     return w;
 }
 
+/* Position of key in the ascending v[0..len), -1 if absent (binary search). */
 static int find_sorted(const int* v, int len, int key)
 {
     int lo = 0, hi = len - 1;
@@ -336,6 +341,9 @@ static int cmp_cap(const void* a, const void* b)
     return (x > y) - (x < y);
 }
 
+/* The fill cap of reading R6: a pattern longer than max_fill keeps the
+ * max_fill indices nearest to k (k itself first, ties to the smaller
+ * index), returned in ascending order. */
 static int apply_cap(int* J, int len, int k, int max_fill)
 {
     if (len <= max_fill) return len;
@@ -811,6 +819,10 @@ static int gmres_icwy(int n, const int64_t* arp, const int* aci, const double* a
     return k;
 }
 
+/* One GMRES solve (Algorithm 3, GMRES line; reading R7) in the Arnoldi form
+ * o->orth selects: MGS (0) and CGS2 (1) here, the one-reduction MGS (2) in
+ * gmres_icwy.  Returns the iterations taken, or -1 for the half-storage
+ * model outside the one-reduction form. */
 int orc_gmres(int n, const int64_t* arp, const int* aci, const double* av,
               const int64_t* prp, const int* pci, const double* pv,
               const double* r, const orc_gmres_opts* o, double* d, int* breakdown, double* relres)
