@@ -33,6 +33,8 @@ EXPORTED = ("spai_ctx_create", "spai_ctx_destroy", "spai_build", "spai_precond_i
 
 
 class spai_csr(C.Structure):
+    """CSR matrix of include/spai_ir.h: int64 rowptr[n+1], int32 col[nnz], float64 val[nnz];
+    on_device = 1 for device pointers."""
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
                 ("val", C.c_void_p), ("on_device", C.c_int)]
 
@@ -41,18 +43,23 @@ SIDE_LEFT, SIDE_RIGHT = 0, 1
 
 
 class spai_opts(C.Structure):
+    """Options of Algorithm 1 (pattern, adaptive Grote-Huckle, eps, alpha, beta, fill cap, u_f,
+    scaling, rho reading, side); built by make_spai_opts."""
     _fields_ = [("init", C.c_int), ("adaptive", C.c_int), ("eps", C.c_double), ("alpha", C.c_int),
                 ("beta", C.c_int), ("max_fill", C.c_int), ("uf", C.c_int), ("scale", C.c_int),
                 ("rho_restricted", C.c_int), ("side", C.c_int)]
 
 
 class ir_opts(C.Structure):
+    """Options of Algorithm 3 (the five precisions, tau, iteration limits, stop rule, Arnoldi form,
+    side); built by make_ir_opts."""
     _fields_ = [("uf", C.c_int), ("u", C.c_int), ("ug", C.c_int), ("up", C.c_int), ("ur", C.c_int),
                 ("tau", C.c_double), ("gmres_max_it", C.c_int), ("ir_max_steps", C.c_int), ("stop", C.c_int),
                 ("stop_tol", C.c_double), ("orth", C.c_int), ("side", C.c_int)]
 
 
 class spai_stats(C.Structure):
+    """Statistics of one SPAI build, with optional per-column host arrays."""
     _fields_ = [("n", C.c_int64), ("nnz_P", C.c_int64), ("cols_converged", C.c_int64),
                 ("cols_fillcap", C.c_int64), ("cols_nonfinite", C.c_int64), ("max_I", C.c_int),
                 ("max_J", C.c_int), ("ms", C.c_double), ("ms_kernel", C.c_double), ("launches", C.c_int),
@@ -60,6 +67,7 @@ class spai_stats(C.Structure):
 
 
 class ir_stats(C.Structure):
+    """Statistics of one refinement solve: steps, GMRES iterations per step, backward errors."""
     _fields_ = [("steps", C.c_int), ("total_its", C.c_int), ("its", C.c_int * SPAI_IR_MAX_STEPS),
                 ("nbe", C.c_double * (SPAI_IR_MAX_STEPS + 1)), ("final_nbe", C.c_double), ("flags", C.c_int),
                 ("nnz_P", C.c_int64), ("ms_spai", C.c_double), ("ms_ir", C.c_double),
@@ -109,10 +117,13 @@ def lib():
 
 
 def strerror(code: int) -> str:
+    """The library's description of a status code (spai_strerror)."""
     return lib().spai_strerror(int(code)).decode()
 
 
 class SpaiError(RuntimeError):
+    """A negative status from the library; .code holds it."""
+
     def __init__(self, code, where):
         super().__init__("%s: %s (%d)" % (where, strerror(code), code))
         self.code = code
@@ -189,6 +200,8 @@ class Context:
 
 
 class Precond:
+    """A preconditioner P = M^T D on the device (spai_build); free() releases it."""
+
     def __init__(self, h, ctx=None):
         self.h = h
         self.ctx = ctx  # keeps the building context alive while the handle lives
@@ -313,6 +326,7 @@ def gmres_ir_solve_batch(ctx: Context, As, bs, xs, Ps=None, opts: ir_opts | None
 
 
 def solver_submit(ctx: Context, A, b, sopts: spai_opts | None, opts: ir_opts) -> int:
+    """Queue one solve on the serving queue (continuous batching); returns its ticket."""
     csr = make_csr(A)
     t = C.c_uint64()
     _check(lib().solver_submit(ctx.h, C.byref(csr), _ptr(b), C.byref(sopts) if sopts is not None else None,
